@@ -1,0 +1,348 @@
+"""FP64 CPU oracle of the meshless RBF leapfrog (test infrastructure only).
+
+Only tests/, ``__graft_entry__.smoke()`` and bench.py's ``cpu_baseline`` /
+``--impl reference`` legs may import this package. It never imports the CUDA
+package and the CUDA package never imports it. The arithmetic lives in
+``oracle.c`` (plain C, FP64, stencil sums in stencil order); this module only
+marshals arrays and assembles problems from its functions.
+
+Pins that tie the oracle to the paper and to mathematics live in
+``tests/test_oracle_*.py``. Every function here is pinned there.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+
+OP_GRAD, OP_LAP_POW, OP_GRAD_VFD = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compiles oracle.c into oracle/_build/liboracle.so (gcc, FP64, no FMA contraction)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _SO + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC",
+                           "-o", tmp, src, "-lm"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _lib.orc_energy_tmz.restype = C.c_double
+        _lib.orc_ricker.restype = C.c_double
+        _lib.orc_ricker.argtypes = [C.c_double] * 3
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i64(a):
+    return np.ascontiguousarray(a, dtype=np.int64)
+
+
+def _check(st, what):
+    if st != 0:
+        raise RuntimeError(f"oracle {what} failed with status {st}")
+
+
+def threads() -> int:
+    """OpenMP threads the oracle uses (OMP_NUM_THREADS, else all cores)."""
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v else (os.cpu_count() or 1)
+
+
+# ------------------------------------------------------------------ O-1
+
+def knn_brute(centres, sources, period, n):
+    centres, sources = _f64(centres), _f64(sources)
+    d = centres.shape[1]
+    out = np.empty((centres.shape[0], n), dtype=np.int64)
+    _check(lib().orc_knn_brute(C.c_int(d), C.c_int64(len(centres)), _p(centres),
+                               C.c_int64(len(sources)), _p(sources), _p(_f64(period)),
+                               C.c_int(n), _p(out)), "knn_brute")
+    return out
+
+
+def knn_cells(centres, sources, period, n, cell=1.0):
+    centres, sources = _f64(centres), _f64(sources)
+    d = centres.shape[1]
+    out = np.empty((centres.shape[0], n), dtype=np.int64)
+    _check(lib().orc_knn_cells(C.c_int(d), C.c_int64(len(centres)), _p(centres),
+                               C.c_int64(len(sources)), _p(sources), _p(_f64(period)),
+                               C.c_int(n), C.c_double(cell), _p(out)), "knn_cells")
+    return out
+
+
+def knn(centres, sources, period, n):
+    """Brute force for small inputs, the cell list otherwise (same result)."""
+    if len(centres) * len(sources) <= 4_000_000:
+        return knn_brute(centres, sources, period, n)
+    return knn_cells(centres, sources, period, n)
+
+
+# ------------------------------------------------------------------ O-2
+
+def monomials(dim, m):
+    e = np.zeros((512, 3), dtype=np.int32)
+    q = lib().orc_monomials(C.c_int(dim), C.c_int(m), _p(e))
+    return e[:q, :dim].copy()
+
+
+def stencil_weights(rel, phs_k, poly_m, op, alpha=0, delta=0.0):
+    """Weights of one stencil from offsets rel (n x d) = x_j - x_c. Returns (nout, n)."""
+    rel = _f64(rel)
+    n, d = rel.shape
+    nout = 1 if op == OP_LAP_POW else d
+    w = np.empty((nout, n))
+    _check(lib().orc_stencil_weights(C.c_int(d), C.c_int(n), _p(rel), C.c_int(phs_k),
+                                     C.c_int(poly_m), C.c_int(op), C.c_int(alpha),
+                                     C.c_double(delta), _p(w)), "stencil_weights")
+    return w
+
+
+def weights(xc, xs, period, idx, n_use, phs_k, poly_m, op, alpha=0, delta=0.0):
+    """Weights for every centre on the first n_use entries of idx. Returns (nout, nc, n_use)."""
+    xc, xs, idx = _f64(xc), _f64(xs), _i64(idx)
+    nc, stride = idx.shape
+    d = xc.shape[1]
+    nout = 1 if op == OP_LAP_POW else d
+    w = np.empty((nout, nc, n_use))
+    _check(lib().orc_weights(C.c_int(d), C.c_int64(nc), _p(xc), _p(xs), _p(_f64(period)),
+                             C.c_int(stride), C.c_int(n_use), _p(idx), C.c_int(phs_k),
+                             C.c_int(poly_m), C.c_int(op), C.c_int(alpha), C.c_double(delta),
+                             _p(w)), "weights")
+    return w
+
+
+def gepp(A, B):
+    A = _f64(A).copy()
+    B = _f64(B).reshape(A.shape[0], -1).copy()
+    _check(lib().orc_gepp(C.c_int(A.shape[0]), _p(A), C.c_int(B.shape[1]), _p(B)), "gepp")
+    return B
+
+
+def ricker(t, f0, t0):
+    return lib().orc_ricker(float(t), float(f0), float(t0))
+
+
+# ------------------------------------------------------------------ problems
+
+@dataclass
+class Stencil:
+    """Stencil of one operator family: idx (N x n, ids into the source set) and weights."""
+
+    idx: np.ndarray
+    w: np.ndarray  # (nout, N, n)
+
+
+@dataclass
+class TMz:
+    """A TMz problem: H node set, E node set (the same object when collocated)."""
+
+    nh: int
+    ne: int
+    hc: Stencil  # H nodes <- E set, d/dx, d/dy
+    hv: Stencil  # H nodes <- H set, Delta^alpha
+    ec: Stencil  # E nodes <- H set, d/dx, d/dy
+    ev: Stencil  # E nodes <- E set, Delta^alpha
+    eps_r: np.ndarray
+    pec: np.ndarray
+    dt: float
+    eps0: float
+    mu0: float
+    gamma: float
+
+
+def _stencil(xc, xs, period, idx, n_use, phs_k, m, op, alpha=0, delta=0.0):
+    idx = _i64(idx)
+    w = weights(xc, xs, period, idx, n_use, phs_k, m, op, alpha, delta)
+    return Stencil(idx=np.ascontiguousarray(idx[:, :n_use]), w=w)
+
+
+def tmz_collocated(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=None, vfd_delta=None,
+                   nh_override=None):
+    """Collocated TMz problem (the paper's layout): one kNN list serves both
+    the curl stencil (its first n entries) and the HV stencil
+    (n_HV = 2 M_{2 alpha} + 1 entries, PHS r^{2 alpha + 1}, monomials up to 2 alpha)."""
+    import math
+    d = nodes.dim
+    nhv = nh_override or (2 * math.comb(2 * alpha + d, d) + 1)
+    L = max(n, nhv)
+    idx = knn(nodes.xyz, nodes.xyz, nodes.period, L)
+    if vfd_delta is None:
+        curl = _stencil(nodes.xyz, nodes.xyz, nodes.period, idx, n, phs_k, m, OP_GRAD)
+    else:
+        curl = _stencil(nodes.xyz, nodes.xyz, nodes.period, idx, n, phs_k, m, OP_GRAD_VFD, 0,
+                        vfd_delta)
+    hv = _stencil(nodes.xyz, nodes.xyz, nodes.period, idx, nhv, 2 * alpha + 1, 2 * alpha,
+                  OP_LAP_POW, alpha)
+    er = np.ones(nodes.n) if eps_r is None else _f64(eps_r)
+    return TMz(nh=nodes.n, ne=nodes.n, hc=curl, hv=hv, ec=curl, ev=hv, eps_r=er,
+               pec=np.ascontiguousarray(nodes.pec, dtype=np.uint8), dt=dt, eps0=eps0, mu0=mu0,
+               gamma=gamma), idx
+
+
+def tmz_staggered(e_nodes, h_nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=None):
+    """Staggered TMz problem: curl stencils are the n nearest nodes of the other
+    set; HV stencils are own-set (n_HV = 2 M_{2 alpha} + 1)."""
+    import math
+    d = e_nodes.dim
+    nhv = 2 * math.comb(2 * alpha + d, d) + 1
+    per = e_nodes.period
+    i_he = knn(h_nodes.xyz, e_nodes.xyz, per, n)
+    i_hh = knn(h_nodes.xyz, h_nodes.xyz, per, nhv)
+    i_eh = knn(e_nodes.xyz, h_nodes.xyz, per, n)
+    i_ee = knn(e_nodes.xyz, e_nodes.xyz, per, nhv)
+    hc = _stencil(h_nodes.xyz, e_nodes.xyz, per, i_he, n, phs_k, m, OP_GRAD)
+    hv = _stencil(h_nodes.xyz, h_nodes.xyz, per, i_hh, nhv, 2 * alpha + 1, 2 * alpha, OP_LAP_POW,
+                  alpha)
+    ec = _stencil(e_nodes.xyz, h_nodes.xyz, per, i_eh, n, phs_k, m, OP_GRAD)
+    ev = _stencil(e_nodes.xyz, e_nodes.xyz, per, i_ee, nhv, 2 * alpha + 1, 2 * alpha, OP_LAP_POW,
+                  alpha)
+    er = np.ones(e_nodes.n) if eps_r is None else _f64(eps_r)
+    return TMz(nh=h_nodes.n, ne=e_nodes.n, hc=hc, hv=hv, ec=ec, ev=ev, eps_r=er,
+               pec=np.ascontiguousarray(e_nodes.pec, dtype=np.uint8), dt=dt, eps0=eps0, mu0=mu0,
+               gamma=gamma)
+
+
+def _tmz_args(p: TMz):
+    hc, hv, ec, ev = p.hc, p.hv, p.ec, p.ev
+    keep = []
+
+    def st(s, k):
+        a = np.ascontiguousarray(s.w[k])
+        keep.append(a)
+        return _p(a)
+
+    args = [C.c_int64(p.nh), C.c_int(hc.idx.shape[1]), _p(hc.idx), st(hc, 0), st(hc, 1),
+            C.c_int(hv.idx.shape[1]), _p(hv.idx), st(hv, 0),
+            C.c_int64(p.ne), C.c_int(ec.idx.shape[1]), _p(ec.idx), st(ec, 0), st(ec, 1),
+            C.c_int(ev.idx.shape[1]), _p(ev.idx), st(ev, 0),
+            _p(p.eps_r), _p(p.pec), C.c_double(p.dt), C.c_double(p.eps0), C.c_double(p.mu0),
+            C.c_double(p.gamma)]
+    return args, keep
+
+
+def run_tmz(p: TMz, ez, hx, hy, nsteps, step0=0, sources=None, probes=None, energy=False):
+    """Runs nsteps of Eq. 19. Returns (ez, hx, hy, probe series (nsteps x P), energy or None)."""
+    ez, hx, hy = _f64(ez).copy(), _f64(hx).copy(), _f64(hy).copy()
+    args, keep = _tmz_args(p)
+    if sources is None:
+        sn = sa = sf = st0 = np.zeros(0)
+        sn = np.zeros(0, np.int64)
+    else:
+        sn, sa, sf, st0 = _i64(sources.node), _f64(sources.amp), _f64(sources.f0), _f64(sources.t0)
+    pr = np.zeros(0, np.int64) if probes is None else _i64(probes)
+    pout = np.zeros((nsteps, len(pr)))
+    eout = np.zeros(nsteps) if energy else None
+    _check(lib().orc_run_tmz(*args, _p(ez), _p(hx), _p(hy), C.c_int64(step0), C.c_int64(nsteps),
+                             C.c_int(len(sn)), _p(sn), _p(sa), _p(sf), _p(st0), C.c_int(len(pr)),
+                             _p(pr), _p(pout), _p(eout)), "run_tmz")
+    del keep
+    return ez, hx, hy, pout, eout
+
+
+def adjoint_step_tmz(p: TMz, lE, lHx, lHy):
+    lE, lHx, lHy = _f64(lE).copy(), _f64(lHx).copy(), _f64(lHy).copy()
+    args, keep = _tmz_args(p)
+    _check(lib().orc_adjoint_step_tmz(*args, _p(lE), _p(lHx), _p(lHy)), "adjoint_step_tmz")
+    del keep
+    return lE, lHx, lHy
+
+
+def grad_tmz(p: TMz, ez, hx, hy, nsteps, sources, probes):
+    """J = dt sum_n sum_p Ez_p^2 and its gradient w.r.t. eps_r and source amplitudes."""
+    args, keep = _tmz_args(p)
+    ez, hx, hy = _f64(ez), _f64(hx), _f64(hy)
+    sn, sa, sf, st0 = _i64(sources.node), _f64(sources.amp), _f64(sources.f0), _f64(sources.t0)
+    pr = _i64(probes)
+    J = C.c_double(0.0)
+    ge = np.zeros(p.ne)
+    ga = np.zeros(len(sn))
+    _check(lib().orc_grad_tmz(*args, _p(ez), _p(hx), _p(hy), C.c_int64(nsteps), C.c_int(len(sn)),
+                              _p(sn), _p(sa), _p(sf), _p(st0), C.c_int(len(pr)), _p(pr),
+                              C.byref(J), _p(ge), _p(ga)), "grad_tmz")
+    del keep
+    return J.value, ge, ga
+
+
+def energy_tmz(ez, eps_r, hxa, hya, hxb, hyb, eta0):
+    ez, eps_r = _f64(ez), _f64(eps_r)
+    hxa, hya, hxb, hyb = _f64(hxa), _f64(hya), _f64(hxb), _f64(hyb)
+    return lib().orc_energy_tmz(C.c_int64(len(ez)), _p(ez), _p(eps_r), C.c_int64(len(hxa)),
+                                _p(hxa), _p(hya), _p(hxb), _p(hyb), C.c_double(eta0))
+
+
+@dataclass
+class Max3D:
+    """A collocated 3D problem."""
+
+    n: int
+    c: Stencil
+    v: Stencil
+    eps_r: np.ndarray
+    wall: np.ndarray
+    dt: float
+    eps0: float
+    mu0: float
+    gamma: float
+
+
+def max3d_collocated(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=None):
+    import math
+    nhv = 2 * math.comb(2 * alpha + 3, 3) + 1
+    L = max(n, nhv)
+    idx = knn(nodes.xyz, nodes.xyz, nodes.period, L)
+    c = _stencil(nodes.xyz, nodes.xyz, nodes.period, idx, n, phs_k, m, OP_GRAD)
+    v = _stencil(nodes.xyz, nodes.xyz, nodes.period, idx, nhv, 2 * alpha + 1, 2 * alpha,
+                 OP_LAP_POW, alpha)
+    er = np.ones(nodes.n) if eps_r is None else _f64(eps_r)
+    return Max3D(n=nodes.n, c=c, v=v, eps_r=er,
+                 wall=np.ascontiguousarray(nodes.normal_axes, dtype=np.uint8), dt=dt, eps0=eps0,
+                 mu0=mu0, gamma=gamma), idx
+
+
+def run_3d(p: Max3D, E, H, nsteps, step0=0, sources=None, probes=None, energy=False):
+    """E, H: (3, N). Returns (E, H, probes, energy)."""
+    E, H = _f64(E).copy(), _f64(H).copy()
+    w = [np.ascontiguousarray(p.c.w[k]) for k in range(3)]
+    wv = np.ascontiguousarray(p.v.w[0])
+    if sources is None:
+        sn = np.zeros(0, np.int64)
+        sa = sf = st0 = np.zeros(0)
+    else:
+        sn, sa, sf, st0 = _i64(sources.node), _f64(sources.amp), _f64(sources.f0), _f64(sources.t0)
+    pr = np.zeros(0, np.int64) if probes is None else _i64(probes)
+    pout = np.zeros((nsteps, len(pr)))
+    eout = np.zeros(nsteps) if energy else None
+    _check(lib().orc_run_3d(C.c_int64(p.n), C.c_int(p.c.idx.shape[1]), _p(p.c.idx), _p(w[0]),
+                            _p(w[1]), _p(w[2]), C.c_int(p.v.idx.shape[1]), _p(p.v.idx), _p(wv),
+                            _p(p.eps_r), _p(p.wall), C.c_double(p.dt), C.c_double(p.eps0),
+                            C.c_double(p.mu0), C.c_double(p.gamma), _p(E), _p(H),
+                            C.c_int64(step0), C.c_int64(nsteps), C.c_int(len(sn)), _p(sn), _p(sa),
+                            _p(sf), _p(st0), C.c_int(len(pr)), _p(pr), _p(pout), _p(eout)),
+           "run_3d")
+    return E, H, pout, eout
