@@ -1,0 +1,408 @@
+"""Benchmark of the meshless RBF-FD leapfrog step on one GB300 (or N replicas).
+
+Workload (default, "pulse2d-staggered-1M"): 2D TMz Gaussian-modulated pulse
+on a periodic 1000 h x 1000 h square, staggered layout: 1,000,000 jittered E
+nodes and 1,000,000 jittered H nodes (offset by (h/2, h/2)); curl stencils of
+the 30 nearest nodes of the other set with PHS r^5 + degree-4 monomials;
+hyperviscosity Delta^3 on the 57 nearest own-set nodes (PHS r^7, degree 6);
+12 points per wavelength; Courant number 0.5. FP32 fields and weights
+(compensated stencil sums), weights solved in FP64 on the GPU. A bench step is
+one leapfrog step (H half step, E half step, source/probe/step-counter update)
+over all 2M nodes; inputs (1.7 GB per step) are larger than L2.
+
+metric: node-field updates/s = (N_E * 1 + N_H * 2) * steps / time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "node-field updates/s & HBM roofline frac, FP32 vs FP64 at stated L2 err"
+UNIT = "node-field updates/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=1000, help="nodes per side of each set")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--plain", action="store_true", help="FP32 without compensated sums")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--accuracy-steps", type=int, default=1000,
+                    help="FP32-vs-FP64 (GPU) relative L2 error after this many steps (0: skip)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 step and the accuracy runs")
+    return ap.parse_args()
+
+
+PARAMS = dict(S=0.5, n=30, k=5, m=4, alpha=3, c=4e-5, wavelength=12.0)
+
+
+def pulse_fields(e, h, nx, dt):
+    S = PARAMS["S"]
+    _, _, _, c0, eta0 = W.units(S)
+    lam = PARAMS["wavelength"]
+    ez, _, _ = W.gaussian_pulse(e.xyz, nx, nx / 2, 2 * lam, c0, eta0, dt, lam)
+    _, hx, hy = W.gaussian_pulse(h.xyz, nx, nx / 2, 2 * lam, c0, eta0, dt, lam)
+    return ez, hx, hy
+
+
+def node_sets(nx):
+    e = W.periodic_box((nx, nx), 0.25, 2, seed_line_y=nx // 2)
+    h = W.periodic_box((nx, nx), 0.25, 3, offset=(0.5, 0.5))
+    return e, h
+
+
+def algorithmic_bytes(n, nhv, s):
+    """Compulsory bytes per node of each half step (staggered; int32 indices, s bytes per real).
+    H pass: indices 4 (n + N_h), weights s (2 n + N_h), fields Ez (gathered once) + H read + H written.
+    E pass: same streams; fields H' + Ez read, Ez written."""
+    h = 4 * (n + nhv) + s * (2 * n + nhv) + 5 * s
+    e = 4 * (n + nhv) + s * (2 * n + nhv) + 4 * s
+    return h, e
+
+
+def build_weights(M, ctx, e, h):
+    """Node sets, kNN stencils and FP64 weights of the staggered workload (setup, timed apart)."""
+    n, k, m, alpha = (PARAMS[x] for x in ("n", "k", "m", "alpha"))
+    nhv = 2 * math.comb(2 * alpha + 2, 2) + 1
+    t = time.time()
+    de, dh = M.Nodes(ctx, e.xyz, e.period), M.Nodes(ctx, h.xyz, h.period)
+    s_he, s_hh = M.Stencils(dh, de, n), M.Stencils(dh, dh, nhv)
+    s_eh, s_ee = M.Stencils(de, dh, n), M.Stencils(de, de, nhv)
+    ctx.sync()
+    t_knn = time.time() - t
+    t = time.time()
+    hc = M.Weights(s_he, n, k, m, M.MFD_OP_GRAD)
+    hv = M.Weights(s_hh, nhv, 2 * alpha + 1, 2 * alpha, M.MFD_OP_LAP_POW, alpha)
+    ec = M.Weights(s_eh, n, k, m, M.MFD_OP_GRAD)
+    ev = M.Weights(s_ee, nhv, 2 * alpha + 1, 2 * alpha, M.MFD_OP_LAP_POW, alpha)
+    ctx.sync()
+    t_w = time.time() - t
+    return (hc, hv, ec, ev), dict(morton_knn_s=round(t_knn, 3), weights_fp64_s=round(t_w, 3)), nhv
+
+
+def make_sim(M, ctx, wts, precision, compensated):
+    S, c, alpha = PARAMS["S"], PARAMS["c"], PARAMS["alpha"]
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    gamma = c * (-1) ** (alpha - 1)
+    hc, hv, ec, ev = wts
+    return M.Sim(ctx, 2, precision, dt, eps0, mu0, gamma, hc, hv, ec, ev, compensated=compensated)
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_record(kernel, s):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel sources are unchanged since that capture (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("csrc_sha") != csrc_sha():
+        return None
+    return d.get("kernels", {}).get(f"{kernel}_fp{8 * s}")
+
+
+def csrc_sha():
+    hsh = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_2508_18205_gb300", "csrc")
+    for f in sorted(os.listdir(cs)):
+        hsh.update(open(os.path.join(cs, f), "rb").read())
+    return hsh.hexdigest()[:16]
+
+
+def cpu_baseline(budget_s=20.0):
+    """The oracle (FP64, OpenMP on the host cores) on a bounded sample of the
+    same workload: a 160 x 160 periodic staggered sub-square with the same
+    stencils, stepped for about budget_s seconds."""
+    import oracle as O
+    S, n, k, m, alpha, c = (PARAMS[x] for x in ("S", "n", "k", "m", "alpha", "c"))
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    nx = 160
+    e, h = node_sets(nx)
+    prob = O.tmz_staggered(e, h, n, k, m, alpha, dt, eps0, mu0, c * (-1) ** (alpha - 1))
+    ez, hx, hy = pulse_fields(e, h, nx, dt)
+    t = time.time()
+    O.run_tmz(prob, ez, hx, hy, 5)
+    per = (time.time() - t) / 5
+    steps = max(5, int(budget_s / max(per, 1e-6)))
+    t = time.time()
+    O.run_tmz(prob, ez, hx, hy, steps)
+    el = time.time() - t
+    updates = (e.n + 2 * h.n) * steps
+    return {"value": updates / el, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+            "sample": f"{nx}x{nx}+{nx}x{nx} staggered periodic sub-square, same stencils, {steps} steps "
+                      f"in {el:.1f} s (FP64)"}
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    per = []
+    for _ in range(a.warmup):
+        pass
+    t0 = time.time()
+    cb = None
+    for _ in range(max(1, a.steps if a.steps <= 3 else 3)):
+        cb = cpu_baseline(budget_s=max(3.0, 30.0 / max(1, min(a.steps, 3))))
+        per.append(cb["value"])
+    v = float(np.median(per))
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "pulse2d-staggered-1M (bounded oracle sample)", "nodes_per_set": a.nx ** 2},
+            "cpu_baseline": {**cb, "value": v},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.time() - t0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = _args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        return run_reference(a, rank, world)
+    import torch
+    import paper_2508_18205_gb300 as M
+    from paper_2508_18205_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = M.MFD_FP64 if a.precision == "fp64" else M.MFD_FP32
+    comp = prec == M.MFD_FP32 and not a.plain
+    nx = a.nx
+    e, h = node_sets(nx)
+    ctx = M.Ctx(local)
+    wts, setup, nhv = build_weights(M, ctx, e, h)
+    sim = make_sim(M, ctx, wts, prec, comp)
+    S = PARAMS["S"]
+    dt = W.units(S)[0]
+    ez, hx, hy = pulse_fields(e, h, nx, dt)
+    probes = W.interior_nodes(e, 16, 24)
+
+    def reset(s_, cap):
+        s_.set_field(M.MFD_EZ, ez)
+        s_.set_field(M.MFD_HX, hx)
+        s_.set_field(M.MFD_HY, hy)
+        s_.set_probes(probes, cap)
+
+    reset(sim, a.steps + a.warmup + 8)
+    stream = ctx.torch_stream()
+    sim.step(a.warmup)
+    sim.step_timed(min(a.steps, 64))  # creates the per-launch event pool
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    sim.step(a.steps)                 # production path: graph replay
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    # per-kernel durations: the same number of steps, every launch bracketed by CUDA events
+    ms = sim.step_timed(a.steps)
+    clocks = sampler.stop()
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        dist.barrier()
+    per_step_updates = e.n + 2 * h.n
+    value = per_step_updates * a.steps * world / elapsed
+    s = 8 if prec == M.MFD_FP64 else 4
+    peak, peak_kind = peaks()
+    roof = roofline(ms, a.steps, e, h, nhv, s, peak, peak_kind)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": elapsed / a.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == M.MFD_FP64 else "f32",
+            "data": "synthetic",
+            "config": {"workload": f"pulse2d-staggered-{nx}x{nx}x2",
+                       "nodes_per_set": nx * nx, "layout": "staggered", "curl_stencil": PARAMS["n"],
+                       "hv_stencil": nhv, "phs": PARAMS["k"], "poly_m": PARAMS["m"], "alpha": PARAMS["alpha"],
+                       "courant": S, "compensated": comp, "l2_flush": "inputs larger than L2 (1.7 GB/step)",
+                       "parallelism": f"replicas{world}", "setup_s": setup},
+            "roofline": roof, "clocks": clocks, "gpu_launches": 3 * a.steps,
+            "event_timed_ms_per_step": (ms[0] + ms[1]) / a.steps}
+    # the plain FP64 GPU step on the same GPU, and FP32 accuracy against it
+    if rank == 0 and not a.no_fp64 and prec == M.MFD_FP32:
+        k64 = min(a.steps, 1000)
+        s64 = make_sim(M, ctx, wts, M.MFD_FP64, False)
+        reset(s64, 8)
+        s64.step(a.warmup)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        s64.step(k64)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        el64 = t0.elapsed_time(t1) / 1e3
+        ms64 = s64.step_timed(k64)
+        line["fp64"] = {"value": per_step_updates * k64 / el64, "unit": UNIT, "steps": k64,
+                        "ms_per_step": el64 / k64 * 1e3,
+                        "roofline": roofline(ms64, k64, e, h, nhv, 8, peak, peak_kind)}
+        del s64
+        if a.accuracy_steps:
+            line["accuracy"] = accuracy(M, ctx, wts, a.accuracy_steps, reset)
+    # end to end through the public API: host fields in, steps, host Ez + probes out
+    if not a.no_e2e:
+        pin = [torch.empty(x.shape[0], dtype=torch.float64, pin_memory=True) for x in (ez, hx, hy)]
+        for t_, x in zip(pin, (ez, hx, hy)):
+            t_.numpy()[:] = x
+        out = torch.empty(e.n, dtype=torch.float64, pin_memory=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.set_field(M.MFD_EZ, pin[0].numpy())
+        sim.set_field(M.MFD_HX, pin[1].numpy())
+        sim.set_field(M.MFD_HY, pin[2].numpy())
+        sim.set_probes(probes, a.steps)
+        sim.step(a.steps)
+        sim.ctx.sync()
+        res = sim.read_probes()
+        lib = M.lib()
+        import ctypes
+        M._ck(lib.mfd_get_field(sim.h, M.MFD_EZ, 0, ctypes.c_void_p(out.data_ptr())))
+        el = time.perf_counter() - t0
+        h2d = 8 * (e.n + 2 * h.n)
+        d2h = 8 * e.n + res.nbytes
+        line["e2e"] = {"value": per_step_updates * a.steps / el * world, "unit": UNIT,
+                       "h2d_bytes_per_step": h2d / a.steps, "d2h_bytes_per_step": d2h / a.steps,
+                       "wall_s": el}
+    if rank == 0 and not a.no_cpu:
+        try:
+            line["cpu_baseline"] = cpu_baseline()
+        except Exception as ex:  # the oracle is test infrastructure; report why it is missing
+            line["cpu_baseline"] = {"value": None, "error": str(ex)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def roofline(ms, steps, e, h, nhv, s, peak, peak_kind):
+    """Dominant half-step kernel: algorithmic bytes per launch / its average event-timed duration."""
+    bh, be = algorithmic_bytes(PARAMS["n"], nhv, s)
+    h_avg = ms[0] / steps / 1e3
+    e_avg = ms[1] / steps / 1e3
+    dom = "h" if h_avg >= e_avg else "e"
+    dom_t = max(h_avg, e_avg)
+    dom_bytes = (bh * h.n) if dom == "h" else (be * e.n)
+    achieved = dom_bytes / dom_t / 1e9
+    kname = "k_h_stag" if dom == "h" else "k_e_stag"
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic_record(kname, s), "kernel": kname, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_t * 1e3,
+            "other_kernel_avg_launch_ms": min(h_avg, e_avg) * 1e3,
+            "other_kernel_achieved_gbs": ((be * e.n) if dom == "h" else (bh * h.n)) / min(h_avg, e_avg) / 1e9}
+
+
+def accuracy(M, ctx, wts, steps, reset):
+    """FP32 (compensated and plain) against FP64, all on the GPU, after `steps` steps:
+    relative L2 error of all fields together and the largest absolute error."""
+    fields = {}
+    for tag, prec, comp in (("fp64", M.MFD_FP64, False), ("fp32_compensated", M.MFD_FP32, True),
+                            ("fp32_plain", M.MFD_FP32, False)):
+        sim = make_sim(M, ctx, wts, prec, comp)
+        reset(sim, steps)
+        sim.step(steps)
+        fields[tag] = np.concatenate([sim.get_field(c) for c in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)])
+        fields[tag + "_probes"] = sim.read_probes()
+        del sim
+    ref = fields["fp64"]
+    out = {"steps": steps}
+    for tag in ("fp32_compensated", "fp32_plain"):
+        d = fields[tag] - ref
+        pd = fields[tag + "_probes"] - fields["fp64_probes"]
+        out[tag] = {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(ref)), "max_abs": float(np.max(np.abs(d))),
+                    "probe_rel_l2": float(np.linalg.norm(pd) / np.linalg.norm(fields["fp64_probes"]))}
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * mfd.h -- C ABI of the GB300 meshless (RBF-FD) Maxwell leapfrog library.
+ *
+ * The method is the meshless generalisation of the FDTD in "An RBF-based
+ * method for computational electromagnetics with reduced numerical
+ * dispersion" (arXiv 2508.18205): the interleaved leapfrog of the FDTD is kept
+ * (Sec. 5), every spatial derivative is a stencil sum D^L f(x_i) =
+ * sum_{j in S(x_i)} w_j f(x_j) over the n nearest nodes (Eq. 16, Eq. 11), the
+ * weights come from a local polyharmonic-spline + monomial interpolant (Eq. 9;
+ * RBF-FD Eq. 13 or RBF-VFD Eqs. 14-15), and a hyperviscosity term
+ * gamma Delta^alpha, itself discretised by RBF-FD, stabilises the update
+ * (Eqs. 17-19).
+ *
+ * Conventions (all calls):
+ *  - Every call returns mfd_status: MFD_OK (0) or a negative error code; the
+ *    message of the last error on the calling thread is mfd_last_error().
+ *    No exception and no abort crosses this boundary.
+ *  - Host pointers are read or written only during the call (the library
+ *    copies what it keeps). Device memory is owned by the library: every
+ *    object is released by its *_destroy function.
+ *  - Node ids at this boundary are always in the caller's order. Internally
+ *    the library reorders every node set along a Morton curve.
+ *  - Work is queued on the context's CUDA stream; calls that return host data
+ *    synchronise that stream. Asynchronous device errors surface as
+ *    MFD_ERR_CUDA at the next synchronising call.
+ *  - Coordinates and all physical parameters are FP64.
+ */
+#ifndef MFD_H
+#define MFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int mfd_status;
+#define MFD_OK 0
+#define MFD_ERR_ARG -1      /* invalid argument (sizes, null pointers, mismatched objects) */
+#define MFD_ERR_OOM -2      /* device or host allocation failed */
+#define MFD_ERR_CUDA -3     /* a CUDA runtime call failed */
+#define MFD_ERR_SINGULAR -4 /* a local weight system (Eq. 9) had an exactly zero pivot */
+#define MFD_ERR_UNSTABLE -5 /* the energy watchdog saw growth beyond its bound or a NaN */
+#define MFD_ERR_TIMEOUT -6  /* a bounded device-side wait gave up */
+#define MFD_ERR_STATE -7    /* call out of order (e.g. stepping before fields are set) */
+
+/* operators for mfd_weights_compute */
+#define MFD_OP_GRAD 0     /* d/dx_a, a < dim, by RBF-FD (Eq. 13): dim outputs */
+#define MFD_OP_LAP_POW 1  /* Delta^alpha by RBF-FD (Eq. 13, Sec. 5.1): one output */
+#define MFD_OP_GRAD_VFD 2 /* d/dx_a by RBF-VFD (Eqs. 14-15) with central differences */
+
+#define MFD_FP32 0
+#define MFD_FP64 1
+
+/* field components */
+#define MFD_EX 0
+#define MFD_EY 1
+#define MFD_EZ 2
+#define MFD_HX 3
+#define MFD_HY 4
+#define MFD_HZ 5
+
+typedef struct mfd_ctx mfd_ctx;
+typedef struct mfd_nodes mfd_nodes;
+typedef struct mfd_stencils mfd_stencils;
+typedef struct mfd_weights mfd_weights;
+typedef struct mfd_sim mfd_sim;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* mfd_last_error(void);
+int mfd_version(void);
+
+/* ------------------------------------------------------------- context */
+
+/* Binds the library to CUDA device `device`. stream: a cudaStream_t to
+ * queue work on, or NULL for a stream the context creates (non-blocking).
+ * A context is used by one host thread at a time. */
+mfd_status mfd_ctx_create(int device, void* stream, mfd_ctx** out);
+/* The cudaStream_t the context queues its work on (for the caller's events). */
+void* mfd_ctx_stream(const mfd_ctx* ctx);
+/* Waits for the context's stream; surfaces asynchronous errors as a status. */
+mfd_status mfd_ctx_sync(mfd_ctx* ctx);
+void mfd_ctx_destroy(mfd_ctx* ctx);
+
+/* --------------------------------------------------------------- nodes */
+
+/* A scattered node set X = {x_i} (Sec. 4, nodes at spacing ~h).
+ * xyz: host, n x dim FP64, caller's order. period: host, dim entries; the
+ * period along each axis, 0 for a non-periodic axis (coordinates of a
+ * periodic axis must lie in [0, period)). dim is 2 or 3; n >= 1.
+ * The node set is copied to the device and reordered along a Morton curve of
+ * its bounding box (ties by caller id). */
+mfd_status mfd_nodes_create(mfd_ctx* ctx, int dim, int64_t n, const double* xyz,
+                            const double* period, mfd_nodes** out);
+int64_t mfd_nodes_count(const mfd_nodes* nodes);
+/* perm (host, n): perm[k] = caller id of the k-th node in device order. */
+mfd_status mfd_nodes_permutation(const mfd_nodes* nodes, int64_t* perm);
+void mfd_nodes_destroy(mfd_nodes* nodes);
+
+/* ------------------------------------------------------------ stencils */
+
+/* kNN stencils S(x_c) (Sec. 4.1, Eq. 11): for every node of `centres`, the n
+ * nodes of `sources` closest to it, sorted by (squared distance, caller id of
+ * the source); periodic axes use the minimum image. Squared distances are
+ * FP64 sums dx*dx + dy*dy (+ dz*dz) taken left to right without fused
+ * multiply-add, so the result is exactly reproducible. centres and sources
+ * may be the same object (collocated stencils start with the centre itself)
+ * and must share dim and periods. 1 <= n <= min(128, count(sources)). */
+mfd_status mfd_stencils_build(const mfd_nodes* centres, const mfd_nodes* sources, int n,
+                              mfd_stencils** out);
+/* idx (host, count(centres) x n): caller ids of the stencil nodes, rows in
+ * the caller's centre order. */
+mfd_status mfd_stencils_read(const mfd_stencils* st, int64_t* idx);
+void mfd_stencils_destroy(mfd_stencils* st);
+
+/* ------------------------------------------------------------- weights */
+
+/* Stencil weights w^L (Eq. 12) on the first n_use entries of each stencil,
+ * from the local interpolant with PHS phi(r) = r^phs_k (phs_k odd, 1..9) and
+ * all monomials of total degree <= poly_m (Eq. 9). Each centre's system is
+ * shifted to x_c, scaled by the stencil radius and solved in FP64 on the GPU.
+ *   op = MFD_OP_GRAD     : RBF-FD first derivatives, dim outputs (Eq. 13)
+ *   op = MFD_OP_LAP_POW  : RBF-FD Delta^alpha, one output (Sec. 5.1);
+ *                          needs phs_k >= 2 alpha + 1
+ *   op = MFD_OP_GRAD_VFD : RBF-VFD first derivatives: the central difference
+ *                          (s(x_c + delta e_a) - s(x_c - delta e_a)) / (2 delta)
+ *                          of the interpolant (Eqs. 14-15); delta > 0.
+ * Returns MFD_ERR_SINGULAR if any system had an exactly zero pivot. */
+mfd_status mfd_weights_compute(const mfd_stencils* st, int n_use, int phs_k, int poly_m, int op,
+                               int alpha, double delta, mfd_weights** out);
+/* w (host, nout x count(centres) x n_use) in the caller's centre order,
+ * entry j of a row being the weight of stencil entry j (mfd_stencils_read). */
+mfd_status mfd_weights_read(const mfd_weights* w, double* host_w);
+void mfd_weights_destroy(mfd_weights* w);
+
+/* ----------------------------------------------------------- simulation */
+
+/* The stepped problem. The H field lives on the centres of h_curl / h_hv, the
+ * E field on the centres of e_curl / e_hv.
+ *   collocated (the paper's method, Sec. 5): one node set; h_curl == e_curl
+ *     (MFD_OP_GRAD or MFD_OP_GRAD_VFD weights) and h_hv == e_hv
+ *     (MFD_OP_LAP_POW). When the curl and HV weights come from one stencils
+ *     object (the curl weights on its first n entries) the kernels read one
+ *     index array for both.
+ *   staggered: an E node set and an H node set; h_curl has H centres and E
+ *     sources, e_curl E centres and H sources; h_hv / e_hv are own-set.
+ * One step n -> n+1 (Eq. 19; 3D: Eq. 2 with the same terms on every component):
+ *   H <- H + dt/mu0 (-curl E^n + gamma D^{Delta^alpha} H)
+ *   E <- E + dt/(eps0 eps_r) (curl H^{n+1/2} + gamma D^{Delta^alpha} E^n)
+ *   then soft sources add amp r(t_{n+1}) to Ez, PEC components are held at 0,
+ *   and probes record Ez^{n+1}.
+ * gamma is the coefficient of Eq. 18 (c (-1)^(alpha-1) h^(2 alpha) in the
+ * paper's units). nrhs field vectors are stepped with the same weights. */
+typedef struct {
+    int dim;       /* 2 (TMz: Ez, Hx, Hy) or 3 (Ex..Hz, collocated only) */
+    int precision; /* MFD_FP32 or MFD_FP64: fields, weights and arithmetic */
+    int nrhs;      /* right-hand sides (>= 1) */
+    int compensated; /* FP32 only: 1 = compensated (two-sum) stencil sums */
+    double dt, eps0, mu0, gamma;
+    const mfd_weights* h_curl;
+    const mfd_weights* h_hv;
+    const mfd_weights* e_curl;
+    const mfd_weights* e_hv;
+} mfd_sim_desc;
+
+mfd_status mfd_sim_create(mfd_ctx* ctx, const mfd_sim_desc* desc, mfd_sim** out);
+/* eps_r (host, count(E nodes), NULL = vacuum) and pec (host, count(E nodes),
+ * NULL = none). 2D: pec[i] != 0 holds Ez_i at 0. 3D: pec[i] bit a set when
+ * the node sits on a wall normal to axis a; every E component tangential to
+ * such a wall is held at 0. Fields of held components are zeroed now. */
+mfd_status mfd_set_materials(mfd_sim* sim, const double* eps_r, const uint8_t* pec);
+/* Field component `comp` (MFD_EX..MFD_HZ) of right-hand side `rhs` from host
+ * FP64 values in the caller's order of its node set. E is taken at t_n, H at
+ * t_n - dt/2 (Eq. 4, Eq. 21). Resets the step counter to 0 when comp == MFD_EZ. */
+mfd_status mfd_set_field(mfd_sim* sim, int comp, int rhs, const double* host);
+mfd_status mfd_get_field(mfd_sim* sim, int comp, int rhs, double* host);
+/* Soft Ricker sources (count >= 0): node (E node, caller id), rhs, amplitude,
+ * centre frequency f0 and delay t0; r(t) = (1 - 2 a) exp(-a),
+ * a = (pi f0 (t - t0))^2, added to Ez after each E update. */
+mfd_status mfd_set_sources(mfd_sim* sim, int count, const int64_t* node, const int32_t* rhs,
+                           const double* amp, const double* f0, const double* t0);
+/* Probes: Ez at `count` E nodes (caller ids) is recorded after every step for
+ * every rhs, for at most `capacity` steps; recording restarts at 0. */
+mfd_status mfd_set_probes(mfd_sim* sim, int count, const int64_t* node, int64_t capacity);
+/* Advances nsteps (>= 0) leapfrog steps on the context stream (launches
+ * replay a captured CUDA graph for long runs). */
+mfd_status mfd_step(mfd_sim* sim, int64_t nsteps);
+/* As mfd_step, without graphs: CUDA events bracket every launch of the H
+ * and E half-step kernels; ms[0], ms[1] receive their summed device times
+ * (synchronises). */
+mfd_status mfd_step_timed(mfd_sim* sim, int64_t nsteps, double* ms);
+/* Probe series recorded since mfd_set_probes: host (steps x count x nrhs FP64);
+ * *steps receives the number of recorded steps. host may be NULL to query. */
+mfd_status mfd_read_probes(mfd_sim* sim, double* host, int64_t* steps);
+/* Eq. 20 at the current time t_n for every rhs (host, nrhs values):
+ * sum_i eps_r,i |E_i|^2 + (mu0/eps0) |H_i|^2 with H averaged between t_n -
+ * dt/2 and t_n + dt/2 (the latter computed on the fly). Multiply by the
+ * domain measure / node count for the integral of Eq. 20. */
+mfd_status mfd_energy(mfd_sim* sim, double* u);
+/* Number of steps taken since the last mfd_set_field(MFD_EZ). */
+int64_t mfd_sim_steps(const mfd_sim* sim);
+void mfd_sim_destroy(mfd_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,281 @@
+"""Python binding of libmfd (include/mfd.h): the GB300 meshless RBF-FD Maxwell leapfrog.
+
+Argument marshalling only: every step of the method (Morton reordering, kNN
+stencils, weight solves, the fused leapfrog half steps, sources, probes,
+energy) runs in the CUDA library. The functions mirror the C ABI names
+(``mfd_nodes_create`` ...); the small classes below own the handles.
+
+The library must be built (``paper_2508_18205_gb300.build.build()``); there
+is no fallback: importing the handles without the built library, or using them
+without a CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmfd.so")
+
+MFD_OK = 0
+MFD_ERR_ARG, MFD_ERR_OOM, MFD_ERR_CUDA, MFD_ERR_SINGULAR = -1, -2, -3, -4
+MFD_ERR_UNSTABLE, MFD_ERR_TIMEOUT, MFD_ERR_STATE = -5, -6, -7
+MFD_OP_GRAD, MFD_OP_LAP_POW, MFD_OP_GRAD_VFD = 0, 1, 2
+MFD_FP32, MFD_FP64 = 0, 1
+MFD_EX, MFD_EY, MFD_EZ, MFD_HX, MFD_HY, MFD_HZ = range(6)
+
+
+class MfdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"mfd status {status}: {msg}")
+        self.status = status
+
+
+class mfd_sim_desc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("precision", C.c_int), ("nrhs", C.c_int), ("compensated", C.c_int),
+                ("dt", C.c_double), ("eps0", C.c_double), ("mu0", C.c_double), ("gamma", C.c_double),
+                ("h_curl", C.c_void_p), ("h_hv", C.c_void_p), ("e_curl", C.c_void_p), ("e_hv", C.c_void_p)]
+
+
+_VP, _I, _I64, _D = C.c_void_p, C.c_int, C.c_int64, C.c_double
+_SIGS = {
+    "mfd_last_error": (C.c_char_p, []),
+    "mfd_version": (C.c_int, []),
+    "mfd_ctx_create": (_I, [_I, _VP, C.POINTER(_VP)]),
+    "mfd_ctx_stream": (_VP, [_VP]),
+    "mfd_ctx_sync": (_I, [_VP]),
+    "mfd_ctx_destroy": (None, [_VP]),
+    "mfd_nodes_create": (_I, [_VP, _I, _I64, _VP, _VP, C.POINTER(_VP)]),
+    "mfd_nodes_count": (_I64, [_VP]),
+    "mfd_nodes_permutation": (_I, [_VP, _VP]),
+    "mfd_nodes_destroy": (None, [_VP]),
+    "mfd_stencils_build": (_I, [_VP, _VP, _I, C.POINTER(_VP)]),
+    "mfd_stencils_read": (_I, [_VP, _VP]),
+    "mfd_stencils_destroy": (None, [_VP]),
+    "mfd_weights_compute": (_I, [_VP, _I, _I, _I, _I, _I, _D, C.POINTER(_VP)]),
+    "mfd_weights_read": (_I, [_VP, _VP]),
+    "mfd_weights_destroy": (None, [_VP]),
+    "mfd_sim_create": (_I, [_VP, C.POINTER(mfd_sim_desc), C.POINTER(_VP)]),
+    "mfd_set_materials": (_I, [_VP, _VP, _VP]),
+    "mfd_set_field": (_I, [_VP, _I, _I, _VP]),
+    "mfd_get_field": (_I, [_VP, _I, _I, _VP]),
+    "mfd_set_sources": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP]),
+    "mfd_set_probes": (_I, [_VP, _I, _VP, _I64]),
+    "mfd_step": (_I, [_VP, _I64]),
+    "mfd_step_timed": (_I, [_VP, _I64, _VP]),
+    "mfd_read_probes": (_I, [_VP, _VP, C.POINTER(_I64)]),
+    "mfd_energy": (_I, [_VP, _VP]),
+    "mfd_sim_steps": (_I64, [_VP]),
+    "mfd_sim_destroy": (None, [_VP]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libmfd (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libmfd is not built ({LIB_PATH}); run paper_2508_18205_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ck(status):
+    if status != MFD_OK:
+        raise MfdError(status, lib().mfd_last_error().decode())
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ------------------------------------------------------------------ handles
+
+class Ctx:
+    """A library context on CUDA device `device` (its own non-blocking stream unless one is given)."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        h = C.c_void_p()
+        _ck(lib().mfd_ctx_create(device, stream, C.byref(h)))
+        self.h = h
+        self.device = device
+
+    @property
+    def stream(self) -> int:
+        return lib().mfd_ctx_stream(self.h) or 0
+
+    def torch_stream(self):
+        import torch
+        return torch.cuda.ExternalStream(self.stream, device=f"cuda:{self.device}")
+
+    def sync(self):
+        _ck(lib().mfd_ctx_sync(self.h))
+
+    def close(self):
+        if self.h:
+            lib().mfd_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Nodes:
+    def __init__(self, ctx: Ctx, xyz, period=None):
+        xyz = _f64(xyz)
+        n, dim = xyz.shape
+        per = _f64(np.zeros(dim) if period is None else period)
+        h = C.c_void_p()
+        _ck(lib().mfd_nodes_create(ctx.h, dim, n, _p(xyz), _p(per), C.byref(h)))
+        self.h, self.ctx, self.n, self.dim = h, ctx, n, dim
+
+    def permutation(self):
+        out = np.empty(self.n, dtype=np.int64)
+        _ck(lib().mfd_nodes_permutation(self.h, _p(out)))
+        return out
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().mfd_nodes_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class Stencils:
+    def __init__(self, centres: Nodes, sources: Nodes, n: int):
+        h = C.c_void_p()
+        _ck(lib().mfd_stencils_build(centres.h, sources.h, n, C.byref(h)))
+        self.h, self.centres, self.sources, self.n = h, centres, sources, n
+
+    def read(self):
+        out = np.empty((self.centres.n, self.n), dtype=np.int64)
+        _ck(lib().mfd_stencils_read(self.h, _p(out)))
+        return out
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().mfd_stencils_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class Weights:
+    def __init__(self, st: Stencils, n_use: int, phs_k: int, poly_m: int, op: int, alpha: int = 0,
+                 delta: float = 0.0):
+        h = C.c_void_p()
+        _ck(lib().mfd_weights_compute(st.h, n_use, phs_k, poly_m, op, alpha, float(delta), C.byref(h)))
+        self.h, self.st, self.n_use, self.op = h, st, n_use, op
+        self.nout = 1 if op == MFD_OP_LAP_POW else st.centres.dim
+
+    def read(self):
+        out = np.empty((self.nout, self.st.centres.n, self.n_use))
+        _ck(lib().mfd_weights_read(self.h, _p(out)))
+        return out
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().mfd_weights_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class Sim:
+    """A stepped problem (see mfd_sim_desc in include/mfd.h)."""
+
+    def __init__(self, ctx: Ctx, dim, precision, dt, eps0, mu0, gamma, h_curl: Weights, h_hv: Weights,
+                 e_curl: Weights = None, e_hv: Weights = None, compensated=False, nrhs=1):
+        e_curl = e_curl or h_curl
+        e_hv = e_hv or h_hv
+        d = mfd_sim_desc(dim, precision, nrhs, int(bool(compensated)), dt, eps0, mu0, gamma,
+                         h_curl.h, h_hv.h, e_curl.h, e_hv.h)
+        h = C.c_void_p()
+        _ck(lib().mfd_sim_create(ctx.h, C.byref(d), C.byref(h)))
+        self.h, self.ctx = h, ctx
+        self._keep = (h_curl, h_hv, e_curl, e_hv)
+        self.ne = e_curl.st.centres.n
+        self.nh = h_curl.st.centres.n
+        self.nprobe = 0
+
+    def set_materials(self, eps_r=None, pec=None):
+        er = None if eps_r is None else _f64(eps_r)
+        pc = None if pec is None else np.ascontiguousarray(pec, dtype=np.uint8)
+        _ck(lib().mfd_set_materials(self.h, _p(er), _p(pc)))
+
+    def set_field(self, comp, values, rhs=0):
+        _ck(lib().mfd_set_field(self.h, comp, rhs, _p(_f64(values))))
+
+    def get_field(self, comp, rhs=0):
+        n = self.ne if comp <= MFD_EZ else self.nh
+        out = np.empty(n)
+        _ck(lib().mfd_get_field(self.h, comp, rhs, _p(out)))
+        return out
+
+    def set_sources(self, node, amp, f0, t0, rhs=None):
+        node = np.ascontiguousarray(node, dtype=np.int64)
+        r = None if rhs is None else np.ascontiguousarray(rhs, dtype=np.int32)
+        _ck(lib().mfd_set_sources(self.h, len(node), _p(node), _p(r), _p(_f64(amp)), _p(_f64(f0)),
+                                  _p(_f64(t0))))
+
+    def set_probes(self, node, capacity):
+        node = np.ascontiguousarray(node, dtype=np.int64)
+        _ck(lib().mfd_set_probes(self.h, len(node), _p(node), int(capacity)))
+        self.nprobe = len(node)
+
+    def step(self, n):
+        _ck(lib().mfd_step(self.h, int(n)))
+
+    def step_timed(self, n):
+        ms = np.zeros(2)
+        _ck(lib().mfd_step_timed(self.h, int(n), _p(ms)))
+        return ms
+
+    def read_probes(self):
+        steps = C.c_int64(0)
+        _ck(lib().mfd_read_probes(self.h, None, C.byref(steps)))
+        out = np.zeros((steps.value, self.nprobe))
+        if steps.value and self.nprobe:
+            _ck(lib().mfd_read_probes(self.h, _p(out), C.byref(steps)))
+        return out
+
+    def energy(self):
+        u = np.zeros(1)
+        _ck(lib().mfd_energy(self.h, _p(u)))
+        return float(u[0])
+
+    @property
+    def steps(self):
+        return int(lib().mfd_sim_steps(self.h))
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().mfd_sim_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass

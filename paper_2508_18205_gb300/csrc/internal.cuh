@@ -1,0 +1,112 @@
+// internal.cuh -- shared declarations of the CUDA library behind include/mfd.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mfd.h"
+
+namespace mfd {
+
+// ------------------------------------------------------------ errors
+
+void set_error(const std::string& msg);
+mfd_status fail(mfd_status st, const std::string& msg);
+
+#define MFD_CUDA(call)                                                                     \
+    do {                                                                                   \
+        cudaError_t e__ = (call);                                                          \
+        if (e__ != cudaSuccess)                                                            \
+            return ::mfd::fail(MFD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+#define MFD_TRY(call)                         \
+    do {                                      \
+        mfd_status s__ = (call);              \
+        if (s__ != MFD_OK) return s__;        \
+    } while (0)
+
+// ------------------------------------------------------------ device buffers
+
+// An owning device allocation (cudaMalloc); freed with the object holding it.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    mfd_status alloc(size_t n) {
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return fail(MFD_ERR_OOM, std::string("cudaMalloc(") + std::to_string(n) + "): " + cudaGetErrorString(e));
+        }
+        bytes = n;
+        return MFD_OK;
+    }
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+}  // namespace mfd
+
+// ------------------------------------------------------------ objects
+
+struct mfd_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sm_count = 0;
+    mfd::DevBuf status;  // device status words (int32[8]) shared by bounded waits
+};
+
+struct mfd_nodes {
+    mfd_ctx* ctx = nullptr;
+    int dim = 2;
+    int64_t n = 0;
+    double period[3] = {0, 0, 0};
+    mfd::DevBuf xyz;   // double [n][dim], device (Morton) order
+    mfd::DevBuf perm;  // int64 [n]: device order -> caller id
+    mfd::DevBuf inv;   // int64 [n]: caller id -> device order
+    std::vector<int64_t> h_perm;
+    std::vector<int64_t> h_inv;
+};
+
+struct mfd_stencils {
+    const mfd_nodes* centres = nullptr;
+    const mfd_nodes* sources = nullptr;
+    int n = 0;
+    mfd::DevBuf idx;  // int32 [centres.n][n], source device ids, rows in centre device order
+};
+
+struct mfd_weights {
+    const mfd_stencils* st = nullptr;
+    int n_use = 0;
+    int nout = 0;
+    int op = 0;
+    int phs_k = 0, poly_m = 0, alpha = 0;
+    double delta = 0;
+    mfd::DevBuf w;  // double [nout][centres.n][n_use], centre device order
+};
+
+namespace mfd {
+
+// ------------------------------------------------------------ setup kernels
+
+mfd_status morton_order(mfd_ctx* ctx, int dim, int64_t n, const double* d_xyz_user,
+                        const double* period, double* d_xyz_sorted, int64_t* d_perm, int64_t* d_inv);
+mfd_status knn_build(const mfd_nodes* centres, const mfd_nodes* sources, int n, int32_t* d_idx);
+mfd_status weights_solve(const mfd_stencils* st, int n_use, int phs_k, int poly_m, int op, int alpha,
+                         double delta, double* d_w);
+
+}  // namespace mfd

@@ -1,0 +1,122 @@
+// kernels.cuh -- the fused leapfrog half-step kernels (Eq. 19 and its 3D form).
+//
+// Layout in HBM (device, Morton order of each node set):
+//  * stencil index and weight streams are "sliced": nodes are grouped in
+//    slices of 32 (one warp); within a slice, chunk c of 4 consecutive
+//    stencil entries of node 32 s + l sits at ((s * C + c) * 32 + l) * 4.
+//    A warp's 128-bit loads of one chunk cover 512 contiguous bytes, and a
+//    thread owns one node (one node per thread, no reductions). Rows are
+//    padded to a multiple of 4 entries with weight 0 and a valid index.
+//  * fields are array-of-structures: 2D collocated {Ez, Hx, Hy, ce} per node
+//    (one 16-byte gather brings all three fields of a neighbour); staggered
+//    {Hx, Hy} on the H set and Ez + ce on the E set; 3D {Ex, Ey, Ez, ce} and
+//    {Hx, Hy, Hz, 0}. ce = dt / (eps0 eps_r) of the node, 0 at a PEC node in 2D.
+//  * weight and index streams are read with L1::no_allocate so that L1 keeps
+//    the gathered fields of the Morton neighbourhood.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mfd {
+
+struct __align__(32) dbl4 {
+    double x, y, z, w;
+};
+
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+    using V2 = float2;
+    using V4 = float4;
+};
+template <> struct Vec<double> {
+    using V2 = double2;
+    using V4 = dbl4;
+};
+
+// ---- streamed (read once) loads: bypass L1 allocation
+__device__ __forceinline__ int4 ld_stream(const int4* p) {
+    int4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+    float4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+__device__ __forceinline__ dbl4 ld_stream(const dbl4* p) {
+    dbl4 v;
+    const double2* q = reinterpret_cast<const double2*>(p);
+    asm("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(q));
+    asm("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(v.z), "=d"(v.w) : "l"(q + 1));
+    return v;
+}
+
+// ---- gathered (reused by neighbours) loads: through L1
+__device__ __forceinline__ float4 ld_gather(const float4* p) { return __ldg(p); }
+__device__ __forceinline__ dbl4 ld_gather(const dbl4* p) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    double2 a = __ldg(q), b = __ldg(q + 1);
+    return dbl4{a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ float2 ld_gather(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ double2 ld_gather(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ float ld_gather(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double ld_gather(const double* p) { return __ldg(p); }
+
+__device__ __forceinline__ void st4(float4* p, float4 v) { *p = v; }
+__device__ __forceinline__ void st4(dbl4* p, dbl4 v) {
+    double2* q = reinterpret_cast<double2*>(p);
+    q[0] = make_double2(v.x, v.y);
+    q[1] = make_double2(v.z, v.w);
+}
+
+// ---- stencil-sum accumulators
+// Plain: fused multiply-add in the working precision.
+template <typename T> struct AccPlain {
+    T s = T(0);
+    __device__ __forceinline__ void add(T w, T f) { s = fma(w, f, s); }
+    __device__ __forceinline__ T get() const { return s; }
+};
+// Compensated FP32 dot product (Ogita, Rump, Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005, Dot2): the exact product error comes
+// from one FMA, the addition error from Knuth's two-sum; both are carried in c.
+struct AccComp {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float w, float f) {
+        float p = __fmul_rn(w, f);
+        float e = __fmaf_rn(w, f, -p);
+        float t = __fadd_rn(s, p);
+        float z = __fsub_rn(t, s);
+        float r = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(r, e));
+    }
+    __device__ __forceinline__ float get() const { return __fadd_rn(s, c); }
+};
+template <typename T, bool COMP> struct AccSel { using type = AccPlain<T>; };
+template <> struct AccSel<float, true> { using type = AccComp; };
+
+// ---- kernel arguments
+template <typename T> struct StencilStreams {
+    const int4* idx_c = nullptr;  // curl index chunks (or the shared index)
+    const int4* idx_v = nullptr;  // HV index chunks (== idx_c when shared)
+    const typename Vec<T>::V4* wx = nullptr;
+    const typename Vec<T>::V4* wy = nullptr;
+    const typename Vec<T>::V4* wz = nullptr;
+    const typename Vec<T>::V4* wv = nullptr;
+    int nc = 0, nv = 0, ni = 0;  // chunks per row: curl weights, HV weights, index (shared: max)
+    int64_t n = 0;               // nodes
+};
+
+template <typename T> struct Coefs {
+    T ch;     // dt / mu0
+    T gamma;  // Eq. 18 coefficient
+};
+
+}  // namespace mfd

@@ -1,0 +1,781 @@
+// sim.cu -- the stepped simulation behind mfd_sim_* (include/mfd.h): packing of
+// weights and stencils into the sliced streams of kernels.cuh, field and
+// material upload, soft sources and probes, graph-captured stepping, energy.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+#include "step.cuh"
+
+namespace mfd {
+
+enum Layout { COLLOC2D = 0, STAG2D = 1, COLLOC3D = 2 };
+
+constexpr int GRAPH_STEPS = 32;  // steps per captured graph (even: ping-pong parity returns)
+
+// ------------------------------------------------------------ packing kernels
+
+// sliced layout: element e -> (slice s, chunk c, lane l, entry q)
+__global__ void k_pack_idx(const int32_t* __restrict__ src, int stride, int64_t N, int n_use, int chunks,
+                           int32_t* __restrict__ dst, int64_t total) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    int q = (int)(e & 3);
+    int lane = (int)((e >> 2) & 31);
+    int64_t rest = e >> 7;
+    int c = (int)(rest % chunks);
+    int64_t s = rest / chunks;
+    int64_t node = s * 32 + lane;
+    int entry = c * 4 + q;
+    int32_t v = 0;
+    if (node < N) v = src[node * stride + (entry < n_use ? entry : 0)];
+    dst[e] = v;
+}
+
+template <typename T>
+__global__ void k_pack_w(const double* __restrict__ w, int64_t N, int n_use, int chunks, T* __restrict__ dst,
+                         int64_t total) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    int q = (int)(e & 3);
+    int lane = (int)((e >> 2) & 31);
+    int64_t rest = e >> 7;
+    int c = (int)(rest % chunks);
+    int64_t s = rest / chunks;
+    int64_t node = s * 32 + lane;
+    int entry = c * 4 + q;
+    dst[e] = (node < N && entry < n_use) ? (T)w[node * n_use + entry] : (T)0;
+}
+
+template <typename T>
+__global__ void k_scatter(const double* __restrict__ src, const int64_t* __restrict__ inv, int64_t n,
+                          T* __restrict__ base, int stride, int offset) {
+    int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    base[inv[u] * stride + offset] = (T)src[u];
+}
+
+template <typename T>
+__global__ void k_gather(const T* __restrict__ base, int stride, int offset, const int64_t* __restrict__ inv, int64_t n,
+                         double* __restrict__ dst) {
+    int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    dst[u] = (double)base[inv[u] * stride + offset];
+}
+
+// ce_i = dt / (eps0 eps_r,i) (0 on 2D PEC nodes), eps_r and held masks in device order
+template <typename T>
+__global__ void k_materials(const double* __restrict__ eps_user, const uint8_t* __restrict__ pec_user,
+                            const int64_t* __restrict__ perm, int64_t n, double dt_eps0, bool pec_zeroes_ce,
+                            T* __restrict__ ce, int ce_stride, int ce_offset, double* __restrict__ eps_dev,
+                            uint8_t* __restrict__ mask_dev) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t u = perm[k];
+    double er = eps_user ? eps_user[u] : 1.0;
+    uint8_t m = pec_user ? pec_user[u] : 0;
+    eps_dev[k] = er;
+    mask_dev[k] = m;
+    double c = dt_eps0 / er;
+    if (pec_zeroes_ce && m) c = 0.0;
+    ce[k * ce_stride + ce_offset] = (T)c;
+}
+
+// hold PEC components at zero: 2D Ez (comps 1 = stride offset), 3D tangential components
+template <typename T>
+__global__ void k_zero_held(T* __restrict__ E, int stride, const uint8_t* __restrict__ mask, int64_t n, bool three_d) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    unsigned m = mask[k];
+    if (!m) return;
+    if (!three_d) {
+        E[k * stride] = T(0);
+        return;
+    }
+    if (m & 6u) E[k * stride + 0] = T(0);
+    if (m & 5u) E[k * stride + 1] = T(0);
+    if (m & 3u) E[k * stride + 2] = T(0);
+}
+
+// soft Ricker sources after the E update, then probes, then the step counter
+template <typename T>
+__global__ void k_post(T* __restrict__ ez, int ez_stride, const uint8_t* __restrict__ mask, unsigned held_bits,
+                       int nsrc, const int64_t* __restrict__ sn, const double* __restrict__ sa,
+                       const double* __restrict__ sf, const double* __restrict__ st0, int nprobe,
+                       const int64_t* __restrict__ pn, T* __restrict__ pbuf, int64_t pcap,
+                       const int64_t* __restrict__ pstep0, int64_t* __restrict__ counter, double dt) {
+    __shared__ int64_t n_s;
+    if (threadIdx.x == 0) n_s = *counter;
+    __syncthreads();
+    const int64_t n = n_s;
+    const double t1 = (double)(n + 1) * dt;
+    const double pi = 3.14159265358979323846;
+    for (int s = threadIdx.x; s < nsrc; s += blockDim.x) {
+        const int64_t i = sn[s];
+        if (mask && (mask[i] & held_bits)) continue;
+        double a = pi * sf[s] * (t1 - st0[s]);
+        a = a * a;
+        const double r = (1.0 - 2.0 * a) * exp(-a);
+        atomicAdd(ez + i * ez_stride, (T)(sa[s] * r));
+    }
+    __syncthreads();
+    if (nprobe > 0) {
+        const int64_t rec = n - *pstep0;
+        if (rec >= 0 && rec < pcap)
+            for (int p = threadIdx.x; p < nprobe; p += blockDim.x) pbuf[rec * nprobe + p] = ez[pn[p] * ez_stride];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *counter = n + 1;
+}
+
+__global__ void k_sum(const double* __restrict__ partial, int n, double* __restrict__ out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) s += partial[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+}  // namespace mfd
+
+using namespace mfd;
+
+struct PackedStencil {
+    DevBuf idx_c, idx_v, wx, wy, wz, wv;
+    int nc = 0, nv = 0, ni = 0;
+    int64_t n = 0;
+};
+
+struct mfd_sim {
+    mfd_ctx* ctx = nullptr;
+    mfd_sim_desc d{};
+    Layout layout = COLLOC2D;
+    bool fp64 = false, comp = false;
+    size_t rs = 4;  // bytes per real
+    const mfd_nodes* eset = nullptr;
+    const mfd_nodes* hset = nullptr;
+    int64_t ne = 0, nh = 0;
+    PackedStencil hp, ep;  // H-pass and E-pass streams (collocated: ep unused)
+    DevBuf s0, s1, s2, s3, s4, s5;
+    DevBuf eps, mask, counter, pstep0;
+    bool has_mask = false;
+    DevBuf src_node, src_amp, src_f0, src_t0;
+    int nsrc = 0;
+    DevBuf probe_node, probe_buf;
+    int nprobe = 0;
+    int64_t probe_cap = 0, probe_from = 0;
+    DevBuf partial, energy_out;
+    int64_t steps = 0;
+    int parity = 0;
+    cudaGraphExec_t graph = nullptr;
+    bool graph_ok = false;
+    std::vector<cudaEvent_t> events;
+    ~mfd_sim() {
+        if (graph) cudaGraphExecDestroy(graph);
+        for (auto e : events) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+mfd_status pack_stream(mfd_ctx* ctx, const mfd_stencils* st, int n_use, int chunks, DevBuf& out) {
+    const int64_t N = st->centres->n;
+    const int64_t slices = (N + 31) / 32;
+    const int64_t total = slices * chunks * 128;
+    MFD_TRY(out.alloc(total * 4));
+    k_pack_idx<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(st->idx.as<int32_t>(), st->n, N, n_use,
+                                                                         chunks, out.as<int32_t>(), total);
+    MFD_CUDA(cudaGetLastError());
+    return MFD_OK;
+}
+
+mfd_status pack_weights(mfd_ctx* ctx, const mfd_weights* w, int out_index, int chunks, bool fp64, DevBuf& out) {
+    const int64_t N = w->st->centres->n;
+    const int64_t slices = (N + 31) / 32;
+    const int64_t total = slices * chunks * 128;
+    MFD_TRY(out.alloc(total * (fp64 ? 8 : 4)));
+    const double* src = w->w.as<double>() + (int64_t)out_index * N * w->n_use;
+    unsigned g = (unsigned)((total + 255) / 256);
+    if (fp64) k_pack_w<double><<<g, 256, 0, ctx->stream>>>(src, N, w->n_use, chunks, out.as<double>(), total);
+    else k_pack_w<float><<<g, 256, 0, ctx->stream>>>(src, N, w->n_use, chunks, out.as<float>(), total);
+    MFD_CUDA(cudaGetLastError());
+    return MFD_OK;
+}
+
+int chunks_of(int n) { return (n + 3) / 4; }
+
+// packs the curl and HV streams of one pass
+mfd_status pack_pass(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* hv, int dim, bool fp64, PackedStencil& p) {
+    p.n = curl->st->centres->n;
+    p.nc = chunks_of(curl->n_use);
+    p.nv = chunks_of(hv->n_use);
+    const bool shared = curl->st == hv->st;
+    if (shared) {
+        p.ni = std::max(p.nc, p.nv);
+        MFD_TRY(pack_stream(ctx, curl->st, std::max(curl->n_use, hv->n_use), p.ni, p.idx_c));
+    } else {
+        p.ni = p.nc;
+        MFD_TRY(pack_stream(ctx, curl->st, curl->n_use, p.nc, p.idx_c));
+        MFD_TRY(pack_stream(ctx, hv->st, hv->n_use, p.nv, p.idx_v));
+    }
+    MFD_TRY(pack_weights(ctx, curl, 0, p.nc, fp64, p.wx));
+    MFD_TRY(pack_weights(ctx, curl, 1, p.nc, fp64, p.wy));
+    if (dim == 3) MFD_TRY(pack_weights(ctx, curl, 2, p.nc, fp64, p.wz));
+    MFD_TRY(pack_weights(ctx, hv, 0, p.nv, fp64, p.wv));
+    return MFD_OK;
+}
+
+template <typename T> StencilStreams<T> streams(const PackedStencil& p) {
+    StencilStreams<T> s;
+    s.idx_c = p.idx_c.as<const int4>();
+    s.idx_v = p.idx_v.p ? p.idx_v.as<const int4>() : s.idx_c;
+    s.wx = p.wx.as<const typename Vec<T>::V4>();
+    s.wy = p.wy.as<const typename Vec<T>::V4>();
+    s.wz = p.wz.p ? p.wz.as<const typename Vec<T>::V4>() : nullptr;
+    s.wv = p.wv.as<const typename Vec<T>::V4>();
+    s.nc = p.nc;
+    s.nv = p.nv;
+    s.ni = p.ni;
+    s.n = p.n;
+    return s;
+}
+
+Launch2D make2d(mfd_sim* sim, int parity) {
+    Launch2D L;
+    L.staggered = sim->layout == STAG2D;
+    L.fp64 = sim->fp64;
+    L.comp = sim->comp;
+    L.hs.f = streams<float>(sim->hp);
+    L.hs.d = streams<double>(sim->hp);
+    if (L.staggered) {
+        L.es.f = streams<float>(sim->ep);
+        L.es.d = streams<double>(sim->ep);
+    }
+    L.kf.ch = (float)(sim->d.dt / sim->d.mu0);
+    L.kf.gamma = (float)sim->d.gamma;
+    L.kd.ch = sim->d.dt / sim->d.mu0;
+    L.kd.gamma = sim->d.gamma;
+    if (!L.staggered) {
+        L.A = sim->s0.p;
+        L.B = sim->s1.p;
+    } else {
+        DevBuf* E[2] = {&sim->s0, &sim->s1};
+        DevBuf* H[2] = {&sim->s2, &sim->s3};
+        L.stag.ez = E[parity]->p;
+        L.stag.ezn = E[parity ^ 1]->p;
+        L.stag.h = H[parity]->p;
+        L.stag.hn = H[parity ^ 1]->p;
+        L.stag.ce = sim->s4.p;
+    }
+    return L;
+}
+
+Launch3D make3d(mfd_sim* sim, int parity) {
+    Launch3D L;
+    L.fp64 = sim->fp64;
+    L.comp = sim->comp;
+    L.s.f = streams<float>(sim->hp);
+    L.s.d = streams<double>(sim->hp);
+    L.kf.ch = (float)(sim->d.dt / sim->d.mu0);
+    L.kf.gamma = (float)sim->d.gamma;
+    L.kd.ch = sim->d.dt / sim->d.mu0;
+    L.kd.gamma = sim->d.gamma;
+    DevBuf* H[2] = {&sim->s2, &sim->s3};
+    L.E = sim->s0.p;
+    L.Es = sim->s1.p;
+    L.H = H[parity]->p;
+    L.Hn = H[parity ^ 1]->p;
+    L.wall = sim->has_mask ? sim->mask.as<const uint8_t>() : nullptr;
+    return L;
+}
+
+// where Ez of the current state lives: base pointer, stride (reals), byte size of a real
+void ez_location(mfd_sim* sim, int parity_after, void** base, int* stride) {
+    if (sim->layout == COLLOC2D) {
+        *base = sim->s0.p;
+        *stride = 4;
+    } else if (sim->layout == STAG2D) {
+        *base = parity_after ? sim->s1.p : sim->s0.p;
+        *stride = 1;
+    } else {
+        *base = (char*)sim->s0.p + 2 * sim->rs;
+        *stride = 4;
+    }
+}
+
+cudaError_t launch_post(mfd_sim* sim, int parity_after) {
+    void* ez;
+    int stride;
+    ez_location(sim, parity_after, &ez, &stride);
+    const uint8_t* mask = sim->has_mask ? sim->mask.as<const uint8_t>() : nullptr;
+    unsigned held = sim->layout == COLLOC3D ? 3u : 0xFFu;
+    const double dt = sim->d.dt;
+    if (sim->fp64)
+        k_post<double><<<1, 256, 0, sim->ctx->stream>>>(
+            (double*)ez, stride, mask, held, sim->nsrc, sim->src_node.as<int64_t>(), sim->src_amp.as<double>(),
+            sim->src_f0.as<double>(), sim->src_t0.as<double>(), sim->nprobe, sim->probe_node.as<int64_t>(),
+            sim->probe_buf.as<double>(), sim->probe_cap, sim->pstep0.as<int64_t>(), sim->counter.as<int64_t>(), dt);
+    else
+        k_post<float><<<1, 256, 0, sim->ctx->stream>>>(
+            (float*)ez, stride, mask, held, sim->nsrc, sim->src_node.as<int64_t>(), sim->src_amp.as<double>(),
+            sim->src_f0.as<double>(), sim->src_t0.as<double>(), sim->nprobe, sim->probe_node.as<int64_t>(),
+            sim->probe_buf.as<float>(), sim->probe_cap, sim->pstep0.as<int64_t>(), sim->counter.as<int64_t>(), dt);
+    return cudaGetLastError();
+}
+
+// enqueues one step; events (optional): before H, between H and E, after E
+cudaError_t enqueue_step(mfd_sim* sim, cudaEvent_t* ev) {
+    cudaStream_t s = sim->ctx->stream;
+    cudaError_t e;
+    const int p = sim->parity;
+    const int pn = (sim->layout == COLLOC2D) ? p : (p ^ 1);
+    if (ev) cudaEventRecord(ev[0], s);
+    if (sim->layout == COLLOC3D) {
+        Launch3D L = make3d(sim, p);
+        if ((e = launch_3d(L, 0, s)) != cudaSuccess) return e;
+        if (ev) cudaEventRecord(ev[1], s);
+        if ((e = launch_3d(L, 1, s)) != cudaSuccess) return e;
+    } else {
+        Launch2D L = make2d(sim, p);
+        if ((e = launch_2d(L, 0, s)) != cudaSuccess) return e;
+        if (ev) cudaEventRecord(ev[1], s);
+        if ((e = launch_2d(L, 1, s)) != cudaSuccess) return e;
+    }
+    if (ev) cudaEventRecord(ev[2], s);
+    if ((e = launch_post(sim, pn)) != cudaSuccess) return e;
+    sim->parity = pn;
+    sim->steps += 1;
+    return cudaSuccess;
+}
+
+mfd_status ensure_graph(mfd_sim* sim) {
+    if (sim->graph_ok) return MFD_OK;
+    if (sim->graph) {
+        cudaGraphExecDestroy(sim->graph);
+        sim->graph = nullptr;
+    }
+    cudaStream_t s = sim->ctx->stream;
+    const int64_t steps0 = sim->steps;
+    const int par0 = sim->parity;
+    MFD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < GRAPH_STEPS && e == cudaSuccess; ++k) e = enqueue_step(sim, nullptr);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    sim->steps = steps0;
+    sim->parity = par0;
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(MFD_ERR_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&sim->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(MFD_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    sim->graph_ok = true;
+    return MFD_OK;
+}
+
+mfd_status upload(mfd_ctx* ctx, DevBuf& dst, const void* host, size_t bytes) {
+    MFD_TRY(dst.alloc(bytes));
+    if (bytes) MFD_CUDA(cudaMemcpyAsync(dst.p, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    return MFD_OK;
+}
+
+mfd_status check_set(const mfd_weights* curl, const mfd_weights* hv, const mfd_nodes* centres,
+                     const mfd_nodes* curl_src) {
+    if (!curl || !hv) return fail(MFD_ERR_ARG, "missing weights");
+    if (curl->op != MFD_OP_GRAD && curl->op != MFD_OP_GRAD_VFD) return fail(MFD_ERR_ARG, "curl weights must be first derivatives");
+    if (hv->op != MFD_OP_LAP_POW) return fail(MFD_ERR_ARG, "hyperviscosity weights must be Delta^alpha");
+    if (curl->st->centres != centres || hv->st->centres != centres) return fail(MFD_ERR_ARG, "weights on a different centre set");
+    if (hv->st->sources != centres) return fail(MFD_ERR_ARG, "hyperviscosity stencils must be own-set");
+    if (curl->st->sources != curl_src) return fail(MFD_ERR_ARG, "curl stencils must take the other field's nodes");
+    return MFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mfd_status mfd_sim_create(mfd_ctx* ctx, const mfd_sim_desc* desc, mfd_sim** out) {
+    if (!ctx || !desc || !out) return fail(MFD_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (desc->dim != 2 && desc->dim != 3) return fail(MFD_ERR_ARG, "dim must be 2 or 3");
+    if (desc->precision != MFD_FP32 && desc->precision != MFD_FP64) return fail(MFD_ERR_ARG, "unknown precision");
+    if (desc->nrhs != 1) return fail(MFD_ERR_ARG, "mfd_sim steps one right-hand side; use the batched API for more");
+    if (!(desc->dt > 0) || !(desc->eps0 > 0) || !(desc->mu0 > 0)) return fail(MFD_ERR_ARG, "dt, eps0, mu0 must be > 0");
+    if (!desc->h_curl || !desc->e_curl) return fail(MFD_ERR_ARG, "missing curl weights");
+    const mfd_nodes* H = desc->h_curl->st->centres;
+    const mfd_nodes* E = desc->e_curl->st->centres;
+    MFD_TRY(check_set(desc->h_curl, desc->h_hv, H, E));
+    MFD_TRY(check_set(desc->e_curl, desc->e_hv, E, H));
+    if (E->ctx != ctx) return fail(MFD_ERR_ARG, "weights belong to another context");
+    if (E->dim != desc->dim) return fail(MFD_ERR_ARG, "dim differs from the node sets");
+    const bool colloc = (E == H);
+    if (colloc && (desc->h_curl != desc->e_curl || desc->h_hv != desc->e_hv))
+        return fail(MFD_ERR_ARG, "collocated: h_curl == e_curl and h_hv == e_hv expected");
+    if (desc->dim == 3 && !colloc) return fail(MFD_ERR_ARG, "3D supports the collocated layout only");
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    mfd_sim* sim = new (std::nothrow) mfd_sim();
+    if (!sim) return fail(MFD_ERR_OOM, "host allocation failed");
+    sim->ctx = ctx;
+    sim->d = *desc;
+    sim->fp64 = desc->precision == MFD_FP64;
+    sim->comp = !sim->fp64 && desc->compensated;
+    sim->rs = sim->fp64 ? 8 : 4;
+    sim->eset = E;
+    sim->hset = H;
+    sim->ne = E->n;
+    sim->nh = H->n;
+    sim->layout = desc->dim == 3 ? COLLOC3D : (colloc ? COLLOC2D : STAG2D);
+    auto bail = [&](mfd_status st) {
+        delete sim;
+        return st;
+    };
+    mfd_status st;
+    if ((st = pack_pass(ctx, desc->h_curl, desc->h_hv, desc->dim, sim->fp64, sim->hp))) return bail(st);
+    if (sim->layout == STAG2D && (st = pack_pass(ctx, desc->e_curl, desc->e_hv, 2, sim->fp64, sim->ep)))
+        return bail(st);
+    const size_t rs = sim->rs;
+    const int64_t ne = sim->ne, nh = sim->nh;
+    if (sim->layout == COLLOC2D) {
+        if ((st = sim->s0.alloc(ne * 4 * rs)) || (st = sim->s1.alloc(ne * 4 * rs))) return bail(st);
+    } else if (sim->layout == STAG2D) {
+        if ((st = sim->s0.alloc(ne * rs)) || (st = sim->s1.alloc(ne * rs)) || (st = sim->s2.alloc(nh * 2 * rs)) ||
+            (st = sim->s3.alloc(nh * 2 * rs)) || (st = sim->s4.alloc(ne * rs)))
+            return bail(st);
+    } else {
+        if ((st = sim->s0.alloc(ne * 4 * rs)) || (st = sim->s1.alloc(ne * 4 * rs)) || (st = sim->s2.alloc(ne * 4 * rs)) ||
+            (st = sim->s3.alloc(ne * 4 * rs)))
+            return bail(st);
+    }
+    for (DevBuf* b : {&sim->s0, &sim->s1, &sim->s2, &sim->s3, &sim->s4})
+        if (b->p) cudaMemsetAsync(b->p, 0, b->bytes, ctx->stream);
+    const int64_t nmax = std::max(ne, nh);
+    if ((st = sim->eps.alloc(ne * 8)) || (st = sim->mask.alloc(ne)) || (st = sim->counter.alloc(8)) ||
+        (st = sim->pstep0.alloc(8)) || (st = sim->partial.alloc(((nmax + 255) / 256) * 8)) ||
+        (st = sim->energy_out.alloc(8)))
+        return bail(st);
+    cudaMemsetAsync(sim->counter.p, 0, 8, ctx->stream);
+    cudaMemsetAsync(sim->pstep0.p, 0, 8, ctx->stream);
+    *out = sim;
+    st = mfd_set_materials(sim, nullptr, nullptr);
+    if (st) {
+        *out = nullptr;
+        return bail(st);
+    }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        delete sim;
+        return fail(MFD_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return MFD_OK;
+}
+
+mfd_status mfd_set_materials(mfd_sim* sim, const double* eps_r, const uint8_t* pec) {
+    if (!sim) return fail(MFD_ERR_ARG, "sim is NULL");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    const int64_t ne = sim->ne;
+    if (eps_r)
+        for (int64_t i = 0; i < ne; ++i)
+            if (!(eps_r[i] > 0)) return fail(MFD_ERR_ARG, "eps_r must be > 0");
+    DevBuf de, dp;
+    if (eps_r) MFD_TRY(upload(ctx, de, eps_r, ne * 8));
+    if (pec) MFD_TRY(upload(ctx, dp, pec, ne));
+    const double dt_eps0 = sim->d.dt / sim->d.eps0;
+    void* ce;
+    int stride, offset;
+    if (sim->layout == STAG2D) {
+        ce = sim->s4.p;
+        stride = 1;
+        offset = 0;
+    } else {
+        ce = sim->s0.p;
+        stride = 4;
+        offset = 3;
+    }
+    const bool zero_ce = sim->layout != COLLOC3D;
+    unsigned g = (unsigned)((ne + 255) / 256);
+    if (sim->fp64)
+        k_materials<double><<<g, 256, 0, ctx->stream>>>(de.as<double>(), dp.as<uint8_t>(), sim->eset->perm.as<int64_t>(),
+                                                        ne, dt_eps0, zero_ce, (double*)ce, stride, offset,
+                                                        sim->eps.as<double>(), sim->mask.as<uint8_t>());
+    else
+        k_materials<float><<<g, 256, 0, ctx->stream>>>(de.as<double>(), dp.as<uint8_t>(), sim->eset->perm.as<int64_t>(),
+                                                       ne, dt_eps0, zero_ce, (float*)ce, stride, offset,
+                                                       sim->eps.as<double>(), sim->mask.as<uint8_t>());
+    MFD_CUDA(cudaGetLastError());
+    sim->has_mask = pec != nullptr;
+    sim->graph_ok = false;
+    if (sim->has_mask) {
+        void* ez;
+        int st2;
+        ez_location(sim, sim->parity, &ez, &st2);
+        void* base = sim->layout == COLLOC3D ? sim->s0.p : ez;
+        int stride2 = sim->layout == COLLOC3D ? 4 : st2;
+        if (sim->fp64)
+            k_zero_held<double><<<g, 256, 0, ctx->stream>>>((double*)base, stride2, sim->mask.as<uint8_t>(), ne,
+                                                            sim->layout == COLLOC3D);
+        else
+            k_zero_held<float><<<g, 256, 0, ctx->stream>>>((float*)base, stride2, sim->mask.as<uint8_t>(), ne,
+                                                           sim->layout == COLLOC3D);
+        MFD_CUDA(cudaGetLastError());
+    }
+    MFD_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MFD_OK;
+}
+
+// locates (buffer, stride, offset, node set) of a component in the current state
+static mfd_status locate(mfd_sim* sim, int comp, void** base, int* stride, int* offset, const mfd_nodes** set) {
+    const bool is_e = comp <= MFD_EZ;
+    if (comp < 0 || comp > MFD_HZ) return fail(MFD_ERR_ARG, "unknown component");
+    if (sim->layout != COLLOC3D && comp != MFD_EZ && comp != MFD_HX && comp != MFD_HY)
+        return fail(MFD_ERR_ARG, "TMz has Ez, Hx, Hy only");
+    *set = is_e ? sim->eset : sim->hset;
+    const int p = sim->parity;
+    if (sim->layout == COLLOC2D) {
+        *base = sim->s0.p;
+        *stride = 4;
+        *offset = comp == MFD_EZ ? 0 : (comp == MFD_HX ? 1 : 2);
+    } else if (sim->layout == STAG2D) {
+        if (is_e) {
+            *base = p ? sim->s1.p : sim->s0.p;
+            *stride = 1;
+            *offset = 0;
+        } else {
+            *base = p ? sim->s3.p : sim->s2.p;
+            *stride = 2;
+            *offset = comp == MFD_HX ? 0 : 1;
+        }
+    } else {
+        *stride = 4;
+        if (is_e) {
+            *base = sim->s0.p;
+            *offset = comp - MFD_EX;
+        } else {
+            *base = p ? sim->s3.p : sim->s2.p;
+            *offset = comp - MFD_HX;
+        }
+    }
+    return MFD_OK;
+}
+
+mfd_status mfd_set_field(mfd_sim* sim, int comp, int rhs, const double* host) {
+    if (!sim || !host) return fail(MFD_ERR_ARG, "NULL argument");
+    if (rhs != 0) return fail(MFD_ERR_ARG, "rhs out of range");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    void* base;
+    int stride, offset;
+    const mfd_nodes* set;
+    MFD_TRY(locate(sim, comp, &base, &stride, &offset, &set));
+    DevBuf tmp;
+    MFD_TRY(upload(ctx, tmp, host, set->n * 8));
+    unsigned g = (unsigned)((set->n + 255) / 256);
+    if (sim->fp64)
+        k_scatter<double><<<g, 256, 0, ctx->stream>>>(tmp.as<double>(), set->inv.as<int64_t>(), set->n, (double*)base,
+                                                      stride, offset);
+    else
+        k_scatter<float><<<g, 256, 0, ctx->stream>>>(tmp.as<double>(), set->inv.as<int64_t>(), set->n, (float*)base,
+                                                     stride, offset);
+    MFD_CUDA(cudaGetLastError());
+    if (comp <= MFD_EZ && sim->has_mask) {
+        if (sim->fp64)
+            k_zero_held<double><<<g, 256, 0, ctx->stream>>>((double*)base + (sim->layout == COLLOC3D ? 0 : offset),
+                                                            stride, sim->mask.as<uint8_t>(), set->n, sim->layout == COLLOC3D);
+        else
+            k_zero_held<float><<<g, 256, 0, ctx->stream>>>((float*)base + (sim->layout == COLLOC3D ? 0 : offset),
+                                                           stride, sim->mask.as<uint8_t>(), set->n, sim->layout == COLLOC3D);
+        MFD_CUDA(cudaGetLastError());
+    }
+    if (comp == MFD_EZ) {
+        MFD_CUDA(cudaMemsetAsync(sim->counter.p, 0, 8, ctx->stream));
+        MFD_CUDA(cudaMemsetAsync(sim->pstep0.p, 0, 8, ctx->stream));
+        sim->steps = 0;
+        sim->probe_from = 0;
+    }
+    MFD_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MFD_OK;
+}
+
+mfd_status mfd_get_field(mfd_sim* sim, int comp, int rhs, double* host) {
+    if (!sim || !host) return fail(MFD_ERR_ARG, "NULL argument");
+    if (rhs != 0) return fail(MFD_ERR_ARG, "rhs out of range");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    void* base;
+    int stride, offset;
+    const mfd_nodes* set;
+    MFD_TRY(locate(sim, comp, &base, &stride, &offset, &set));
+    DevBuf tmp;
+    MFD_TRY(tmp.alloc(set->n * 8));
+    unsigned g = (unsigned)((set->n + 255) / 256);
+    if (sim->fp64)
+        k_gather<double><<<g, 256, 0, ctx->stream>>>((const double*)base, stride, offset, set->inv.as<int64_t>(), set->n,
+                                                     tmp.as<double>());
+    else
+        k_gather<float><<<g, 256, 0, ctx->stream>>>((const float*)base, stride, offset, set->inv.as<int64_t>(), set->n,
+                                                    tmp.as<double>());
+    MFD_CUDA(cudaGetLastError());
+    MFD_CUDA(cudaMemcpyAsync(host, tmp.p, set->n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    MFD_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MFD_OK;
+}
+
+mfd_status mfd_set_sources(mfd_sim* sim, int count, const int64_t* node, const int32_t* rhs, const double* amp,
+                           const double* f0, const double* t0) {
+    if (!sim || count < 0) return fail(MFD_ERR_ARG, "bad arguments");
+    if (count > 0 && (!node || !amp || !f0 || !t0)) return fail(MFD_ERR_ARG, "NULL source arrays");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    std::vector<int64_t> dev_node(count);
+    for (int s = 0; s < count; ++s) {
+        if (node[s] < 0 || node[s] >= sim->ne) return fail(MFD_ERR_ARG, "source node out of range");
+        if (rhs && rhs[s] != 0) return fail(MFD_ERR_ARG, "source rhs out of range");
+        if (!(f0[s] > 0)) return fail(MFD_ERR_ARG, "source frequency must be > 0");
+        dev_node[s] = sim->eset->h_inv[node[s]];
+    }
+    MFD_TRY(upload(ctx, sim->src_node, dev_node.data(), count * 8));
+    MFD_TRY(upload(ctx, sim->src_amp, amp, count * 8));
+    MFD_TRY(upload(ctx, sim->src_f0, f0, count * 8));
+    MFD_TRY(upload(ctx, sim->src_t0, t0, count * 8));
+    sim->nsrc = count;
+    sim->graph_ok = false;
+    MFD_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MFD_OK;
+}
+
+mfd_status mfd_set_probes(mfd_sim* sim, int count, const int64_t* node, int64_t capacity) {
+    if (!sim || count < 0 || capacity < 0) return fail(MFD_ERR_ARG, "bad arguments");
+    if (count > 0 && !node) return fail(MFD_ERR_ARG, "NULL probe array");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    std::vector<int64_t> dev_node(count);
+    for (int p = 0; p < count; ++p) {
+        if (node[p] < 0 || node[p] >= sim->ne) return fail(MFD_ERR_ARG, "probe node out of range");
+        dev_node[p] = sim->eset->h_inv[node[p]];
+    }
+    MFD_TRY(upload(ctx, sim->probe_node, dev_node.data(), count * 8));
+    MFD_TRY(sim->probe_buf.alloc(std::max<int64_t>(1, capacity * count) * sim->rs));
+    sim->nprobe = count;
+    sim->probe_cap = capacity;
+    sim->probe_from = sim->steps;
+    int64_t from = sim->steps;
+    MFD_CUDA(cudaMemcpyAsync(sim->pstep0.p, &from, 8, cudaMemcpyHostToDevice, ctx->stream));
+    sim->graph_ok = false;
+    MFD_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MFD_OK;
+}
+
+mfd_status mfd_step(mfd_sim* sim, int64_t nsteps) {
+    if (!sim || nsteps < 0) return fail(MFD_ERR_ARG, "bad arguments");
+    MFD_CUDA(cudaSetDevice(sim->ctx->device));
+    int64_t left = nsteps;
+    if (left >= 2 * GRAPH_STEPS) {
+        if (sim->parity) {
+            MFD_CUDA(enqueue_step(sim, nullptr));
+            --left;
+        }
+        MFD_TRY(ensure_graph(sim));
+        while (left >= GRAPH_STEPS) {
+            MFD_CUDA(cudaGraphLaunch(sim->graph, sim->ctx->stream));
+            sim->steps += GRAPH_STEPS;
+            left -= GRAPH_STEPS;
+        }
+    }
+    while (left > 0) {
+        MFD_CUDA(enqueue_step(sim, nullptr));
+        --left;
+    }
+    return MFD_OK;
+}
+
+mfd_status mfd_step_timed(mfd_sim* sim, int64_t nsteps, double* ms) {
+    if (!sim || nsteps < 0 || !ms) return fail(MFD_ERR_ARG, "bad arguments");
+    MFD_CUDA(cudaSetDevice(sim->ctx->device));
+    const size_t need = (size_t)nsteps * 3;
+    while (sim->events.size() < need) {
+        cudaEvent_t e;
+        MFD_CUDA(cudaEventCreate(&e));
+        sim->events.push_back(e);
+    }
+    for (int64_t k = 0; k < nsteps; ++k) MFD_CUDA(enqueue_step(sim, &sim->events[3 * k]));
+    MFD_CUDA(cudaStreamSynchronize(sim->ctx->stream));
+    double h = 0, e = 0;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        float a = 0, b = 0;
+        MFD_CUDA(cudaEventElapsedTime(&a, sim->events[3 * k], sim->events[3 * k + 1]));
+        MFD_CUDA(cudaEventElapsedTime(&b, sim->events[3 * k + 1], sim->events[3 * k + 2]));
+        h += a;
+        e += b;
+    }
+    ms[0] = h;
+    ms[1] = e;
+    return MFD_OK;
+}
+
+mfd_status mfd_read_probes(mfd_sim* sim, double* host, int64_t* steps) {
+    if (!sim) return fail(MFD_ERR_ARG, "sim is NULL");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    int64_t rec = std::min(sim->steps - sim->probe_from, sim->probe_cap);
+    if (rec < 0) rec = 0;
+    if (steps) *steps = rec;
+    if (!host || rec == 0 || sim->nprobe == 0) {
+        MFD_CUDA(cudaStreamSynchronize(ctx->stream));
+        return MFD_OK;
+    }
+    const int64_t count = rec * sim->nprobe;
+    if (sim->fp64) {
+        MFD_CUDA(cudaMemcpyAsync(host, sim->probe_buf.p, count * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        MFD_CUDA(cudaStreamSynchronize(ctx->stream));
+    } else {
+        std::vector<float> tmp(count);
+        MFD_CUDA(cudaMemcpyAsync(tmp.data(), sim->probe_buf.p, count * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        MFD_CUDA(cudaStreamSynchronize(ctx->stream));
+        for (int64_t i = 0; i < count; ++i) host[i] = tmp[i];
+    }
+    return MFD_OK;
+}
+
+mfd_status mfd_energy(mfd_sim* sim, double* u) {
+    if (!sim || !u) return fail(MFD_ERR_ARG, "NULL argument");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    const double eta2 = sim->d.mu0 / sim->d.eps0;
+    const int64_t nmax = std::max(sim->ne, sim->nh);
+    const unsigned grid = (unsigned)((nmax + 255) / 256);
+    if (sim->layout == COLLOC3D) {
+        MFD_CUDA(launch_energy_3d(make3d(sim, sim->parity), sim->eps.as<double>(), eta2, sim->partial.as<double>(), grid,
+                                  ctx->stream));
+    } else {
+        MFD_CUDA(launch_energy_2d(make2d(sim, sim->parity), sim->eps.as<double>(), sim->ne, eta2,
+                                  sim->partial.as<double>(), grid, ctx->stream));
+    }
+    k_sum<<<1, 256, 0, ctx->stream>>>(sim->partial.as<double>(), (int)grid, sim->energy_out.as<double>());
+    MFD_CUDA(cudaGetLastError());
+    MFD_CUDA(cudaMemcpyAsync(u, sim->energy_out.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    MFD_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MFD_OK;
+}
+
+int64_t mfd_sim_steps(const mfd_sim* sim) { return sim ? sim->steps : -1; }
+
+void mfd_sim_destroy(mfd_sim* sim) {
+    if (!sim) return;
+    cudaSetDevice(sim->ctx->device);
+    cudaStreamSynchronize(sim->ctx->stream);
+    delete sim;
+}
+
+}  // extern "C"

@@ -1,0 +1,274 @@
+// step3d.cu -- fused 3D full-vector half steps (Eq. 2 with the hyperviscosity
+// terms of Eqs. 17-18 on every component), collocated:
+//   H pass, node i:  H' = H + ch (-curl E + gamma Dv H),  E* = E + ce gamma Dv E
+//   E pass, node i:  E' = E* + ce curl H', then every component tangential to
+//                    a PEC wall the node sits on is held at 0.
+// curl F = (Dy Fz - Dz Fy, Dz Fx - Dx Fz, Dx Fy - Dy Fx).
+#include "kernels.cuh"
+#include "step.cuh"
+
+namespace mfd {
+
+template <typename T> struct Curl {
+    T dyz, dzy, dzx, dxz, dxy, dyx;  // Dy Fz, Dz Fy, Dz Fx, Dx Fz, Dx Fy, Dy Fx
+};
+
+template <typename T, int NC, int NV, bool SHARED, bool COMP>
+__device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typename Vec<T>::V4* __restrict__ E,
+                                        const typename Vec<T>::V4* __restrict__ H, int64_t i, Curl<T>& cu,
+                                        T vh[3], T ve[3]) {
+    using V4 = typename Vec<T>::V4;
+    using Acc = typename AccSel<T, COMP>::type;
+    const int nc = NC ? NC : s.nc;
+    const int nv = NV ? NV : s.nv;
+    const int64_t slice = i >> 5;
+    const int lane = (int)(i & 31);
+    Acc a_yz, a_zy, a_zx, a_xz, a_xy, a_yx, hx, hy, hz, ex, ey, ez;
+    const V4* px = s.wx + slice * nc * 32 + lane;
+    const V4* py = s.wy + slice * nc * 32 + lane;
+    const V4* pz = s.wz + slice * nc * 32 + lane;
+    const V4* pv = s.wv + slice * nv * 32 + lane;
+    auto curl4 = [&](const V4& wx, const V4& wy, const V4& wz, const V4* f) {
+        const T* wxa = &wx.x;
+        const T* wya = &wy.x;
+        const T* wza = &wz.x;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            a_yz.add(wya[q], f[q].z);
+            a_zy.add(wza[q], f[q].y);
+            a_zx.add(wza[q], f[q].x);
+            a_xz.add(wxa[q], f[q].z);
+            a_xy.add(wxa[q], f[q].y);
+            a_yx.add(wya[q], f[q].x);
+        }
+    };
+    auto hv4 = [&](const V4& wv, const V4* e, const V4* h) {
+        const T* wva = &wv.x;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            hx.add(wva[q], h[q].x);
+            hy.add(wva[q], h[q].y);
+            hz.add(wva[q], h[q].z);
+            ex.add(wva[q], e[q].x);
+            ey.add(wva[q], e[q].y);
+            ez.add(wva[q], e[q].z);
+        }
+    };
+    if constexpr (SHARED) {
+        const int ni = (NC && NV) ? (NC > NV ? NC : NV) : s.ni;
+        const int4* ip = s.idx_c + slice * ni * 32 + lane;
+#pragma unroll
+        for (int c = 0; c < ni; ++c) {
+            const int4 id = ld_stream(ip + c * 32);
+            V4 e[4], h[4];
+            e[0] = ld_gather(E + id.x);
+            e[1] = ld_gather(E + id.y);
+            e[2] = ld_gather(E + id.z);
+            e[3] = ld_gather(E + id.w);
+            if (c < nc) curl4(ld_stream(px + c * 32), ld_stream(py + c * 32), ld_stream(pz + c * 32), e);
+            if (c < nv) {
+                h[0] = ld_gather(H + id.x);
+                h[1] = ld_gather(H + id.y);
+                h[2] = ld_gather(H + id.z);
+                h[3] = ld_gather(H + id.w);
+                hv4(ld_stream(pv + c * 32), e, h);
+            }
+        }
+    } else {
+        const int4* ic = s.idx_c + slice * nc * 32 + lane;
+        const int4* iv = s.idx_v + slice * nv * 32 + lane;
+#pragma unroll
+        for (int c = 0; c < nc; ++c) {
+            const int4 id = ld_stream(ic + c * 32);
+            V4 e[4];
+            e[0] = ld_gather(E + id.x);
+            e[1] = ld_gather(E + id.y);
+            e[2] = ld_gather(E + id.z);
+            e[3] = ld_gather(E + id.w);
+            curl4(ld_stream(px + c * 32), ld_stream(py + c * 32), ld_stream(pz + c * 32), e);
+        }
+#pragma unroll
+        for (int c = 0; c < nv; ++c) {
+            const int4 id = ld_stream(iv + c * 32);
+            V4 e[4], h[4];
+            e[0] = ld_gather(E + id.x);
+            e[1] = ld_gather(E + id.y);
+            e[2] = ld_gather(E + id.z);
+            e[3] = ld_gather(E + id.w);
+            h[0] = ld_gather(H + id.x);
+            h[1] = ld_gather(H + id.y);
+            h[2] = ld_gather(H + id.z);
+            h[3] = ld_gather(H + id.w);
+            hv4(ld_stream(pv + c * 32), e, h);
+        }
+    }
+    cu.dyz = a_yz.get();
+    cu.dzy = a_zy.get();
+    cu.dzx = a_zx.get();
+    cu.dxz = a_xz.get();
+    cu.dxy = a_xy.get();
+    cu.dyx = a_yx.get();
+    vh[0] = hx.get();
+    vh[1] = hy.get();
+    vh[2] = hz.get();
+    ve[0] = ex.get();
+    ve[1] = ey.get();
+    ve[2] = ez.get();
+}
+
+template <typename T, int NC, int NV, bool SHARED, bool COMP>
+__global__ void __launch_bounds__(256) k_h3(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V4* __restrict__ E,
+                                            typename Vec<T>::V4* __restrict__ Es,
+                                            const typename Vec<T>::V4* __restrict__ H,
+                                            typename Vec<T>::V4* __restrict__ Hn) {
+    using V4 = typename Vec<T>::V4;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= s.n) return;
+    Curl<T> cu;
+    T vh[3], ve[3];
+    h3_node<T, NC, NV, SHARED, COMP>(s, E, H, i, cu, vh, ve);
+    const V4 h = ld_gather(H + i), e = ld_gather(E + i);
+    V4 ho, eo;
+    ho.x = h.x + k.ch * (-(cu.dyz - cu.dzy) + k.gamma * vh[0]);
+    ho.y = h.y + k.ch * (-(cu.dzx - cu.dxz) + k.gamma * vh[1]);
+    ho.z = h.z + k.ch * (-(cu.dxy - cu.dyx) + k.gamma * vh[2]);
+    ho.w = T(0);
+    eo.x = e.x + e.w * (k.gamma * ve[0]);
+    eo.y = e.y + e.w * (k.gamma * ve[1]);
+    eo.z = e.z + e.w * (k.gamma * ve[2]);
+    eo.w = e.w;
+    st4(Hn + i, ho);
+    st4(Es + i, eo);
+}
+
+template <typename T, int NC, bool SHARED, bool COMP>
+__global__ void __launch_bounds__(256) k_e3(StencilStreams<T> s, const typename Vec<T>::V4* __restrict__ Hn,
+                                            const typename Vec<T>::V4* __restrict__ Es,
+                                            const uint8_t* __restrict__ wall, typename Vec<T>::V4* __restrict__ E) {
+    using V4 = typename Vec<T>::V4;
+    using Acc = typename AccSel<T, COMP>::type;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= s.n) return;
+    const int nc = NC ? NC : s.nc;
+    const int ni = SHARED ? s.ni : nc;
+    const int64_t slice = i >> 5;
+    const int lane = (int)(i & 31);
+    const int4* ip = s.idx_c + slice * ni * 32 + lane;
+    const V4* px = s.wx + slice * nc * 32 + lane;
+    const V4* py = s.wy + slice * nc * 32 + lane;
+    const V4* pz = s.wz + slice * nc * 32 + lane;
+    Acc a_yz, a_zy, a_zx, a_xz, a_xy, a_yx;
+#pragma unroll
+    for (int c = 0; c < nc; ++c) {
+        const int4 id = ld_stream(ip + c * 32);
+        const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32), wz = ld_stream(pz + c * 32);
+        V4 f[4];
+        f[0] = ld_gather(Hn + id.x);
+        f[1] = ld_gather(Hn + id.y);
+        f[2] = ld_gather(Hn + id.z);
+        f[3] = ld_gather(Hn + id.w);
+        const T* wxa = &wx.x;
+        const T* wya = &wy.x;
+        const T* wza = &wz.x;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            a_yz.add(wya[q], f[q].z);
+            a_zy.add(wza[q], f[q].y);
+            a_zx.add(wza[q], f[q].x);
+            a_xz.add(wxa[q], f[q].z);
+            a_xy.add(wxa[q], f[q].y);
+            a_yx.add(wya[q], f[q].x);
+        }
+    }
+    const V4 e = ld_gather(Es + i);
+    V4 o;
+    o.x = e.x + e.w * (a_yz.get() - a_zy.get());
+    o.y = e.y + e.w * (a_zx.get() - a_xz.get());
+    o.z = e.z + e.w * (a_xy.get() - a_yx.get());
+    o.w = e.w;
+    const unsigned m = wall ? wall[i] : 0u;
+    if (m) {
+        // component b is tangential to the wall normal to axis a != b
+        if (m & 6u) o.x = T(0);
+        if (m & 5u) o.y = T(0);
+        if (m & 3u) o.z = T(0);
+    }
+    st4(E + i, o);
+}
+
+template <typename T, bool COMP>
+__global__ void __launch_bounds__(256) k_energy3(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V4* __restrict__ E,
+                                                 const typename Vec<T>::V4* __restrict__ H,
+                                                 const double* __restrict__ eps_r, double eta2,
+                                                 double* __restrict__ partial) {
+    using V4 = typename Vec<T>::V4;
+    __shared__ double red[256];
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double u = 0.0;
+    if (i < s.n) {
+        Curl<T> cu;
+        T vh[3], ve[3];
+        if (s.idx_v == s.idx_c)
+            h3_node<T, 0, 0, true, COMP>(s, E, H, i, cu, vh, ve);
+        else
+            h3_node<T, 0, 0, false, COMP>(s, E, H, i, cu, vh, ve);
+        const V4 h = H[i], e = E[i];
+        const double h1[3] = {(double)(h.x + k.ch * (-(cu.dyz - cu.dzy) + k.gamma * vh[0])),
+                              (double)(h.y + k.ch * (-(cu.dzx - cu.dxz) + k.gamma * vh[1])),
+                              (double)(h.z + k.ch * (-(cu.dxy - cu.dyx) + k.gamma * vh[2]))};
+        const double h0[3] = {(double)h.x, (double)h.y, (double)h.z};
+        const double ev[3] = {(double)e.x, (double)e.y, (double)e.z};
+        for (int a = 0; a < 3; ++a) {
+            double av = 0.5 * (h0[a] + h1[a]);
+            u += eps_r[i] * ev[a] * ev[a] + eta2 * av * av;
+        }
+    }
+    red[threadIdx.x] = u;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+template <typename T, bool COMP>
+static cudaError_t launch3(const Launch3D& L, const StencilStreams<T>& s, const Coefs<T>& k, int pass, cudaStream_t st) {
+    using V4 = typename Vec<T>::V4;
+    const unsigned grid = (unsigned)((s.n + 255) / 256);
+    const bool shared = s.idx_v == s.idx_c;
+    const V4* E = static_cast<const V4*>(L.E);
+    V4* Es = static_cast<V4*>(L.Es);
+    const V4* H = static_cast<const V4*>(L.H);
+    V4* Hn = static_cast<V4*>(L.Hn);
+    if (pass == 0) {
+        if (shared && s.nc == 10 && s.nv == 18) k_h3<T, 10, 18, true, COMP><<<grid, 256, 0, st>>>(s, k, E, Es, H, Hn);
+        else if (shared) k_h3<T, 0, 0, true, COMP><<<grid, 256, 0, st>>>(s, k, E, Es, H, Hn);
+        else k_h3<T, 0, 0, false, COMP><<<grid, 256, 0, st>>>(s, k, E, Es, H, Hn);
+    } else {
+        V4* Eo = const_cast<V4*>(E);
+        if (shared && s.nc == 10) k_e3<T, 10, true, COMP><<<grid, 256, 0, st>>>(s, Hn, Es, L.wall, Eo);
+        else if (shared) k_e3<T, 0, true, COMP><<<grid, 256, 0, st>>>(s, Hn, Es, L.wall, Eo);
+        else k_e3<T, 0, false, COMP><<<grid, 256, 0, st>>>(s, Hn, Es, L.wall, Eo);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_3d(const Launch3D& L, int pass, cudaStream_t st) {
+    if (L.fp64) return launch3<double, false>(L, L.s.d, L.kd, pass, st);
+    if (L.comp) return launch3<float, true>(L, L.s.f, L.kf, pass, st);
+    return launch3<float, false>(L, L.s.f, L.kf, pass, st);
+}
+
+cudaError_t launch_energy_3d(const Launch3D& L, const double* eps_r, double eta2, double* partial, unsigned grid,
+                             cudaStream_t st) {
+    if (L.fp64)
+        k_energy3<double, false><<<grid, 256, 0, st>>>(L.s.d, L.kd, (const dbl4*)L.E, (const dbl4*)L.H, eps_r, eta2, partial);
+    else if (L.comp)
+        k_energy3<float, true><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.E, (const float4*)L.H, eps_r, eta2, partial);
+    else
+        k_energy3<float, false><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.E, (const float4*)L.H, eps_r, eta2, partial);
+    return cudaGetLastError();
+}
+
+}  // namespace mfd
