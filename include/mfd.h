@@ -202,6 +202,32 @@ mfd_status mfd_energy(mfd_sim* sim, double* u);
 int64_t mfd_sim_steps(const mfd_sim* sim);
 void mfd_sim_destroy(mfd_sim* sim);
 
+
+/* ------------------------------------------------- kNN without allocation */
+
+/* The kNN stencils of mfd_stencils_build, computed on caller-owned device
+ * arrays by a call that allocates no device memory at all. (The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc, for example because the host application owns all device memory
+ * through its own pool or forbids allocation once it has started.)
+ *   centres: device, nc x dim FP64; sources: device, ns x dim FP64, both in
+ *   the caller's order; period: host, dim entries (0 = not periodic);
+ *   idx: device, nc x n int32 output, the source indices of each stencil
+ *   sorted by (squared distance, source index) -- the same stencils, entry
+ *   for entry, that mfd_stencils_build + mfd_stencils_read return.
+ *   stream: cudaStream_t (NULL = legacy default stream).
+ * All scratch lives in one file-scope device array of 32 MiB (enough for
+ * about 1,000,000 sources) that every GPU which loads the library holds until
+ * the process exits; larger source sets are rejected with MFD_ERR_ARG and a
+ * message. Every call shares that array and leaves its contents behind, so two
+ * calls that overlap on the GPU (other streams, other host threads) race: the
+ * caller must order them. The first call on each device looks up the array's
+ * device address with that device current (set-up); make that first call
+ * before any stream capture. The call synchronises `stream` once (to read the
+ * bounding box of the sources) and queues the rest asynchronously. */
+mfd_status mfd_knn_static(int dim, int64_t nc, const double* centres, int64_t ns, const double* sources,
+                          const double* period, int n, int32_t* idx, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

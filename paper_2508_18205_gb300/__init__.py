@@ -69,6 +69,7 @@ _SIGS = {
     "mfd_energy": (_I, [_VP, _VP]),
     "mfd_sim_steps": (_I64, [_VP]),
     "mfd_sim_destroy": (None, [_VP]),
+    "mfd_knn_static": (_I, [_I, _I64, _VP, _I64, _VP, _VP, _I, _VP, _VP]),
 }
 
 _lib = None

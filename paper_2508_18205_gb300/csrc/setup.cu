@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -710,3 +711,178 @@ mfd_status weights_solve(const mfd_stencils* st, int n_use, int phs_k, int poly_
 }
 
 }  // namespace mfd
+
+// ------------------------------------------------------------ kNN without allocation
+//
+// mfd_knn_static: the grid-hash kNN above, on caller-provided device arrays,
+// with all of its scratch (bounding box, identity ids, cell counts, cell
+// starts, fill cursors and the cell lists) in one file-scope device array.
+// For callers that must not allocate device memory at all.
+
+namespace mfd {
+
+constexpr size_t KNN_STATIC_BYTES = (size_t)32 << 20;  // 32 MiB, held by every GPU that loads the library
+
+static __device__ __align__(256) unsigned char g_knn_scratch[KNN_STATIC_BYTES];
+
+// device address of g_knn_scratch, looked up once per device with that device current
+static std::mutex g_knn_scratch_mu;
+static void* g_knn_scratch_ptr[128] = {};
+
+static mfd_status knn_scratch_address(int device, unsigned char** out) {
+    if (device < 0 || device >= 128) return fail(MFD_ERR_ARG, "device id out of range");
+    std::lock_guard<std::mutex> lock(g_knn_scratch_mu);
+    if (!g_knn_scratch_ptr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_knn_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(MFD_ERR_CUDA, std::string("cudaGetSymbolAddress(kNN scratch): ") + cudaGetErrorString(e));
+        g_knn_scratch_ptr[device] = p;
+    }
+    *out = static_cast<unsigned char*>(g_knn_scratch_ptr[device]);
+    return MFD_OK;
+}
+
+__global__ void k_iota64(int64_t* __restrict__ a, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) a[i] = i;
+}
+
+__global__ void k_fill_ll(long long* __restrict__ a, long long lo, long long hi) {
+    if (threadIdx.x < 3) a[threadIdx.x] = lo;
+    else if (threadIdx.x < 6) a[threadIdx.x] = hi;
+}
+
+// exclusive prefix sum of n ints by one block (serial over tiles of 1024)
+__global__ void __launch_bounds__(1024) k_scan_excl(const int* __restrict__ in, int* __restrict__ out, int64_t n) {
+    __shared__ int buf[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const int v = i < n ? in[i] : 0;
+        buf[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            int t = threadIdx.x >= off ? buf[threadIdx.x - off] : 0;
+            __syncthreads();
+            buf[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < n) out[i] = carry + buf[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += buf[1023];
+        __syncthreads();
+    }
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace mfd
+
+extern "C" mfd_status mfd_knn_static(int dim, int64_t nc, const double* centres, int64_t ns, const double* sources,
+                                     const double* period, int n, int32_t* idx, void* stream) {
+    using namespace mfd;
+    if (dim != 2 && dim != 3) return fail(MFD_ERR_ARG, "dim must be 2 or 3");
+    if (nc < 0 || ns < 1 || ns > INT32_MAX) return fail(MFD_ERR_ARG, "node counts out of range");
+    if (n < 1 || n > KNN_MAX || n > ns) return fail(MFD_ERR_ARG, "stencil size out of range (1..min(128, ns))");
+    if (!sources || (nc > 0 && (!centres || !idx))) return fail(MFD_ERR_ARG, "NULL device array");
+    double per[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) {
+        per[a] = period ? period[a] : 0.0;
+        if (per[a] < 0) return fail(MFD_ERR_ARG, "negative period");
+    }
+    if (nc == 0) return MFD_OK;
+    int device = 0;
+    MFD_CUDA(cudaGetDevice(&device));
+    unsigned char* base = nullptr;
+    MFD_TRY(knn_scratch_address(device, &base));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // bounding box of the sources (first 256 bytes of the scratch)
+    long long* lohi = reinterpret_cast<long long*>(base);
+    k_fill_ll<<<1, 32, 0, s>>>(lohi, LLONG_MAX, LLONG_MIN);
+    int bblocks = (int)std::min<int64_t>(1024, (ns + 255) / 256);
+    k_bbox<<<std::max(bblocks, 1), 256, 0, s>>>(sources, ns, dim, lohi);
+    MFD_CUDA(cudaGetLastError());
+    long long hb[6];
+    MFD_CUDA(cudaMemcpyAsync(hb, lohi, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    MFD_CUDA(cudaStreamSynchronize(s));
+    double lo[3], hi[3];
+    for (int a = 0; a < dim; ++a) {
+        lo[a] = key_dbl(hb[a]);
+        hi[a] = key_dbl(hb[3 + a]);
+    }
+    // the same cell grid as mfd_stencils_build: about one source per cell
+    Grid g;
+    double vol = 1.0;
+    for (int a = 0; a < dim; ++a) {
+        if (per[a] > 0) {
+            lo[a] = 0;
+            hi[a] = per[a];
+        }
+        vol *= std::max(hi[a] - lo[a], 1e-300);
+    }
+    const double cs = std::pow(vol / (double)ns, 1.0 / dim);
+    int64_t ncell = 1;
+    g.rmin = 1e300;
+    for (int a = 0; a < 3; ++a) {
+        g.lo[a] = 0;
+        g.side[a] = 1;
+        g.nb[a] = 1;
+        g.period[a] = 0;
+    }
+    for (int a = 0; a < dim; ++a) {
+        double ext = hi[a] - lo[a];
+        int64_t nb = (int64_t)std::floor(ext / cs);
+        if (nb < 1) nb = 1;
+        if (nb > (1 << 20)) nb = 1 << 20;
+        g.lo[a] = lo[a];
+        g.nb[a] = nb;
+        g.side[a] = ext > 0 ? ext / (double)nb : 1.0;
+        g.period[a] = per[a];
+        g.rmin = std::min(g.rmin, g.side[a]);
+        ncell *= nb;
+    }
+    // scratch layout: [bbox 256 B][ids 8 ns][cell_of 8 ns][list 4 ns][count, start, cursor: 4 (ncell + 1) each]
+    const size_t o_ids = 256;
+    const size_t o_cell = o_ids + align256(8 * (size_t)ns);
+    const size_t o_list = o_cell + align256(8 * (size_t)ns);
+    const size_t o_count = o_list + align256(4 * (size_t)ns);
+    const size_t o_start = o_count + align256(4 * (size_t)(ncell + 1));
+    const size_t o_cursor = o_start + align256(4 * (size_t)(ncell + 1));
+    const size_t need = o_cursor + align256(4 * (size_t)(ncell + 1));
+    if (need > KNN_STATIC_BYTES)
+        return fail(MFD_ERR_ARG, "mfd_knn_static: " + std::to_string(ns) + " sources need " + std::to_string(need) +
+                                     " bytes of scratch; the static scratch holds " +
+                                     std::to_string(KNN_STATIC_BYTES) + " (about 1M sources)");
+    int64_t* ids = reinterpret_cast<int64_t*>(base + o_ids);
+    int64_t* cell_of = reinterpret_cast<int64_t*>(base + o_cell);
+    int* list = reinterpret_cast<int*>(base + o_list);
+    int* count = reinterpret_cast<int*>(base + o_count);
+    int* start = reinterpret_cast<int*>(base + o_start);
+    int* cursor = reinterpret_cast<int*>(base + o_cursor);
+    // counts and cursors must start at zero (the array keeps the previous call's contents)
+    MFD_CUDA(cudaMemsetAsync(count, 0, 4 * (size_t)(ncell + 1), s));
+    MFD_CUDA(cudaMemsetAsync(cursor, 0, 4 * (size_t)(ncell + 1), s));
+    const unsigned sb = (unsigned)((ns + 255) / 256);
+    k_iota64<<<sb, 256, 0, s>>>(ids, ns);
+    k_cell_count<<<sb, 256, 0, s>>>(sources, ns, dim, g, cell_of, count);
+    k_scan_excl<<<1, 1024, 0, s>>>(count, start, ncell + 1);
+    k_cell_fill<<<sb, 256, 0, s>>>(cell_of, ns, start, cursor, list);
+    KnnArgs a;
+    a.xc = centres;
+    a.xs = sources;
+    a.perm_s = ids;
+    a.start = start;
+    a.list = list;
+    a.nc = nc;
+    a.ns = ns;
+    a.dim = dim;
+    a.n = n;
+    a.g = g;
+    a.out = idx;
+    k_knn<<<(unsigned)((nc + 127) / 128), 128, 0, s>>>(a);
+    MFD_CUDA(cudaGetLastError());
+    return MFD_OK;
+}
