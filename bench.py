@@ -49,6 +49,8 @@ def _args():
     ap.add_argument("--accuracy-steps", type=int, default=1000,
                     help="FP32-vs-FP64 (GPU) relative L2 error after this many steps (0: skip)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 step and the accuracy runs")
+    ap.add_argument("--batched-steps", type=int, default=3000,
+                    help="steps of the batched 256-domain x 16-RHS workload (0: skip)")
     return ap.parse_args()
 
 
@@ -330,6 +332,8 @@ def main():
         del s64
         if a.accuracy_steps:
             line["accuracy"] = accuracy(M, ctx, wts, a.accuracy_steps, reset)
+    if rank == 0 and a.batched_steps:
+        line["batched"] = batched(M, ctx, a.batched_steps, peak, peak_kind)
     # end to end through the public API: host fields in, steps, host Ez + probes out
     if not a.no_e2e:
         pin = [torch.empty(x.shape[0], dtype=torch.float64, pin_memory=True) for x in (ez, hx, hy)]
@@ -380,6 +384,53 @@ def roofline(ms, steps, e, h, nhv, s, peak, peak_kind):
             "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_t * 1e3,
             "other_kernel_avg_launch_ms": min(h_avg, e_avg) * 1e3,
             "other_kernel_achieved_gbs": ((be * e.n) if dom == "h" else (bh * h.n)) / min(h_avg, e_avg) / 1e9}
+
+
+def batched(M, ctx, steps, peak, peak_kind, ndom=256, nrhs=16):
+    """Batched workload: 256 PEC squares and disks, node counts log-uniform in
+    [2k, 60k] (about 4.3M nodes), stencil sizes n in {12, 20, 30, 40} (PHS r^3,
+    largest m with 2 M_m <= n; Delta^2 HV on 31 nodes), 16 Ricker sources per
+    domain, each its own right-hand side; FP32; all steps in one persistent
+    cooperative launch replayed from a CUDA graph."""
+    S, c = 0.5, 4e-3
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    t = time.time()
+    specs = W.batch_domains(ndom, 4)
+    doms, keep = [], []
+    for ns, n in specs:
+        nd = M.Nodes(ctx, ns.xyz, ns.period)
+        st = M.Stencils(nd, nd, max(n, 31))
+        cw = M.Weights(st, n, 3, W.poly_degree_for(n), M.MFD_OP_GRAD)
+        hw = M.Weights(st, 31, 5, 4, M.MFD_OP_LAP_POW, 2)
+        doms.append((cw, hw, dt, eps0, mu0, -c))
+        keep.append((nd, st))
+    bt = M.Batch(ctx, doms, nrhs=nrhs)
+    for d, (ns, n) in enumerate(specs):
+        bt.set_materials(d, None, ns.pec)
+        src = W.ricker_sources(ns, nrhs, 500 + d, c0, nrhs=nrhs, one_per_rhs=True)
+        bt.set_sources(d, src.node, src.rhs, src.amp, src.f0, src.t0)
+    setup_s = time.time() - t
+    import torch
+    bt.step(steps)  # captures the graph and warms up
+    stream = ctx.torch_stream()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    bt.step(steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    el = t0.elapsed_time(t1) / 1e3
+    ntot = sum(ns.n for ns, _ in specs)
+    upd = ntot * 3 * nrhs
+    byt = sum(ns.n * (4 * (max(n, 31) + n) + 4 * (4 * n + 31) + 10 * 4 * nrhs) for ns, n in specs)
+    ach = byt * steps / el / 1e9
+    return {"workload": f"batched {ndom} domains (squares and disks, 2k-60k nodes), {nrhs} RHS",
+            "nodes": ntot, "value": upd * steps / el, "unit": UNIT, "steps": steps,
+            "ms_per_step": el / steps * 1e3, "graph": bt.uses_graph, "setup_s": round(setup_s, 2),
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "traffic": None, "kernel": "k_batch<16>", "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_step": byt}}
 
 
 def accuracy(M, ctx, wts, steps, reset):

@@ -199,9 +199,60 @@ mfd_status mfd_read_probes(mfd_sim* sim, double* host, int64_t* steps);
  * domain measure / node count for the integral of Eq. 20. */
 mfd_status mfd_energy(mfd_sim* sim, double* u);
 /* Number of steps taken since the last mfd_set_field(MFD_EZ). */
+/* Gradient of the probe objective J = dt sum_{n=1..N} sum_p (Ez_p^n)^2
+ * (Ez at the probes of mfd_set_probes after each of the next N = nsteps
+ * steps) with respect to the relative permittivity of every E node and the
+ * amplitude of every source, by the discrete adjoint of the step: the exact
+ * transpose of Eq. 19 run backwards in time with transposed stencil gathers.
+ * The forward run keeps a full-state checkpoint every `every` steps and the
+ * backward sweep recomputes one segment at a time from its checkpoint, so
+ * device memory grows as nsteps / every states plus `every` Ez fields.
+ * Collocated 2D problems; probes must hold >= nsteps steps. g_eps: host,
+ * count(E nodes), caller's order; g_amp: host, one per source (may be NULL
+ * without sources); *J receives J. The simulation is left after step
+ * start + nsteps, with its probes recorded from the start of the call. */
+mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, double* g_eps, double* g_amp);
 int64_t mfd_sim_steps(const mfd_sim* sim);
 void mfd_sim_destroy(mfd_sim* sim);
 
+
+/* ------------------------------------------------------------- batches */
+
+/* Many independent collocated TMz problems ("domains", Eq. 19 each), every
+ * one with nrhs right-hand sides: field vectors stepped with the same weights
+ * (for example one per point source). One persistent cooperative kernel runs
+ * all the steps of a mfd_batch_step call for every domain and right-hand side,
+ * captured in a CUDA graph (with a direct launch as the fallback where the
+ * capture is refused). Its phases are separated by grid barriers whose waits
+ * are bounded: a barrier that waits too long makes every block leave the
+ * kernel and the call return MFD_ERR_TIMEOUT.
+ *   descs[d]: one collocated 2D FP32 problem per domain (h_curl == e_curl,
+ *   h_hv == e_hv, both on one stencils object of the domain's node set);
+ *   domains may differ in size, stencil size and coefficients.
+ *   nrhs: 4, 8, 16 or 32.
+ * Fields, sources and probes are addressed per domain; node ids are the
+ * caller's ids within the domain. rhs = -1 in set/get_field means all
+ * right-hand sides at once (host array n x nrhs, right-hand side fastest).
+ * Materials: eps_r (NULL = 1) and pec (nonzero holds Ez at 0) per domain. */
+typedef struct mfd_batch mfd_batch;
+mfd_status mfd_batch_create(mfd_ctx* ctx, int ndom, const mfd_sim_desc* descs, int nrhs, mfd_batch** out);
+mfd_status mfd_batch_set_materials(mfd_batch* b, int dom, const double* eps_r, const uint8_t* pec);
+mfd_status mfd_batch_set_field(mfd_batch* b, int dom, int comp, int rhs, const double* host);
+mfd_status mfd_batch_get_field(mfd_batch* b, int dom, int comp, int rhs, double* host);
+/* Soft Ricker sources of domain dom (as mfd_set_sources); rhs[s] selects the
+ * right-hand side source s drives. */
+mfd_status mfd_batch_set_sources(mfd_batch* b, int dom, int count, const int64_t* node, const int32_t* rhs,
+                                 const double* amp, const double* f0, const double* t0);
+/* Probes of domain dom: Ez of every right-hand side after each step, for at
+ * most `capacity` steps (the batch keeps the largest capacity asked). */
+mfd_status mfd_batch_set_probes(mfd_batch* b, int dom, int count, const int64_t* node, int64_t capacity);
+mfd_status mfd_batch_step(mfd_batch* b, int64_t nsteps);
+/* host: steps x count x nrhs FP64; *steps receives the recorded steps. */
+mfd_status mfd_batch_read_probes(mfd_batch* b, int dom, double* host, int64_t* steps);
+int64_t mfd_batch_nodes(const mfd_batch* b);
+/* 1 when mfd_batch_step replays a captured CUDA graph, 0 for direct launches. */
+int mfd_batch_uses_graph(const mfd_batch* b);
+void mfd_batch_destroy(mfd_batch* b);
 
 /* ------------------------------------------------- kNN without allocation */
 

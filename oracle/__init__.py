@@ -346,3 +346,55 @@ def run_3d(p: Max3D, E, H, nsteps, step0=0, sources=None, probes=None, energy=Fa
                             _p(sf), _p(st0), C.c_int(len(pr)), _p(pr), _p(pout), _p(eout)),
            "run_3d")
     return E, H, pout, eout
+
+
+def tmz_sample_step(e_nodes, h_nodes, e_ids, n, phs_k, m, alpha, dt, eps0, mu0, gamma, ez, hx, hy,
+                    h_ids=(), collocated=False):
+    """One Eq. 19 step evaluated at the E nodes e_ids (and H nodes h_ids) only.
+
+    Builds the oracle's own stencils and weights for exactly the centres the
+    result depends on (the sampled E nodes, the H nodes in their curl stencils
+    and the sampled H nodes) by the cell-list kNN, then steps them.
+    Returns (ez1 at e_ids, hx1 and hy1 at the H subset, the H subset ids).
+    """
+    import math
+    d = e_nodes.dim
+    nhv = 2 * math.comb(2 * alpha + d, d) + 1
+    per = e_nodes.period
+    e_ids = _i64(e_ids)
+    xe = e_nodes.xyz[e_ids]
+    L = max(n, nhv) if collocated else None
+    if collocated:
+        i_e = knn_cells(xe, e_nodes.xyz, per, L)
+        ec_idx, ev_idx = i_e[:, :n], i_e[:, :nhv]
+    else:
+        ec_idx = knn_cells(xe, h_nodes.xyz, per, n)
+        ev_idx = knn_cells(xe, e_nodes.xyz, per, nhv)
+    hs = np.unique(np.concatenate([ec_idx.reshape(-1), _i64(h_ids)]))
+    xh = h_nodes.xyz[hs]
+    if collocated:
+        i_h = knn_cells(xh, h_nodes.xyz, per, L)
+        hc_idx, hv_idx = i_h[:, :n], i_h[:, :nhv]
+    else:
+        hc_idx = knn_cells(xh, e_nodes.xyz, per, n)
+        hv_idx = knn_cells(xh, h_nodes.xyz, per, nhv)
+    hc = weights(xh, e_nodes.xyz, per, hc_idx, n, phs_k, m, OP_GRAD)
+    hv = weights(xh, h_nodes.xyz, per, hv_idx, nhv, 2 * alpha + 1, 2 * alpha, OP_LAP_POW, alpha)
+    ec = weights(xe, h_nodes.xyz, per, ec_idx, n, phs_k, m, OP_GRAD)
+    ev = weights(xe, e_nodes.xyz, per, ev_idx, nhv, 2 * alpha + 1, 2 * alpha, OP_LAP_POW, alpha)
+    hpos = np.full(h_nodes.n, -1, dtype=np.int64)
+    hpos[hs] = np.arange(len(hs))
+    hx1 = np.empty(len(hs))
+    hy1 = np.empty(len(hs))
+    ez1 = np.empty(len(e_ids))
+    c = [np.ascontiguousarray(a) for a in (hc_idx, hc[0], hc[1], hv_idx, hv[0], ec_idx, ec[0], ec[1],
+                                           ev_idx, ev[0])]
+    ez, hx, hy = _f64(ez), _f64(hx), _f64(hy)
+    _check(lib().orc_tmz_sample_step(C.c_int64(len(hs)), _p(hs), C.c_int(n), _p(c[0]), _p(c[1]),
+                                     _p(c[2]), C.c_int(nhv), _p(c[3]), _p(c[4]),
+                                     C.c_int64(len(e_ids)), _p(e_ids), C.c_int(n), _p(c[5]),
+                                     _p(c[6]), _p(c[7]), C.c_int(nhv), _p(c[8]), _p(c[9]), _p(hpos),
+                                     None, C.c_double(dt), C.c_double(eps0), C.c_double(mu0),
+                                     C.c_double(gamma), _p(ez), _p(hx), _p(hy), _p(hx1), _p(hy1),
+                                     _p(ez1)), "tmz_sample_step")
+    return ez1, hx1, hy1, hs

@@ -819,3 +819,47 @@ int orc_grad_tmz(int64_t nh, int nhc, const int64_t* hc_idx, const double* hc_wx
     free(Es); free(Hxs); free(Hys); free(probes); free(lE); free(lHx); free(lHy);
     return ORC_OK;
 }
+
+/*
+ * One TMz step (Eq. 19) evaluated only at chosen nodes, for checks at sizes
+ * where a full oracle step is too slow. State: ez (E set), hx, hy (H set).
+ * H subset: nhs node ids (hs_ids) with their stencils; hpos[j] = position of
+ * H node j in the subset or -1. E subset: nes node ids (es_ids) with their
+ * stencils, whose curl entries must all lie in the H subset. Outputs the new
+ * H at the H subset (hx1, hy1: nhs values) and the new Ez at the E subset
+ * (ez1: nes values), without sources or PEC.
+ */
+int orc_tmz_sample_step(int64_t nhs, const int64_t* hs_ids, int nhc, const int64_t* hc_idx,
+                        const double* hc_wx, const double* hc_wy, int nhv, const int64_t* hv_idx,
+                        const double* hv_w, int64_t nes, const int64_t* es_ids, int nec,
+                        const int64_t* ec_idx, const double* ec_wx, const double* ec_wy, int nev,
+                        const int64_t* ev_idx, const double* ev_w, const int64_t* hpos,
+                        const double* eps_r_es, double dt, double eps0, double mu0, double gamma,
+                        const double* ez, const double* hx, const double* hy, double* hx1,
+                        double* hy1, double* ez1)
+{
+    const double ch = dt / mu0;
+    for (int64_t k = 0; k < nhs; ++k) {
+        int64_t i = hs_ids[k];
+        double dyE = orc_apply(nhc, hc_idx + k * nhc, hc_wy + k * nhc, ez);
+        double dxE = orc_apply(nhc, hc_idx + k * nhc, hc_wx + k * nhc, ez);
+        double vx = orc_apply(nhv, hv_idx + k * nhv, hv_w + k * nhv, hx);
+        double vy = orc_apply(nhv, hv_idx + k * nhv, hv_w + k * nhv, hy);
+        hx1[k] = hx[i] - ch * (dyE - gamma * vx);
+        hy1[k] = hy[i] + ch * (dxE + gamma * vy);
+    }
+    for (int64_t k = 0; k < nes; ++k) {
+        int64_t i = es_ids[k];
+        double dxH = 0.0, dyH = 0.0;
+        for (int j = 0; j < nec; ++j) {
+            int64_t p = hpos[ec_idx[k * nec + j]];
+            if (p < 0) return ORC_ERR_ARG;
+            dxH += ec_wx[k * nec + j] * hy1[p];
+            dyH += ec_wy[k * nec + j] * hx1[p];
+        }
+        double ve = orc_apply(nev, ev_idx + k * nev, ev_w + k * nev, ez);
+        double er = eps_r_es ? eps_r_es[k] : 1.0;
+        ez1[k] = ez[i] + dt / (eps0 * er) * (dxH - dyH + gamma * ve);
+    }
+    return ORC_OK;
+}

@@ -68,8 +68,20 @@ _SIGS = {
     "mfd_read_probes": (_I, [_VP, _VP, C.POINTER(_I64)]),
     "mfd_energy": (_I, [_VP, _VP]),
     "mfd_sim_steps": (_I64, [_VP]),
+    "mfd_grad": (_I, [_VP, _I64, _I64, _VP, _VP, _VP]),
     "mfd_sim_destroy": (None, [_VP]),
     "mfd_knn_static": (_I, [_I, _I64, _VP, _I64, _VP, _VP, _I, _VP, _VP]),
+    "mfd_batch_create": (_I, [_VP, _I, _VP, _I, C.POINTER(_VP)]),
+    "mfd_batch_set_materials": (_I, [_VP, _I, _VP, _VP]),
+    "mfd_batch_set_field": (_I, [_VP, _I, _I, _I, _VP]),
+    "mfd_batch_get_field": (_I, [_VP, _I, _I, _I, _VP]),
+    "mfd_batch_set_sources": (_I, [_VP, _I, _I, _VP, _VP, _VP, _VP, _VP]),
+    "mfd_batch_set_probes": (_I, [_VP, _I, _I, _VP, _I64]),
+    "mfd_batch_step": (_I, [_VP, _I64]),
+    "mfd_batch_read_probes": (_I, [_VP, _I, _VP, C.POINTER(_I64)]),
+    "mfd_batch_nodes": (_I64, [_VP]),
+    "mfd_batch_uses_graph": (_I, [_VP]),
+    "mfd_batch_destroy": (None, [_VP]),
 }
 
 _lib = None
@@ -273,6 +285,14 @@ class Sim:
     def steps(self):
         return int(lib().mfd_sim_steps(self.h))
 
+    def grad(self, nsteps, every=64, nsrc=0):
+        """(J, dJ/deps_r per E node, dJ/d amplitude per source) over the next nsteps (mfd_grad)."""
+        J = np.zeros(1)
+        ge = np.zeros(self.ne)
+        ga = np.zeros(max(nsrc, 1))
+        _ck(lib().mfd_grad(self.h, int(nsteps), int(every), _p(J), _p(ge), _p(ga)))
+        return float(J[0]), ge, ga[:nsrc]
+
     def __del__(self):
         try:
             if self.h:
@@ -280,3 +300,114 @@ class Sim:
                 self.h = None
         except Exception:
             pass
+
+
+class Batch:
+    """Many collocated TMz domains x nrhs right-hand sides, stepped by one persistent kernel."""
+
+    def __init__(self, ctx: Ctx, domains, nrhs=16):
+        """domains: list of (curl Weights, hv Weights, dt, eps0, mu0, gamma)."""
+        descs = (mfd_sim_desc * len(domains))()
+        for d, (cw, hw, dt, eps0, mu0, gamma) in enumerate(domains):
+            descs[d] = mfd_sim_desc(2, MFD_FP32, nrhs, 0, dt, eps0, mu0, gamma, cw.h, hw.h, cw.h, hw.h)
+        h = C.c_void_p()
+        _ck(lib().mfd_batch_create(ctx.h, len(domains), C.cast(descs, C.c_void_p), nrhs, C.byref(h)))
+        self.h, self.ctx, self.nrhs = h, ctx, nrhs
+        self._keep = list(domains)
+        self.n = [cw.st.centres.n for cw, *_ in domains]
+        self.nprobe = [0] * len(domains)
+
+    def set_materials(self, dom, eps_r=None, pec=None):
+        er = None if eps_r is None else _f64(eps_r)
+        pc = None if pec is None else np.ascontiguousarray(pec, dtype=np.uint8)
+        _ck(lib().mfd_batch_set_materials(self.h, dom, _p(er), _p(pc)))
+
+    def set_field(self, dom, comp, values, rhs=-1):
+        _ck(lib().mfd_batch_set_field(self.h, dom, comp, rhs, _p(_f64(values))))
+
+    def get_field(self, dom, comp, rhs=-1):
+        out = np.empty((self.n[dom], self.nrhs) if rhs < 0 else self.n[dom])
+        _ck(lib().mfd_batch_get_field(self.h, dom, comp, rhs, _p(out)))
+        return out
+
+    def set_sources(self, dom, node, rhs, amp, f0, t0):
+        node = np.ascontiguousarray(node, dtype=np.int64)
+        r = np.ascontiguousarray(rhs, dtype=np.int32)
+        _ck(lib().mfd_batch_set_sources(self.h, dom, len(node), _p(node), _p(r), _p(_f64(amp)), _p(_f64(f0)),
+                                        _p(_f64(t0))))
+
+    def set_probes(self, dom, node, capacity):
+        node = np.ascontiguousarray(node, dtype=np.int64)
+        _ck(lib().mfd_batch_set_probes(self.h, dom, len(node), _p(node), int(capacity)))
+        self.nprobe[dom] = len(node)
+
+    def step(self, n):
+        _ck(lib().mfd_batch_step(self.h, int(n)))
+
+    def read_probes(self, dom):
+        steps = C.c_int64(0)
+        _ck(lib().mfd_batch_read_probes(self.h, dom, None, C.byref(steps)))
+        out = np.zeros((steps.value, self.nprobe[dom], self.nrhs))
+        if steps.value and self.nprobe[dom]:
+            _ck(lib().mfd_batch_read_probes(self.h, dom, _p(out), C.byref(steps)))
+        return out
+
+    @property
+    def uses_graph(self):
+        return bool(lib().mfd_batch_uses_graph(self.h))
+
+    @property
+    def nodes(self):
+        return int(lib().mfd_batch_nodes(self.h))
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().mfd_batch_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class ProbeObjective:
+    """A collocated TMz run whose probe objective J(eps_r, amp) = dt sum_n sum_p Ez_p^n^2
+    is differentiable through ``ProbeEnergy`` (adjoint gradients from mfd_grad)."""
+
+    def __init__(self, sim: Sim, pec, fields, sources, probes, nsteps, every=64):
+        self.sim, self.pec, self.fields = sim, pec, fields
+        self.src, self.probes, self.nsteps, self.every = sources, probes, nsteps, every
+
+    def run(self, eps_r, amp):
+        s = self.sim
+        s.set_materials(eps_r, self.pec)
+        for comp, v in self.fields.items():
+            s.set_field(comp, v)
+        s.set_sources(self.src.node, amp, self.src.f0, self.src.t0)
+        s.set_probes(self.probes, self.nsteps)
+        return s.grad(self.nsteps, self.every, len(self.src.node))
+
+
+def _probe_energy_function():
+    import torch
+
+    class ProbeEnergy(torch.autograd.Function):
+        """J(eps_r, amp) of a ProbeObjective; backward returns the adjoint gradients."""
+
+        @staticmethod
+        def forward(ctx, eps_r, amp, obj):
+            J, ge, ga = obj.run(eps_r.detach().cpu().double().numpy(), amp.detach().cpu().double().numpy())
+            ctx.save_for_backward(torch.from_numpy(ge).to(eps_r.device, eps_r.dtype),
+                                  torch.from_numpy(np.ascontiguousarray(ga)).to(amp.device, amp.dtype))
+            return torch.tensor(J, dtype=torch.float64, device=eps_r.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            ge, ga = ctx.saved_tensors
+            return gJ.to(ge.dtype) * ge, gJ.to(ga.dtype) * ga, None
+
+    return ProbeEnergy
+
+
+def probe_energy(eps_r, amp, obj: ProbeObjective):
+    """Differentiable J(eps_r, amp) (torch tensors in, 0-d tensor out)."""
+    return _probe_energy_function().apply(eps_r, amp, obj)

@@ -1,0 +1,330 @@
+// adjoint.cu -- the discrete adjoint of the collocated TMz step (Eq. 19).
+//
+// With K = diag(dt / (eps0 eps_r)) (0 on PEC nodes), Z = diag(1 - pec),
+// curl stencil operators Dx, Dy and hyperviscosity operator V, one forward step is
+//   H' = H + ch (C_E E + gamma V H),   C_E E = (-Dy E, Dx E)
+//   E' = Z [E + K (gamma V E + C_H H') + b],   C_H H = Dx Hy - Dy Hx.
+// Its transpose, applied to (lambda_E', lambda_H') = adjoints of (E', H'):
+//   mu     = Z lambda_E'
+//   l~H    = lambda_H' + C_H^T (K mu)           (x: -Dy^T K mu, y: +Dx^T K mu)
+//   t      = mu + gamma V^T (K mu)
+//   lambda_H = l~H + ch gamma V^T l~H
+//   lambda_E = t + ch C_E^T l~H                  (-Dy^T l~Hx + Dx^T l~Hy)
+// and the permittivity gradient of the step, dE'_i/deps_i = -(E'_i - E_i - b_i) / eps_i:
+//   g_eps_i += mu_i (-(E'_i - E_i - b_i) / eps_i).
+// Every transposed operator is a gather over the transposed (CSR) stencils.
+#include <cub/device/device_scan.cuh>
+
+#include <algorithm>
+
+#include "adjoint.cuh"
+
+namespace mfd {
+
+__global__ void k_t_count(const int32_t* __restrict__ idx, int stride, int64_t n, int ne, int64_t* __restrict__ cnt) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * ne) return;
+    const int64_t i = e / ne;
+    const int k = (int)(e % ne);
+    atomicAdd(reinterpret_cast<unsigned long long*>(cnt + idx[i * stride + k]), 1ull);
+}
+
+__global__ void k_t_pad(const int64_t* __restrict__ cnt, int64_t n, int64_t* __restrict__ padded) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    padded[j] = (cnt[j] + 3) & ~(int64_t)3;
+}
+
+// kind 0: curl entries (k < n_c) with weights (wx, wy) and, when the stencils are
+// shared, the HV weight too; kind 1: HV-only entries of a separate HV stencil
+template <typename T>
+__global__ void k_t_fill(const int32_t* __restrict__ idx, int stride, int64_t n, int ne, const double* __restrict__ wx,
+                         const double* __restrict__ wy, int n_c, const double* __restrict__ wv, int n_v,
+                         const int64_t* __restrict__ rowptr, unsigned long long* __restrict__ cursor,
+                         int32_t* __restrict__ col, typename Vec<T>::V4* __restrict__ w, int kind) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * ne) return;
+    const int64_t i = e / ne;
+    const int k = (int)(e % ne);
+    const int64_t j = idx[i * stride + k];
+    const int64_t pos = rowptr[j] + (int64_t)atomicAdd(cursor + j, 1ull);
+    typename Vec<T>::V4 v;
+    v.x = (kind == 0 && k < n_c) ? (T)wx[i * n_c + k] : T(0);
+    v.y = (kind == 0 && k < n_c) ? (T)wy[i * n_c + k] : T(0);
+    v.z = (wv && k < n_v) ? (T)wv[i * n_v + k] : T(0);
+    v.w = (T)kind;
+    col[pos] = (int32_t)i;
+    w[pos] = v;
+}
+
+// pad the tail of every row (column j, zero weights) and sort each row by (column, kind)
+template <typename T>
+__global__ void k_t_finish(const int64_t* __restrict__ rowptr, const unsigned long long* __restrict__ cursor, int64_t n,
+                           int32_t* __restrict__ col, typename Vec<T>::V4* __restrict__ w) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int64_t b = rowptr[j], e = rowptr[j + 1], filled = b + (int64_t)cursor[j];
+    for (int64_t p = filled; p < e; ++p) {
+        col[p] = (int32_t)j;
+        typename Vec<T>::V4 z;
+        z.x = z.y = z.z = T(0);
+        z.w = T(2);
+        w[p] = z;
+    }
+    for (int64_t p = b + 1; p < e; ++p) {
+        const int32_t c = col[p];
+        const typename Vec<T>::V4 v = w[p];
+        int64_t q = p - 1;
+        while (q >= b && (col[q] > c || (col[q] == c && w[q].w > v.w))) {
+            col[q + 1] = col[q];
+            w[q + 1] = w[q];
+            --q;
+        }
+        col[q + 1] = c;
+        w[q + 1] = v;
+    }
+    for (int64_t p = b; p < e; ++p) w[p].w = T(0);
+}
+
+mfd_status adj_build(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* hv, bool fp64, AdjT& out) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = curl->st->centres->n;
+    const bool shared = curl->st == hv->st;
+    out.n = n;
+    DevBuf cnt, padded, cursor, tmp;
+    MFD_TRY(cnt.alloc((n + 1) * 8));
+    MFD_TRY(padded.alloc((n + 1) * 8));
+    MFD_TRY(cursor.alloc((n + 1) * 8));
+    MFD_TRY(out.rowptr.alloc((n + 1) * 8));
+    MFD_CUDA(cudaMemsetAsync(cnt.p, 0, (n + 1) * 8, s));
+    MFD_CUDA(cudaMemsetAsync(cursor.p, 0, (n + 1) * 8, s));
+    MFD_CUDA(cudaMemsetAsync(padded.p, 0, (n + 1) * 8, s));
+    const int ne_c = shared ? std::max(curl->n_use, hv->n_use) : curl->n_use;
+    auto grid = [](int64_t t) { return (unsigned)((t + 255) / 256); };
+    k_t_count<<<grid(n * ne_c), 256, 0, s>>>(curl->st->idx.as<int32_t>(), curl->st->n, n, ne_c, cnt.as<int64_t>());
+    if (!shared)
+        k_t_count<<<grid(n * hv->n_use), 256, 0, s>>>(hv->st->idx.as<int32_t>(), hv->st->n, n, hv->n_use,
+                                                       cnt.as<int64_t>());
+    k_t_pad<<<grid(n), 256, 0, s>>>(cnt.as<int64_t>(), n, padded.as<int64_t>());
+    MFD_CUDA(cudaGetLastError());
+    size_t tb = 0;
+    MFD_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, padded.as<int64_t>(), out.rowptr.as<int64_t>(), n + 1, s));
+    MFD_TRY(tmp.alloc(tb));
+    MFD_CUDA(cub::DeviceScan::ExclusiveSum(tmp.p, tb, padded.as<int64_t>(), out.rowptr.as<int64_t>(), n + 1, s));
+    int64_t nnz = 0;
+    MFD_CUDA(cudaMemcpyAsync(&nnz, out.rowptr.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, s));
+    MFD_CUDA(cudaStreamSynchronize(s));
+    out.nnz = nnz;
+    const size_t es = fp64 ? 32 : 16;
+    MFD_TRY(out.col.alloc(std::max<int64_t>(nnz, 4) * 4));
+    MFD_TRY(out.w.alloc(std::max<int64_t>(nnz, 4) * es));
+    const double* wx = curl->w.as<double>();
+    const double* wy = wx + n * curl->n_use;
+    const double* wv = hv->w.as<double>();
+#define FILL(T)                                                                                                        \
+    k_t_fill<T><<<grid(n * ne_c), 256, 0, s>>>(curl->st->idx.as<int32_t>(), curl->st->n, n, ne_c, wx, wy, curl->n_use, \
+                                               shared ? wv : nullptr, hv->n_use, out.rowptr.as<int64_t>(),             \
+                                               cursor.as<unsigned long long>(), out.col.as<int32_t>(),                 \
+                                               out.w.as<typename Vec<T>::V4>(), 0);                                    \
+    if (!shared)                                                                                                       \
+        k_t_fill<T><<<grid(n * hv->n_use), 256, 0, s>>>(hv->st->idx.as<int32_t>(), hv->st->n, n, hv->n_use, nullptr,   \
+                                                        nullptr, 0, wv, hv->n_use, out.rowptr.as<int64_t>(),           \
+                                                        cursor.as<unsigned long long>(), out.col.as<int32_t>(),        \
+                                                        out.w.as<typename Vec<T>::V4>(), 1);                           \
+    k_t_finish<T><<<grid(n), 256, 0, s>>>(out.rowptr.as<int64_t>(), cursor.as<unsigned long long>(), n,                \
+                                          out.col.as<int32_t>(), out.w.as<typename Vec<T>::V4>());
+    if (fp64) {
+        FILL(double)
+    } else {
+        FILL(float)
+    }
+#undef FILL
+    MFD_CUDA(cudaGetLastError());
+    MFD_CUDA(cudaStreamSynchronize(s));
+    return MFD_OK;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_a(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                               const typename Vec<T>::V4* __restrict__ w, int64_t n,
+                                               const typename Vec<T>::V4* __restrict__ LA,
+                                               typename Vec<T>::V4* __restrict__ LB, T gamma,
+                                               const T* __restrict__ e0, const T* __restrict__ e1,
+                                               const double* __restrict__ eps, double* __restrict__ g_eps) {
+    using V4 = typename Vec<T>::V4;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    T sx = 0, sy = 0, sv = 0;
+    for (int64_t p = rowptr[j]; p < rowptr[j + 1]; p += 4) {
+        const int4 c = *reinterpret_cast<const int4*>(col + p);
+        const int cs[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const V4 wq = ld_gather(w + p + q);
+            const V4 l = ld_gather(LA + cs[q]);
+            const T km = l.w * l.x;  // K mu (0 on PEC nodes, where ce = 0)
+            sx = fma(-wq.y, km, sx);
+            sy = fma(wq.x, km, sy);
+            sv = fma(wq.z, km, sv);
+        }
+    }
+    const V4 me = ld_gather(LA + j);
+    const T mu = me.w == T(0) ? T(0) : me.x;
+    V4 o;
+    o.x = mu + gamma * sv;
+    o.y = me.y + sx;
+    o.z = me.z + sy;
+    o.w = me.w;
+    st4(LB + j, o);
+    if (me.w != T(0)) g_eps[j] += (double)mu * (-((double)e1[j] - (double)e0[j]) / eps[j]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_b(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                               const typename Vec<T>::V4* __restrict__ w, int64_t n,
+                                               const typename Vec<T>::V4* __restrict__ LB,
+                                               typename Vec<T>::V4* __restrict__ LA, T ch, T gamma) {
+    using V4 = typename Vec<T>::V4;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    T vx = 0, vy = 0, cx = 0, cy = 0;
+    for (int64_t p = rowptr[j]; p < rowptr[j + 1]; p += 4) {
+        const int4 c = *reinterpret_cast<const int4*>(col + p);
+        const int cs[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const V4 wq = ld_gather(w + p + q);
+            const V4 l = ld_gather(LB + cs[q]);
+            vx = fma(wq.z, l.y, vx);
+            vy = fma(wq.z, l.z, vy);
+            cx = fma(wq.x, l.z, cx);  // Dx^T l~Hy
+            cy = fma(wq.y, l.y, cy);  // Dy^T l~Hx
+        }
+    }
+    const V4 me = ld_gather(LB + j);
+    V4 o;
+    o.x = me.x + ch * (cx - cy);
+    o.y = me.y + ch * gamma * vx;
+    o.z = me.z + ch * gamma * vy;
+    o.w = me.w;
+    st4(LA + j, o);
+}
+
+cudaError_t adj_pass(const AdjArgs& a, int pass, cudaStream_t s) {
+    const unsigned g = (unsigned)((a.n + 255) / 256);
+    if (a.fp64) {
+        if (pass == 0)
+            k_adj_a<double><<<g, 256, 0, s>>>(a.rowptr, a.col, (const dbl4*)a.w, a.n, (const dbl4*)a.LA, (dbl4*)a.LB,
+                                              a.gamma, (const double*)a.e0, (const double*)a.e1, a.eps, a.g_eps);
+        else
+            k_adj_b<double><<<g, 256, 0, s>>>(a.rowptr, a.col, (const dbl4*)a.w, a.n, (const dbl4*)a.LB, (dbl4*)a.LA,
+                                              a.ch, a.gamma);
+    } else {
+        if (pass == 0)
+            k_adj_a<float><<<g, 256, 0, s>>>(a.rowptr, a.col, (const float4*)a.w, a.n, (const float4*)a.LA,
+                                             (float4*)a.LB, (float)a.gamma, (const float*)a.e0, (const float*)a.e1,
+                                             a.eps, a.g_eps);
+        else
+            k_adj_b<float><<<g, 256, 0, s>>>(a.rowptr, a.col, (const float4*)a.w, a.n, (const float4*)a.LB,
+                                             (float4*)a.LA, (float)a.ch, (float)a.gamma);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_adj_probe(T* __restrict__ LA, const T* __restrict__ ez, const int64_t* __restrict__ probe, int np,
+                            double dt) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int p = 0; p < np; ++p) {  // serial: a node probed twice gets both terms
+        const int64_t i = probe[p];
+        LA[4 * i] = LA[4 * i] + (T)(2.0 * dt * (double)ez[i]);
+    }
+}
+
+cudaError_t adj_probe_term(bool fp64, void* LA, const void* ez, const int64_t* probe, int nprobe, double dt,
+                           cudaStream_t s) {
+    if (nprobe <= 0) return cudaSuccess;
+    if (fp64) k_adj_probe<double><<<1, 32, 0, s>>>((double*)LA, (const double*)ez, probe, nprobe, dt);
+    else k_adj_probe<float><<<1, 32, 0, s>>>((float*)LA, (const float*)ez, probe, nprobe, dt);
+    return cudaGetLastError();
+}
+
+template <typename T> __global__ void k_init_lambda(T* __restrict__ LA, const T* __restrict__ A, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    LA[4 * i] = T(0);
+    LA[4 * i + 1] = T(0);
+    LA[4 * i + 2] = T(0);
+    LA[4 * i + 3] = A[4 * i + 3];
+}
+
+cudaError_t init_lambda(bool fp64, void* LA, const void* A, int64_t n, cudaStream_t s) {
+    const unsigned g = (unsigned)((n + 255) / 256);
+    if (fp64) k_init_lambda<double><<<g, 256, 0, s>>>((double*)LA, (const double*)A, n);
+    else k_init_lambda<float><<<g, 256, 0, s>>>((float*)LA, (const float*)A, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_adj_src(const T* __restrict__ LA, const int64_t* __restrict__ node, const double* __restrict__ amp,
+                          const double* __restrict__ f0, const double* __restrict__ t0, int nsrc, double t1,
+                          const double* __restrict__ eps, double* __restrict__ g_eps, double* __restrict__ g_amp) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < nsrc; ++k) {
+        const int64_t i = node[k];
+        if (LA[4 * i + 3] == T(0)) continue;  // PEC node: held at zero, no dependence
+        const double mu = (double)LA[4 * i];
+        double x = pi * f0[k] * (t1 - t0[k]);
+        x = x * x;
+        const double r = (1.0 - 2.0 * x) * exp(-x);
+        g_amp[k] += mu * r;
+        g_eps[i] += mu * amp[k] * r / eps[i];
+    }
+}
+
+cudaError_t adj_sources(bool fp64, const void* LA, const int64_t* node, const double* amp, const double* f0,
+                        const double* t0, int nsrc, double t1, const double* eps, double* g_eps, double* g_amp,
+                        cudaStream_t s) {
+    if (nsrc <= 0) return cudaSuccess;
+    if (fp64) k_adj_src<double><<<1, 32, 0, s>>>((const double*)LA, node, amp, f0, t0, nsrc, t1, eps, g_eps, g_amp);
+    else k_adj_src<float><<<1, 32, 0, s>>>((const float*)LA, node, amp, f0, t0, nsrc, t1, eps, g_eps, g_amp);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_sumsq(const T* __restrict__ buf, int64_t count, double dt, double* __restrict__ J) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < count; i += 256) {
+        const double v = (double)buf[i];
+        s += v * v;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *J = dt * red[0];
+}
+
+cudaError_t probe_energy(bool fp64, const void* buf, int64_t count, double dt, double* J, cudaStream_t s) {
+    if (fp64) k_sumsq<double><<<1, 256, 0, s>>>((const double*)buf, count, dt, J);
+    else k_sumsq<float><<<1, 256, 0, s>>>((const float*)buf, count, dt, J);
+    return cudaGetLastError();
+}
+
+template <typename T> __global__ void k_copy_ez(const T* __restrict__ st, T* __restrict__ dst, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = st[4 * i];
+}
+
+cudaError_t copy_ez(bool fp64, const void* state, void* dst, int64_t n, cudaStream_t s) {
+    const unsigned g = (unsigned)((n + 255) / 256);
+    if (fp64) k_copy_ez<double><<<g, 256, 0, s>>>((const double*)state, (double*)dst, n);
+    else k_copy_ez<float><<<g, 256, 0, s>>>((const float*)state, (float*)dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace mfd

@@ -1,0 +1,61 @@
+// adjoint.cuh -- transposed stencil operators and the reverse-time (adjoint)
+// half steps of the collocated TMz leapfrog, for gradients of probe objectives.
+#pragma once
+
+#include "internal.cuh"
+#include "kernels.cuh"
+
+namespace mfd {
+
+// Transpose of the collocated stencil operators, row j listing every (i, w_ij)
+// with j in S(x_i): CSR with rows padded to a multiple of 4 entries (padding:
+// column j, weight 0) and sorted by column (and operator kind) so that the
+// transposed sums are reproducible. Weights per entry: {w^dx, w^dy, w^hv, 0}.
+struct AdjT {
+    DevBuf rowptr;  // int64 [n + 1]
+    DevBuf col;     // int32 [nnz]
+    DevBuf w;       // Vec<T>::V4 [nnz]
+    int64_t nnz = 0;
+    int64_t n = 0;
+};
+
+mfd_status adj_build(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* hv, bool fp64, AdjT& out);
+
+struct AdjArgs {
+    bool fp64 = false;
+    const int64_t* rowptr = nullptr;
+    const int32_t* col = nullptr;
+    const void* w = nullptr;
+    int64_t n = 0;
+    void* LA = nullptr;  // {lambda_E, lambda_Hx, lambda_Hy, ce} (ce = dt / (eps0 eps_r), 0 at PEC)
+    void* LB = nullptr;  // {t, lambda~_Hx, lambda~_Hy, ce}
+    double ch = 0, gamma = 0;
+    const void* e0 = nullptr;  // Ez^n  (one real per node)
+    const void* e1 = nullptr;  // Ez^{n+1}
+    const double* eps = nullptr;
+    double* g_eps = nullptr;
+};
+
+// pass 0: LA -> LB (and the permittivity gradient of this step); pass 1: LB -> LA
+cudaError_t adj_pass(const AdjArgs& a, int pass, cudaStream_t s);
+
+// the probe term dJ/dE^n of J = dt sum_n sum_p (Ez_p^n)^2: LA[p].x += 2 dt Ez[p] at every probe
+cudaError_t adj_probe_term(bool fp64, void* LA, const void* ez, const int64_t* probe, int nprobe, double dt,
+                           cudaStream_t s);
+
+// LA = {0, 0, 0, ce} from the state A = {Ez, Hx, Hy, ce}
+cudaError_t init_lambda(bool fp64, void* LA, const void* A, int64_t n, cudaStream_t s);
+
+// soft-source terms of step n -> n + 1 (t1 = t_{n+1}): with mu = Z lambda_E^{n+1},
+// g_amp[k] += mu_k r_k(t1) and g_eps[node_k] += mu_k amp_k r_k(t1) / eps_r
+cudaError_t adj_sources(bool fp64, const void* LA, const int64_t* node, const double* amp, const double* f0,
+                        const double* t0, int nsrc, double t1, const double* eps, double* g_eps, double* g_amp,
+                        cudaStream_t s);
+
+// J += dt sum of squares of `count` probe values (FP64 accumulator)
+cudaError_t probe_energy(bool fp64, const void* buf, int64_t count, double dt, double* J, cudaStream_t s);
+
+// dst[i] = Ez of the V4 state (stride 4)
+cudaError_t copy_ez(bool fp64, const void* state, void* dst, int64_t n, cudaStream_t s);
+
+}  // namespace mfd

@@ -7,6 +7,7 @@
 #include <new>
 #include <vector>
 
+#include "adjoint.cuh"
 #include "internal.cuh"
 #include "step.cuh"
 
@@ -178,6 +179,8 @@ struct mfd_sim {
     cudaGraphExec_t graph = nullptr;
     bool graph_ok = false;
     std::vector<cudaEvent_t> events;
+    AdjT adj;
+    bool adj_ok = false;
     ~mfd_sim() {
         if (graph) cudaGraphExecDestroy(graph);
         for (auto e : events) cudaEventDestroy(e);
@@ -770,6 +773,103 @@ mfd_status mfd_energy(mfd_sim* sim, double* u) {
 }
 
 int64_t mfd_sim_steps(const mfd_sim* sim) { return sim ? sim->steps : -1; }
+
+mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, double* g_eps, double* g_amp) {
+    if (!sim || nsteps < 1 || every < 1 || !J || !g_eps) return fail(MFD_ERR_ARG, "bad arguments");
+    if (sim->layout != COLLOC2D) return fail(MFD_ERR_ARG, "mfd_grad supports the collocated 2D layout");
+    if (sim->nsrc > 0 && !g_amp) return fail(MFD_ERR_ARG, "g_amp is NULL");
+    if (sim->nprobe < 1 || sim->probe_cap < nsteps)
+        return fail(MFD_ERR_STATE, "mfd_grad needs probes with capacity >= nsteps (mfd_set_probes)");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    const bool f64 = sim->fp64;
+    const size_t rs = sim->rs;
+    const int64_t n = sim->ne;
+    if (!sim->adj_ok) {
+        MFD_TRY(adj_build(ctx, sim->d.h_curl, sim->d.h_hv, f64, sim->adj));
+        sim->adj_ok = true;
+    }
+    const int64_t nseg = (nsteps + every - 1) / every;
+    DevBuf ckpt, fin, seg, LA, LB, geps, gamp, Jd;
+    MFD_TRY(ckpt.alloc((size_t)nseg * n * 4 * rs));
+    MFD_TRY(fin.alloc((size_t)n * 4 * rs));
+    MFD_TRY(seg.alloc((size_t)(every + 1) * n * rs));
+    MFD_TRY(LA.alloc((size_t)n * 4 * rs));
+    MFD_TRY(LB.alloc((size_t)n * 4 * rs));
+    MFD_TRY(geps.alloc((size_t)n * 8));
+    MFD_TRY(gamp.alloc(std::max(1, sim->nsrc) * 8));
+    MFD_TRY(Jd.alloc(8));
+    MFD_CUDA(cudaMemsetAsync(geps.p, 0, geps.bytes, s));
+    MFD_CUDA(cudaMemsetAsync(gamp.p, 0, gamp.bytes, s));
+    const int64_t start = sim->steps;
+    // probes record from the first step of this call
+    sim->probe_from = start;
+    MFD_CUDA(cudaMemcpyAsync(sim->pstep0.p, &start, 8, cudaMemcpyHostToDevice, s));
+    const size_t sbytes = (size_t)n * 4 * rs;
+    // forward, with a checkpoint of the full state at the start of every segment
+    for (int64_t g = 0; g < nseg; ++g) {
+        MFD_CUDA(cudaMemcpyAsync((char*)ckpt.p + g * sbytes, sim->s0.p, sbytes, cudaMemcpyDeviceToDevice, s));
+        MFD_TRY(mfd_step(sim, std::min(every, nsteps - g * every)));
+    }
+    MFD_CUDA(cudaMemcpyAsync(fin.p, sim->s0.p, sbytes, cudaMemcpyDeviceToDevice, s));
+    MFD_CUDA(probe_energy(f64, sim->probe_buf.p, nsteps * sim->nprobe, sim->d.dt, Jd.as<double>(), s));
+    // lambda^N: dJ/dE^N at the probes, zero elsewhere
+    MFD_CUDA(init_lambda(f64, LA.p, fin.p, n, s));
+    MFD_CUDA(copy_ez(f64, fin.p, seg.p, n, s));
+    MFD_CUDA(adj_probe_term(f64, LA.p, seg.p, sim->probe_node.as<int64_t>(), sim->nprobe, sim->d.dt, s));
+    AdjArgs a;
+    a.fp64 = f64;
+    a.rowptr = sim->adj.rowptr.as<int64_t>();
+    a.col = sim->adj.col.as<int32_t>();
+    a.w = sim->adj.w.p;
+    a.n = n;
+    a.LA = LA.p;
+    a.LB = LB.p;
+    a.ch = sim->d.dt / sim->d.mu0;
+    a.gamma = sim->d.gamma;
+    a.eps = sim->eps.as<double>();
+    a.g_eps = geps.as<double>();
+    for (int64_t g = nseg - 1; g >= 0; --g) {
+        const int64_t s0 = start + g * every;
+        const int64_t len = std::min(every, nsteps - g * every);
+        // recompute the segment from its checkpoint, keeping Ez at every level
+        MFD_CUDA(cudaMemcpyAsync(sim->s0.p, (char*)ckpt.p + g * sbytes, sbytes, cudaMemcpyDeviceToDevice, s));
+        MFD_CUDA(cudaMemcpyAsync(sim->counter.p, &s0, 8, cudaMemcpyHostToDevice, s));
+        sim->steps = s0;
+        MFD_CUDA(copy_ez(f64, sim->s0.p, seg.p, n, s));
+        for (int64_t k = 0; k < len; ++k) {
+            MFD_CUDA(enqueue_step(sim, nullptr));
+            MFD_CUDA(copy_ez(f64, sim->s0.p, (char*)seg.p + (k + 1) * n * rs, n, s));
+        }
+        MFD_CUDA(cudaStreamSynchronize(s));  // s0 above lives on the host stack of this iteration
+        for (int64_t k = len - 1; k >= 0; --k) {
+            const int64_t step = s0 + k;  // step -> step + 1
+            MFD_CUDA(adj_sources(f64, LA.p, sim->src_node.as<int64_t>(), sim->src_amp.as<double>(),
+                                 sim->src_f0.as<double>(), sim->src_t0.as<double>(), sim->nsrc,
+                                 (double)(step + 1) * sim->d.dt, sim->eps.as<double>(), geps.as<double>(),
+                                 gamp.as<double>(), s));
+            a.e0 = (char*)seg.p + k * n * rs;
+            a.e1 = (char*)seg.p + (k + 1) * n * rs;
+            MFD_CUDA(adj_pass(a, 0, s));
+            MFD_CUDA(adj_pass(a, 1, s));
+            if (step - start >= 1)
+                MFD_CUDA(adj_probe_term(f64, LA.p, a.e0, sim->probe_node.as<int64_t>(), sim->nprobe, sim->d.dt, s));
+        }
+    }
+    // leave the simulation where a plain run of nsteps would
+    const int64_t end = start + nsteps;
+    MFD_CUDA(cudaMemcpyAsync(sim->s0.p, fin.p, sbytes, cudaMemcpyDeviceToDevice, s));
+    MFD_CUDA(cudaMemcpyAsync(sim->counter.p, &end, 8, cudaMemcpyHostToDevice, s));
+    sim->steps = end;
+    std::vector<double> gd(n);
+    MFD_CUDA(cudaMemcpyAsync(gd.data(), geps.p, n * 8, cudaMemcpyDeviceToHost, s));
+    MFD_CUDA(cudaMemcpyAsync(J, Jd.p, 8, cudaMemcpyDeviceToHost, s));
+    if (sim->nsrc > 0) MFD_CUDA(cudaMemcpyAsync(g_amp, gamp.p, sim->nsrc * 8, cudaMemcpyDeviceToHost, s));
+    MFD_CUDA(cudaStreamSynchronize(s));
+    for (int64_t k = 0; k < n; ++k) g_eps[sim->eset->h_perm[k]] = gd[k];
+    return MFD_OK;
+}
 
 void mfd_sim_destroy(mfd_sim* sim) {
     if (!sim) return;

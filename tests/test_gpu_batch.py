@@ -1,0 +1,113 @@
+"""Batched domains x right-hand sides (one persistent cooperative kernel) against the oracle.
+
+Each domain (PEC squares and disks of different sizes and stencil sizes
+n in {12, 20, 30, 40}, PHS r^3 with the largest m such that 2 M_m <= n,
+Delta^2 hyperviscosity) carries R right-hand sides; right-hand side r has its
+own random initial fields and its own Ricker source. Every right-hand side of
+every domain must match an independent single-RHS oracle run: relative L2
+over the domain's fields (all right-hand sides) and probe series within 1e-5
+(FP32).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+M = pytest.importorskip("paper_2508_18205_gb300")
+
+S, C_HV, ALPHA = 0.5, 4e-3, 2
+
+
+def _domains(ctx, specs):
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    doms, keep = [], []
+    for ns, n in specs:
+        m = W.poly_degree_for(n)
+        nd = M.Nodes(ctx, ns.xyz, ns.period)
+        st = M.Stencils(nd, nd, max(n, 31))
+        cw = M.Weights(st, n, 3, m, M.MFD_OP_GRAD)
+        hw = M.Weights(st, 31, 5, 4, M.MFD_OP_LAP_POW, ALPHA)
+        doms.append((cw, hw, dt, eps0, mu0, -C_HV))
+        keep.append((nd, st))
+    return doms, keep
+
+
+@pytest.mark.parametrize("R", [16, 4, 32])
+def test_batch_matches_single_rhs_oracle(R):
+    ctx = M.Ctx(0)
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    specs = [(W.pec_box((30, 30), 0.25, 1), 12), (W.disk(15.0, 0.25, 2), 20),
+             (W.pec_box((41, 33), 0.25, 3), 30), (W.disk(19.5, 0.25, 4), 40),
+             (W.pec_box((9, 9), 0.25, 5), 12)]
+    if R != 16:
+        specs = specs[:2]
+    doms, keep = _domains(ctx, specs)
+    bt = M.Batch(ctx, doms, nrhs=R)
+    nsteps = 150
+    rng = np.random.default_rng(R)
+    init, srcs, probes = [], [], []
+    for d, (ns, n) in enumerate(specs):
+        eps = W.eps_r_uniform(ns.n, 100 + d)
+        bt.set_materials(d, eps, ns.pec)
+        f = 0.1 * rng.standard_normal((3, ns.n, R))
+        f[0][ns.pec == 1] = 0
+        for c, comp in enumerate((M.MFD_EZ, M.MFD_HX, M.MFD_HY)):
+            bt.set_field(d, comp, f[c])
+        src = W.ricker_sources(ns, R, 200 + d, c0, nrhs=R, one_per_rhs=True)
+        bt.set_sources(d, src.node, src.rhs, src.amp, src.f0, src.t0)
+        pr = W.interior_nodes(ns, 4, 300 + d)
+        bt.set_probes(d, pr, nsteps)
+        init.append((f, eps))
+        srcs.append(src)
+        probes.append(pr)
+    bt.step(nsteps)
+    for d, (ns, n) in enumerate(specs):
+        f, eps = init[d]
+        prob, _ = O.tmz_collocated(ns, n, 3, W.poly_degree_for(n), ALPHA, dt, eps0, mu0, -C_HV, eps_r=eps)
+        got = [bt.get_field(d, comp) for comp in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)]
+        gp = bt.read_probes(d)
+        ref = [np.zeros((ns.n, R)) for _ in range(3)]
+        rp = np.zeros((nsteps, len(probes[d]), R))
+        for r in range(R):
+            sel = srcs[d].rhs == r
+            sub = W.Sources(node=srcs[d].node[sel], rhs=srcs[d].rhs[sel], amp=srcs[d].amp[sel],
+                            f0=srcs[d].f0[sel], t0=srcs[d].t0[sel])
+            e1, x1, y1, p1, _ = O.run_tmz(prob, f[0][:, r], f[1][:, r], f[2][:, r], nsteps, sources=sub,
+                                          probes=probes[d])
+            ref[0][:, r], ref[1][:, r], ref[2][:, r] = e1, x1, y1
+            rp[:, :, r] = p1
+        g = np.concatenate([x.reshape(-1) for x in got])
+        rr = np.concatenate([x.reshape(-1) for x in ref])
+        err = np.linalg.norm(g - rr) / np.linalg.norm(rr)
+        perr = np.linalg.norm(gp - rp) / np.linalg.norm(rp)
+        assert err <= 1e-5, (d, err)
+        assert perr <= 1e-5, (d, perr)
+        assert np.all(got[0][ns.pec == 1] == 0)
+
+
+def test_batch_repeated_steps_continue():
+    """Two step calls of k steps equal one call of 2k steps (the step counter and sources carry on)."""
+    ctx = M.Ctx(0)
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    specs = [(W.pec_box((20, 20), 0.25, 7), 12), (W.disk(11.0, 0.25, 8), 20)]
+    out = []
+    for split in (False, True):
+        doms, keep = _domains(ctx, specs)
+        bt = M.Batch(ctx, doms, nrhs=16)
+        for d, (ns, n) in enumerate(specs):
+            bt.set_materials(d, None, ns.pec)
+            src = W.ricker_sources(ns, 16, 400 + d, c0, nrhs=16, one_per_rhs=True)
+            bt.set_sources(d, src.node, src.rhs, src.amp, src.f0, src.t0)
+        if split:
+            bt.step(40)
+            bt.step(40)
+        else:
+            bt.step(80)
+        out.append([bt.get_field(d, M.MFD_EZ) for d in range(len(specs))])
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)

@@ -299,3 +299,33 @@ def test_pec_nodes_stay_zero_and_3d_tangential():
         # a node on one wall keeps its normal component
         normal_only = (m == (1 << b))
         assert np.any(E[b][normal_only] != 0)
+
+
+def test_sampled_step_equals_full_step():
+    """The oracle's sampled one-step evaluation equals its full step on every sampled node."""
+    S, alpha = 0.5, 3
+    dt, eps0, mu0, c0, eta0 = _units(S)
+    e = W.periodic_box((30, 30), 0.25, 71)
+    h = W.periodic_box((30, 30), 0.25, 72, offset=(0.5, 0.5))
+    prob = O.tmz_staggered(e, h, 30, 5, 4, alpha, dt, eps0, mu0, 4e-5)
+    rng = np.random.default_rng(9)
+    ez = rng.standard_normal(e.n)
+    hx, hy = rng.standard_normal((2, h.n))
+    full = O.run_tmz(prob, ez, hx, hy, 1)
+    ids = W.interior_nodes(e, 20, 73)
+    hids = W.interior_nodes(h, 7, 74)
+    ez1, hx1, hy1, hs = O.tmz_sample_step(e, h, ids, 30, 5, 4, alpha, dt, eps0, mu0, 4e-5, ez, hx, hy,
+                                          h_ids=hids)
+    assert np.allclose(ez1, full[0][ids], rtol=0, atol=1e-13)
+    assert np.allclose(hx1, full[1][hs], rtol=0, atol=1e-13)
+    assert np.allclose(hy1, full[2][hs], rtol=0, atol=1e-13)
+    assert set(hids) <= set(hs)
+    # collocated layout (one node set)
+    nodes = W.periodic_box((25, 25), 0.25, 75)
+    p2, _ = O.tmz_collocated(nodes, 12, 3, 2, 2, dt, eps0, mu0, -4e-3)
+    f2 = O.run_tmz(p2, ez[:nodes.n], hx[:nodes.n], hy[:nodes.n], 1)
+    ids2 = W.interior_nodes(nodes, 15, 76)
+    e2, x2, y2, hs2 = O.tmz_sample_step(nodes, nodes, ids2, 12, 3, 2, 2, dt, eps0, mu0, -4e-3, ez[:nodes.n],
+                                        hx[:nodes.n], hy[:nodes.n], collocated=True)
+    assert np.allclose(e2, f2[0][ids2], rtol=0, atol=1e-13)
+    assert np.allclose(x2, f2[1][hs2], rtol=0, atol=1e-13)

@@ -310,3 +310,30 @@ def units(courant: float):
 def n_monomials(m: int, d: int) -> int:
     """M_m = C(m + d, d): the number of monomials of total degree <= m in d variables."""
     return math.comb(m + d, d)
+
+
+def batch_domains(count: int, seed: int, n_min: int = 2000, n_max: int = 60000,
+                  stencils=(12, 20, 30, 40), jitter: float = 0.25):
+    """`count` domains for the batched workload: squares and disks (alternating
+    draws), node counts log-uniform in [n_min, n_max], stencil size drawn
+    uniformly from `stencils`. Returns a list of (NodeSet, n)."""
+    u = uniform(seed, 3 * count).reshape(count, 3)
+    out = []
+    for d in range(count):
+        target = math.exp(math.log(n_min) + (math.log(n_max) - math.log(n_min)) * u[d, 0])
+        n = stencils[min(int(u[d, 1] * len(stencils)), len(stencils) - 1)]
+        if u[d, 2] < 0.5:
+            side = max(8, int(round(math.sqrt(target))))
+            ns = pec_box((side, side), jitter, seed * 1000 + d)
+        else:
+            ns = disk(max(6.0, math.sqrt(target / math.pi)), jitter, seed * 1000 + d)
+        out.append((ns, n))
+    return out
+
+
+def poly_degree_for(n: int) -> int:
+    """The largest augmentation degree m with 2 M_m <= n in 2D (n = 12, 20, 30, 40 -> 2, 3, 4, 4)."""
+    m = 0
+    while 2 * n_monomials(m + 1, 2) <= n:
+        m += 1
+    return m
