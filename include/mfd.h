@@ -254,6 +254,14 @@ int64_t mfd_batch_nodes(const mfd_batch* b);
 int mfd_batch_uses_graph(const mfd_batch* b);
 void mfd_batch_destroy(mfd_batch* b);
 
+/* ----------------------------------------------------------- diagnostics */
+
+/* Measured FMA throughput of `device` in GFLOP/s (FP64 and FP32): eight
+ * independent FMA chains per thread on every SM, best of five timed launches.
+ * The paper has no counterpart; it is the denominator of the FP64 step's ALU
+ * roofline. */
+mfd_status mfd_fma_peak(int device, double* fp64_gflops, double* fp32_gflops);
+
 /* ------------------------------------------------- kNN without allocation */
 
 /* The kNN stencils of mfd_stencils_build, computed on caller-owned device

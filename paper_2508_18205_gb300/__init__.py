@@ -69,6 +69,7 @@ _SIGS = {
     "mfd_energy": (_I, [_VP, _VP]),
     "mfd_sim_steps": (_I64, [_VP]),
     "mfd_grad": (_I, [_VP, _I64, _I64, _VP, _VP, _VP]),
+    "mfd_fma_peak": (_I, [_I, _VP, _VP]),
     "mfd_sim_destroy": (None, [_VP]),
     "mfd_knn_static": (_I, [_I, _I64, _VP, _I64, _VP, _VP, _I, _VP, _VP]),
     "mfd_batch_create": (_I, [_VP, _I, _VP, _I, C.POINTER(_VP)]),
@@ -117,6 +118,13 @@ def _p(a):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def fma_peak(device=0):
+    """(FP64, FP32) FMA throughput of the device in GFLOP/s (mfd_fma_peak)."""
+    a, b = np.zeros(1), np.zeros(1)
+    _ck(lib().mfd_fma_peak(device, _p(a), _p(b)))
+    return float(a[0]), float(b[0])
 
 
 # ------------------------------------------------------------------ handles

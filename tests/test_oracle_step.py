@@ -329,3 +329,18 @@ def test_sampled_step_equals_full_step():
                                         hx[:nodes.n], hy[:nodes.n], collocated=True)
     assert np.allclose(e2, f2[0][ids2], rtol=0, atol=1e-13)
     assert np.allclose(x2, f2[1][hs2], rtol=0, atol=1e-13)
+
+
+def test_3d_energy_of_constant_fields():
+    """Eq. 20 in 3D: constant fields have zero curl and zero HV (sum of weights 0), so
+    U = sum_i eps_r,i |E|^2 + eta0^2 |H|^2 exactly (up to the weights' round-off)."""
+    S = 0.4
+    dt, eps0, mu0, c0, eta0 = _units(S)
+    nodes = W.periodic_box((6, 6, 6), 0.25, 81)
+    er = W.eps_r_uniform(nodes.n, 82)
+    prob, _ = O.max3d_collocated(nodes, 20, 3, 2, 2, dt, eps0, mu0, -1e-3, eps_r=er)
+    E = np.tile(np.array([[0.3], [-0.2], [0.5]]), (1, nodes.n))
+    H = np.tile(np.array([[0.1], [0.4], [-0.7]]), (1, nodes.n))
+    _, _, _, en = O.run_3d(prob, E, H, 1, energy=True)
+    ref = np.sum(er) * (0.09 + 0.04 + 0.25) + (mu0 / eps0) * nodes.n * (0.01 + 0.16 + 0.49)
+    assert abs(en[0] - ref) <= 1e-9 * ref
