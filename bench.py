@@ -163,6 +163,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(elapsed_s, units, dist=None):
+    """Whole-job throughput of N replicas: the slowest rank's time (max over
+    ranks, all-reduced) and value = units x world / that time. Returns
+    (max elapsed seconds, value)."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(elapsed_s)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_s = float(t.item())
+    return elapsed_s, units * world / elapsed_s
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -216,26 +231,38 @@ def cpu_baseline(budget_s=20.0):
 
 
 def run_reference(a, rank, world):
+    """The reference arm: the FP64 oracle as it stands, on the host cores, one
+    bench step = one leapfrog step of a bounded sample of the workload (a
+    160 x 160 + 160 x 160 staggered periodic sub-square with the same stencils
+    and coefficients). Rank 0 alone runs it."""
     if rank != 0:
         return
     import oracle as O
     O.build()
-    per = []
-    for _ in range(a.warmup):
-        pass
+    S, n, k, m, alpha, c = (PARAMS[x] for x in ("S", "n", "k", "m", "alpha", "c"))
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    nx = 160
+    e, h = node_sets(nx)
     t0 = time.time()
-    cb = None
-    for _ in range(max(1, a.steps if a.steps <= 3 else 3)):
-        cb = cpu_baseline(budget_s=max(3.0, 30.0 / max(1, min(a.steps, 3))))
-        per.append(cb["value"])
-    v = float(np.median(per))
+    prob = O.tmz_staggered(e, h, n, k, m, alpha, dt, eps0, mu0, c * (-1) ** (alpha - 1))
+    setup = time.time() - t0
+    ez, hx, hy = pulse_fields(e, h, nx, dt)
+    if a.warmup:
+        ez, hx, hy, _, _ = O.run_tmz(prob, ez, hx, hy, a.warmup)
+    t0 = time.perf_counter()
+    O.run_tmz(prob, ez, hx, hy, a.steps, step0=a.warmup)
+    el = time.perf_counter() - t0
+    v = (e.n + 2 * h.n) * a.steps / el
+    cb = {"value": v, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+          "sample": f"{nx}x{nx}+{nx}x{nx} staggered periodic sub-square of the workload, same stencils, "
+                    f"{a.steps} FP64 steps in {el:.2f} s (setup {setup:.1f} s)"}
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": el / a.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "pulse2d-staggered-1M (bounded oracle sample)", "nodes_per_set": a.nx ** 2},
-            "cpu_baseline": {**cb, "value": v},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": time.time() - t0}
+            "config": {"workload": f"pulse2d-staggered-{a.nx}x{a.nx}x2 (bounded sample: {nx}x{nx}x2)",
+                       "nodes_per_set": nx * nx},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -274,6 +301,7 @@ def main():
         s_.set_probes(probes, cap)
 
     reset(sim, a.steps + a.warmup + 8)
+    blocks = sim.autotune(20)
     stream = ctx.torch_stream()
     sim.step(a.warmup)
     sim.step_timed(min(a.steps, 64))  # creates the per-launch event pool
@@ -292,13 +320,10 @@ def main():
     # per-kernel durations: the same number of steps, every launch bracketed by CUDA events
     ms = sim.step_timed(a.steps)
     clocks = sampler.stop()
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-        dist.barrier()
     per_step_updates = e.n + 2 * h.n
-    value = per_step_updates * a.steps * world / elapsed
+    elapsed, value = aggregate(elapsed, per_step_updates * a.steps, dist)
+    if dist:
+        dist.barrier()
     s = 8 if prec == M.MFD_FP64 else 4
     peak, peak_kind = peaks()
     roof = roofline(ms, a.steps, e, h, nhv, s, peak, peak_kind)
@@ -310,7 +335,8 @@ def main():
                        "nodes_per_set": nx * nx, "layout": "staggered", "curl_stencil": PARAMS["n"],
                        "hv_stencil": nhv, "phs": PARAMS["k"], "poly_m": PARAMS["m"], "alpha": PARAMS["alpha"],
                        "courant": S, "compensated": comp, "l2_flush": "inputs larger than L2 (1.7 GB/step)",
-                       "parallelism": f"replicas{world}", "setup_s": setup},
+                       "parallelism": f"replicas{world}", "setup_s": setup,
+                       "autotuned_blocks": {"h_pass": blocks[0], "e_pass": blocks[1]}},
             "roofline": roof, "clocks": clocks, "gpu_launches": 3 * a.steps,
             "event_timed_ms_per_step": (ms[0] + ms[1]) / a.steps}
     # the plain FP64 GPU step on the same GPU, and FP32 accuracy against it
@@ -318,6 +344,7 @@ def main():
         k64 = min(a.steps, 1000)
         s64 = make_sim(M, ctx, wts, M.MFD_FP64, False)
         reset(s64, 8)
+        s64.autotune(10)
         s64.step(a.warmup)
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)

@@ -198,6 +198,20 @@ mfd_status mfd_read_probes(mfd_sim* sim, double* host, int64_t* steps);
  * dt/2 and t_n + dt/2 (the latter computed on the fly). Multiply by the
  * domain measure / node count for the integral of Eq. 20. */
 mfd_status mfd_energy(mfd_sim* sim, double* u);
+/* Energy watchdog (failure detection for the instability of Sec. 5 / App. A):
+ * with every > 0, mfd_step computes Eq. 20 after every `every` steps and
+ * returns MFD_ERR_UNSTABLE (with the steps taken so far kept) once the energy
+ * exceeds max_ratio times its value at this call, or is NaN. every = 0 turns
+ * it off. Needs the fields set (nonzero energy). */
+mfd_status mfd_set_watchdog(mfd_sim* sim, int64_t every, double max_ratio);
+/* Threads per block of the H and E half-step kernels (64, 128, 256 or 512;
+ * 256 by default). */
+mfd_status mfd_sim_set_blocks(mfd_sim* sim, int block_h, int block_e);
+/* Autotuner: times each half-step kernel on this problem `reps` times with
+ * 128, 256 and 512 threads per block, keeps the fastest for each (chosen[0]:
+ * H pass, chosen[1]: E pass; may be NULL) and restores the fields, so the
+ * simulation does not advance. */
+mfd_status mfd_sim_autotune(mfd_sim* sim, int reps, int* chosen);
 /* Number of steps taken since the last mfd_set_field(MFD_EZ). */
 /* Gradient of the probe objective J = dt sum_{n=1..N} sum_p (Ez_p^n)^2
  * (Ez at the probes of mfd_set_probes after each of the next N = nsteps

@@ -70,6 +70,9 @@ _SIGS = {
     "mfd_sim_steps": (_I64, [_VP]),
     "mfd_grad": (_I, [_VP, _I64, _I64, _VP, _VP, _VP]),
     "mfd_fma_peak": (_I, [_I, _VP, _VP]),
+    "mfd_sim_set_blocks": (_I, [_VP, _I, _I]),
+    "mfd_set_watchdog": (_I, [_VP, _I64, _D]),
+    "mfd_sim_autotune": (_I, [_VP, _I, _VP]),
     "mfd_sim_destroy": (None, [_VP]),
     "mfd_knn_static": (_I, [_I, _I64, _VP, _I64, _VP, _VP, _I, _VP, _VP]),
     "mfd_batch_create": (_I, [_VP, _I, _VP, _I, C.POINTER(_VP)]),
@@ -292,6 +295,18 @@ class Sim:
     @property
     def steps(self):
         return int(lib().mfd_sim_steps(self.h))
+
+    def set_watchdog(self, every, max_ratio=1.5):
+        _ck(lib().mfd_set_watchdog(self.h, int(every), float(max_ratio)))
+
+    def set_blocks(self, block_h, block_e):
+        _ck(lib().mfd_sim_set_blocks(self.h, int(block_h), int(block_e)))
+
+    def autotune(self, reps=20):
+        """Times 128/256/512 threads per block for each half-step kernel and keeps the fastest."""
+        ch = np.zeros(2, dtype=np.int32)
+        _ck(lib().mfd_sim_autotune(self.h, int(reps), _p(ch)))
+        return int(ch[0]), int(ch[1])
 
     def grad(self, nsteps, every=64, nsrc=0):
         """(J, dJ/deps_r per E node, dJ/d amplitude per source) over the next nsteps (mfd_grad)."""

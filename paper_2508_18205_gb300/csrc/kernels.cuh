@@ -77,6 +77,9 @@ __device__ __forceinline__ void st4(dbl4* p, dbl4 v) {
 }
 
 // ---- stencil-sum accumulators
+// The "compensated" option compensates the curl sums, which carry the O(1)
+// update of the fields; the hyperviscosity sums are multiplied by gamma
+// (1e-5 .. 1e-2) and stay plain FMA sums.
 // Plain: fused multiply-add in the working precision.
 template <typename T> struct AccPlain {
     T s = T(0);

@@ -181,6 +181,9 @@ struct mfd_sim {
     std::vector<cudaEvent_t> events;
     AdjT adj;
     bool adj_ok = false;
+    int block[2] = {256, 256};  // threads per block of the H and E half-step kernels (autotuned)
+    int64_t watch_every = 0;    // energy watchdog: check every this many steps (0: off)
+    double watch_ratio = 0, watch_u0 = 0;
     ~mfd_sim() {
         if (graph) cudaGraphExecDestroy(graph);
         for (auto e : events) cudaEventDestroy(e);
@@ -266,6 +269,8 @@ Launch2D make2d(mfd_sim* sim, int parity) {
     L.kf.gamma = (float)sim->d.gamma;
     L.kd.ch = sim->d.dt / sim->d.mu0;
     L.kd.gamma = sim->d.gamma;
+    L.block[0] = sim->block[0];
+    L.block[1] = sim->block[1];
     if (!L.staggered) {
         L.A = sim->s0.p;
         L.B = sim->s1.p;
@@ -291,6 +296,8 @@ Launch3D make3d(mfd_sim* sim, int parity) {
     L.kf.gamma = (float)sim->d.gamma;
     L.kd.ch = sim->d.dt / sim->d.mu0;
     L.kd.gamma = sim->d.gamma;
+    L.block[0] = sim->block[0];
+    L.block[1] = sim->block[1];
     DevBuf* H[2] = {&sim->s2, &sim->s3};
     L.E = sim->s0.p;
     L.Es = sim->s1.p;
@@ -407,6 +414,8 @@ mfd_status check_set(const mfd_weights* curl, const mfd_weights* hv, const mfd_n
 }  // namespace
 
 extern "C" {
+
+mfd_status mfd_energy(mfd_sim* sim, double* u);
 
 mfd_status mfd_sim_create(mfd_ctx* ctx, const mfd_sim_desc* desc, mfd_sim** out) {
     if (!ctx || !desc || !out) return fail(MFD_ERR_ARG, "NULL argument");
@@ -680,7 +689,7 @@ mfd_status mfd_set_probes(mfd_sim* sim, int count, const int64_t* node, int64_t 
     return MFD_OK;
 }
 
-mfd_status mfd_step(mfd_sim* sim, int64_t nsteps) {
+static mfd_status step_plain(mfd_sim* sim, int64_t nsteps) {
     if (!sim || nsteps < 0) return fail(MFD_ERR_ARG, "bad arguments");
     MFD_CUDA(cudaSetDevice(sim->ctx->device));
     int64_t left = nsteps;
@@ -699,6 +708,37 @@ mfd_status mfd_step(mfd_sim* sim, int64_t nsteps) {
     while (left > 0) {
         MFD_CUDA(enqueue_step(sim, nullptr));
         --left;
+    }
+    return MFD_OK;
+}
+
+mfd_status mfd_step(mfd_sim* sim, int64_t nsteps) {
+    if (!sim || nsteps < 0) return fail(MFD_ERR_ARG, "bad arguments");
+    if (sim->watch_every <= 0) return step_plain(sim, nsteps);
+    for (int64_t done = 0; done < nsteps;) {
+        const int64_t k = std::min(sim->watch_every, nsteps - done);
+        MFD_TRY(step_plain(sim, k));
+        done += k;
+        double u = 0;
+        MFD_TRY(mfd_energy(sim, &u));
+        if (!(u == u) || !(u <= sim->watch_ratio * sim->watch_u0))
+            return fail(MFD_ERR_UNSTABLE, "energy watchdog: U = " + std::to_string(u) + " after step " +
+                                              std::to_string(sim->steps) + " exceeds " +
+                                              std::to_string(sim->watch_ratio) + " x U0 = " +
+                                              std::to_string(sim->watch_u0) + " (or is NaN)");
+    }
+    return MFD_OK;
+}
+
+mfd_status mfd_set_watchdog(mfd_sim* sim, int64_t every, double max_ratio) {
+    if (!sim || every < 0 || (every > 0 && !(max_ratio > 0))) return fail(MFD_ERR_ARG, "bad arguments");
+    sim->watch_every = every;
+    sim->watch_ratio = max_ratio;
+    if (every > 0) {
+        double u = 0;
+        MFD_TRY(mfd_energy(sim, &u));
+        if (!(u > 0)) return fail(MFD_ERR_STATE, "energy watchdog needs nonzero fields (set them first)");
+        sim->watch_u0 = u;
     }
     return MFD_OK;
 }
@@ -773,6 +813,86 @@ mfd_status mfd_energy(mfd_sim* sim, double* u) {
 }
 
 int64_t mfd_sim_steps(const mfd_sim* sim) { return sim ? sim->steps : -1; }
+
+static bool block_ok(int b) { return b == 64 || b == 128 || b == 256 || b == 512; }
+
+mfd_status mfd_sim_set_blocks(mfd_sim* sim, int block_h, int block_e) {
+    if (!sim || !block_ok(block_h) || !block_ok(block_e)) return fail(MFD_ERR_ARG, "block sizes: 64, 128, 256 or 512");
+    sim->block[0] = block_h;
+    sim->block[1] = block_e;
+    sim->graph_ok = false;
+    return MFD_OK;
+}
+
+mfd_status mfd_sim_autotune(mfd_sim* sim, int reps, int* chosen) {
+    if (!sim || reps < 1) return fail(MFD_ERR_ARG, "bad arguments");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    // the timed launches overwrite state buffers: keep a copy and put it back
+    DevBuf* bufs[5] = {&sim->s0, &sim->s1, &sim->s2, &sim->s3, &sim->s4};
+    DevBuf save[5];
+    for (int b = 0; b < 5; ++b)
+        if (bufs[b]->p) {
+            MFD_TRY(save[b].alloc(bufs[b]->bytes));
+            MFD_CUDA(cudaMemcpyAsync(save[b].p, bufs[b]->p, bufs[b]->bytes, cudaMemcpyDeviceToDevice, s));
+        }
+    cudaEvent_t e0, e1;
+    MFD_CUDA(cudaEventCreate(&e0));
+    MFD_CUDA(cudaEventCreate(&e1));
+    const int cand[3] = {128, 256, 512};
+    int best[2] = {sim->block[0], sim->block[1]};
+    mfd_status st = MFD_OK;
+    for (int pass = 0; pass < 2 && st == MFD_OK; ++pass) {
+        float tbest = 1e30f;
+        for (int c = 0; c < 3 && st == MFD_OK; ++c) {
+            int blk[2] = {best[0], best[1]};
+            blk[pass] = cand[c];
+            cudaError_t e = cudaSuccess;
+            auto launch = [&]() {
+                if (sim->layout == COLLOC3D) {
+                    Launch3D L = make3d(sim, sim->parity);
+                    L.block[0] = blk[0];
+                    L.block[1] = blk[1];
+                    return launch_3d(L, pass, s);
+                }
+                Launch2D L = make2d(sim, sim->parity);
+                L.block[0] = blk[0];
+                L.block[1] = blk[1];
+                return launch_2d(L, pass, s);
+            };
+            e = launch();
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+            cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                st = fail(MFD_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+                break;
+            }
+            if (ms < tbest) {
+                tbest = ms;
+                best[pass] = cand[c];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int b = 0; b < 5; ++b)
+        if (bufs[b]->p) cudaMemcpyAsync(bufs[b]->p, save[b].p, bufs[b]->bytes, cudaMemcpyDeviceToDevice, s);
+    MFD_CUDA(cudaStreamSynchronize(s));
+    if (st != MFD_OK) return st;
+    sim->block[0] = best[0];
+    sim->block[1] = best[1];
+    sim->graph_ok = false;
+    if (chosen) {
+        chosen[0] = best[0];
+        chosen[1] = best[1];
+    }
+    return MFD_OK;
+}
 
 mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, double* g_eps, double* g_amp) {
     if (!sim || nsteps < 1 || every < 1 || !J || !g_eps) return fail(MFD_ERR_ARG, "bad arguments");

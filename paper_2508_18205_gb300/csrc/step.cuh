@@ -24,6 +24,7 @@ struct Launch2D {
     Both<void> hs, es;  // stencil streams of the H pass and the E pass
     Coefs<float> kf;
     Coefs<double> kd;
+    int block[2] = {256, 256};  // threads per block of the H pass and the E pass
     void* A = nullptr;  // collocated state {Ez, Hx, Hy, ce}^n
     void* B = nullptr;  // collocated intermediate {E*, Hx', Hy', ce}
     Stag2DPtrs stag;
@@ -44,6 +45,7 @@ struct Launch3D {
     const void* H = nullptr;   // {Hx, Hy, Hz, 0}^{n-1/2}
     void* Hn = nullptr;        // ^{n+1/2}
     const uint8_t* wall = nullptr;  // bit a: node on a wall normal to axis a
+    int block[2] = {256, 256};      // threads per block of the H pass and the E pass
 };
 
 cudaError_t launch_3d(const Launch3D& L, int pass, cudaStream_t st);

@@ -21,12 +21,14 @@ template <typename T, int NC, int NV, bool SHARED, bool COMP>
 __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const typename Vec<T>::V4* __restrict__ A,
                                               int64_t i, T& dxE, T& dyE, T& vx, T& vy, T& ve) {
     using V4 = typename Vec<T>::V4;
-    using Acc = typename AccSel<T, COMP>::type;
+    using Acc = typename AccSel<T, COMP>::type;  // curl sums (compensated when COMP)
+    using AccV = AccPlain<T>;                    // hyperviscosity sums (scaled by gamma)
     const int nc = NC ? NC : s.nc;
     const int nv = NV ? NV : s.nv;
     const int64_t slice = i >> 5;
     const int lane = (int)(i & 31);
-    Acc ax, ay, hx, hy, he;
+    Acc ax, ay;
+    AccV hx, hy, he;
     if constexpr (SHARED) {
         const int ni = (NC && NV) ? (NC > NV ? NC : NV) : s.ni;
         const int4* ip = s.idx_c + slice * ni * 32 + lane;
@@ -88,7 +90,7 @@ __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const 
 }
 
 template <typename T, int NC, int NV, bool SHARED, bool COMP>
-__global__ void __launch_bounds__(256) k_h_colloc(StencilStreams<T> s, Coefs<T> k,
+__global__ void __launch_bounds__(512) k_h_colloc(StencilStreams<T> s, Coefs<T> k,
                                                   const typename Vec<T>::V4* __restrict__ A,
                                                   typename Vec<T>::V4* __restrict__ B) {
     using V4 = typename Vec<T>::V4;
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(256) k_h_colloc(StencilStreams<T> s, Coefs<T> 
 }
 
 template <typename T, int NC, bool SHARED, bool COMP>
-__global__ void __launch_bounds__(256) k_e_colloc(StencilStreams<T> s, const typename Vec<T>::V4* __restrict__ B,
+__global__ void __launch_bounds__(512) k_e_colloc(StencilStreams<T> s, const typename Vec<T>::V4* __restrict__ B,
                                                   typename Vec<T>::V4* __restrict__ A) {
     using V4 = typename Vec<T>::V4;
     using Acc = typename AccSel<T, COMP>::type;
@@ -179,6 +181,7 @@ __device__ __forceinline__ void h_stag_node(const StencilStreams<T>& s, const T*
     using V4 = typename Vec<T>::V4;
     using V2 = typename Vec<T>::V2;
     using Acc = typename AccSel<T, COMP>::type;
+    using AccV = AccPlain<T>;
     const int nc = NC ? NC : s.nc;
     const int nv = NV ? NV : s.nv;
     const int64_t slice = i >> 5;
@@ -188,7 +191,8 @@ __device__ __forceinline__ void h_stag_node(const StencilStreams<T>& s, const T*
     const V4* px = s.wx + slice * nc * 32 + lane;
     const V4* py = s.wy + slice * nc * 32 + lane;
     const V4* pv = s.wv + slice * nv * 32 + lane;
-    Acc ax, ay, hx, hy;
+    Acc ax, ay;
+    AccV hx, hy;
 #pragma unroll
     for (int c = 0; c < nc; ++c) {
         const int4 id = ld_stream(ic + c * 32);
@@ -214,7 +218,7 @@ __device__ __forceinline__ void h_stag_node(const StencilStreams<T>& s, const T*
 }
 
 template <typename T, int NC, int NV, bool COMP>
-__global__ void __launch_bounds__(256) k_h_stag(StencilStreams<T> s, Coefs<T> k, const T* __restrict__ Ez,
+__global__ void __launch_bounds__(512) k_h_stag(StencilStreams<T> s, Coefs<T> k, const T* __restrict__ Ez,
                                                 const typename Vec<T>::V2* __restrict__ H,
                                                 typename Vec<T>::V2* __restrict__ Hn) {
     using V2 = typename Vec<T>::V2;
@@ -230,7 +234,7 @@ __global__ void __launch_bounds__(256) k_h_stag(StencilStreams<T> s, Coefs<T> k,
 }
 
 template <typename T, int NC, int NV, bool COMP>
-__global__ void __launch_bounds__(256) k_e_stag(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V2* __restrict__ Hn,
+__global__ void __launch_bounds__(512) k_e_stag(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V2* __restrict__ Hn,
                                                 const T* __restrict__ Ez, const T* __restrict__ ce,
                                                 T* __restrict__ Ezn) {
     using V4 = typename Vec<T>::V4;
@@ -247,7 +251,8 @@ __global__ void __launch_bounds__(256) k_e_stag(StencilStreams<T> s, Coefs<T> k,
     const V4* px = s.wx + slice * nc * 32 + lane;
     const V4* py = s.wy + slice * nc * 32 + lane;
     const V4* pv = s.wv + slice * nv * 32 + lane;
-    Acc dxHy, dyHx, he;
+    Acc dxHy, dyHx;
+    AccPlain<T> he;
 #pragma unroll
     for (int c = 0; c < nc; ++c) {
         const int4 id = ld_stream(ic + c * 32);
@@ -301,32 +306,32 @@ __global__ void __launch_bounds__(256) k_energy_stag(StencilStreams<T> s, Coefs<
 
 template <typename T, bool COMP>
 static cudaError_t launch_colloc_pass(int pass, const StencilStreams<T>& s, const Coefs<T>& k, void* A, void* B,
-                                      cudaStream_t st) {
+                                      int block, cudaStream_t st) {
     using V4 = typename Vec<T>::V4;
     const bool shared = s.idx_v == s.idx_c;
-    const unsigned grid = (unsigned)((s.n + 255) / 256);
+    const unsigned grid = (unsigned)((s.n + block - 1) / block);
     V4* a = static_cast<V4*>(A);
     V4* b = static_cast<V4*>(B);
 #define MFD_H(NC, NV)                                                                    \
     if (s.nc == NC && s.nv == NV) {                                                      \
-        if (shared) k_h_colloc<T, NC, NV, true, COMP><<<grid, 256, 0, st>>>(s, k, a, b); \
-        else k_h_colloc<T, NC, NV, false, COMP><<<grid, 256, 0, st>>>(s, k, a, b);       \
+        if (shared) k_h_colloc<T, NC, NV, true, COMP><<<grid, block, 0, st>>>(s, k, a, b); \
+        else k_h_colloc<T, NC, NV, false, COMP><<<grid, block, 0, st>>>(s, k, a, b);       \
         return cudaGetLastError();                                                       \
     }
 #define MFD_E(NC)                                                                     \
     if (s.nc == NC) {                                                                 \
-        if (shared) k_e_colloc<T, NC, true, COMP><<<grid, 256, 0, st>>>(s, b, a);     \
-        else k_e_colloc<T, NC, false, COMP><<<grid, 256, 0, st>>>(s, b, a);           \
+        if (shared) k_e_colloc<T, NC, true, COMP><<<grid, block, 0, st>>>(s, b, a);     \
+        else k_e_colloc<T, NC, false, COMP><<<grid, block, 0, st>>>(s, b, a);           \
         return cudaGetLastError();                                                    \
     }
     if (pass == 0) {
         MFD_H(3, 8) MFD_H(5, 8) MFD_H(8, 8) MFD_H(10, 8)
-        if (shared) k_h_colloc<T, 0, 0, true, COMP><<<grid, 256, 0, st>>>(s, k, a, b);
-        else k_h_colloc<T, 0, 0, false, COMP><<<grid, 256, 0, st>>>(s, k, a, b);
+        if (shared) k_h_colloc<T, 0, 0, true, COMP><<<grid, block, 0, st>>>(s, k, a, b);
+        else k_h_colloc<T, 0, 0, false, COMP><<<grid, block, 0, st>>>(s, k, a, b);
     } else {
         MFD_E(3) MFD_E(5) MFD_E(8) MFD_E(10)
-        if (shared) k_e_colloc<T, 0, true, COMP><<<grid, 256, 0, st>>>(s, b, a);
-        else k_e_colloc<T, 0, false, COMP><<<grid, 256, 0, st>>>(s, b, a);
+        if (shared) k_e_colloc<T, 0, true, COMP><<<grid, block, 0, st>>>(s, b, a);
+        else k_e_colloc<T, 0, false, COMP><<<grid, block, 0, st>>>(s, b, a);
     }
 #undef MFD_H
 #undef MFD_E
@@ -335,35 +340,36 @@ static cudaError_t launch_colloc_pass(int pass, const StencilStreams<T>& s, cons
 
 template <typename T, bool COMP>
 static cudaError_t launch_stag_pass(int pass, const StencilStreams<T>& s, const Coefs<T>& k, const Stag2DPtrs& p,
-                                    cudaStream_t st) {
+                                    int block, cudaStream_t st) {
     using V2 = typename Vec<T>::V2;
-    const unsigned grid = (unsigned)((s.n + 255) / 256);
+    const unsigned grid = (unsigned)((s.n + block - 1) / block);
     const T* ez = static_cast<const T*>(p.ez);
     T* ezn = static_cast<T*>(p.ezn);
     const V2* h = static_cast<const V2*>(p.h);
     V2* hn = static_cast<V2*>(p.hn);
     const T* ce = static_cast<const T*>(p.ce);
     if (pass == 0) {
-        if (s.nc == 8 && s.nv == 15) k_h_stag<T, 8, 15, COMP><<<grid, 256, 0, st>>>(s, k, ez, h, hn);
-        else if (s.nc == 3 && s.nv == 8) k_h_stag<T, 3, 8, COMP><<<grid, 256, 0, st>>>(s, k, ez, h, hn);
-        else k_h_stag<T, 0, 0, COMP><<<grid, 256, 0, st>>>(s, k, ez, h, hn);
+        if (s.nc == 8 && s.nv == 15) k_h_stag<T, 8, 15, COMP><<<grid, block, 0, st>>>(s, k, ez, h, hn);
+        else if (s.nc == 3 && s.nv == 8) k_h_stag<T, 3, 8, COMP><<<grid, block, 0, st>>>(s, k, ez, h, hn);
+        else k_h_stag<T, 0, 0, COMP><<<grid, block, 0, st>>>(s, k, ez, h, hn);
     } else {
-        if (s.nc == 8 && s.nv == 15) k_e_stag<T, 8, 15, COMP><<<grid, 256, 0, st>>>(s, k, hn, ez, ce, ezn);
-        else if (s.nc == 3 && s.nv == 8) k_e_stag<T, 3, 8, COMP><<<grid, 256, 0, st>>>(s, k, hn, ez, ce, ezn);
-        else k_e_stag<T, 0, 0, COMP><<<grid, 256, 0, st>>>(s, k, hn, ez, ce, ezn);
+        if (s.nc == 8 && s.nv == 15) k_e_stag<T, 8, 15, COMP><<<grid, block, 0, st>>>(s, k, hn, ez, ce, ezn);
+        else if (s.nc == 3 && s.nv == 8) k_e_stag<T, 3, 8, COMP><<<grid, block, 0, st>>>(s, k, hn, ez, ce, ezn);
+        else k_e_stag<T, 0, 0, COMP><<<grid, block, 0, st>>>(s, k, hn, ez, ce, ezn);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_2d(const Launch2D& L, int pass, cudaStream_t st) {
+    const int b = L.block[pass];
     if (L.staggered) {
-        if (L.fp64) return launch_stag_pass<double, false>(pass, pass == 0 ? L.hs.d : L.es.d, L.kd, L.stag, st);
-        if (L.comp) return launch_stag_pass<float, true>(pass, pass == 0 ? L.hs.f : L.es.f, L.kf, L.stag, st);
-        return launch_stag_pass<float, false>(pass, pass == 0 ? L.hs.f : L.es.f, L.kf, L.stag, st);
+        if (L.fp64) return launch_stag_pass<double, false>(pass, pass == 0 ? L.hs.d : L.es.d, L.kd, L.stag, b, st);
+        if (L.comp) return launch_stag_pass<float, true>(pass, pass == 0 ? L.hs.f : L.es.f, L.kf, L.stag, b, st);
+        return launch_stag_pass<float, false>(pass, pass == 0 ? L.hs.f : L.es.f, L.kf, L.stag, b, st);
     }
-    if (L.fp64) return launch_colloc_pass<double, false>(pass, L.hs.d, L.kd, L.A, L.B, st);
-    if (L.comp) return launch_colloc_pass<float, true>(pass, L.hs.f, L.kf, L.A, L.B, st);
-    return launch_colloc_pass<float, false>(pass, L.hs.f, L.kf, L.A, L.B, st);
+    if (L.fp64) return launch_colloc_pass<double, false>(pass, L.hs.d, L.kd, L.A, L.B, b, st);
+    if (L.comp) return launch_colloc_pass<float, true>(pass, L.hs.f, L.kf, L.A, L.B, b, st);
+    return launch_colloc_pass<float, false>(pass, L.hs.f, L.kf, L.A, L.B, b, st);
 }
 
 cudaError_t launch_energy_2d(const Launch2D& L, const double* eps_r, int64_t ne, double eta2, double* partial,

@@ -23,7 +23,8 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
     const int nv = NV ? NV : s.nv;
     const int64_t slice = i >> 5;
     const int lane = (int)(i & 31);
-    Acc a_yz, a_zy, a_zx, a_xz, a_xy, a_yx, hx, hy, hz, ex, ey, ez;
+    Acc a_yz, a_zy, a_zx, a_xz, a_xy, a_yx;            // curl sums (compensated when COMP)
+    AccPlain<T> hx, hy, hz, ex, ey, ez;                 // hyperviscosity sums (scaled by gamma)
     const V4* px = s.wx + slice * nc * 32 + lane;
     const V4* py = s.wy + slice * nc * 32 + lane;
     const V4* pz = s.wz + slice * nc * 32 + lane;
@@ -117,7 +118,7 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
 }
 
 template <typename T, int NC, int NV, bool SHARED, bool COMP>
-__global__ void __launch_bounds__(256) k_h3(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V4* __restrict__ E,
+__global__ void __launch_bounds__(512) k_h3(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V4* __restrict__ E,
                                             typename Vec<T>::V4* __restrict__ Es,
                                             const typename Vec<T>::V4* __restrict__ H,
                                             typename Vec<T>::V4* __restrict__ Hn) {
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(256) k_h3(StencilStreams<T> s, Coefs<T> k, con
 }
 
 template <typename T, int NC, bool SHARED, bool COMP>
-__global__ void __launch_bounds__(256) k_e3(StencilStreams<T> s, const typename Vec<T>::V4* __restrict__ Hn,
+__global__ void __launch_bounds__(512) k_e3(StencilStreams<T> s, const typename Vec<T>::V4* __restrict__ Hn,
                                             const typename Vec<T>::V4* __restrict__ Es,
                                             const uint8_t* __restrict__ wall, typename Vec<T>::V4* __restrict__ E) {
     using V4 = typename Vec<T>::V4;
@@ -235,21 +236,22 @@ __global__ void __launch_bounds__(256) k_energy3(StencilStreams<T> s, Coefs<T> k
 template <typename T, bool COMP>
 static cudaError_t launch3(const Launch3D& L, const StencilStreams<T>& s, const Coefs<T>& k, int pass, cudaStream_t st) {
     using V4 = typename Vec<T>::V4;
-    const unsigned grid = (unsigned)((s.n + 255) / 256);
+    const int block = L.block[pass];
+    const unsigned grid = (unsigned)((s.n + block - 1) / block);
     const bool shared = s.idx_v == s.idx_c;
     const V4* E = static_cast<const V4*>(L.E);
     V4* Es = static_cast<V4*>(L.Es);
     const V4* H = static_cast<const V4*>(L.H);
     V4* Hn = static_cast<V4*>(L.Hn);
     if (pass == 0) {
-        if (shared && s.nc == 10 && s.nv == 18) k_h3<T, 10, 18, true, COMP><<<grid, 256, 0, st>>>(s, k, E, Es, H, Hn);
-        else if (shared) k_h3<T, 0, 0, true, COMP><<<grid, 256, 0, st>>>(s, k, E, Es, H, Hn);
-        else k_h3<T, 0, 0, false, COMP><<<grid, 256, 0, st>>>(s, k, E, Es, H, Hn);
+        if (shared && s.nc == 10 && s.nv == 18) k_h3<T, 10, 18, true, COMP><<<grid, block, 0, st>>>(s, k, E, Es, H, Hn);
+        else if (shared) k_h3<T, 0, 0, true, COMP><<<grid, block, 0, st>>>(s, k, E, Es, H, Hn);
+        else k_h3<T, 0, 0, false, COMP><<<grid, block, 0, st>>>(s, k, E, Es, H, Hn);
     } else {
         V4* Eo = const_cast<V4*>(E);
-        if (shared && s.nc == 10) k_e3<T, 10, true, COMP><<<grid, 256, 0, st>>>(s, Hn, Es, L.wall, Eo);
-        else if (shared) k_e3<T, 0, true, COMP><<<grid, 256, 0, st>>>(s, Hn, Es, L.wall, Eo);
-        else k_e3<T, 0, false, COMP><<<grid, 256, 0, st>>>(s, Hn, Es, L.wall, Eo);
+        if (shared && s.nc == 10) k_e3<T, 10, true, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, Eo);
+        else if (shared) k_e3<T, 0, true, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, Eo);
+        else k_e3<T, 0, false, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, Eo);
     }
     return cudaGetLastError();
 }

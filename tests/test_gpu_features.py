@@ -1,0 +1,108 @@
+"""GPU features around the step: the block-size autotuner, the energy watchdog,
+RBF-VFD curl weights in the step, and the FP64 FMA peak probe.
+
+* autotune restores the fields (the simulation does not advance) and any block
+  size gives bit-identical fields (one thread per node, same arithmetic);
+* the watchdog returns MFD_ERR_UNSTABLE for the unstabilised scheme on
+  scattered nodes (App. A) and stays silent with hyperviscosity;
+* a collocated step with RBF-VFD (delta = h/2) curl weights matches the oracle
+  (FP64 1e-10).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+M = pytest.importorskip("paper_2508_18205_gb300")
+
+
+def _colloc(ctx, nodes, gamma, prec=1, vfd=None, S=0.5):
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    nd = M.Nodes(ctx, nodes.xyz, nodes.period)
+    st = M.Stencils(nd, nd, 31)
+    if vfd is None:
+        cw = M.Weights(st, 12, 3, 2, M.MFD_OP_GRAD)
+    else:
+        cw = M.Weights(st, 12, 3, 2, M.MFD_OP_GRAD_VFD, 0, vfd)
+    hw = M.Weights(st, 31, 5, 4, M.MFD_OP_LAP_POW, 2)
+    return M.Sim(ctx, 2, prec, dt, eps0, mu0, gamma, cw, hw)
+
+
+def test_autotune_keeps_state_and_blocks_do_not_change_results():
+    ctx = M.Ctx(0)
+    dt, eps0, mu0, c0, eta0 = W.units(0.5)
+    e = W.periodic_box((40, 40), 0.25, 1)
+    h = W.periodic_box((40, 40), 0.25, 2, offset=(0.5, 0.5))
+    de, dh = M.Nodes(ctx, e.xyz, e.period), M.Nodes(ctx, h.xyz, h.period)
+    hc = M.Weights(M.Stencils(dh, de, 30), 30, 5, 4, M.MFD_OP_GRAD)
+    hv = M.Weights(M.Stencils(dh, dh, 57), 57, 7, 6, M.MFD_OP_LAP_POW, 3)
+    ec = M.Weights(M.Stencils(de, dh, 30), 30, 5, 4, M.MFD_OP_GRAD)
+    ev = M.Weights(M.Stencils(de, de, 57), 57, 7, 6, M.MFD_OP_LAP_POW, 3)
+    rng = np.random.default_rng(3)
+    f = [rng.standard_normal(e.n), rng.standard_normal(h.n), rng.standard_normal(h.n)]
+    outs = []
+    for blocks in ("tune", (128, 512), (512, 64)):
+        sim = M.Sim(ctx, 2, 0, dt, eps0, mu0, 4e-5, hc, hv, ec, ev, compensated=True)
+        for c, v in zip((M.MFD_EZ, M.MFD_HX, M.MFD_HY), f):
+            sim.set_field(c, v)
+        if blocks == "tune":
+            ch = sim.autotune(5)
+            assert all(b in (128, 256, 512) for b in ch)
+            assert sim.steps == 0
+            assert np.array_equal(sim.get_field(M.MFD_EZ), f[0].astype(np.float32).astype(np.float64))
+        else:
+            sim.set_blocks(*blocks)
+        sim.step(70)
+        outs.append([sim.get_field(c) for c in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)])
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
+
+
+def test_watchdog_flags_the_unstabilised_scheme():
+    ctx = M.Ctx(0)
+    S = 1.0 / (10.0 * np.sqrt(2.0))
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    nodes = W.periodic_box((30, 30), 0.25, 4)
+    ez, hx, hy = W.gaussian_pulse(nodes.xyz, 30, 15, 4.0, c0, eta0, dt)
+    for gamma, expect_unstable in ((0.0, True), (-3e-3, False)):
+        sim = _colloc(ctx, nodes, gamma, prec=1, S=S)
+        sim.set_field(M.MFD_EZ, ez)
+        sim.set_field(M.MFD_HX, hx)
+        sim.set_field(M.MFD_HY, hy)
+        sim.set_watchdog(100, 1.5)
+        if expect_unstable:
+            with pytest.raises(M.MfdError) as ex:
+                sim.step(6000)
+            assert ex.value.status == M.MFD_ERR_UNSTABLE
+            assert 0 < sim.steps < 6000
+        else:
+            sim.step(3000)
+            assert sim.steps == 3000
+
+
+def test_vfd_curl_weights_step_matches_oracle():
+    ctx = M.Ctx(0)
+    dt, eps0, mu0, c0, eta0 = W.units(0.5)
+    nodes = W.pec_box((31, 27), 0.25, 6)
+    sim = _colloc(ctx, nodes, -4e-3, prec=1, vfd=0.5)
+    sim.set_materials(None, nodes.pec)
+    ez, hx, hy = W.tm11_fields(nodes.xyz, 30.0, c0, mu0, 0.0, -0.5 * dt)
+    ez[nodes.pec == 1] = 0
+    sim.set_field(M.MFD_EZ, ez)
+    sim.set_field(M.MFD_HX, hx)
+    sim.set_field(M.MFD_HY, hy)
+    sim.step(100)
+    prob, _ = O.tmz_collocated(nodes, 12, 3, 2, 2, dt, eps0, mu0, -4e-3, vfd_delta=0.5)
+    re, rx, ry, _, _ = O.run_tmz(prob, ez, hx, hy, 100)
+    got = np.concatenate([sim.get_field(c) for c in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)])
+    ref = np.concatenate([re, rx, ry])
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_fma_peak_probe_is_sane():
+    g64, g32 = M.fma_peak(0)
+    assert 100.0 < g64 < 1e5 and 1e3 < g32 < 1e6 and g32 > g64
