@@ -16,8 +16,10 @@
  *    message of the last error on the calling thread is mfd_last_error().
  *    No exception and no abort crosses this boundary.
  *  - Host pointers are read or written only during the call (the library
- *    copies what it keeps). Device memory is owned by the library: every
- *    object is released by its *_destroy function.
+ *    copies what it keeps). Device memory is owned by the library.
+ *  - Objects are reference counted: *_destroy drops the caller's reference,
+ *    and every object keeps the objects it was created from (context, node
+ *    sets, stencils, weights) alive, so handles may be destroyed in any order.
  *  - Node ids at this boundary are always in the caller's order. Internally
  *    the library reorders every node set along a Morton curve.
  *  - Work is queued on the context's CUDA stream; calls that return host data

@@ -16,6 +16,59 @@ mfd_status fail(mfd_status st, const std::string& msg) {
     return st;
 }
 
+void retain(const mfd_ctx* c) {
+    if (c) const_cast<mfd_ctx*>(c)->refs.fetch_add(1);
+}
+void retain(const mfd_nodes* n) {
+    if (n) const_cast<mfd_nodes*>(n)->refs.fetch_add(1);
+}
+void retain(const mfd_stencils* s) {
+    if (s) const_cast<mfd_stencils*>(s)->refs.fetch_add(1);
+}
+void retain(const mfd_weights* w) {
+    if (w) const_cast<mfd_weights*>(w)->refs.fetch_add(1);
+}
+
+void release(const mfd_ctx* cc) {
+    mfd_ctx* ctx = const_cast<mfd_ctx*>(cc);
+    if (!ctx || ctx->refs.fetch_sub(1) != 1) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->own_stream && ctx->stream) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaStreamDestroy(ctx->stream);
+    }
+    delete ctx;
+}
+
+void release(const mfd_nodes* cn) {
+    mfd_nodes* n = const_cast<mfd_nodes*>(cn);
+    if (!n || n->refs.fetch_sub(1) != 1) return;
+    mfd_ctx* ctx = n->ctx;
+    cudaSetDevice(ctx->device);
+    delete n;
+    release(ctx);
+}
+
+void release(const mfd_stencils* cs) {
+    mfd_stencils* s = const_cast<mfd_stencils*>(cs);
+    if (!s || s->refs.fetch_sub(1) != 1) return;
+    const mfd_nodes* c = s->centres;
+    const mfd_nodes* src = s->sources;
+    cudaSetDevice(c->ctx->device);
+    delete s;
+    release(c);
+    release(src);
+}
+
+void release(const mfd_weights* cw) {
+    mfd_weights* w = const_cast<mfd_weights*>(cw);
+    if (!w || w->refs.fetch_sub(1) != 1) return;
+    const mfd_stencils* st = w->st;
+    cudaSetDevice(st->centres->ctx->device);
+    delete w;
+    release(st);
+}
+
 static mfd_status use_device(const mfd_ctx* ctx) {
     MFD_CUDA(cudaSetDevice(ctx->device));
     return MFD_OK;
@@ -85,15 +138,7 @@ mfd_status mfd_ctx_sync(mfd_ctx* ctx) {
     return MFD_OK;
 }
 
-void mfd_ctx_destroy(mfd_ctx* ctx) {
-    if (!ctx) return;
-    cudaSetDevice(ctx->device);
-    if (ctx->own_stream && ctx->stream) {
-        cudaStreamSynchronize(ctx->stream);
-        cudaStreamDestroy(ctx->stream);
-    }
-    delete ctx;
-}
+void mfd_ctx_destroy(mfd_ctx* ctx) { release(ctx); }
 
 mfd_status mfd_nodes_create(mfd_ctx* ctx, int dim, int64_t n, const double* xyz, const double* period,
                             mfd_nodes** out) {
@@ -140,6 +185,7 @@ mfd_status mfd_nodes_create(mfd_ctx* ctx, int dim, int64_t n, const double* xyz,
         delete nd;
         return fail(MFD_ERR_CUDA, cudaGetErrorString(e));
     }
+    retain(ctx);
     *out = nd;
     return MFD_OK;
 }
@@ -152,11 +198,7 @@ mfd_status mfd_nodes_permutation(const mfd_nodes* nodes, int64_t* perm) {
     return MFD_OK;
 }
 
-void mfd_nodes_destroy(mfd_nodes* nodes) {
-    if (!nodes) return;
-    cudaSetDevice(nodes->ctx->device);
-    delete nodes;
-}
+void mfd_nodes_destroy(mfd_nodes* nodes) { release(nodes); }
 
 mfd_status mfd_stencils_build(const mfd_nodes* centres, const mfd_nodes* sources, int n, mfd_stencils** out) {
     if (!centres || !sources || !out) return fail(MFD_ERR_ARG, "NULL argument");
@@ -178,6 +220,8 @@ mfd_status mfd_stencils_build(const mfd_nodes* centres, const mfd_nodes* sources
         delete s;
         return st;
     }
+    retain(centres);
+    retain(sources);
     *out = s;
     return MFD_OK;
 }
@@ -198,11 +242,7 @@ mfd_status mfd_stencils_read(const mfd_stencils* st, int64_t* idx) {
     return MFD_OK;
 }
 
-void mfd_stencils_destroy(mfd_stencils* st) {
-    if (!st) return;
-    cudaSetDevice(st->centres->ctx->device);
-    delete st;
-}
+void mfd_stencils_destroy(mfd_stencils* st) { release(st); }
 
 mfd_status mfd_weights_compute(const mfd_stencils* st, int n_use, int phs_k, int poly_m, int op, int alpha,
                                double delta, mfd_weights** out) {
@@ -232,6 +272,7 @@ mfd_status mfd_weights_compute(const mfd_stencils* st, int n_use, int phs_k, int
         delete w;
         return s;
     }
+    retain(st);
     *out = w;
     return MFD_OK;
 }
@@ -251,10 +292,6 @@ mfd_status mfd_weights_read(const mfd_weights* w, double* host_w) {
     return MFD_OK;
 }
 
-void mfd_weights_destroy(mfd_weights* w) {
-    if (!w) return;
-    cudaSetDevice(w->st->centres->ctx->device);
-    delete w;
-}
+void mfd_weights_destroy(mfd_weights* w) { release(w); }
 
 }  // extern "C"

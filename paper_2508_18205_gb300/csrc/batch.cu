@@ -356,6 +356,7 @@ struct BatchDomain {
 
 struct mfd_batch {
     mfd_ctx* ctx = nullptr;
+    std::vector<const mfd_weights*> held;  // one reference on every domain's weights
     int R = 16;
     int ndom = 0;
     int64_t ntot = 0;
@@ -629,6 +630,13 @@ mfd_status mfd_batch_create(mfd_ctx* ctx, int ndom, const mfd_sim_desc* descs, i
     if ((st = build_tables(b))) return bail(st);
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return bail(fail(MFD_ERR_CUDA, cudaGetErrorString(e)));
+    retain(ctx);
+    for (int d = 0; d < ndom; ++d) {
+        retain(descs[d].h_curl);
+        retain(descs[d].h_hv);
+        b->held.push_back(descs[d].h_curl);
+        b->held.push_back(descs[d].h_hv);
+    }
     *out = b;
     return MFD_OK;
 }
@@ -823,9 +831,13 @@ int mfd_batch_uses_graph(const mfd_batch* b) { return b && b->use_graph ? 1 : 0;
 
 void mfd_batch_destroy(mfd_batch* b) {
     if (!b) return;
-    cudaSetDevice(b->ctx->device);
-    cudaStreamSynchronize(b->ctx->stream);
+    mfd_ctx* ctx = b->ctx;
+    std::vector<const mfd_weights*> held = b->held;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
     delete b;
+    for (const mfd_weights* w : held) release(w);
+    release(ctx);
 }
 
 }  // extern "C"

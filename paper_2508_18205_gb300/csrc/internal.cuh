@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -62,7 +63,12 @@ struct DevBuf {
 
 // ------------------------------------------------------------ objects
 
+// Every object is reference counted: the creator's reference is dropped by its
+// *_destroy call, and each object holds one reference on every object it was
+// created from, so a context, node set, stencil set or weight set lives as long
+// as anything built on it (destruction order does not matter).
 struct mfd_ctx {
+    std::atomic<int> refs{1};
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -71,6 +77,7 @@ struct mfd_ctx {
 };
 
 struct mfd_nodes {
+    std::atomic<int> refs{1};
     mfd_ctx* ctx = nullptr;
     int dim = 2;
     int64_t n = 0;
@@ -83,6 +90,7 @@ struct mfd_nodes {
 };
 
 struct mfd_stencils {
+    std::atomic<int> refs{1};
     const mfd_nodes* centres = nullptr;
     const mfd_nodes* sources = nullptr;
     int n = 0;
@@ -90,6 +98,7 @@ struct mfd_stencils {
 };
 
 struct mfd_weights {
+    std::atomic<int> refs{1};
     const mfd_stencils* st = nullptr;
     int n_use = 0;
     int nout = 0;
@@ -100,6 +109,16 @@ struct mfd_weights {
 };
 
 namespace mfd {
+
+// reference counting (see above); release frees the object when the count drops to 0
+void retain(const mfd_ctx* c);
+void retain(const mfd_nodes* n);
+void retain(const mfd_stencils* s);
+void retain(const mfd_weights* w);
+void release(const mfd_ctx* c);
+void release(const mfd_nodes* n);
+void release(const mfd_stencils* s);
+void release(const mfd_weights* w);
 
 // ------------------------------------------------------------ setup kernels
 

@@ -490,6 +490,11 @@ mfd_status mfd_sim_create(mfd_ctx* ctx, const mfd_sim_desc* desc, mfd_sim** out)
         delete sim;
         return fail(MFD_ERR_CUDA, cudaGetErrorString(e));
     }
+    retain(ctx);
+    retain(desc->h_curl);
+    retain(desc->h_hv);
+    retain(desc->e_curl);
+    retain(desc->e_hv);
     return MFD_OK;
 }
 
@@ -993,9 +998,13 @@ mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, doub
 
 void mfd_sim_destroy(mfd_sim* sim) {
     if (!sim) return;
-    cudaSetDevice(sim->ctx->device);
-    cudaStreamSynchronize(sim->ctx->stream);
+    mfd_ctx* ctx = sim->ctx;
+    const mfd_weights* w[4] = {sim->d.h_curl, sim->d.h_hv, sim->d.e_curl, sim->d.e_hv};
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
     delete sim;
+    for (const mfd_weights* x : w) release(x);
+    release(ctx);
 }
 
 }  // extern "C"

@@ -106,3 +106,29 @@ def test_vfd_curl_weights_step_matches_oracle():
 def test_fma_peak_probe_is_sane():
     g64, g32 = M.fma_peak(0)
     assert 100.0 < g64 < 1e5 and 1e3 < g32 < 1e6 and g32 > g64
+
+
+def test_handles_may_be_destroyed_in_any_order():
+    """Objects are reference counted: dropping the context, node set, stencils and
+    weights handles before the simulation leaves the simulation usable."""
+    ctx = M.Ctx(0)
+    dt, eps0, mu0, c0, eta0 = W.units(0.5)
+    nodes = W.pec_box((20, 20), 0.25, 8)
+    nd = M.Nodes(ctx, nodes.xyz, nodes.period)
+    st = M.Stencils(nd, nd, 31)
+    cw = M.Weights(st, 12, 3, 2, M.MFD_OP_GRAD)
+    hw = M.Weights(st, 31, 5, 4, M.MFD_OP_LAP_POW, 2)
+    sim = M.Sim(ctx, 2, 1, dt, eps0, mu0, -4e-3, cw, hw)
+    L = M.lib()
+    for obj, fn in ((ctx, L.mfd_ctx_destroy), (nd, L.mfd_nodes_destroy), (st, L.mfd_stencils_destroy),
+                    (cw, L.mfd_weights_destroy), (hw, L.mfd_weights_destroy)):
+        fn(obj.h)
+        obj.h = None
+    ez, hx, hy = W.tm11_fields(nodes.xyz, 19.0, c0, mu0, 0.0, -0.5 * dt)
+    sim.set_field(M.MFD_EZ, ez)
+    sim.set_field(M.MFD_HX, hx)
+    sim.set_field(M.MFD_HY, hy)
+    sim.step(40)
+    assert np.all(np.isfinite(sim.get_field(M.MFD_EZ)))
+    L.mfd_sim_destroy(sim.h)
+    sim.h = None
