@@ -51,6 +51,10 @@ def _args():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 step and the accuracy runs")
     ap.add_argument("--cube-steps", type=int, default=200,
                     help="steps of the 3D 200^3 workload (0: skip)")
+    ap.add_argument("--cube-nx", type=int, default=200, help="nodes per side of the 3D cube")
+    ap.add_argument("--batched-ndom", type=int, default=256, help="domains of the batched workload")
+    ap.add_argument("--only", default="all", choices=["all", "batched", "cube3d"],
+                    help="run one section alone (profiling); prints that section as the JSON line")
     ap.add_argument("--batched-steps", type=int, default=3000,
                     help="steps of the batched 256-domain x 16-RHS workload (0: skip)")
     return ap.parse_args()
@@ -278,6 +282,15 @@ def main():
     from paper_2508_18205_gb300 import build as B
     B.build()
     torch.cuda.set_device(local)
+    if a.only != "all":
+        ctx = M.Ctx(local)
+        peak, peak_kind = peaks()
+        if a.only == "batched":
+            r = batched(M, ctx, a.batched_steps, peak, peak_kind, ndom=a.batched_ndom)
+        else:
+            r = cube3d(M, ctx, a.cube_steps, peak, peak_kind, nx=a.cube_nx)
+        print(json.dumps(r), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -118,7 +118,7 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
 }
 
 template <typename T, int NC, int NV, bool SHARED, bool COMP>
-__global__ void __launch_bounds__(512) k_h3(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V4* __restrict__ E,
+__global__ void __launch_bounds__(512, 2) k_h3(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V4* __restrict__ E,
                                             typename Vec<T>::V4* __restrict__ Es,
                                             const typename Vec<T>::V4* __restrict__ H,
                                             typename Vec<T>::V4* __restrict__ Hn) {
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(512) k_h3(StencilStreams<T> s, Coefs<T> k, con
 }
 
 template <typename T, int NC, bool SHARED, bool COMP>
-__global__ void __launch_bounds__(512) k_e3(StencilStreams<T> s, const typename Vec<T>::V4* __restrict__ Hn,
+__global__ void __launch_bounds__(512, 2) k_e3(StencilStreams<T> s, const typename Vec<T>::V4* __restrict__ Hn,
                                             const typename Vec<T>::V4* __restrict__ Es,
                                             const uint8_t* __restrict__ wall, typename Vec<T>::V4* __restrict__ E) {
     using V4 = typename Vec<T>::V4;
