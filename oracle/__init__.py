@@ -398,3 +398,41 @@ def tmz_sample_step(e_nodes, h_nodes, e_ids, n, phs_k, m, alpha, dt, eps0, mu0, 
                                      C.c_double(gamma), _p(ez), _p(hx), _p(hy), _p(hx1), _p(hy1),
                                      _p(ez1)), "tmz_sample_step")
     return ez1, hx1, hy1, hs
+
+
+def max3d_sample_step(nodes, e_ids, n, phs_k, m, alpha, dt, eps0, mu0, gamma, E, H, eps_r=None, h_ids=()):
+    """One 3D collocated step evaluated at the nodes e_ids (E') and at the H nodes
+    they depend on plus h_ids (H'), with the oracle's own stencils and weights
+    for exactly those centres. Returns (E1 (3 x len(e_ids)), H1 (3 x nhs), H subset ids)."""
+    import math
+    nhv = 2 * math.comb(2 * alpha + 3, 3) + 1
+    L = max(n, nhv)
+    per = nodes.period
+    e_ids = _i64(e_ids)
+    ie = knn_cells(nodes.xyz[e_ids], nodes.xyz, per, L)
+    hs = np.unique(np.concatenate([ie[:, :n].reshape(-1), _i64(h_ids)]))
+    ih = knn_cells(nodes.xyz[hs], nodes.xyz, per, L)
+
+    def w(xc, idx):
+        c = weights(xc, nodes.xyz, per, idx, n, phs_k, m, OP_GRAD)
+        v = weights(xc, nodes.xyz, per, idx, nhv, 2 * alpha + 1, 2 * alpha, OP_LAP_POW, alpha)
+        return c, v
+
+    hc, hv = w(nodes.xyz[hs], ih)
+    ec, ev = w(nodes.xyz[e_ids], ie)
+    hpos = np.full(nodes.n, -1, dtype=np.int64)
+    hpos[hs] = np.arange(len(hs))
+    arr = [np.ascontiguousarray(a) for a in (ih[:, :n], hc[0], hc[1], hc[2], ih[:, :nhv], hv[0],
+                                             ie[:, :n], ec[0], ec[1], ec[2], ie[:, :nhv], ev[0])]
+    er = None if eps_r is None else _f64(np.asarray(eps_r)[e_ids])
+    wall = np.ascontiguousarray(nodes.normal_axes[e_ids], dtype=np.uint8)
+    E, H = _f64(E), _f64(H)
+    H1 = np.empty((3, len(hs)))
+    E1 = np.empty((3, len(e_ids)))
+    _check(lib().orc_3d_sample_step(C.c_int64(len(hs)), _p(hs), C.c_int(n), _p(arr[0]), _p(arr[1]), _p(arr[2]),
+                                    _p(arr[3]), C.c_int(nhv), _p(arr[4]), _p(arr[5]), C.c_int64(len(e_ids)),
+                                    _p(e_ids), _p(arr[6]), _p(arr[7]), _p(arr[8]), _p(arr[9]), _p(arr[10]),
+                                    _p(arr[11]), _p(hpos), _p(er), _p(wall), C.c_int64(nodes.n),
+                                    C.c_double(dt), C.c_double(eps0), C.c_double(mu0), C.c_double(gamma),
+                                    _p(E), _p(H), _p(H1), _p(E1)), "3d_sample_step")
+    return E1, H1, hs

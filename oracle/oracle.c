@@ -863,3 +863,57 @@ int orc_tmz_sample_step(int64_t nhs, const int64_t* hs_ids, int nhc, const int64
     }
     return ORC_OK;
 }
+
+/*
+ * One 3D step (the collocated full-vector form of Eq. 19) evaluated only at
+ * chosen nodes. E, H: 3 x N state. H subset: nhs node ids with curl and HV
+ * stencils (hs_*); E subset: nes node ids with their stencils (es_*), whose
+ * curl entries must lie in the H subset (hpos maps node -> subset position).
+ * Outputs H' at the H subset (H1: 3 x nhs) and E' at the E subset (E1: 3 x
+ * nes, tangential components zeroed per wall mask), without sources.
+ */
+int orc_3d_sample_step(int64_t nhs, const int64_t* hs_ids, int nc, const int64_t* hc_idx, const double* hwx,
+                       const double* hwy, const double* hwz, int nv, const int64_t* hv_idx, const double* hwv,
+                       int64_t nes, const int64_t* es_ids, const int64_t* ec_idx, const double* ewx,
+                       const double* ewy, const double* ewz, const int64_t* ev_idx, const double* ewv,
+                       const int64_t* hpos, const double* eps_r_es, const uint8_t* wall_es, int64_t N,
+                       double dt, double eps0, double mu0, double gamma, const double* E, const double* H,
+                       double* H1, double* E1)
+{
+    const double ch = dt / mu0;
+    const double* Ex = E; const double* Ey = E + N; const double* Ez = E + 2 * N;
+    for (int64_t k = 0; k < nhs; ++k) {
+        int64_t i = hs_ids[k];
+        const int64_t* ci = hc_idx + k * nc;
+        double dyEz = orc_apply(nc, ci, hwy + k * nc, Ez), dzEy = orc_apply(nc, ci, hwz + k * nc, Ey);
+        double dzEx = orc_apply(nc, ci, hwz + k * nc, Ex), dxEz = orc_apply(nc, ci, hwx + k * nc, Ez);
+        double dxEy = orc_apply(nc, ci, hwx + k * nc, Ey), dyEx = orc_apply(nc, ci, hwy + k * nc, Ex);
+        double c[3] = {dyEz - dzEy, dzEx - dxEz, dxEy - dyEx};
+        for (int a = 0; a < 3; ++a) {
+            double vh = orc_apply(nv, hv_idx + k * nv, hwv + k * nv, H + a * N);
+            H1[a * nhs + k] = H[a * N + i] + ch * (-c[a] + gamma * vh);
+        }
+    }
+    for (int64_t k = 0; k < nes; ++k) {
+        int64_t i = es_ids[k];
+        double d[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  /* d[axis][component] of H' */
+        for (int j = 0; j < nc; ++j) {
+            int64_t p = hpos[ec_idx[k * nc + j]];
+            if (p < 0) return ORC_ERR_ARG;
+            const double w[3] = {ewx[k * nc + j], ewy[k * nc + j], ewz[k * nc + j]};
+            for (int ax = 0; ax < 3; ++ax)
+                for (int cmp = 0; cmp < 3; ++cmp) d[ax][cmp] += w[ax] * H1[cmp * nhs + p];
+        }
+        double c[3] = {d[1][2] - d[2][1], d[2][0] - d[0][2], d[0][1] - d[1][0]};
+        double er = eps_r_es ? eps_r_es[k] : 1.0;
+        for (int a = 0; a < 3; ++a) {
+            double ve = orc_apply(nv, ev_idx + k * nv, ewv + k * nv, E + a * N);
+            E1[a * nes + k] = E[a * N + i] + dt / (eps0 * er) * (c[a] + gamma * ve);
+        }
+        unsigned m = wall_es ? wall_es[k] : 0u;
+        for (int b = 0; b < 3; ++b)
+            for (int a = 0; a < 3; ++a)
+                if (((m >> a) & 1u) && a != b) E1[b * nes + k] = 0.0;
+    }
+    return ORC_OK;
+}

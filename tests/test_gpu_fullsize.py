@@ -78,3 +78,81 @@ def test_fullsize_one_step_sampled(setup, prec, tol):
     ref = np.concatenate([ez1, hx1, hy1])
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert err <= tol, err
+
+
+def test_cube3d_8M_one_step_sampled():
+    """The 3D workload at its full size (200^3 = 8M nodes, n = 40, N_h = 71, eps_r
+    field): one step from the GPU state after 12 steps, sampled where the fields
+    live, against the oracle's sampled 3D step (FP32 1e-6, FP64 1e-12)."""
+    import math
+    ctx = M.Ctx(0)
+    S, c, n, k, m, alpha = 0.5, 1e-3, 40, 3, 3, 2
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    nx = 200
+    nodes = W.periodic_box((nx, nx, nx), 0.25, 3)
+    er = W.eps_r_smooth_3d(nodes.xyz, nodes.box_hi, 33)
+    nd = M.Nodes(ctx, nodes.xyz, nodes.period)
+    nhv = 2 * math.comb(2 * alpha + 3, 3) + 1
+    st = M.Stencils(nd, nd, max(n, nhv))
+    cw = M.Weights(st, n, k, m, M.MFD_OP_GRAD)
+    hw = M.Weights(st, nhv, 2 * alpha + 1, 2 * alpha, M.MFD_OP_LAP_POW, alpha)
+    (ex, ey, ez), (hx, hy, hz) = W.tm110_fields_3d(nodes.xyz, nx / 2, c0, mu0, 0.0, -0.5 * dt)
+    rng = np.random.default_rng(12)
+    ids = np.sort(rng.choice(nodes.n, 24, replace=False))
+    for prec, tol in ((0, 1e-6), (1, 1e-12)):
+        sim = M.Sim(ctx, 3, prec, dt, eps0, mu0, -c, cw, hw, compensated=True)
+        sim.set_materials(er, None)
+        for comp, v in zip(range(6), (ex, ey, ez, hx, hy, hz)):
+            sim.set_field(comp, v)
+        sim.step(12)
+        E0 = np.stack([sim.get_field(a) for a in range(3)])
+        H0 = np.stack([sim.get_field(3 + a) for a in range(3)])
+        sim.step(1)
+        E1 = np.stack([sim.get_field(a)[ids] for a in range(3)])
+        RE, RH, hs = O.max3d_sample_step(nodes, ids, n, k, m, alpha, dt, eps0, mu0, -c, E0, H0, eps_r=er)
+        H1 = np.stack([sim.get_field(3 + a)[hs] for a in range(3)])
+        got = np.concatenate([E1.reshape(-1), H1.reshape(-1)])
+        ref = np.concatenate([RE.reshape(-1), RH.reshape(-1)])
+        assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref), (prec, np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        del sim
+
+
+def test_batched_256_domains_sampled_domains():
+    """The batched workload at full size (256 domains, 4.3M nodes, 16 RHS): three
+    whole domains (every right-hand side) after 120 steps against single-RHS
+    oracle runs (1e-5, FP32)."""
+    ctx = M.Ctx(0)
+    S, c = 0.5, 4e-3
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    specs = W.batch_domains(256, 4)
+    doms, keep = [], []
+    for ns, n in specs:
+        nd = M.Nodes(ctx, ns.xyz, ns.period)
+        st = M.Stencils(nd, nd, max(n, 31))
+        cw = M.Weights(st, n, 3, W.poly_degree_for(n), M.MFD_OP_GRAD)
+        hw = M.Weights(st, 31, 5, 4, M.MFD_OP_LAP_POW, 2)
+        doms.append((cw, hw, dt, eps0, mu0, -c))
+        keep.append((nd, st))
+    bt = M.Batch(ctx, doms, nrhs=16)
+    srcs = []
+    for d, (ns, n) in enumerate(specs):
+        bt.set_materials(d, None, ns.pec)
+        src = W.ricker_sources(ns, 16, 500 + d, c0, nrhs=16, one_per_rhs=True)
+        bt.set_sources(d, src.node, src.rhs, src.amp, src.f0, src.t0)
+        srcs.append(src)
+    nsteps = 120
+    bt.step(nsteps)
+    sizes = np.array([ns.n for ns, _ in specs])
+    pick = list(np.argsort(sizes)[:2]) + [int(np.argsort(sizes)[len(sizes) // 2])]
+    for d in pick:
+        ns, n = specs[d]
+        prob, _ = O.tmz_collocated(ns, n, 3, W.poly_degree_for(n), 2, dt, eps0, mu0, -c)
+        got = bt.get_field(int(d), M.MFD_EZ)
+        ref = np.zeros((ns.n, 16))
+        z = np.zeros(ns.n)
+        for r in range(16):
+            sel = srcs[d].rhs == r
+            sub = W.Sources(node=srcs[d].node[sel], rhs=srcs[d].rhs[sel], amp=srcs[d].amp[sel],
+                            f0=srcs[d].f0[sel], t0=srcs[d].t0[sel])
+            ref[:, r] = O.run_tmz(prob, z, z, z, nsteps, sources=sub)[0]
+        assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), d

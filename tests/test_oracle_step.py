@@ -344,3 +344,20 @@ def test_3d_energy_of_constant_fields():
     _, _, _, en = O.run_3d(prob, E, H, 1, energy=True)
     ref = np.sum(er) * (0.09 + 0.04 + 0.25) + (mu0 / eps0) * nodes.n * (0.01 + 0.16 + 0.49)
     assert abs(en[0] - ref) <= 1e-9 * ref
+
+
+def test_3d_sampled_step_equals_full_step():
+    """The oracle's sampled 3D step equals its full 3D step on every sampled node (PEC walls included)."""
+    S = 0.4
+    dt, eps0, mu0, c0, eta0 = _units(S)
+    nodes = W.pec_box((7, 8, 7), 0.25, 83)
+    er = W.eps_r_uniform(nodes.n, 84)
+    prob, _ = O.max3d_collocated(nodes, 40, 3, 3, 2, dt, eps0, mu0, -1e-3, eps_r=er)
+    rng = np.random.default_rng(10)
+    E = rng.standard_normal((3, nodes.n))
+    H = rng.standard_normal((3, nodes.n))
+    E1f, H1f, _, _ = O.run_3d(prob, E, H, 1)
+    ids = np.sort(rng.choice(nodes.n, 25, replace=False))
+    E1, H1, hs = O.max3d_sample_step(nodes, ids, 40, 3, 3, 2, dt, eps0, mu0, -1e-3, E, H, eps_r=er)
+    assert np.allclose(E1, E1f[:, ids], rtol=0, atol=1e-12)
+    assert np.allclose(H1, H1f[:, hs], rtol=0, atol=1e-12)
