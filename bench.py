@@ -543,7 +543,7 @@ def cube3d(M, ctx, steps, peak, peak_kind, nx=200):
             "value": nodes.n * 6 * steps / el, "unit": UNIT, "steps": steps, "ms_per_step": el / steps * 1e3,
             "setup_s": {"generate": round(gen_s, 2), "morton_knn": round(t_knn, 2), "weights_fp64": round(t_w, 2)},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "traffic": None, "kernel": dom, "peak_kind": peak_kind,
+                         "traffic": traffic_record(dom, s4), "kernel": dom, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": dom_b, "avg_launch_ms": dom_t * 1e3,
                          "other_kernel_avg_launch_ms": min(h_avg, e_avg) * 1e3,
                          "step_achieved_gbs": (bh + be) * nodes.n / (el / steps) / 1e9}}

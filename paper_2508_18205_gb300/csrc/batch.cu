@@ -136,14 +136,21 @@ __device__ void h_tile(const BArgs& a, const BTile t) {
     const float4* py = a.wy + d.wc0 + slice * d.nc * NPW + g;
     const float4* pv = a.wv + d.wv0 + slice * d.nv * NPW + g;
     float4 dx = {0, 0, 0, 0}, dy = dx, vx = dx, vy = dx, ve = dx;
+    // the stream values of chunk c + 1 are requested before the gathers of
+    // chunk c, so the DRAM latency of the streams overlaps the gathers
+    const float4 z4 = {0, 0, 0, 0};
+    int4 nid = ld_stream(ip);
+    float4 nwx = d.nc > 0 ? ld_stream(px) : z4, nwy = d.nc > 0 ? ld_stream(py) : z4;
+    float4 nwv = d.nv > 0 ? ld_stream(pv) : z4;
     for (int c = 0; c < d.ni; ++c) {
-        const int4 id = ld_stream(ip + c * NPW);
-        float4 wx = {0, 0, 0, 0}, wy = wx, wv = wx;
-        if (c < d.nc) {
-            wx = ld_stream(px + c * NPW);
-            wy = ld_stream(py + c * NPW);
+        const int4 id = nid;
+        const float4 wx = nwx, wy = nwy, wv = nwv;
+        if (c + 1 < d.ni) {
+            nid = ld_stream(ip + (c + 1) * NPW);
+            nwx = c + 1 < d.nc ? ld_stream(px + (c + 1) * NPW) : z4;
+            nwy = c + 1 < d.nc ? ld_stream(py + (c + 1) * NPW) : z4;
+            nwv = c + 1 < d.nv ? ld_stream(pv + (c + 1) * NPW) : z4;
         }
-        if (c < d.nv) wv = ld_stream(pv + c * NPW);
         const int ids[4] = {id.x, id.y, id.z, id.w};
         const float wxs[4] = {wx.x, wx.y, wx.z, wx.w}, wys[4] = {wy.x, wy.y, wy.z, wy.w};
         const float wvs[4] = {wv.x, wv.y, wv.z, wv.w};
@@ -195,9 +202,16 @@ __device__ void e_tile(const BArgs& a, const BTile t) {
         const float4* px = a.wx + d.wc0 + slice * d.nc * NPW + g;
         const float4* py = a.wy + d.wc0 + slice * d.nc * NPW + g;
         float4 dxhy = {0, 0, 0, 0}, dyhx = dxhy;
+        int4 nid = ld_stream(ip);
+        float4 nwx = ld_stream(px), nwy = ld_stream(py);
         for (int c = 0; c < d.nc; ++c) {
-            const int4 id = ld_stream(ip + c * NPW);
-            const float4 wx = ld_stream(px + c * NPW), wy = ld_stream(py + c * NPW);
+            const int4 id = nid;
+            const float4 wx = nwx, wy = nwy;
+            if (c + 1 < d.nc) {
+                nid = ld_stream(ip + (c + 1) * NPW);
+                nwx = ld_stream(px + (c + 1) * NPW);
+                nwy = ld_stream(py + (c + 1) * NPW);
+            }
             const int ids[4] = {id.x, id.y, id.z, id.w};
             const float wxs[4] = {wx.x, wx.y, wx.z, wx.w}, wys[4] = {wy.x, wy.y, wy.z, wy.w};
 #pragma unroll
