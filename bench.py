@@ -53,7 +53,8 @@ def _args():
                     help="steps of the 3D 200^3 workload (0: skip)")
     ap.add_argument("--cube-nx", type=int, default=200, help="nodes per side of the 3D cube")
     ap.add_argument("--batched-ndom", type=int, default=256, help="domains of the batched workload")
-    ap.add_argument("--only", default="all", choices=["all", "batched", "cube3d"],
+    ap.add_argument("--no-extra", action="store_true", help="skip the cavity (FP64) and adjoint sections")
+    ap.add_argument("--only", default="all", choices=["all", "batched", "cube3d", "cavity", "adjoint"],
                     help="run one section alone (profiling); prints that section as the JSON line")
     ap.add_argument("--batched-steps", type=int, default=3000,
                     help="steps of the batched 256-domain x 16-RHS workload (0: skip)")
@@ -191,21 +192,22 @@ def peaks():
 
 
 def traffic_record(kernel, s):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
-    kernel sources are unchanged since that capture (else None)."""
+    """DRAM bytes per launch of `kernel` (s-byte reals) from the committed ncu
+    summary (profiles/traffic.json), if the source files that define the
+    kernel are unchanged since that capture (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    if d.get("csrc_sha") != csrc_sha():
+    rec = json.load(open(p)).get("kernels", {}).get(f"{kernel}_fp{8 * s}")
+    if not rec or rec.get("sha") != sources_sha(rec.get("sources", [])):
         return None
-    return d.get("kernels", {}).get(f"{kernel}_fp{8 * s}")
+    return rec.get("bytes")
 
 
-def csrc_sha():
+def sources_sha(files):
     hsh = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2508_18205_gb300", "csrc")
-    for f in sorted(os.listdir(cs)):
+    for f in sorted(files):
         hsh.update(open(os.path.join(cs, f), "rb").read())
     return hsh.hexdigest()[:16]
 
@@ -287,6 +289,10 @@ def main():
         peak, peak_kind = peaks()
         if a.only == "batched":
             r = batched(M, ctx, a.batched_steps, peak, peak_kind, ndom=a.batched_ndom)
+        elif a.only == "cavity":
+            r = cavity(M, ctx)
+        elif a.only == "adjoint":
+            r = adjoint(M, ctx)
         else:
             r = cube3d(M, ctx, a.cube_steps, peak, peak_kind, nx=a.cube_nx)
         print(json.dumps(r), flush=True)
@@ -390,6 +396,9 @@ def main():
         line["batched"] = batched(M, ctx, a.batched_steps, peak, peak_kind)
     if rank == 0 and a.cube_steps:
         line["cube3d"] = cube3d(M, ctx, a.cube_steps, peak, peak_kind)
+    if rank == 0 and not a.no_extra:
+        line["cavity_fp64"] = cavity(M, ctx)
+        line["adjoint"] = adjoint(M, ctx)
     # end to end through the public API: host fields in, steps, host Ez + probes out
     if not a.no_e2e:
         pin = [torch.empty(x.shape[0], dtype=torch.float64, pin_memory=True) for x in (ez, hx, hy)]
@@ -547,6 +556,103 @@ def cube3d(M, ctx, steps, peak, peak_kind, nx=200):
                          "algorithmic_bytes_per_launch": dom_b, "avg_launch_ms": dom_t * 1e3,
                          "other_kernel_avg_launch_ms": min(h_avg, e_avg) * 1e3,
                          "step_achieved_gbs": (bh + be) * nodes.n / (el / steps) / 1e9}}
+
+
+def cavity(M, ctx, steps=1000):
+    """The plain method of the paper, FP64: 100 x 100 jittered nodes in a PEC
+    square, collocated 12-node stencils (r^3, degree 2), Delta^2 HV, TM11 mode,
+    CFL 0.5, 1000 steps, Ez probed at 16 nodes. L2-resident (about 9 MB per
+    step): latency-bound, so only updates/s are reported. Also the relative L2
+    error against the exact TM11 mode at the end."""
+    S, c = 0.5, 4e-3
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    nodes = W.pec_box((100, 100), 0.25, 1)
+    nd = M.Nodes(ctx, nodes.xyz, nodes.period)
+    st = M.Stencils(nd, nd, 31)
+    cw = M.Weights(st, 12, 3, 2, M.MFD_OP_GRAD)
+    hw = M.Weights(st, 31, 5, 4, M.MFD_OP_LAP_POW, 2)
+    sim = M.Sim(ctx, 2, M.MFD_FP64, dt, eps0, mu0, -c, cw, hw)
+    sim.set_materials(None, nodes.pec)
+    ez, hx, hy = W.tm11_fields(nodes.xyz, 99.0, c0, mu0, 0.0, -0.5 * dt)
+    ez[nodes.pec == 1] = 0
+    probes = W.interior_nodes(nodes, 16, 14)
+    import torch
+
+    def run():
+        sim.set_field(M.MFD_EZ, ez)
+        sim.set_field(M.MFD_HX, hx)
+        sim.set_field(M.MFD_HY, hy)
+        sim.set_probes(probes, steps)
+        stream = ctx.torch_stream()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        sim.step(steps)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / 1e3
+
+    run()
+    el = run()
+    T = steps * dt
+    ea, xa, ya = W.tm11_fields(nodes.xyz, 99.0, c0, mu0, T, T - 0.5 * dt)
+    got = np.concatenate([sim.get_field(cc) for cc in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)])
+    ref = np.concatenate([ea, xa, ya])
+    return {"workload": "cavity TM11, 100x100 PEC, n=12, FP64, 1000 steps", "nodes": nodes.n,
+            "value": nodes.n * 3 * steps / el, "unit": UNIT, "steps": steps, "ms_per_step": el / steps * 1e3,
+            "roofline": "n/a (L2-resident, latency-bound)",
+            "rel_l2_vs_exact_mode": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+
+
+def adjoint(M, ctx, steps=4000, every=64):
+    """Differentiation workload: 500 x 500 PEC box, n = 20 (r^3, degree 2),
+    Delta^2 HV, eps_r = 1 + 0.5 U, 4 Ricker sources, 8 probes, FP32, 4000
+    steps: J = dt sum Ez_p^2 and dJ/deps_r, dJ/d amplitudes by the adjoint with
+    checkpoints every 64 steps. Reports the forward step rate and the time of one
+    gradient (forward with checkpoints + segment recomputation + adjoint)."""
+    S, c = 0.5, 4e-3
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    nodes = W.pec_box((500, 500), 0.25, 5)
+    nd = M.Nodes(ctx, nodes.xyz, nodes.period)
+    st = M.Stencils(nd, nd, 31)
+    cw = M.Weights(st, 20, 3, 2, M.MFD_OP_GRAD)
+    hw = M.Weights(st, 31, 5, 4, M.MFD_OP_LAP_POW, 2)
+    sim = M.Sim(ctx, 2, M.MFD_FP32, dt, eps0, mu0, -c, cw, hw, compensated=True)
+    eps = W.eps_r_uniform(nodes.n, 55)
+    src = W.ricker_sources(nodes, 4, 56, c0)
+    probes = W.interior_nodes(nodes, 8, 57)
+    z = np.zeros(nodes.n)
+
+    def setup():
+        sim.set_materials(eps, nodes.pec)
+        for cc in (M.MFD_EZ, M.MFD_HX, M.MFD_HY):
+            sim.set_field(cc, z)
+        sim.set_sources(src.node, src.amp, src.f0, src.t0)
+        sim.set_probes(probes, steps)
+
+    setup()
+    sim.autotune(10)
+    import torch
+    stream = ctx.torch_stream()
+    sim.step(steps)
+    setup()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    sim.step(steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    fwd = t0.elapsed_time(t1) / 1e3
+    setup()
+    t = time.perf_counter()
+    J, ge, ga = sim.grad(steps, every, len(src.node))
+    gs = time.perf_counter() - t
+    return {"workload": "adjoint 500x500 PEC, n=20, FP32, 4000 steps, checkpoints every 64", "nodes": nodes.n,
+            "forward_value": nodes.n * 3 * steps / fwd, "unit": UNIT, "forward_ms_per_step": fwd / steps * 1e3,
+            "gradient_s": gs, "gradient_over_forward": gs / fwd, "J": J,
+            "grad_norm_eps": float(np.linalg.norm(ge)), "grad_amp": [float(x) for x in ga]}
 
 
 def accuracy(M, ctx, wts, steps, reset):
