@@ -278,6 +278,62 @@ void mfd_batch_destroy(mfd_batch* b);
  * roofline. */
 mfd_status mfd_fma_peak(int device, double* fp64_gflops, double* fp32_gflops);
 
+/* ------------------------------------------- partition and halo (host only) */
+
+/* Decomposition of the stepped problem over several GPUs, one shard each. The
+ * paper runs on one machine and has no decomposition; these calls give the
+ * index structures a sharded run needs, with no communication: every stencil
+ * sum of Eq. 16 at a node a shard owns reads owned nodes and a halo of nodes
+ * owned by other shards, and one exchange of the field just updated (E before
+ * the H half step, H before the E half step of Eq. 19) refreshes the halo.
+ * These calls run on the host only: they make no CUDA call and work without a
+ * GPU. Partitions and halo plans copy what they need and hold no reference on
+ * other objects. */
+typedef struct mfd_partition mfd_partition;
+typedef struct mfd_halo mfd_halo;
+
+/* Cuts the n nodes of a set, taken in `order` (host, n caller ids, a
+ * permutation: order[r] = caller id of the r-th node; NULL = caller order;
+ * mfd_nodes_permutation gives the library's Morton order), into nshards
+ * contiguous ranges: shard s owns positions [floor(s n / nshards),
+ * floor((s + 1) n / nshards)), so shard sizes differ by at most one.
+ * 1 <= nshards <= 65536; n >= 0. A non-permutation order is MFD_ERR_ARG. */
+mfd_status mfd_partition_create(int64_t n, const int64_t* order, int nshards, mfd_partition** out);
+/* owner: host, n int32 output: the shard owning each node (caller id). */
+mfd_status mfd_partition_owner(const mfd_partition* part, int32_t* owner);
+/* The nodes `shard` owns, in partition order: *count is always set; ids
+ * (host, *count int64, caller ids) is written when not NULL. */
+mfd_status mfd_partition_owned(const mfd_partition* part, int shard, int64_t* count, int64_t* ids);
+void mfd_partition_destroy(mfd_partition* part);
+
+/* Halo plan of one source node set (partitioned by `src`) for the nsets
+ * stencil sets that read it. Stencil set k has its centres partitioned by
+ * centres[k] (a partition with as many nodes as set k has rows; it may be
+ * `src` itself for own-set stencils) and ncols[k] entries per row; idx[k] is
+ * host int64 [rows][ncols[k]], caller ids into the source set, rows in the
+ * caller order of the centres (mfd_stencils_read). The halo of shard s is the
+ * set of source nodes that some stencil of a centre s owns references and
+ * that another shard owns; it is ordered by owning shard, then by partition
+ * order. An entry outside [0, count(src)) is MFD_ERR_ARG. 1 <= nsets <= 16. */
+mfd_status mfd_halo_create(const mfd_partition* src, int nsets, const mfd_partition* const* centres,
+                           const int* ncols, const int64_t* const* idx, mfd_halo** out);
+/* Number of halo nodes of `shard` (*count), optionally their caller ids (ids,
+ * host, *count int64, halo order). */
+mfd_status mfd_halo_nodes(const mfd_halo* halo, int shard, int64_t* count, int64_t* ids);
+/* The source nodes shard `from` sends to shard `to` in each exchange, in the
+ * order they take in the receiver's halo (a contiguous block of it): *count is
+ * always set (0 when from == to), ids (host, *count int64, caller ids) is
+ * written when not NULL. */
+mfd_status mfd_halo_send(const mfd_halo* halo, int from, int to, int64_t* count, int64_t* ids);
+/* Stencil set k localised to `shard`: local_idx (host int32 [owned centres of
+ * shard][ncols[k]], rows in partition order of the centres) holds, for every
+ * entry, the local source index: p in [0, owned) for the p-th owned source
+ * node (partition order), owned + j for the j-th halo node. A shard that keeps
+ * its owned values followed by its halo in one array applies the stencils
+ * unchanged on it. */
+mfd_status mfd_halo_local_idx(const mfd_halo* halo, int shard, int set, int32_t* local_idx);
+void mfd_halo_destroy(mfd_halo* halo);
+
 /* ------------------------------------------------- kNN without allocation */
 
 /* The kNN stencils of mfd_stencils_build, computed on caller-owned device

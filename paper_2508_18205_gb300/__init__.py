@@ -75,6 +75,15 @@ _SIGS = {
     "mfd_sim_autotune": (_I, [_VP, _I, _VP]),
     "mfd_sim_destroy": (None, [_VP]),
     "mfd_knn_static": (_I, [_I, _I64, _VP, _I64, _VP, _VP, _I, _VP, _VP]),
+    "mfd_partition_create": (_I, [_I64, _VP, _I, C.POINTER(_VP)]),
+    "mfd_partition_owner": (_I, [_VP, _VP]),
+    "mfd_partition_owned": (_I, [_VP, _I, C.POINTER(_I64), _VP]),
+    "mfd_partition_destroy": (None, [_VP]),
+    "mfd_halo_create": (_I, [_VP, _I, _VP, _VP, _VP, C.POINTER(_VP)]),
+    "mfd_halo_nodes": (_I, [_VP, _I, C.POINTER(_I64), _VP]),
+    "mfd_halo_send": (_I, [_VP, _I, _I, C.POINTER(_I64), _VP]),
+    "mfd_halo_local_idx": (_I, [_VP, _I, _I, _VP]),
+    "mfd_halo_destroy": (None, [_VP]),
     "mfd_batch_create": (_I, [_VP, _I, _VP, _I, C.POINTER(_VP)]),
     "mfd_batch_set_materials": (_I, [_VP, _I, _VP, _VP]),
     "mfd_batch_set_field": (_I, [_VP, _I, _I, _I, _VP]),
@@ -224,6 +233,88 @@ class Weights:
         try:
             if self.h:
                 lib().mfd_weights_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class Partition:
+    """A node set of n nodes cut into nshards contiguous ranges of `order`
+    (mfd_partition_create; host only, no GPU needed)."""
+
+    def __init__(self, n: int, nshards: int, order=None):
+        o = None if order is None else np.ascontiguousarray(order, dtype=np.int64)
+        if o is not None and o.shape != (n,):
+            raise ValueError("order must hold n caller ids")
+        h = C.c_void_p()
+        _ck(lib().mfd_partition_create(int(n), _p(o), int(nshards), C.byref(h)))
+        self.h, self.n, self.nshards = h, int(n), int(nshards)
+
+    def owner(self):
+        out = np.empty(self.n, dtype=np.int32)
+        _ck(lib().mfd_partition_owner(self.h, _p(out)))
+        return out
+
+    def owned(self, shard: int):
+        c = C.c_int64()
+        _ck(lib().mfd_partition_owned(self.h, shard, C.byref(c), None))
+        out = np.empty(c.value, dtype=np.int64)
+        _ck(lib().mfd_partition_owned(self.h, shard, C.byref(c), _p(out)))
+        return out
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().mfd_partition_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class HaloPlan:
+    """Halo plan of one source set for the stencil sets that read it
+    (mfd_halo_create). sets: sequence of (centre Partition, idx [rows][ncols]
+    caller ids into the source set)."""
+
+    def __init__(self, src: Partition, sets):
+        parts = [c for c, _ in sets]
+        idxs = [np.ascontiguousarray(i, dtype=np.int64) for _, i in sets]
+        for c, i in zip(parts, idxs):
+            if i.ndim != 2 or i.shape[0] != c.n:
+                raise ValueError("each stencil set needs idx of shape (centres, ncols)")
+        cp = (C.c_void_p * len(sets))(*[c.h.value for c in parts])
+        nc = (C.c_int * len(sets))(*[i.shape[1] for i in idxs])
+        ip = (C.c_void_p * len(sets))(*[i.ctypes.data for i in idxs])
+        h = C.c_void_p()
+        _ck(lib().mfd_halo_create(src.h, len(sets), C.cast(cp, C.c_void_p), C.cast(nc, C.c_void_p),
+                                  C.cast(ip, C.c_void_p), C.byref(h)))
+        self.h, self.src, self.parts = h, src, parts
+        self.ncols = [i.shape[1] for i in idxs]
+
+    def nodes(self, shard: int):
+        c = C.c_int64()
+        _ck(lib().mfd_halo_nodes(self.h, shard, C.byref(c), None))
+        out = np.empty(c.value, dtype=np.int64)
+        _ck(lib().mfd_halo_nodes(self.h, shard, C.byref(c), _p(out)))
+        return out
+
+    def send(self, frm: int, to: int):
+        c = C.c_int64()
+        _ck(lib().mfd_halo_send(self.h, frm, to, C.byref(c), None))
+        out = np.empty(c.value, dtype=np.int64)
+        _ck(lib().mfd_halo_send(self.h, frm, to, C.byref(c), _p(out)))
+        return out
+
+    def local_idx(self, shard: int, k: int):
+        rows = len(self.parts[k].owned(shard))
+        out = np.empty((rows, self.ncols[k]), dtype=np.int32)
+        _ck(lib().mfd_halo_local_idx(self.h, shard, k, _p(out)))
+        return out
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().mfd_halo_destroy(self.h)
                 self.h = None
         except Exception:
             pass

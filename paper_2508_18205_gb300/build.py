@@ -1,6 +1,7 @@
 """Builds libmfd.so (the CUDA library behind include/mfd.h) in-tree for sm_103a.
 
-Each translation unit is compiled by its own nvcc process (in parallel), then
+Each translation unit (CUDA .cu, host-only .cpp) is compiled by its own nvcc
+process (in parallel), then
 linked into paper_2508_18205_gb300/_build/libmfd.so.
 """
 from __future__ import annotations
@@ -28,7 +29,7 @@ def _nvcc():
 
 
 def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
 
 
 def _stale(objs, deps):
@@ -47,7 +48,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         return LIB
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
-    objs = [os.path.join(OUT, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(OUT, os.path.splitext(os.path.basename(s))[0] + ".o") for s in srcs]
 
     def one(args):
         src, obj = args
