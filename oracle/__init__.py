@@ -4,7 +4,9 @@ Only tests/, ``__graft_entry__.smoke()`` and bench.py's ``cpu_baseline`` /
 ``--impl reference`` legs may import this package. It never imports the CUDA
 package and the CUDA package never imports it. The arithmetic lives in
 ``oracle.c`` (plain C, FP64, stencil sums in stencil order); this module only
-marshals arrays and assembles problems from its functions.
+marshals arrays and assembles problems from its functions. The dispersion
+analysis of Sec. 6 is ``oracle/dispersion.py`` (numpy, with numpy's FFT as the
+transform).
 
 Pins that tie the oracle to the paper and to mathematics live in
 ``tests/test_oracle_*.py``. Every function here is pinned there.
