@@ -267,6 +267,23 @@ def run_tmz(p: TMz, ez, hx, hy, nsteps, step0=0, sources=None, probes=None, ener
     return ez, hx, hy, pout, eout
 
 
+def run_yee(nx, ny, ch, ce, dt, ez, hx, hy, nsteps, step0=0, sources=None, probes=None):
+    """FDTD (Yee) TMz steps on a periodic nx x ny grid (Eq. 5); fields are
+    (ny, nx) arrays (Ez at cell centres' nodes, Hx / Hy staggered, Eq. 4).
+    Returns (ez, hx, hy, probe series (nsteps x P))."""
+    ez, hx, hy = (np.ascontiguousarray(_f64(a).reshape(ny, nx)).copy() for a in (ez, hx, hy))
+    if sources is None:
+        sn, sa, sf, st0 = np.zeros(0, np.int64), np.zeros(0), np.zeros(0), np.zeros(0)
+    else:
+        sn, sa, sf, st0 = _i64(sources.node), _f64(sources.amp), _f64(sources.f0), _f64(sources.t0)
+    pr = np.zeros(0, np.int64) if probes is None else _i64(probes)
+    pout = np.zeros((nsteps, len(pr)))
+    _check(lib().orc_run_yee(C.c_int64(nx), C.c_int64(ny), C.c_double(ch), C.c_double(ce), C.c_double(dt),
+                             _p(ez), _p(hx), _p(hy), C.c_int64(step0), C.c_int64(nsteps), C.c_int(len(sn)),
+                             _p(sn), _p(sa), _p(sf), _p(st0), C.c_int(len(pr)), _p(pr), _p(pout)), "run_yee")
+    return ez, hx, hy, pout
+
+
 def adjoint_step_tmz(p: TMz, lE, lHx, lHy):
     lE, lHx, lHy = _f64(lE).copy(), _f64(lHx).copy(), _f64(lHy).copy()
     args, keep = _tmz_args(p)

@@ -917,3 +917,45 @@ int orc_3d_sample_step(int64_t nhs, const int64_t* hs_ids, int nc, const int64_t
     }
     return ORC_OK;
 }
+
+/*
+ * FDTD (Yee) scheme for TMz on a periodic nx x ny grid of spacing h (Eq. 4,
+ * Eq. 5): Ez[j][i] at (i h, j h) and time n dt; Hx[j][i] at (i h, (j + 1/2) h),
+ * Hy[j][i] at ((i + 1/2) h, j h), both at time (n - 1/2) dt. Per step, with
+ * ch = dt / (mu0 h) (S_c / eta0 in Eq. 5) and ce = dt / (eps0 h) (eta0 S_c):
+ *   Hx[j][i] -= ch (Ez[j+1][i] - Ez[j][i])
+ *   Hy[j][i] += ch (Ez[j][i+1] - Ez[j][i])
+ *   Ez[j][i] += ce (Hy[j][i] - Hy[j][i-1] - Hx[j][i] + Hx[j-1][i])   (new H)
+ * indices wrapping periodically. Then soft Ricker sources add to Ez at
+ * t_{n+1} = (n + 1) dt and probes record Ez (cell index j nx + i).
+ */
+int orc_run_yee(int64_t nx, int64_t ny, double ch, double ce, double dt, double* ez, double* hx, double* hy,
+                int64_t step0, int64_t nsteps, int nsrc, const int64_t* src_cell, const double* src_amp,
+                const double* src_f0, const double* src_t0, int nprobe, const int64_t* probe_cell,
+                double* probe_out)
+{
+    if (nx < 1 || ny < 1) return ORC_ERR_ARG;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        int64_t n = step0 + k;
+        for (int64_t j = 0; j < ny; ++j) {
+            int64_t jp = (j + 1) % ny;
+            for (int64_t i = 0; i < nx; ++i) {
+                int64_t ip = (i + 1) % nx;
+                double e = ez[j * nx + i];
+                hx[j * nx + i] -= ch * (ez[jp * nx + i] - e);
+                hy[j * nx + i] += ch * (ez[j * nx + ip] - e);
+            }
+        }
+        for (int64_t j = 0; j < ny; ++j) {
+            int64_t jm = (j + ny - 1) % ny;
+            for (int64_t i = 0; i < nx; ++i) {
+                int64_t im = (i + nx - 1) % nx;
+                ez[j * nx + i] += ce * (hy[j * nx + i] - hy[j * nx + im] - hx[j * nx + i] + hx[jm * nx + i]);
+            }
+        }
+        double t1 = (double)(n + 1) * dt;
+        for (int s = 0; s < nsrc; ++s) ez[src_cell[s]] += src_amp[s] * orc_ricker(t1, src_f0[s], src_t0[s]);
+        for (int p = 0; p < nprobe; ++p) probe_out[k * nprobe + p] = ez[probe_cell[p]];
+    }
+    return ORC_OK;
+}
