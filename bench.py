@@ -52,9 +52,10 @@ def _args():
     ap.add_argument("--cube-steps", type=int, default=200,
                     help="steps of the 3D 200^3 workload (0: skip)")
     ap.add_argument("--cube-nx", type=int, default=200, help="nodes per side of the 3D cube")
+    ap.add_argument("--yee-grid", type=int, default=8192, help="cells per side of the FDTD roofline grid")
     ap.add_argument("--batched-ndom", type=int, default=256, help="domains of the batched workload")
     ap.add_argument("--no-extra", action="store_true", help="skip the cavity (FP64) and adjoint sections")
-    ap.add_argument("--only", default="all", choices=["all", "batched", "cube3d", "cavity", "adjoint"],
+    ap.add_argument("--only", default="all", choices=["all", "batched", "cube3d", "cavity", "adjoint", "dispersion", "hv_search", "yee"],
                     help="run one section alone (profiling); prints that section as the JSON line")
     ap.add_argument("--batched-steps", type=int, default=3000,
                     help="steps of the batched 256-domain x 16-RHS workload (0: skip)")
@@ -293,6 +294,20 @@ def main():
             r = cavity(M, ctx)
         elif a.only == "adjoint":
             r = adjoint(M, ctx)
+        elif a.only == "hv_search":
+            r = hv_search(M, ctx)
+        elif a.only == "yee":
+            r = yee(M, ctx, peak, peak_kind, big=a.yee_grid)
+        elif a.only == "dispersion":
+            e, h = node_sets(a.nx)
+            wts, _, _ = build_weights(M, ctx, e, h)
+            ez, hx, hy = pulse_fields(e, h, a.nx, W.units(PARAMS["S"])[0])
+
+            def reset(s_, cap):
+                for comp_, v in ((M.MFD_EZ, ez), (M.MFD_HX, hx), (M.MFD_HY, hy)):
+                    s_.set_field(comp_, v)
+                s_.set_probes(W.interior_nodes(e, 16, 24), cap)
+            r = dispersion(M, ctx, wts, e, reset, not a.plain)
         else:
             r = cube3d(M, ctx, a.cube_steps, peak, peak_kind, nx=a.cube_nx)
         print(json.dumps(r), flush=True)
@@ -392,6 +407,8 @@ def main():
         del s64
         if a.accuracy_steps:
             line["accuracy"] = accuracy(M, ctx, wts, a.accuracy_steps, reset)
+    if rank == 0 and not a.no_extra:
+        line["dispersion"] = dispersion(M, ctx, wts, e, reset, comp)
     if rank == 0 and a.batched_steps:
         line["batched"] = batched(M, ctx, a.batched_steps, peak, peak_kind)
     if rank == 0 and a.cube_steps:
@@ -399,6 +416,8 @@ def main():
     if rank == 0 and not a.no_extra:
         line["cavity_fp64"] = cavity(M, ctx)
         line["adjoint"] = adjoint(M, ctx)
+        line["hv_search"] = hv_search(M, ctx)
+        line["yee"] = yee(M, ctx, peak, peak_kind)
     # end to end through the public API: host fields in, steps, host Ez + probes out
     if not a.no_e2e:
         pin = [torch.empty(x.shape[0], dtype=torch.float64, pin_memory=True) for x in (ez, hx, hy)]
@@ -653,6 +672,193 @@ def adjoint(M, ctx, steps=4000, every=64):
             "forward_value": nodes.n * 3 * steps / fwd, "unit": UNIT, "forward_ms_per_step": fwd / steps * 1e3,
             "gradient_s": gs, "gradient_over_forward": gs / fwd, "J": J,
             "grad_norm_eps": float(np.linalg.norm(ge)), "grad_amp": [float(x) for x in ga]}
+
+
+def yee(M, ctx, peak, peak_kind, big=8192, steps=1000, nx=1000, pulse_steps=5000, stride=4):
+    """The FDTD (Yee) reference scheme (Eq. 5) on the GPU, FP32:
+    (a) throughput and HBM roofline of the fused step kernel on a big x big
+        periodic grid (compulsory bytes: Ez, Hx, Hy read and written once,
+        24 B per cell and step), random fields;
+    (b) the pulse workload's problem on an nx x nx grid (carrier 12 h, S = 0.5,
+        pulse_steps steps): updates/s next to the meshless step, and the phase
+        speed at the carrier measured on row nx/2 (Sec. 6 analysis) against
+        Eq. 6 and the physical speed."""
+    import math
+    import torch
+    S = PARAMS["S"]
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    out = {}
+    y = M.Yee(ctx, big, big, M.MFD_FP32, dt, 1.0, eps0, mu0)
+    rng = np.random.default_rng(1)
+    for comp in (M.MFD_EZ, M.MFD_HX, M.MFD_HY):
+        y.set_field(comp, rng.standard_normal((big, big)))
+    y.step(64)
+    stream = ctx.torch_stream()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    y.step(steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    el = t0.elapsed_time(t1) / 1e3
+    k = min(steps, 200)
+    ms = y.step_timed(k) / k
+    cells = big * big
+    alg = 24.0 * cells
+    out["grid"] = {"cells": cells, "steps": steps, "ms_per_step": el / steps * 1e3,
+                   "value": 3 * cells * steps / el, "unit": UNIT,
+                   "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                                "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": None, "kernel": "k_yee",
+                                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg,
+                                "avg_launch_ms": ms}}
+    del y
+    lam = PARAMS["wavelength"]
+    g = np.arange(nx, dtype=float)
+    xy = np.stack(np.meshgrid(g, g), -1).reshape(-1, 2)
+    for tag, direction, x0, line, h_line, phi in (
+            ("pulse", (1, 0), nx / 2, np.arange(nx) + (nx // 2) * nx, 1.0, 0.0),
+            ("pulse_45", (1, 1), nx / math.sqrt(2) / 2, np.arange(nx) * (nx + 1), math.sqrt(2), math.pi / 4)):
+        y = M.Yee(ctx, nx, nx, M.MFD_FP32, dt, 1.0, eps0, mu0)
+        ez, _, _ = W.gaussian_pulse(xy, nx, x0, 2 * lam, c0, eta0, dt, lam, direction=direction)
+        _, hx, _ = W.gaussian_pulse(xy + np.array([0.0, 0.5]), nx, x0, 2 * lam, c0, eta0, dt, lam,
+                                    direction=direction)  # Hx at (i, j + 1/2)
+        _, _, hy = W.gaussian_pulse(xy + np.array([0.5, 0.0]), nx, x0, 2 * lam, c0, eta0, dt, lam,
+                                    direction=direction)  # Hy at (i + 1/2, j)
+        y.set_field(M.MFD_EZ, ez)
+        y.set_field(M.MFD_HX, hx)
+        y.set_field(M.MFD_HY, hy)
+        y.set_probes(line, pulse_steps)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        y.step(pulse_steps)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        el = t0.elapsed_time(t1) / 1e3
+        nt = pulse_steps // stride
+        samples = y.read_probes()[stride - 1::stride]
+        spec, kidx, c, _ = M.dispersion(ctx, samples, h_line, stride * dt, c0, 1)
+        rep = _ridge_report(M, spec, kidx, c, nt, stride * dt, phi, el, 0.0, stride, h_line)
+        out[tag] = {"cells": nx * nx, "steps": pulse_steps, "ms_per_step": el / pulse_steps * 1e3,
+                    "value": 3 * nx * nx * pulse_steps / el, "unit": UNIT,
+                    "l2_note": "24 MB state: L2-resident, launch/latency bound",
+                    "carrier": rep["carrier"], "band_j": rep["band_j"], "err_l1": rep["err_l1"],
+                    "eq6_err_l1": rep["fdtd_err_l1"]}
+        del y
+    return out
+
+
+def hv_search(M, ctx, nx=200, steps=10000, ncand=16, rounds=2):
+    """The hyperviscosity coefficient search (mfd_hv_search) on the setup of
+    Sec. 6: a periodic jittered 200 x 200 layout, Courant number 1/(10 sqrt 2),
+    a sigma = 2 h Gaussian pulse, alpha = 2, here with n = 30 (PHS r^5,
+    monomials to degree 4), 10,000 steps per round, ncand candidates per round
+    in [1e-6, 1e-1], energy checked every 100 steps against 1 % growth."""
+    import math
+    S = 1 / (10 * math.sqrt(2))
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    nodes = W.periodic_box((nx, nx), 0.25, 6)
+    nd = M.Nodes(ctx, nodes.xyz, nodes.period)
+    st = M.Stencils(nd, nd, 31)
+    cw = M.Weights(st, 30, 5, 4, M.MFD_OP_GRAD)
+    hw = M.Weights(st, 31, 5, 4, M.MFD_OP_LAP_POW, 2)
+    ez, hx, hy = W.gaussian_pulse(nodes.xyz, nx, nx / 2, 2.0, c0, eta0, dt, None)
+    t0 = time.perf_counter()
+    c, hist = M.hv_search(ctx, cw, hw, dt, eps0, mu0, ez, hx, hy, -6.0, -1.0, ncand=ncand, rounds=rounds,
+                          nsteps=steps, check_every=100, tol=0.01)
+    el = time.perf_counter() - t0
+    updates = nodes.n * 3 * ncand * steps * rounds
+    last = hist[-1]
+    k = int(np.argmin(np.abs(last[:, 0] - math.log10(c))))
+    return {"workload": f"hv-search periodic {nx}x{nx}, S=1/(10 sqrt 2), sigma=2, n=30, alpha=2",
+            "nodes": int(nodes.n), "candidates_per_round": ncand, "rounds": rounds, "steps_per_round": steps,
+            "log10_c": math.log10(c), "u_max_at_c": float(last[k, 1]), "u_end_at_c": float(last[k, 2]),
+            "final_interval_log10": 5.0 / ncand ** rounds,
+            "seconds": el, "value": updates / el, "unit": UNIT,
+            "paper_log10_c_context": -4.76}
+
+
+def _line_analysis(M, sim, steps, stride, h_line, phi):
+    """Runs `steps` steps with the line's probes set and analyses them (Sec. 6):
+    c(w) at the carrier and the l1 error of Eq. 26 over the band where the
+    spectrum is present (rows whose largest component is >= 1 % of the overall
+    largest), next to the Yee scheme's phase speed (Eq. 6) at angle phi."""
+    import math
+    S = PARAMS["S"]
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    sim.ctx.sync()
+    t_run = time.perf_counter() - t0
+    nt = steps // stride
+    dts = stride * dt
+    t0 = time.perf_counter()
+    sim.dispersion(stride, nt, h_line, c0, 1, spectrum=False)
+    t_an = time.perf_counter() - t0
+    spec, kidx, c, _ = sim.dispersion(stride, nt, h_line, c0, 1)
+    return _ridge_report(M, spec, kidx, c, nt, dts, phi, t_run, t_an, stride, h_line)
+
+
+def _ridge_report(M, spec, kidx, c, nt, dts, phi, t_run, t_an, stride, h_line):
+    """c(w) at the carrier, and Eq. 25-26 summed over the band of the pulse:
+    the contiguous rows around the carrier's row (positive frequencies,
+    j < nt / 2; a real signal mirrors them at nt - j) whose largest component
+    is >= 1 % of the carrier row's. The Yee phase speed (Eq. 6) at the same
+    frequencies and angle for comparison."""
+    import math
+    S = PARAMS["S"]
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    rowmax = spec.max(axis=1)
+    w0 = c0 * 2 * math.pi / PARAMS["wavelength"]  # carrier angular frequency (per dt)
+    j0 = int(round(w0 * nt * dts / (2 * math.pi)))
+    lo = hi = j0
+    while lo > 1 and rowmax[lo - 1] >= 1e-2 * rowmax[j0]:
+        lo -= 1
+    while hi + 1 < (nt + 1) // 2 and rowmax[hi + 1] >= 1e-2 * rowmax[j0]:
+        hi += 1
+    band = range(lo, hi + 1)
+    fd = {j: M.fdtd_phase_speed(2 * math.pi * j / (nt * dts) * dt, S, phi) for j in band}
+    return {"samples": nt, "stride": stride, "h_line": h_line, "run_s": t_run, "analysis_ms": t_an * 1e3,
+            "carrier": {"j": j0, "k_index": int(kidx[j0]), "c": float(c[j0]), "rel_err": float(abs(c[j0] - c0) / c0),
+                        "fdtd_c": fd[j0], "fdtd_rel_err": abs(fd[j0] - c0) / c0},
+            "band_j": [lo, hi], "err_l1": float(sum(abs(c[j] - c0) for j in band)),
+            "fdtd_err_l1": float(sum(abs(fd[j] - c0) for j in band))}
+
+
+def dispersion(M, ctx, wts, e, reset, comp, steps=5000, stride=4):
+    """Phase speed of the pulse workload against the physical one (Sec. 6,
+    Eqs. 24-26), analysed on the GPU (mfd_sim_dispersion): at 0 degrees on the
+    equispaced seed line y = L/2 of the E set, and at 45 degrees (Eq. 27: the
+    same modulated pulse along the diagonal) on an E set whose diagonal x = y
+    is equispaced (spacing sqrt 2), each with every node of the line a probe."""
+    import math
+    nx = int(round(e.period[0]))
+    lam = PARAMS["wavelength"]
+    dt, eps0, mu0, c0, eta0 = W.units(PARAMS["S"])
+    line = np.nonzero(e.xyz[:, 1] == nx // 2)[0]
+    line = line[np.argsort(e.xyz[line, 0])]
+    sim = make_sim(M, ctx, wts, M.MFD_FP32, comp)
+    reset(sim, 8)
+    sim.set_probes(line, steps)
+    out = {"c0": c0, "steps": steps, "line_nodes": int(len(line)),
+           "phi_0": _line_analysis(M, sim, steps, stride, 1.0, 0.0)}
+    del sim
+    # 45 degrees: the E set with an equispaced diagonal, the H set as before
+    e45 = W.periodic_box((nx, nx), 0.25, 2, seed_diagonal=True)
+    h45 = W.periodic_box((nx, nx), 0.25, 3, offset=(0.5, 0.5))
+    wts45, _, _ = build_weights(M, ctx, e45, h45)
+    sim = make_sim(M, ctx, wts45, M.MFD_FP32, comp)
+    x0 = nx / math.sqrt(2) / 2
+    ez, _, _ = W.gaussian_pulse(e45.xyz, nx, x0, 2 * lam, c0, eta0, dt, lam, direction=(1, 1))
+    _, hx, hy = W.gaussian_pulse(h45.xyz, nx, x0, 2 * lam, c0, eta0, dt, lam, direction=(1, 1))
+    for comp_, v in ((M.MFD_EZ, ez), (M.MFD_HX, hx), (M.MFD_HY, hy)):
+        sim.set_field(comp_, v)
+    diag = np.nonzero(e45.xyz[:, 0] == e45.xyz[:, 1])[0]
+    diag = diag[np.argsort(e45.xyz[diag, 0])]
+    sim.set_probes(diag, steps)
+    out["phi_45"] = _line_analysis(M, sim, steps, stride, math.sqrt(2), math.pi / 4)
+    del sim, wts45
+    return out
 
 
 def accuracy(M, ctx, wts, steps, reset):

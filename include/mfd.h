@@ -268,7 +268,45 @@ mfd_status mfd_batch_read_probes(mfd_batch* b, int dom, double* host, int64_t* s
 int64_t mfd_batch_nodes(const mfd_batch* b);
 /* 1 when mfd_batch_step replays a captured CUDA graph, 0 for direct launches. */
 int mfd_batch_uses_graph(const mfd_batch* b);
+/* The hyperviscosity coefficient gamma of every right-hand side of domain dom
+ * (host, nrhs FP64, finite; replaces the domain's gamma from mfd_batch_create,
+ * which all right-hand sides start with). Right-hand sides that differ only in
+ * gamma run several values of the coefficient of Eq. 18 in one launch. */
+mfd_status mfd_batch_set_gamma(mfd_batch* b, int dom, const double* gamma);
+/* Energy of Eq. 20 of every right-hand side of domain dom in its current state
+ * (host output, nrhs FP64): sum over nodes of eps_r Ez^2 + eta0^2 |H|^2 with H
+ * averaged between t - dt/2 and t + dt/2 (the next H half step is computed,
+ * not applied), eta0^2 = mu0 / eps0, as mfd_energy. */
+mfd_status mfd_batch_energy(mfd_batch* b, int dom, double* u);
 void mfd_batch_destroy(mfd_batch* b);
+
+/* ------------------------------------------------- hyperviscosity search */
+
+/* The coefficient c of gamma = c (-1)^(alpha-1) h^(2 alpha) (Sec. 5.1, with h
+ * = 1 in the caller's units) by multisection on log10 c, the search by which
+ * the paper picks c (Sec. 5.1, Sec. 6). Reading: the paper names the method
+ * (a bisection) but not its criterion; here the answer is the smallest stable
+ * c of [10^log10_lo, 10^log10_hi] to the search's resolution, the least
+ * dissipative stable choice.
+ *   Round r runs ncand (4, 8, 16 or 32) candidates log10 c_k = lo + (hi - lo)
+ *   (k + 1) / ncand, k = 0 .. ncand - 1, at once as right-hand sides of one
+ *   batched collocated FP32 domain (curl, hv: weights on one own-set stencil
+ *   set, as mfd_batch_create; alpha from hv), each from the fields ez, hx, hy
+ *   (host, caller order; H at t - dt/2) and the optional materials eps_r /
+ *   pec (NULL: vacuum, no PEC), for nsteps steps. Candidate k is stable when
+ *   u(t) = U(t) / U(0) (Eq. 20, mfd_batch_energy) stays <= 1 + tol and finite
+ *   at every check, taken every check_every steps and after the last step.
+ *   The next interval is [c_{k*-1}, c_{k*}] around the first stable candidate
+ *   k* (lo kept when k* = 0).
+ * Out: *c_out = 10^hi after `rounds` rounds (a stable value); history (host,
+ * nullable) [rounds][ncand][3] = (log10 c_k, max u, final u), a round that
+ * stops early (every candidate failed) reports its last u. No stable candidate
+ * in a round (the upper end must be stable) is MFD_ERR_UNSTABLE with
+ * *c_out = NaN and the history up to that round. */
+mfd_status mfd_hv_search(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* hv, double dt, double eps0,
+                         double mu0, const double* eps_r, const uint8_t* pec, const double* ez, const double* hx,
+                         const double* hy, double log10_lo, double log10_hi, int ncand, int rounds, int64_t nsteps,
+                         int64_t check_every, double tol, double* c_out, double* history);
 
 /* ----------------------------------------------------------- diagnostics */
 
@@ -277,6 +315,67 @@ void mfd_batch_destroy(mfd_batch* b);
  * The paper has no counterpart; it is the denominator of the FP64 step's ALU
  * roofline. */
 mfd_status mfd_fma_peak(int device, double* fp64_gflops, double* fp32_gflops);
+
+/* ------------------------------------------------------- FDTD reference */
+
+/* The FDTD (Yee) scheme for TMz (Eq. 4, Eq. 5), the grid method the paper
+ * generalises and compares with (Sec. 3, Sec. 6), on a periodic nx x ny grid
+ * of spacing h: Ez[j][i] at (i h, j h) and time n dt, Hx[j][i] at
+ * (i h, (j + 1/2) h) and Hy[j][i] at ((i + 1/2) h, j h), both at (n - 1/2) dt.
+ * A step is Eq. 5 with S_c / eta0 = dt / (mu0 h) and eta0 S_c = dt / (eps0 h)
+ * (stable for S_c <= 1/sqrt(2)), then soft Ricker sources (as mfd_set_sources,
+ * cell index j nx + i), then probes. One fused kernel per step; long runs
+ * replay a CUDA graph. FP64 results equal the reference arithmetic of Eq. 5
+ * taken term by term (no fused multiply-add) bit for bit.
+ * 2 <= nx < 2^30, 2 <= ny <= 524280; fields in host arrays are ny x nx FP64. */
+typedef struct mfd_yee mfd_yee;
+mfd_status mfd_yee_create(mfd_ctx* ctx, int64_t nx, int64_t ny, int precision, double dt, double h, double eps0,
+                          double mu0, mfd_yee** out);
+/* comp: MFD_EZ, MFD_HX or MFD_HY; host ny x nx FP64. */
+mfd_status mfd_yee_set_field(mfd_yee* y, int comp, const double* host);
+mfd_status mfd_yee_get_field(mfd_yee* y, int comp, double* host);
+mfd_status mfd_yee_set_sources(mfd_yee* y, int count, const int64_t* cell, const double* amp, const double* f0,
+                               const double* t0);
+/* Ez of `count` cells after each step, for at most `capacity` steps. */
+mfd_status mfd_yee_set_probes(mfd_yee* y, int count, const int64_t* cell, int64_t capacity);
+mfd_status mfd_yee_step(mfd_yee* y, int64_t nsteps);
+/* nsteps steps, each bracketed by CUDA events; *ms = the summed step times. */
+mfd_status mfd_yee_step_timed(mfd_yee* y, int64_t nsteps, double* ms);
+/* host: steps x count FP64; *steps receives the recorded steps. */
+mfd_status mfd_yee_read_probes(mfd_yee* y, double* host, int64_t* steps);
+void mfd_yee_destroy(mfd_yee* y);
+
+/* ------------------------------------------------------------ dispersion */
+
+/* Numerical dispersion of a run (Sec. 6, Eqs. 24-26), computed on the GPU in
+ * FP64. Input: Ez sampled at nx equispaced nodes of a line (spacing h_line
+ * along it, in the order of increasing position along the propagation
+ * direction) at nt instants dt_sample apart: samples[n][m], host, nt x nx.
+ *   spectrum |E(k_i, w_j)| = |sum_n sum_m w_n s[n][m] exp(-i k_i x_m)
+ *            exp(+i w_j t_n)| with the symmetric Hann window
+ *            w_n = 1/2 - 1/2 cos(2 pi n / (nt - 1)) in time (w = 1 if nt == 1),
+ *            k_i = 2 pi i / (nx h_line), w_j = 2 pi j / (nt dt_sample), so a
+ *            wave travelling along the line appears at positive k and w;
+ *   kidx[j] = argmax over 0 <= i < nx of |E(k_i, w_j)| (smallest i on ties);
+ *   c[j]    = w_j / k_kidx[j] (Eq. 24): NaN for j = 0, +inf if kidx[j] = 0;
+ *   err_l1  = sum over 1 <= j <= jmax of |c[j] - c_ref| (Eqs. 25-26; Eq. 26
+ *             starts at j = 0, where w_0 = 0 leaves c undefined).
+ * Outputs (host, each may be NULL): spectrum nt x nx (row j), kidx nt int32,
+ * c nt, err_l1 one double. 1 <= nx, nt <= 4096; 0 <= jmax < nt. */
+mfd_status mfd_dispersion(mfd_ctx* ctx, int nx, int nt, const double* samples, double h_line, double dt_sample,
+                          double c_ref, int jmax, double* spectrum, int32_t* kidx, double* c, double* err_l1);
+/* The same analysis of a simulation's own probe series, without a host round
+ * trip: the probes (mfd_set_probes, in line order) are the nx line nodes and
+ * the samples are the records after steps stride, 2 stride, ..., nt stride
+ * counted from mfd_set_probes (dt_sample = stride dt). Needs nt * stride
+ * recorded steps. */
+mfd_status mfd_sim_dispersion(mfd_sim* sim, int stride, int nt, double h_line, double c_ref, int jmax,
+                              double* spectrum, int32_t* kidx, double* c, double* err_l1);
+/* Phase speed, in h per dt, of the FDTD (Yee) scheme on a square grid with
+ * Courant number S = c dt / h at angular frequency omega (omega_dt = omega dt)
+ * and propagation angle phi (Eq. 6), on the branch through k = 0; NaN above
+ * the grid's cut-off. Host only. */
+mfd_status mfd_fdtd_phase_speed(double omega_dt, double courant, double phi, double* c);
 
 /* ------------------------------------------- partition and halo (host only) */
 

@@ -75,6 +75,18 @@ _SIGS = {
     "mfd_sim_autotune": (_I, [_VP, _I, _VP]),
     "mfd_sim_destroy": (None, [_VP]),
     "mfd_knn_static": (_I, [_I, _I64, _VP, _I64, _VP, _VP, _I, _VP, _VP]),
+    "mfd_yee_create": (_I, [_VP, _I64, _I64, _I, _D, _D, _D, _D, C.POINTER(_VP)]),
+    "mfd_yee_set_field": (_I, [_VP, _I, _VP]),
+    "mfd_yee_get_field": (_I, [_VP, _I, _VP]),
+    "mfd_yee_set_sources": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
+    "mfd_yee_set_probes": (_I, [_VP, _I, _VP, _I64]),
+    "mfd_yee_step": (_I, [_VP, _I64]),
+    "mfd_yee_step_timed": (_I, [_VP, _I64, _VP]),
+    "mfd_yee_read_probes": (_I, [_VP, _VP, C.POINTER(_I64)]),
+    "mfd_yee_destroy": (None, [_VP]),
+    "mfd_dispersion": (_I, [_VP, _I, _I, _VP, _D, _D, _D, _I, _VP, _VP, _VP, _VP]),
+    "mfd_sim_dispersion": (_I, [_VP, _I, _I, _D, _D, _I, _VP, _VP, _VP, _VP]),
+    "mfd_fdtd_phase_speed": (_I, [_D, _D, _D, _VP]),
     "mfd_partition_create": (_I, [_I64, _VP, _I, C.POINTER(_VP)]),
     "mfd_partition_owner": (_I, [_VP, _VP]),
     "mfd_partition_owned": (_I, [_VP, _I, C.POINTER(_I64), _VP]),
@@ -94,7 +106,11 @@ _SIGS = {
     "mfd_batch_read_probes": (_I, [_VP, _I, _VP, C.POINTER(_I64)]),
     "mfd_batch_nodes": (_I64, [_VP]),
     "mfd_batch_uses_graph": (_I, [_VP]),
+    "mfd_batch_set_gamma": (_I, [_VP, _I, _VP]),
+    "mfd_batch_energy": (_I, [_VP, _I, _VP]),
     "mfd_batch_destroy": (None, [_VP]),
+    "mfd_hv_search": (_I, [_VP, _VP, _VP, _D, _D, _D, _VP, _VP, _VP, _VP, _VP, _D, _D, _I, _I, _I64, _I64, _D, _VP,
+                           _VP]),
 }
 
 _lib = None
@@ -130,6 +146,44 @@ def _p(a):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _dispersion_out(nt, nx, want_spectrum):
+    spec = np.empty((nt, nx)) if want_spectrum else None
+    return spec, np.empty(nt, dtype=np.int32), np.empty(nt), np.zeros(1)
+
+
+def dispersion(ctx, samples, h_line, dt_sample, c_ref, jmax, spectrum=True):
+    """Numerical dispersion of line samples (mfd_dispersion, Sec. 6, Eqs. 24-26):
+    (spectrum |E(k_i, w_j)| or None, argmax index i(j), c(w_j), ||err||_1)."""
+    s = _f64(samples)
+    nt, nx = s.shape
+    spec, kidx, c, l1 = _dispersion_out(nt, nx, spectrum)
+    _ck(lib().mfd_dispersion(ctx.h, nx, nt, _p(s), float(h_line), float(dt_sample), float(c_ref), int(jmax),
+                             _p(spec), _p(kidx), _p(c), _p(l1)))
+    return spec, kidx, c, float(l1[0])
+
+
+def hv_search(ctx, curl, hv, dt, eps0, mu0, ez, hx, hy, log10_lo, log10_hi, ncand=16, rounds=2, nsteps=2000,
+              check_every=100, tol=0.01, eps_r=None, pec=None):
+    """Smallest stable hyperviscosity coefficient c by multisection (mfd_hv_search).
+    Returns (c, history[rounds][ncand][3] = (log10 c, max u, final u)); raises
+    MfdError (MFD_ERR_UNSTABLE) when a round has no stable candidate."""
+    er = None if eps_r is None else _f64(eps_r)
+    pc = None if pec is None else np.ascontiguousarray(pec, dtype=np.uint8)
+    hist = np.full((rounds, ncand, 3), np.nan)
+    c = np.zeros(1)
+    _ck(lib().mfd_hv_search(ctx.h, curl.h, hv.h, float(dt), float(eps0), float(mu0), _p(er), _p(pc), _p(_f64(ez)),
+                            _p(_f64(hx)), _p(_f64(hy)), float(log10_lo), float(log10_hi), int(ncand), int(rounds),
+                            int(nsteps), int(check_every), float(tol), _p(c), _p(hist)))
+    return float(c[0]), hist
+
+
+def fdtd_phase_speed(omega_dt, courant, phi):
+    """Phase speed of the Yee scheme in h per dt (mfd_fdtd_phase_speed, Eq. 6)."""
+    c = np.zeros(1)
+    _ck(lib().mfd_fdtd_phase_speed(float(omega_dt), float(courant), float(phi), _p(c)))
+    return float(c[0])
 
 
 def fma_peak(device=0):
@@ -233,6 +287,58 @@ class Weights:
         try:
             if self.h:
                 lib().mfd_weights_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class Yee:
+    """FDTD (Yee) TMz on a periodic nx x ny grid (mfd_yee_*, Eq. 5)."""
+
+    def __init__(self, ctx: Ctx, nx, ny, precision, dt, h, eps0, mu0):
+        hd = C.c_void_p()
+        _ck(lib().mfd_yee_create(ctx.h, int(nx), int(ny), precision, float(dt), float(h), float(eps0), float(mu0),
+                                 C.byref(hd)))
+        self.h, self.ctx, self.nx, self.ny, self.nprobe = hd, ctx, int(nx), int(ny), 0
+
+    def set_field(self, comp, values):
+        v = _f64(values).reshape(self.ny, self.nx)
+        _ck(lib().mfd_yee_set_field(self.h, comp, _p(np.ascontiguousarray(v))))
+
+    def get_field(self, comp):
+        out = np.empty((self.ny, self.nx))
+        _ck(lib().mfd_yee_get_field(self.h, comp, _p(out)))
+        return out
+
+    def set_sources(self, cell, amp, f0, t0):
+        cell = np.ascontiguousarray(cell, dtype=np.int64)
+        _ck(lib().mfd_yee_set_sources(self.h, len(cell), _p(cell), _p(_f64(amp)), _p(_f64(f0)), _p(_f64(t0))))
+
+    def set_probes(self, cell, capacity):
+        cell = np.ascontiguousarray(cell, dtype=np.int64)
+        _ck(lib().mfd_yee_set_probes(self.h, len(cell), _p(cell), int(capacity)))
+        self.nprobe = len(cell)
+
+    def step(self, n):
+        _ck(lib().mfd_yee_step(self.h, int(n)))
+
+    def step_timed(self, n):
+        ms = np.zeros(1)
+        _ck(lib().mfd_yee_step_timed(self.h, int(n), _p(ms)))
+        return float(ms[0])
+
+    def read_probes(self):
+        steps = C.c_int64(0)
+        _ck(lib().mfd_yee_read_probes(self.h, None, C.byref(steps)))
+        out = np.zeros((steps.value, self.nprobe))
+        if steps.value and self.nprobe:
+            _ck(lib().mfd_yee_read_probes(self.h, _p(out), C.byref(steps)))
+        return out
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().mfd_yee_destroy(self.h)
                 self.h = None
         except Exception:
             pass
@@ -383,6 +489,13 @@ class Sim:
         _ck(lib().mfd_energy(self.h, _p(u)))
         return float(u[0])
 
+    def dispersion(self, stride, nt, h_line, c_ref, jmax, spectrum=True):
+        """mfd_sim_dispersion: the analysis of the probe series (probes = the line)."""
+        spec, kidx, c, l1 = _dispersion_out(nt, self.nprobe, spectrum)
+        _ck(lib().mfd_sim_dispersion(self.h, int(stride), int(nt), float(h_line), float(c_ref), int(jmax),
+                                     _p(spec), _p(kidx), _p(c), _p(l1)))
+        return spec, kidx, c, float(l1[0])
+
     @property
     def steps(self):
         return int(lib().mfd_sim_steps(self.h))
@@ -443,6 +556,19 @@ class Batch:
         out = np.empty((self.n[dom], self.nrhs) if rhs < 0 else self.n[dom])
         _ck(lib().mfd_batch_get_field(self.h, dom, comp, rhs, _p(out)))
         return out
+
+    def set_gamma(self, dom, gamma):
+        """Per right-hand side hyperviscosity coefficients (mfd_batch_set_gamma)."""
+        g = _f64(gamma)
+        if g.shape != (self.nrhs,):
+            raise ValueError("one gamma per right-hand side")
+        _ck(lib().mfd_batch_set_gamma(self.h, dom, _p(g)))
+
+    def energy(self, dom):
+        """Eq. 20 energy of every right-hand side of domain dom (mfd_batch_energy)."""
+        u = np.empty(self.nrhs)
+        _ck(lib().mfd_batch_energy(self.h, dom, _p(u)))
+        return u
 
     def set_sources(self, dom, node, rhs, amp, f0, t0):
         node = np.ascontiguousarray(node, dtype=np.int64)

@@ -38,7 +38,7 @@ struct BDom {
     int64_t wc0;     // first float4 of the domain's curl weight streams
     int64_t wv0;     // first float4 of the domain's HV weight stream
     int n, nc, nv, ni;
-    float ch, gamma;
+    float ch;
     double dt;
 };
 
@@ -58,6 +58,7 @@ struct BArgs {
     float* A;   // [node][3][R]: Ez, Hx, Hy
     float* B;   // [node][3][R]: E*, Hx', Hy'
     const float* ce;
+    const float* gam;  // [domain][R]: the hyperviscosity coefficient gamma of every right-hand side
     // sources grouped by tile
     const int* src_start;  // ntile + 1
     const int64_t* src_node;
@@ -169,19 +170,20 @@ __device__ void h_tile(const BArgs& a, const BTile t) {
     const float cei = a.ce[i];
     const float* me = a.A + i * 3 * R + 4 * q;
     const float4 ez = ld_f4(me), hx = ld_f4(me + R), hy = ld_f4(me + 2 * R);
+    const float4 gm = ld_f4(a.gam + t.dom * R + 4 * q);
     float4 es, hxn, hyn;
-    es.x = ez.x + cei * (d.gamma * ve.x);
-    es.y = ez.y + cei * (d.gamma * ve.y);
-    es.z = ez.z + cei * (d.gamma * ve.z);
-    es.w = ez.w + cei * (d.gamma * ve.w);
-    hxn.x = hx.x - d.ch * (dy.x - d.gamma * vx.x);
-    hxn.y = hx.y - d.ch * (dy.y - d.gamma * vx.y);
-    hxn.z = hx.z - d.ch * (dy.z - d.gamma * vx.z);
-    hxn.w = hx.w - d.ch * (dy.w - d.gamma * vx.w);
-    hyn.x = hy.x + d.ch * (dx.x + d.gamma * vy.x);
-    hyn.y = hy.y + d.ch * (dx.y + d.gamma * vy.y);
-    hyn.z = hy.z + d.ch * (dx.z + d.gamma * vy.z);
-    hyn.w = hy.w + d.ch * (dx.w + d.gamma * vy.w);
+    es.x = ez.x + cei * (gm.x * ve.x);
+    es.y = ez.y + cei * (gm.y * ve.y);
+    es.z = ez.z + cei * (gm.z * ve.z);
+    es.w = ez.w + cei * (gm.w * ve.w);
+    hxn.x = hx.x - d.ch * (dy.x - gm.x * vx.x);
+    hxn.y = hx.y - d.ch * (dy.y - gm.y * vx.y);
+    hxn.z = hx.z - d.ch * (dy.z - gm.z * vx.z);
+    hxn.w = hx.w - d.ch * (dy.w - gm.w * vx.w);
+    hyn.x = hy.x + d.ch * (dx.x + gm.x * vy.x);
+    hyn.y = hy.y + d.ch * (dx.y + gm.y * vy.y);
+    hyn.z = hy.z + d.ch * (dx.z + gm.z * vy.z);
+    hyn.w = hy.w + d.ch * (dx.w + gm.w * vy.w);
     float* out = a.B + i * 3 * R + 4 * q;
     st_f4(out, es);
     st_f4(out + R, hxn);
@@ -282,6 +284,85 @@ __global__ void __launch_bounds__(BT_THREADS) k_batch(BArgs a) {
 }
 
 // ---- packing: [slice of NPW nodes][chunk][node][4 entries], global ids / FP32 weights
+// Eq. 20 per right-hand side of one domain, with H averaged between the
+// half steps: the H half step of the current state is recomputed (not
+// written) and U_r = sum_i eps_r,i Ez_i^2 + eta0^2 |(H^{n-1/2} + H^{n+1/2}) / 2|^2,
+// eps_r,i = dt / (eps0 ce_i) (PEC nodes hold Ez = 0). One block per tile of the
+// domain writes its partial sums (fixed order, so the result is reproducible).
+template <int R>
+__global__ void __launch_bounds__(BT_THREADS) k_benergy(BArgs a, int dom, int tile0, double eta2, double dt_eps0,
+                                                        double* __restrict__ partial) {
+    constexpr int LPN = R / 4;
+    constexpr int NPW = 32 / LPN;
+    constexpr int TN = 8 * NPW;
+    __shared__ double acc[TN][R];
+    const BTile t = a.tile[tile0 + blockIdx.x];
+    const BDom d = a.dom[dom];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane / LPN, q = lane % LPN;
+    const int slot = warp * NPW + g;
+    const int local = t.first + slot;
+    double u[4] = {0.0, 0.0, 0.0, 0.0};
+    if (local < d.n) {
+        const int64_t sl = local / NPW;
+        const int4* ip = a.idx + d.idx0 + sl * d.ni * NPW + g;
+        const float4* px = a.wx + d.wc0 + sl * d.nc * NPW + g;
+        const float4* py = a.wy + d.wc0 + sl * d.nc * NPW + g;
+        const float4* pv = a.wv + d.wv0 + sl * d.nv * NPW + g;
+        float4 dx = {0, 0, 0, 0}, dy = dx, vx = dx, vy = dx;
+        for (int c = 0; c < d.ni; ++c) {
+            const int4 id = ip[c * NPW];
+            const int ids[4] = {id.x, id.y, id.z, id.w};
+            const float4 wx = c < d.nc ? px[c * NPW] : make_float4(0, 0, 0, 0);
+            const float4 wy = c < d.nc ? py[c * NPW] : make_float4(0, 0, 0, 0);
+            const float4 wv = c < d.nv ? pv[c * NPW] : make_float4(0, 0, 0, 0);
+            const float wxs[4] = {wx.x, wx.y, wx.z, wx.w}, wys[4] = {wy.x, wy.y, wy.z, wy.w};
+            const float wvs[4] = {wv.x, wv.y, wv.z, wv.w};
+            for (int e = 0; e < 4; ++e) {
+                const float* f = a.A + (int64_t)ids[e] * 3 * R + 4 * q;
+                const float4 ez = ld_f4(f), hx = ld_f4(f + R), hy = ld_f4(f + 2 * R);
+                dx = f4_fma(wxs[e], ez, dx);
+                dy = f4_fma(wys[e], ez, dy);
+                vx = f4_fma(wvs[e], hx, vx);
+                vy = f4_fma(wvs[e], hy, vy);
+            }
+        }
+        const int64_t i = d.node0 + local;
+        const float cei = a.ce[i];
+        const float* me = a.A + i * 3 * R + 4 * q;
+        const float4 ez = ld_f4(me), hx = ld_f4(me + R), hy = ld_f4(me + 2 * R);
+        const float4 gm = ld_f4(a.gam + dom * R + 4 * q);
+        const float ezs[4] = {ez.x, ez.y, ez.z, ez.w}, hxs[4] = {hx.x, hx.y, hx.z, hx.w};
+        const float hys[4] = {hy.x, hy.y, hy.z, hy.w}, gs[4] = {gm.x, gm.y, gm.z, gm.w};
+        const float dxs[4] = {dx.x, dx.y, dx.z, dx.w}, dys[4] = {dy.x, dy.y, dy.z, dy.w};
+        const float vxs[4] = {vx.x, vx.y, vx.z, vx.w}, vys[4] = {vy.x, vy.y, vy.z, vy.w};
+        const double er = cei > 0.0f ? dt_eps0 / (double)cei : 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float hx1 = hxs[k] - d.ch * (dys[k] - gs[k] * vxs[k]);
+            const float hy1 = hys[k] + d.ch * (dxs[k] + gs[k] * vys[k]);
+            const double ax = 0.5 * ((double)hxs[k] + (double)hx1), ay = 0.5 * ((double)hys[k] + (double)hy1);
+            u[k] = er * (double)ezs[k] * (double)ezs[k] + eta2 * (ax * ax + ay * ay);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[slot][4 * q + k] = u[k];
+    __syncthreads();
+    if (threadIdx.x < R) {
+        double s = 0.0;
+        for (int j = 0; j < TN; ++j) s += acc[j][threadIdx.x];
+        partial[(int64_t)blockIdx.x * R + threadIdx.x] = s;
+    }
+}
+
+__global__ void k_benergy_sum(const double* __restrict__ partial, int nblocks, int R, double* __restrict__ u) {
+    const int r = threadIdx.x;
+    if (r >= R) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * R + r];
+    u[r] = s;
+}
+
 __global__ void k_bpack_idx(const int32_t* __restrict__ src, int stride, int n_use, int64_t N, int chunks, int npw,
                             int64_t node0, int32_t* __restrict__ dst, int64_t total) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -359,7 +440,7 @@ struct BatchDomain {
     const mfd_nodes* nodes = nullptr;
     int64_t node0 = 0;
     int n = 0;
-    double dt = 0, eps0 = 0;
+    double dt = 0, eps0 = 0, mu0 = 0;
     std::vector<int64_t> src_node;
     std::vector<int> src_rhs;
     std::vector<double> src_amp, src_f0, src_t0;
@@ -375,7 +456,7 @@ struct mfd_batch {
     int ndom = 0;
     int64_t ntot = 0;
     std::vector<BatchDomain> dom;
-    DevBuf d_dom, d_tile, idx, wx, wy, wv, A, B, ce, counter, pstep0, bar;
+    DevBuf d_dom, d_tile, idx, wx, wy, wv, A, B, ce, gam, counter, pstep0, bar;
     DevBuf src_start, src_node, src_rhs, src_amp, src_f0, src_t0;
     DevBuf prb_start, prb_node, prb_slot, prb_buf;
     int ntile = 0;
@@ -490,6 +571,7 @@ BArgs make_args(mfd_batch* b, int nsteps) {
     a.A = b->A.as<float>();
     a.B = b->B.as<float>();
     a.ce = b->ce.as<const float>();
+    a.gam = b->gam.as<const float>();
     a.src_start = b->src_start.as<const int>();
     a.src_node = b->src_node.as<const int64_t>();
     a.src_rhs = b->src_rhs.as<const int>();
@@ -558,6 +640,7 @@ mfd_status mfd_batch_create(mfd_ctx* ctx, int ndom, const mfd_sim_desc* descs, i
     const int NPW = 32 / (nrhs / 4);
     b->tile_nodes = 8 * NPW;
     std::vector<BDom> hd(ndom);
+    std::vector<float> gam_h;
     int64_t node0 = 0, idx0 = 0, wc0 = 0, wv0 = 0;
     for (int d = 0; d < ndom; ++d) {
         const mfd_sim_desc& s = descs[d];
@@ -577,6 +660,8 @@ mfd_status mfd_batch_create(mfd_ctx* ctx, int ndom, const mfd_sim_desc* descs, i
         D.n = (int)nd->n;
         D.dt = s.dt;
         D.eps0 = s.eps0;
+        D.mu0 = s.mu0;
+        for (int r = 0; r < nrhs; ++r) gam_h.push_back((float)s.gamma);
         BDom& h = hd[d];
         h.node0 = node0;
         h.n = D.n;
@@ -584,7 +669,6 @@ mfd_status mfd_batch_create(mfd_ctx* ctx, int ndom, const mfd_sim_desc* descs, i
         h.nv = (hw->n_use + 3) / 4;
         h.ni = std::max(h.nc, h.nv);
         h.ch = (float)(s.dt / s.mu0);
-        h.gamma = (float)s.gamma;
         h.dt = s.dt;
         const int64_t slices = (D.n + NPW - 1) / NPW;
         h.idx0 = idx0;
@@ -604,7 +688,8 @@ mfd_status mfd_batch_create(mfd_ctx* ctx, int ndom, const mfd_sim_desc* descs, i
     if ((st = b->idx.alloc(idx0 * 16)) || (st = b->wx.alloc(wc0 * 16)) || (st = b->wy.alloc(wc0 * 16)) ||
         (st = b->wv.alloc(wv0 * 16)) || (st = b->A.alloc(node0 * 3 * R * 4)) || (st = b->B.alloc(node0 * 3 * R * 4)) ||
         (st = b->ce.alloc(node0 * 4)) || (st = b->counter.alloc(8)) || (st = b->pstep0.alloc(8)) ||
-        (st = b->bar.alloc(16)) || (st = upload_vec(ctx, b->d_dom, hd)) || (st = upload_vec(ctx, b->d_tile, b->tiles)))
+        (st = b->bar.alloc(16)) || (st = upload_vec(ctx, b->d_dom, hd)) || (st = upload_vec(ctx, b->d_tile, b->tiles)) ||
+        (st = upload_vec(ctx, b->gam, gam_h)))
         return bail(st);
     cudaStream_t s = ctx->stream;
     cudaMemsetAsync(b->A.p, 0, b->A.bytes, s);
@@ -836,6 +921,48 @@ mfd_status mfd_batch_read_probes(mfd_batch* b, int dom, double* host, int64_t* s
         for (int p = 0; p < np; ++p)
             for (int r = 0; r < b->R; ++r)
                 host[(k * np + p) * b->R + r] = tmp[(k * b->prb_slots + D.prb_slot0 + p) * b->R + r];
+    return MFD_OK;
+}
+
+mfd_status mfd_batch_set_gamma(mfd_batch* b, int dom, const double* gamma) {
+    if (!b || !gamma || dom < 0 || dom >= b->ndom) return fail(MFD_ERR_ARG, "bad arguments");
+    std::vector<float> g(b->R);
+    for (int r = 0; r < b->R; ++r) {
+        if (!std::isfinite(gamma[r])) return fail(MFD_ERR_ARG, "gamma must be finite");
+        g[r] = (float)gamma[r];
+    }
+    MFD_CUDA(cudaSetDevice(b->ctx->device));
+    MFD_CUDA(cudaMemcpyAsync(b->gam.as<float>() + (size_t)dom * b->R, g.data(), b->R * 4, cudaMemcpyHostToDevice,
+                             b->ctx->stream));
+    MFD_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    return MFD_OK;
+}
+
+mfd_status mfd_batch_energy(mfd_batch* b, int dom, double* u) {
+    if (!b || !u || dom < 0 || dom >= b->ndom) return fail(MFD_ERR_ARG, "bad arguments");
+    MFD_CUDA(cudaSetDevice(b->ctx->device));
+    int tile0 = 0;
+    for (int d = 0; d < dom; ++d) tile0 += (b->dom[d].n + b->tile_nodes - 1) / b->tile_nodes;
+    const BatchDomain& D = b->dom[dom];
+    const int nt = (D.n + b->tile_nodes - 1) / b->tile_nodes;
+    const int R = b->R;
+    DevBuf part, du;
+    MFD_TRY(part.alloc((size_t)nt * R * 8));
+    MFD_TRY(du.alloc((size_t)R * 8));
+    BArgs a = make_args(b, 0);
+    cudaStream_t s = b->ctx->stream;
+    const double eta2 = D.mu0 / D.eps0, dt_eps0 = D.dt / D.eps0;
+    switch (R) {
+        case 4: k_benergy<4><<<nt, BT_THREADS, 0, s>>>(a, dom, tile0, eta2, dt_eps0, part.as<double>()); break;
+        case 8: k_benergy<8><<<nt, BT_THREADS, 0, s>>>(a, dom, tile0, eta2, dt_eps0, part.as<double>()); break;
+        case 16: k_benergy<16><<<nt, BT_THREADS, 0, s>>>(a, dom, tile0, eta2, dt_eps0, part.as<double>()); break;
+        default: k_benergy<32><<<nt, BT_THREADS, 0, s>>>(a, dom, tile0, eta2, dt_eps0, part.as<double>()); break;
+    }
+    MFD_CUDA(cudaGetLastError());
+    k_benergy_sum<<<1, 32, 0, s>>>(part.as<double>(), nt, R, du.as<double>());
+    MFD_CUDA(cudaGetLastError());
+    MFD_CUDA(cudaMemcpyAsync(u, du.p, R * 8, cudaMemcpyDeviceToHost, s));
+    MFD_CUDA(cudaStreamSynchronize(s));
     return MFD_OK;
 }
 

@@ -128,4 +128,11 @@ mfd_status knn_build(const mfd_nodes* centres, const mfd_nodes* sources, int n, 
 mfd_status weights_solve(const mfd_stencils* st, int n_use, int phs_k, int poly_m, int op, int alpha,
                          double delta, double* d_w);
 
+// ------------------------------------------------------------ dispersion (Sec. 6)
+
+mfd_status dispersion_check(int nx, int nt, double h_line, double dt_sample, int jmax);
+// d_samples: device FP64 [nt][nx]; outputs are host pointers (each may be NULL)
+mfd_status dispersion_run(mfd_ctx* ctx, int nx, int nt, const double* d_samples, double h_line, double dt_sample,
+                          double c_ref, int jmax, double* spectrum, int32_t* kidx, double* c, double* err_l1);
+
 }  // namespace mfd

@@ -9,8 +9,11 @@
 //    padded to a multiple of 4 entries with weight 0 and a valid index.
 //  * fields are array-of-structures: 2D collocated {Ez, Hx, Hy, ce} per node
 //    (one 16-byte gather brings all three fields of a neighbour); staggered
-//    {Hx, Hy} on the H set and Ez + ce on the E set; 3D {Ex, Ey, Ez, ce} and
-//    {Hx, Hy, Hz, 0}. ce = dt / (eps0 eps_r) of the node, 0 at a PEC node in 2D.
+//    {Hx, Hy} on the H set and Ez + ce on the E set; 3D one block per node
+//    {Ex, Ey, Ez, ce, Hx, Hy, Hz, 0} (32 bytes in FP32, one gather), with the
+//    H half step writing E* and H' to separate {., ., ., ce} / {., ., ., 0}
+//    arrays from which the E half step reassembles the block.
+//    ce = dt / (eps0 eps_r) of the node, 0 at a PEC node in 2D.
 //  * weight and index streams are read with L1::no_allocate so that L1 keeps
 //    the gathered fields of the Morton neighbourhood.
 #pragma once
@@ -68,6 +71,38 @@ __device__ __forceinline__ float2 ld_gather(const float2* p) { return __ldg(p); 
 __device__ __forceinline__ double2 ld_gather(const double2* p) { return __ldg(p); }
 __device__ __forceinline__ float ld_gather(const float* p) { return __ldg(p); }
 __device__ __forceinline__ double ld_gather(const double* p) { return __ldg(p); }
+
+// One node of the interleaved 3D state: its E block {Ex, Ey, Ez, ce} followed
+// by its H block {Hx, Hy, Hz, 0} (p points at the E block, 32-byte aligned in
+// FP32). Both blocks come in one 256-bit load (FP32) or two (FP64), so a
+// stencil entry touches one cache line instead of one line per block.
+__device__ __forceinline__ void ld_gather_eh(const float4* p, float4& e, float4& h) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(e.x), "=f"(e.y), "=f"(e.z), "=f"(e.w), "=f"(h.x), "=f"(h.y), "=f"(h.z), "=f"(h.w)
+        : "l"(p));
+}
+__device__ __forceinline__ void ld_gather_eh(const dbl4* p, dbl4& e, dbl4& h) {
+    asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];"
+        : "=d"(e.x), "=d"(e.y), "=d"(e.z), "=d"(e.w)
+        : "l"(p));
+    asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];"
+        : "=d"(h.x), "=d"(h.y), "=d"(h.z), "=d"(h.w)
+        : "l"(p + 1));
+}
+
+// writes one node's E and H blocks of the interleaved 3D state (one 256-bit
+// store in FP32, two in FP64)
+__device__ __forceinline__ void st_eh(float4* p, float4 e, float4 h) {
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(e.x), "f"(e.y), "f"(e.z),
+                 "f"(e.w), "f"(h.x), "f"(h.y), "f"(h.z), "f"(h.w)
+                 : "memory");
+}
+__device__ __forceinline__ void st_eh(dbl4* p, dbl4 e, dbl4 h) {
+    asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(e.x), "d"(e.y), "d"(e.z), "d"(e.w)
+                 : "memory");
+    asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p + 1), "d"(h.x), "d"(h.y), "d"(h.z), "d"(h.w)
+                 : "memory");
+}
 
 __device__ __forceinline__ void st4(float4* p, float4 v) { *p = v; }
 __device__ __forceinline__ void st4(dbl4* p, dbl4 v) {

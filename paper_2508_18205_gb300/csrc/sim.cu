@@ -145,6 +145,15 @@ __global__ void k_sum(const double* __restrict__ partial, int n, double* __restr
     if (threadIdx.x == 0) *out = red[0];
 }
 
+// probe records (T [rec][np]) after steps stride, 2 stride, ... -> FP64 [nt][np]
+template <typename T>
+__global__ void k_probe_samples(const T* __restrict__ buf, int np, int stride, int nt, double* __restrict__ out) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)nt * np) return;
+    const int64_t n = e / np, m = e % np;
+    out[e] = (double)buf[((n + 1) * stride - 1) * np + m];  // record of step (n + 1) stride
+}
+
 }  // namespace mfd
 
 using namespace mfd;
@@ -298,11 +307,10 @@ Launch3D make3d(mfd_sim* sim, int parity) {
     L.kd.gamma = sim->d.gamma;
     L.block[0] = sim->block[0];
     L.block[1] = sim->block[1];
-    DevBuf* H[2] = {&sim->s2, &sim->s3};
-    L.E = sim->s0.p;
+    (void)parity;  // the 3D state is rewritten in place by the E pass
+    L.F = sim->s0.p;
     L.Es = sim->s1.p;
-    L.H = H[parity]->p;
-    L.Hn = H[parity ^ 1]->p;
+    L.Hn = sim->s2.p;
     L.wall = sim->has_mask ? sim->mask.as<const uint8_t>() : nullptr;
     return L;
 }
@@ -317,7 +325,7 @@ void ez_location(mfd_sim* sim, int parity_after, void** base, int* stride) {
         *stride = 1;
     } else {
         *base = (char*)sim->s0.p + 2 * sim->rs;
-        *stride = 4;
+        *stride = 8;
     }
 }
 
@@ -346,7 +354,7 @@ cudaError_t enqueue_step(mfd_sim* sim, cudaEvent_t* ev) {
     cudaStream_t s = sim->ctx->stream;
     cudaError_t e;
     const int p = sim->parity;
-    const int pn = (sim->layout == COLLOC2D) ? p : (p ^ 1);
+    const int pn = (sim->layout == STAG2D) ? (p ^ 1) : p;
     if (ev) cudaEventRecord(ev[0], s);
     if (sim->layout == COLLOC3D) {
         Launch3D L = make3d(sim, p);
@@ -465,8 +473,8 @@ mfd_status mfd_sim_create(mfd_ctx* ctx, const mfd_sim_desc* desc, mfd_sim** out)
             (st = sim->s3.alloc(nh * 2 * rs)) || (st = sim->s4.alloc(ne * rs)))
             return bail(st);
     } else {
-        if ((st = sim->s0.alloc(ne * 4 * rs)) || (st = sim->s1.alloc(ne * 4 * rs)) || (st = sim->s2.alloc(ne * 4 * rs)) ||
-            (st = sim->s3.alloc(ne * 4 * rs)))
+        // 3D: s0 = interleaved state {E block, H block} per node, s1 = E*, s2 = H'
+        if ((st = sim->s0.alloc(ne * 8 * rs)) || (st = sim->s1.alloc(ne * 4 * rs)) || (st = sim->s2.alloc(ne * 4 * rs)))
             return bail(st);
     }
     for (DevBuf* b : {&sim->s0, &sim->s1, &sim->s2, &sim->s3, &sim->s4})
@@ -518,7 +526,7 @@ mfd_status mfd_set_materials(mfd_sim* sim, const double* eps_r, const uint8_t* p
         offset = 0;
     } else {
         ce = sim->s0.p;
-        stride = 4;
+        stride = sim->layout == COLLOC3D ? 8 : 4;
         offset = 3;
     }
     const bool zero_ce = sim->layout != COLLOC3D;
@@ -539,7 +547,7 @@ mfd_status mfd_set_materials(mfd_sim* sim, const double* eps_r, const uint8_t* p
         int st2;
         ez_location(sim, sim->parity, &ez, &st2);
         void* base = sim->layout == COLLOC3D ? sim->s0.p : ez;
-        int stride2 = sim->layout == COLLOC3D ? 4 : st2;
+        int stride2 = st2;
         if (sim->fp64)
             k_zero_held<double><<<g, 256, 0, ctx->stream>>>((double*)base, stride2, sim->mask.as<uint8_t>(), ne,
                                                             sim->layout == COLLOC3D);
@@ -575,14 +583,9 @@ static mfd_status locate(mfd_sim* sim, int comp, void** base, int* stride, int* 
             *offset = comp == MFD_HX ? 0 : 1;
         }
     } else {
-        *stride = 4;
-        if (is_e) {
-            *base = sim->s0.p;
-            *offset = comp - MFD_EX;
-        } else {
-            *base = p ? sim->s3.p : sim->s2.p;
-            *offset = comp - MFD_HX;
-        }
+        *stride = 8;
+        *base = sim->s0.p;
+        *offset = is_e ? comp - MFD_EX : 4 + comp - MFD_HX;
     }
     return MFD_OK;
 }
@@ -794,6 +797,28 @@ mfd_status mfd_read_probes(mfd_sim* sim, double* host, int64_t* steps) {
         for (int64_t i = 0; i < count; ++i) host[i] = tmp[i];
     }
     return MFD_OK;
+}
+
+mfd_status mfd_sim_dispersion(mfd_sim* sim, int stride, int nt, double h_line, double c_ref, int jmax,
+                              double* spectrum, int32_t* kidx, double* c, double* err_l1) {
+    if (!sim || stride < 1) return fail(MFD_ERR_ARG, "mfd_sim_dispersion: NULL sim or stride < 1");
+    const int nx = sim->nprobe;
+    MFD_TRY(dispersion_check(nx, nt, h_line, stride * sim->d.dt, jmax));
+    const int64_t rec = std::min(sim->steps - sim->probe_from, sim->probe_cap);
+    if (rec < (int64_t)nt * stride)
+        return fail(MFD_ERR_STATE, "mfd_sim_dispersion: fewer recorded steps than nt * stride");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    DevBuf s;
+    MFD_TRY(s.alloc((size_t)nx * nt * 8));
+    const unsigned g = (unsigned)(((int64_t)nx * nt + 255) / 256);
+    if (sim->fp64)
+        k_probe_samples<double><<<g, 256, 0, ctx->stream>>>(sim->probe_buf.as<double>(), nx, stride, nt, s.as<double>());
+    else
+        k_probe_samples<float><<<g, 256, 0, ctx->stream>>>(sim->probe_buf.as<float>(), nx, stride, nt, s.as<double>());
+    MFD_CUDA(cudaGetLastError());
+    return dispersion_run(ctx, nx, nt, s.as<double>(), h_line, stride * sim->d.dt, c_ref, jmax, spectrum, kidx, c,
+                          err_l1);
 }
 
 mfd_status mfd_energy(mfd_sim* sim, double* u) {

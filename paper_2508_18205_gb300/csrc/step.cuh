@@ -40,10 +40,9 @@ struct Launch3D {
     Both<void> s;
     Coefs<float> kf;
     Coefs<double> kd;
-    const void* E = nullptr;   // {Ex, Ey, Ez, ce}^n
+    void* F = nullptr;         // per node {Ex, Ey, Ez, ce}^n then {Hx, Hy, Hz, 0}^{n-1/2}
     void* Es = nullptr;        // {E*, ce}
-    const void* H = nullptr;   // {Hx, Hy, Hz, 0}^{n-1/2}
-    void* Hn = nullptr;        // ^{n+1/2}
+    void* Hn = nullptr;        // {Hx, Hy, Hz, 0}^{n+1/2}
     const uint8_t* wall = nullptr;  // bit a: node on a wall normal to axis a
     int block[2] = {256, 256};      // threads per block of the H pass and the E pass
 };

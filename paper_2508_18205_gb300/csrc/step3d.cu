@@ -4,6 +4,11 @@
 //   E pass, node i:  E' = E* + ce curl H', then every component tangential to
 //                    a PEC wall the node sits on is held at 0.
 // curl F = (Dy Fz - Dz Fy, Dz Fx - Dx Fz, Dx Fy - Dy Fx).
+//
+// State: F holds per node the E block {Ex, Ey, Ez, ce} at F[2 i] and the H
+// block {Hx, Hy, Hz, 0} at F[2 i + 1]. Every HV entry needs both blocks of its
+// neighbour, fetched by one 32-byte gather. The H pass writes E* and H' to
+// their own arrays (Es, Hn); the E pass gathers H' and writes both blocks of F.
 #include "kernels.cuh"
 #include "step.cuh"
 
@@ -14,9 +19,8 @@ template <typename T> struct Curl {
 };
 
 template <typename T, int NC, int NV, bool SHARED, bool COMP>
-__device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typename Vec<T>::V4* __restrict__ E,
-                                        const typename Vec<T>::V4* __restrict__ H, int64_t i, Curl<T>& cu,
-                                        T vh[3], T ve[3]) {
+__device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typename Vec<T>::V4* __restrict__ F,
+                                        int64_t i, Curl<T>& cu, T vh[3], T ve[3]) {
     using V4 = typename Vec<T>::V4;
     using Acc = typename AccSel<T, COMP>::type;
     const int nc = NC ? NC : s.nc;
@@ -62,18 +66,19 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
         for (int c = 0; c < ni; ++c) {
             const int4 id = ld_stream(ip + c * 32);
             V4 e[4], h[4];
-            e[0] = ld_gather(E + id.x);
-            e[1] = ld_gather(E + id.y);
-            e[2] = ld_gather(E + id.z);
-            e[3] = ld_gather(E + id.w);
-            if (c < nc) curl4(ld_stream(px + c * 32), ld_stream(py + c * 32), ld_stream(pz + c * 32), e);
             if (c < nv) {
-                h[0] = ld_gather(H + id.x);
-                h[1] = ld_gather(H + id.y);
-                h[2] = ld_gather(H + id.z);
-                h[3] = ld_gather(H + id.w);
-                hv4(ld_stream(pv + c * 32), e, h);
+                ld_gather_eh(F + 2 * (int64_t)id.x, e[0], h[0]);
+                ld_gather_eh(F + 2 * (int64_t)id.y, e[1], h[1]);
+                ld_gather_eh(F + 2 * (int64_t)id.z, e[2], h[2]);
+                ld_gather_eh(F + 2 * (int64_t)id.w, e[3], h[3]);
+            } else {
+                e[0] = ld_gather(F + 2 * (int64_t)id.x);
+                e[1] = ld_gather(F + 2 * (int64_t)id.y);
+                e[2] = ld_gather(F + 2 * (int64_t)id.z);
+                e[3] = ld_gather(F + 2 * (int64_t)id.w);
             }
+            if (c < nc) curl4(ld_stream(px + c * 32), ld_stream(py + c * 32), ld_stream(pz + c * 32), e);
+            if (c < nv) hv4(ld_stream(pv + c * 32), e, h);
         }
     } else {
         const int4* ic = s.idx_c + slice * nc * 32 + lane;
@@ -82,24 +87,20 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
         for (int c = 0; c < nc; ++c) {
             const int4 id = ld_stream(ic + c * 32);
             V4 e[4];
-            e[0] = ld_gather(E + id.x);
-            e[1] = ld_gather(E + id.y);
-            e[2] = ld_gather(E + id.z);
-            e[3] = ld_gather(E + id.w);
+            e[0] = ld_gather(F + 2 * (int64_t)id.x);
+            e[1] = ld_gather(F + 2 * (int64_t)id.y);
+            e[2] = ld_gather(F + 2 * (int64_t)id.z);
+            e[3] = ld_gather(F + 2 * (int64_t)id.w);
             curl4(ld_stream(px + c * 32), ld_stream(py + c * 32), ld_stream(pz + c * 32), e);
         }
 #pragma unroll
         for (int c = 0; c < nv; ++c) {
             const int4 id = ld_stream(iv + c * 32);
             V4 e[4], h[4];
-            e[0] = ld_gather(E + id.x);
-            e[1] = ld_gather(E + id.y);
-            e[2] = ld_gather(E + id.z);
-            e[3] = ld_gather(E + id.w);
-            h[0] = ld_gather(H + id.x);
-            h[1] = ld_gather(H + id.y);
-            h[2] = ld_gather(H + id.z);
-            h[3] = ld_gather(H + id.w);
+            ld_gather_eh(F + 2 * (int64_t)id.x, e[0], h[0]);
+            ld_gather_eh(F + 2 * (int64_t)id.y, e[1], h[1]);
+            ld_gather_eh(F + 2 * (int64_t)id.z, e[2], h[2]);
+            ld_gather_eh(F + 2 * (int64_t)id.w, e[3], h[3]);
             hv4(ld_stream(pv + c * 32), e, h);
         }
     }
@@ -118,17 +119,17 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
 }
 
 template <typename T, int NC, int NV, bool SHARED, bool COMP>
-__global__ void __launch_bounds__(512, 2) k_h3(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V4* __restrict__ E,
+__global__ void __launch_bounds__(512, 2) k_h3(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V4* __restrict__ F,
                                             typename Vec<T>::V4* __restrict__ Es,
-                                            const typename Vec<T>::V4* __restrict__ H,
                                             typename Vec<T>::V4* __restrict__ Hn) {
     using V4 = typename Vec<T>::V4;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= s.n) return;
     Curl<T> cu;
     T vh[3], ve[3];
-    h3_node<T, NC, NV, SHARED, COMP>(s, E, H, i, cu, vh, ve);
-    const V4 h = ld_gather(H + i), e = ld_gather(E + i);
+    h3_node<T, NC, NV, SHARED, COMP>(s, F, i, cu, vh, ve);
+    V4 e, h;
+    ld_gather_eh(F + 2 * i, e, h);
     V4 ho, eo;
     ho.x = h.x + k.ch * (-(cu.dyz - cu.dzy) + k.gamma * vh[0]);
     ho.y = h.y + k.ch * (-(cu.dzx - cu.dxz) + k.gamma * vh[1]);
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(512, 2) k_h3(StencilStreams<T> s, Coefs<T> k, 
 template <typename T, int NC, bool SHARED, bool COMP>
 __global__ void __launch_bounds__(512, 2) k_e3(StencilStreams<T> s, const typename Vec<T>::V4* __restrict__ Hn,
                                             const typename Vec<T>::V4* __restrict__ Es,
-                                            const uint8_t* __restrict__ wall, typename Vec<T>::V4* __restrict__ E) {
+                                            const uint8_t* __restrict__ wall, typename Vec<T>::V4* __restrict__ F) {
     using V4 = typename Vec<T>::V4;
     using Acc = typename AccSel<T, COMP>::type;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -182,6 +183,7 @@ __global__ void __launch_bounds__(512, 2) k_e3(StencilStreams<T> s, const typena
         }
     }
     const V4 e = ld_gather(Es + i);
+    const V4 hown = ld_gather(Hn + i);
     V4 o;
     o.x = e.x + e.w * (a_yz.get() - a_zy.get());
     o.y = e.y + e.w * (a_zx.get() - a_xz.get());
@@ -194,12 +196,11 @@ __global__ void __launch_bounds__(512, 2) k_e3(StencilStreams<T> s, const typena
         if (m & 5u) o.y = T(0);
         if (m & 3u) o.z = T(0);
     }
-    st4(E + i, o);
+    st_eh(F + 2 * i, o, hown);
 }
 
 template <typename T, bool COMP>
-__global__ void __launch_bounds__(256) k_energy3(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V4* __restrict__ E,
-                                                 const typename Vec<T>::V4* __restrict__ H,
+__global__ void __launch_bounds__(256) k_energy3(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V4* __restrict__ F,
                                                  const double* __restrict__ eps_r, double eta2,
                                                  double* __restrict__ partial) {
     using V4 = typename Vec<T>::V4;
@@ -210,10 +211,10 @@ __global__ void __launch_bounds__(256) k_energy3(StencilStreams<T> s, Coefs<T> k
         Curl<T> cu;
         T vh[3], ve[3];
         if (s.idx_v == s.idx_c)
-            h3_node<T, 0, 0, true, COMP>(s, E, H, i, cu, vh, ve);
+            h3_node<T, 0, 0, true, COMP>(s, F, i, cu, vh, ve);
         else
-            h3_node<T, 0, 0, false, COMP>(s, E, H, i, cu, vh, ve);
-        const V4 h = H[i], e = E[i];
+            h3_node<T, 0, 0, false, COMP>(s, F, i, cu, vh, ve);
+        const V4 e = F[2 * i], h = F[2 * i + 1];
         const double h1[3] = {(double)(h.x + k.ch * (-(cu.dyz - cu.dzy) + k.gamma * vh[0])),
                               (double)(h.y + k.ch * (-(cu.dzx - cu.dxz) + k.gamma * vh[1])),
                               (double)(h.z + k.ch * (-(cu.dxy - cu.dyx) + k.gamma * vh[2]))};
@@ -239,19 +240,17 @@ static cudaError_t launch3(const Launch3D& L, const StencilStreams<T>& s, const 
     const int block = L.block[pass];
     const unsigned grid = (unsigned)((s.n + block - 1) / block);
     const bool shared = s.idx_v == s.idx_c;
-    const V4* E = static_cast<const V4*>(L.E);
+    V4* F = static_cast<V4*>(L.F);
     V4* Es = static_cast<V4*>(L.Es);
-    const V4* H = static_cast<const V4*>(L.H);
     V4* Hn = static_cast<V4*>(L.Hn);
     if (pass == 0) {
-        if (shared && s.nc == 10 && s.nv == 18) k_h3<T, 10, 18, true, COMP><<<grid, block, 0, st>>>(s, k, E, Es, H, Hn);
-        else if (shared) k_h3<T, 0, 0, true, COMP><<<grid, block, 0, st>>>(s, k, E, Es, H, Hn);
-        else k_h3<T, 0, 0, false, COMP><<<grid, block, 0, st>>>(s, k, E, Es, H, Hn);
+        if (shared && s.nc == 10 && s.nv == 18) k_h3<T, 10, 18, true, COMP><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
+        else if (shared) k_h3<T, 0, 0, true, COMP><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
+        else k_h3<T, 0, 0, false, COMP><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
     } else {
-        V4* Eo = const_cast<V4*>(E);
-        if (shared && s.nc == 10) k_e3<T, 10, true, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, Eo);
-        else if (shared) k_e3<T, 0, true, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, Eo);
-        else k_e3<T, 0, false, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, Eo);
+        if (shared && s.nc == 10) k_e3<T, 10, true, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F);
+        else if (shared) k_e3<T, 0, true, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F);
+        else k_e3<T, 0, false, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F);
     }
     return cudaGetLastError();
 }
@@ -265,11 +264,11 @@ cudaError_t launch_3d(const Launch3D& L, int pass, cudaStream_t st) {
 cudaError_t launch_energy_3d(const Launch3D& L, const double* eps_r, double eta2, double* partial, unsigned grid,
                              cudaStream_t st) {
     if (L.fp64)
-        k_energy3<double, false><<<grid, 256, 0, st>>>(L.s.d, L.kd, (const dbl4*)L.E, (const dbl4*)L.H, eps_r, eta2, partial);
+        k_energy3<double, false><<<grid, 256, 0, st>>>(L.s.d, L.kd, (const dbl4*)L.F, eps_r, eta2, partial);
     else if (L.comp)
-        k_energy3<float, true><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.E, (const float4*)L.H, eps_r, eta2, partial);
+        k_energy3<float, true><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.F, eps_r, eta2, partial);
     else
-        k_energy3<float, false><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.E, (const float4*)L.H, eps_r, eta2, partial);
+        k_energy3<float, false><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.F, eps_r, eta2, partial);
     return cudaGetLastError();
 }
 

@@ -113,13 +113,16 @@ def pec_box(shape, jitter: float, seed: int) -> NodeSet:
                    normal_axes=normal_axes, meta={"kind": "pec_box", "shape": shape})
 
 
-def periodic_box(shape, jitter: float, seed: int, offset=None, seed_line_y=None) -> NodeSet:
+def periodic_box(shape, jitter: float, seed: int, offset=None, seed_line_y=None,
+                 seed_diagonal: bool = False) -> NodeSet:
     """Regular grid of `shape` nodes on the periodic box [0, shape[a]) per axis.
 
     Every node is moved by U(-jitter, jitter) per axis and wrapped into the
     box. `offset` shifts the whole lattice (the H set of the staggered layout
     sits at +(1/2, 1/2)). Nodes whose unshifted y equals `seed_line_y` keep
-    their y coordinate (an equispaced line for Fourier sampling).
+    their y coordinate (an equispaced line for Fourier sampling); with
+    seed_diagonal, the nodes whose unshifted x equals y are not moved (an
+    equispaced diagonal, spacing sqrt(2), for sampling at 45 degrees).
     """
     shape = tuple(int(s) for s in shape)
     d = len(shape)
@@ -131,6 +134,8 @@ def periodic_box(shape, jitter: float, seed: int, offset=None, seed_line_y=None)
         line = xyz[:, 1] == seed_line_y
         jit[line, 1] = 0.0
         jit[line, 0] = 0.0
+    if seed_diagonal:
+        jit[xyz[:, 0] == xyz[:, 1]] = 0.0
     if offset is not None:
         xyz = xyz + np.asarray(offset, dtype=np.float64)
     xyz = xyz + jit
@@ -271,24 +276,34 @@ def tm110_fields_3d(xyz: np.ndarray, L: float, c0: float, mu0: float, t_e: float
 
 
 def gaussian_pulse(xyz: np.ndarray, period_x: float, x0: float, sigma: float, c0: float,
-                   eta0: float, dt: float, wavelength: float | None = None):
-    """Plane pulse along +x on a periodic box (d'Alembert data).
+                   eta0: float, dt: float, wavelength: float | None = None, direction=(1, 0)):
+    """Plane pulse on a periodic square box of side period_x (d'Alembert data).
 
-    Ez(x, 0) = f(x - x0); Hx(-dt/2) = 0; Hy(-dt/2) = -f(x - x0 + c0 dt/2)/eta0, with
-    f(s) = exp(-s^2/(2 sigma^2)) [times cos(2 pi s / wavelength) for a
-    modulated pulse]. s is taken as the minimum image on the period.
+    Along +x (direction (1, 0)): Ez(x, 0) = f(x - x0); Hx(-dt/2) = 0;
+    Hy(-dt/2) = -f(x - x0 + c0 dt/2)/eta0, with f(s) = exp(-s^2/(2 sigma^2))
+    [times cos(2 pi s / wavelength) for a modulated pulse], s the minimum
+    image on the period. For an integer direction (p, q) at angle phi the
+    coordinate is d = x cos(phi) + y sin(phi), periodic with period
+    period_x / sqrt(p^2 + q^2) on the box, and (Eq. 27)
+    Hx = sin(phi) f(d - x0 + c0 dt/2)/eta0, Hy = -cos(phi) f(...)/eta0.
     """
+    p, q = direction
+    norm = math.hypot(p, q)
+    cp, sp = p / norm, q / norm
+    period = period_x / norm
+
     def f(s):
-        s = s - period_x * np.round(s / period_x)
+        s = s - period * np.round(s / period)
         v = np.exp(-s * s / (2.0 * sigma * sigma))
         if wavelength is not None:
             v = v * np.cos(2.0 * np.pi * s / wavelength)
         return v
 
-    x = xyz[:, 0]
-    ez = f(x - x0)
-    hx = np.zeros_like(ez)
-    hy = -f(x - x0 + 0.5 * c0 * dt) / eta0
+    d = xyz[:, 0] * cp + xyz[:, 1] * sp
+    ez = f(d - x0)
+    g = f(d - x0 + 0.5 * c0 * dt) / eta0
+    hx = sp * g if q != 0 else np.zeros_like(ez)
+    hy = -cp * g
     return ez, hx, hy
 
 
