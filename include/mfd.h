@@ -327,7 +327,7 @@ mfd_status mfd_fma_peak(int device, double* fp64_gflops, double* fp32_gflops);
  * cell index j nx + i), then probes. One fused kernel per step; long runs
  * replay a CUDA graph. FP64 results equal the reference arithmetic of Eq. 5
  * taken term by term (no fused multiply-add) bit for bit.
- * 2 <= nx < 2^30, 2 <= ny <= 524280; fields in host arrays are ny x nx FP64. */
+ * 2 <= nx < 2^30, 2 <= ny <= 2097120; fields in host arrays are ny x nx FP64. */
 typedef struct mfd_yee mfd_yee;
 mfd_status mfd_yee_create(mfd_ctx* ctx, int64_t nx, int64_t ny, int precision, double dt, double h, double eps0,
                           double mu0, mfd_yee** out);

@@ -86,6 +86,49 @@ __global__ void k_t_finish(const int64_t* __restrict__ rowptr, const unsigned lo
     for (int64_t p = b; p < e; ++p) w[p].w = T(0);
 }
 
+// chunks of the longest row of every slice of 32 rows
+__global__ void k_t_slice_len(const int64_t* __restrict__ rowptr, int64_t n, int64_t* __restrict__ len) {
+    const int64_t sl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (sl >= (n + 31) / 32) return;
+    int64_t m = 0;
+    for (int64_t j = sl * 32; j < n && j < sl * 32 + 32; ++j) m = max(m, (rowptr[j + 1] - rowptr[j]) / 4);
+    len[sl] = m;
+}
+
+template <typename T>
+__global__ void k_t_slice_fill(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                               const typename Vec<T>::V4* __restrict__ w, int64_t n, const int64_t* __restrict__ off,
+                               int4* __restrict__ scol, typename Vec<T>::V4* __restrict__ sx,
+                               typename Vec<T>::V4* __restrict__ sy, typename Vec<T>::V4* __restrict__ sv) {
+    using V4 = typename Vec<T>::V4;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int64_t sl = j >> 5, lane = j & 31;
+    const int64_t nc = off[sl + 1] - off[sl];
+    const int64_t b = rowptr[j], len = (rowptr[j + 1] - b) / 4;
+    for (int64_t c = 0; c < nc; ++c) {
+        const int64_t d = (off[sl] + c) * 32 + lane;
+        int4 ci;
+        V4 x, y, v;
+        if (c < len) {
+            const int64_t p = b + 4 * c;
+            ci = make_int4(col[p], col[p + 1], col[p + 2], col[p + 3]);
+            x.x = w[p].x; x.y = w[p + 1].x; x.z = w[p + 2].x; x.w = w[p + 3].x;
+            y.x = w[p].y; y.y = w[p + 1].y; y.z = w[p + 2].y; y.w = w[p + 3].y;
+            v.x = w[p].z; v.y = w[p + 1].z; v.z = w[p + 2].z; v.w = w[p + 3].z;
+        } else {
+            ci = make_int4((int)j, (int)j, (int)j, (int)j);
+            x.x = x.y = x.z = x.w = T(0);
+            y = x;
+            v = x;
+        }
+        scol[d] = ci;
+        sx[d] = x;
+        sy[d] = y;
+        sv[d] = v;
+    }
+}
+
 mfd_status adj_build(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* hv, bool fp64, AdjT& out) {
     cudaStream_t s = ctx->stream;
     const int64_t n = curl->st->centres->n;
@@ -140,13 +183,46 @@ mfd_status adj_build(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* h
     }
 #undef FILL
     MFD_CUDA(cudaGetLastError());
+    // the sliced copy the step kernels read
+    const int64_t nsl = (n + 31) / 32;
+    DevBuf slen;
+    MFD_TRY(slen.alloc((nsl + 1) * 8));
+    MFD_TRY(out.off.alloc((nsl + 1) * 8));
+    MFD_CUDA(cudaMemsetAsync(slen.p, 0, (nsl + 1) * 8, s));
+    k_t_slice_len<<<grid(nsl), 256, 0, s>>>(out.rowptr.as<int64_t>(), n, slen.as<int64_t>());
+    MFD_CUDA(cudaGetLastError());
+    size_t tb2 = 0;
+    MFD_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb2, slen.as<int64_t>(), out.off.as<int64_t>(), nsl + 1, s));
+    DevBuf tmp2;
+    MFD_TRY(tmp2.alloc(tb2));
+    MFD_CUDA(cub::DeviceScan::ExclusiveSum(tmp2.p, tb2, slen.as<int64_t>(), out.off.as<int64_t>(), nsl + 1, s));
+    MFD_CUDA(cudaMemcpyAsync(&out.chunks, out.off.as<int64_t>() + nsl, 8, cudaMemcpyDeviceToHost, s));
     MFD_CUDA(cudaStreamSynchronize(s));
+    const int64_t ent = std::max<int64_t>(out.chunks, 1) * 32;
+    MFD_TRY(out.scol.alloc(ent * 16));
+    MFD_TRY(out.sx.alloc(ent * es));
+    MFD_TRY(out.sy.alloc(ent * es));
+    MFD_TRY(out.sv.alloc(ent * es));
+    if (fp64)
+        k_t_slice_fill<double><<<grid(n), 256, 0, s>>>(out.rowptr.as<int64_t>(), out.col.as<int32_t>(), out.w.as<dbl4>(), n,
+                                                       out.off.as<int64_t>(), out.scol.as<int4>(), out.sx.as<dbl4>(),
+                                                       out.sy.as<dbl4>(), out.sv.as<dbl4>());
+    else
+        k_t_slice_fill<float><<<grid(n), 256, 0, s>>>(out.rowptr.as<int64_t>(), out.col.as<int32_t>(), out.w.as<float4>(), n,
+                                                      out.off.as<int64_t>(), out.scol.as<int4>(), out.sx.as<float4>(),
+                                                      out.sy.as<float4>(), out.sv.as<float4>());
+    MFD_CUDA(cudaGetLastError());
+    MFD_CUDA(cudaStreamSynchronize(s));
+    out.col.release();  // the kernels read the sliced copy only
+    out.w.release();
     return MFD_OK;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_a(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                               const typename Vec<T>::V4* __restrict__ w, int64_t n,
+__global__ void __launch_bounds__(256) k_adj_a(const int64_t* __restrict__ off, const int4* __restrict__ scol,
+                                               const typename Vec<T>::V4* __restrict__ sx,
+                                               const typename Vec<T>::V4* __restrict__ sy,
+                                               const typename Vec<T>::V4* __restrict__ sv, int64_t n,
                                                const typename Vec<T>::V4* __restrict__ LA,
                                                typename Vec<T>::V4* __restrict__ LB, T gamma,
                                                const T* __restrict__ e0, const T* __restrict__ e1,
@@ -154,51 +230,67 @@ __global__ void __launch_bounds__(256) k_adj_a(const int64_t* __restrict__ rowpt
     using V4 = typename Vec<T>::V4;
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
-    T sx = 0, sy = 0, sv = 0;
-    for (int64_t p = rowptr[j]; p < rowptr[j + 1]; p += 4) {
-        const int4 c = *reinterpret_cast<const int4*>(col + p);
-        const int cs[4] = {c.x, c.y, c.z, c.w};
+    const int64_t sl = j >> 5;
+    const int64_t base = off[sl] * 32 + (j & 31);
+    const int nc = (int)(off[sl + 1] - off[sl]);
+    T ax = 0, ay = 0, av = 0;
+    for (int c = 0; c < nc; ++c) {
+        const int64_t d = base + (int64_t)c * 32;
+        const int4 id = ld_stream(scol + d);
+        const V4 wx = ld_stream(sx + d), wy = ld_stream(sy + d), wv = ld_stream(sv + d);
+        const int ids[4] = {id.x, id.y, id.z, id.w};
+        const T* wxs = &wx.x;
+        const T* wys = &wy.x;
+        const T* wvs = &wv.x;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const V4 wq = ld_gather(w + p + q);
-            const V4 l = ld_gather(LA + cs[q]);
+            const V4 l = ld_gather(LA + ids[q]);
             const T km = l.w * l.x;  // K mu (0 on PEC nodes, where ce = 0)
-            sx = fma(-wq.y, km, sx);
-            sy = fma(wq.x, km, sy);
-            sv = fma(wq.z, km, sv);
+            ax = fma(-wys[q], km, ax);
+            ay = fma(wxs[q], km, ay);
+            av = fma(wvs[q], km, av);
         }
     }
     const V4 me = ld_gather(LA + j);
     const T mu = me.w == T(0) ? T(0) : me.x;
     V4 o;
-    o.x = mu + gamma * sv;
-    o.y = me.y + sx;
-    o.z = me.z + sy;
+    o.x = mu + gamma * av;
+    o.y = me.y + ax;
+    o.z = me.z + ay;
     o.w = me.w;
     st4(LB + j, o);
     if (me.w != T(0)) g_eps[j] += (double)mu * (-((double)e1[j] - (double)e0[j]) / eps[j]);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_b(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                               const typename Vec<T>::V4* __restrict__ w, int64_t n,
+__global__ void __launch_bounds__(256) k_adj_b(const int64_t* __restrict__ off, const int4* __restrict__ scol,
+                                               const typename Vec<T>::V4* __restrict__ sx,
+                                               const typename Vec<T>::V4* __restrict__ sy,
+                                               const typename Vec<T>::V4* __restrict__ sv, int64_t n,
                                                const typename Vec<T>::V4* __restrict__ LB,
                                                typename Vec<T>::V4* __restrict__ LA, T ch, T gamma) {
     using V4 = typename Vec<T>::V4;
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
+    const int64_t sl = j >> 5;
+    const int64_t base = off[sl] * 32 + (j & 31);
+    const int nc = (int)(off[sl + 1] - off[sl]);
     T vx = 0, vy = 0, cx = 0, cy = 0;
-    for (int64_t p = rowptr[j]; p < rowptr[j + 1]; p += 4) {
-        const int4 c = *reinterpret_cast<const int4*>(col + p);
-        const int cs[4] = {c.x, c.y, c.z, c.w};
+    for (int c = 0; c < nc; ++c) {
+        const int64_t d = base + (int64_t)c * 32;
+        const int4 id = ld_stream(scol + d);
+        const V4 wx = ld_stream(sx + d), wy = ld_stream(sy + d), wv = ld_stream(sv + d);
+        const int ids[4] = {id.x, id.y, id.z, id.w};
+        const T* wxs = &wx.x;
+        const T* wys = &wy.x;
+        const T* wvs = &wv.x;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const V4 wq = ld_gather(w + p + q);
-            const V4 l = ld_gather(LB + cs[q]);
-            vx = fma(wq.z, l.y, vx);
-            vy = fma(wq.z, l.z, vy);
-            cx = fma(wq.x, l.z, cx);  // Dx^T l~Hy
-            cy = fma(wq.y, l.y, cy);  // Dy^T l~Hx
+            const V4 l = ld_gather(LB + ids[q]);
+            vx = fma(wvs[q], l.y, vx);
+            vy = fma(wvs[q], l.z, vy);
+            cx = fma(wxs[q], l.z, cx);  // Dx^T l~Hy
+            cy = fma(wys[q], l.y, cy);  // Dy^T l~Hx
         }
     }
     const V4 me = ld_gather(LB + j);
@@ -213,28 +305,30 @@ __global__ void __launch_bounds__(256) k_adj_b(const int64_t* __restrict__ rowpt
 cudaError_t adj_pass(const AdjArgs& a, int pass, cudaStream_t s) {
     const unsigned g = (unsigned)((a.n + 255) / 256);
     if (a.fp64) {
+        const dbl4 *x = (const dbl4*)a.sx, *y = (const dbl4*)a.sy, *v = (const dbl4*)a.sv;
         if (pass == 0)
-            k_adj_a<double><<<g, 256, 0, s>>>(a.rowptr, a.col, (const dbl4*)a.w, a.n, (const dbl4*)a.LA, (dbl4*)a.LB,
-                                              a.gamma, (const double*)a.e0, (const double*)a.e1, a.eps, a.g_eps);
+            k_adj_a<double><<<g, 256, 0, s>>>(a.off, a.scol, x, y, v, a.n, (const dbl4*)a.LA, (dbl4*)a.LB, a.gamma,
+                                              (const double*)a.e0, (const double*)a.e1, a.eps, a.g_eps);
         else
-            k_adj_b<double><<<g, 256, 0, s>>>(a.rowptr, a.col, (const dbl4*)a.w, a.n, (const dbl4*)a.LB, (dbl4*)a.LA,
-                                              a.ch, a.gamma);
+            k_adj_b<double><<<g, 256, 0, s>>>(a.off, a.scol, x, y, v, a.n, (const dbl4*)a.LB, (dbl4*)a.LA, a.ch,
+                                              a.gamma);
     } else {
+        const float4 *x = (const float4*)a.sx, *y = (const float4*)a.sy, *v = (const float4*)a.sv;
         if (pass == 0)
-            k_adj_a<float><<<g, 256, 0, s>>>(a.rowptr, a.col, (const float4*)a.w, a.n, (const float4*)a.LA,
-                                             (float4*)a.LB, (float)a.gamma, (const float*)a.e0, (const float*)a.e1,
-                                             a.eps, a.g_eps);
+            k_adj_a<float><<<g, 256, 0, s>>>(a.off, a.scol, x, y, v, a.n, (const float4*)a.LA, (float4*)a.LB,
+                                             (float)a.gamma, (const float*)a.e0, (const float*)a.e1, a.eps, a.g_eps);
         else
-            k_adj_b<float><<<g, 256, 0, s>>>(a.rowptr, a.col, (const float4*)a.w, a.n, (const float4*)a.LB,
-                                             (float4*)a.LA, (float)a.ch, (float)a.gamma);
+            k_adj_b<float><<<g, 256, 0, s>>>(a.off, a.scol, x, y, v, a.n, (const float4*)a.LB, (float4*)a.LA,
+                                             (float)a.ch, (float)a.gamma);
     }
     return cudaGetLastError();
 }
 
 template <typename T>
 __global__ void k_adj_probe(T* __restrict__ LA, const T* __restrict__ ez, const int64_t* __restrict__ probe, int np,
-                            double dt) {
+                            double dt, const int64_t* __restrict__ seg0, int k, int64_t min_step) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    if (seg0 && *seg0 + k < min_step) return;
     for (int p = 0; p < np; ++p) {  // serial: a node probed twice gets both terms
         const int64_t i = probe[p];
         LA[4 * i] = LA[4 * i] + (T)(2.0 * dt * (double)ez[i]);
@@ -242,10 +336,10 @@ __global__ void k_adj_probe(T* __restrict__ LA, const T* __restrict__ ez, const 
 }
 
 cudaError_t adj_probe_term(bool fp64, void* LA, const void* ez, const int64_t* probe, int nprobe, double dt,
-                           cudaStream_t s) {
+                           cudaStream_t s, const int64_t* seg0, int k, int64_t min_step) {
     if (nprobe <= 0) return cudaSuccess;
-    if (fp64) k_adj_probe<double><<<1, 32, 0, s>>>((double*)LA, (const double*)ez, probe, nprobe, dt);
-    else k_adj_probe<float><<<1, 32, 0, s>>>((float*)LA, (const float*)ez, probe, nprobe, dt);
+    if (fp64) k_adj_probe<double><<<1, 32, 0, s>>>((double*)LA, (const double*)ez, probe, nprobe, dt, seg0, k, min_step);
+    else k_adj_probe<float><<<1, 32, 0, s>>>((float*)LA, (const float*)ez, probe, nprobe, dt, seg0, k, min_step);
     return cudaGetLastError();
 }
 
@@ -267,9 +361,11 @@ cudaError_t init_lambda(bool fp64, void* LA, const void* A, int64_t n, cudaStrea
 
 template <typename T>
 __global__ void k_adj_src(const T* __restrict__ LA, const int64_t* __restrict__ node, const double* __restrict__ amp,
-                          const double* __restrict__ f0, const double* __restrict__ t0, int nsrc, double t1,
-                          const double* __restrict__ eps, double* __restrict__ g_eps, double* __restrict__ g_amp) {
+                          const double* __restrict__ f0, const double* __restrict__ t0, int nsrc,
+                          const int64_t* __restrict__ seg0, int kstep, double dt, const double* __restrict__ eps,
+                          double* __restrict__ g_eps, double* __restrict__ g_amp) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const double t1 = (double)(*seg0 + kstep + 1) * dt;
     const double pi = 3.14159265358979323846;
     for (int k = 0; k < nsrc; ++k) {
         const int64_t i = node[k];
@@ -284,11 +380,13 @@ __global__ void k_adj_src(const T* __restrict__ LA, const int64_t* __restrict__ 
 }
 
 cudaError_t adj_sources(bool fp64, const void* LA, const int64_t* node, const double* amp, const double* f0,
-                        const double* t0, int nsrc, double t1, const double* eps, double* g_eps, double* g_amp,
-                        cudaStream_t s) {
+                        const double* t0, int nsrc, const int64_t* seg0, int k, double dt, const double* eps,
+                        double* g_eps, double* g_amp, cudaStream_t s) {
     if (nsrc <= 0) return cudaSuccess;
-    if (fp64) k_adj_src<double><<<1, 32, 0, s>>>((const double*)LA, node, amp, f0, t0, nsrc, t1, eps, g_eps, g_amp);
-    else k_adj_src<float><<<1, 32, 0, s>>>((const float*)LA, node, amp, f0, t0, nsrc, t1, eps, g_eps, g_amp);
+    if (fp64)
+        k_adj_src<double><<<1, 32, 0, s>>>((const double*)LA, node, amp, f0, t0, nsrc, seg0, k, dt, eps, g_eps, g_amp);
+    else
+        k_adj_src<float><<<1, 32, 0, s>>>((const float*)LA, node, amp, f0, t0, nsrc, seg0, k, dt, eps, g_eps, g_amp);
     return cudaGetLastError();
 }
 

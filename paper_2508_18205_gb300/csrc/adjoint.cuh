@@ -11,21 +11,34 @@ namespace mfd {
 // with j in S(x_i): CSR with rows padded to a multiple of 4 entries (padding:
 // column j, weight 0) and sorted by column (and operator kind) so that the
 // transposed sums are reproducible. Weights per entry: {w^dx, w^dy, w^hv, 0}.
+//
+// The kernels read the transpose in the sliced layout of the forward streams:
+// rows in slices of 32 (one warp), each slice padded to its longest row (in
+// chunks of 4 entries); chunk c of row 32 s + l at (off[s] + c) * 32 + l, one
+// int4 of columns and one 4-vector per operator (dx, dy, hv weights), so a
+// warp's loads of a chunk are contiguous. Padding: column = the row, weight 0.
 struct AdjT {
     DevBuf rowptr;  // int64 [n + 1]
     DevBuf col;     // int32 [nnz]
     DevBuf w;       // Vec<T>::V4 [nnz]
     int64_t nnz = 0;
     int64_t n = 0;
+    // sliced form
+    DevBuf off;     // int64 [slices + 1], in chunks
+    DevBuf scol;    // int4 [off[slices] * 32]
+    DevBuf sx, sy, sv;  // Vec<T>::V4 [off[slices] * 32]
+    int64_t chunks = 0;
 };
 
 mfd_status adj_build(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* hv, bool fp64, AdjT& out);
 
 struct AdjArgs {
     bool fp64 = false;
-    const int64_t* rowptr = nullptr;
-    const int32_t* col = nullptr;
-    const void* w = nullptr;
+    const int64_t* off = nullptr;
+    const int4* scol = nullptr;
+    const void* sx = nullptr;
+    const void* sy = nullptr;
+    const void* sv = nullptr;
     int64_t n = 0;
     void* LA = nullptr;  // {lambda_E, lambda_Hx, lambda_Hy, ce} (ce = dt / (eps0 eps_r), 0 at PEC)
     void* LB = nullptr;  // {t, lambda~_Hx, lambda~_Hy, ce}
@@ -39,18 +52,21 @@ struct AdjArgs {
 // pass 0: LA -> LB (and the permittivity gradient of this step); pass 1: LB -> LA
 cudaError_t adj_pass(const AdjArgs& a, int pass, cudaStream_t s);
 
-// the probe term dJ/dE^n of J = dt sum_n sum_p (Ez_p^n)^2: LA[p].x += 2 dt Ez[p] at every probe
+// the probe term dJ/dE^n of J = dt sum_n sum_p (Ez_p^n)^2: LA[p].x += 2 dt Ez[p] at every probe.
+// With seg0 (device) the term belongs to step n = *seg0 + k and is skipped when n < min_step
+// (the state before the first recorded step is not an objective term).
 cudaError_t adj_probe_term(bool fp64, void* LA, const void* ez, const int64_t* probe, int nprobe, double dt,
-                           cudaStream_t s);
+                           cudaStream_t s, const int64_t* seg0 = nullptr, int k = 0, int64_t min_step = 0);
 
 // LA = {0, 0, 0, ce} from the state A = {Ez, Hx, Hy, ce}
 cudaError_t init_lambda(bool fp64, void* LA, const void* A, int64_t n, cudaStream_t s);
 
-// soft-source terms of step n -> n + 1 (t1 = t_{n+1}): with mu = Z lambda_E^{n+1},
+// soft-source terms of step n -> n + 1 with n = *seg0 + k (seg0 on the device, so
+// that a captured segment replays for any segment; t1 = t_{n+1}): with mu = Z lambda_E^{n+1},
 // g_amp[k] += mu_k r_k(t1) and g_eps[node_k] += mu_k amp_k r_k(t1) / eps_r
 cudaError_t adj_sources(bool fp64, const void* LA, const int64_t* node, const double* amp, const double* f0,
-                        const double* t0, int nsrc, double t1, const double* eps, double* g_eps, double* g_amp,
-                        cudaStream_t s);
+                        const double* t0, int nsrc, const int64_t* seg0, int k, double dt, const double* eps,
+                        double* g_eps, double* g_amp, cudaStream_t s);
 
 // J += dt sum of squares of `count` probe values (FP64 accumulator)
 cudaError_t probe_energy(bool fp64, const void* buf, int64_t count, double dt, double* J, cudaStream_t s);

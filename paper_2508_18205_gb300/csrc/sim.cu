@@ -970,9 +970,11 @@ mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, doub
     MFD_CUDA(adj_probe_term(f64, LA.p, seg.p, sim->probe_node.as<int64_t>(), sim->nprobe, sim->d.dt, s));
     AdjArgs a;
     a.fp64 = f64;
-    a.rowptr = sim->adj.rowptr.as<int64_t>();
-    a.col = sim->adj.col.as<int32_t>();
-    a.w = sim->adj.w.p;
+    a.off = sim->adj.off.as<int64_t>();
+    a.scol = sim->adj.scol.as<int4>();
+    a.sx = sim->adj.sx.p;
+    a.sy = sim->adj.sy.p;
+    a.sv = sim->adj.sv.p;
     a.n = n;
     a.LA = LA.p;
     a.LB = LB.p;
@@ -980,31 +982,77 @@ mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, doub
     a.gamma = sim->d.gamma;
     a.eps = sim->eps.as<double>();
     a.g_eps = geps.as<double>();
-    for (int64_t g = nseg - 1; g >= 0; --g) {
-        const int64_t s0 = start + g * every;
-        const int64_t len = std::min(every, nsteps - g * every);
-        // recompute the segment from its checkpoint, keeping Ez at every level
-        MFD_CUDA(cudaMemcpyAsync(sim->s0.p, (char*)ckpt.p + g * sbytes, sbytes, cudaMemcpyDeviceToDevice, s));
-        MFD_CUDA(cudaMemcpyAsync(sim->counter.p, &s0, 8, cudaMemcpyHostToDevice, s));
-        sim->steps = s0;
-        MFD_CUDA(copy_ez(f64, sim->s0.p, seg.p, n, s));
-        for (int64_t k = 0; k < len; ++k) {
-            MFD_CUDA(enqueue_step(sim, nullptr));
-            MFD_CUDA(copy_ez(f64, sim->s0.p, (char*)seg.p + (k + 1) * n * rs, n, s));
+    // Backward over the segments. A full segment (every steps) is two CUDA
+    // graphs, captured once and replayed for every full segment: the
+    // recomputation from its checkpoint (keeping Ez of every level) and the
+    // adjoint sweep. The step number of the segment's start lives on the
+    // device (seg0) so the captured source and probe terms follow it.
+    DevBuf seg0;
+    MFD_TRY(seg0.alloc(8));
+    std::vector<int64_t> starts(nseg);  // host copies stay valid until the final sync
+    for (int64_t g = 0; g < nseg; ++g) starts[g] = start + g * every;
+    auto recompute = [&](int64_t len) -> cudaError_t {
+        cudaError_t e = copy_ez(f64, sim->s0.p, seg.p, n, s);
+        for (int64_t k = 0; k < len && e == cudaSuccess; ++k) {
+            e = enqueue_step(sim, nullptr);
+            if (e == cudaSuccess) e = copy_ez(f64, sim->s0.p, (char*)seg.p + (k + 1) * n * rs, n, s);
         }
-        MFD_CUDA(cudaStreamSynchronize(s));  // s0 above lives on the host stack of this iteration
-        for (int64_t k = len - 1; k >= 0; --k) {
-            const int64_t step = s0 + k;  // step -> step + 1
-            MFD_CUDA(adj_sources(f64, LA.p, sim->src_node.as<int64_t>(), sim->src_amp.as<double>(),
-                                 sim->src_f0.as<double>(), sim->src_t0.as<double>(), sim->nsrc,
-                                 (double)(step + 1) * sim->d.dt, sim->eps.as<double>(), geps.as<double>(),
-                                 gamp.as<double>(), s));
-            a.e0 = (char*)seg.p + k * n * rs;
-            a.e1 = (char*)seg.p + (k + 1) * n * rs;
-            MFD_CUDA(adj_pass(a, 0, s));
-            MFD_CUDA(adj_pass(a, 1, s));
-            if (step - start >= 1)
-                MFD_CUDA(adj_probe_term(f64, LA.p, a.e0, sim->probe_node.as<int64_t>(), sim->nprobe, sim->d.dt, s));
+        return e;
+    };
+    auto sweep = [&](int64_t len) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        for (int64_t k = len - 1; k >= 0 && e == cudaSuccess; --k) {  // step seg0 + k -> seg0 + k + 1
+            e = adj_sources(f64, LA.p, sim->src_node.as<int64_t>(), sim->src_amp.as<double>(), sim->src_f0.as<double>(),
+                            sim->src_t0.as<double>(), sim->nsrc, seg0.as<int64_t>(), (int)k, sim->d.dt,
+                            sim->eps.as<double>(), geps.as<double>(), gamp.as<double>(), s);
+            AdjArgs ak = a;
+            ak.e0 = (char*)seg.p + k * n * rs;
+            ak.e1 = (char*)seg.p + (k + 1) * n * rs;
+            if (e == cudaSuccess) e = adj_pass(ak, 0, s);
+            if (e == cudaSuccess) e = adj_pass(ak, 1, s);
+            if (e == cudaSuccess)
+                e = adj_probe_term(f64, LA.p, ak.e0, sim->probe_node.as<int64_t>(), sim->nprobe, sim->d.dt, s,
+                                   seg0.as<int64_t>(), (int)k, start + 1);
+        }
+        return e;
+    };
+    auto capture = [&](auto&& body, cudaGraphExec_t* out) -> mfd_status {
+        const int64_t steps0 = sim->steps;
+        MFD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = body();
+        cudaGraph_t gr = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(s, &gr);
+        sim->steps = steps0;  // the captured steps have not run
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            cudaGetLastError();
+            return fail(MFD_ERR_CUDA, std::string("gradient graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        e = cudaGraphInstantiate(out, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) return fail(MFD_ERR_CUDA, std::string("gradient graph instantiate: ") + cudaGetErrorString(e));
+        return MFD_OK;
+    };
+    struct GraphGuard {
+        cudaGraphExec_t g = nullptr;
+        ~GraphGuard() {
+            if (g) cudaGraphExecDestroy(g);
+        }
+    } grec, gadj;
+    for (int64_t g = nseg - 1; g >= 0; --g) {
+        const int64_t len = std::min(every, nsteps - g * every);
+        MFD_CUDA(cudaMemcpyAsync(sim->s0.p, (char*)ckpt.p + g * sbytes, sbytes, cudaMemcpyDeviceToDevice, s));
+        MFD_CUDA(cudaMemcpyAsync(sim->counter.p, &starts[g], 8, cudaMemcpyHostToDevice, s));
+        MFD_CUDA(cudaMemcpyAsync(seg0.p, &starts[g], 8, cudaMemcpyHostToDevice, s));
+        sim->steps = starts[g];
+        if (len == every && nseg >= 2) {
+            if (!grec.g) MFD_TRY(capture([&] { return recompute(len); }, &grec.g));
+            if (!gadj.g) MFD_TRY(capture([&] { return sweep(len); }, &gadj.g));
+            MFD_CUDA(cudaGraphLaunch(grec.g, s));
+            MFD_CUDA(cudaGraphLaunch(gadj.g, s));
+        } else {
+            MFD_CUDA(recompute(len));
+            MFD_CUDA(sweep(len));
         }
     }
     // leave the simulation where a plain run of nsteps would

@@ -1,8 +1,9 @@
 // yee.cu -- the FDTD (Yee) scheme for TMz (Eq. 4, Eq. 5) on a periodic grid:
 // the reference the paper compares its meshless method with (Sec. 3, Sec. 6).
 //
-// One fused kernel per step: a block owns a 32 x 8 tile, stages Ez of the tile
-// plus a one-cell ring in shared memory, computes H' of the tile and of the
+// One fused kernel per step: a block of 32 x 8 threads owns a 32 x 32 tile
+// (four cells of a column per thread), stages Ez of the tile plus the one-cell
+// ring the stencil reads in shared memory, computes H' of the tile and of the
 // one-cell ring on its low sides (recomputed, not exchanged: the neighbour
 // computes the same values bit for bit), writes H', then E' of the tile from
 // the staged H'. State ping-pongs between two buffers so that no block reads
@@ -20,7 +21,9 @@
 
 namespace mfd {
 
-constexpr int YT_X = 32, YT_Y = 8;
+constexpr int YT_X = 32, YT_Y = 32;  // tile of cells
+constexpr int YB_Y = 8;               // thread rows: each thread owns YT_Y / YB_Y cells of a column
+constexpr int YR = YT_Y / YB_Y;
 
 __device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
@@ -29,52 +32,77 @@ __device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(
 __device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
 
-template <typename T>
-__global__ void __launch_bounds__(YT_X * YT_Y) k_yee(int nx, int ny, T ch, T ce, const T* __restrict__ ez,
-                                                     const T* __restrict__ hx, const T* __restrict__ hy,
-                                                     T* __restrict__ ez_o, T* __restrict__ hx_o, T* __restrict__ hy_o) {
-    __shared__ T se[YT_Y + 2][YT_X + 2];   // Ez at x0-1 .. x0+32, y0-1 .. y0+8
-    __shared__ T shy[YT_Y][YT_X + 1];      // Hy' at x0-1 .. x0+31, y0 .. y0+7
-    __shared__ T shx[YT_Y + 1][YT_X];      // Hx' at x0 .. x0+31, y0-1 .. y0+7
+// periodic index of v in [-1, n + tile): one compare when the grid is at least
+// one tile wide (BIG), a full reduction otherwise
+template <bool BIG> __device__ __forceinline__ int wrap(int v, int n) {
+    if (BIG) return v < 0 ? v + n : (v >= n ? v - n : v);
+    return ((v % n) + n) % n;
+}
+
+template <typename T, bool BIG>
+__global__ void __launch_bounds__(YT_X * YB_Y, 6) k_yee(int nx, int ny, T ch, T ce, const T* __restrict__ ez,
+                                                        const T* __restrict__ hx, const T* __restrict__ hy,
+                                                        T* __restrict__ ez_o, T* __restrict__ hx_o,
+                                                        T* __restrict__ hy_o) {
+    // staged Ez at x0-1 .. x0+32, y0-1 .. y0+32 (corners unused), new H with the
+    // low-side ring: Hy' at x0-1 .. x0+31, Hx' at y0-1 .. y0+31
+    __shared__ T se[YT_Y + 2][YT_X + 2];
+    __shared__ T shy[YT_Y][YT_X + 1];
+    __shared__ T shx[YT_Y + 1][YT_X];
     const int x0 = blockIdx.x * YT_X, y0 = blockIdx.y * YT_Y;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int t = ty * YT_X + tx;
-    for (int k = t; k < (YT_Y + 2) * (YT_X + 2); k += YT_X * YT_Y) {
-        const int r = k / (YT_X + 2), c = k % (YT_X + 2);
-        // periodic wrap; the tile may be wider than a small grid, so reduce fully
-        const int gx = ((x0 - 1 + c) % nx + nx) % nx, gy = ((y0 - 1 + r) % ny + ny) % ny;
-        se[r][c] = ez[(int64_t)gy * nx + gx];
+    const int i = x0 + tx, gi = wrap<BIG>(i, nx);
+    const int xl = wrap<BIG>(x0 - 1, nx);
+    // every global load of the step is issued before the first barrier: Ez of
+    // the tile and its ring, and the old H of the own cells and of the ring
+    T ohx[YR], ohy[YR], ohl[YR];
+#pragma unroll
+    for (int k = 0; k < YR; ++k) {
+        const int r = ty + k * YB_Y;
+        const int64_t row = (int64_t)wrap<BIG>(y0 + r, ny) * nx;
+        se[r + 1][tx + 1] = ez[row + gi];
+        ohx[k] = hx[row + gi];
+        ohy[k] = hy[row + gi];
+        if (tx == 0) {
+            se[r + 1][0] = ez[row + xl];
+            ohl[k] = hy[row + xl];
+        }
+        if (tx == YT_X - 1) se[r + 1][YT_X + 1] = ez[row + wrap<BIG>(x0 + YT_X, nx)];
     }
+    T ohb = T(0);
+    if (ty == 0) {
+        const int64_t row = (int64_t)wrap<BIG>(y0 - 1, ny) * nx;
+        se[0][tx + 1] = ez[row + gi];
+        ohb = hx[row + gi];
+    }
+    if (ty == YB_Y - 1) se[YT_Y + 1][tx + 1] = ez[(int64_t)wrap<BIG>(y0 + YT_Y, ny) * nx + gi];
     __syncthreads();
-    const int i = x0 + tx, j = y0 + ty;
-    const bool in = i < nx && j < ny;
-    // H' of the own cell: Hx at (i, j + 1/2), Hy at (i + 1/2, j)
-    if (in) {
-        const int64_t g = (int64_t)j * nx + i;
-        const T e = se[ty + 1][tx + 1];
-        const T hxn = rn_sub(hx[g], rn_mul(ch, rn_sub(se[ty + 2][tx + 1], e)));
-        const T hyn = rn_add(hy[g], rn_mul(ch, rn_sub(se[ty + 1][tx + 2], e)));
-        shx[ty + 1][tx] = hxn;
-        shy[ty][tx + 1] = hyn;
-        hx_o[g] = hxn;
-        hy_o[g] = hyn;
+    // H' of the own cells (Hx at (i, j + 1/2), Hy at (i + 1/2, j)) and of the low-side ring
+#pragma unroll
+    for (int k = 0; k < YR; ++k) {
+        const int r = ty + k * YB_Y, j = y0 + r;
+        const T e = se[r + 1][tx + 1];
+        const T hxn = rn_sub(ohx[k], rn_mul(ch, rn_sub(se[r + 2][tx + 1], e)));
+        const T hyn = rn_add(ohy[k], rn_mul(ch, rn_sub(se[r + 1][tx + 2], e)));
+        shx[r + 1][tx] = hxn;
+        shy[r][tx + 1] = hyn;
+        if (i < nx && j < ny) {
+            const int64_t g = (int64_t)j * nx + i;
+            hx_o[g] = hxn;
+            hy_o[g] = hyn;
+        }
+        if (tx == 0) shy[r][0] = rn_add(ohl[k], rn_mul(ch, rn_sub(se[r + 1][1], se[r + 1][0])));
     }
-    // the ring on the low sides: Hy' at (x0 - 1 + 1/2, j), Hx' at (i, y0 - 1 + 1/2)
-    if (tx == 0 && j < ny) {
-        const int gx = x0 == 0 ? nx - 1 : x0 - 1;
-        const T e = se[ty + 1][0];
-        shy[ty][0] = rn_add(hy[(int64_t)j * nx + gx], rn_mul(ch, rn_sub(se[ty + 1][1], e)));
-    }
-    if (ty == 0 && i < nx) {
-        const int gy = y0 == 0 ? ny - 1 : y0 - 1;
-        const T e = se[0][tx + 1];
-        shx[0][tx] = rn_sub(hx[(int64_t)gy * nx + i], rn_mul(ch, rn_sub(se[1][tx + 1], e)));
-    }
+    if (ty == 0) shx[0][tx] = rn_sub(ohb, rn_mul(ch, rn_sub(se[1][tx + 1], se[0][tx + 1])));
     __syncthreads();
-    if (in) {
-        // (Hy(i) - Hy(i-1)) - Hx(j) + Hx(j-1), left to right
-        const T curl = rn_add(rn_sub(rn_sub(shy[ty][tx + 1], shy[ty][tx]), shx[ty + 1][tx]), shx[ty][tx]);
-        ez_o[(int64_t)j * nx + i] = rn_add(se[ty + 1][tx + 1], rn_mul(ce, curl));
+#pragma unroll
+    for (int k = 0; k < YR; ++k) {
+        const int r = ty + k * YB_Y, j = y0 + r;
+        if (i < nx && j < ny) {
+            // (Hy(i) - Hy(i-1)) - Hx(j) + Hx(j-1), left to right
+            const T curl = rn_add(rn_sub(rn_sub(shy[r][tx + 1], shy[r][tx]), shx[r + 1][tx]), shx[r][tx]);
+            ez_o[(int64_t)j * nx + i] = rn_add(se[r + 1][tx + 1], rn_mul(ce, curl));
+        }
     }
 }
 
@@ -148,16 +176,22 @@ constexpr int YEE_GRAPH_STEPS = 32;
 cudaError_t yee_enqueue(mfd_yee* y) {
     cudaStream_t s = y->ctx->stream;
     const dim3 grid((unsigned)((y->nx + YT_X - 1) / YT_X), (unsigned)((y->ny + YT_Y - 1) / YT_Y));
-    const dim3 block(YT_X, YT_Y);
+    const dim3 block(YT_X, YB_Y);
     const int a = y->cur, b = y->cur ^ 1;
-    if (y->fp64)
-        k_yee<double><<<grid, block, 0, s>>>((int)y->nx, (int)y->ny, y->ch, y->ce, y->f[a][0].as<double>(),
-                                             y->f[a][1].as<double>(), y->f[a][2].as<double>(), y->f[b][0].as<double>(),
-                                             y->f[b][1].as<double>(), y->f[b][2].as<double>());
-    else
-        k_yee<float><<<grid, block, 0, s>>>((int)y->nx, (int)y->ny, (float)y->ch, (float)y->ce, y->f[a][0].as<float>(),
-                                            y->f[a][1].as<float>(), y->f[a][2].as<float>(), y->f[b][0].as<float>(),
-                                            y->f[b][1].as<float>(), y->f[b][2].as<float>());
+    const bool big = y->nx >= YT_X && y->ny >= YT_Y;
+    const int nx = (int)y->nx, ny = (int)y->ny;
+    if (y->fp64) {
+        const double *e = y->f[a][0].as<double>(), *hx = y->f[a][1].as<double>(), *hy = y->f[a][2].as<double>();
+        double *eo = y->f[b][0].as<double>(), *hxo = y->f[b][1].as<double>(), *hyo = y->f[b][2].as<double>();
+        if (big) k_yee<double, true><<<grid, block, 0, s>>>(nx, ny, y->ch, y->ce, e, hx, hy, eo, hxo, hyo);
+        else k_yee<double, false><<<grid, block, 0, s>>>(nx, ny, y->ch, y->ce, e, hx, hy, eo, hxo, hyo);
+    } else {
+        const float *e = y->f[a][0].as<float>(), *hx = y->f[a][1].as<float>(), *hy = y->f[a][2].as<float>();
+        float *eo = y->f[b][0].as<float>(), *hxo = y->f[b][1].as<float>(), *hyo = y->f[b][2].as<float>();
+        const float ch = (float)y->ch, ce = (float)y->ce;
+        if (big) k_yee<float, true><<<grid, block, 0, s>>>(nx, ny, ch, ce, e, hx, hy, eo, hxo, hyo);
+        else k_yee<float, false><<<grid, block, 0, s>>>(nx, ny, ch, ce, e, hx, hy, eo, hxo, hyo);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     y->cur = b;
@@ -230,7 +264,7 @@ mfd_status mfd_yee_create(mfd_ctx* ctx, int64_t nx, int64_t ny, int precision, d
     if (!ctx || !out) return fail(MFD_ERR_ARG, "mfd_yee_create: NULL argument");
     *out = nullptr;
     if (nx < 2 || ny < 2 || nx > INT32_MAX / 2 || ny > 65535LL * YT_Y)
-        return fail(MFD_ERR_ARG, "mfd_yee_create: need 2 <= nx < 2^30 and 2 <= ny <= 524280");
+        return fail(MFD_ERR_ARG, "mfd_yee_create: need 2 <= nx < 2^30 and 2 <= ny <= 2097120");
     if (!(dt > 0) || !(h > 0) || !(eps0 > 0) || !(mu0 > 0)) return fail(MFD_ERR_ARG, "dt, h, eps0, mu0 must be > 0");
     if (precision != MFD_FP32 && precision != MFD_FP64) return fail(MFD_ERR_ARG, "precision");
     MFD_CUDA(cudaSetDevice(ctx->device));

@@ -28,7 +28,7 @@ def _yee(ctx, nx, ny, prec, S, fields):
     return y, dt, eps0, mu0
 
 
-@pytest.mark.parametrize("nx,ny,steps", [(40, 32, 100), (10, 6, 67), (33, 17, 1), (64, 64, 130)])
+@pytest.mark.parametrize("nx,ny,steps", [(40, 32, 100), (10, 6, 67), (33, 17, 1), (64, 64, 130), (70, 45, 66)])
 def test_yee_fp64_bit_exact(nx, ny, steps):
     """Ragged tiles (40 = 32 + 8), a grid smaller than one tile, one step,
     and runs long enough to replay the graph from both buffer parities."""
