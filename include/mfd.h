@@ -214,20 +214,28 @@ mfd_status mfd_sim_set_blocks(mfd_sim* sim, int block_h, int block_e);
  * H pass, chosen[1]: E pass; may be NULL) and restores the fields, so the
  * simulation does not advance. */
 mfd_status mfd_sim_autotune(mfd_sim* sim, int reps, int* chosen);
-/* Number of steps taken since the last mfd_set_field(MFD_EZ). */
 /* Gradient of the probe objective J = dt sum_{n=1..N} sum_p (Ez_p^n)^2
  * (Ez at the probes of mfd_set_probes after each of the next N = nsteps
  * steps) with respect to the relative permittivity of every E node and the
  * amplitude of every source, by the discrete adjoint of the step: the exact
  * transpose of Eq. 19 run backwards in time with transposed stencil gathers.
- * The forward run keeps a full-state checkpoint every `every` steps and the
- * backward sweep recomputes one segment at a time from its checkpoint, so
- * device memory grows as nsteps / every states plus `every` Ez fields.
- * Collocated 2D problems; probes must hold >= nsteps steps. g_eps: host,
- * count(E nodes), caller's order; g_amp: host, one per source (may be NULL
- * without sources); *J receives J. The simulation is left after step
- * start + nsteps, with its probes recorded from the start of the call. */
+ * The step is linear in the fields, so the adjoint needs the forward run only
+ * through Ez of every level:
+ *   every == 0: Ez of all nsteps + 1 levels is kept on the device when it fits
+ *     in a quarter of the free device memory (nothing is recomputed), else as
+ *     every == 64;
+ *   every >= 1: the forward run keeps a full-state checkpoint every `every`
+ *     steps and the backward sweep recomputes one segment at a time from its
+ *     checkpoint, so device memory grows as nsteps / every states plus
+ *     `every` Ez fields.
+ * Both give the same gradient up to the order of atomic additions where two
+ * sources or two probes share a node. Collocated 2D problems; probes must hold
+ * >= nsteps steps. g_eps: host, count(E nodes), caller's order; g_amp: host,
+ * one per source (may be NULL without sources); *J receives J. The simulation
+ * is left after step start + nsteps, with its probes recorded from the start
+ * of the call. every < 0 is MFD_ERR_ARG. */
 mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, double* g_eps, double* g_amp);
+/* Number of steps taken since the last mfd_set_field(MFD_EZ). */
 int64_t mfd_sim_steps(const mfd_sim* sim);
 void mfd_sim_destroy(mfd_sim* sim);
 

@@ -512,7 +512,7 @@ class Sim:
         _ck(lib().mfd_sim_autotune(self.h, int(reps), _p(ch)))
         return int(ch[0]), int(ch[1])
 
-    def grad(self, nsteps, every=64, nsrc=0):
+    def grad(self, nsteps, every=0, nsrc=0):
         """(J, dJ/deps_r per E node, dJ/d amplitude per source) over the next nsteps (mfd_grad)."""
         J = np.zeros(1)
         ge = np.zeros(self.ne)
@@ -613,7 +613,7 @@ class ProbeObjective:
     """A collocated TMz run whose probe objective J(eps_r, amp) = dt sum_n sum_p Ez_p^n^2
     is differentiable through ``ProbeEnergy`` (adjoint gradients from mfd_grad)."""
 
-    def __init__(self, sim: Sim, pec, fields, sources, probes, nsteps, every=64):
+    def __init__(self, sim: Sim, pec, fields, sources, probes, nsteps, every=0):
         self.sim, self.pec, self.fields = sim, pec, fields
         self.src, self.probes, self.nsteps, self.every = sources, probes, nsteps, every
 

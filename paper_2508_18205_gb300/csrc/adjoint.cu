@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(256) k_adj_a(const int64_t* __restrict__ off, 
                                                const typename Vec<T>::V4* __restrict__ sv, int64_t n,
                                                const typename Vec<T>::V4* __restrict__ LA,
                                                typename Vec<T>::V4* __restrict__ LB, T gamma,
-                                               const T* __restrict__ e0, const T* __restrict__ e1,
+                                               const T* __restrict__ ez, const int64_t* __restrict__ slot0, int kl,
                                                const double* __restrict__ eps, double* __restrict__ g_eps) {
     using V4 = typename Vec<T>::V4;
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -259,7 +259,10 @@ __global__ void __launch_bounds__(256) k_adj_a(const int64_t* __restrict__ off, 
     o.z = me.z + ay;
     o.w = me.w;
     st4(LB + j, o);
-    if (me.w != T(0)) g_eps[j] += (double)mu * (-((double)e1[j] - (double)e0[j]) / eps[j]);
+    if (me.w != T(0)) {
+        const T* e0 = ez + (*slot0 + kl) * n;
+        g_eps[j] += (double)mu * (-((double)e0[n + j] - (double)e0[j]) / eps[j]);
+    }
 }
 
 template <typename T>
@@ -308,7 +311,7 @@ cudaError_t adj_pass(const AdjArgs& a, int pass, cudaStream_t s) {
         const dbl4 *x = (const dbl4*)a.sx, *y = (const dbl4*)a.sy, *v = (const dbl4*)a.sv;
         if (pass == 0)
             k_adj_a<double><<<g, 256, 0, s>>>(a.off, a.scol, x, y, v, a.n, (const dbl4*)a.LA, (dbl4*)a.LB, a.gamma,
-                                              (const double*)a.e0, (const double*)a.e1, a.eps, a.g_eps);
+                                              (const double*)a.ez, a.slot0, a.k, a.eps, a.g_eps);
         else
             k_adj_b<double><<<g, 256, 0, s>>>(a.off, a.scol, x, y, v, a.n, (const dbl4*)a.LB, (dbl4*)a.LA, a.ch,
                                               a.gamma);
@@ -316,7 +319,7 @@ cudaError_t adj_pass(const AdjArgs& a, int pass, cudaStream_t s) {
         const float4 *x = (const float4*)a.sx, *y = (const float4*)a.sy, *v = (const float4*)a.sv;
         if (pass == 0)
             k_adj_a<float><<<g, 256, 0, s>>>(a.off, a.scol, x, y, v, a.n, (const float4*)a.LA, (float4*)a.LB,
-                                             (float)a.gamma, (const float*)a.e0, (const float*)a.e1, a.eps, a.g_eps);
+                                             (float)a.gamma, (const float*)a.ez, a.slot0, a.k, a.eps, a.g_eps);
         else
             k_adj_b<float><<<g, 256, 0, s>>>(a.off, a.scol, x, y, v, a.n, (const float4*)a.LB, (float4*)a.LA,
                                              (float)a.ch, (float)a.gamma);
@@ -326,20 +329,27 @@ cudaError_t adj_pass(const AdjArgs& a, int pass, cudaStream_t s) {
 
 template <typename T>
 __global__ void k_adj_probe(T* __restrict__ LA, const T* __restrict__ ez, const int64_t* __restrict__ probe, int np,
-                            double dt, const int64_t* __restrict__ seg0, int k, int64_t min_step) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+                            double dt, const int64_t* __restrict__ seg0, int k, int64_t min_step,
+                            const int64_t* __restrict__ slot0, int64_t n) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
     if (seg0 && *seg0 + k < min_step) return;
-    for (int p = 0; p < np; ++p) {  // serial: a node probed twice gets both terms
-        const int64_t i = probe[p];
-        LA[4 * i] = LA[4 * i] + (T)(2.0 * dt * (double)ez[i]);
-    }
+    const T* e = slot0 ? ez + (*slot0 + k) * n : ez;
+    const int64_t i = probe[p];
+    atomicAdd(LA + 4 * i, (T)(2.0 * dt * (double)e[i]));  // a node probed twice gets both terms
 }
 
 cudaError_t adj_probe_term(bool fp64, void* LA, const void* ez, const int64_t* probe, int nprobe, double dt,
-                           cudaStream_t s, const int64_t* seg0, int k, int64_t min_step) {
+                           cudaStream_t s, const int64_t* seg0, int k, int64_t min_step, const int64_t* slot0,
+                           int64_t n) {
     if (nprobe <= 0) return cudaSuccess;
-    if (fp64) k_adj_probe<double><<<1, 32, 0, s>>>((double*)LA, (const double*)ez, probe, nprobe, dt, seg0, k, min_step);
-    else k_adj_probe<float><<<1, 32, 0, s>>>((float*)LA, (const float*)ez, probe, nprobe, dt, seg0, k, min_step);
+    const unsigned g = (unsigned)((nprobe + 127) / 128);
+    if (fp64)
+        k_adj_probe<double><<<g, 128, 0, s>>>((double*)LA, (const double*)ez, probe, nprobe, dt, seg0, k, min_step,
+                                              slot0, n);
+    else
+        k_adj_probe<float><<<g, 128, 0, s>>>((float*)LA, (const float*)ez, probe, nprobe, dt, seg0, k, min_step, slot0,
+                                             n);
     return cudaGetLastError();
 }
 
@@ -364,29 +374,29 @@ __global__ void k_adj_src(const T* __restrict__ LA, const int64_t* __restrict__ 
                           const double* __restrict__ f0, const double* __restrict__ t0, int nsrc,
                           const int64_t* __restrict__ seg0, int kstep, double dt, const double* __restrict__ eps,
                           double* __restrict__ g_eps, double* __restrict__ g_amp) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;  // one thread per source
+    if (k >= nsrc) return;
     const double t1 = (double)(*seg0 + kstep + 1) * dt;
     const double pi = 3.14159265358979323846;
-    for (int k = 0; k < nsrc; ++k) {
-        const int64_t i = node[k];
-        if (LA[4 * i + 3] == T(0)) continue;  // PEC node: held at zero, no dependence
-        const double mu = (double)LA[4 * i];
-        double x = pi * f0[k] * (t1 - t0[k]);
-        x = x * x;
-        const double r = (1.0 - 2.0 * x) * exp(-x);
-        g_amp[k] += mu * r;
-        g_eps[i] += mu * amp[k] * r / eps[i];
-    }
+    const int64_t i = node[k];
+    if (LA[4 * i + 3] == T(0)) return;  // PEC node: held at zero, no dependence
+    const double mu = (double)LA[4 * i];
+    double x = pi * f0[k] * (t1 - t0[k]);
+    x = x * x;
+    const double r = (1.0 - 2.0 * x) * exp(-x);
+    g_amp[k] += mu * r;
+    atomicAdd(g_eps + i, mu * amp[k] * r / eps[i]);  // two sources on one node add in either order
 }
 
 cudaError_t adj_sources(bool fp64, const void* LA, const int64_t* node, const double* amp, const double* f0,
                         const double* t0, int nsrc, const int64_t* seg0, int k, double dt, const double* eps,
                         double* g_eps, double* g_amp, cudaStream_t s) {
     if (nsrc <= 0) return cudaSuccess;
+    const unsigned g = (unsigned)((nsrc + 127) / 128);
     if (fp64)
-        k_adj_src<double><<<1, 32, 0, s>>>((const double*)LA, node, amp, f0, t0, nsrc, seg0, k, dt, eps, g_eps, g_amp);
+        k_adj_src<double><<<g, 128, 0, s>>>((const double*)LA, node, amp, f0, t0, nsrc, seg0, k, dt, eps, g_eps, g_amp);
     else
-        k_adj_src<float><<<1, 32, 0, s>>>((const float*)LA, node, amp, f0, t0, nsrc, seg0, k, dt, eps, g_eps, g_amp);
+        k_adj_src<float><<<g, 128, 0, s>>>((const float*)LA, node, amp, f0, t0, nsrc, seg0, k, dt, eps, g_eps, g_amp);
     return cudaGetLastError();
 }
 
@@ -416,6 +426,21 @@ cudaError_t probe_energy(bool fp64, const void* buf, int64_t count, double dt, d
 template <typename T> __global__ void k_copy_ez(const T* __restrict__ st, T* __restrict__ dst, int64_t n) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) dst[i] = st[4 * i];
+}
+
+template <typename T>
+__global__ void k_copy_ez_level(const T* __restrict__ st, T* __restrict__ hist, int64_t n,
+                                const int64_t* __restrict__ counter, int64_t start) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) hist[(*counter - start) * n + i] = st[4 * i];
+}
+
+cudaError_t copy_ez_level(bool fp64, const void* state, void* hist, int64_t n, const int64_t* counter, int64_t start,
+                          cudaStream_t s) {
+    const unsigned g = (unsigned)((n + 255) / 256);
+    if (fp64) k_copy_ez_level<double><<<g, 256, 0, s>>>((const double*)state, (double*)hist, n, counter, start);
+    else k_copy_ez_level<float><<<g, 256, 0, s>>>((const float*)state, (float*)hist, n, counter, start);
+    return cudaGetLastError();
 }
 
 cudaError_t copy_ez(bool fp64, const void* state, void* dst, int64_t n, cudaStream_t s) {

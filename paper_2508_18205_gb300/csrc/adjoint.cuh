@@ -43,8 +43,11 @@ struct AdjArgs {
     void* LA = nullptr;  // {lambda_E, lambda_Hx, lambda_Hy, ce} (ce = dt / (eps0 eps_r), 0 at PEC)
     void* LB = nullptr;  // {t, lambda~_Hx, lambda~_Hy, ce}
     double ch = 0, gamma = 0;
-    const void* e0 = nullptr;  // Ez^n  (one real per node)
-    const void* e1 = nullptr;  // Ez^{n+1}
+    // Ez of the step's two levels: ez + (*slot0 + k) * n (Ez^n) and the level after it
+    // (Ez^{n+1}); slot0 lives on the device so that a captured segment replays anywhere
+    const void* ez = nullptr;
+    const int64_t* slot0 = nullptr;
+    int k = 0;
     const double* eps = nullptr;
     double* g_eps = nullptr;
 };
@@ -52,11 +55,14 @@ struct AdjArgs {
 // pass 0: LA -> LB (and the permittivity gradient of this step); pass 1: LB -> LA
 cudaError_t adj_pass(const AdjArgs& a, int pass, cudaStream_t s);
 
-// the probe term dJ/dE^n of J = dt sum_n sum_p (Ez_p^n)^2: LA[p].x += 2 dt Ez[p] at every probe.
-// With seg0 (device) the term belongs to step n = *seg0 + k and is skipped when n < min_step
-// (the state before the first recorded step is not an objective term).
+// the probe term dJ/dE^n of J = dt sum_n sum_p (Ez_p^n)^2: LA[p].x += 2 dt Ez[p] at every probe,
+// Ez = ez + (*slot0 + k) * n (ez itself when slot0 is NULL). With seg0 (device) the term
+// belongs to step n = *seg0 + k and is skipped when n < min_step (the state before the first
+// recorded step is not an objective term). One thread per probe (atomic adds: two probes on
+// one node add in either order).
 cudaError_t adj_probe_term(bool fp64, void* LA, const void* ez, const int64_t* probe, int nprobe, double dt,
-                           cudaStream_t s, const int64_t* seg0 = nullptr, int k = 0, int64_t min_step = 0);
+                           cudaStream_t s, const int64_t* seg0 = nullptr, int k = 0, int64_t min_step = 0,
+                           const int64_t* slot0 = nullptr, int64_t n = 0);
 
 // LA = {0, 0, 0, ce} from the state A = {Ez, Hx, Hy, ce}
 cudaError_t init_lambda(bool fp64, void* LA, const void* A, int64_t n, cudaStream_t s);
@@ -73,5 +79,9 @@ cudaError_t probe_energy(bool fp64, const void* buf, int64_t count, double dt, d
 
 // dst[i] = Ez of the V4 state (stride 4)
 cudaError_t copy_ez(bool fp64, const void* state, void* dst, int64_t n, cudaStream_t s);
+// the same into level (*counter - start) of an Ez history (after a step, the counter holds
+// the level just reached), so that captured forward steps fill the history anywhere
+cudaError_t copy_ez_level(bool fp64, const void* state, void* hist, int64_t n, const int64_t* counter,
+                          int64_t start, cudaStream_t s);
 
 }  // namespace mfd

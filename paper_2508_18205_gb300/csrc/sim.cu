@@ -925,7 +925,7 @@ mfd_status mfd_sim_autotune(mfd_sim* sim, int reps, int* chosen) {
 }
 
 mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, double* g_eps, double* g_amp) {
-    if (!sim || nsteps < 1 || every < 1 || !J || !g_eps) return fail(MFD_ERR_ARG, "bad arguments");
+    if (!sim || nsteps < 1 || every < 0 || !J || !g_eps) return fail(MFD_ERR_ARG, "bad arguments");
     if (sim->layout != COLLOC2D) return fail(MFD_ERR_ARG, "mfd_grad supports the collocated 2D layout");
     if (sim->nsrc > 0 && !g_amp) return fail(MFD_ERR_ARG, "g_amp is NULL");
     if (sim->nprobe < 1 || sim->probe_cap < nsteps)
@@ -940,82 +940,50 @@ mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, doub
         MFD_TRY(adj_build(ctx, sim->d.h_curl, sim->d.h_hv, f64, sim->adj));
         sim->adj_ok = true;
     }
-    const int64_t nseg = (nsteps + every - 1) / every;
-    DevBuf ckpt, fin, seg, LA, LB, geps, gamp, Jd;
-    MFD_TRY(ckpt.alloc((size_t)nseg * n * 4 * rs));
-    MFD_TRY(fin.alloc((size_t)n * 4 * rs));
-    MFD_TRY(seg.alloc((size_t)(every + 1) * n * rs));
-    MFD_TRY(LA.alloc((size_t)n * 4 * rs));
-    MFD_TRY(LB.alloc((size_t)n * 4 * rs));
+    // The step is linear in the fields, so the adjoint needs the forward run only
+    // through Ez of every level (the permittivity gradient). With every == 0 that
+    // history is kept whole when it fits in a quarter of the free device memory
+    // and nothing is recomputed; otherwise (every >= 1, or no room) the full state
+    // is checkpointed every `every` (64) steps and each segment is recomputed from
+    // its checkpoint in the backward sweep.
+    size_t free_b = 0, total_b = 0;
+    MFD_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const bool whole = every == 0 && (size_t)(nsteps + 1) * n * rs <= free_b / 4;
+    if (every == 0) every = 64;
+    const int64_t G = whole ? 64 : every;  // steps per captured segment
+    const int64_t nseg = (nsteps + G - 1) / G;
+    const size_t sbytes = (size_t)n * 4 * rs;
+    DevBuf ckpt, fin, hist, LA, LB, geps, gamp, Jd, seg0, slot0;
+    if (!whole) {
+        MFD_TRY(ckpt.alloc((size_t)nseg * sbytes));
+        MFD_TRY(fin.alloc(sbytes));
+    }
+    MFD_TRY(hist.alloc((size_t)((whole ? nsteps : every) + 1) * n * rs));
+    MFD_TRY(LA.alloc(sbytes));
+    MFD_TRY(LB.alloc(sbytes));
     MFD_TRY(geps.alloc((size_t)n * 8));
     MFD_TRY(gamp.alloc(std::max(1, sim->nsrc) * 8));
     MFD_TRY(Jd.alloc(8));
+    MFD_TRY(seg0.alloc(8));
+    MFD_TRY(slot0.alloc(8));
     MFD_CUDA(cudaMemsetAsync(geps.p, 0, geps.bytes, s));
     MFD_CUDA(cudaMemsetAsync(gamp.p, 0, gamp.bytes, s));
     const int64_t start = sim->steps;
     // probes record from the first step of this call
     sim->probe_from = start;
     MFD_CUDA(cudaMemcpyAsync(sim->pstep0.p, &start, 8, cudaMemcpyHostToDevice, s));
-    const size_t sbytes = (size_t)n * 4 * rs;
-    // forward, with a checkpoint of the full state at the start of every segment
+    MFD_CUDA(cudaMemcpyAsync(sim->counter.p, &start, 8, cudaMemcpyHostToDevice, s));
+    std::vector<int64_t> starts(nseg), slots(nseg);  // host sources of async copies: valid until the end
     for (int64_t g = 0; g < nseg; ++g) {
-        MFD_CUDA(cudaMemcpyAsync((char*)ckpt.p + g * sbytes, sim->s0.p, sbytes, cudaMemcpyDeviceToDevice, s));
-        MFD_TRY(mfd_step(sim, std::min(every, nsteps - g * every)));
+        starts[g] = start + g * G;
+        slots[g] = whole ? g * G : 0;
     }
-    MFD_CUDA(cudaMemcpyAsync(fin.p, sim->s0.p, sbytes, cudaMemcpyDeviceToDevice, s));
-    MFD_CUDA(probe_energy(f64, sim->probe_buf.p, nsteps * sim->nprobe, sim->d.dt, Jd.as<double>(), s));
-    // lambda^N: dJ/dE^N at the probes, zero elsewhere
-    MFD_CUDA(init_lambda(f64, LA.p, fin.p, n, s));
-    MFD_CUDA(copy_ez(f64, fin.p, seg.p, n, s));
-    MFD_CUDA(adj_probe_term(f64, LA.p, seg.p, sim->probe_node.as<int64_t>(), sim->nprobe, sim->d.dt, s));
-    AdjArgs a;
-    a.fp64 = f64;
-    a.off = sim->adj.off.as<int64_t>();
-    a.scol = sim->adj.scol.as<int4>();
-    a.sx = sim->adj.sx.p;
-    a.sy = sim->adj.sy.p;
-    a.sv = sim->adj.sv.p;
-    a.n = n;
-    a.LA = LA.p;
-    a.LB = LB.p;
-    a.ch = sim->d.dt / sim->d.mu0;
-    a.gamma = sim->d.gamma;
-    a.eps = sim->eps.as<double>();
-    a.g_eps = geps.as<double>();
-    // Backward over the segments. A full segment (every steps) is two CUDA
-    // graphs, captured once and replayed for every full segment: the
-    // recomputation from its checkpoint (keeping Ez of every level) and the
-    // adjoint sweep. The step number of the segment's start lives on the
-    // device (seg0) so the captured source and probe terms follow it.
-    DevBuf seg0;
-    MFD_TRY(seg0.alloc(8));
-    std::vector<int64_t> starts(nseg);  // host copies stay valid until the final sync
-    for (int64_t g = 0; g < nseg; ++g) starts[g] = start + g * every;
-    auto recompute = [&](int64_t len) -> cudaError_t {
-        cudaError_t e = copy_ez(f64, sim->s0.p, seg.p, n, s);
-        for (int64_t k = 0; k < len && e == cudaSuccess; ++k) {
-            e = enqueue_step(sim, nullptr);
-            if (e == cudaSuccess) e = copy_ez(f64, sim->s0.p, (char*)seg.p + (k + 1) * n * rs, n, s);
+    struct GraphGuard {
+        cudaGraphExec_t g = nullptr;
+        ~GraphGuard() {
+            if (g) cudaGraphExecDestroy(g);
         }
-        return e;
-    };
-    auto sweep = [&](int64_t len) -> cudaError_t {
-        cudaError_t e = cudaSuccess;
-        for (int64_t k = len - 1; k >= 0 && e == cudaSuccess; --k) {  // step seg0 + k -> seg0 + k + 1
-            e = adj_sources(f64, LA.p, sim->src_node.as<int64_t>(), sim->src_amp.as<double>(), sim->src_f0.as<double>(),
-                            sim->src_t0.as<double>(), sim->nsrc, seg0.as<int64_t>(), (int)k, sim->d.dt,
-                            sim->eps.as<double>(), geps.as<double>(), gamp.as<double>(), s);
-            AdjArgs ak = a;
-            ak.e0 = (char*)seg.p + k * n * rs;
-            ak.e1 = (char*)seg.p + (k + 1) * n * rs;
-            if (e == cudaSuccess) e = adj_pass(ak, 0, s);
-            if (e == cudaSuccess) e = adj_pass(ak, 1, s);
-            if (e == cudaSuccess)
-                e = adj_probe_term(f64, LA.p, ak.e0, sim->probe_node.as<int64_t>(), sim->nprobe, sim->d.dt, s,
-                                   seg0.as<int64_t>(), (int)k, start + 1);
-        }
-        return e;
-    };
+    } gfwd, grec, gadj;
     auto capture = [&](auto&& body, cudaGraphExec_t* out) -> mfd_status {
         const int64_t steps0 = sim->steps;
         MFD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -1033,31 +1001,112 @@ mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, doub
         if (e != cudaSuccess) return fail(MFD_ERR_CUDA, std::string("gradient graph instantiate: ") + cudaGetErrorString(e));
         return MFD_OK;
     };
-    struct GraphGuard {
-        cudaGraphExec_t g = nullptr;
-        ~GraphGuard() {
-            if (g) cudaGraphExecDestroy(g);
+    // ---- forward
+    if (whole) {
+        // every step also writes its Ez level into the history (level = counter - start)
+        MFD_CUDA(copy_ez(f64, sim->s0.p, hist.p, n, s));
+        auto fwd = [&](int64_t len) -> cudaError_t {
+            cudaError_t e = cudaSuccess;
+            for (int64_t k = 0; k < len && e == cudaSuccess; ++k) {
+                e = enqueue_step(sim, nullptr);
+                if (e == cudaSuccess) e = copy_ez_level(f64, sim->s0.p, hist.p, n, sim->counter.as<int64_t>(), start, s);
+            }
+            return e;
+        };
+        for (int64_t g = 0; g < nseg; ++g) {
+            const int64_t len = std::min(G, nsteps - g * G);
+            if (len == G && nseg >= 2) {
+                if (!gfwd.g) MFD_TRY(capture([&] { return fwd(len); }, &gfwd.g));
+                MFD_CUDA(cudaGraphLaunch(gfwd.g, s));
+                sim->steps += len;
+            } else {
+                MFD_CUDA(fwd(len));
+            }
         }
-    } grec, gadj;
+    } else {
+        // a checkpoint of the full state at the start of every segment
+        for (int64_t g = 0; g < nseg; ++g) {
+            MFD_CUDA(cudaMemcpyAsync((char*)ckpt.p + g * sbytes, sim->s0.p, sbytes, cudaMemcpyDeviceToDevice, s));
+            MFD_TRY(mfd_step(sim, std::min(G, nsteps - g * G)));
+        }
+        MFD_CUDA(cudaMemcpyAsync(fin.p, sim->s0.p, sbytes, cudaMemcpyDeviceToDevice, s));
+    }
+    MFD_CUDA(probe_energy(f64, sim->probe_buf.p, nsteps * sim->nprobe, sim->d.dt, Jd.as<double>(), s));
+    // lambda^N: dJ/dE^N at the probes, zero elsewhere
+    MFD_CUDA(init_lambda(f64, LA.p, sim->s0.p, n, s));
+    // Ez^N: the last level of the whole history, or staged in level 0 of the segment buffer
+    void* ezN = whole ? (char*)hist.p + (size_t)nsteps * n * rs : hist.p;
+    if (!whole) MFD_CUDA(copy_ez(f64, sim->s0.p, ezN, n, s));
+    MFD_CUDA(adj_probe_term(f64, LA.p, ezN, sim->probe_node.as<int64_t>(), sim->nprobe, sim->d.dt, s));
+    AdjArgs a;
+    a.fp64 = f64;
+    a.off = sim->adj.off.as<int64_t>();
+    a.scol = sim->adj.scol.as<int4>();
+    a.sx = sim->adj.sx.p;
+    a.sy = sim->adj.sy.p;
+    a.sv = sim->adj.sv.p;
+    a.n = n;
+    a.LA = LA.p;
+    a.LB = LB.p;
+    a.ch = sim->d.dt / sim->d.mu0;
+    a.gamma = sim->d.gamma;
+    a.eps = sim->eps.as<double>();
+    a.g_eps = geps.as<double>();
+    a.ez = hist.p;
+    a.slot0 = slot0.as<int64_t>();
+    // ---- backward over the segments; a full segment is a captured graph replayed
+    // for every full segment (the segment's first step and first level live on the
+    // device: seg0, slot0)
+    auto recompute = [&](int64_t len) -> cudaError_t {
+        cudaError_t e = copy_ez(f64, sim->s0.p, hist.p, n, s);
+        for (int64_t k = 0; k < len && e == cudaSuccess; ++k) {
+            e = enqueue_step(sim, nullptr);
+            if (e == cudaSuccess) e = copy_ez(f64, sim->s0.p, (char*)hist.p + (k + 1) * n * rs, n, s);
+        }
+        return e;
+    };
+    auto sweep = [&](int64_t len) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        for (int64_t k = len - 1; k >= 0 && e == cudaSuccess; --k) {  // step seg0 + k -> seg0 + k + 1
+            e = adj_sources(f64, LA.p, sim->src_node.as<int64_t>(), sim->src_amp.as<double>(), sim->src_f0.as<double>(),
+                            sim->src_t0.as<double>(), sim->nsrc, seg0.as<int64_t>(), (int)k, sim->d.dt,
+                            sim->eps.as<double>(), geps.as<double>(), gamp.as<double>(), s);
+            AdjArgs ak = a;
+            ak.k = (int)k;
+            if (e == cudaSuccess) e = adj_pass(ak, 0, s);
+            if (e == cudaSuccess) e = adj_pass(ak, 1, s);
+            if (e == cudaSuccess)
+                e = adj_probe_term(f64, LA.p, hist.p, sim->probe_node.as<int64_t>(), sim->nprobe, sim->d.dt, s,
+                                   seg0.as<int64_t>(), (int)k, start + 1, slot0.as<int64_t>(), n);
+        }
+        return e;
+    };
     for (int64_t g = nseg - 1; g >= 0; --g) {
-        const int64_t len = std::min(every, nsteps - g * every);
-        MFD_CUDA(cudaMemcpyAsync(sim->s0.p, (char*)ckpt.p + g * sbytes, sbytes, cudaMemcpyDeviceToDevice, s));
-        MFD_CUDA(cudaMemcpyAsync(sim->counter.p, &starts[g], 8, cudaMemcpyHostToDevice, s));
+        const int64_t len = std::min(G, nsteps - g * G);
         MFD_CUDA(cudaMemcpyAsync(seg0.p, &starts[g], 8, cudaMemcpyHostToDevice, s));
-        sim->steps = starts[g];
-        if (len == every && nseg >= 2) {
-            if (!grec.g) MFD_TRY(capture([&] { return recompute(len); }, &grec.g));
+        MFD_CUDA(cudaMemcpyAsync(slot0.p, &slots[g], 8, cudaMemcpyHostToDevice, s));
+        const bool graphs = len == G && nseg >= 2;
+        if (!whole) {
+            MFD_CUDA(cudaMemcpyAsync(sim->s0.p, (char*)ckpt.p + g * sbytes, sbytes, cudaMemcpyDeviceToDevice, s));
+            MFD_CUDA(cudaMemcpyAsync(sim->counter.p, &starts[g], 8, cudaMemcpyHostToDevice, s));
+            sim->steps = starts[g];
+            if (graphs) {
+                if (!grec.g) MFD_TRY(capture([&] { return recompute(len); }, &grec.g));
+                MFD_CUDA(cudaGraphLaunch(grec.g, s));
+            } else {
+                MFD_CUDA(recompute(len));
+            }
+        }
+        if (graphs) {
             if (!gadj.g) MFD_TRY(capture([&] { return sweep(len); }, &gadj.g));
-            MFD_CUDA(cudaGraphLaunch(grec.g, s));
             MFD_CUDA(cudaGraphLaunch(gadj.g, s));
         } else {
-            MFD_CUDA(recompute(len));
             MFD_CUDA(sweep(len));
         }
     }
     // leave the simulation where a plain run of nsteps would
     const int64_t end = start + nsteps;
-    MFD_CUDA(cudaMemcpyAsync(sim->s0.p, fin.p, sbytes, cudaMemcpyDeviceToDevice, s));
+    if (!whole) MFD_CUDA(cudaMemcpyAsync(sim->s0.p, fin.p, sbytes, cudaMemcpyDeviceToDevice, s));
     MFD_CUDA(cudaMemcpyAsync(sim->counter.p, &end, 8, cudaMemcpyHostToDevice, s));
     sim->steps = end;
     std::vector<double> gd(n);

@@ -77,11 +77,14 @@ def test_adjoint_matches_oracle(prec, tol):
 
 
 def test_checkpoint_spacing_does_not_change_the_gradient():
+    """Checkpoints every 1, 8 or 1000 steps, or the whole Ez history (every = 0,
+    no recomputation): the same operations in the same order, the same bits."""
     ctx = M.Ctx(0)
     nodes = W.pec_box((17, 17), 0.25, 93)
     src, probes, eps, ez, hx, hy = _setup(nodes, 94)
+    assert len(set(src.node)) == len(src.node) and len(set(probes)) == len(probes)
     out = []
-    for every in (1, 8, 1000):
+    for every in (0, 1, 8, 1000, 64):
         sim = _problem(ctx, nodes, 1)
         out.append(_gpu_grad(sim, nodes, src, probes, eps, ez, hx, hy, 40, every))
     for J, ge, ga in out[1:]:
