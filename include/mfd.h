@@ -177,6 +177,15 @@ mfd_status mfd_set_materials(mfd_sim* sim, const double* eps_r, const uint8_t* p
  * t_n - dt/2 (Eq. 4, Eq. 21). Resets the step counter to 0 when comp == MFD_EZ. */
 mfd_status mfd_set_field(mfd_sim* sim, int comp, int rhs, const double* host);
 mfd_status mfd_get_field(mfd_sim* sim, int comp, int rhs, double* host);
+/* Zero-copy variants of mfd_set_field / mfd_get_field: `dev` is a device
+ * pointer (FP64, caller's node order, on the context's device, e.g. a torch
+ * CUDA tensor's storage) and `stream` the cudaStream_t on which the caller
+ * produces or consumes it (NULL: the legacy default stream). The library's
+ * stream waits for the work already queued on `stream` before it reads or
+ * writes `dev`, and `stream` waits for the library's copy before anything the
+ * caller queues after the call; no host synchronisation. */
+mfd_status mfd_set_field_device(mfd_sim* sim, int comp, int rhs, const double* dev, void* stream);
+mfd_status mfd_get_field_device(mfd_sim* sim, int comp, int rhs, double* dev, void* stream);
 /* Soft Ricker sources (count >= 0): node (E node, caller id), rhs, amplitude,
  * centre frequency f0 and delay t0; r(t) = (1 - 2 a) exp(-a),
  * a = (pi f0 (t - t0))^2, added to Ez after each E update. */
@@ -263,6 +272,10 @@ mfd_status mfd_batch_create(mfd_ctx* ctx, int ndom, const mfd_sim_desc* descs, i
 mfd_status mfd_batch_set_materials(mfd_batch* b, int dom, const double* eps_r, const uint8_t* pec);
 mfd_status mfd_batch_set_field(mfd_batch* b, int dom, int comp, int rhs, const double* host);
 mfd_status mfd_batch_get_field(mfd_batch* b, int dom, int comp, int rhs, double* host);
+/* Zero-copy variants (device FP64 n x nrhs, or n for one rhs; stream ordering
+ * as mfd_set_field_device). */
+mfd_status mfd_batch_set_field_device(mfd_batch* b, int dom, int comp, int rhs, const double* dev, void* stream);
+mfd_status mfd_batch_get_field_device(mfd_batch* b, int dom, int comp, int rhs, double* dev, void* stream);
 /* Soft Ricker sources of domain dom (as mfd_set_sources); rhs[s] selects the
  * right-hand side source s drives. */
 mfd_status mfd_batch_set_sources(mfd_batch* b, int dom, int count, const int64_t* node, const int32_t* rhs,

@@ -61,6 +61,8 @@ _SIGS = {
     "mfd_set_materials": (_I, [_VP, _VP, _VP]),
     "mfd_set_field": (_I, [_VP, _I, _I, _VP]),
     "mfd_get_field": (_I, [_VP, _I, _I, _VP]),
+    "mfd_set_field_device": (_I, [_VP, _I, _I, _VP, _VP]),
+    "mfd_get_field_device": (_I, [_VP, _I, _I, _VP, _VP]),
     "mfd_set_sources": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP]),
     "mfd_set_probes": (_I, [_VP, _I, _VP, _I64]),
     "mfd_step": (_I, [_VP, _I64]),
@@ -100,6 +102,8 @@ _SIGS = {
     "mfd_batch_set_materials": (_I, [_VP, _I, _VP, _VP]),
     "mfd_batch_set_field": (_I, [_VP, _I, _I, _I, _VP]),
     "mfd_batch_get_field": (_I, [_VP, _I, _I, _I, _VP]),
+    "mfd_batch_set_field_device": (_I, [_VP, _I, _I, _I, _VP, _VP]),
+    "mfd_batch_get_field_device": (_I, [_VP, _I, _I, _I, _VP, _VP]),
     "mfd_batch_set_sources": (_I, [_VP, _I, _I, _VP, _VP, _VP, _VP, _VP]),
     "mfd_batch_set_probes": (_I, [_VP, _I, _I, _VP, _I64]),
     "mfd_batch_step": (_I, [_VP, _I64]),
@@ -148,6 +152,23 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _is_cuda_tensor(a):
+    return getattr(a, "is_cuda", False) and hasattr(a, "data_ptr")
+
+
+def _dev_ptr(t):
+    """Device pointer of a contiguous torch CUDA FP64 tensor (raises otherwise)."""
+    import torch
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("device field buffers are contiguous float64 CUDA tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _torch_stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
 def _dispersion_out(nt, nx, want_spectrum):
     spec = np.empty((nt, nx)) if want_spectrum else None
     return spec, np.empty(nt, dtype=np.int32), np.empty(nt), np.zeros(1)
@@ -177,6 +198,33 @@ def hv_search(ctx, curl, hv, dt, eps0, mu0, ez, hx, hy, log10_lo, log10_hi, ncan
                             _p(_f64(hx)), _p(_f64(hy)), float(log10_lo), float(log10_hi), int(ncand), int(rounds),
                             int(nsteps), int(check_every), float(tol), _p(c), _p(hist)))
     return float(c[0]), hist
+
+
+# TEz mode (Sec. 2: TEz is TMz with the roles of E and H interchanged). The
+# TMz step advances (Hx, Hy) at half steps with dt/mu0 and Ez at whole steps
+# with dt/(eps0 eps_r); under (Ez, Hx, Hy, eps0, mu0) <- (Hz, -Ex, -Ey, mu0, eps0)
+# the same step advances TEz: (Ex, Ey) at half steps with dt/eps0 and Hz at
+# whole steps with dt/(mu0 mu_r). So a Sim or Yee created with the constants
+# tez_constants(eps0, mu0) steps TEz fields stored through tez_set / tez_get;
+# its per-node material (set_materials) is then mu_r, the permittivity is
+# uniform, and a wall held at zero holds Hz (a magnetic wall).
+TEZ_FIELDS = {"Hz": (MFD_EZ, 1.0), "Ex": (MFD_HX, -1.0), "Ey": (MFD_HY, -1.0)}
+
+
+def tez_constants(eps0, mu0):
+    """(eps0, mu0) to create a TMz Sim or Yee that steps the TEz mode."""
+    return mu0, eps0
+
+
+def tez_set(obj, name, values):
+    """Sets TEz field `name` ("Hz", "Ex" or "Ey") of a Sim or Yee created with tez_constants."""
+    comp, sign = TEZ_FIELDS[name]
+    obj.set_field(comp, sign * np.asarray(values, dtype=np.float64))
+
+
+def tez_get(obj, name):
+    comp, sign = TEZ_FIELDS[name]
+    return sign * obj.get_field(comp)
 
 
 def fdtd_phase_speed(omega_dt, courant, phi):
@@ -449,9 +497,16 @@ class Sim:
         _ck(lib().mfd_set_materials(self.h, _p(er), _p(pc)))
 
     def set_field(self, comp, values, rhs=0):
+        if _is_cuda_tensor(values):  # zero copy: torch CUDA FP64 tensor on the current stream
+            _ck(lib().mfd_set_field_device(self.h, comp, rhs, _dev_ptr(values), _torch_stream()))
+            return
         _ck(lib().mfd_set_field(self.h, comp, rhs, _p(_f64(values))))
 
-    def get_field(self, comp, rhs=0):
+    def get_field(self, comp, rhs=0, out=None):
+        """Host FP64 array, or, with `out` a torch CUDA FP64 tensor, into it (zero copy)."""
+        if out is not None and _is_cuda_tensor(out):
+            _ck(lib().mfd_get_field_device(self.h, comp, rhs, _dev_ptr(out), _torch_stream()))
+            return out
         n = self.ne if comp <= MFD_EZ else self.nh
         out = np.empty(n)
         _ck(lib().mfd_get_field(self.h, comp, rhs, _p(out)))
@@ -550,9 +605,15 @@ class Batch:
         _ck(lib().mfd_batch_set_materials(self.h, dom, _p(er), _p(pc)))
 
     def set_field(self, dom, comp, values, rhs=-1):
+        if _is_cuda_tensor(values):
+            _ck(lib().mfd_batch_set_field_device(self.h, dom, comp, rhs, _dev_ptr(values), _torch_stream()))
+            return
         _ck(lib().mfd_batch_set_field(self.h, dom, comp, rhs, _p(_f64(values))))
 
-    def get_field(self, dom, comp, rhs=-1):
+    def get_field(self, dom, comp, rhs=-1, out=None):
+        if out is not None and _is_cuda_tensor(out):
+            _ck(lib().mfd_batch_get_field_device(self.h, dom, comp, rhs, _dev_ptr(out), _torch_stream()))
+            return out
         out = np.empty((self.n[dom], self.nrhs) if rhs < 0 else self.n[dom])
         _ck(lib().mfd_batch_get_field(self.h, dom, comp, rhs, _p(out)))
         return out

@@ -16,6 +16,17 @@ mfd_status fail(mfd_status st, const std::string& msg) {
     return st;
 }
 
+mfd_status order_streams(cudaStream_t from, cudaStream_t to) {
+    if (from == to) return MFD_OK;
+    cudaEvent_t e;
+    MFD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaError_t r = cudaEventRecord(e, from);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(to, e, 0);
+    cudaEventDestroy(e);
+    if (r != cudaSuccess) return fail(MFD_ERR_CUDA, std::string("stream ordering: ") + cudaGetErrorString(r));
+    return MFD_OK;
+}
+
 void retain(const mfd_ctx* c) {
     if (c) const_cast<mfd_ctx*>(c)->refs.fetch_add(1);
 }

@@ -763,47 +763,89 @@ mfd_status mfd_batch_set_materials(mfd_batch* b, int dom, const double* eps_r, c
     return MFD_OK;
 }
 
-mfd_status mfd_batch_set_field(mfd_batch* b, int dom, int comp, int rhs, const double* host) {
-    if (!b || !host || dom < 0 || dom >= b->ndom) return fail(MFD_ERR_ARG, "bad arguments");
+static mfd_status batch_field_args(mfd_batch* b, int dom, int comp, int rhs, int* c, int* nr) {
+    if (!b || dom < 0 || dom >= b->ndom) return fail(MFD_ERR_ARG, "bad arguments");
     if (comp != MFD_EZ && comp != MFD_HX && comp != MFD_HY) return fail(MFD_ERR_ARG, "TMz has Ez, Hx, Hy only");
     if (rhs < -1 || rhs >= b->R) return fail(MFD_ERR_ARG, "rhs out of range");
-    MFD_CUDA(cudaSetDevice(b->ctx->device));
+    *c = comp == MFD_EZ ? 0 : (comp == MFD_HX ? 1 : 2);
+    *nr = rhs < 0 ? b->R : 1;
+    return MFD_OK;
+}
+
+// caller-order FP64 values (device, n x nr) into the state
+static mfd_status batch_scatter(mfd_batch* b, int dom, int comp, int rhs, const double* dsrc) {
+    int c, nr;
+    MFD_TRY(batch_field_args(b, dom, comp, rhs, &c, &nr));
     const BatchDomain& D = b->dom[dom];
-    const int nr = rhs < 0 ? b->R : 1;
-    DevBuf tmp;
-    MFD_TRY(tmp.alloc((size_t)D.n * nr * 8));
-    MFD_CUDA(cudaMemcpyAsync(tmp.p, host, (size_t)D.n * nr * 8, cudaMemcpyHostToDevice, b->ctx->stream));
-    const int c = comp == MFD_EZ ? 0 : (comp == MFD_HX ? 1 : 2);
     const int64_t tot = (int64_t)D.n * nr;
     k_bscatter<<<(unsigned)((tot + 255) / 256), 256, 0, b->ctx->stream>>>(
-        tmp.as<double>(), D.nodes->inv.as<int64_t>(), D.n, nr, rhs < 0 ? 0 : rhs, b->A.as<float>(), D.node0, c, b->R);
+        dsrc, D.nodes->inv.as<int64_t>(), D.n, nr, rhs < 0 ? 0 : rhs, b->A.as<float>(), D.node0, c, b->R);
     MFD_CUDA(cudaGetLastError());
     if (comp == MFD_EZ) {  // PEC nodes (ce == 0) stay at zero
         k_bzero_held<<<(unsigned)((D.n + 255) / 256), 256, 0, b->ctx->stream>>>(b->ce.as<float>(), b->A.as<float>(),
                                                                                 D.node0, D.n, b->R);
         MFD_CUDA(cudaGetLastError());
     }
+    return MFD_OK;
+}
+
+static mfd_status batch_gather(mfd_batch* b, int dom, int comp, int rhs, double* ddst) {
+    int c, nr;
+    MFD_TRY(batch_field_args(b, dom, comp, rhs, &c, &nr));
+    const BatchDomain& D = b->dom[dom];
+    const int64_t tot = (int64_t)D.n * nr;
+    k_bgather<<<(unsigned)((tot + 255) / 256), 256, 0, b->ctx->stream>>>(
+        b->A.as<float>(), D.nodes->inv.as<int64_t>(), D.n, nr, rhs < 0 ? 0 : rhs, D.node0, c, b->R, ddst);
+    MFD_CUDA(cudaGetLastError());
+    return MFD_OK;
+}
+
+mfd_status mfd_batch_set_field(mfd_batch* b, int dom, int comp, int rhs, const double* host) {
+    int c, nr;
+    if (!host) return fail(MFD_ERR_ARG, "bad arguments");
+    MFD_TRY(batch_field_args(b, dom, comp, rhs, &c, &nr));
+    MFD_CUDA(cudaSetDevice(b->ctx->device));
+    const size_t bytes = (size_t)b->dom[dom].n * nr * 8;
+    DevBuf tmp;
+    MFD_TRY(tmp.alloc(bytes));
+    MFD_CUDA(cudaMemcpyAsync(tmp.p, host, bytes, cudaMemcpyHostToDevice, b->ctx->stream));
+    MFD_TRY(batch_scatter(b, dom, comp, rhs, tmp.as<double>()));
     MFD_CUDA(cudaStreamSynchronize(b->ctx->stream));
     return MFD_OK;
 }
 
 mfd_status mfd_batch_get_field(mfd_batch* b, int dom, int comp, int rhs, double* host) {
-    if (!b || !host || dom < 0 || dom >= b->ndom) return fail(MFD_ERR_ARG, "bad arguments");
-    if (comp != MFD_EZ && comp != MFD_HX && comp != MFD_HY) return fail(MFD_ERR_ARG, "TMz has Ez, Hx, Hy only");
-    if (rhs < -1 || rhs >= b->R) return fail(MFD_ERR_ARG, "rhs out of range");
+    int c, nr;
+    if (!host) return fail(MFD_ERR_ARG, "bad arguments");
+    MFD_TRY(batch_field_args(b, dom, comp, rhs, &c, &nr));
     MFD_CUDA(cudaSetDevice(b->ctx->device));
-    const BatchDomain& D = b->dom[dom];
-    const int nr = rhs < 0 ? b->R : 1;
+    const size_t bytes = (size_t)b->dom[dom].n * nr * 8;
     DevBuf tmp;
-    MFD_TRY(tmp.alloc((size_t)D.n * nr * 8));
-    const int c = comp == MFD_EZ ? 0 : (comp == MFD_HX ? 1 : 2);
-    const int64_t tot = (int64_t)D.n * nr;
-    k_bgather<<<(unsigned)((tot + 255) / 256), 256, 0, b->ctx->stream>>>(
-        b->A.as<float>(), D.nodes->inv.as<int64_t>(), D.n, nr, rhs < 0 ? 0 : rhs, D.node0, c, b->R, tmp.as<double>());
-    MFD_CUDA(cudaGetLastError());
-    MFD_CUDA(cudaMemcpyAsync(host, tmp.p, (size_t)D.n * nr * 8, cudaMemcpyDeviceToHost, b->ctx->stream));
+    MFD_TRY(tmp.alloc(bytes));
+    MFD_TRY(batch_gather(b, dom, comp, rhs, tmp.as<double>()));
+    MFD_CUDA(cudaMemcpyAsync(host, tmp.p, bytes, cudaMemcpyDeviceToHost, b->ctx->stream));
     MFD_CUDA(cudaStreamSynchronize(b->ctx->stream));
     return MFD_OK;
+}
+
+mfd_status mfd_batch_set_field_device(mfd_batch* b, int dom, int comp, int rhs, const double* dev, void* stream) {
+    int c, nr;
+    if (!dev) return fail(MFD_ERR_ARG, "bad arguments");
+    MFD_TRY(batch_field_args(b, dom, comp, rhs, &c, &nr));
+    MFD_CUDA(cudaSetDevice(b->ctx->device));
+    MFD_TRY(order_streams((cudaStream_t)stream, b->ctx->stream));
+    MFD_TRY(batch_scatter(b, dom, comp, rhs, dev));
+    return order_streams(b->ctx->stream, (cudaStream_t)stream);
+}
+
+mfd_status mfd_batch_get_field_device(mfd_batch* b, int dom, int comp, int rhs, double* dev, void* stream) {
+    int c, nr;
+    if (!dev) return fail(MFD_ERR_ARG, "bad arguments");
+    MFD_TRY(batch_field_args(b, dom, comp, rhs, &c, &nr));
+    MFD_CUDA(cudaSetDevice(b->ctx->device));
+    MFD_TRY(order_streams((cudaStream_t)stream, b->ctx->stream));
+    MFD_TRY(batch_gather(b, dom, comp, rhs, dev));
+    return order_streams(b->ctx->stream, (cudaStream_t)stream);
 }
 
 mfd_status mfd_batch_set_sources(mfd_batch* b, int dom, int count, const int64_t* node, const int32_t* rhs,

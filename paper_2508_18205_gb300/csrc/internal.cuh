@@ -110,6 +110,9 @@ struct mfd_weights {
 
 namespace mfd {
 
+// makes `to` wait for the work queued so far on `from` (an event; nothing if equal)
+mfd_status order_streams(cudaStream_t from, cudaStream_t to);
+
 // reference counting (see above); release frees the object when the count drops to 0
 void retain(const mfd_ctx* c);
 void retain(const mfd_nodes* n);

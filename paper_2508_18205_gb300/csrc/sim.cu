@@ -590,24 +590,18 @@ static mfd_status locate(mfd_sim* sim, int comp, void** base, int* stride, int* 
     return MFD_OK;
 }
 
-mfd_status mfd_set_field(mfd_sim* sim, int comp, int rhs, const double* host) {
-    if (!sim || !host) return fail(MFD_ERR_ARG, "NULL argument");
-    if (rhs != 0) return fail(MFD_ERR_ARG, "rhs out of range");
+// scatter of caller-order FP64 values (device) into component comp of the state
+static mfd_status scatter_field(mfd_sim* sim, int comp, const double* dsrc) {
     mfd_ctx* ctx = sim->ctx;
-    MFD_CUDA(cudaSetDevice(ctx->device));
     void* base;
     int stride, offset;
     const mfd_nodes* set;
     MFD_TRY(locate(sim, comp, &base, &stride, &offset, &set));
-    DevBuf tmp;
-    MFD_TRY(upload(ctx, tmp, host, set->n * 8));
     unsigned g = (unsigned)((set->n + 255) / 256);
     if (sim->fp64)
-        k_scatter<double><<<g, 256, 0, ctx->stream>>>(tmp.as<double>(), set->inv.as<int64_t>(), set->n, (double*)base,
-                                                      stride, offset);
+        k_scatter<double><<<g, 256, 0, ctx->stream>>>(dsrc, set->inv.as<int64_t>(), set->n, (double*)base, stride, offset);
     else
-        k_scatter<float><<<g, 256, 0, ctx->stream>>>(tmp.as<double>(), set->inv.as<int64_t>(), set->n, (float*)base,
-                                                     stride, offset);
+        k_scatter<float><<<g, 256, 0, ctx->stream>>>(dsrc, set->inv.as<int64_t>(), set->n, (float*)base, stride, offset);
     MFD_CUDA(cudaGetLastError());
     if (comp <= MFD_EZ && sim->has_mask) {
         if (sim->fp64)
@@ -624,6 +618,39 @@ mfd_status mfd_set_field(mfd_sim* sim, int comp, int rhs, const double* host) {
         sim->steps = 0;
         sim->probe_from = 0;
     }
+    return MFD_OK;
+}
+
+// gather of component comp into caller-order FP64 values (device)
+static mfd_status gather_field(mfd_sim* sim, int comp, double* ddst, int64_t* count) {
+    mfd_ctx* ctx = sim->ctx;
+    void* base;
+    int stride, offset;
+    const mfd_nodes* set;
+    MFD_TRY(locate(sim, comp, &base, &stride, &offset, &set));
+    if (count) *count = set->n;
+    if (!ddst) return MFD_OK;
+    unsigned g = (unsigned)((set->n + 255) / 256);
+    if (sim->fp64)
+        k_gather<double><<<g, 256, 0, ctx->stream>>>((const double*)base, stride, offset, set->inv.as<int64_t>(), set->n,
+                                                     ddst);
+    else
+        k_gather<float><<<g, 256, 0, ctx->stream>>>((const float*)base, stride, offset, set->inv.as<int64_t>(), set->n,
+                                                    ddst);
+    MFD_CUDA(cudaGetLastError());
+    return MFD_OK;
+}
+
+mfd_status mfd_set_field(mfd_sim* sim, int comp, int rhs, const double* host) {
+    if (!sim || !host) return fail(MFD_ERR_ARG, "NULL argument");
+    if (rhs != 0) return fail(MFD_ERR_ARG, "rhs out of range");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    int64_t n = 0;
+    MFD_TRY(gather_field(sim, comp, nullptr, &n));
+    DevBuf tmp;
+    MFD_TRY(upload(ctx, tmp, host, n * 8));
+    MFD_TRY(scatter_field(sim, comp, tmp.as<double>()));
     MFD_CUDA(cudaStreamSynchronize(ctx->stream));
     return MFD_OK;
 }
@@ -633,23 +660,34 @@ mfd_status mfd_get_field(mfd_sim* sim, int comp, int rhs, double* host) {
     if (rhs != 0) return fail(MFD_ERR_ARG, "rhs out of range");
     mfd_ctx* ctx = sim->ctx;
     MFD_CUDA(cudaSetDevice(ctx->device));
-    void* base;
-    int stride, offset;
-    const mfd_nodes* set;
-    MFD_TRY(locate(sim, comp, &base, &stride, &offset, &set));
+    int64_t n = 0;
+    MFD_TRY(gather_field(sim, comp, nullptr, &n));
     DevBuf tmp;
-    MFD_TRY(tmp.alloc(set->n * 8));
-    unsigned g = (unsigned)((set->n + 255) / 256);
-    if (sim->fp64)
-        k_gather<double><<<g, 256, 0, ctx->stream>>>((const double*)base, stride, offset, set->inv.as<int64_t>(), set->n,
-                                                     tmp.as<double>());
-    else
-        k_gather<float><<<g, 256, 0, ctx->stream>>>((const float*)base, stride, offset, set->inv.as<int64_t>(), set->n,
-                                                    tmp.as<double>());
-    MFD_CUDA(cudaGetLastError());
-    MFD_CUDA(cudaMemcpyAsync(host, tmp.p, set->n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    MFD_TRY(tmp.alloc(n * 8));
+    MFD_TRY(gather_field(sim, comp, tmp.as<double>(), nullptr));
+    MFD_CUDA(cudaMemcpyAsync(host, tmp.p, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
     MFD_CUDA(cudaStreamSynchronize(ctx->stream));
     return MFD_OK;
+}
+
+mfd_status mfd_set_field_device(mfd_sim* sim, int comp, int rhs, const double* dev, void* stream) {
+    if (!sim || !dev) return fail(MFD_ERR_ARG, "NULL argument");
+    if (rhs != 0) return fail(MFD_ERR_ARG, "rhs out of range");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    MFD_TRY(order_streams((cudaStream_t)stream, ctx->stream));  // the values are ready on the caller's stream
+    MFD_TRY(scatter_field(sim, comp, dev));
+    return order_streams(ctx->stream, (cudaStream_t)stream);    // the caller may reuse dev after this
+}
+
+mfd_status mfd_get_field_device(mfd_sim* sim, int comp, int rhs, double* dev, void* stream) {
+    if (!sim || !dev) return fail(MFD_ERR_ARG, "NULL argument");
+    if (rhs != 0) return fail(MFD_ERR_ARG, "rhs out of range");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    MFD_TRY(order_streams((cudaStream_t)stream, ctx->stream));  // the caller is done with dev
+    MFD_TRY(gather_field(sim, comp, dev, nullptr));
+    return order_streams(ctx->stream, (cudaStream_t)stream);
 }
 
 mfd_status mfd_set_sources(mfd_sim* sim, int count, const int64_t* node, const int32_t* rhs, const double* amp,

@@ -132,3 +132,39 @@ def test_handles_may_be_destroyed_in_any_order():
     assert np.all(np.isfinite(sim.get_field(M.MFD_EZ)))
     L.mfd_sim_destroy(sim.h)
     sim.h = None
+
+
+def test_zero_copy_field_io_matches_host_path():
+    """mfd_set_field_device / mfd_get_field_device (torch CUDA tensors on the
+    current stream) give the same state and results as the host path, for a
+    simulation and a batch."""
+    torch = pytest.importorskip("torch")
+    ctx = M.Ctx(0)
+    dt, eps0, mu0, c0, eta0 = W.units(0.5)
+    nodes = W.pec_box((30, 26), 0.25, 71)
+    nd = M.Nodes(ctx, nodes.xyz, nodes.period)
+    st = M.Stencils(nd, nd, 31)
+    cw = M.Weights(st, 12, 3, 2, M.MFD_OP_GRAD)
+    hw = M.Weights(st, 31, 5, 4, M.MFD_OP_LAP_POW, 2)
+    rng = np.random.default_rng(2)
+    f = {c: rng.standard_normal(nodes.n) for c in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)}
+    out = []
+    for device in (False, True):
+        sim = M.Sim(ctx, 2, M.MFD_FP32, dt, eps0, mu0, -4e-3, cw, hw, compensated=True)
+        sim.set_materials(None, nodes.pec)
+        for c, v in f.items():
+            sim.set_field(c, torch.tensor(v, device="cuda") if device else v)
+        sim.step(50)
+        if device:
+            res = [sim.get_field(c, out=torch.empty(nodes.n, dtype=torch.float64, device="cuda")) for c in f]
+            torch.cuda.synchronize()
+            out.append(np.concatenate([r.cpu().numpy() for r in res]))
+        else:
+            out.append(np.concatenate([sim.get_field(c) for c in f]))
+    assert np.array_equal(out[0], out[1])
+    bt = M.Batch(ctx, [(cw, hw, dt, eps0, mu0, -4e-3)], nrhs=4)
+    v = rng.standard_normal((nodes.n, 4))
+    bt.set_field(0, M.MFD_EZ, torch.tensor(v, device="cuda"))
+    back = bt.get_field(0, M.MFD_EZ, out=torch.empty((nodes.n, 4), dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    assert np.array_equal(back.cpu().numpy(), v.astype(np.float32).astype(np.float64))
