@@ -513,7 +513,9 @@ def batched(M, ctx, steps, peak, peak_kind, ndom=256, nrhs=16):
             "nodes": ntot, "value": upd * steps / el, "unit": UNIT, "steps": steps,
             "ms_per_step": el / steps * 1e3, "graph": bt.uses_graph, "setup_s": round(setup_s, 2),
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "traffic": None, "kernel": "k_batch<16>", "peak_kind": peak_kind,
+                         "traffic": traffic_record("k_batch16_256dom", 4) if (ndom, nrhs) == (256, 16) else None,
+                         "traffic_unit": "DRAM bytes per step (the persistent launch runs all steps)",
+                         "kernel": "k_batch<16>", "peak_kind": peak_kind,
                          "algorithmic_bytes_per_step": byt}}
 
 
@@ -718,7 +720,8 @@ def yee(M, ctx, peak, peak_kind, big=8192, steps=1000, nx=1000, pulse_steps=5000
     out["grid"] = {"cells": cells, "steps": steps, "ms_per_step": el / steps * 1e3,
                    "value": 3 * cells * steps / el, "unit": UNIT,
                    "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                                "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": None, "kernel": "k_yee",
+                                "frac": alg / (ms / 1e3) / 1e9 / peak,
+                                "traffic": traffic_record(f"k_yee_{big}", 4), "kernel": "k_yee",
                                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg,
                                 "avg_launch_ms": ms}}
     del y
