@@ -42,7 +42,7 @@ template <bool BIG> __device__ __forceinline__ int wrap(int v, int n) {
 }
 
 template <typename T, bool BIG, int RY = yee_ry<T>()>
-__global__ void __launch_bounds__(YT_X * YB_Y, 6) k_yee(int nx, int ny, T ch, T ce, const T* __restrict__ ez,
+__global__ void __launch_bounds__(YT_X * YB_Y, 8) k_yee(int nx, int ny, T ch, T ce, const T* __restrict__ ez,
                                                         const T* __restrict__ hx, const T* __restrict__ hy,
                                                         T* __restrict__ ez_o, T* __restrict__ hx_o,
                                                         T* __restrict__ hy_o) {
