@@ -714,14 +714,16 @@ def yee(M, ctx, peak, peak_kind, big=8192, steps=1000, nx=1000, pulse_steps=5000
     torch.cuda.synchronize()
     el = t0.elapsed_time(t1) / 1e3
     k = min(steps, 200)
-    ms = y.step_timed(k) / k
+    spl = y.steps_per_launch  # 2: two steps fused per launch (no sources or probes here)
+    ms = y.step_timed(k) / k * spl  # per launch
     cells = big * big
-    alg = 24.0 * cells
+    alg = 24.0 * cells  # Ez, Hx, Hy read and written once per launch
     out["grid"] = {"cells": cells, "steps": steps, "ms_per_step": el / steps * 1e3,
-                   "value": 3 * cells * steps / el, "unit": UNIT,
+                   "value": 3 * cells * steps / el, "unit": UNIT, "steps_per_launch": spl,
                    "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                                 "frac": alg / (ms / 1e3) / 1e9 / peak,
-                                "traffic": traffic_record(f"k_yee_{big}", 4), "kernel": "k_yee",
+                                "traffic": traffic_record(f"k_yee{spl}_{big}", 4),
+                                "kernel": "k_yee2" if spl == 2 else "k_yee",
                                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg,
                                 "avg_launch_ms": ms}}
     del y

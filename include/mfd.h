@@ -345,8 +345,8 @@ mfd_status mfd_fma_peak(int device, double* fp64_gflops, double* fp32_gflops);
  * (i h, (j + 1/2) h) and Hy[j][i] at ((i + 1/2) h, j h), both at (n - 1/2) dt.
  * A step is Eq. 5 with S_c / eta0 = dt / (mu0 h) and eta0 S_c = dt / (eps0 h)
  * (stable for S_c <= 1/sqrt(2)), then soft Ricker sources (as mfd_set_sources,
- * cell index j nx + i), then probes. One fused kernel per step; long runs
- * replay a CUDA graph. FP64 results equal the reference arithmetic of Eq. 5
+ * cell index j nx + i), then probes. One fused kernel per step (two steps per
+ * launch when there are no sources and probes); long runs replay a CUDA graph. FP64 results equal the reference arithmetic of Eq. 5
  * taken term by term (no fused multiply-add) bit for bit.
  * 2 <= nx < 2^30, 2 <= ny <= 2097120; fields in host arrays are ny x nx FP64. */
 typedef struct mfd_yee mfd_yee;
@@ -360,8 +360,12 @@ mfd_status mfd_yee_set_sources(mfd_yee* y, int count, const int64_t* cell, const
 /* Ez of `count` cells after each step, for at most `capacity` steps. */
 mfd_status mfd_yee_set_probes(mfd_yee* y, int count, const int64_t* cell, int64_t capacity);
 mfd_status mfd_yee_step(mfd_yee* y, int64_t nsteps);
-/* nsteps steps, each bracketed by CUDA events; *ms = the summed step times. */
+/* nsteps steps, each launch bracketed by CUDA events; *ms = the summed launch times. */
 mfd_status mfd_yee_step_timed(mfd_yee* y, int64_t nsteps, double* ms);
+/* Steps one kernel launch advances: 2 without sources and probes (two steps
+ * fused in shared memory, halving the DRAM traffic per step; results equal the
+ * one-step kernel's bit for bit), else 1. */
+int mfd_yee_steps_per_launch(const mfd_yee* y);
 /* host: steps x count FP64; *steps receives the recorded steps. */
 mfd_status mfd_yee_read_probes(mfd_yee* y, double* host, int64_t* steps);
 void mfd_yee_destroy(mfd_yee* y);

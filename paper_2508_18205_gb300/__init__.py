@@ -85,6 +85,7 @@ _SIGS = {
     "mfd_yee_step": (_I, [_VP, _I64]),
     "mfd_yee_step_timed": (_I, [_VP, _I64, _VP]),
     "mfd_yee_read_probes": (_I, [_VP, _VP, C.POINTER(_I64)]),
+    "mfd_yee_steps_per_launch": (_I, [_VP]),
     "mfd_yee_destroy": (None, [_VP]),
     "mfd_dispersion": (_I, [_VP, _I, _I, _VP, _D, _D, _D, _I, _VP, _VP, _VP, _VP]),
     "mfd_sim_dispersion": (_I, [_VP, _I, _I, _D, _D, _I, _VP, _VP, _VP, _VP]),
@@ -374,6 +375,10 @@ class Yee:
         ms = np.zeros(1)
         _ck(lib().mfd_yee_step_timed(self.h, int(n), _p(ms)))
         return float(ms[0])
+
+    @property
+    def steps_per_launch(self):
+        return int(lib().mfd_yee_steps_per_launch(self.h))
 
     def read_probes(self):
         steps = C.c_int64(0)

@@ -1,7 +1,8 @@
 // yee.cu -- the FDTD (Yee) scheme for TMz (Eq. 4, Eq. 5) on a periodic grid:
 // the reference the paper compares its meshless method with (Sec. 3, Sec. 6).
 //
-// One fused kernel per step: a block of 32 x 8 threads owns a 32 x 32 tile
+// One fused kernel per step (two fused steps per launch when there are no
+// sources and probes, below): a block of 32 x 8 threads owns a 32 x 32 tile
 // (four cells of a column per thread), stages Ez of the tile plus the one-cell
 // ring the stencil reads in shared memory, computes H' of the tile and of the
 // one-cell ring on its low sides (recomputed, not exchanged: the neighbour
@@ -109,6 +110,77 @@ __global__ void __launch_bounds__(YT_X * YB_Y, 8) k_yee(int nx, int ny, T ch, T 
     }
 }
 
+// Two steps per launch (temporal blocking), for runs without sources or probes
+// (their terms sit between the steps): a block stages Ez^n with a 2-cell ring
+// and the old H with the ring H^{n+1/2} needs, then computes in shared memory
+// H^{n+1/2} (tile + 2-cell ring on the low sides, + 1 on the high sides), E^{n+1}
+// (tile + 1-cell ring), H^{n+3/2} (tile + low 1-cell ring) and E^{n+2} (tile), and
+// writes the tile once: 6 reals of DRAM traffic per cell for two steps. Every
+// value is computed with the one-step kernel's arithmetic, so results match it
+// (and the reference in FP64) bit for bit.
+constexpr int Y2_T = 32;           // tile side
+constexpr int Y2_E = Y2_T + 4;     // staged Ez: x0-2 .. x0+33
+constexpr int Y2_H = Y2_T + 3;     // staged H:  x0-2 .. x0+32
+
+template <typename T, bool BIG>
+__global__ void __launch_bounds__(YT_X * YB_Y, 4) k_yee2(int nx, int ny, T ch, T ce, const T* __restrict__ ez,
+                                                         const T* __restrict__ hx, const T* __restrict__ hy,
+                                                         T* __restrict__ ez_o, T* __restrict__ hx_o,
+                                                         T* __restrict__ hy_o) {
+    __shared__ T se[Y2_E][Y2_E];   // [r][c]: Ez at (x0 - 2 + c, y0 - 2 + r); E^n, then E^{n+1} in place
+    __shared__ T sx[Y2_H][Y2_H];   // Hx at (x0 - 2 + c, y0 - 2 + r + 1/2): old, then n+1/2, then n+3/2
+    __shared__ T sy[Y2_H][Y2_H];   // Hy at (x0 - 2 + c + 1/2, y0 - 2 + r)
+    const int x0 = blockIdx.x * Y2_T, y0 = blockIdx.y * Y2_T;
+    const int t = threadIdx.y * YT_X + threadIdx.x;
+    constexpr int NT = YT_X * YB_Y;
+    for (int k = t; k < Y2_E * Y2_E; k += NT) {
+        const int r = k / Y2_E, c = k % Y2_E;
+        const int gx = wrap<BIG>(x0 - 2 + c, nx), gy = wrap<BIG>(y0 - 2 + r, ny);
+        const int64_t g = (int64_t)gy * nx + gx;
+        se[r][c] = ez[g];
+        if (r < Y2_H && c < Y2_H) {
+            sx[r][c] = hx[g];
+            sy[r][c] = hy[g];
+        }
+    }
+    __syncthreads();
+    // H^{n+1/2} on the whole staged H region (it reads Ez one cell up and right)
+    for (int k = t; k < Y2_H * Y2_H; k += NT) {
+        const int r = k / Y2_H, c = k % Y2_H;
+        const T e = se[r][c];
+        sx[r][c] = rn_sub(sx[r][c], rn_mul(ch, rn_sub(se[r + 1][c], e)));
+        sy[r][c] = rn_add(sy[r][c], rn_mul(ch, rn_sub(se[r][c + 1], e)));
+    }
+    __syncthreads();
+    // E^{n+1} on x0-1 .. x0+32, y0-1 .. y0+32 (staged rows / columns 1 .. 34), in place
+    for (int k = t; k < (Y2_T + 2) * (Y2_T + 2); k += NT) {
+        const int r = 1 + k / (Y2_T + 2), c = 1 + k % (Y2_T + 2);
+        const T curl = rn_add(rn_sub(rn_sub(sy[r][c], sy[r][c - 1]), sx[r][c]), sx[r - 1][c]);
+        se[r][c] = rn_add(se[r][c], rn_mul(ce, curl));
+    }
+    __syncthreads();
+    // H^{n+3/2} on x0-1 .. x0+31, y0-1 .. y0+31 (staged 1 .. 33)
+    for (int k = t; k < (Y2_T + 1) * (Y2_T + 1); k += NT) {
+        const int r = 1 + k / (Y2_T + 1), c = 1 + k % (Y2_T + 1);
+        const T e = se[r][c];
+        sx[r][c] = rn_sub(sx[r][c], rn_mul(ch, rn_sub(se[r + 1][c], e)));
+        sy[r][c] = rn_add(sy[r][c], rn_mul(ch, rn_sub(se[r][c + 1], e)));
+    }
+    __syncthreads();
+    // E^{n+2} on the tile (staged 2 .. 33) and the tile's H^{n+3/2}, written once
+    for (int k = t; k < Y2_T * Y2_T; k += NT) {
+        const int r = 2 + k / Y2_T, c = 2 + k % Y2_T;
+        const int i = x0 + c - 2, j = y0 + r - 2;
+        if (i < nx && j < ny) {
+            const T curl = rn_add(rn_sub(rn_sub(sy[r][c], sy[r][c - 1]), sx[r][c]), sx[r - 1][c]);
+            const int64_t g = (int64_t)j * nx + i;
+            ez_o[g] = rn_add(se[r][c], rn_mul(ce, curl));
+            hx_o[g] = sx[r][c];
+            hy_o[g] = sy[r][c];
+        }
+    }
+}
+
 // soft Ricker sources after the E update, then probes, then the step counter
 template <typename T>
 __global__ void k_yee_post(T* __restrict__ ez, int nsrc, const int64_t* __restrict__ sn, const double* __restrict__ sa,
@@ -176,6 +248,33 @@ namespace {
 
 constexpr int YEE_GRAPH_STEPS = 32;
 
+// two steps in one launch; only without sources and probes
+cudaError_t yee_enqueue2(mfd_yee* y) {
+    cudaStream_t s = y->ctx->stream;
+    const dim3 grid((unsigned)((y->nx + Y2_T - 1) / Y2_T), (unsigned)((y->ny + Y2_T - 1) / Y2_T));
+    const dim3 block(YT_X, YB_Y);
+    const int a = y->cur, b = y->cur ^ 1;
+    const bool big = y->nx >= Y2_T + 2 && y->ny >= Y2_T + 2;  // the staged ring reaches x0 + 33
+    const int nx = (int)y->nx, ny = (int)y->ny;
+    if (y->fp64) {
+        const double *e = y->f[a][0].as<double>(), *hx = y->f[a][1].as<double>(), *hy = y->f[a][2].as<double>();
+        double *eo = y->f[b][0].as<double>(), *hxo = y->f[b][1].as<double>(), *hyo = y->f[b][2].as<double>();
+        if (big) k_yee2<double, true><<<grid, block, 0, s>>>(nx, ny, y->ch, y->ce, e, hx, hy, eo, hxo, hyo);
+        else k_yee2<double, false><<<grid, block, 0, s>>>(nx, ny, y->ch, y->ce, e, hx, hy, eo, hxo, hyo);
+    } else {
+        const float *e = y->f[a][0].as<float>(), *hx = y->f[a][1].as<float>(), *hy = y->f[a][2].as<float>();
+        float *eo = y->f[b][0].as<float>(), *hxo = y->f[b][1].as<float>(), *hyo = y->f[b][2].as<float>();
+        const float ch = (float)y->ch, ce = (float)y->ce;
+        if (big) k_yee2<float, true><<<grid, block, 0, s>>>(nx, ny, ch, ce, e, hx, hy, eo, hxo, hyo);
+        else k_yee2<float, false><<<grid, block, 0, s>>>(nx, ny, ch, ce, e, hx, hy, eo, hxo, hyo);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    y->cur = b;
+    y->steps += 2;
+    return cudaSuccess;
+}
+
 cudaError_t yee_enqueue(mfd_yee* y) {
     cudaStream_t s = y->ctx->stream;
     const int tile_y = YB_Y * (y->fp64 ? yee_ry<double>() : yee_ry<float>());
@@ -234,7 +333,10 @@ mfd_status yee_graph(mfd_yee* y) {
     const int64_t steps0 = y->steps;
     MFD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < YEE_GRAPH_STEPS && e == cudaSuccess; ++k) e = yee_enqueue(y);
+    if (y->nsrc == 0 && y->nprobe == 0)
+        for (int k = 0; k < YEE_GRAPH_STEPS && e == cudaSuccess; k += 2) e = yee_enqueue2(y);
+    else
+        for (int k = 0; k < YEE_GRAPH_STEPS && e == cudaSuccess; ++k) e = yee_enqueue(y);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
     y->cur = cur0;
@@ -397,12 +499,20 @@ mfd_status mfd_yee_step(mfd_yee* y, int64_t nsteps) {
             left -= YEE_GRAPH_STEPS;
         }
     }
+    const bool two = y->nsrc == 0 && y->nprobe == 0;
     while (left > 0) {
-        MFD_CUDA(yee_enqueue(y));
-        --left;
+        if (two && left >= 2) {
+            MFD_CUDA(yee_enqueue2(y));
+            left -= 2;
+        } else {
+            MFD_CUDA(yee_enqueue(y));
+            --left;
+        }
     }
     return MFD_OK;
 }
+
+int mfd_yee_steps_per_launch(const mfd_yee* y) { return y && y->nsrc == 0 && y->nprobe == 0 ? 2 : 1; }
 
 mfd_status mfd_yee_step_timed(mfd_yee* y, int64_t nsteps, double* ms) {
     if (!y || nsteps < 0 || !ms) return fail(MFD_ERR_ARG, "bad arguments");
@@ -411,9 +521,11 @@ mfd_status mfd_yee_step_timed(mfd_yee* y, int64_t nsteps, double* ms) {
     for (auto& e : y->ev)
         if (!e) MFD_CUDA(cudaEventCreate(&e));
     double tot = 0.0;
-    for (int64_t k = 0; k < nsteps; ++k) {
+    const bool two = y->nsrc == 0 && y->nprobe == 0;
+    for (int64_t k = 0; k < nsteps; k += (two && k + 1 < nsteps) ? 2 : 1) {
         MFD_CUDA(cudaEventRecord(y->ev[0], s));
-        MFD_CUDA(yee_enqueue(y));
+        if (two && k + 1 < nsteps) MFD_CUDA(yee_enqueue2(y));
+        else MFD_CUDA(yee_enqueue(y));
         MFD_CUDA(cudaEventRecord(y->ev[1], s));
         MFD_CUDA(cudaEventSynchronize(y->ev[1]));
         float t = 0.f;
