@@ -330,3 +330,57 @@ def test_graph_and_direct_launches_agree(ctx):
     assert sims[0].steps == sims[1].steps == 131
     for c in (M.MFD_EZ, M.MFD_HX, M.MFD_HY):
         assert np.array_equal(sims[0].get_field(c), sims[1].get_field(c))
+
+
+@pytest.mark.parametrize("layout", ["colloc", "stag"])
+def test_fp32_within_1e5_at_every_100th_step(ctx, layout):
+    """FP32 with compensated curl sums against the FP64 oracle over 1000 steps:
+    the relative L2 error of all fields stays <= 1e-5 at every 100th step and
+    at the end, and so does the probe series over the whole run (the largest
+    error seen is in the assertion message)."""
+    S = 0.5
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    if layout == "colloc":
+        c = 4e-3
+        nodes = W.pec_box((33, 33), 0.25, 31)
+        er = W.eps_r_uniform(nodes.n, 32)
+        sim = _gpu_colloc(ctx, nodes, 12, 3, 2, 2, dt, eps0, mu0, -c, 0, True)
+        sim.set_materials(er, nodes.pec)
+        ez, hx, hy = W.tm11_fields(nodes.xyz, 32.0, c0, mu0, 0.0, -0.5 * dt)
+        ez[nodes.pec == 1] = 0
+        src = W.ricker_sources(nodes, 3, 33, c0)
+        probes = W.interior_nodes(nodes, 16, 34)
+        prob, _ = O.tmz_collocated(nodes, 12, 3, 2, 2, dt, eps0, mu0, -c, eps_r=er)
+    else:
+        c, alpha, nx, n, nhv = 4e-5, 3, 36, 30, 57
+        e = W.periodic_box((nx, nx), 0.25, 35, seed_line_y=nx // 2)
+        h = W.periodic_box((nx, nx), 0.25, 36, offset=(0.5, 0.5))
+        de, dh = M.Nodes(ctx, e.xyz, e.period), M.Nodes(ctx, h.xyz, h.period)
+        hc = M.Weights(M.Stencils(dh, de, n), n, 5, 4, M.MFD_OP_GRAD)
+        hv = M.Weights(M.Stencils(dh, dh, nhv), nhv, 7, 6, M.MFD_OP_LAP_POW, alpha)
+        ec = M.Weights(M.Stencils(de, dh, n), n, 5, 4, M.MFD_OP_GRAD)
+        ev = M.Weights(M.Stencils(de, de, nhv), nhv, 7, 6, M.MFD_OP_LAP_POW, alpha)
+        sim = M.Sim(ctx, 2, 0, dt, eps0, mu0, c, hc, hv, ec, ev, compensated=True)
+        ez, _, _ = W.gaussian_pulse(e.xyz, nx, nx / 2, 6.0, c0, eta0, dt, 12.0)
+        _, hx, hy = W.gaussian_pulse(h.xyz, nx, nx / 2, 6.0, c0, eta0, dt, 12.0)
+        src = None
+        probes = W.interior_nodes(e, 8, 37)
+        prob = O.tmz_staggered(e, h, n, 5, 4, alpha, dt, eps0, mu0, c)
+    for comp_, v in ((M.MFD_EZ, ez), (M.MFD_HX, hx), (M.MFD_HY, hy)):
+        sim.set_field(comp_, v)
+    if src is not None:
+        sim.set_sources(src.node, src.amp, src.f0, src.t0)
+    sim.set_probes(probes, 1000)
+    ref = [ez, hx, hy]
+    rprobes, worst = [], 0.0
+    for k in range(10):
+        sim.step(100)
+        out = O.run_tmz(prob, *ref, 100, step0=100 * k, sources=src, probes=probes)
+        ref = list(out[:3])
+        rprobes.append(out[3])
+        got = [sim.get_field(cc) for cc in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)]
+        err = _rel_all(got, ref)
+        worst = max(worst, err)
+        assert err <= 1e-5, (layout, 100 * (k + 1), err)
+    perr = _rel(sim.read_probes(), np.concatenate(rprobes))
+    assert perr <= 1e-5, (layout, perr, worst)
