@@ -360,7 +360,21 @@ def main():
         dist.barrier()
     s = 8 if prec == M.MFD_FP64 else 4
     peak, peak_kind = peaks()
-    roof = roofline(ms, a.steps, e, h, nhv, s, peak, peak_kind)
+    stats = sim.index_stats()
+    roof = roofline(ms, a.steps, e, h, nhv, s, peak, peak_kind, stats)
+    # the same steps with 32-bit indices everywhere, for comparison (bit-identical fields)
+    k32 = min(a.steps, 1000)
+    sim.set_index_format(M.MFD_INDEX_I32)
+    sim.step(4)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    sim.step(k32)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    i32_ms = t_start.elapsed_time(t_end) / k32
+    sim.set_index_format(M.MFD_INDEX_Q16)
+    step_bytes = format_bytes(PARAMS["n"], nhv, s, stats)
+    step_gb = (step_bytes[0] * h.n + step_bytes[1] * e.n) / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": elapsed / a.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == M.MFD_FP64 else "f32",
@@ -368,11 +382,13 @@ def main():
             "config": {"workload": f"pulse2d-staggered-{nx}x{nx}x2",
                        "nodes_per_set": nx * nx, "layout": "staggered", "curl_stencil": PARAMS["n"],
                        "hv_stencil": nhv, "phs": PARAMS["k"], "poly_m": PARAMS["m"], "alpha": PARAMS["alpha"],
-                       "courant": S, "compensated": comp, "l2_flush": "inputs larger than L2 (1.7 GB/step)",
+                       "courant": S, "compensated": comp, "l2_flush": f"inputs larger than L2 ({step_gb:.2f} GB/step)",
                        "parallelism": f"replicas{world}", "setup_s": setup,
                        "autotuned_blocks": {"h_pass": blocks[0], "e_pass": blocks[1]}},
             "roofline": roof, "clocks": clocks, "gpu_launches": 3 * a.steps,
-            "event_timed_ms_per_step": (ms[0] + ms[1]) / a.steps}
+            "event_timed_ms_per_step": (ms[0] + ms[1]) / a.steps,
+            "index_i32": {"ms_per_step": i32_ms, "steps": k32,
+                          "value": per_step_updates / (i32_ms / 1e3) * world}}
     # the plain FP64 GPU step on the same GPU, and FP32 accuracy against it
     if rank == 0 and not a.no_fp64 and prec == M.MFD_FP32:
         k64 = min(a.steps, 1000)
@@ -402,7 +418,7 @@ def main():
                                      "unit": "TFLOP/s", "frac": dom_fl / dom_t / 1e9 / g64, "traffic": None,
                                      "kernel": kn, "peak_kind": "measured live (FP64 FMA chains, mfd_fma_peak)",
                                      "flops_per_launch": dom_fl, "avg_launch_ms": dom_t * 1e3,
-                                     "hbm": roofline(ms64, k64, e, h, nhv, 8, peak, peak_kind)},
+                                     "hbm": roofline(ms64, k64, e, h, nhv, 8, peak, peak_kind, stats)},
                         "fma_peak_gflops": {"fp64": g64, "fp32": g32}}
         del s64
         if a.accuracy_steps:
@@ -453,8 +469,26 @@ def main():
         dist.destroy_process_group()
 
 
-def roofline(ms, steps, e, h, nhv, s, peak, peak_kind):
-    """Dominant half-step kernel: algorithmic bytes per launch / its average event-timed duration."""
+def format_bytes(n, nhv, s, stats):
+    """Compulsory bytes per node of each half step in the 16-bit index format
+    (mfd_sim_set_index_format): 2 bytes per entry, 4 in the slices that keep
+    32-bit entries, plus the two 4-byte bases per slice and stream."""
+    out = []
+    for p, fields in (("h", 5), ("e", 4)):
+        sl, wc, wv = stats[p]
+        if sl == 0:  # no 16-bit streams: 32-bit entries
+            out.append(algorithmic_bytes(n, nhv, s)[0 if p == "h" else 1])
+            continue
+        idx = sum((2 + 2 * w / sl) * k for w, k in ((wc, n), (wv, nhv))) + 2 * 8 / 32
+        out.append(idx + s * (2 * n + nhv) + fields * s)
+    return tuple(out)
+
+
+def roofline(ms, steps, e, h, nhv, s, peak, peak_kind, stats=None):
+    """Dominant half-step kernel: algorithmic bytes per launch / its average
+    event-timed duration. The algorithmic bytes count 32-bit indices; with
+    index statistics, the bytes of the 16-bit index format the kernels read
+    are reported beside them."""
     bh, be = algorithmic_bytes(PARAMS["n"], nhv, s)
     h_avg = ms[0] / steps / 1e3
     e_avg = ms[1] / steps / 1e3
@@ -463,11 +497,20 @@ def roofline(ms, steps, e, h, nhv, s, peak, peak_kind):
     dom_bytes = (bh * h.n) if dom == "h" else (be * e.n)
     achieved = dom_bytes / dom_t / 1e9
     kname = "k_h_stag" if dom == "h" else "k_e_stag"
-    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic_record(kname, s), "kernel": kname, "peak_kind": peak_kind,
-            "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_t * 1e3,
-            "other_kernel_avg_launch_ms": min(h_avg, e_avg) * 1e3,
-            "other_kernel_achieved_gbs": ((be * e.n) if dom == "h" else (bh * h.n)) / min(h_avg, e_avg) / 1e9}
+    r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+         "traffic": traffic_record(kname, s), "kernel": kname, "peak_kind": peak_kind,
+         "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_t * 1e3,
+         "other_kernel_avg_launch_ms": min(h_avg, e_avg) * 1e3,
+         "other_kernel_achieved_gbs": ((be * e.n) if dom == "h" else (bh * h.n)) / min(h_avg, e_avg) / 1e9}
+    if stats is not None and stats["h"][0] > 0:
+        fh, fe = format_bytes(PARAMS["n"], nhv, s, stats)
+        fb = (fh * h.n) if dom == "h" else (fe * e.n)
+        r["index_format"] = {"name": "q16", "bytes_per_launch": fb, "achieved": fb / dom_t / 1e9,
+                             "frac": fb / dom_t / 1e9 / peak,
+                             "slices_with_32bit_entries": {"h_pass": list(stats["h"][1:]),
+                                                           "e_pass": list(stats["e"][1:]),
+                                                           "slices": stats["h"][0]}}
+    return r
 
 
 def batched(M, ctx, steps, peak, peak_kind, ndom=256, nrhs=16):

@@ -24,6 +24,7 @@ MFD_ERR_ARG, MFD_ERR_OOM, MFD_ERR_CUDA, MFD_ERR_SINGULAR = -1, -2, -3, -4
 MFD_ERR_UNSTABLE, MFD_ERR_TIMEOUT, MFD_ERR_STATE = -5, -6, -7
 MFD_OP_GRAD, MFD_OP_LAP_POW, MFD_OP_GRAD_VFD = 0, 1, 2
 MFD_FP32, MFD_FP64 = 0, 1
+MFD_INDEX_Q16, MFD_INDEX_I32 = 0, 1
 MFD_EX, MFD_EY, MFD_EZ, MFD_HX, MFD_HY, MFD_HZ = range(6)
 
 
@@ -75,6 +76,8 @@ _SIGS = {
     "mfd_sim_set_blocks": (_I, [_VP, _I, _I]),
     "mfd_set_watchdog": (_I, [_VP, _I64, _D]),
     "mfd_sim_autotune": (_I, [_VP, _I, _VP]),
+    "mfd_sim_set_index_format": (_I, [_VP, _I]),
+    "mfd_sim_index_stats": (_I, [_VP, _VP]),
     "mfd_sim_destroy": (None, [_VP]),
     "mfd_knn_static": (_I, [_I, _I64, _VP, _I64, _VP, _VP, _I, _VP, _VP]),
     "mfd_yee_create": (_I, [_VP, _I64, _I64, _I, _D, _D, _D, _D, C.POINTER(_VP)]),
@@ -565,6 +568,16 @@ class Sim:
 
     def set_blocks(self, block_h, block_e):
         _ck(lib().mfd_sim_set_blocks(self.h, int(block_h), int(block_e)))
+
+    def set_index_format(self, fmt):
+        """MFD_INDEX_Q16 (default) or MFD_INDEX_I32 indices in the staggered kernels (mfd_sim_set_index_format)."""
+        _ck(lib().mfd_sim_set_index_format(self.h, int(fmt)))
+
+    def index_stats(self):
+        """{"h"|"e": (slices, 32-bit curl slices, 32-bit HV slices)} (mfd_sim_index_stats)."""
+        out = np.zeros(6, dtype=np.int64)
+        _ck(lib().mfd_sim_index_stats(self.h, _p(out)))
+        return {"h": tuple(int(x) for x in out[:3]), "e": tuple(int(x) for x in out[3:])}
 
     def autotune(self, reps=20):
         """Times 128/256/512 threads per block for each half-step kernel and keeps the fastest."""

@@ -51,6 +51,58 @@ __global__ void k_pack_w(const double* __restrict__ w, int64_t N, int n_use, int
     dst[e] = (node < N && entry < n_use) ? (T)w[node * n_use + entry] : (T)0;
 }
 
+// Q16 bases of one slice (one thread per slice): b0 is the smallest neighbour
+// id; b1 the smallest id past b0's window of 32768; the slice is wide (b0 = -1)
+// when an id falls outside both windows. Covering the ids with at most two
+// windows, each opened at the smallest id not yet covered, succeeds whenever
+// any two windows cover them.
+__global__ void k_q16_bases(const int32_t* __restrict__ src, int stride, int64_t N, int n_use, int64_t slices,
+                            int2* __restrict__ bases, unsigned long long* __restrict__ wide) {
+    const int64_t sl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (sl >= slices) return;
+    const int64_t lo = sl * 32, hi = lo + 32 < N ? lo + 32 : N;
+    int64_t b0 = INT64_MAX, b1 = INT64_MAX;
+    for (int64_t i = lo; i < hi; ++i)
+        for (int e = 0; e < n_use; ++e) b0 = min(b0, (int64_t)src[i * stride + e]);
+    for (int64_t i = lo; i < hi; ++i)
+        for (int e = 0; e < n_use; ++e) {
+            const int64_t v = src[i * stride + e];
+            if (v > b0 + 32767) b1 = min(b1, v);
+        }
+    bool ok = true;
+    if (b1 != INT64_MAX)
+        for (int64_t i = lo; i < hi && ok; ++i)
+            for (int e = 0; e < n_use; ++e) {
+                const int64_t v = src[i * stride + e];
+                if (v > b0 + 32767 && v > b1 + 32767) ok = false;
+            }
+    if (b1 == INT64_MAX) b1 = b0 + 32768;
+    bases[sl] = ok ? make_int2((int)b0, (int)(b1 - 32768)) : make_int2(-1, 0);
+    if (!ok) atomicAdd(wide, 1ull);
+}
+
+// Q16 entries, laid out as the 32-bit chunks with 8 entries per chunk:
+// element e -> (slice s, chunk c, lane l, entry q)
+__global__ void k_pack_q16(const int32_t* __restrict__ src, int stride, int64_t N, int n_use, int chunks8,
+                           const int2* __restrict__ bases, uint16_t* __restrict__ dst, int64_t total) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int q = (int)(e & 7);
+    const int lane = (int)((e >> 3) & 31);
+    const int64_t rest = e >> 8;
+    const int c = (int)(rest % chunks8);
+    const int64_t sl = rest / chunks8;
+    const int64_t node = sl * 32 + lane;
+    const int entry = c * 8 + q;
+    const int2 b = bases[sl];
+    unsigned v = 0;
+    if (b.x >= 0 && node < N) {
+        const int64_t id = src[node * stride + (entry < n_use ? entry : 0)];
+        v = id - b.x <= 32767 ? (unsigned)(id - b.x) : (unsigned)(id - b.y);
+    }
+    dst[e] = (uint16_t)v;
+}
+
 template <typename T>
 __global__ void k_scatter(const double* __restrict__ src, const int64_t* __restrict__ inv, int64_t n,
                           T* __restrict__ base, int stride, int offset) {
@@ -160,6 +212,8 @@ using namespace mfd;
 
 struct PackedStencil {
     DevBuf idx_c, idx_v, wx, wy, wz, wv;
+    DevBuf q_c, q_v, qb_c, qb_v;     // Q16 index streams and bases (staggered layout)
+    int64_t wide_c = 0, wide_v = 0;  // slices left on the 32-bit streams
     int nc = 0, nv = 0, ni = 0;
     int64_t n = 0;
 };
@@ -191,6 +245,7 @@ struct mfd_sim {
     AdjT adj;
     bool adj_ok = false;
     int block[2] = {256, 256};  // threads per block of the H and E half-step kernels (autotuned)
+    bool q16 = true;            // staggered kernels read Q16 indices (mfd_sim_set_index_format)
     int64_t watch_every = 0;    // energy watchdog: check every this many steps (0: off)
     double watch_ratio = 0, watch_u0 = 0;
     ~mfd_sim() {
@@ -227,6 +282,33 @@ mfd_status pack_weights(mfd_ctx* ctx, const mfd_weights* w, int out_index, int c
 
 int chunks_of(int n) { return (n + 3) / 4; }
 
+// Q16 form of one index stream (chunks4 chunks of 4 entries per row)
+mfd_status pack_q16(mfd_ctx* ctx, const mfd_stencils* st, int n_use, int chunks4, DevBuf& q, DevBuf& qb,
+                    int64_t& wide) {
+    const int64_t N = st->centres->n;
+    const int64_t slices = (N + 31) / 32;
+    const int chunks8 = (chunks4 + 1) / 2;
+    const int64_t total = slices * chunks8 * 256;
+    MFD_TRY(q.alloc(total * 2));
+    MFD_TRY(qb.alloc(slices * sizeof(int2)));
+    DevBuf cnt;
+    MFD_TRY(cnt.alloc(8));
+    MFD_CUDA(cudaMemsetAsync(cnt.p, 0, 8, ctx->stream));
+    k_q16_bases<<<(unsigned)((slices + 127) / 128), 128, 0, ctx->stream>>>(st->idx.as<int32_t>(), st->n, N, n_use,
+                                                                          slices, qb.as<int2>(),
+                                                                          cnt.as<unsigned long long>());
+    MFD_CUDA(cudaGetLastError());
+    k_pack_q16<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(st->idx.as<int32_t>(), st->n, N, n_use,
+                                                                        chunks8, qb.as<int2>(), q.as<uint16_t>(),
+                                                                        total);
+    MFD_CUDA(cudaGetLastError());
+    unsigned long long w = 0;
+    MFD_CUDA(cudaMemcpyAsync(&w, cnt.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    MFD_CUDA(cudaStreamSynchronize(ctx->stream));
+    wide = (int64_t)w;
+    return MFD_OK;
+}
+
 // packs the curl and HV streams of one pass
 mfd_status pack_pass(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* hv, int dim, bool fp64, PackedStencil& p) {
     p.n = curl->st->centres->n;
@@ -240,6 +322,10 @@ mfd_status pack_pass(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* h
         p.ni = p.nc;
         MFD_TRY(pack_stream(ctx, curl->st, curl->n_use, p.nc, p.idx_c));
         MFD_TRY(pack_stream(ctx, hv->st, hv->n_use, p.nv, p.idx_v));
+        if (dim == 2 && curl->st->centres != curl->st->sources) {  // staggered
+            MFD_TRY(pack_q16(ctx, curl->st, curl->n_use, p.nc, p.q_c, p.qb_c, p.wide_c));
+            MFD_TRY(pack_q16(ctx, hv->st, hv->n_use, p.nv, p.q_v, p.qb_v, p.wide_v));
+        }
     }
     MFD_TRY(pack_weights(ctx, curl, 0, p.nc, fp64, p.wx));
     MFD_TRY(pack_weights(ctx, curl, 1, p.nc, fp64, p.wy));
@@ -248,10 +334,16 @@ mfd_status pack_pass(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* h
     return MFD_OK;
 }
 
-template <typename T> StencilStreams<T> streams(const PackedStencil& p) {
+template <typename T> StencilStreams<T> streams(const PackedStencil& p, bool q16 = false) {
     StencilStreams<T> s;
     s.idx_c = p.idx_c.as<const int4>();
     s.idx_v = p.idx_v.p ? p.idx_v.as<const int4>() : s.idx_c;
+    if (q16 && p.q_c.p && p.q_v.p) {
+        s.q_c = p.q_c.as<const uint4>();
+        s.q_v = p.q_v.as<const uint4>();
+        s.qb_c = p.qb_c.as<const int2>();
+        s.qb_v = p.qb_v.as<const int2>();
+    }
     s.wx = p.wx.as<const typename Vec<T>::V4>();
     s.wy = p.wy.as<const typename Vec<T>::V4>();
     s.wz = p.wz.p ? p.wz.as<const typename Vec<T>::V4>() : nullptr;
@@ -268,11 +360,11 @@ Launch2D make2d(mfd_sim* sim, int parity) {
     L.staggered = sim->layout == STAG2D;
     L.fp64 = sim->fp64;
     L.comp = sim->comp;
-    L.hs.f = streams<float>(sim->hp);
-    L.hs.d = streams<double>(sim->hp);
+    L.hs.f = streams<float>(sim->hp, sim->q16);
+    L.hs.d = streams<double>(sim->hp, sim->q16);
     if (L.staggered) {
-        L.es.f = streams<float>(sim->ep);
-        L.es.d = streams<double>(sim->ep);
+        L.es.f = streams<float>(sim->ep, sim->q16);
+        L.es.d = streams<double>(sim->ep, sim->q16);
     }
     L.kf.ch = (float)(sim->d.dt / sim->d.mu0);
     L.kf.gamma = (float)sim->d.gamma;
@@ -889,6 +981,26 @@ mfd_status mfd_sim_set_blocks(mfd_sim* sim, int block_h, int block_e) {
     sim->block[0] = block_h;
     sim->block[1] = block_e;
     sim->graph_ok = false;
+    return MFD_OK;
+}
+
+mfd_status mfd_sim_set_index_format(mfd_sim* sim, int format) {
+    if (!sim || (format != MFD_INDEX_Q16 && format != MFD_INDEX_I32)) return fail(MFD_ERR_ARG, "bad arguments");
+    sim->q16 = format == MFD_INDEX_Q16;
+    sim->graph_ok = false;
+    return MFD_OK;
+}
+
+mfd_status mfd_sim_index_stats(const mfd_sim* sim, int64_t* out) {
+    if (!sim || !out) return fail(MFD_ERR_ARG, "NULL argument");
+    const PackedStencil* ps[2] = {&sim->hp, &sim->ep};
+    for (int p = 0; p < 2; ++p) {
+        const PackedStencil& k = *ps[p];
+        const bool has = sim->layout == STAG2D && k.q_c.p != nullptr;
+        out[3 * p] = has ? (k.n + 31) / 32 : 0;
+        out[3 * p + 1] = has ? k.wide_c : 0;
+        out[3 * p + 2] = has ? k.wide_v : 0;
+    }
     return MFD_OK;
 }
 

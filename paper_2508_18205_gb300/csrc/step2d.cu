@@ -186,31 +186,25 @@ __device__ __forceinline__ void h_stag_node(const StencilStreams<T>& s, const T*
     const int nv = NV ? NV : s.nv;
     const int64_t slice = i >> 5;
     const int lane = (int)(i & 31);
-    const int4* ic = s.idx_c + slice * nc * 32 + lane;
-    const int4* iv = s.idx_v + slice * nv * 32 + lane;
     const V4* px = s.wx + slice * nc * 32 + lane;
     const V4* py = s.wy + slice * nc * 32 + lane;
     const V4* pv = s.wv + slice * nv * 32 + lane;
     Acc ax, ay;
     AccV hx, hy;
-#pragma unroll
-    for (int c = 0; c < nc; ++c) {
-        const int4 id = ld_stream(ic + c * 32);
+    for_idx4<NC>(nc, slice, lane, s.idx_c, s.q_c, s.qb_c, [&](int c, int4 id) {
         const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32);
         const T f0 = ld_gather(Ez + id.x), f1 = ld_gather(Ez + id.y);
         const T f2 = ld_gather(Ez + id.z), f3 = ld_gather(Ez + id.w);
         ax.add(wx.x, f0); ax.add(wx.y, f1); ax.add(wx.z, f2); ax.add(wx.w, f3);
         ay.add(wy.x, f0); ay.add(wy.y, f1); ay.add(wy.z, f2); ay.add(wy.w, f3);
-    }
-#pragma unroll
-    for (int c = 0; c < nv; ++c) {
-        const int4 id = ld_stream(iv + c * 32);
+    });
+    for_idx4<NV>(nv, slice, lane, s.idx_v, s.q_v, s.qb_v, [&](int c, int4 id) {
         const V4 wv = ld_stream(pv + c * 32);
         const V2 f0 = ld_gather(H + id.x), f1 = ld_gather(H + id.y);
         const V2 f2 = ld_gather(H + id.z), f3 = ld_gather(H + id.w);
         hx.add(wv.x, f0.x); hx.add(wv.y, f1.x); hx.add(wv.z, f2.x); hx.add(wv.w, f3.x);
         hy.add(wv.x, f0.y); hy.add(wv.y, f1.y); hy.add(wv.z, f2.y); hy.add(wv.w, f3.y);
-    }
+    });
     dxE = ax.get();
     dyE = ay.get();
     vx = hx.get();
@@ -246,30 +240,24 @@ __global__ void __launch_bounds__(512) k_e_stag(StencilStreams<T> s, Coefs<T> k,
     const int nv = NV ? NV : s.nv;
     const int64_t slice = i >> 5;
     const int lane = (int)(i & 31);
-    const int4* ic = s.idx_c + slice * nc * 32 + lane;
-    const int4* iv = s.idx_v + slice * nv * 32 + lane;
     const V4* px = s.wx + slice * nc * 32 + lane;
     const V4* py = s.wy + slice * nc * 32 + lane;
     const V4* pv = s.wv + slice * nv * 32 + lane;
     Acc dxHy, dyHx;
     AccPlain<T> he;
-#pragma unroll
-    for (int c = 0; c < nc; ++c) {
-        const int4 id = ld_stream(ic + c * 32);
+    for_idx4<NC>(nc, slice, lane, s.idx_c, s.q_c, s.qb_c, [&](int c, int4 id) {
         const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32);
         const V2 f0 = ld_gather(Hn + id.x), f1 = ld_gather(Hn + id.y);
         const V2 f2 = ld_gather(Hn + id.z), f3 = ld_gather(Hn + id.w);
         dxHy.add(wx.x, f0.y); dxHy.add(wx.y, f1.y); dxHy.add(wx.z, f2.y); dxHy.add(wx.w, f3.y);
         dyHx.add(wy.x, f0.x); dyHx.add(wy.y, f1.x); dyHx.add(wy.z, f2.x); dyHx.add(wy.w, f3.x);
-    }
-#pragma unroll
-    for (int c = 0; c < nv; ++c) {
-        const int4 id = ld_stream(iv + c * 32);
+    });
+    for_idx4<NV>(nv, slice, lane, s.idx_v, s.q_v, s.qb_v, [&](int c, int4 id) {
         const V4 wv = ld_stream(pv + c * 32);
         const T f0 = ld_gather(Ez + id.x), f1 = ld_gather(Ez + id.y);
         const T f2 = ld_gather(Ez + id.z), f3 = ld_gather(Ez + id.w);
         he.add(wv.x, f0); he.add(wv.y, f1); he.add(wv.z, f2); he.add(wv.w, f3);
-    }
+    });
     const T e = ld_gather(Ez + i);
     Ezn[i] = e + ld_gather(ce + i) * (dxHy.get() - dyHx.get() + k.gamma * he.get());
 }

@@ -156,3 +156,27 @@ def test_batched_256_domains_sampled_domains():
                             f0=srcs[d].f0[sel], t0=srcs[d].t0[sel])
             ref[:, r] = O.run_tmz(prob, z, z, z, nsteps, sources=sub)[0]
         assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), d
+
+
+def test_fullsize_index_formats_bit_identical(setup):
+    """The benchmark's launch configuration (FP32, compensated sums, 16-bit
+    indices with two windows per slice, 32-bit fallback): three steps from
+    random fields equal the 32-bit index format on every node, bit for bit."""
+    ctx, e, h, wts, nhv = setup
+    sim = bench.make_sim(M, ctx, wts, 0, True)
+    stats = sim.index_stats()
+    for p in ("h", "e"):
+        assert stats[p][0] == 1000 * 1000 // 32
+        assert 0 < stats[p][1] < stats[p][0] // 50 and 0 < stats[p][2] < stats[p][0] // 50, stats
+    rng = np.random.default_rng(83)
+    f = [rng.standard_normal(e.n), rng.standard_normal(h.n), rng.standard_normal(h.n)]
+    comps = (M.MFD_EZ, M.MFD_HX, M.MFD_HY)
+    runs = []
+    for fmt in (M.MFD_INDEX_Q16, M.MFD_INDEX_I32):
+        sim.set_index_format(fmt)
+        for cc, v in zip(comps, f):
+            sim.set_field(cc, v)
+        sim.step(3)
+        runs.append([sim.get_field(cc) for cc in comps])
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)

@@ -384,3 +384,43 @@ def test_fp32_within_1e5_at_every_100th_step(ctx, layout):
         assert err <= 1e-5, (layout, 100 * (k + 1), err)
     perr = _rel(sim.read_probes(), np.concatenate(rprobes))
     assert perr <= 1e-5, (layout, perr, worst)
+
+
+@pytest.mark.parametrize("prec,comp,tol", [(1, False, 1e-10), (0, True, 1e-5)])
+def test_staggered_q16_indices_with_two_windows_and_wide_slices(ctx, prec, comp, tol):
+    """400 x 400 nodes per set: the Morton seams and the periodic wraps give
+    slices whose neighbours need two 16-bit index windows and slices that keep
+    32-bit indices. Every field after 20 steps against the oracle, and the
+    32-bit index format gives bit-identical fields."""
+    S, c, alpha, nx, n, nhv = 0.5, 4e-5, 3, 400, 30, 57
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    e = W.periodic_box((nx, nx), 0.25, 35)
+    h = W.periodic_box((nx, nx), 0.25, 36, offset=(0.5, 0.5))
+    de, dh = M.Nodes(ctx, e.xyz, e.period), M.Nodes(ctx, h.xyz, h.period)
+    hc = M.Weights(M.Stencils(dh, de, n), n, 5, 4, M.MFD_OP_GRAD)
+    hv = M.Weights(M.Stencils(dh, dh, nhv), nhv, 7, 6, M.MFD_OP_LAP_POW, alpha)
+    ec = M.Weights(M.Stencils(de, dh, n), n, 5, 4, M.MFD_OP_GRAD)
+    ev = M.Weights(M.Stencils(de, de, nhv), nhv, 7, 6, M.MFD_OP_LAP_POW, alpha)
+    sim = M.Sim(ctx, 2, prec, dt, eps0, mu0, c, hc, hv, ec, ev, compensated=comp)
+    stats = sim.index_stats()
+    for p in ("h", "e"):
+        assert stats[p][0] == nx * nx // 32
+        assert stats[p][1] > 0 and stats[p][2] > 0, stats  # some slices keep 32-bit indices
+        assert stats[p][1] < stats[p][0] // 100 and stats[p][2] < stats[p][0] // 100, stats
+    rng = np.random.default_rng(37)
+    f = [rng.standard_normal(nx * nx) for _ in range(3)]
+    if prec == 0:
+        f = [a.astype(np.float32).astype(np.float64) for a in f]
+    comps = (M.MFD_EZ, M.MFD_HX, M.MFD_HY)
+    runs = []
+    for fmt in (M.MFD_INDEX_Q16, M.MFD_INDEX_I32):
+        sim.set_index_format(fmt)
+        for cc, v in zip(comps, f):
+            sim.set_field(cc, v)
+        sim.step(20)
+        runs.append([sim.get_field(cc) for cc in comps])
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
+    prob = O.tmz_staggered(e, h, n, 5, 4, alpha, dt, eps0, mu0, c)
+    re, rx, ry, _, _ = O.run_tmz(prob, *f, 20)
+    assert _rel_all(runs[0], [re, rx, ry]) <= tol
