@@ -612,25 +612,6 @@ def cube3d(M, ctx, steps, peak, peak_kind, nx=200):
     dom_b = (bh if dom == "k_h3" else be) * nodes.n
     dom_t = max(h_avg, e_avg)
     ach = dom_b / dom_t / 1e9
-    # the 16-bit index format: 2 bytes per entry (4 in the slices that keep 32-bit
-    # entries) plus four 4-byte bases per slice, in place of 4 bytes per entry
-    sl, wide, _ = sim.index_stats()["h"]
-    per_entry = 2 + 2 * wide / sl if sl else 4
-    base_b = 16 / 32 if sl else 0
-    fh = bh - (4 - per_entry) * max(n, nhv) + base_b
-    fe = be - (4 - per_entry) * n + base_b
-    fb = (fh if dom == "k_h3" else fe) * nodes.n
-    # the same steps with 32-bit indices everywhere, for comparison (bit-identical fields)
-    k32 = min(steps, 100)
-    sim.set_index_format(M.MFD_INDEX_I32)
-    sim.step(2)
-    torch.cuda.synchronize()
-    t0.record(stream)
-    sim.step(k32)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    i32_ms = t0.elapsed_time(t1) / k32
-    sim.set_index_format(M.MFD_INDEX_Q16)
     return {"workload": f"cube3d {nx}^3 periodic, n={n}, N_h={nhv}, FP32", "nodes": nodes.n,
             "value": nodes.n * 6 * steps / el, "unit": UNIT, "steps": steps, "ms_per_step": el / steps * 1e3,
             "setup_s": {"generate": round(gen_s, 2), "morton_knn": round(t_knn, 2), "weights_fp64": round(t_w, 2)},
@@ -638,11 +619,7 @@ def cube3d(M, ctx, steps, peak, peak_kind, nx=200):
                          "traffic": traffic_record(dom, s4), "kernel": dom, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": dom_b, "avg_launch_ms": dom_t * 1e3,
                          "other_kernel_avg_launch_ms": min(h_avg, e_avg) * 1e3,
-                         "step_achieved_gbs": (bh + be) * nodes.n / (el / steps) / 1e9,
-                         "index_format": {"name": "q16 (four windows)", "bytes_per_launch": fb,
-                                          "achieved": fb / dom_t / 1e9, "frac": fb / dom_t / 1e9 / peak,
-                                          "slices_with_32bit_entries": wide, "slices": sl}},
-            "index_i32": {"ms_per_step": i32_ms, "steps": k32}}
+                         "step_achieved_gbs": (bh + be) * nodes.n / (el / steps) / 1e9}}
 
 
 def cavity(M, ctx, steps=1000):

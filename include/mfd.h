@@ -223,26 +223,22 @@ mfd_status mfd_sim_set_blocks(mfd_sim* sim, int block_h, int block_e);
  * H pass, chosen[1]: E pass; may be NULL) and restores the fields, so the
  * simulation does not advance. */
 mfd_status mfd_sim_autotune(mfd_sim* sim, int reps, int* chosen);
-/* Index format of the staggered and the 3D step kernels. The stencil sums are
- * the same in both formats (same entries, same order), so the fields are
- * bit-identical.
+/* Index format of the staggered step kernels. The stencil sums are the same
+ * in both formats (same entries, same order), so the fields are bit-identical.
  *   MFD_INDEX_Q16 (the default): per slice of 32 nodes (one warp) and per
- *     stencil stream, K bases and 16-bit entries, each naming a node in one of
- *     K windows of 65536 / K ids (staggered: K = 2 windows of 32768 ids per
- *     stream; 3D: K = 4 windows of 16384 ids on the shared index stream); a
- *     slice whose neighbour ids do not fit K windows (Morton seams and
- *     periodic wraps: about 0.5 % of slices in 2D, 3 % in 3D) keeps its 32-bit
- *     entries. Halves the index bytes each step reads.
+ *     stencil stream, two bases and 16-bit entries (id = b0 + u for
+ *     u < 32768, else b1 + u - 32768); a slice whose neighbour ids do not fit
+ *     two windows of 32768 ids (rare: Morton seams and periodic wraps) keeps
+ *     its 32-bit entries. Halves the index bytes each step reads.
  *   MFD_INDEX_I32: 32-bit entries everywhere.
- * The collocated 2D layout always reads 32-bit entries. Returns MFD_ERR_ARG
- * for another format. */
+ * The collocated and 3D layouts always read 32-bit entries. Returns
+ * MFD_ERR_ARG for another format. */
 #define MFD_INDEX_Q16 0
 #define MFD_INDEX_I32 1
 mfd_status mfd_sim_set_index_format(mfd_sim* sim, int format);
 /* out (host, 6 values) = {slices, slices whose curl stream is 32-bit, slices
- * whose HV stream is 32-bit} of the H pass, then the same of the E pass (3D:
- * one shared stream, so both counts are its 32-bit slices, and both passes
- * read it); zeros when the layout has no Q16 streams (collocated 2D). */
+ * whose HV stream is 32-bit} of the H pass, then the same of the E pass;
+ * zeros when the layout has no Q16 streams (collocated, 3D). */
 mfd_status mfd_sim_index_stats(const mfd_sim* sim, int64_t* out);
 /* Gradient of the probe objective J = dt sum_{n=1..N} sum_p (Ez_p^n)^2
  * (Ez at the probes of mfd_set_probes after each of the next N = nsteps

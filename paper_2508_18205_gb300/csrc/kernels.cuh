@@ -16,16 +16,14 @@
 //    ce = dt / (eps0 eps_r) of the node, 0 at a PEC node in 2D.
 //  * weight and index streams are read with L1::no_allocate so that L1 keeps
 //    the gathered fields of the Morton neighbourhood.
-//  * the staggered and the 3D step kernels read their indices in a 16-bit
-//    form (Q16): per slice and stream K bases (K = 2 windows of 32768 ids in
-//    the staggered layout, K = 4 windows of 16384 ids in 3D, where the Morton
-//    curve splits a slice's neighbourhood more often) and 16-bit entries
-//    u = k S + (node - b_k) for window k of size S. The bases are stored as
-//    B_k = b_k - k S, so the node is u + B_{u / S}. Chunks hold 8 entries
-//    (16 bytes) per lane, laid out like the 32-bit chunks. A slice whose
-//    neighbours do not fit K windows has B_0 < 0 and its kernels read the
-//    32-bit stream instead (the choice is per warp, so the branch does not
-//    diverge).
+//  * the staggered step kernels read their indices in a 16-bit form (Q16):
+//    per slice and stream two bases {b0, b1 - 32768}; entry u < 32768 is node
+//    b0 + u, entry u >= 32768 is node b1 + (u - 32768), so one slice may draw
+//    its neighbours from two index windows of 32768 nodes (a Morton seam or a
+//    periodic wrap). Chunks hold 8 entries (16 bytes) per lane, laid out like
+//    the 32-bit chunks. A slice whose neighbours do not fit two windows has
+//    b0 < 0 and its kernels read the 32-bit stream instead (the choice is per
+//    warp, so the branch does not diverge).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -168,9 +166,8 @@ template <typename T> struct StencilStreams {
     const int4* idx_v = nullptr;  // HV index chunks (== idx_c when shared)
     const uint4* q_c = nullptr;   // Q16 curl index chunks (8 entries), or null
     const uint4* q_v = nullptr;   // Q16 HV index chunks
-    const int2* qb_c = nullptr;   // Q16 bases of the curl stream, two windows per slice (staggered)
+    const int2* qb_c = nullptr;   // Q16 bases of the curl stream, one pair per slice
     const int2* qb_v = nullptr;   // Q16 bases of the HV stream
-    const int4* qb4 = nullptr;    // Q16 bases of the shared stream q_c, four windows per slice (3D)
     const typename Vec<T>::V4* wx = nullptr;
     const typename Vec<T>::V4* wy = nullptr;
     const typename Vec<T>::V4* wz = nullptr;
@@ -181,40 +178,32 @@ template <typename T> struct StencilStreams {
 
 // ---- Q16 index decoding (see the layout notes at the top)
 __device__ __forceinline__ int q16_id(unsigned u, int2 b) { return (int)u + ((u & 0x8000u) ? b.y : b.x); }
-__device__ __forceinline__ int q16_id(unsigned u, int4 b) {
-    const unsigned k = u >> 14;
-    const int lo = (k & 1u) ? b.y : b.x;
-    const int hi = (k & 1u) ? b.w : b.z;
-    return (int)u + ((k & 2u) ? hi : lo);
-}
-template <typename B> __device__ __forceinline__ int4 q16_lo(uint4 u, B b) {
+__device__ __forceinline__ int4 q16_lo(uint4 u, int2 b) {
     return make_int4(q16_id(u.x & 0xffffu, b), q16_id(u.x >> 16, b), q16_id(u.y & 0xffffu, b), q16_id(u.y >> 16, b));
 }
-template <typename B> __device__ __forceinline__ int4 q16_hi(uint4 u, B b) {
+__device__ __forceinline__ int4 q16_hi(uint4 u, int2 b) {
     return make_int4(q16_id(u.z & 0xffffu, b), q16_id(u.z >> 16, b), q16_id(u.w & 0xffffu, b), q16_id(u.w >> 16, b));
 }
-__device__ __forceinline__ int2 wide_bases(const int2*) { return make_int2(-1, 0); }
-__device__ __forceinline__ int4 wide_bases(const int4*) { return make_int4(-1, 0, 0, 0); }
 
-// Calls body(c, id) for the first N4 (or n4_rt when N4 == 0) chunks of 4
-// stencil entries of the node in lane `lane` of slice `slice`, in a stream of
-// row4 chunks of 4 per row, taking the indices from the Q16 stream when the
-// slice has one and from the 32-bit stream otherwise.
-template <int N4, typename B, typename Body>
-__device__ __forceinline__ void for_idx4(int n4_rt, int row4, int64_t slice, int lane, const int4* __restrict__ idx,
-                                         const uint4* __restrict__ q, const B* __restrict__ qb, Body&& body) {
+// Calls body(c, id) for the N4 (or n4_rt when N4 == 0) chunks of 4 stencil
+// entries of the node in lane `lane` of slice `slice`, taking the indices from
+// the Q16 stream when the slice has one and from the 32-bit stream otherwise.
+template <int N4, typename Body>
+__device__ __forceinline__ void for_idx4(int n4_rt, int64_t slice, int lane, const int4* __restrict__ idx,
+                                         const uint4* __restrict__ q, const int2* __restrict__ qb, Body&& body) {
     const int n4 = N4 ? N4 : n4_rt;
-    const B b = q ? ld_stream(qb + slice) : wide_bases(qb);
+    const int n8 = (n4 + 1) >> 1;
+    const int2 b = q ? ld_stream(qb + slice) : make_int2(-1, 0);
     if (b.x >= 0) {
-        const uint4* p = q + slice * ((row4 + 1) >> 1) * 32 + lane;
+        const uint4* p = q + slice * n8 * 32 + lane;
 #pragma unroll
-        for (int c8 = 0; c8 < (N4 ? (N4 + 1) / 2 : (n4 + 1) >> 1); ++c8) {
+        for (int c8 = 0; c8 < (N4 ? (N4 + 1) / 2 : n8); ++c8) {
             const uint4 u = ld_stream(p + c8 * 32);
             body(2 * c8, q16_lo(u, b));
             if (2 * c8 + 1 < n4) body(2 * c8 + 1, q16_hi(u, b));
         }
     } else {
-        const int4* p = idx + slice * row4 * 32 + lane;
+        const int4* p = idx + slice * n4 * 32 + lane;
 #pragma unroll
         for (int c = 0; c < n4; ++c) body(c, ld_stream(p + c * 32));
     }

@@ -51,54 +51,40 @@ __global__ void k_pack_w(const double* __restrict__ w, int64_t N, int n_use, int
     dst[e] = (node < N && entry < n_use) ? (T)w[node * n_use + entry] : (T)0;
 }
 
-// Q16 bases of one slice (one thread per slice), for KW windows of S = 65536 / KW
-// ids: window k opens at the smallest id the windows before it do not cover;
-// covering the ids with at most KW windows this way succeeds whenever any KW
-// windows of that size cover them. The slice is wide (B_0 = -1) when KW
-// windows do not suffice. Stored: B_k = b_k - k S (see kernels.cuh).
-template <int KW>
+// Q16 bases of one slice (one thread per slice): b0 is the smallest neighbour
+// id; b1 the smallest id past b0's window of 32768; the slice is wide (b0 = -1)
+// when an id falls outside both windows. Covering the ids with at most two
+// windows, each opened at the smallest id not yet covered, succeeds whenever
+// any two windows cover them.
 __global__ void k_q16_bases(const int32_t* __restrict__ src, int stride, int64_t N, int n_use, int64_t slices,
-                            int* __restrict__ bases, unsigned long long* __restrict__ wide) {
-    constexpr int64_t S = 65536 / KW;
+                            int2* __restrict__ bases, unsigned long long* __restrict__ wide) {
     const int64_t sl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (sl >= slices) return;
     const int64_t lo = sl * 32, hi = lo + 32 < N ? lo + 32 : N;
-    int64_t b[KW];
-    int used = 0;
-    for (int k = 0; k < KW; ++k) {
-        int64_t m = INT64_MAX;
-        for (int64_t i = lo; i < hi; ++i)
-            for (int e = 0; e < n_use; ++e) {
-                const int64_t v = src[i * stride + e];
-                bool cov = false;
-                for (int j = 0; j < used; ++j) cov = cov || (v >= b[j] && v < b[j] + S);
-                if (!cov) m = min(m, v);
-            }
-        if (m == INT64_MAX) break;
-        b[used++] = m;
-    }
-    bool ok = true;
-    for (int64_t i = lo; i < hi && ok; ++i)
+    int64_t b0 = INT64_MAX, b1 = INT64_MAX;
+    for (int64_t i = lo; i < hi; ++i)
+        for (int e = 0; e < n_use; ++e) b0 = min(b0, (int64_t)src[i * stride + e]);
+    for (int64_t i = lo; i < hi; ++i)
         for (int e = 0; e < n_use; ++e) {
             const int64_t v = src[i * stride + e];
-            bool cov = false;
-            for (int j = 0; j < used; ++j) cov = cov || (v >= b[j] && v < b[j] + S);
-            if (!cov) ok = false;
+            if (v > b0 + 32767) b1 = min(b1, v);
         }
-    int* out = bases + sl * KW;
-    for (int k = 0; k < KW; ++k) {
-        const int64_t bk = k < used ? b[k] : (used ? b[0] : 0);
-        out[k] = ok ? (int)(bk - k * S) : (k == 0 ? -1 : 0);
-    }
+    bool ok = true;
+    if (b1 != INT64_MAX)
+        for (int64_t i = lo; i < hi && ok; ++i)
+            for (int e = 0; e < n_use; ++e) {
+                const int64_t v = src[i * stride + e];
+                if (v > b0 + 32767 && v > b1 + 32767) ok = false;
+            }
+    if (b1 == INT64_MAX) b1 = b0 + 32768;
+    bases[sl] = ok ? make_int2((int)b0, (int)(b1 - 32768)) : make_int2(-1, 0);
     if (!ok) atomicAdd(wide, 1ull);
 }
 
 // Q16 entries, laid out as the 32-bit chunks with 8 entries per chunk:
 // element e -> (slice s, chunk c, lane l, entry q)
-template <int KW>
 __global__ void k_pack_q16(const int32_t* __restrict__ src, int stride, int64_t N, int n_use, int chunks8,
-                           const int* __restrict__ bases, uint16_t* __restrict__ dst, int64_t total) {
-    constexpr int64_t S = 65536 / KW;
+                           const int2* __restrict__ bases, uint16_t* __restrict__ dst, int64_t total) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= total) return;
     const int q = (int)(e & 7);
@@ -108,17 +94,11 @@ __global__ void k_pack_q16(const int32_t* __restrict__ src, int stride, int64_t 
     const int64_t sl = rest / chunks8;
     const int64_t node = sl * 32 + lane;
     const int entry = c * 8 + q;
-    const int* B = bases + sl * KW;
+    const int2 b = bases[sl];
     unsigned v = 0;
-    if (B[0] >= 0 && node < N) {
+    if (b.x >= 0 && node < N) {
         const int64_t id = src[node * stride + (entry < n_use ? entry : 0)];
-        for (int k = KW - 1; k >= 0; --k) {  // the last window that starts at or before id holds it
-            const int64_t bk = (int64_t)B[k] + k * S;
-            if (id >= bk && id < bk + S) {
-                v = (unsigned)(id - B[k]);
-                break;
-            }
-        }
+        v = id - b.x <= 32767 ? (unsigned)(id - b.x) : (unsigned)(id - b.y);
     }
     dst[e] = (uint16_t)v;
 }
@@ -302,32 +282,25 @@ mfd_status pack_weights(mfd_ctx* ctx, const mfd_weights* w, int out_index, int c
 
 int chunks_of(int n) { return (n + 3) / 4; }
 
-// Q16 form of one index stream (chunks4 chunks of 4 entries per row) with kw
-// windows (2 or 4) per slice
-mfd_status pack_q16(mfd_ctx* ctx, const mfd_stencils* st, int n_use, int chunks4, int kw, DevBuf& q, DevBuf& qb,
+// Q16 form of one index stream (chunks4 chunks of 4 entries per row)
+mfd_status pack_q16(mfd_ctx* ctx, const mfd_stencils* st, int n_use, int chunks4, DevBuf& q, DevBuf& qb,
                     int64_t& wide) {
     const int64_t N = st->centres->n;
     const int64_t slices = (N + 31) / 32;
     const int chunks8 = (chunks4 + 1) / 2;
     const int64_t total = slices * chunks8 * 256;
     MFD_TRY(q.alloc(total * 2));
-    MFD_TRY(qb.alloc(slices * kw * sizeof(int)));
+    MFD_TRY(qb.alloc(slices * sizeof(int2)));
     DevBuf cnt;
     MFD_TRY(cnt.alloc(8));
     MFD_CUDA(cudaMemsetAsync(cnt.p, 0, 8, ctx->stream));
-    const unsigned gb = (unsigned)((slices + 127) / 128), gp = (unsigned)((total + 255) / 256);
-    const int32_t* src = st->idx.as<int32_t>();
-    if (kw == 2) {
-        k_q16_bases<2><<<gb, 128, 0, ctx->stream>>>(src, st->n, N, n_use, slices, qb.as<int>(),
-                                                     cnt.as<unsigned long long>());
-        MFD_CUDA(cudaGetLastError());
-        k_pack_q16<2><<<gp, 256, 0, ctx->stream>>>(src, st->n, N, n_use, chunks8, qb.as<int>(), q.as<uint16_t>(), total);
-    } else {
-        k_q16_bases<4><<<gb, 128, 0, ctx->stream>>>(src, st->n, N, n_use, slices, qb.as<int>(),
-                                                     cnt.as<unsigned long long>());
-        MFD_CUDA(cudaGetLastError());
-        k_pack_q16<4><<<gp, 256, 0, ctx->stream>>>(src, st->n, N, n_use, chunks8, qb.as<int>(), q.as<uint16_t>(), total);
-    }
+    k_q16_bases<<<(unsigned)((slices + 127) / 128), 128, 0, ctx->stream>>>(st->idx.as<int32_t>(), st->n, N, n_use,
+                                                                          slices, qb.as<int2>(),
+                                                                          cnt.as<unsigned long long>());
+    MFD_CUDA(cudaGetLastError());
+    k_pack_q16<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(st->idx.as<int32_t>(), st->n, N, n_use,
+                                                                        chunks8, qb.as<int2>(), q.as<uint16_t>(),
+                                                                        total);
     MFD_CUDA(cudaGetLastError());
     unsigned long long w = 0;
     MFD_CUDA(cudaMemcpyAsync(&w, cnt.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -345,17 +318,13 @@ mfd_status pack_pass(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* h
     if (shared) {
         p.ni = std::max(p.nc, p.nv);
         MFD_TRY(pack_stream(ctx, curl->st, std::max(curl->n_use, hv->n_use), p.ni, p.idx_c));
-        if (dim == 3) {  // the shared stream of the 3D kernels, four windows per slice
-            MFD_TRY(pack_q16(ctx, curl->st, std::max(curl->n_use, hv->n_use), p.ni, 4, p.q_c, p.qb_c, p.wide_c));
-            p.wide_v = p.wide_c;
-        }
     } else {
         p.ni = p.nc;
         MFD_TRY(pack_stream(ctx, curl->st, curl->n_use, p.nc, p.idx_c));
         MFD_TRY(pack_stream(ctx, hv->st, hv->n_use, p.nv, p.idx_v));
         if (dim == 2 && curl->st->centres != curl->st->sources) {  // staggered
-            MFD_TRY(pack_q16(ctx, curl->st, curl->n_use, p.nc, 2, p.q_c, p.qb_c, p.wide_c));
-            MFD_TRY(pack_q16(ctx, hv->st, hv->n_use, p.nv, 2, p.q_v, p.qb_v, p.wide_v));
+            MFD_TRY(pack_q16(ctx, curl->st, curl->n_use, p.nc, p.q_c, p.qb_c, p.wide_c));
+            MFD_TRY(pack_q16(ctx, hv->st, hv->n_use, p.nv, p.q_v, p.qb_v, p.wide_v));
         }
     }
     MFD_TRY(pack_weights(ctx, curl, 0, p.nc, fp64, p.wx));
@@ -369,14 +338,11 @@ template <typename T> StencilStreams<T> streams(const PackedStencil& p, bool q16
     StencilStreams<T> s;
     s.idx_c = p.idx_c.as<const int4>();
     s.idx_v = p.idx_v.p ? p.idx_v.as<const int4>() : s.idx_c;
-    if (q16 && p.q_c.p && p.q_v.p) {  // staggered: two windows per slice and stream
+    if (q16 && p.q_c.p && p.q_v.p) {
         s.q_c = p.q_c.as<const uint4>();
         s.q_v = p.q_v.as<const uint4>();
         s.qb_c = p.qb_c.as<const int2>();
         s.qb_v = p.qb_v.as<const int2>();
-    } else if (q16 && p.q_c.p) {  // 3D: one shared stream, four windows per slice
-        s.q_c = p.q_c.as<const uint4>();
-        s.qb4 = p.qb_c.as<const int4>();
     }
     s.wx = p.wx.as<const typename Vec<T>::V4>();
     s.wy = p.wy.as<const typename Vec<T>::V4>();
@@ -425,8 +391,8 @@ Launch3D make3d(mfd_sim* sim, int parity) {
     Launch3D L;
     L.fp64 = sim->fp64;
     L.comp = sim->comp;
-    L.s.f = streams<float>(sim->hp, sim->q16);
-    L.s.d = streams<double>(sim->hp, sim->q16);
+    L.s.f = streams<float>(sim->hp);
+    L.s.d = streams<double>(sim->hp);
     L.kf.ch = (float)(sim->d.dt / sim->d.mu0);
     L.kf.gamma = (float)sim->d.gamma;
     L.kd.ch = sim->d.dt / sim->d.mu0;
@@ -1030,11 +996,10 @@ mfd_status mfd_sim_index_stats(const mfd_sim* sim, int64_t* out) {
     const PackedStencil* ps[2] = {&sim->hp, &sim->ep};
     for (int p = 0; p < 2; ++p) {
         const PackedStencil& k = *ps[p];
-        const PackedStencil& kk = sim->layout == COLLOC3D ? sim->hp : k;  // 3D: both passes read hp
-        const bool has = (sim->layout == STAG2D || sim->layout == COLLOC3D) && kk.q_c.p != nullptr;
-        out[3 * p] = has ? (kk.n + 31) / 32 : 0;
-        out[3 * p + 1] = has ? kk.wide_c : 0;
-        out[3 * p + 2] = has ? kk.wide_v : 0;
+        const bool has = sim->layout == STAG2D && k.q_c.p != nullptr;
+        out[3 * p] = has ? (k.n + 31) / 32 : 0;
+        out[3 * p + 1] = has ? k.wide_c : 0;
+        out[3 * p + 2] = has ? k.wide_v : 0;
     }
     return MFD_OK;
 }

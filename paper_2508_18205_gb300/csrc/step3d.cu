@@ -60,9 +60,11 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
         }
     };
     if constexpr (SHARED) {
-        constexpr int NI = (NC && NV) ? (NC > NV ? NC : NV) : 0;
-        const int ni = NI ? NI : s.ni;
-        for_idx4<NI>(ni, ni, slice, lane, s.idx_c, s.q_c, s.qb4, [&](int c, int4 id) {
+        const int ni = (NC && NV) ? (NC > NV ? NC : NV) : s.ni;
+        const int4* ip = s.idx_c + slice * ni * 32 + lane;
+#pragma unroll
+        for (int c = 0; c < ni; ++c) {
+            const int4 id = ld_stream(ip + c * 32);
             V4 e[4], h[4];
             if (c < nv) {
                 ld_gather_eh(F + 2 * (int64_t)id.x, e[0], h[0]);
@@ -77,7 +79,7 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
             }
             if (c < nc) curl4(ld_stream(px + c * 32), ld_stream(py + c * 32), ld_stream(pz + c * 32), e);
             if (c < nv) hv4(ld_stream(pv + c * 32), e, h);
-        });
+        }
     } else {
         const int4* ic = s.idx_c + slice * nc * 32 + lane;
         const int4* iv = s.idx_v + slice * nv * 32 + lane;
@@ -153,12 +155,14 @@ __global__ void __launch_bounds__(512, 2) k_e3(StencilStreams<T> s, const typena
     const int ni = SHARED ? s.ni : nc;
     const int64_t slice = i >> 5;
     const int lane = (int)(i & 31);
+    const int4* ip = s.idx_c + slice * ni * 32 + lane;
     const V4* px = s.wx + slice * nc * 32 + lane;
     const V4* py = s.wy + slice * nc * 32 + lane;
     const V4* pz = s.wz + slice * nc * 32 + lane;
     Acc a_yz, a_zy, a_zx, a_xz, a_xy, a_yx;
-    // the curl stencil is the first nc chunks of the index rows (ni chunks each)
-    for_idx4<NC>(nc, ni, slice, lane, s.idx_c, SHARED ? s.q_c : nullptr, s.qb4, [&](int c, int4 id) {
+#pragma unroll
+    for (int c = 0; c < nc; ++c) {
+        const int4 id = ld_stream(ip + c * 32);
         const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32), wz = ld_stream(pz + c * 32);
         V4 f[4];
         f[0] = ld_gather(Hn + id.x);
@@ -177,7 +181,7 @@ __global__ void __launch_bounds__(512, 2) k_e3(StencilStreams<T> s, const typena
             a_xy.add(wxa[q], f[q].y);
             a_yx.add(wya[q], f[q].x);
         }
-    });
+    }
     const V4 e = ld_gather(Es + i);
     const V4 hown = ld_gather(Hn + i);
     V4 o;

@@ -424,28 +424,3 @@ def test_staggered_q16_indices_with_two_windows_and_wide_slices(ctx, prec, comp,
     prob = O.tmz_staggered(e, h, n, 5, 4, alpha, dt, eps0, mu0, c)
     re, rx, ry, _, _ = O.run_tmz(prob, *f, 20)
     assert _rel_all(runs[0], [re, rx, ry]) <= tol
-
-
-def test_3d_q16_indices_four_windows_bit_identical(ctx):
-    """64^3 periodic nodes: the 3D shared index stream in the 16-bit form with
-    four windows per slice (some slices keep 32-bit entries) gives fields
-    bit-identical to the 32-bit form after 4 steps, from random fields."""
-    S, c, nx = 0.5, 1e-3, 64
-    dt, eps0, mu0, c0, eta0 = W.units(S)
-    nodes = W.periodic_box((nx, nx, nx), 0.25, 38)
-    sim = _gpu_colloc(ctx, nodes, 40, 3, 3, 2, dt, eps0, mu0, -c, 0, comp=True)
-    stats = sim.index_stats()
-    for p in ("h", "e"):
-        assert stats[p][0] == nx ** 3 // 32
-        assert 0 < stats[p][1] < stats[p][0] // 10, stats
-    rng = np.random.default_rng(39)
-    f = [rng.standard_normal(nodes.n) for _ in range(6)]
-    runs = []
-    for fmt in (M.MFD_INDEX_Q16, M.MFD_INDEX_I32):
-        sim.set_index_format(fmt)
-        for cc, v in enumerate(f):
-            sim.set_field(cc, v)
-        sim.step(4)
-        runs.append([sim.get_field(cc) for cc in range(6)])
-    for a, b in zip(*runs):
-        assert np.array_equal(a, b)
