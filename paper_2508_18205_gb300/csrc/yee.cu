@@ -1,9 +1,8 @@
 // yee.cu -- the FDTD (Yee) scheme for TMz (Eq. 4, Eq. 5) on a periodic grid:
 // the reference the paper compares its meshless method with (Sec. 3, Sec. 6).
 //
-// One fused kernel per step (two fused steps per launch in a persistent,
-// pipelined kernel when there are no sources and probes, below): a block of
-// 32 x 8 threads owns a 32 x 32 tile
+// One fused kernel per step (two fused steps per launch when there are no
+// sources and probes, below): a block of 32 x 8 threads owns a 32 x 32 tile
 // (four cells of a column per thread), stages Ez of the tile plus the one-cell
 // ring the stencil reads in shared memory, computes H' of the tile and of the
 // one-cell ring on its low sides (recomputed, not exchanged: the neighbour
@@ -15,7 +14,6 @@
 // Arithmetic follows Eq. 5 term by term with round-to-nearest operations (no
 // contraction), in the oracle's order, so FP64 results are reproducible
 // bit for bit.
-#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -112,50 +110,6 @@ __global__ void __launch_bounds__(YT_X * YB_Y, 8) k_yee(int nx, int ny, T ch, T 
     }
 }
 
-constexpr int Y2_T = 32;           // tile side
-constexpr int Y2_E = Y2_T + 4;     // staged Ez: x0-2 .. x0+33
-constexpr int Y2_H = Y2_T + 3;     // staged H:  x0-2 .. x0+32
-
-// One stage of the two-step kernel's shared memory: Ez with its 2-cell ring
-// ([r][c] = Ez at (x0 - 2 + c, y0 - 2 + r); E^n, then E^{n+1} in place) and
-// Hx / Hy with theirs (Hx at (x0 - 2 + c, y0 - 2 + r + 1/2), Hy at
-// (x0 - 2 + c + 1/2, y0 - 2 + r): old, then n+1/2, then n+3/2).
-template <typename T> struct Y2Stage {
-    T e[Y2_E][Y2_E];
-    T x[Y2_H][Y2_H];
-    T y[Y2_H][Y2_H];
-};
-
-__device__ __forceinline__ void cp_async(float* dst, const float* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async(double* dst, const double* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// requests the staged values of tile `tile` (asynchronous copies into st)
-template <typename T, bool BIG>
-__device__ __forceinline__ void y2_request(Y2Stage<T>& st, int tile, int ntx, int nx, int ny, const T* __restrict__ ez,
-                                           const T* __restrict__ hx, const T* __restrict__ hy) {
-    const int x0 = (tile % ntx) * Y2_T, y0 = (tile / ntx) * Y2_T;
-    const int t = threadIdx.y * YT_X + threadIdx.x;
-    constexpr int NT = YT_X * YB_Y;
-    for (int k = t; k < Y2_E * Y2_E; k += NT) {
-        const int r = k / Y2_E, c = k % Y2_E;
-        const int gx = wrap<BIG>(x0 - 2 + c, nx), gy = wrap<BIG>(y0 - 2 + r, ny);
-        const int64_t g = (int64_t)gy * nx + gx;
-        cp_async(&st.e[r][c], ez + g);
-        if (r < Y2_H && c < Y2_H) {
-            cp_async(&st.x[r][c], hx + g);
-            cp_async(&st.y[r][c], hy + g);
-        }
-    }
-}
-
 // Two steps per launch (temporal blocking), for runs without sources or probes
 // (their terms sit between the steps): a block stages Ez^n with a 2-cell ring
 // and the old H with the ring H^{n+1/2} needs, then computes in shared memory
@@ -164,71 +118,67 @@ __device__ __forceinline__ void y2_request(Y2Stage<T>& st, int tile, int ntx, in
 // writes the tile once: 6 reals of DRAM traffic per cell for two steps. Every
 // value is computed with the one-step kernel's arithmetic, so results match it
 // (and the reference in FP64) bit for bit.
-// The kernel is persistent and pipelined: a block walks the tiles with a
-// stride of the grid and requests the staged values of its next tile
-// (cp.async into the second of two stages) before it computes the current one,
-// so the DRAM latency of a tile's loads overlaps the previous tile's
-// arithmetic.
+constexpr int Y2_T = 32;           // tile side
+constexpr int Y2_E = Y2_T + 4;     // staged Ez: x0-2 .. x0+33
+constexpr int Y2_H = Y2_T + 3;     // staged H:  x0-2 .. x0+32
+
 template <typename T, bool BIG>
-__global__ void __launch_bounds__(YT_X * YB_Y, 4) k_yee2(int nx, int ny, int ntx, int ntiles, T ch, T ce,
-                                                         const T* __restrict__ ez, const T* __restrict__ hx,
-                                                         const T* __restrict__ hy, T* __restrict__ ez_o,
-                                                         T* __restrict__ hx_o, T* __restrict__ hy_o) {
-    extern __shared__ __align__(16) unsigned char y2_smem[];
-    Y2Stage<T>* stage = reinterpret_cast<Y2Stage<T>*>(y2_smem);
+__global__ void __launch_bounds__(YT_X * YB_Y, 4) k_yee2(int nx, int ny, T ch, T ce, const T* __restrict__ ez,
+                                                         const T* __restrict__ hx, const T* __restrict__ hy,
+                                                         T* __restrict__ ez_o, T* __restrict__ hx_o,
+                                                         T* __restrict__ hy_o) {
+    __shared__ T se[Y2_E][Y2_E];   // [r][c]: Ez at (x0 - 2 + c, y0 - 2 + r); E^n, then E^{n+1} in place
+    __shared__ T sx[Y2_H][Y2_H];   // Hx at (x0 - 2 + c, y0 - 2 + r + 1/2): old, then n+1/2, then n+3/2
+    __shared__ T sy[Y2_H][Y2_H];   // Hy at (x0 - 2 + c + 1/2, y0 - 2 + r)
+    const int x0 = blockIdx.x * Y2_T, y0 = blockIdx.y * Y2_T;
     const int t = threadIdx.y * YT_X + threadIdx.x;
     constexpr int NT = YT_X * YB_Y;
-    int tile = blockIdx.x, cur = 0;
-    if (tile < ntiles) y2_request<T, BIG>(stage[0], tile, ntx, nx, ny, ez, hx, hy);
-    cp_commit();
-    for (; tile < ntiles; tile += gridDim.x, cur ^= 1) {
-        const int next = tile + gridDim.x;
-        if (next < ntiles) y2_request<T, BIG>(stage[cur ^ 1], next, ntx, nx, ny, ez, hx, hy);
-        cp_commit();
-        cp_wait<1>();  // this tile's group has landed (the next tile's may still be in flight)
-        __syncthreads();
-        T(*se)[Y2_E] = stage[cur].e;
-        T(*sx)[Y2_H] = stage[cur].x;
-        T(*sy)[Y2_H] = stage[cur].y;
-        const int x0 = (tile % ntx) * Y2_T, y0 = (tile / ntx) * Y2_T;
-        // H^{n+1/2} on the whole staged H region (it reads Ez one cell up and right)
-        for (int k = t; k < Y2_H * Y2_H; k += NT) {
-            const int r = k / Y2_H, c = k % Y2_H;
-            const T e = se[r][c];
-            sx[r][c] = rn_sub(sx[r][c], rn_mul(ch, rn_sub(se[r + 1][c], e)));
-            sy[r][c] = rn_add(sy[r][c], rn_mul(ch, rn_sub(se[r][c + 1], e)));
+    for (int k = t; k < Y2_E * Y2_E; k += NT) {
+        const int r = k / Y2_E, c = k % Y2_E;
+        const int gx = wrap<BIG>(x0 - 2 + c, nx), gy = wrap<BIG>(y0 - 2 + r, ny);
+        const int64_t g = (int64_t)gy * nx + gx;
+        se[r][c] = ez[g];
+        if (r < Y2_H && c < Y2_H) {
+            sx[r][c] = hx[g];
+            sy[r][c] = hy[g];
         }
-        __syncthreads();
-        // E^{n+1} on x0-1 .. x0+32, y0-1 .. y0+32 (staged rows / columns 1 .. 34), in place
-        for (int k = t; k < (Y2_T + 2) * (Y2_T + 2); k += NT) {
-            const int r = 1 + k / (Y2_T + 2), c = 1 + k % (Y2_T + 2);
-            const T curl = rn_add(rn_sub(rn_sub(sy[r][c], sy[r][c - 1]), sx[r][c]), sx[r - 1][c]);
-            se[r][c] = rn_add(se[r][c], rn_mul(ce, curl));
-        }
-        __syncthreads();
-        // H^{n+3/2} on x0-1 .. x0+31, y0-1 .. y0+31 (staged 1 .. 33)
-        for (int k = t; k < (Y2_T + 1) * (Y2_T + 1); k += NT) {
-            const int r = 1 + k / (Y2_T + 1), c = 1 + k % (Y2_T + 1);
-            const T e = se[r][c];
-            sx[r][c] = rn_sub(sx[r][c], rn_mul(ch, rn_sub(se[r + 1][c], e)));
-            sy[r][c] = rn_add(sy[r][c], rn_mul(ch, rn_sub(se[r][c + 1], e)));
-        }
-        __syncthreads();
-        // E^{n+2} on the tile (staged 2 .. 33) and the tile's H^{n+3/2}, written once
-        for (int k = t; k < Y2_T * Y2_T; k += NT) {
-            const int r = 2 + k / Y2_T, c = 2 + k % Y2_T;
-            const int i = x0 + c - 2, j = y0 + r - 2;
-            if (i < nx && j < ny) {
-                const T curl = rn_add(rn_sub(rn_sub(sy[r][c], sy[r][c - 1]), sx[r][c]), sx[r - 1][c]);
-                const int64_t g = (int64_t)j * nx + i;
-                ez_o[g] = rn_add(se[r][c], rn_mul(ce, curl));
-                hx_o[g] = sx[r][c];
-                hy_o[g] = sy[r][c];
-            }
-        }
-        __syncthreads();  // the next iteration requests into the stage read above
     }
-    cp_wait<0>();
+    __syncthreads();
+    // H^{n+1/2} on the whole staged H region (it reads Ez one cell up and right)
+    for (int k = t; k < Y2_H * Y2_H; k += NT) {
+        const int r = k / Y2_H, c = k % Y2_H;
+        const T e = se[r][c];
+        sx[r][c] = rn_sub(sx[r][c], rn_mul(ch, rn_sub(se[r + 1][c], e)));
+        sy[r][c] = rn_add(sy[r][c], rn_mul(ch, rn_sub(se[r][c + 1], e)));
+    }
+    __syncthreads();
+    // E^{n+1} on x0-1 .. x0+32, y0-1 .. y0+32 (staged rows / columns 1 .. 34), in place
+    for (int k = t; k < (Y2_T + 2) * (Y2_T + 2); k += NT) {
+        const int r = 1 + k / (Y2_T + 2), c = 1 + k % (Y2_T + 2);
+        const T curl = rn_add(rn_sub(rn_sub(sy[r][c], sy[r][c - 1]), sx[r][c]), sx[r - 1][c]);
+        se[r][c] = rn_add(se[r][c], rn_mul(ce, curl));
+    }
+    __syncthreads();
+    // H^{n+3/2} on x0-1 .. x0+31, y0-1 .. y0+31 (staged 1 .. 33)
+    for (int k = t; k < (Y2_T + 1) * (Y2_T + 1); k += NT) {
+        const int r = 1 + k / (Y2_T + 1), c = 1 + k % (Y2_T + 1);
+        const T e = se[r][c];
+        sx[r][c] = rn_sub(sx[r][c], rn_mul(ch, rn_sub(se[r + 1][c], e)));
+        sy[r][c] = rn_add(sy[r][c], rn_mul(ch, rn_sub(se[r][c + 1], e)));
+    }
+    __syncthreads();
+    // E^{n+2} on the tile (staged 2 .. 33) and the tile's H^{n+3/2}, written once
+    for (int k = t; k < Y2_T * Y2_T; k += NT) {
+        const int r = 2 + k / Y2_T, c = 2 + k % Y2_T;
+        const int i = x0 + c - 2, j = y0 + r - 2;
+        if (i < nx && j < ny) {
+            const T curl = rn_add(rn_sub(rn_sub(sy[r][c], sy[r][c - 1]), sx[r][c]), sx[r - 1][c]);
+            const int64_t g = (int64_t)j * nx + i;
+            ez_o[g] = rn_add(se[r][c], rn_mul(ce, curl));
+            hx_o[g] = sx[r][c];
+            hy_o[g] = sy[r][c];
+        }
+    }
 }
 
 // soft Ricker sources after the E update, then probes, then the step counter
@@ -287,7 +237,6 @@ struct mfd_yee {
     cudaGraphExec_t graph = nullptr;
     bool graph_ok = false;
     cudaEvent_t ev[2] = {nullptr, nullptr};
-    int grid2 = 1;  // blocks of the persistent two-step kernel
     ~mfd_yee() {
         if (graph) cudaGraphExecDestroy(graph);
         for (auto& e : ev)
@@ -302,45 +251,28 @@ constexpr int YEE_GRAPH_STEPS = 32;
 // two steps in one launch; only without sources and probes
 cudaError_t yee_enqueue2(mfd_yee* y) {
     cudaStream_t s = y->ctx->stream;
+    const dim3 grid((unsigned)((y->nx + Y2_T - 1) / Y2_T), (unsigned)((y->ny + Y2_T - 1) / Y2_T));
     const dim3 block(YT_X, YB_Y);
     const int a = y->cur, b = y->cur ^ 1;
     const bool big = y->nx >= Y2_T + 2 && y->ny >= Y2_T + 2;  // the staged ring reaches x0 + 33
     const int nx = (int)y->nx, ny = (int)y->ny;
-    const int ntx = (nx + Y2_T - 1) / Y2_T, ntiles = ntx * ((ny + Y2_T - 1) / Y2_T);
-    const unsigned grid = (unsigned)std::min(y->grid2, ntiles);
     if (y->fp64) {
-        const size_t smem = 2 * sizeof(Y2Stage<double>);
         const double *e = y->f[a][0].as<double>(), *hx = y->f[a][1].as<double>(), *hy = y->f[a][2].as<double>();
         double *eo = y->f[b][0].as<double>(), *hxo = y->f[b][1].as<double>(), *hyo = y->f[b][2].as<double>();
-        if (big) k_yee2<double, true><<<grid, block, smem, s>>>(nx, ny, ntx, ntiles, y->ch, y->ce, e, hx, hy, eo, hxo, hyo);
-        else k_yee2<double, false><<<grid, block, smem, s>>>(nx, ny, ntx, ntiles, y->ch, y->ce, e, hx, hy, eo, hxo, hyo);
+        if (big) k_yee2<double, true><<<grid, block, 0, s>>>(nx, ny, y->ch, y->ce, e, hx, hy, eo, hxo, hyo);
+        else k_yee2<double, false><<<grid, block, 0, s>>>(nx, ny, y->ch, y->ce, e, hx, hy, eo, hxo, hyo);
     } else {
-        const size_t smem = 2 * sizeof(Y2Stage<float>);
         const float *e = y->f[a][0].as<float>(), *hx = y->f[a][1].as<float>(), *hy = y->f[a][2].as<float>();
         float *eo = y->f[b][0].as<float>(), *hxo = y->f[b][1].as<float>(), *hyo = y->f[b][2].as<float>();
         const float ch = (float)y->ch, ce = (float)y->ce;
-        if (big) k_yee2<float, true><<<grid, block, smem, s>>>(nx, ny, ntx, ntiles, ch, ce, e, hx, hy, eo, hxo, hyo);
-        else k_yee2<float, false><<<grid, block, smem, s>>>(nx, ny, ntx, ntiles, ch, ce, e, hx, hy, eo, hxo, hyo);
+        if (big) k_yee2<float, true><<<grid, block, 0, s>>>(nx, ny, ch, ce, e, hx, hy, eo, hxo, hyo);
+        else k_yee2<float, false><<<grid, block, 0, s>>>(nx, ny, ch, ce, e, hx, hy, eo, hxo, hyo);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     y->cur = b;
     y->steps += 2;
     return cudaSuccess;
-}
-
-// the two-step kernel's shared memory (two stages) and its persistent grid:
-// the resident blocks of every SM
-template <typename T> cudaError_t yee2_setup_t(mfd_yee* y) {
-    const size_t smem = 2 * sizeof(Y2Stage<T>);
-    cudaError_t e = cudaFuncSetAttribute(k_yee2<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_yee2<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0, sms = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_yee2<T, true>, YT_X * YB_Y, smem);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, y->ctx->device);
-    y->grid2 = std::max(1, per_sm) * std::max(1, sms);
-    return e;
 }
 
 cudaError_t yee_enqueue(mfd_yee* y) {
@@ -466,8 +398,7 @@ mfd_status mfd_yee_create(mfd_ctx* ctx, int64_t nx, int64_t ny, int precision, d
         for (int k = 0; k < 3; ++k) cudaMemsetAsync(y->f[p][k].p, 0, bytes, ctx->stream);
     cudaMemsetAsync(y->counter.p, 0, 8, ctx->stream);
     cudaMemsetAsync(y->pstep0.p, 0, 8, ctx->stream);
-    cudaError_t e = y->fp64 ? yee2_setup_t<double>(y) : yee2_setup_t<float>(y);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         delete y;
         return fail(MFD_ERR_CUDA, cudaGetErrorString(e));
