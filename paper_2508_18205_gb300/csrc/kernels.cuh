@@ -172,11 +172,6 @@ template <typename T> struct StencilStreams {
     const typename Vec<T>::V4* wy = nullptr;
     const typename Vec<T>::V4* wz = nullptr;
     const typename Vec<T>::V4* wv = nullptr;
-    // staggered layout: the curl weights interleaved by entry pairs, chunk j of a
-    // row = {wx_2j, wy_2j, wx_2j+1, wy_2j+1} (ncw = ceil(n / 2) chunks: no padding
-    // for even n), in place of wx and wy
-    const typename Vec<T>::V4* wxy = nullptr;
-    int ncw = 0;
     int nc = 0, nv = 0, ni = 0;  // chunks per row: curl weights, HV weights, index (shared: max)
     int64_t n = 0;               // nodes
 };

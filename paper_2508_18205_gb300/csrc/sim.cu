@@ -103,23 +103,6 @@ __global__ void k_pack_q16(const int32_t* __restrict__ src, int stride, int64_t 
     dst[e] = (uint16_t)v;
 }
 
-// curl weights of the staggered layout interleaved by entry pairs: element e ->
-// (slice s, chunk c, lane l, q), entry 2c + q / 2 of output q % 2 (Dx, Dy)
-template <typename T>
-__global__ void k_pack_wxy(const double* __restrict__ w, int64_t N, int n_use, int ncw, T* __restrict__ dst,
-                           int64_t total) {
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= total) return;
-    const int q = (int)(e & 3);
-    const int lane = (int)((e >> 2) & 31);
-    const int64_t rest = e >> 7;
-    const int c = (int)(rest % ncw);
-    const int64_t s = rest / ncw;
-    const int64_t node = s * 32 + lane;
-    const int entry = 2 * c + (q >> 1), comp = q & 1;
-    dst[e] = (node < N && entry < n_use) ? (T)w[((int64_t)comp * N + node) * n_use + entry] : (T)0;
-}
-
 template <typename T>
 __global__ void k_scatter(const double* __restrict__ src, const int64_t* __restrict__ inv, int64_t n,
                           T* __restrict__ base, int stride, int offset) {
@@ -228,10 +211,10 @@ __global__ void k_probe_samples(const T* __restrict__ buf, int np, int stride, i
 using namespace mfd;
 
 struct PackedStencil {
-    DevBuf idx_c, idx_v, wx, wy, wz, wv, wxy;
+    DevBuf idx_c, idx_v, wx, wy, wz, wv;
     DevBuf q_c, q_v, qb_c, qb_v;     // Q16 index streams and bases (staggered layout)
     int64_t wide_c = 0, wide_v = 0;  // slices left on the 32-bit streams
-    int nc = 0, nv = 0, ni = 0, ncw = 0;
+    int nc = 0, nv = 0, ni = 0;
     int64_t n = 0;
 };
 
@@ -344,19 +327,8 @@ mfd_status pack_pass(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* h
             MFD_TRY(pack_q16(ctx, hv->st, hv->n_use, p.nv, p.q_v, p.qb_v, p.wide_v));
         }
     }
-    if (dim == 2 && !shared && curl->st->centres != curl->st->sources) {  // staggered: interleaved Dx, Dy
-        p.ncw = (curl->n_use + 1) / 2;
-        const int64_t total = (p.n + 31) / 32 * p.ncw * 128;
-        MFD_TRY(p.wxy.alloc(total * (fp64 ? 8 : 4)));
-        const double* src = curl->w.as<double>();
-        const unsigned g = (unsigned)((total + 255) / 256);
-        if (fp64) k_pack_wxy<double><<<g, 256, 0, ctx->stream>>>(src, p.n, curl->n_use, p.ncw, p.wxy.as<double>(), total);
-        else k_pack_wxy<float><<<g, 256, 0, ctx->stream>>>(src, p.n, curl->n_use, p.ncw, p.wxy.as<float>(), total);
-        MFD_CUDA(cudaGetLastError());
-    } else {
-        MFD_TRY(pack_weights(ctx, curl, 0, p.nc, fp64, p.wx));
-        MFD_TRY(pack_weights(ctx, curl, 1, p.nc, fp64, p.wy));
-    }
+    MFD_TRY(pack_weights(ctx, curl, 0, p.nc, fp64, p.wx));
+    MFD_TRY(pack_weights(ctx, curl, 1, p.nc, fp64, p.wy));
     if (dim == 3) MFD_TRY(pack_weights(ctx, curl, 2, p.nc, fp64, p.wz));
     MFD_TRY(pack_weights(ctx, hv, 0, p.nv, fp64, p.wv));
     return MFD_OK;
@@ -372,10 +344,8 @@ template <typename T> StencilStreams<T> streams(const PackedStencil& p, bool q16
         s.qb_c = p.qb_c.as<const int2>();
         s.qb_v = p.qb_v.as<const int2>();
     }
-    s.wx = p.wx.p ? p.wx.as<const typename Vec<T>::V4>() : nullptr;
-    s.wy = p.wy.p ? p.wy.as<const typename Vec<T>::V4>() : nullptr;
-    s.wxy = p.wxy.p ? p.wxy.as<const typename Vec<T>::V4>() : nullptr;
-    s.ncw = p.ncw;
+    s.wx = p.wx.as<const typename Vec<T>::V4>();
+    s.wy = p.wy.as<const typename Vec<T>::V4>();
     s.wz = p.wz.p ? p.wz.as<const typename Vec<T>::V4>() : nullptr;
     s.wv = p.wv.as<const typename Vec<T>::V4>();
     s.nc = p.nc;

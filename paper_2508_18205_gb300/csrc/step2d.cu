@@ -174,20 +174,6 @@ __global__ void __launch_bounds__(256) k_energy_colloc(StencilStreams<T> s, Coef
 
 // ------------------------------------------------------------ staggered
 
-// the Dx and Dy weights of curl chunk c (entries 4c .. 4c + 3) from the
-// interleaved stream: pair chunks 2c and 2c + 1 (the second absent past the
-// row's end, where the entries carry weight 0 as padding does)
-template <typename T>
-__device__ __forceinline__ void wxy_chunk(const typename Vec<T>::V4* p, int c, int ncw, typename Vec<T>::V4& wx,
-                                          typename Vec<T>::V4& wy) {
-    using V4 = typename Vec<T>::V4;
-    const V4 a = ld_stream(p + (2 * c) * 32);
-    V4 b{};
-    if (2 * c + 1 < ncw) b = ld_stream(p + (2 * c + 1) * 32);
-    wx = V4{a.x, a.z, b.x, b.z};
-    wy = V4{a.y, a.w, b.y, b.w};
-}
-
 template <typename T, int NC, int NV, bool COMP>
 __device__ __forceinline__ void h_stag_node(const StencilStreams<T>& s, const T* __restrict__ Ez,
                                             const typename Vec<T>::V2* __restrict__ H, int64_t i, T& dxE, T& dyE,
@@ -200,7 +186,8 @@ __device__ __forceinline__ void h_stag_node(const StencilStreams<T>& s, const T*
     const int nv = NV ? NV : s.nv;
     const int64_t slice = i >> 5;
     const int lane = (int)(i & 31);
-    const V4* pxy = s.wxy + slice * s.ncw * 32 + lane;
+    const V4* px = s.wx + slice * nc * 32 + lane;
+    const V4* py = s.wy + slice * nc * 32 + lane;
     const V4* pv = s.wv + slice * nv * 32 + lane;
     Acc ax, ay;
     AccV hx, hy;
@@ -214,8 +201,7 @@ __device__ __forceinline__ void h_stag_node(const StencilStreams<T>& s, const T*
         hy.add(wv.x, f0.y); hy.add(wv.y, f1.y); hy.add(wv.z, f2.y); hy.add(wv.w, f3.y);
     });
     for_idx4<NC>(nc, slice, lane, s.idx_c, s.q_c, s.qb_c, [&](int c, int4 id) {
-        V4 wx, wy;
-        wxy_chunk<T>(pxy, c, s.ncw, wx, wy);
+        const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32);
         const T f0 = ld_gather(Ez + id.x), f1 = ld_gather(Ez + id.y);
         const T f2 = ld_gather(Ez + id.z), f3 = ld_gather(Ez + id.w);
         ax.add(wx.x, f0); ax.add(wx.y, f1); ax.add(wx.z, f2); ax.add(wx.w, f3);
@@ -256,13 +242,13 @@ __global__ void __launch_bounds__(512) k_e_stag(StencilStreams<T> s, Coefs<T> k,
     const int nv = NV ? NV : s.nv;
     const int64_t slice = i >> 5;
     const int lane = (int)(i & 31);
-    const V4* pxy = s.wxy + slice * s.ncw * 32 + lane;
+    const V4* px = s.wx + slice * nc * 32 + lane;
+    const V4* py = s.wy + slice * nc * 32 + lane;
     const V4* pv = s.wv + slice * nv * 32 + lane;
     Acc dxHy, dyHx;
     AccPlain<T> he;
     for_idx4<NC>(nc, slice, lane, s.idx_c, s.q_c, s.qb_c, [&](int c, int4 id) {
-        V4 wx, wy;
-        wxy_chunk<T>(pxy, c, s.ncw, wx, wy);
+        const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32);
         const V2 f0 = ld_gather(Hn + id.x), f1 = ld_gather(Hn + id.y);
         const V2 f2 = ld_gather(Hn + id.z), f3 = ld_gather(Hn + id.w);
         dxHy.add(wx.x, f0.y); dxHy.add(wx.y, f1.y); dxHy.add(wx.z, f2.y); dxHy.add(wx.w, f3.y);
