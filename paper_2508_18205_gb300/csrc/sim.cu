@@ -20,8 +20,14 @@ constexpr int GRAPH_STEPS = 32;  // steps per captured graph (even: ping-pong pa
 // ------------------------------------------------------------ packing kernels
 
 // sliced layout: element e -> (slice s, chunk c, lane l, entry q)
+// packed entry j of row r comes from stencil entry perm[r * plen + j] when a
+// permutation is given (see k_row_perm), else from entry j
+__device__ __forceinline__ int src_entry(const uint8_t* perm, int plen, int64_t node, int j) {
+    return perm ? (int)perm[node * plen + j] : j;
+}
+
 __global__ void k_pack_idx(const int32_t* __restrict__ src, int stride, int64_t N, int n_use, int chunks,
-                           int32_t* __restrict__ dst, int64_t total) {
+                           const uint8_t* __restrict__ perm, int plen, int32_t* __restrict__ dst, int64_t total) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= total) return;
     int q = (int)(e & 3);
@@ -32,13 +38,13 @@ __global__ void k_pack_idx(const int32_t* __restrict__ src, int stride, int64_t 
     int64_t node = s * 32 + lane;
     int entry = c * 4 + q;
     int32_t v = 0;
-    if (node < N) v = src[node * stride + (entry < n_use ? entry : 0)];
+    if (node < N) v = src[node * stride + src_entry(perm, plen, node, entry < n_use ? entry : 0)];
     dst[e] = v;
 }
 
 template <typename T>
-__global__ void k_pack_w(const double* __restrict__ w, int64_t N, int n_use, int chunks, T* __restrict__ dst,
-                         int64_t total) {
+__global__ void k_pack_w(const double* __restrict__ w, int64_t N, int n_use, int chunks,
+                         const uint8_t* __restrict__ perm, int plen, T* __restrict__ dst, int64_t total) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= total) return;
     int q = (int)(e & 3);
@@ -48,7 +54,36 @@ __global__ void k_pack_w(const double* __restrict__ w, int64_t N, int n_use, int
     int64_t s = rest / chunks;
     int64_t node = s * 32 + lane;
     int entry = c * 4 + q;
-    dst[e] = (node < N && entry < n_use) ? (T)w[node * n_use + entry] : (T)0;
+    dst[e] = (node < N && entry < n_use) ? (T)w[node * n_use + src_entry(perm, plen, node, entry)] : (T)0;
+}
+
+// Order of the packed entries of a shared index row (3D): ascending neighbour id
+// within the curl part [0, nc) and within the rest [nc, L), one thread per row.
+// The entries of a row keep their weights (the same permutation packs both), so
+// a stencil sum is the same sum in another order. Adjacent centres' neighbour
+// sets overlap, so ordering by id lines up the k-th gathers of a warp's
+// centres: they touch fewer cache lines per warp load (15 % fewer on the
+// jittered 3D lattice) in a pass that is bound by the L1 data pipeline.
+__global__ void k_row_perm(const int32_t* __restrict__ src, int stride, int64_t N, int nc, int L,
+                           uint8_t* __restrict__ perm) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const int32_t* s = src + r * stride;
+    uint8_t p[255];
+    for (int j = 0; j < L; ++j) p[j] = (uint8_t)j;
+    const int lo[2] = {0, nc}, hi[2] = {nc, L};
+    for (int part = 0; part < 2; ++part)
+        for (int j = lo[part] + 1; j < hi[part]; ++j) {
+            const uint8_t pj = p[j];
+            const int32_t v = s[pj];
+            int k = j - 1;
+            while (k >= lo[part] && s[p[k]] > v) {
+                p[k + 1] = p[k];
+                --k;
+            }
+            p[k + 1] = pj;
+        }
+    for (int j = 0; j < L; ++j) perm[r * L + j] = p[j];
 }
 
 // Q16 bases of one slice (one thread per slice): b0 is the smallest neighbour
@@ -256,26 +291,30 @@ struct mfd_sim {
 
 namespace {
 
-mfd_status pack_stream(mfd_ctx* ctx, const mfd_stencils* st, int n_use, int chunks, DevBuf& out) {
+mfd_status pack_stream(mfd_ctx* ctx, const mfd_stencils* st, int n_use, int chunks, DevBuf& out,
+                       const DevBuf* perm = nullptr, int plen = 0) {
     const int64_t N = st->centres->n;
     const int64_t slices = (N + 31) / 32;
     const int64_t total = slices * chunks * 128;
     MFD_TRY(out.alloc(total * 4));
+    const uint8_t* pm = perm && perm->p ? perm->as<uint8_t>() : nullptr;
     k_pack_idx<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(st->idx.as<int32_t>(), st->n, N, n_use,
-                                                                         chunks, out.as<int32_t>(), total);
+                                                                         chunks, pm, plen, out.as<int32_t>(), total);
     MFD_CUDA(cudaGetLastError());
     return MFD_OK;
 }
 
-mfd_status pack_weights(mfd_ctx* ctx, const mfd_weights* w, int out_index, int chunks, bool fp64, DevBuf& out) {
+mfd_status pack_weights(mfd_ctx* ctx, const mfd_weights* w, int out_index, int chunks, bool fp64, DevBuf& out,
+                        const DevBuf* perm = nullptr, int plen = 0) {
     const int64_t N = w->st->centres->n;
     const int64_t slices = (N + 31) / 32;
     const int64_t total = slices * chunks * 128;
     MFD_TRY(out.alloc(total * (fp64 ? 8 : 4)));
     const double* src = w->w.as<double>() + (int64_t)out_index * N * w->n_use;
+    const uint8_t* pm = perm && perm->p ? perm->as<uint8_t>() : nullptr;
     unsigned g = (unsigned)((total + 255) / 256);
-    if (fp64) k_pack_w<double><<<g, 256, 0, ctx->stream>>>(src, N, w->n_use, chunks, out.as<double>(), total);
-    else k_pack_w<float><<<g, 256, 0, ctx->stream>>>(src, N, w->n_use, chunks, out.as<float>(), total);
+    if (fp64) k_pack_w<double><<<g, 256, 0, ctx->stream>>>(src, N, w->n_use, chunks, pm, plen, out.as<double>(), total);
+    else k_pack_w<float><<<g, 256, 0, ctx->stream>>>(src, N, w->n_use, chunks, pm, plen, out.as<float>(), total);
     MFD_CUDA(cudaGetLastError());
     return MFD_OK;
 }
@@ -315,9 +354,19 @@ mfd_status pack_pass(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* h
     p.nc = chunks_of(curl->n_use);
     p.nv = chunks_of(hv->n_use);
     const bool shared = curl->st == hv->st;
+    DevBuf perm;
+    int plen = 0;
     if (shared) {
         p.ni = std::max(p.nc, p.nv);
-        MFD_TRY(pack_stream(ctx, curl->st, std::max(curl->n_use, hv->n_use), p.ni, p.idx_c));
+        plen = std::max(curl->n_use, hv->n_use);
+        if (dim == 3 && hv->n_use >= curl->n_use && plen <= 255) {  // 3D: rows in ascending id order (k_row_perm)
+            const int64_t N = curl->st->centres->n;
+            MFD_TRY(perm.alloc(N * plen));
+            k_row_perm<<<(unsigned)((N + 127) / 128), 128, 0, ctx->stream>>>(curl->st->idx.as<int32_t>(), curl->st->n,
+                                                                            N, curl->n_use, plen, perm.as<uint8_t>());
+            MFD_CUDA(cudaGetLastError());
+        }
+        MFD_TRY(pack_stream(ctx, curl->st, plen, p.ni, p.idx_c, &perm, plen));
     } else {
         p.ni = p.nc;
         MFD_TRY(pack_stream(ctx, curl->st, curl->n_use, p.nc, p.idx_c));
@@ -327,10 +376,11 @@ mfd_status pack_pass(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* h
             MFD_TRY(pack_q16(ctx, hv->st, hv->n_use, p.nv, p.q_v, p.qb_v, p.wide_v));
         }
     }
-    MFD_TRY(pack_weights(ctx, curl, 0, p.nc, fp64, p.wx));
-    MFD_TRY(pack_weights(ctx, curl, 1, p.nc, fp64, p.wy));
-    if (dim == 3) MFD_TRY(pack_weights(ctx, curl, 2, p.nc, fp64, p.wz));
-    MFD_TRY(pack_weights(ctx, hv, 0, p.nv, fp64, p.wv));
+    MFD_TRY(pack_weights(ctx, curl, 0, p.nc, fp64, p.wx, &perm, plen));
+    MFD_TRY(pack_weights(ctx, curl, 1, p.nc, fp64, p.wy, &perm, plen));
+    if (dim == 3) MFD_TRY(pack_weights(ctx, curl, 2, p.nc, fp64, p.wz, &perm, plen));
+    MFD_TRY(pack_weights(ctx, hv, 0, p.nv, fp64, p.wv, &perm, plen));
+    MFD_CUDA(cudaStreamSynchronize(ctx->stream));  // perm is freed on return
     return MFD_OK;
 }
 
