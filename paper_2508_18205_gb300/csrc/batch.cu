@@ -363,8 +363,15 @@ __global__ void k_benergy_sum(const double* __restrict__ partial, int nblocks, i
     u[r] = s;
 }
 
+// packed entry j of a row comes from stencil entry perm[node * plen + j] (the
+// id order of launch_row_perm) when perm is given
+__device__ __forceinline__ int bsrc_entry(const uint8_t* perm, int plen, int64_t node, int j) {
+    return perm ? (int)perm[node * plen + j] : j;
+}
+
 __global__ void k_bpack_idx(const int32_t* __restrict__ src, int stride, int n_use, int64_t N, int chunks, int npw,
-                            int64_t node0, int32_t* __restrict__ dst, int64_t total) {
+                            int64_t node0, const uint8_t* __restrict__ perm, int plen, int32_t* __restrict__ dst,
+                            int64_t total) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= total) return;
     const int q = (int)(e & 3);
@@ -376,12 +383,12 @@ __global__ void k_bpack_idx(const int32_t* __restrict__ src, int stride, int n_u
     const int64_t node = s * npw + g;
     const int entry = c * 4 + q;
     int32_t v = (int32_t)node0;
-    if (node < N) v = (int32_t)(node0 + src[node * stride + (entry < n_use ? entry : 0)]);
+    if (node < N) v = (int32_t)(node0 + src[node * stride + bsrc_entry(perm, plen, node, entry < n_use ? entry : 0)]);
     dst[e] = v;
 }
 
 __global__ void k_bpack_w(const double* __restrict__ w, int n_use, int64_t N, int chunks, int npw,
-                          float* __restrict__ dst, int64_t total) {
+                          const uint8_t* __restrict__ perm, int plen, float* __restrict__ dst, int64_t total) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= total) return;
     const int q = (int)(e & 3);
@@ -392,7 +399,7 @@ __global__ void k_bpack_w(const double* __restrict__ w, int n_use, int64_t N, in
     const int64_t s = r2 / chunks;
     const int64_t node = s * npw + g;
     const int entry = c * 4 + q;
-    dst[e] = (node < N && entry < n_use) ? (float)w[node * n_use + entry] : 0.0f;
+    dst[e] = (node < N && entry < n_use) ? (float)w[node * n_use + bsrc_entry(perm, plen, node, entry)] : 0.0f;
 }
 
 __global__ void k_bscatter(const double* __restrict__ src, const int64_t* __restrict__ inv, int64_t n, int nrhs_src,
@@ -697,24 +704,39 @@ mfd_status mfd_batch_create(mfd_ctx* ctx, int ndom, const mfd_sim_desc* descs, i
     cudaMemsetAsync(b->counter.p, 0, 8, s);
     cudaMemsetAsync(b->pstep0.p, 0, 8, s);
     cudaMemsetAsync(b->bar.p, 0, 16, s);
+    cudaError_t e0 = cudaSuccess;
     for (int d = 0; d < ndom; ++d) {
         const mfd_weights* cw = descs[d].h_curl;
         const mfd_weights* hw = descs[d].h_hv;
         const BDom& h = hd[d];
         const int64_t N = h.n;
         const int64_t slices = (N + NPW - 1) / NPW;
+        // rows in ascending neighbour id within the shorter stencil and the rest (launch_row_perm)
+        const int plen = std::max(cw->n_use, hw->n_use);
+        DevBuf perm;
+        if (plen <= 255) {
+            if ((st = perm.alloc(N * plen))) return bail(st);
+            e0 = launch_row_perm(cw->st->idx.as<int32_t>(), cw->st->n, N, std::min(cw->n_use, hw->n_use), plen,
+                                 perm.as<uint8_t>(), s);
+            if (e0 != cudaSuccess) return bail(fail(MFD_ERR_CUDA, cudaGetErrorString(e0)));
+        }
+        const uint8_t* pm = perm.p ? perm.as<uint8_t>() : nullptr;
         int64_t tot = slices * h.ni * NPW * 4;
-        k_bpack_idx<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(cw->st->idx.as<int32_t>(), cw->st->n,
-                                                                   std::max(cw->n_use, hw->n_use), N, h.ni, NPW,
-                                                                   h.node0, b->idx.as<int32_t>() + h.idx0 * 4, tot);
+        k_bpack_idx<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(cw->st->idx.as<int32_t>(), cw->st->n, plen, N, h.ni,
+                                                                   NPW, h.node0, pm, plen,
+                                                                   b->idx.as<int32_t>() + h.idx0 * 4, tot);
         tot = slices * h.nc * NPW * 4;
-        k_bpack_w<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(cw->w.as<double>(), cw->n_use, N, h.nc, NPW,
+        k_bpack_w<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(cw->w.as<double>(), cw->n_use, N, h.nc, NPW, pm, plen,
                                                                  b->wx.as<float>() + h.wc0 * 4, tot);
         k_bpack_w<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(cw->w.as<double>() + N * cw->n_use, cw->n_use, N, h.nc,
-                                                                 NPW, b->wy.as<float>() + h.wc0 * 4, tot);
+                                                                 NPW, pm, plen, b->wy.as<float>() + h.wc0 * 4, tot);
         tot = slices * h.nv * NPW * 4;
-        k_bpack_w<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(hw->w.as<double>(), hw->n_use, N, h.nv, NPW,
+        k_bpack_w<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(hw->w.as<double>(), hw->n_use, N, h.nv, NPW, pm, plen,
                                                                  b->wv.as<float>() + h.wv0 * 4, tot);
+        if (pm) {  // perm is freed at the end of this iteration
+            e0 = cudaStreamSynchronize(s);
+            if (e0 != cudaSuccess) return bail(fail(MFD_ERR_CUDA, cudaGetErrorString(e0)));
+        }
         k_bmaterials<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(nullptr, nullptr, b->dom[d].nodes->perm.as<int64_t>(), N,
                                                                  h.node0, descs[d].dt / descs[d].eps0, b->ce.as<float>(),
                                                                  b->A.as<float>(), R);

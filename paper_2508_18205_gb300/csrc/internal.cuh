@@ -130,6 +130,10 @@ mfd_status morton_order(mfd_ctx* ctx, int dim, int64_t n, const double* d_xyz_us
 mfd_status knn_build(const mfd_nodes* centres, const mfd_nodes* sources, int n, int32_t* d_idx);
 mfd_status weights_solve(const mfd_stencils* st, int n_use, int phs_k, int poly_m, int op, int alpha,
                          double delta, double* d_w);
+// per row of a shared index array (n rows of `stride` entries, len <= 255 used):
+// the order that sorts entries [0, m) and [m, len) by neighbour id (k_row_perm)
+cudaError_t launch_row_perm(const int32_t* idx, int stride, int64_t n, int m, int len, uint8_t* perm,
+                            cudaStream_t s);
 
 // ------------------------------------------------------------ dispersion (Sec. 6)
 

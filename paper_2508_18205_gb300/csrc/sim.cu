@@ -57,34 +57,6 @@ __global__ void k_pack_w(const double* __restrict__ w, int64_t N, int n_use, int
     dst[e] = (node < N && entry < n_use) ? (T)w[node * n_use + src_entry(perm, plen, node, entry)] : (T)0;
 }
 
-// Order of the packed entries of a shared index row (3D): ascending neighbour id
-// within the curl part [0, nc) and within the rest [nc, L), one thread per row.
-// The entries of a row keep their weights (the same permutation packs both), so
-// a stencil sum is the same sum in another order. Adjacent centres' neighbour
-// sets overlap, so ordering by id lines up the k-th gathers of a warp's
-// centres: they touch fewer cache lines per warp load (15 % fewer on the
-// jittered 3D lattice) in a pass that is bound by the L1 data pipeline.
-__global__ void k_row_perm(const int32_t* __restrict__ src, int stride, int64_t N, int nc, int L,
-                           uint8_t* __restrict__ perm) {
-    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r >= N) return;
-    const int32_t* s = src + r * stride;
-    uint8_t p[255];
-    for (int j = 0; j < L; ++j) p[j] = (uint8_t)j;
-    const int lo[2] = {0, nc}, hi[2] = {nc, L};
-    for (int part = 0; part < 2; ++part)
-        for (int j = lo[part] + 1; j < hi[part]; ++j) {
-            const uint8_t pj = p[j];
-            const int32_t v = s[pj];
-            int k = j - 1;
-            while (k >= lo[part] && s[p[k]] > v) {
-                p[k + 1] = p[k];
-                --k;
-            }
-            p[k + 1] = pj;
-        }
-    for (int j = 0; j < L; ++j) perm[r * L + j] = p[j];
-}
 
 // Q16 bases of one slice (one thread per slice): b0 is the smallest neighbour
 // id; b1 the smallest id past b0's window of 32768; the slice is wide (b0 = -1)
@@ -359,12 +331,11 @@ mfd_status pack_pass(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* h
     if (shared) {
         p.ni = std::max(p.nc, p.nv);
         plen = std::max(curl->n_use, hv->n_use);
-        if (dim == 3 && hv->n_use >= curl->n_use && plen <= 255) {  // 3D: rows in ascending id order (k_row_perm)
+        if (dim == 3 && plen <= 255) {  // 3D: rows in ascending id order (k_row_perm)
             const int64_t N = curl->st->centres->n;
             MFD_TRY(perm.alloc(N * plen));
-            k_row_perm<<<(unsigned)((N + 127) / 128), 128, 0, ctx->stream>>>(curl->st->idx.as<int32_t>(), curl->st->n,
-                                                                            N, curl->n_use, plen, perm.as<uint8_t>());
-            MFD_CUDA(cudaGetLastError());
+            MFD_CUDA(launch_row_perm(curl->st->idx.as<int32_t>(), curl->st->n, N,
+                                     std::min(curl->n_use, hv->n_use), plen, perm.as<uint8_t>(), ctx->stream));
         }
         MFD_TRY(pack_stream(ctx, curl->st, plen, p.ni, p.idx_c, &perm, plen));
     } else {
