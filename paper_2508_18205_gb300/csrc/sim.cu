@@ -331,7 +331,7 @@ mfd_status pack_pass(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* h
     if (shared) {
         p.ni = std::max(p.nc, p.nv);
         plen = std::max(curl->n_use, hv->n_use);
-        if (dim == 3 && plen <= 255) {  // 3D: rows in ascending id order (k_row_perm)
+        if (plen <= 255) {  // rows in ascending id order (launch_row_perm)
             const int64_t N = curl->st->centres->n;
             MFD_TRY(perm.alloc(N * plen));
             MFD_CUDA(launch_row_perm(curl->st->idx.as<int32_t>(), curl->st->n, N,
