@@ -711,14 +711,13 @@ mfd_status mfd_batch_create(mfd_ctx* ctx, int ndom, const mfd_sim_desc* descs, i
         const BDom& h = hd[d];
         const int64_t N = h.n;
         const int64_t slices = (N + NPW - 1) / NPW;
-        // the rows of a warp's nodes with aligned slots within the shorter stencil and the rest
-        // (launch_slot_align)
+        // rows in ascending neighbour id within the shorter stencil and the rest (launch_row_perm)
         const int plen = std::max(cw->n_use, hw->n_use);
         DevBuf perm;
         if (plen <= 255) {
             if ((st = perm.alloc(N * plen))) return bail(st);
-            e0 = launch_slot_align(cw->st->idx.as<int32_t>(), cw->st->n, N, NPW, std::min(cw->n_use, hw->n_use), plen,
-                                   perm.as<uint8_t>(), s);
+            e0 = launch_row_perm(cw->st->idx.as<int32_t>(), cw->st->n, N, std::min(cw->n_use, hw->n_use), plen,
+                                 perm.as<uint8_t>(), s);
             if (e0 != cudaSuccess) return bail(fail(MFD_ERR_CUDA, cudaGetErrorString(e0)));
         }
         const uint8_t* pm = perm.p ? perm.as<uint8_t>() : nullptr;

@@ -134,11 +134,6 @@ mfd_status weights_solve(const mfd_stencils* st, int n_use, int phs_k, int poly_
 // the order that sorts entries [0, m) and [m, len) by neighbour id (k_row_perm)
 cudaError_t launch_row_perm(const int32_t* idx, int stride, int64_t n, int m, int len, uint8_t* perm,
                             cudaStream_t s);
-// the same for groups of `group` (<= 32) consecutive rows stepped by one warp:
-// slots aligned so that the group's rows name the same node in a slot as often
-// as their neighbour sets allow (k_slot_align)
-cudaError_t launch_slot_align(const int32_t* idx, int stride, int64_t n, int group, int m, int len, uint8_t* perm,
-                              cudaStream_t s);
 
 // ------------------------------------------------------------ dispersion (Sec. 6)
 

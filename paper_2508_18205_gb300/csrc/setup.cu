@@ -134,105 +134,6 @@ cudaError_t launch_row_perm(const int32_t* idx, int stride, int64_t n, int m, in
     return cudaGetLastError();
 }
 
-// Slot alignment of a group of G consecutive rows (the rows one warp steps
-// together), within [0, m) and within [m, len) of the rows: slot by slot, the
-// node held by the most rows' unplaced entries (ties: the smallest id) goes to
-// that slot in every row holding it, and each other row places its smallest
-// unplaced id there. The k-th gathers of the warp then name the same node as
-// often as the neighbour sets allow. One thread per group; a group whose part
-// holds more than ALIGN_MAX entries keeps the id order. perm as launch_row_perm.
-constexpr int ALIGN_MAX = 640;
-constexpr int ALIGN_ROWS = 32;
-
-__global__ void k_slot_align(const int32_t* __restrict__ src, int stride, int64_t N, int G, int m, int L,
-                             uint8_t* __restrict__ perm) {
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t r0 = g * G;
-    if (r0 >= N) return;
-    const int rows = (int)(N - r0 < G ? N - r0 : G);
-    int32_t uni[ALIGN_MAX];
-    int cnt[ALIGN_MAX];
-    uint64_t used[ALIGN_ROWS];
-    const int lo[2] = {0, m}, hi[2] = {m, L};
-    for (int part = 0; part < 2; ++part) {
-        const int a = lo[part], b = hi[part], w = b - a;
-        if (w <= 0) continue;
-        const bool fits = rows * w <= ALIGN_MAX && w <= 64 && rows <= ALIGN_ROWS;
-        if (!fits) {  // id order within the part
-            for (int r = 0; r < rows; ++r) {
-                const int32_t* s = src + (r0 + r) * stride;
-                uint8_t* pr = perm + (r0 + r) * L;
-                for (int j = a; j < b; ++j) pr[j] = (uint8_t)j;
-                for (int j = a + 1; j < b; ++j) {
-                    const uint8_t pj = pr[j];
-                    int k = j - 1;
-                    while (k >= a && s[pr[k]] > s[pj]) {
-                        pr[k + 1] = pr[k];
-                        --k;
-                    }
-                    pr[k + 1] = pj;
-                }
-            }
-            continue;
-        }
-        // the union of the part's ids, sorted, with the count of rows holding each
-        int nu = 0;
-        for (int r = 0; r < rows; ++r) {
-            const int32_t* s = src + (r0 + r) * stride;
-            for (int j = a; j < b; ++j) {
-                const int32_t v = s[j];
-                int k = nu - 1;
-                while (k >= 0 && uni[k] > v) --k;
-                if (k >= 0 && uni[k] == v) {
-                    ++cnt[k];
-                    continue;
-                }
-                for (int q = nu; q > k + 1; --q) {
-                    uni[q] = uni[q - 1];
-                    cnt[q] = cnt[q - 1];
-                }
-                uni[k + 1] = v;
-                cnt[k + 1] = 1;
-                ++nu;
-            }
-            used[r] = 0;
-        }
-        for (int slot = a; slot < b; ++slot) {
-            int best = -1;
-            for (int u = 0; u < nu; ++u)
-                if (cnt[u] > 0 && (best < 0 || cnt[u] > cnt[best])) best = u;
-            for (int r = 0; r < rows; ++r) {
-                const int32_t* s = src + (r0 + r) * stride;
-                int pick = -1, smallest = -1;
-                for (int j = a; j < b; ++j) {
-                    if (used[r] >> (j - a) & 1ull) continue;
-                    if (s[j] == uni[best]) pick = j;
-                    if (smallest < 0 || s[j] < s[smallest]) smallest = j;
-                }
-                if (pick < 0) pick = smallest;
-                used[r] |= 1ull << (pick - a);
-                perm[(r0 + r) * L + slot] = (uint8_t)pick;
-                int lo_u = 0, hi_u = nu - 1;  // the union entry of the placed id
-                while (lo_u < hi_u) {
-                    const int mid = (lo_u + hi_u) >> 1;
-                    if (uni[mid] < s[pick]) lo_u = mid + 1;
-                    else hi_u = mid;
-                }
-                --cnt[lo_u];
-            }
-        }
-    }
-}
-
-cudaError_t launch_slot_align(const int32_t* idx, int stride, int64_t n, int group, int m, int len, uint8_t* perm,
-                              cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    if (group > ALIGN_ROWS) return cudaErrorInvalidValue;
-    const int64_t groups = (n + group - 1) / group;
-    k_slot_align<<<(unsigned)((groups + 63) / 64), 64, 0, s>>>(idx, stride, n, group, m, len, perm);
-    return cudaGetLastError();
-}
-
 struct Box {
     double lo[3], scale[3];
 };
