@@ -345,6 +345,7 @@ def test_fp32_within_1e5_at_every_100th_step(ctx, layout):
         nodes = W.pec_box((33, 33), 0.25, 31)
         er = W.eps_r_uniform(nodes.n, 32)
         sim = _gpu_colloc(ctx, nodes, 12, 3, 2, 2, dt, eps0, mu0, -c, 0, True)
+        assert sim.index_stats() == {"h": (0, 0, 0), "e": (0, 0, 0)}  # collocated 2D: 32-bit indices
         sim.set_materials(er, nodes.pec)
         ez, hx, hy = W.tm11_fields(nodes.xyz, 32.0, c0, mu0, 0.0, -0.5 * dt)
         ez[nodes.pec == 1] = 0
@@ -402,6 +403,9 @@ def test_staggered_q16_indices_with_two_windows_and_wide_slices(ctx, prec, comp,
     ec = M.Weights(M.Stencils(de, dh, n), n, 5, 4, M.MFD_OP_GRAD)
     ev = M.Weights(M.Stencils(de, de, nhv), nhv, 7, 6, M.MFD_OP_LAP_POW, alpha)
     sim = M.Sim(ctx, 2, prec, dt, eps0, mu0, c, hc, hv, ec, ev, compensated=comp)
+    with pytest.raises(M.MfdError) as ei:
+        sim.set_index_format(7)
+    assert ei.value.status == M.MFD_ERR_ARG
     stats = sim.index_stats()
     for p in ("h", "e"):
         assert stats[p][0] == nx * nx // 32
