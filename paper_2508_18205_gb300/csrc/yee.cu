@@ -130,56 +130,47 @@ __global__ void __launch_bounds__(YT_X * YB_Y, 4) k_yee2(int nx, int ny, T ch, T
     __shared__ T se[Y2_E][Y2_E];   // [r][c]: Ez at (x0 - 2 + c, y0 - 2 + r); E^n, then E^{n+1} in place
     __shared__ T sx[Y2_H][Y2_H];   // Hx at (x0 - 2 + c, y0 - 2 + r + 1/2): old, then n+1/2, then n+3/2
     __shared__ T sy[Y2_H][Y2_H];   // Hy at (x0 - 2 + c + 1/2, y0 - 2 + r)
-    // Thread (tx, ty) owns staged columns tx and tx + 32 (the second only for the
-    // ring columns 32 .. 35, lanes 0 .. 3) and rows ty, ty + 8, ...: no divisions,
-    // conflict-free rows of shared memory, and one wrapped column index per thread.
     const int x0 = blockIdx.x * Y2_T, y0 = blockIdx.y * Y2_T;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int gx0 = wrap<BIG>(x0 - 2 + tx, nx), gx1 = wrap<BIG>(x0 - 2 + tx + Y2_T, nx);
-    for (int r = ty; r < Y2_E; r += YB_Y) {
-        const int64_t row = (int64_t)wrap<BIG>(y0 - 2 + r, ny) * nx;
-        se[r][tx] = ez[row + gx0];
-        if (r < Y2_H) {
-            sx[r][tx] = hx[row + gx0];
-            sy[r][tx] = hy[row + gx0];
-        }
-        if (tx < Y2_E - Y2_T) {
-            se[r][tx + Y2_T] = ez[row + gx1];
-            if (r < Y2_H && tx + Y2_T < Y2_H) {
-                sx[r][tx + Y2_T] = hx[row + gx1];
-                sy[r][tx + Y2_T] = hy[row + gx1];
-            }
+    const int t = threadIdx.y * YT_X + threadIdx.x;
+    constexpr int NT = YT_X * YB_Y;
+    for (int k = t; k < Y2_E * Y2_E; k += NT) {
+        const int r = k / Y2_E, c = k % Y2_E;
+        const int gx = wrap<BIG>(x0 - 2 + c, nx), gy = wrap<BIG>(y0 - 2 + r, ny);
+        const int64_t g = (int64_t)gy * nx + gx;
+        se[r][c] = ez[g];
+        if (r < Y2_H && c < Y2_H) {
+            sx[r][c] = hx[g];
+            sy[r][c] = hy[g];
         }
     }
     __syncthreads();
-    // H^{n+1/2} on the whole staged H region, rows / columns 0 .. 34 (it reads Ez one
-    // cell up and right)
-    for (int r = ty; r < Y2_H; r += YB_Y)
-        for (int c = tx; c < Y2_H; c += Y2_T) {
-            const T e = se[r][c];
-            sx[r][c] = rn_sub(sx[r][c], rn_mul(ch, rn_sub(se[r + 1][c], e)));
-            sy[r][c] = rn_add(sy[r][c], rn_mul(ch, rn_sub(se[r][c + 1], e)));
-        }
+    // H^{n+1/2} on the whole staged H region (it reads Ez one cell up and right)
+    for (int k = t; k < Y2_H * Y2_H; k += NT) {
+        const int r = k / Y2_H, c = k % Y2_H;
+        const T e = se[r][c];
+        sx[r][c] = rn_sub(sx[r][c], rn_mul(ch, rn_sub(se[r + 1][c], e)));
+        sy[r][c] = rn_add(sy[r][c], rn_mul(ch, rn_sub(se[r][c + 1], e)));
+    }
     __syncthreads();
     // E^{n+1} on x0-1 .. x0+32, y0-1 .. y0+32 (staged rows / columns 1 .. 34), in place
-    for (int r = 1 + ty; r <= Y2_T + 2; r += YB_Y)
-        for (int c = 1 + tx; c <= Y2_T + 2; c += Y2_T) {
-            const T curl = rn_add(rn_sub(rn_sub(sy[r][c], sy[r][c - 1]), sx[r][c]), sx[r - 1][c]);
-            se[r][c] = rn_add(se[r][c], rn_mul(ce, curl));
-        }
+    for (int k = t; k < (Y2_T + 2) * (Y2_T + 2); k += NT) {
+        const int r = 1 + k / (Y2_T + 2), c = 1 + k % (Y2_T + 2);
+        const T curl = rn_add(rn_sub(rn_sub(sy[r][c], sy[r][c - 1]), sx[r][c]), sx[r - 1][c]);
+        se[r][c] = rn_add(se[r][c], rn_mul(ce, curl));
+    }
     __syncthreads();
     // H^{n+3/2} on x0-1 .. x0+31, y0-1 .. y0+31 (staged 1 .. 33)
-    for (int r = 1 + ty; r <= Y2_T + 1; r += YB_Y)
-        for (int c = 1 + tx; c <= Y2_T + 1; c += Y2_T) {
-            const T e = se[r][c];
-            sx[r][c] = rn_sub(sx[r][c], rn_mul(ch, rn_sub(se[r + 1][c], e)));
-            sy[r][c] = rn_add(sy[r][c], rn_mul(ch, rn_sub(se[r][c + 1], e)));
-        }
+    for (int k = t; k < (Y2_T + 1) * (Y2_T + 1); k += NT) {
+        const int r = 1 + k / (Y2_T + 1), c = 1 + k % (Y2_T + 1);
+        const T e = se[r][c];
+        sx[r][c] = rn_sub(sx[r][c], rn_mul(ch, rn_sub(se[r + 1][c], e)));
+        sy[r][c] = rn_add(sy[r][c], rn_mul(ch, rn_sub(se[r][c + 1], e)));
+    }
     __syncthreads();
     // E^{n+2} on the tile (staged 2 .. 33) and the tile's H^{n+3/2}, written once
-    const int i = x0 + tx;
-    for (int r = 2 + ty; r < 2 + Y2_T; r += YB_Y) {
-        const int c = 2 + tx, j = y0 + r - 2;
+    for (int k = t; k < Y2_T * Y2_T; k += NT) {
+        const int r = 2 + k / Y2_T, c = 2 + k % Y2_T;
+        const int i = x0 + c - 2, j = y0 + r - 2;
         if (i < nx && j < ny) {
             const T curl = rn_add(rn_sub(rn_sub(sy[r][c], sy[r][c - 1]), sx[r][c]), sx[r - 1][c]);
             const int64_t g = (int64_t)j * nx + i;
