@@ -91,8 +91,7 @@ __global__ void k_q16_bases(const int32_t* __restrict__ src, int stride, int64_t
 // Q16 entries, laid out as the 32-bit chunks with 8 entries per chunk:
 // element e -> (slice s, chunk c, lane l, entry q)
 __global__ void k_pack_q16(const int32_t* __restrict__ src, int stride, int64_t N, int n_use, int chunks8,
-                           const int2* __restrict__ bases, const uint8_t* __restrict__ perm, int plen,
-                           uint16_t* __restrict__ dst, int64_t total) {
+                           const int2* __restrict__ bases, uint16_t* __restrict__ dst, int64_t total) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= total) return;
     const int q = (int)(e & 7);
@@ -105,7 +104,7 @@ __global__ void k_pack_q16(const int32_t* __restrict__ src, int stride, int64_t 
     const int2 b = bases[sl];
     unsigned v = 0;
     if (b.x >= 0 && node < N) {
-        const int64_t id = src[node * stride + src_entry(perm, plen, node, entry < n_use ? entry : 0)];
+        const int64_t id = src[node * stride + (entry < n_use ? entry : 0)];
         v = id - b.x <= 32767 ? (unsigned)(id - b.x) : (unsigned)(id - b.y);
     }
     dst[e] = (uint16_t)v;
@@ -295,8 +294,7 @@ mfd_status pack_weights(mfd_ctx* ctx, const mfd_weights* w, int out_index, int c
 int chunks_of(int n) { return (n + 3) / 4; }
 
 // Q16 form of one index stream (chunks4 chunks of 4 entries per row)
-mfd_status pack_q16(mfd_ctx* ctx, const mfd_stencils* st, int n_use, int chunks4, const DevBuf& perm, DevBuf& q,
-                    DevBuf& qb,
+mfd_status pack_q16(mfd_ctx* ctx, const mfd_stencils* st, int n_use, int chunks4, DevBuf& q, DevBuf& qb,
                     int64_t& wide) {
     const int64_t N = st->centres->n;
     const int64_t slices = (N + 31) / 32;
@@ -311,9 +309,9 @@ mfd_status pack_q16(mfd_ctx* ctx, const mfd_stencils* st, int n_use, int chunks4
                                                                           slices, qb.as<int2>(),
                                                                           cnt.as<unsigned long long>());
     MFD_CUDA(cudaGetLastError());
-    k_pack_q16<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(
-        st->idx.as<int32_t>(), st->n, N, n_use, chunks8, qb.as<int2>(), perm.p ? perm.as<uint8_t>() : nullptr, n_use,
-        q.as<uint16_t>(), total);
+    k_pack_q16<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(st->idx.as<int32_t>(), st->n, N, n_use,
+                                                                        chunks8, qb.as<int2>(), q.as<uint16_t>(),
+                                                                        total);
     MFD_CUDA(cudaGetLastError());
     unsigned long long w = 0;
     MFD_CUDA(cudaMemcpyAsync(&w, cnt.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -340,35 +338,19 @@ mfd_status pack_pass(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* h
                                      std::min(curl->n_use, hv->n_use), plen, perm.as<uint8_t>(), ctx->stream));
         }
         MFD_TRY(pack_stream(ctx, curl->st, plen, p.ni, p.idx_c, &perm, plen));
-        MFD_TRY(pack_weights(ctx, curl, 0, p.nc, fp64, p.wx, &perm, plen));
-        MFD_TRY(pack_weights(ctx, curl, 1, p.nc, fp64, p.wy, &perm, plen));
-        if (dim == 3) MFD_TRY(pack_weights(ctx, curl, 2, p.nc, fp64, p.wz, &perm, plen));
-        MFD_TRY(pack_weights(ctx, hv, 0, p.nv, fp64, p.wv, &perm, plen));
     } else {
-        // separate curl and HV streams: each row in ascending neighbour id (launch_row_perm)
         p.ni = p.nc;
-        const int64_t N = curl->st->centres->n;
-        DevBuf perm_c, perm_v;
-        if (curl->n_use <= 255 && hv->n_use <= 255) {
-            MFD_TRY(perm_c.alloc(N * curl->n_use));
-            MFD_TRY(perm_v.alloc(N * hv->n_use));
-            MFD_CUDA(launch_row_perm(curl->st->idx.as<int32_t>(), curl->st->n, N, curl->n_use, curl->n_use,
-                                     perm_c.as<uint8_t>(), ctx->stream));
-            MFD_CUDA(launch_row_perm(hv->st->idx.as<int32_t>(), hv->st->n, N, hv->n_use, hv->n_use,
-                                     perm_v.as<uint8_t>(), ctx->stream));
-        }
-        MFD_TRY(pack_stream(ctx, curl->st, curl->n_use, p.nc, p.idx_c, &perm_c, curl->n_use));
-        MFD_TRY(pack_stream(ctx, hv->st, hv->n_use, p.nv, p.idx_v, &perm_v, hv->n_use));
+        MFD_TRY(pack_stream(ctx, curl->st, curl->n_use, p.nc, p.idx_c));
+        MFD_TRY(pack_stream(ctx, hv->st, hv->n_use, p.nv, p.idx_v));
         if (dim == 2 && curl->st->centres != curl->st->sources) {  // staggered
-            MFD_TRY(pack_q16(ctx, curl->st, curl->n_use, p.nc, perm_c, p.q_c, p.qb_c, p.wide_c));
-            MFD_TRY(pack_q16(ctx, hv->st, hv->n_use, p.nv, perm_v, p.q_v, p.qb_v, p.wide_v));
+            MFD_TRY(pack_q16(ctx, curl->st, curl->n_use, p.nc, p.q_c, p.qb_c, p.wide_c));
+            MFD_TRY(pack_q16(ctx, hv->st, hv->n_use, p.nv, p.q_v, p.qb_v, p.wide_v));
         }
-        MFD_TRY(pack_weights(ctx, curl, 0, p.nc, fp64, p.wx, &perm_c, curl->n_use));
-        MFD_TRY(pack_weights(ctx, curl, 1, p.nc, fp64, p.wy, &perm_c, curl->n_use));
-        if (dim == 3) MFD_TRY(pack_weights(ctx, curl, 2, p.nc, fp64, p.wz, &perm_c, curl->n_use));
-        MFD_TRY(pack_weights(ctx, hv, 0, p.nv, fp64, p.wv, &perm_v, hv->n_use));
-        MFD_CUDA(cudaStreamSynchronize(ctx->stream));  // the permutations are freed on return
     }
+    MFD_TRY(pack_weights(ctx, curl, 0, p.nc, fp64, p.wx, &perm, plen));
+    MFD_TRY(pack_weights(ctx, curl, 1, p.nc, fp64, p.wy, &perm, plen));
+    if (dim == 3) MFD_TRY(pack_weights(ctx, curl, 2, p.nc, fp64, p.wz, &perm, plen));
+    MFD_TRY(pack_weights(ctx, hv, 0, p.nv, fp64, p.wv, &perm, plen));
     MFD_CUDA(cudaStreamSynchronize(ctx->stream));  // perm is freed on return
     return MFD_OK;
 }
