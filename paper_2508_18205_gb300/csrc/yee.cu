@@ -111,72 +111,87 @@ __global__ void __launch_bounds__(YT_X * YB_Y, 8) k_yee(int nx, int ny, T ch, T 
 }
 
 // Two steps per launch (temporal blocking), for runs without sources or probes
-// (their terms sit between the steps): a block stages Ez^n with a 2-cell ring
-// and the old H with the ring H^{n+1/2} needs, then computes in shared memory
-// H^{n+1/2} (tile + 2-cell ring on the low sides, + 1 on the high sides), E^{n+1}
-// (tile + 1-cell ring), H^{n+3/2} (tile + low 1-cell ring) and E^{n+2} (tile), and
-// writes the tile once: 6 reals of DRAM traffic per cell for two steps. Every
-// value is computed with the one-step kernel's arithmetic, so results match it
-// (and the reference in FP64) bit for bit.
-constexpr int Y2_T = 32;           // tile side
-constexpr int Y2_E = Y2_T + 4;     // staged Ez: x0-2 .. x0+33
-constexpr int Y2_H = Y2_T + 3;     // staged H:  x0-2 .. x0+32
+// (their terms sit between the steps). A block stages a 32-column by 36-row
+// window of the grid in registers: lane c of warp w holds column x0 - 2 + c of
+// rows y0 - 2 + 4w .. y0 + 1 + 4w (nine warps, 36 rows), Ez and the old Hx, Hy
+// of each. It computes H^{n+1/2}, E^{n+1}, H^{n+3/2} and E^{n+2}: neighbours
+// along x come from the adjacent lane by a shuffle, neighbours along y from the
+// thread's own registers or, across warps, through one shared row per warp and
+// half step. The valid region shrinks by a cell per half step, leaving the
+// 28 x 32 tile (columns 2 .. 29, rows 2 .. 33 of the window), written once: 6
+// reals of DRAM traffic per cell for two steps. Every value is computed with the
+// one-step kernel's arithmetic, so results match it (and the reference in FP64)
+// bit for bit.
+constexpr int Y2_TX = 28;  // tile columns (the window is 32 = Y2_TX + 4)
+constexpr int Y2_TY = 32;  // tile rows (the window is 36)
+constexpr int Y2_W = 9;    // warps; four window rows each
 
 template <typename T, bool BIG>
-__global__ void __launch_bounds__(YT_X * YB_Y, 4) k_yee2(int nx, int ny, T ch, T ce, const T* __restrict__ ez,
-                                                         const T* __restrict__ hx, const T* __restrict__ hy,
-                                                         T* __restrict__ ez_o, T* __restrict__ hx_o,
-                                                         T* __restrict__ hy_o) {
-    __shared__ T se[Y2_E][Y2_E];   // [r][c]: Ez at (x0 - 2 + c, y0 - 2 + r); E^n, then E^{n+1} in place
-    __shared__ T sx[Y2_H][Y2_H];   // Hx at (x0 - 2 + c, y0 - 2 + r + 1/2): old, then n+1/2, then n+3/2
-    __shared__ T sy[Y2_H][Y2_H];   // Hy at (x0 - 2 + c + 1/2, y0 - 2 + r)
-    const int x0 = blockIdx.x * Y2_T, y0 = blockIdx.y * Y2_T;
-    const int t = threadIdx.y * YT_X + threadIdx.x;
-    constexpr int NT = YT_X * YB_Y;
-    for (int k = t; k < Y2_E * Y2_E; k += NT) {
-        const int r = k / Y2_E, c = k % Y2_E;
-        const int gx = wrap<BIG>(x0 - 2 + c, nx), gy = wrap<BIG>(y0 - 2 + r, ny);
-        const int64_t g = (int64_t)gy * nx + gx;
-        se[r][c] = ez[g];
-        if (r < Y2_H && c < Y2_H) {
-            sx[r][c] = hx[g];
-            sy[r][c] = hy[g];
+__global__ void __launch_bounds__(32 * Y2_W) k_yee2(int nx, int ny, T ch, T ce, const T* __restrict__ ez,
+                                                    const T* __restrict__ hx, const T* __restrict__ hy,
+                                                    T* __restrict__ ez_o, T* __restrict__ hx_o,
+                                                    T* __restrict__ hy_o) {
+    __shared__ T xe[Y2_W][32];  // per warp: E^{n+1} of its first row
+    __shared__ T xh[Y2_W][32];  // per warp: Hx of its last row (H^{n+1/2}, then H^{n+3/2})
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int x0 = blockIdx.x * Y2_TX, y0 = blockIdx.y * Y2_TY;
+    const int gx = wrap<BIG>(x0 - 2 + lane, nx);
+    const int r0 = 4 * w;  // window rows r0 .. r0 + 3
+    T e[5], sx[4], sy[4];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int64_t g = (int64_t)wrap<BIG>(y0 - 2 + r0 + k, ny) * nx + gx;
+        e[k] = ez[g];
+        if (k < 4) {
+            sx[k] = hx[g];
+            sy[k] = hy[g];
         }
     }
-    __syncthreads();
-    // H^{n+1/2} on the whole staged H region (it reads Ez one cell up and right)
-    for (int k = t; k < Y2_H * Y2_H; k += NT) {
-        const int r = k / Y2_H, c = k % Y2_H;
-        const T e = se[r][c];
-        sx[r][c] = rn_sub(sx[r][c], rn_mul(ch, rn_sub(se[r + 1][c], e)));
-        sy[r][c] = rn_add(sy[r][c], rn_mul(ch, rn_sub(se[r][c + 1], e)));
+    // H^{n+1/2}: valid on window columns 0 .. 30, rows 0 .. 34
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T right = __shfl_down_sync(FULL, e[k], 1);
+        sx[k] = rn_sub(sx[k], rn_mul(ch, rn_sub(e[k + 1], e[k])));
+        sy[k] = rn_add(sy[k], rn_mul(ch, rn_sub(right, e[k])));
     }
+    xh[w][lane] = sx[3];
     __syncthreads();
-    // E^{n+1} on x0-1 .. x0+32, y0-1 .. y0+32 (staged rows / columns 1 .. 34), in place
-    for (int k = t; k < (Y2_T + 2) * (Y2_T + 2); k += NT) {
-        const int r = 1 + k / (Y2_T + 2), c = 1 + k % (Y2_T + 2);
-        const T curl = rn_add(rn_sub(rn_sub(sy[r][c], sy[r][c - 1]), sx[r][c]), sx[r - 1][c]);
-        se[r][c] = rn_add(se[r][c], rn_mul(ce, curl));
+    T below = w > 0 ? xh[w - 1][lane] : sx[0];  // Hx of row r0 - 1 (row 0 is outside the valid region)
+    // E^{n+1}: valid on columns 1 .. 30, rows 1 .. 34
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T left = __shfl_up_sync(FULL, sy[k], 1);
+        const T down = k > 0 ? sx[k - 1] : below;
+        const T curl = rn_add(rn_sub(rn_sub(sy[k], left), sx[k]), down);
+        e[k] = rn_add(e[k], rn_mul(ce, curl));
     }
-    __syncthreads();
-    // H^{n+3/2} on x0-1 .. x0+31, y0-1 .. y0+31 (staged 1 .. 33)
-    for (int k = t; k < (Y2_T + 1) * (Y2_T + 1); k += NT) {
-        const int r = 1 + k / (Y2_T + 1), c = 1 + k % (Y2_T + 1);
-        const T e = se[r][c];
-        sx[r][c] = rn_sub(sx[r][c], rn_mul(ch, rn_sub(se[r + 1][c], e)));
-        sy[r][c] = rn_add(sy[r][c], rn_mul(ch, rn_sub(se[r][c + 1], e)));
+    xe[w][lane] = e[0];
+    __syncthreads();  // also: every warp has read xh above
+    e[4] = w + 1 < Y2_W ? xe[w + 1][lane] : e[3];  // E^{n+1} of row r0 + 4 (row 36: outside)
+    // H^{n+3/2}: valid on columns 1 .. 29, rows 1 .. 33
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T right = __shfl_down_sync(FULL, e[k], 1);
+        sx[k] = rn_sub(sx[k], rn_mul(ch, rn_sub(e[k + 1], e[k])));
+        sy[k] = rn_add(sy[k], rn_mul(ch, rn_sub(right, e[k])));
     }
+    xh[w][lane] = sx[3];
     __syncthreads();
-    // E^{n+2} on the tile (staged 2 .. 33) and the tile's H^{n+3/2}, written once
-    for (int k = t; k < Y2_T * Y2_T; k += NT) {
-        const int r = 2 + k / Y2_T, c = 2 + k % Y2_T;
-        const int i = x0 + c - 2, j = y0 + r - 2;
-        if (i < nx && j < ny) {
-            const T curl = rn_add(rn_sub(rn_sub(sy[r][c], sy[r][c - 1]), sx[r][c]), sx[r - 1][c]);
+    below = w > 0 ? xh[w - 1][lane] : sx[0];
+    // E^{n+2} on the tile (columns 2 .. 29, rows 2 .. 33) with the tile's H^{n+3/2}
+    const int i = x0 - 2 + lane;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T left = __shfl_up_sync(FULL, sy[k], 1);
+        const T down = k > 0 ? sx[k - 1] : below;
+        const T curl = rn_add(rn_sub(rn_sub(sy[k], left), sx[k]), down);
+        const int row = r0 + k, j = y0 - 2 + row;
+        if (lane >= 2 && lane < 2 + Y2_TX && row >= 2 && row < 2 + Y2_TY && i < nx && j < ny) {
             const int64_t g = (int64_t)j * nx + i;
-            ez_o[g] = rn_add(se[r][c], rn_mul(ce, curl));
-            hx_o[g] = sx[r][c];
-            hy_o[g] = sy[r][c];
+            ez_o[g] = rn_add(e[k], rn_mul(ce, curl));
+            hx_o[g] = sx[k];
+            hy_o[g] = sy[k];
         }
     }
 }
@@ -251,10 +266,12 @@ constexpr int YEE_GRAPH_STEPS = 32;
 // two steps in one launch; only without sources and probes
 cudaError_t yee_enqueue2(mfd_yee* y) {
     cudaStream_t s = y->ctx->stream;
-    const dim3 grid((unsigned)((y->nx + Y2_T - 1) / Y2_T), (unsigned)((y->ny + Y2_T - 1) / Y2_T));
-    const dim3 block(YT_X, YB_Y);
+    const dim3 grid((unsigned)((y->nx + Y2_TX - 1) / Y2_TX), (unsigned)((y->ny + Y2_TY - 1) / Y2_TY));
+    const dim3 block(32, Y2_W);
     const int a = y->cur, b = y->cur ^ 1;
-    const bool big = y->nx >= Y2_T + 2 && y->ny >= Y2_T + 2;  // the staged ring reaches x0 + 33
+    // one compare per wrap while the window's columns x0-2 .. x0+29 and rows y0-2 .. y0+33 stay
+    // within one period of the grid on either side
+    const bool big = y->nx >= Y2_TX + 2 && y->ny >= Y2_TY + 2;
     const int nx = (int)y->nx, ny = (int)y->ny;
     if (y->fp64) {
         const double *e = y->f[a][0].as<double>(), *hx = y->f[a][1].as<double>(), *hy = y->f[a][2].as<double>();
