@@ -380,7 +380,7 @@ mfd_status mfd_yee_step(mfd_yee* y, int64_t nsteps);
 /* nsteps steps, each launch bracketed by CUDA events; *ms = the summed launch times. */
 mfd_status mfd_yee_step_timed(mfd_yee* y, int64_t nsteps, double* ms);
 /* Steps one kernel launch advances: 2 without sources and probes (two steps
- * fused in shared memory, halving the DRAM traffic per step; results equal the
+ * fused in one launch, halving the DRAM traffic per step; results equal the
  * one-step kernel's bit for bit), else 1. */
 int mfd_yee_steps_per_launch(const mfd_yee* y);
 /* host: steps x count FP64; *steps receives the recorded steps. */

@@ -1,15 +1,13 @@
 // yee.cu -- the FDTD (Yee) scheme for TMz (Eq. 4, Eq. 5) on a periodic grid:
 // the reference the paper compares its meshless method with (Sec. 3, Sec. 6).
 //
-// One fused kernel per step (two fused steps per launch when there are no
-// sources and probes, below): a block of 32 x 8 threads owns a 32 x 32 tile
-// (four cells of a column per thread), stages Ez of the tile plus the one-cell
-// ring the stencil reads in shared memory, computes H' of the tile and of the
-// one-cell ring on its low sides (recomputed, not exchanged: the neighbour
-// computes the same values bit for bit), writes H', then E' of the tile from
-// the staged H'. State ping-pongs between two buffers so that no block reads
-// what another block of the same step writes. Compulsory traffic per cell
-// and step: Ez, Hx, Hy read once and written once (6 reals).
+// One fused kernel per launch (k_yee, below) advances one step, or two when
+// there are no sources and probes: a block holds a window of the grid in
+// registers and writes the cells whose dependency cone lies inside it. State
+// ping-pongs between two buffers so that no block reads what another block of
+// the same launch writes. Soft sources and probes follow each one-step launch
+// in k_yee_post. Compulsory traffic per cell and launch: Ez, Hx, Hy read once
+// and written once (6 reals).
 //
 // Arithmetic follows Eq. 5 term by term with round-to-nearest operations (no
 // contraction), in the oracle's order, so FP64 results are reproducible
@@ -21,12 +19,6 @@
 #include "internal.cuh"
 
 namespace mfd {
-
-constexpr int YT_X = 32;  // tile width; the tile height is YB_Y * RY
-constexpr int YB_Y = 8;   // thread rows: each thread owns RY cells of a column
-// cells per thread: 32 x 32 tiles (measured on 8192^2 FP32: 0.43 ms per step;
-// 32 x 64 tiles with eight cells per thread and fewer resident blocks: 0.58 ms)
-template <typename T> constexpr int yee_ry() { return 4; }
 
 __device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
@@ -42,106 +34,42 @@ template <bool BIG> __device__ __forceinline__ int wrap(int v, int n) {
     return ((v % n) + n) % n;
 }
 
-template <typename T, bool BIG, int RY = yee_ry<T>()>
-__global__ void __launch_bounds__(YT_X * YB_Y, 8) k_yee(int nx, int ny, T ch, T ce, const T* __restrict__ ez,
-                                                        const T* __restrict__ hx, const T* __restrict__ hy,
-                                                        T* __restrict__ ez_o, T* __restrict__ hx_o,
-                                                        T* __restrict__ hy_o) {
-    // staged Ez at x0-1 .. x0+32, y0-1 .. y0+YT_Y (corners unused), new H with the
-    // low-side ring: Hy' at x0-1 .. x0+31, Hx' at y0-1 .. y0+YT_Y-1
-    constexpr int YT_Y = YB_Y * RY, YR = RY;
-    __shared__ T se[YT_Y + 2][YT_X + 2];
-    __shared__ T shy[YT_Y][YT_X + 1];
-    __shared__ T shx[YT_Y + 1][YT_X];
-    const int x0 = blockIdx.x * YT_X, y0 = blockIdx.y * YT_Y;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i = x0 + tx, gi = wrap<BIG>(i, nx);
-    const int xl = wrap<BIG>(x0 - 1, nx);
-    // every global load of the step is issued before the first barrier: Ez of
-    // the tile and its ring, and the old H of the own cells and of the ring
-    T ohx[YR], ohy[YR], ohl[YR];
-#pragma unroll
-    for (int k = 0; k < YR; ++k) {
-        const int r = ty + k * YB_Y;
-        const int64_t row = (int64_t)wrap<BIG>(y0 + r, ny) * nx;
-        se[r + 1][tx + 1] = ez[row + gi];
-        ohx[k] = hx[row + gi];
-        ohy[k] = hy[row + gi];
-        if (tx == 0) {
-            se[r + 1][0] = ez[row + xl];
-            ohl[k] = hy[row + xl];
-        }
-        if (tx == YT_X - 1) se[r + 1][YT_X + 1] = ez[row + wrap<BIG>(x0 + YT_X, nx)];
-    }
-    T ohb = T(0);
-    if (ty == 0) {
-        const int64_t row = (int64_t)wrap<BIG>(y0 - 1, ny) * nx;
-        se[0][tx + 1] = ez[row + gi];
-        ohb = hx[row + gi];
-    }
-    if (ty == YB_Y - 1) se[YT_Y + 1][tx + 1] = ez[(int64_t)wrap<BIG>(y0 + YT_Y, ny) * nx + gi];
-    __syncthreads();
-    // H' of the own cells (Hx at (i, j + 1/2), Hy at (i + 1/2, j)) and of the low-side ring
-#pragma unroll
-    for (int k = 0; k < YR; ++k) {
-        const int r = ty + k * YB_Y, j = y0 + r;
-        const T e = se[r + 1][tx + 1];
-        const T hxn = rn_sub(ohx[k], rn_mul(ch, rn_sub(se[r + 2][tx + 1], e)));
-        const T hyn = rn_add(ohy[k], rn_mul(ch, rn_sub(se[r + 1][tx + 2], e)));
-        shx[r + 1][tx] = hxn;
-        shy[r][tx + 1] = hyn;
-        if (i < nx && j < ny) {
-            const int64_t g = (int64_t)j * nx + i;
-            hx_o[g] = hxn;
-            hy_o[g] = hyn;
-        }
-        if (tx == 0) shy[r][0] = rn_add(ohl[k], rn_mul(ch, rn_sub(se[r + 1][1], se[r + 1][0])));
-    }
-    if (ty == 0) shx[0][tx] = rn_sub(ohb, rn_mul(ch, rn_sub(se[1][tx + 1], se[0][tx + 1])));
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < YR; ++k) {
-        const int r = ty + k * YB_Y, j = y0 + r;
-        if (i < nx && j < ny) {
-            // (Hy(i) - Hy(i-1)) - Hx(j) + Hx(j-1), left to right
-            const T curl = rn_add(rn_sub(rn_sub(shy[r][tx + 1], shy[r][tx]), shx[r + 1][tx]), shx[r][tx]);
-            ez_o[(int64_t)j * nx + i] = rn_add(se[r + 1][tx + 1], rn_mul(ce, curl));
-        }
-    }
-}
-
-// Two steps per launch (temporal blocking), for runs without sources or probes
-// (their terms sit between the steps). A block stages a 32-column by 36-row
-// window of the grid in registers: lane c of warp w holds column x0 - 2 + c of
-// rows y0 - 2 + 4w .. y0 + 1 + 4w (nine warps, 36 rows), Ez and the old Hx, Hy
-// of each. It computes H^{n+1/2}, E^{n+1}, H^{n+3/2} and E^{n+2}: neighbours
+// The step kernel, one or two steps per launch (two, temporal blocking, for runs
+// without sources or probes, whose terms sit between the steps). A block holds
+// a 32-column by 36-row window of the grid in registers: lane c of warp w holds
+// column x0 - S + c of rows y0 - S + 4w .. y0 - S + 3 + 4w (nine warps, 36 rows;
+// S = the steps per launch), Ez and the old Hx, Hy of each. It computes
+// H^{n+1/2} and E^{n+1} (and, for two steps, H^{n+3/2} and E^{n+2}): neighbours
 // along x come from the adjacent lane by a shuffle, neighbours along y from the
 // thread's own registers or, across warps, through one shared row per warp and
-// half step. The valid region shrinks by a cell per half step, leaving the
-// 28 x 32 tile (columns 2 .. 29, rows 2 .. 33 of the window), written once: 6
-// reals of DRAM traffic per cell for two steps. Every value is computed with the
-// one-step kernel's arithmetic, so results match it (and the reference in FP64)
-// bit for bit.
-constexpr int Y2_TX = 28;  // tile columns (the window is 32 = Y2_TX + 4)
-constexpr int Y2_TY = 32;  // tile rows (the window is 36)
-constexpr int Y2_W = 9;    // warps; four window rows each
+// half step. The valid region shrinks by a cell per half step on the sides the
+// stencil reads, leaving a (32 - 2S) x (36 - 2S) tile (window columns and rows
+// S .. end - S), written once: 6 reals of DRAM traffic per cell and launch.
+// Arithmetic follows Eq. 5 term by term with round-to-nearest operations (no
+// contraction), in the oracle's order, so FP64 results are reproducible bit for
+// bit and do not depend on the steps per launch.
+constexpr int YW_W = 9;  // warps; four window rows each
+template <int S> constexpr int yee_tile_x() { return 32 - 2 * S; }
+template <int S> constexpr int yee_tile_y() { return 36 - 2 * S; }
 
-template <typename T, bool BIG>
-__global__ void __launch_bounds__(32 * Y2_W) k_yee2(int nx, int ny, T ch, T ce, const T* __restrict__ ez,
-                                                    const T* __restrict__ hx, const T* __restrict__ hy,
-                                                    T* __restrict__ ez_o, T* __restrict__ hx_o,
-                                                    T* __restrict__ hy_o) {
-    __shared__ T xe[Y2_W][32];  // per warp: E^{n+1} of its first row
-    __shared__ T xh[Y2_W][32];  // per warp: Hx of its last row (H^{n+1/2}, then H^{n+3/2})
+template <typename T, bool BIG, int S>
+__global__ void __launch_bounds__(32 * YW_W) k_yee(int nx, int ny, T ch, T ce, const T* __restrict__ ez,
+                                                   const T* __restrict__ hx, const T* __restrict__ hy,
+                                                   T* __restrict__ ez_o, T* __restrict__ hx_o,
+                                                   T* __restrict__ hy_o) {
+    static_assert(S == 1 || S == 2, "one or two steps per launch");
+    constexpr int TX = yee_tile_x<S>(), TY = yee_tile_y<S>();
+    __shared__ T xe[YW_W][32];  // per warp: E^{n+1} of its first row
+    __shared__ T xh[YW_W][32];  // per warp: Hx of its last row (H^{n+1/2}, then H^{n+3/2})
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x, w = threadIdx.y;
-    const int x0 = blockIdx.x * Y2_TX, y0 = blockIdx.y * Y2_TY;
-    const int gx = wrap<BIG>(x0 - 2 + lane, nx);
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int gx = wrap<BIG>(x0 - S + lane, nx);
     const int r0 = 4 * w;  // window rows r0 .. r0 + 3
     T e[5], sx[4], sy[4];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        const int64_t g = (int64_t)wrap<BIG>(y0 - 2 + r0 + k, ny) * nx + gx;
+        const int64_t g = (int64_t)wrap<BIG>(y0 - S + r0 + k, ny) * nx + gx;
         e[k] = ez[g];
         if (k < 4) {
             sx[k] = hx[g];
@@ -159,39 +87,52 @@ __global__ void __launch_bounds__(32 * Y2_W) k_yee2(int nx, int ny, T ch, T ce, 
     __syncthreads();
     T below = w > 0 ? xh[w - 1][lane] : sx[0];  // Hx of row r0 - 1 (row 0 is outside the valid region)
     // E^{n+1}: valid on columns 1 .. 30, rows 1 .. 34
+    const int i = x0 - S + lane;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const T left = __shfl_up_sync(FULL, sy[k], 1);
         const T down = k > 0 ? sx[k - 1] : below;
         const T curl = rn_add(rn_sub(rn_sub(sy[k], left), sx[k]), down);
-        e[k] = rn_add(e[k], rn_mul(ce, curl));
+        const T en = rn_add(e[k], rn_mul(ce, curl));
+        if constexpr (S == 1) {
+            const int row = r0 + k, j = y0 - 1 + row;
+            if (lane >= 1 && lane < 1 + TX && row >= 1 && row < 1 + TY && i < nx && j < ny) {
+                const int64_t g = (int64_t)j * nx + i;
+                ez_o[g] = en;
+                hx_o[g] = sx[k];
+                hy_o[g] = sy[k];
+            }
+        } else {
+            e[k] = en;
+        }
     }
-    xe[w][lane] = e[0];
-    __syncthreads();  // also: every warp has read xh above
-    e[4] = w + 1 < Y2_W ? xe[w + 1][lane] : e[3];  // E^{n+1} of row r0 + 4 (row 36: outside)
-    // H^{n+3/2}: valid on columns 1 .. 29, rows 1 .. 33
+    if constexpr (S == 2) {
+        xe[w][lane] = e[0];
+        __syncthreads();  // also: every warp has read xh above
+        e[4] = w + 1 < YW_W ? xe[w + 1][lane] : e[3];  // E^{n+1} of row r0 + 4 (row 36: outside)
+        // H^{n+3/2}: valid on columns 1 .. 29, rows 1 .. 33
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const T right = __shfl_down_sync(FULL, e[k], 1);
-        sx[k] = rn_sub(sx[k], rn_mul(ch, rn_sub(e[k + 1], e[k])));
-        sy[k] = rn_add(sy[k], rn_mul(ch, rn_sub(right, e[k])));
-    }
-    xh[w][lane] = sx[3];
-    __syncthreads();
-    below = w > 0 ? xh[w - 1][lane] : sx[0];
-    // E^{n+2} on the tile (columns 2 .. 29, rows 2 .. 33) with the tile's H^{n+3/2}
-    const int i = x0 - 2 + lane;
+        for (int k = 0; k < 4; ++k) {
+            const T right = __shfl_down_sync(FULL, e[k], 1);
+            sx[k] = rn_sub(sx[k], rn_mul(ch, rn_sub(e[k + 1], e[k])));
+            sy[k] = rn_add(sy[k], rn_mul(ch, rn_sub(right, e[k])));
+        }
+        xh[w][lane] = sx[3];
+        __syncthreads();
+        below = w > 0 ? xh[w - 1][lane] : sx[0];
+        // E^{n+2} on the tile (columns 2 .. 29, rows 2 .. 33) with the tile's H^{n+3/2}
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const T left = __shfl_up_sync(FULL, sy[k], 1);
-        const T down = k > 0 ? sx[k - 1] : below;
-        const T curl = rn_add(rn_sub(rn_sub(sy[k], left), sx[k]), down);
-        const int row = r0 + k, j = y0 - 2 + row;
-        if (lane >= 2 && lane < 2 + Y2_TX && row >= 2 && row < 2 + Y2_TY && i < nx && j < ny) {
-            const int64_t g = (int64_t)j * nx + i;
-            ez_o[g] = rn_add(e[k], rn_mul(ce, curl));
-            hx_o[g] = sx[k];
-            hy_o[g] = sy[k];
+        for (int k = 0; k < 4; ++k) {
+            const T left = __shfl_up_sync(FULL, sy[k], 1);
+            const T down = k > 0 ? sx[k - 1] : below;
+            const T curl = rn_add(rn_sub(rn_sub(sy[k], left), sx[k]), down);
+            const int row = r0 + k, j = y0 - 2 + row;
+            if (lane >= 2 && lane < 2 + TX && row >= 2 && row < 2 + TY && i < nx && j < ny) {
+                const int64_t g = (int64_t)j * nx + i;
+                ez_o[g] = rn_add(e[k], rn_mul(ce, curl));
+                hx_o[g] = sx[k];
+                hy_o[g] = sy[k];
+            }
         }
     }
 }
@@ -264,57 +205,47 @@ namespace {
 constexpr int YEE_GRAPH_STEPS = 32;
 
 // two steps in one launch; only without sources and probes
-cudaError_t yee_enqueue2(mfd_yee* y) {
+// one launch of k_yee with S steps (S = 2 only without sources and probes)
+template <int S> cudaError_t yee_launch(mfd_yee* y) {
     cudaStream_t s = y->ctx->stream;
-    const dim3 grid((unsigned)((y->nx + Y2_TX - 1) / Y2_TX), (unsigned)((y->ny + Y2_TY - 1) / Y2_TY));
-    const dim3 block(32, Y2_W);
+    const dim3 grid((unsigned)((y->nx + yee_tile_x<S>() - 1) / yee_tile_x<S>()),
+                    (unsigned)((y->ny + yee_tile_y<S>() - 1) / yee_tile_y<S>()));
+    const dim3 block(32, YW_W);
     const int a = y->cur, b = y->cur ^ 1;
-    // one compare per wrap while the window's columns x0-2 .. x0+29 and rows y0-2 .. y0+33 stay
-    // within one period of the grid on either side
-    const bool big = y->nx >= Y2_TX + 2 && y->ny >= Y2_TY + 2;
+    // one compare per wrap while the window (columns x0-S .. x0-S+31, rows y0-S .. y0-S+36)
+    // stays within one period of the grid on either side
+    const bool big = y->nx >= 32 && y->ny >= 37;
     const int nx = (int)y->nx, ny = (int)y->ny;
     if (y->fp64) {
         const double *e = y->f[a][0].as<double>(), *hx = y->f[a][1].as<double>(), *hy = y->f[a][2].as<double>();
         double *eo = y->f[b][0].as<double>(), *hxo = y->f[b][1].as<double>(), *hyo = y->f[b][2].as<double>();
-        if (big) k_yee2<double, true><<<grid, block, 0, s>>>(nx, ny, y->ch, y->ce, e, hx, hy, eo, hxo, hyo);
-        else k_yee2<double, false><<<grid, block, 0, s>>>(nx, ny, y->ch, y->ce, e, hx, hy, eo, hxo, hyo);
+        if (big) k_yee<double, true, S><<<grid, block, 0, s>>>(nx, ny, y->ch, y->ce, e, hx, hy, eo, hxo, hyo);
+        else k_yee<double, false, S><<<grid, block, 0, s>>>(nx, ny, y->ch, y->ce, e, hx, hy, eo, hxo, hyo);
     } else {
         const float *e = y->f[a][0].as<float>(), *hx = y->f[a][1].as<float>(), *hy = y->f[a][2].as<float>();
         float *eo = y->f[b][0].as<float>(), *hxo = y->f[b][1].as<float>(), *hyo = y->f[b][2].as<float>();
         const float ch = (float)y->ch, ce = (float)y->ce;
-        if (big) k_yee2<float, true><<<grid, block, 0, s>>>(nx, ny, ch, ce, e, hx, hy, eo, hxo, hyo);
-        else k_yee2<float, false><<<grid, block, 0, s>>>(nx, ny, ch, ce, e, hx, hy, eo, hxo, hyo);
+        if (big) k_yee<float, true, S><<<grid, block, 0, s>>>(nx, ny, ch, ce, e, hx, hy, eo, hxo, hyo);
+        else k_yee<float, false, S><<<grid, block, 0, s>>>(nx, ny, ch, ce, e, hx, hy, eo, hxo, hyo);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     y->cur = b;
-    y->steps += 2;
     return cudaSuccess;
+}
+
+// two steps in one launch; only without sources and probes
+cudaError_t yee_enqueue2(mfd_yee* y) {
+    cudaError_t e = yee_launch<2>(y);
+    if (e == cudaSuccess) y->steps += 2;
+    return e;
 }
 
 cudaError_t yee_enqueue(mfd_yee* y) {
     cudaStream_t s = y->ctx->stream;
-    const int tile_y = YB_Y * (y->fp64 ? yee_ry<double>() : yee_ry<float>());
-    const dim3 grid((unsigned)((y->nx + YT_X - 1) / YT_X), (unsigned)((y->ny + tile_y - 1) / tile_y));
-    const dim3 block(YT_X, YB_Y);
-    const int a = y->cur, b = y->cur ^ 1;
-    const bool big = y->nx >= YT_X && y->ny >= tile_y;
-    const int nx = (int)y->nx, ny = (int)y->ny;
-    if (y->fp64) {
-        const double *e = y->f[a][0].as<double>(), *hx = y->f[a][1].as<double>(), *hy = y->f[a][2].as<double>();
-        double *eo = y->f[b][0].as<double>(), *hxo = y->f[b][1].as<double>(), *hyo = y->f[b][2].as<double>();
-        if (big) k_yee<double, true><<<grid, block, 0, s>>>(nx, ny, y->ch, y->ce, e, hx, hy, eo, hxo, hyo);
-        else k_yee<double, false><<<grid, block, 0, s>>>(nx, ny, y->ch, y->ce, e, hx, hy, eo, hxo, hyo);
-    } else {
-        const float *e = y->f[a][0].as<float>(), *hx = y->f[a][1].as<float>(), *hy = y->f[a][2].as<float>();
-        float *eo = y->f[b][0].as<float>(), *hxo = y->f[b][1].as<float>(), *hyo = y->f[b][2].as<float>();
-        const float ch = (float)y->ch, ce = (float)y->ce;
-        if (big) k_yee<float, true><<<grid, block, 0, s>>>(nx, ny, ch, ce, e, hx, hy, eo, hxo, hyo);
-        else k_yee<float, false><<<grid, block, 0, s>>>(nx, ny, ch, ce, e, hx, hy, eo, hxo, hyo);
-    }
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = yee_launch<1>(y);
     if (e != cudaSuccess) return e;
-    y->cur = b;
+    const int b = y->cur;
     if (y->nsrc > 0 || y->nprobe > 0) {
         if (y->fp64)
             k_yee_post<double><<<1, 256, 0, s>>>(y->f[b][0].as<double>(), y->nsrc, y->src_node.as<int64_t>(),
@@ -386,7 +317,7 @@ mfd_status mfd_yee_create(mfd_ctx* ctx, int64_t nx, int64_t ny, int precision, d
                           double mu0, mfd_yee** out) {
     if (!ctx || !out) return fail(MFD_ERR_ARG, "mfd_yee_create: NULL argument");
     *out = nullptr;
-    if (nx < 2 || ny < 2 || nx > INT32_MAX / 2 || ny > 65535LL * YB_Y * 4)
+    if (nx < 2 || ny < 2 || nx > INT32_MAX / 2 || ny > 65535LL * yee_tile_y<2>())
         return fail(MFD_ERR_ARG, "mfd_yee_create: need 2 <= nx < 2^30 and 2 <= ny <= 2097120");
     if (!(dt > 0) || !(h > 0) || !(eps0 > 0) || !(mu0 > 0)) return fail(MFD_ERR_ARG, "dt, h, eps0, mu0 must be > 0");
     if (precision != MFD_FP32 && precision != MFD_FP64) return fail(MFD_ERR_ARG, "precision");
