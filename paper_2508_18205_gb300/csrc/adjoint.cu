@@ -218,6 +218,20 @@ mfd_status adj_build(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* h
     return MFD_OK;
 }
 
+// first entry of the ascending list v[0 .. m) that is >= key
+__device__ __forceinline__ int lower_bound_i64(const int64_t* v, int m, int64_t key) {
+    int lo = 0, hi = m;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (v[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ bool has_bit(const uint32_t* mask, int64_t j) {
+    return mask && ((mask[j >> 5] >> (j & 31)) & 1u);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_a(const int64_t* __restrict__ off, const int4* __restrict__ scol,
                                                const typename Vec<T>::V4* __restrict__ sx,
@@ -226,10 +240,29 @@ __global__ void __launch_bounds__(256) k_adj_a(const int64_t* __restrict__ off, 
                                                const typename Vec<T>::V4* __restrict__ LA,
                                                typename Vec<T>::V4* __restrict__ LB, T gamma,
                                                const T* __restrict__ ez, const int64_t* __restrict__ slot0, int kl,
-                                               const double* __restrict__ eps, double* __restrict__ g_eps) {
+                                               const double* __restrict__ eps, double* __restrict__ g_eps,
+                                               AdjTerms tm) {
     using V4 = typename Vec<T>::V4;
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
+    if (has_bit(tm.smask, j)) {
+        // the soft-source terms of step n -> n + 1 at node j (mu = lambda_E^{n+1}; a PEC node is
+        // held at zero and has no dependence)
+        const V4 l = ld_gather(LA + j);
+        if (l.w != T(0)) {
+            const double mu = (double)l.x;
+            const double t1 = (double)(*tm.seg0 + kl + 1) * tm.dt;
+            const double pi = 3.14159265358979323846;
+            for (int q = lower_bound_i64(tm.snode, tm.nsrc, j); q < tm.nsrc && tm.snode[q] == j; ++q) {
+                const int k = tm.sidx[q];
+                double x = pi * tm.f0[k] * (t1 - tm.t0[k]);
+                x = x * x;
+                const double r = (1.0 - 2.0 * x) * exp(-x);
+                tm.g_amp[k] += mu * r;
+                g_eps[j] += mu * tm.amp[k] * r / eps[j];
+            }
+        }
+    }
     const int64_t sl = j >> 5;
     const int64_t base = off[sl] * 32 + (j & 31);
     const int nc = (int)(off[sl + 1] - off[sl]);
@@ -271,7 +304,9 @@ __global__ void __launch_bounds__(256) k_adj_b(const int64_t* __restrict__ off, 
                                                const typename Vec<T>::V4* __restrict__ sy,
                                                const typename Vec<T>::V4* __restrict__ sv, int64_t n,
                                                const typename Vec<T>::V4* __restrict__ LB,
-                                               typename Vec<T>::V4* __restrict__ LA, T ch, T gamma) {
+                                               typename Vec<T>::V4* __restrict__ LA, T ch, T gamma,
+                                               const T* __restrict__ ez, const int64_t* __restrict__ slot0, int kl,
+                                               AdjTerms tm) {
     using V4 = typename Vec<T>::V4;
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -302,27 +337,34 @@ __global__ void __launch_bounds__(256) k_adj_b(const int64_t* __restrict__ off, 
     o.y = me.y + ch * gamma * vx;
     o.z = me.z + ch * gamma * vy;
     o.w = me.w;
+    if (has_bit(tm.pmask, j) && *tm.seg0 + kl >= tm.min_step) {
+        // the probe terms dJ/dE^n at node j, n = *seg0 + kl (one per probe on the node)
+        const T e = ez[(*slot0 + kl) * n + j];
+        for (int q = lower_bound_i64(tm.pnode, tm.nprobe, j); q < tm.nprobe && tm.pnode[q] == j; ++q)
+            o.x += (T)(2.0 * tm.dt * (double)e);
+    }
     st4(LA + j, o);
 }
 
 cudaError_t adj_pass(const AdjArgs& a, int pass, cudaStream_t s) {
     const unsigned g = (unsigned)((a.n + 255) / 256);
+    const AdjTerms tm = a.terms ? *a.terms : AdjTerms{};
     if (a.fp64) {
         const dbl4 *x = (const dbl4*)a.sx, *y = (const dbl4*)a.sy, *v = (const dbl4*)a.sv;
         if (pass == 0)
             k_adj_a<double><<<g, 256, 0, s>>>(a.off, a.scol, x, y, v, a.n, (const dbl4*)a.LA, (dbl4*)a.LB, a.gamma,
-                                              (const double*)a.ez, a.slot0, a.k, a.eps, a.g_eps);
+                                              (const double*)a.ez, a.slot0, a.k, a.eps, a.g_eps, tm);
         else
             k_adj_b<double><<<g, 256, 0, s>>>(a.off, a.scol, x, y, v, a.n, (const dbl4*)a.LB, (dbl4*)a.LA, a.ch,
-                                              a.gamma);
+                                              a.gamma, (const double*)a.ez, a.slot0, a.k, tm);
     } else {
         const float4 *x = (const float4*)a.sx, *y = (const float4*)a.sy, *v = (const float4*)a.sv;
         if (pass == 0)
             k_adj_a<float><<<g, 256, 0, s>>>(a.off, a.scol, x, y, v, a.n, (const float4*)a.LA, (float4*)a.LB,
-                                             (float)a.gamma, (const float*)a.ez, a.slot0, a.k, a.eps, a.g_eps);
+                                             (float)a.gamma, (const float*)a.ez, a.slot0, a.k, a.eps, a.g_eps, tm);
         else
             k_adj_b<float><<<g, 256, 0, s>>>(a.off, a.scol, x, y, v, a.n, (const float4*)a.LB, (float4*)a.LA,
-                                             (float)a.ch, (float)a.gamma);
+                                             (float)a.ch, (float)a.gamma, (const float*)a.ez, a.slot0, a.k, tm);
     }
     return cudaGetLastError();
 }
@@ -366,37 +408,6 @@ cudaError_t init_lambda(bool fp64, void* LA, const void* A, int64_t n, cudaStrea
     const unsigned g = (unsigned)((n + 255) / 256);
     if (fp64) k_init_lambda<double><<<g, 256, 0, s>>>((double*)LA, (const double*)A, n);
     else k_init_lambda<float><<<g, 256, 0, s>>>((float*)LA, (const float*)A, n);
-    return cudaGetLastError();
-}
-
-template <typename T>
-__global__ void k_adj_src(const T* __restrict__ LA, const int64_t* __restrict__ node, const double* __restrict__ amp,
-                          const double* __restrict__ f0, const double* __restrict__ t0, int nsrc,
-                          const int64_t* __restrict__ seg0, int kstep, double dt, const double* __restrict__ eps,
-                          double* __restrict__ g_eps, double* __restrict__ g_amp) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;  // one thread per source
-    if (k >= nsrc) return;
-    const double t1 = (double)(*seg0 + kstep + 1) * dt;
-    const double pi = 3.14159265358979323846;
-    const int64_t i = node[k];
-    if (LA[4 * i + 3] == T(0)) return;  // PEC node: held at zero, no dependence
-    const double mu = (double)LA[4 * i];
-    double x = pi * f0[k] * (t1 - t0[k]);
-    x = x * x;
-    const double r = (1.0 - 2.0 * x) * exp(-x);
-    g_amp[k] += mu * r;
-    atomicAdd(g_eps + i, mu * amp[k] * r / eps[i]);  // two sources on one node add in either order
-}
-
-cudaError_t adj_sources(bool fp64, const void* LA, const int64_t* node, const double* amp, const double* f0,
-                        const double* t0, int nsrc, const int64_t* seg0, int k, double dt, const double* eps,
-                        double* g_eps, double* g_amp, cudaStream_t s) {
-    if (nsrc <= 0) return cudaSuccess;
-    const unsigned g = (unsigned)((nsrc + 127) / 128);
-    if (fp64)
-        k_adj_src<double><<<g, 128, 0, s>>>((const double*)LA, node, amp, f0, t0, nsrc, seg0, k, dt, eps, g_eps, g_amp);
-    else
-        k_adj_src<float><<<g, 128, 0, s>>>((const float*)LA, node, amp, f0, t0, nsrc, seg0, k, dt, eps, g_eps, g_amp);
     return cudaGetLastError();
 }
 

@@ -50,12 +50,39 @@ struct AdjArgs {
     int k = 0;
     const double* eps = nullptr;
     double* g_eps = nullptr;
+    // the per-step source and probe terms, done by the threads of their nodes
+    // inside the passes (see AdjTerms)
+    const struct AdjTerms* terms = nullptr;
+};
+
+// Source and probe terms of a backward step, fused into the passes: the thread
+// of node j finds its sources (pass 0) or probes (pass 1) through a bit per node
+// and a node-sorted list. Pass 0 adds, before the step's own permittivity term,
+// g_amp[k] += mu r_k(t_{n+1}) and g_eps[j] += mu amp_k r_k(t_{n+1}) / eps_r for
+// every source k at j (mu = lambda_E^{n+1} at j, n = *seg0 + k_step); pass 1 adds
+// 2 dt Ez^n(j) to lambda_E^n once per probe at j when n >= min_step.
+struct AdjTerms {
+    const uint32_t* smask = nullptr;  // bit j: node j holds a source
+    const int64_t* snode = nullptr;   // source nodes, ascending (ties in source order)
+    const int* sidx = nullptr;        // the source index of each entry of snode
+    int nsrc = 0;
+    const double* amp = nullptr;
+    const double* f0 = nullptr;
+    const double* t0 = nullptr;
+    double* g_amp = nullptr;
+    const uint32_t* pmask = nullptr;  // bit j: node j holds a probe
+    const int64_t* pnode = nullptr;   // probe nodes, ascending
+    int nprobe = 0;
+    const int64_t* seg0 = nullptr;    // first step of the segment (device)
+    double dt = 0;
+    int64_t min_step = 0;
 };
 
 // pass 0: LA -> LB (and the permittivity gradient of this step); pass 1: LB -> LA
 cudaError_t adj_pass(const AdjArgs& a, int pass, cudaStream_t s);
 
-// the probe term dJ/dE^n of J = dt sum_n sum_p (Ez_p^n)^2: LA[p].x += 2 dt Ez[p] at every probe,
+// the probe term dJ/dE^n of J = dt sum_n sum_p (Ez_p^n)^2: LA[p].x += 2 dt Ez[p] at every probe
+// (the backward steps add it inside pass 1, AdjTerms; this kernel serves the last level),
 // Ez = ez + (*slot0 + k) * n (ez itself when slot0 is NULL). With seg0 (device) the term
 // belongs to step n = *seg0 + k and is skipped when n < min_step (the state before the first
 // recorded step is not an objective term). One thread per probe (atomic adds: two probes on
@@ -66,13 +93,6 @@ cudaError_t adj_probe_term(bool fp64, void* LA, const void* ez, const int64_t* p
 
 // LA = {0, 0, 0, ce} from the state A = {Ez, Hx, Hy, ce}
 cudaError_t init_lambda(bool fp64, void* LA, const void* A, int64_t n, cudaStream_t s);
-
-// soft-source terms of step n -> n + 1 with n = *seg0 + k (seg0 on the device, so
-// that a captured segment replays for any segment; t1 = t_{n+1}): with mu = Z lambda_E^{n+1},
-// g_amp[k] += mu_k r_k(t1) and g_eps[node_k] += mu_k amp_k r_k(t1) / eps_r
-cudaError_t adj_sources(bool fp64, const void* LA, const int64_t* node, const double* amp, const double* f0,
-                        const double* t0, int nsrc, const int64_t* seg0, int k, double dt, const double* eps,
-                        double* g_eps, double* g_amp, cudaStream_t s);
 
 // J += dt sum of squares of `count` probe values (FP64 accumulator)
 cudaError_t probe_energy(bool fp64, const void* buf, int64_t count, double dt, double* J, cudaStream_t s);

@@ -293,6 +293,13 @@ mfd_status pack_weights(mfd_ctx* ctx, const mfd_weights* w, int out_index, int c
 
 int chunks_of(int n) { return (n + 3) / 4; }
 
+// a host vector into a new device buffer (at least one element), synchronously
+template <typename T> mfd_status upload_host(DevBuf& b, const std::vector<T>& v) {
+    MFD_TRY(b.alloc(std::max<size_t>(1, v.size()) * sizeof(T)));
+    if (!v.empty()) MFD_CUDA(cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return MFD_OK;
+}
+
 // Q16 form of one index stream (chunks4 chunks of 4 entries per row)
 mfd_status pack_q16(mfd_ctx* ctx, const mfd_stencils* st, int n_use, int chunks4, DevBuf& q, DevBuf& qb,
                     int64_t& wide) {
@@ -1225,6 +1232,47 @@ mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, doub
     a.g_eps = geps.as<double>();
     a.ez = hist.p;
     a.slot0 = slot0.as<int64_t>();
+    // the per-step source and probe terms, fused into the passes: node bits and node-sorted lists
+    AdjTerms terms;
+    DevBuf d_smask, d_pmask, d_snode, d_sidx, d_pnode;
+    {
+        const int64_t words = (n + 31) / 32;
+        std::vector<int64_t> hs(sim->nsrc), hp(sim->nprobe);
+        MFD_CUDA(cudaStreamSynchronize(s));
+        if (sim->nsrc) MFD_CUDA(cudaMemcpy(hs.data(), sim->src_node.p, sim->nsrc * 8, cudaMemcpyDeviceToHost));
+        MFD_CUDA(cudaMemcpy(hp.data(), sim->probe_node.p, sim->nprobe * 8, cudaMemcpyDeviceToHost));
+        std::vector<int> order(sim->nsrc);
+        for (int k = 0; k < sim->nsrc; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hs[x] < hs[y]; });
+        std::vector<int64_t> sn(sim->nsrc);
+        std::vector<uint32_t> sm(words, 0u), pm(words, 0u);
+        for (int q = 0; q < sim->nsrc; ++q) {
+            sn[q] = hs[order[q]];
+            sm[sn[q] >> 5] |= 1u << (sn[q] & 31);
+        }
+        std::sort(hp.begin(), hp.end());
+        for (int64_t v : hp) pm[v >> 5] |= 1u << (v & 31);
+        MFD_TRY(upload_host(d_smask, sm));
+        MFD_TRY(upload_host(d_pmask, pm));
+        MFD_TRY(upload_host(d_snode, sn));
+        MFD_TRY(upload_host(d_sidx, order));
+        MFD_TRY(upload_host(d_pnode, hp));
+        terms.smask = sim->nsrc ? d_smask.as<uint32_t>() : nullptr;
+        terms.snode = d_snode.as<int64_t>();
+        terms.sidx = d_sidx.as<int>();
+        terms.nsrc = sim->nsrc;
+        terms.amp = sim->src_amp.as<double>();
+        terms.f0 = sim->src_f0.as<double>();
+        terms.t0 = sim->src_t0.as<double>();
+        terms.g_amp = gamp.as<double>();
+        terms.pmask = d_pmask.as<uint32_t>();
+        terms.pnode = d_pnode.as<int64_t>();
+        terms.nprobe = sim->nprobe;
+        terms.seg0 = seg0.as<int64_t>();
+        terms.dt = sim->d.dt;
+        terms.min_step = start + 1;
+    }
+    a.terms = &terms;
     // ---- backward over the segments; a full segment is a captured graph replayed
     // for every full segment (the segment's first step and first level live on the
     // device: seg0, slot0)
@@ -1239,16 +1287,11 @@ mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, doub
     auto sweep = [&](int64_t len) -> cudaError_t {
         cudaError_t e = cudaSuccess;
         for (int64_t k = len - 1; k >= 0 && e == cudaSuccess; --k) {  // step seg0 + k -> seg0 + k + 1
-            e = adj_sources(f64, LA.p, sim->src_node.as<int64_t>(), sim->src_amp.as<double>(), sim->src_f0.as<double>(),
-                            sim->src_t0.as<double>(), sim->nsrc, seg0.as<int64_t>(), (int)k, sim->d.dt,
-                            sim->eps.as<double>(), geps.as<double>(), gamp.as<double>(), s);
+            // pass 0 adds the step's source terms, pass 1 the probe terms of level seg0 + k (AdjTerms)
             AdjArgs ak = a;
             ak.k = (int)k;
-            if (e == cudaSuccess) e = adj_pass(ak, 0, s);
+            e = adj_pass(ak, 0, s);
             if (e == cudaSuccess) e = adj_pass(ak, 1, s);
-            if (e == cudaSuccess)
-                e = adj_probe_term(f64, LA.p, hist.p, sim->probe_node.as<int64_t>(), sim->nprobe, sim->d.dt, s,
-                                   seg0.as<int64_t>(), (int)k, start + 1, slot0.as<int64_t>(), n);
         }
         return e;
     };
