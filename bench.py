@@ -385,7 +385,7 @@ def main():
                        "courant": S, "compensated": comp, "l2_flush": f"inputs larger than L2 ({step_gb:.2f} GB/step)",
                        "parallelism": f"replicas{world}", "setup_s": setup,
                        "autotuned_blocks": {"h_pass": blocks[0], "e_pass": blocks[1]}},
-            "roofline": roof, "clocks": clocks, "gpu_launches": 2 * a.steps,
+            "roofline": roof, "clocks": clocks, "gpu_launches": 3 * a.steps,
             "event_timed_ms_per_step": (ms[0] + ms[1]) / a.steps,
             "index_i32": {"ms_per_step": i32_ms, "steps": k32,
                           "value": per_step_updates / (i32_ms / 1e3) * world}}

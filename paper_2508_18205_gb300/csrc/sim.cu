@@ -160,6 +160,37 @@ __global__ void k_zero_held(T* __restrict__ E, int stride, const uint8_t* __rest
     if (m & 3u) E[k * stride + 2] = T(0);
 }
 
+// soft Ricker sources after the E update, then probes, then the step counter
+template <typename T>
+__global__ void k_post(T* __restrict__ ez, int ez_stride, const uint8_t* __restrict__ mask, unsigned held_bits,
+                       int nsrc, const int64_t* __restrict__ sn, const double* __restrict__ sa,
+                       const double* __restrict__ sf, const double* __restrict__ st0, int nprobe,
+                       const int64_t* __restrict__ pn, T* __restrict__ pbuf, int64_t pcap,
+                       const int64_t* __restrict__ pstep0, int64_t* __restrict__ counter, double dt) {
+    __shared__ int64_t n_s;
+    if (threadIdx.x == 0) n_s = *counter;
+    __syncthreads();
+    const int64_t n = n_s;
+    const double t1 = (double)(n + 1) * dt;
+    const double pi = 3.14159265358979323846;
+    for (int s = threadIdx.x; s < nsrc; s += blockDim.x) {
+        const int64_t i = sn[s];
+        if (mask && (mask[i] & held_bits)) continue;
+        double a = pi * sf[s] * (t1 - st0[s]);
+        a = a * a;
+        const double r = (1.0 - 2.0 * a) * exp(-a);
+        atomicAdd(ez + i * ez_stride, (T)(sa[s] * r));
+    }
+    __syncthreads();
+    if (nprobe > 0) {
+        const int64_t rec = n - *pstep0;
+        if (rec >= 0 && rec < pcap)
+            for (int p = threadIdx.x; p < nprobe; p += blockDim.x) pbuf[rec * nprobe + p] = ez[pn[p] * ez_stride];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *counter = n + 1;
+}
+
 __global__ void k_sum(const double* __restrict__ partial, int n, double* __restrict__ out) {
     __shared__ double red[256];
     double s = 0.0;
@@ -206,8 +237,6 @@ struct mfd_sim {
     PackedStencil hp, ep;  // H-pass and E-pass streams (collocated: ep unused)
     DevBuf s0, s1, s2, s3, s4, s5;
     DevBuf eps, mask, counter, pstep0;
-    // sources and probes for the E pass (PostArgs): node bits and node-sorted lists
-    DevBuf post_smask, post_snode, post_sidx, post_pmask, post_pnode, post_pidx, done;
     bool has_mask = false;
     DevBuf src_node, src_amp, src_f0, src_t0;
     int nsrc = 0;
@@ -354,46 +383,6 @@ template <typename T> StencilStreams<T> streams(const PackedStencil& p, bool q16
     return s;
 }
 
-// node bits (n nodes) and the node-sorted order of a list of nodes (ties keep the list's order)
-mfd_status node_lists(int64_t n, const std::vector<int64_t>& nodes, DevBuf& mask, DevBuf& sorted, DevBuf& index) {
-    std::vector<int> order(nodes.size());
-    for (size_t k = 0; k < nodes.size(); ++k) order[k] = (int)k;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return nodes[x] < nodes[y]; });
-    std::vector<int64_t> sn(nodes.size());
-    std::vector<uint32_t> bits((n + 31) / 32, 0u);
-    for (size_t q = 0; q < nodes.size(); ++q) {
-        sn[q] = nodes[order[q]];
-        bits[sn[q] >> 5] |= 1u << (sn[q] & 31);
-    }
-    MFD_TRY(upload_host(mask, bits));
-    MFD_TRY(upload_host(sorted, sn));
-    return upload_host(index, order);
-}
-
-PostArgs post_args(mfd_sim* sim) {
-    PostArgs pa;
-    if (sim->nsrc > 0) pa.smask = sim->post_smask.as<uint32_t>();
-    pa.snode = sim->post_snode.as<int64_t>();
-    pa.sidx = sim->post_sidx.as<int>();
-    pa.nsrc = sim->nsrc;
-    pa.amp = sim->src_amp.as<double>();
-    pa.f0 = sim->src_f0.as<double>();
-    pa.t0 = sim->src_t0.as<double>();
-    pa.held = sim->has_mask ? sim->mask.as<uint8_t>() : nullptr;
-    pa.held_bits = sim->layout == COLLOC3D ? 3u : 0xFFu;
-    if (sim->nprobe > 0) pa.pmask = sim->post_pmask.as<uint32_t>();
-    pa.pnode = sim->post_pnode.as<int64_t>();
-    pa.pidx = sim->post_pidx.as<int>();
-    pa.nprobe = sim->nprobe;
-    pa.pbuf = sim->probe_buf.p;
-    pa.pcap = sim->probe_cap;
-    pa.pstep0 = sim->pstep0.as<int64_t>();
-    pa.counter = sim->counter.as<int64_t>();
-    pa.done = sim->done.as<unsigned>();
-    pa.dt = sim->d.dt;
-    return pa;
-}
-
 Launch2D make2d(mfd_sim* sim, int parity) {
     Launch2D L;
     L.staggered = sim->layout == STAG2D;
@@ -411,7 +400,6 @@ Launch2D make2d(mfd_sim* sim, int parity) {
     L.kd.gamma = sim->d.gamma;
     L.block[0] = sim->block[0];
     L.block[1] = sim->block[1];
-    L.post = post_args(sim);
     if (!L.staggered) {
         L.A = sim->s0.p;
         L.B = sim->s1.p;
@@ -444,7 +432,6 @@ Launch3D make3d(mfd_sim* sim, int parity) {
     L.Es = sim->s1.p;
     L.Hn = sim->s2.p;
     L.wall = sim->has_mask ? sim->mask.as<const uint8_t>() : nullptr;
-    L.post = post_args(sim);
     return L;
 }
 
@@ -460,6 +447,26 @@ void ez_location(mfd_sim* sim, int parity_after, void** base, int* stride) {
         *base = (char*)sim->s0.p + 2 * sim->rs;
         *stride = 8;
     }
+}
+
+cudaError_t launch_post(mfd_sim* sim, int parity_after) {
+    void* ez;
+    int stride;
+    ez_location(sim, parity_after, &ez, &stride);
+    const uint8_t* mask = sim->has_mask ? sim->mask.as<const uint8_t>() : nullptr;
+    unsigned held = sim->layout == COLLOC3D ? 3u : 0xFFu;
+    const double dt = sim->d.dt;
+    if (sim->fp64)
+        k_post<double><<<1, 256, 0, sim->ctx->stream>>>(
+            (double*)ez, stride, mask, held, sim->nsrc, sim->src_node.as<int64_t>(), sim->src_amp.as<double>(),
+            sim->src_f0.as<double>(), sim->src_t0.as<double>(), sim->nprobe, sim->probe_node.as<int64_t>(),
+            sim->probe_buf.as<double>(), sim->probe_cap, sim->pstep0.as<int64_t>(), sim->counter.as<int64_t>(), dt);
+    else
+        k_post<float><<<1, 256, 0, sim->ctx->stream>>>(
+            (float*)ez, stride, mask, held, sim->nsrc, sim->src_node.as<int64_t>(), sim->src_amp.as<double>(),
+            sim->src_f0.as<double>(), sim->src_t0.as<double>(), sim->nprobe, sim->probe_node.as<int64_t>(),
+            sim->probe_buf.as<float>(), sim->probe_cap, sim->pstep0.as<int64_t>(), sim->counter.as<int64_t>(), dt);
+    return cudaGetLastError();
 }
 
 // enqueues one step; events (optional): before H, between H and E, after E
@@ -481,6 +488,7 @@ cudaError_t enqueue_step(mfd_sim* sim, cudaEvent_t* ev) {
         if ((e = launch_2d(L, 1, s)) != cudaSuccess) return e;
     }
     if (ev) cudaEventRecord(ev[2], s);
+    if ((e = launch_post(sim, pn)) != cudaSuccess) return e;
     sim->parity = pn;
     sim->steps += 1;
     return cudaSuccess;
@@ -592,13 +600,11 @@ mfd_status mfd_sim_create(mfd_ctx* ctx, const mfd_sim_desc* desc, mfd_sim** out)
     for (DevBuf* b : {&sim->s0, &sim->s1, &sim->s2, &sim->s3, &sim->s4})
         if (b->p) cudaMemsetAsync(b->p, 0, b->bytes, ctx->stream);
     const int64_t nmax = std::max(ne, nh);
-    if ((st = sim->done.alloc(4)) || (st = sim->eps.alloc(ne * 8)) || (st = sim->mask.alloc(ne)) ||
-        (st = sim->counter.alloc(8)) ||
+    if ((st = sim->eps.alloc(ne * 8)) || (st = sim->mask.alloc(ne)) || (st = sim->counter.alloc(8)) ||
         (st = sim->pstep0.alloc(8)) || (st = sim->partial.alloc(((nmax + 255) / 256) * 8)) ||
         (st = sim->energy_out.alloc(8)))
         return bail(st);
     cudaMemsetAsync(sim->counter.p, 0, 8, ctx->stream);
-    cudaMemsetAsync(sim->done.p, 0, 4, ctx->stream);
     cudaMemsetAsync(sim->pstep0.p, 0, 8, ctx->stream);
     *out = sim;
     st = mfd_set_materials(sim, nullptr, nullptr);
@@ -821,8 +827,6 @@ mfd_status mfd_set_sources(mfd_sim* sim, int count, const int64_t* node, const i
     MFD_TRY(upload(ctx, sim->src_amp, amp, count * 8));
     MFD_TRY(upload(ctx, sim->src_f0, f0, count * 8));
     MFD_TRY(upload(ctx, sim->src_t0, t0, count * 8));
-    MFD_CUDA(cudaStreamSynchronize(ctx->stream));
-    MFD_TRY(node_lists(sim->ne, dev_node, sim->post_smask, sim->post_snode, sim->post_sidx));
     sim->nsrc = count;
     sim->graph_ok = false;
     MFD_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -840,8 +844,6 @@ mfd_status mfd_set_probes(mfd_sim* sim, int count, const int64_t* node, int64_t 
         dev_node[p] = sim->eset->h_inv[node[p]];
     }
     MFD_TRY(upload(ctx, sim->probe_node, dev_node.data(), count * 8));
-    MFD_CUDA(cudaStreamSynchronize(ctx->stream));
-    MFD_TRY(node_lists(sim->ne, dev_node, sim->post_pmask, sim->post_pnode, sim->post_pidx));
     MFD_TRY(sim->probe_buf.alloc(std::max<int64_t>(1, capacity * count) * sim->rs));
     sim->nprobe = count;
     sim->probe_cap = capacity;
@@ -1035,11 +1037,10 @@ mfd_status mfd_sim_autotune(mfd_sim* sim, int reps, int* chosen) {
     mfd_ctx* ctx = sim->ctx;
     MFD_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t s = ctx->stream;
-    // the timed launches overwrite state buffers and advance the step counter (the E pass):
-    // keep a copy and put it back
-    DevBuf* bufs[6] = {&sim->s0, &sim->s1, &sim->s2, &sim->s3, &sim->s4, &sim->counter};
-    DevBuf save[6];
-    for (int b = 0; b < 6; ++b)
+    // the timed launches overwrite state buffers: keep a copy and put it back
+    DevBuf* bufs[5] = {&sim->s0, &sim->s1, &sim->s2, &sim->s3, &sim->s4};
+    DevBuf save[5];
+    for (int b = 0; b < 5; ++b)
         if (bufs[b]->p) {
             MFD_TRY(save[b].alloc(bufs[b]->bytes));
             MFD_CUDA(cudaMemcpyAsync(save[b].p, bufs[b]->p, bufs[b]->bytes, cudaMemcpyDeviceToDevice, s));
@@ -1087,7 +1088,7 @@ mfd_status mfd_sim_autotune(mfd_sim* sim, int reps, int* chosen) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    for (int b = 0; b < 6; ++b)
+    for (int b = 0; b < 5; ++b)
         if (bufs[b]->p) cudaMemcpyAsync(bufs[b]->p, save[b].p, bufs[b]->bytes, cudaMemcpyDeviceToDevice, s);
     MFD_CUDA(cudaStreamSynchronize(s));
     if (st != MFD_OK) return st;

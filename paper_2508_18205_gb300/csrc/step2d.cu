@@ -108,11 +108,12 @@ __global__ void __launch_bounds__(512) k_h_colloc(StencilStreams<T> s, Coefs<T> 
 }
 
 template <typename T, int NC, bool SHARED, bool COMP>
-__device__ __forceinline__ void e_colloc_node(const StencilStreams<T>& s, const typename Vec<T>::V4* __restrict__ B,
-                                              typename Vec<T>::V4* __restrict__ A, int64_t i, const PostArgs& pa,
-                                              int64_t nstep) {
+__global__ void __launch_bounds__(512) k_e_colloc(StencilStreams<T> s, const typename Vec<T>::V4* __restrict__ B,
+                                                  typename Vec<T>::V4* __restrict__ A) {
     using V4 = typename Vec<T>::V4;
     using Acc = typename AccSel<T, COMP>::type;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= s.n) return;
     const int nc = NC ? NC : s.nc;
     const int ni = SHARED ? s.ni : nc;
     const int64_t slice = i >> 5;
@@ -132,22 +133,12 @@ __device__ __forceinline__ void e_colloc_node(const StencilStreams<T>& s, const 
     }
     const V4 me = ld_gather(B + i);
     V4 out;
-    out.x = post_node<T>(pa, i, me.x + me.w * (dxHy.get() - dyHx.get()), nstep);
+    out.x = me.x + me.w * (dxHy.get() - dyHx.get());
     out.y = me.y;
     out.z = me.z;
     out.w = me.w;
     st4(A + i, out);
 }
-
-template <typename T, int NC, bool SHARED, bool COMP>
-__global__ void __launch_bounds__(512) k_e_colloc(StencilStreams<T> s, const typename Vec<T>::V4* __restrict__ B,
-                                                  typename Vec<T>::V4* __restrict__ A, PostArgs pa) {
-    const int64_t nstep = post_step(pa);
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < s.n) e_colloc_node<T, NC, SHARED, COMP>(s, B, A, i, pa, nstep);
-    post_finish(pa, nstep);
-}
-
 
 // energy (Eq. 20) of the collocated state at t_n: H averaged with the H
 // update computed on the fly; per-block partial sums in FP64
@@ -239,13 +230,14 @@ __global__ void __launch_bounds__(512) k_h_stag(StencilStreams<T> s, Coefs<T> k,
 }
 
 template <typename T, int NC, int NV, bool COMP>
-__device__ __forceinline__ void e_stag_node(const StencilStreams<T>& s, const Coefs<T>& k,
-                                            const typename Vec<T>::V2* __restrict__ Hn, const T* __restrict__ Ez,
-                                            const T* __restrict__ ce, T* __restrict__ Ezn, int64_t i,
-                                            const PostArgs& pa, int64_t nstep) {
+__global__ void __launch_bounds__(512) k_e_stag(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V2* __restrict__ Hn,
+                                                const T* __restrict__ Ez, const T* __restrict__ ce,
+                                                T* __restrict__ Ezn) {
     using V4 = typename Vec<T>::V4;
     using V2 = typename Vec<T>::V2;
     using Acc = typename AccSel<T, COMP>::type;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= s.n) return;
     const int nc = NC ? NC : s.nc;
     const int nv = NV ? NV : s.nv;
     const int64_t slice = i >> 5;
@@ -269,17 +261,7 @@ __device__ __forceinline__ void e_stag_node(const StencilStreams<T>& s, const Co
         he.add(wv.x, f0); he.add(wv.y, f1); he.add(wv.z, f2); he.add(wv.w, f3);
     });
     const T e = ld_gather(Ez + i);
-    Ezn[i] = post_node<T>(pa, i, e + ld_gather(ce + i) * (dxHy.get() - dyHx.get() + k.gamma * he.get()), nstep);
-}
-
-template <typename T, int NC, int NV, bool COMP>
-__global__ void __launch_bounds__(512) k_e_stag(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V2* __restrict__ Hn,
-                                                const T* __restrict__ Ez, const T* __restrict__ ce,
-                                                T* __restrict__ Ezn, PostArgs pa) {
-    const int64_t nstep = post_step(pa);
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < s.n) e_stag_node<T, NC, NV, COMP>(s, k, Hn, Ez, ce, Ezn, i, pa, nstep);
-    post_finish(pa, nstep);
+    Ezn[i] = e + ld_gather(ce + i) * (dxHy.get() - dyHx.get() + k.gamma * he.get());
 }
 
 template <typename T, bool COMP>
@@ -314,7 +296,7 @@ __global__ void __launch_bounds__(256) k_energy_stag(StencilStreams<T> s, Coefs<
 
 template <typename T, bool COMP>
 static cudaError_t launch_colloc_pass(int pass, const StencilStreams<T>& s, const Coefs<T>& k, void* A, void* B,
-                                      int block, cudaStream_t st, const PostArgs& pa) {
+                                      int block, cudaStream_t st) {
     using V4 = typename Vec<T>::V4;
     const bool shared = s.idx_v == s.idx_c;
     const unsigned grid = (unsigned)((s.n + block - 1) / block);
@@ -328,8 +310,8 @@ static cudaError_t launch_colloc_pass(int pass, const StencilStreams<T>& s, cons
     }
 #define MFD_E(NC)                                                                     \
     if (s.nc == NC) {                                                                 \
-        if (shared) k_e_colloc<T, NC, true, COMP><<<grid, block, 0, st>>>(s, b, a, pa);     \
-        else k_e_colloc<T, NC, false, COMP><<<grid, block, 0, st>>>(s, b, a, pa);           \
+        if (shared) k_e_colloc<T, NC, true, COMP><<<grid, block, 0, st>>>(s, b, a);     \
+        else k_e_colloc<T, NC, false, COMP><<<grid, block, 0, st>>>(s, b, a);           \
         return cudaGetLastError();                                                    \
     }
     if (pass == 0) {
@@ -338,8 +320,8 @@ static cudaError_t launch_colloc_pass(int pass, const StencilStreams<T>& s, cons
         else k_h_colloc<T, 0, 0, false, COMP><<<grid, block, 0, st>>>(s, k, a, b);
     } else {
         MFD_E(3) MFD_E(5) MFD_E(8) MFD_E(10)
-        if (shared) k_e_colloc<T, 0, true, COMP><<<grid, block, 0, st>>>(s, b, a, pa);
-        else k_e_colloc<T, 0, false, COMP><<<grid, block, 0, st>>>(s, b, a, pa);
+        if (shared) k_e_colloc<T, 0, true, COMP><<<grid, block, 0, st>>>(s, b, a);
+        else k_e_colloc<T, 0, false, COMP><<<grid, block, 0, st>>>(s, b, a);
     }
 #undef MFD_H
 #undef MFD_E
@@ -348,7 +330,7 @@ static cudaError_t launch_colloc_pass(int pass, const StencilStreams<T>& s, cons
 
 template <typename T, bool COMP>
 static cudaError_t launch_stag_pass(int pass, const StencilStreams<T>& s, const Coefs<T>& k, const Stag2DPtrs& p,
-                                    int block, cudaStream_t st, const PostArgs& pa) {
+                                    int block, cudaStream_t st) {
     using V2 = typename Vec<T>::V2;
     const unsigned grid = (unsigned)((s.n + block - 1) / block);
     const T* ez = static_cast<const T*>(p.ez);
@@ -361,9 +343,9 @@ static cudaError_t launch_stag_pass(int pass, const StencilStreams<T>& s, const 
         else if (s.nc == 3 && s.nv == 8) k_h_stag<T, 3, 8, COMP><<<grid, block, 0, st>>>(s, k, ez, h, hn);
         else k_h_stag<T, 0, 0, COMP><<<grid, block, 0, st>>>(s, k, ez, h, hn);
     } else {
-        if (s.nc == 8 && s.nv == 15) k_e_stag<T, 8, 15, COMP><<<grid, block, 0, st>>>(s, k, hn, ez, ce, ezn, pa);
-        else if (s.nc == 3 && s.nv == 8) k_e_stag<T, 3, 8, COMP><<<grid, block, 0, st>>>(s, k, hn, ez, ce, ezn, pa);
-        else k_e_stag<T, 0, 0, COMP><<<grid, block, 0, st>>>(s, k, hn, ez, ce, ezn, pa);
+        if (s.nc == 8 && s.nv == 15) k_e_stag<T, 8, 15, COMP><<<grid, block, 0, st>>>(s, k, hn, ez, ce, ezn);
+        else if (s.nc == 3 && s.nv == 8) k_e_stag<T, 3, 8, COMP><<<grid, block, 0, st>>>(s, k, hn, ez, ce, ezn);
+        else k_e_stag<T, 0, 0, COMP><<<grid, block, 0, st>>>(s, k, hn, ez, ce, ezn);
     }
     return cudaGetLastError();
 }
@@ -371,13 +353,13 @@ static cudaError_t launch_stag_pass(int pass, const StencilStreams<T>& s, const 
 cudaError_t launch_2d(const Launch2D& L, int pass, cudaStream_t st) {
     const int b = L.block[pass];
     if (L.staggered) {
-        if (L.fp64) return launch_stag_pass<double, false>(pass, pass == 0 ? L.hs.d : L.es.d, L.kd, L.stag, b, st, L.post);
-        if (L.comp) return launch_stag_pass<float, true>(pass, pass == 0 ? L.hs.f : L.es.f, L.kf, L.stag, b, st, L.post);
-        return launch_stag_pass<float, false>(pass, pass == 0 ? L.hs.f : L.es.f, L.kf, L.stag, b, st, L.post);
+        if (L.fp64) return launch_stag_pass<double, false>(pass, pass == 0 ? L.hs.d : L.es.d, L.kd, L.stag, b, st);
+        if (L.comp) return launch_stag_pass<float, true>(pass, pass == 0 ? L.hs.f : L.es.f, L.kf, L.stag, b, st);
+        return launch_stag_pass<float, false>(pass, pass == 0 ? L.hs.f : L.es.f, L.kf, L.stag, b, st);
     }
-    if (L.fp64) return launch_colloc_pass<double, false>(pass, L.hs.d, L.kd, L.A, L.B, b, st, L.post);
-    if (L.comp) return launch_colloc_pass<float, true>(pass, L.hs.f, L.kf, L.A, L.B, b, st, L.post);
-    return launch_colloc_pass<float, false>(pass, L.hs.f, L.kf, L.A, L.B, b, st, L.post);
+    if (L.fp64) return launch_colloc_pass<double, false>(pass, L.hs.d, L.kd, L.A, L.B, b, st);
+    if (L.comp) return launch_colloc_pass<float, true>(pass, L.hs.f, L.kf, L.A, L.B, b, st);
+    return launch_colloc_pass<float, false>(pass, L.hs.f, L.kf, L.A, L.B, b, st);
 }
 
 cudaError_t launch_energy_2d(const Launch2D& L, const double* eps_r, int64_t ne, double eta2, double* partial,

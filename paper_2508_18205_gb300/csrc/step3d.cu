@@ -144,12 +144,13 @@ __global__ void __launch_bounds__(512, 2) k_h3(StencilStreams<T> s, Coefs<T> k, 
 }
 
 template <typename T, int NC, bool SHARED, bool COMP>
-__device__ __forceinline__ void e3_node(const StencilStreams<T>& s, const typename Vec<T>::V4* __restrict__ Hn,
-                                        const typename Vec<T>::V4* __restrict__ Es, const uint8_t* __restrict__ wall,
-                                        typename Vec<T>::V4* __restrict__ F, int64_t i, const PostArgs& pa,
-                                        int64_t nstep) {
+__global__ void __launch_bounds__(512, 2) k_e3(StencilStreams<T> s, const typename Vec<T>::V4* __restrict__ Hn,
+                                            const typename Vec<T>::V4* __restrict__ Es,
+                                            const uint8_t* __restrict__ wall, typename Vec<T>::V4* __restrict__ F) {
     using V4 = typename Vec<T>::V4;
     using Acc = typename AccSel<T, COMP>::type;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= s.n) return;
     const int nc = NC ? NC : s.nc;
     const int ni = SHARED ? s.ni : nc;
     const int64_t slice = i >> 5;
@@ -195,19 +196,7 @@ __device__ __forceinline__ void e3_node(const StencilStreams<T>& s, const typena
         if (m & 5u) o.y = T(0);
         if (m & 3u) o.z = T(0);
     }
-    o.z = post_node<T>(pa, i, o.z, nstep);  // soft sources drive Ez, the probes record it
     st_eh(F + 2 * i, o, hown);
-}
-
-template <typename T, int NC, bool SHARED, bool COMP>
-__global__ void __launch_bounds__(512, 2) k_e3(StencilStreams<T> s, const typename Vec<T>::V4* __restrict__ Hn,
-                                            const typename Vec<T>::V4* __restrict__ Es,
-                                            const uint8_t* __restrict__ wall, typename Vec<T>::V4* __restrict__ F,
-                                            PostArgs pa) {
-    const int64_t nstep = post_step(pa);
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < s.n) e3_node<T, NC, SHARED, COMP>(s, Hn, Es, wall, F, i, pa, nstep);
-    post_finish(pa, nstep);
 }
 
 template <typename T, bool COMP>
@@ -259,9 +248,9 @@ static cudaError_t launch3(const Launch3D& L, const StencilStreams<T>& s, const 
         else if (shared) k_h3<T, 0, 0, true, COMP><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
         else k_h3<T, 0, 0, false, COMP><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
     } else {
-        if (shared && s.nc == 10) k_e3<T, 10, true, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F, L.post);
-        else if (shared) k_e3<T, 0, true, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F, L.post);
-        else k_e3<T, 0, false, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F, L.post);
+        if (shared && s.nc == 10) k_e3<T, 10, true, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F);
+        else if (shared) k_e3<T, 0, true, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F);
+        else k_e3<T, 0, false, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F);
     }
     return cudaGetLastError();
 }
