@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(32 * YW_W) k_yee(int nx, int ny, T ch, T ce, c
                                                    const T* __restrict__ hx, const T* __restrict__ hy,
                                                    T* __restrict__ ez_o, T* __restrict__ hx_o,
                                                    T* __restrict__ hy_o) {
-    static_assert(S == 1 || S == 2, "one or two steps per launch");
+    static_assert(S >= 1 && S <= 4, "one to four steps per launch");
     constexpr int TX = yee_tile_x<S>(), TY = yee_tile_y<S>();
     __shared__ T xe[YW_W][32];  // per warp: E^{n+1} of its first row
     __shared__ T xh[YW_W][32];  // per warp: Hx of its last row (H^{n+1/2}, then H^{n+3/2})
@@ -76,41 +76,10 @@ __global__ void __launch_bounds__(32 * YW_W) k_yee(int nx, int ny, T ch, T ce, c
             sy[k] = hy[g];
         }
     }
-    // H^{n+1/2}: valid on window columns 0 .. 30, rows 0 .. 34
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const T right = __shfl_down_sync(FULL, e[k], 1);
-        sx[k] = rn_sub(sx[k], rn_mul(ch, rn_sub(e[k + 1], e[k])));
-        sy[k] = rn_add(sy[k], rn_mul(ch, rn_sub(right, e[k])));
-    }
-    xh[w][lane] = sx[3];
-    __syncthreads();
-    T below = w > 0 ? xh[w - 1][lane] : sx[0];  // Hx of row r0 - 1 (row 0 is outside the valid region)
-    // E^{n+1}: valid on columns 1 .. 30, rows 1 .. 34
     const int i = x0 - S + lane;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const T left = __shfl_up_sync(FULL, sy[k], 1);
-        const T down = k > 0 ? sx[k - 1] : below;
-        const T curl = rn_add(rn_sub(rn_sub(sy[k], left), sx[k]), down);
-        const T en = rn_add(e[k], rn_mul(ce, curl));
-        if constexpr (S == 1) {
-            const int row = r0 + k, j = y0 - 1 + row;
-            if (lane >= 1 && lane < 1 + TX && row >= 1 && row < 1 + TY && i < nx && j < ny) {
-                const int64_t g = (int64_t)j * nx + i;
-                ez_o[g] = en;
-                hx_o[g] = sx[k];
-                hy_o[g] = sy[k];
-            }
-        } else {
-            e[k] = en;
-        }
-    }
-    if constexpr (S == 2) {
-        xe[w][lane] = e[0];
-        __syncthreads();  // also: every warp has read xh above
-        e[4] = w + 1 < YW_W ? xe[w + 1][lane] : e[3];  // E^{n+1} of row r0 + 4 (row 36: outside)
-        // H^{n+3/2}: valid on columns 1 .. 29, rows 1 .. 33
+    for (int st = 0; st < S; ++st) {
+        // H half step st: valid on window columns st .. 30 - st, rows st .. 34 - st
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const T right = __shfl_down_sync(FULL, e[k], 1);
@@ -118,21 +87,32 @@ __global__ void __launch_bounds__(32 * YW_W) k_yee(int nx, int ny, T ch, T ce, c
             sy[k] = rn_add(sy[k], rn_mul(ch, rn_sub(right, e[k])));
         }
         xh[w][lane] = sx[3];
-        __syncthreads();
-        below = w > 0 ? xh[w - 1][lane] : sx[0];
-        // E^{n+2} on the tile (columns 2 .. 29, rows 2 .. 33) with the tile's H^{n+3/2}
+        __syncthreads();  // also: every warp has read xe of the previous step
+        const T below = w > 0 ? xh[w - 1][lane] : sx[0];  // Hx of row r0 - 1 (row 0 is outside the valid region)
+        // E half step st: valid on columns st + 1 .. 30 - st, rows st + 1 .. 34 - st; after the
+        // last, the tile (columns and rows S .. end - S) is written with its H
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const T left = __shfl_up_sync(FULL, sy[k], 1);
             const T down = k > 0 ? sx[k - 1] : below;
             const T curl = rn_add(rn_sub(rn_sub(sy[k], left), sx[k]), down);
-            const int row = r0 + k, j = y0 - 2 + row;
-            if (lane >= 2 && lane < 2 + TX && row >= 2 && row < 2 + TY && i < nx && j < ny) {
-                const int64_t g = (int64_t)j * nx + i;
-                ez_o[g] = rn_add(e[k], rn_mul(ce, curl));
-                hx_o[g] = sx[k];
-                hy_o[g] = sy[k];
+            const T en = rn_add(e[k], rn_mul(ce, curl));
+            if (st + 1 < S) {
+                e[k] = en;
+            } else {
+                const int row = r0 + k, j = y0 - S + row;
+                if (lane >= S && lane < S + TX && row >= S && row < S + TY && i < nx && j < ny) {
+                    const int64_t g = (int64_t)j * nx + i;
+                    ez_o[g] = en;
+                    hx_o[g] = sx[k];
+                    hy_o[g] = sy[k];
+                }
             }
+        }
+        if (st + 1 < S) {
+            xe[w][lane] = e[0];
+            __syncthreads();  // also: every warp has read xh above
+            e[4] = w + 1 < YW_W ? xe[w + 1][lane] : e[3];  // E of row r0 + 4 (row 36: outside)
         }
     }
 }
@@ -203,9 +183,12 @@ struct mfd_yee {
 namespace {
 
 constexpr int YEE_GRAPH_STEPS = 32;
+// steps per launch without sources and probes; YEE_GRAPH_STEPS / YEE_MULTI launches per graph
+// must be even (each launch swaps the buffers)
+constexpr int YEE_MULTI = 2;
+static_assert(YEE_GRAPH_STEPS % (2 * YEE_MULTI) == 0, "an even number of launches per graph");
 
-// two steps in one launch; only without sources and probes
-// one launch of k_yee with S steps (S = 2 only without sources and probes)
+// one launch of k_yee with S steps (S > 1 only without sources and probes)
 template <int S> cudaError_t yee_launch(mfd_yee* y) {
     cudaStream_t s = y->ctx->stream;
     const dim3 grid((unsigned)((y->nx + yee_tile_x<S>() - 1) / yee_tile_x<S>()),
@@ -234,10 +217,10 @@ template <int S> cudaError_t yee_launch(mfd_yee* y) {
     return cudaSuccess;
 }
 
-// two steps in one launch; only without sources and probes
-cudaError_t yee_enqueue2(mfd_yee* y) {
-    cudaError_t e = yee_launch<2>(y);
-    if (e == cudaSuccess) y->steps += 2;
+// YEE_MULTI steps in one launch; only without sources and probes
+cudaError_t yee_enqueue_multi(mfd_yee* y) {
+    cudaError_t e = yee_launch<YEE_MULTI>(y);
+    if (e == cudaSuccess) y->steps += YEE_MULTI;
     return e;
 }
 
@@ -282,7 +265,7 @@ mfd_status yee_graph(mfd_yee* y) {
     MFD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     if (y->nsrc == 0 && y->nprobe == 0)
-        for (int k = 0; k < YEE_GRAPH_STEPS && e == cudaSuccess; k += 2) e = yee_enqueue2(y);
+        for (int k = 0; k < YEE_GRAPH_STEPS && e == cudaSuccess; k += YEE_MULTI) e = yee_enqueue_multi(y);
     else
         for (int k = 0; k < YEE_GRAPH_STEPS && e == cudaSuccess; ++k) e = yee_enqueue(y);
     cudaGraph_t g = nullptr;
@@ -447,11 +430,11 @@ mfd_status mfd_yee_step(mfd_yee* y, int64_t nsteps) {
             left -= YEE_GRAPH_STEPS;
         }
     }
-    const bool two = y->nsrc == 0 && y->nprobe == 0;
+    const bool multi = y->nsrc == 0 && y->nprobe == 0;
     while (left > 0) {
-        if (two && left >= 2) {
-            MFD_CUDA(yee_enqueue2(y));
-            left -= 2;
+        if (multi && left >= YEE_MULTI) {
+            MFD_CUDA(yee_enqueue_multi(y));
+            left -= YEE_MULTI;
         } else {
             MFD_CUDA(yee_enqueue(y));
             --left;
@@ -460,7 +443,7 @@ mfd_status mfd_yee_step(mfd_yee* y, int64_t nsteps) {
     return MFD_OK;
 }
 
-int mfd_yee_steps_per_launch(const mfd_yee* y) { return y && y->nsrc == 0 && y->nprobe == 0 ? 2 : 1; }
+int mfd_yee_steps_per_launch(const mfd_yee* y) { return y && y->nsrc == 0 && y->nprobe == 0 ? YEE_MULTI : 1; }
 
 mfd_status mfd_yee_step_timed(mfd_yee* y, int64_t nsteps, double* ms) {
     if (!y || nsteps < 0 || !ms) return fail(MFD_ERR_ARG, "bad arguments");
@@ -469,10 +452,10 @@ mfd_status mfd_yee_step_timed(mfd_yee* y, int64_t nsteps, double* ms) {
     for (auto& e : y->ev)
         if (!e) MFD_CUDA(cudaEventCreate(&e));
     double tot = 0.0;
-    const bool two = y->nsrc == 0 && y->nprobe == 0;
-    for (int64_t k = 0; k < nsteps; k += (two && k + 1 < nsteps) ? 2 : 1) {
+    const bool multi = y->nsrc == 0 && y->nprobe == 0;
+    for (int64_t k = 0; k < nsteps; k += (multi && k + YEE_MULTI <= nsteps) ? YEE_MULTI : 1) {
         MFD_CUDA(cudaEventRecord(y->ev[0], s));
-        if (two && k + 1 < nsteps) MFD_CUDA(yee_enqueue2(y));
+        if (multi && k + YEE_MULTI <= nsteps) MFD_CUDA(yee_enqueue_multi(y));
         else MFD_CUDA(yee_enqueue(y));
         MFD_CUDA(cudaEventRecord(y->ev[1], s));
         MFD_CUDA(cudaEventSynchronize(y->ev[1]));
