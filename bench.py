@@ -757,7 +757,7 @@ def yee(M, ctx, peak, peak_kind, big=8192, steps=1000, nx=1000, pulse_steps=5000
     torch.cuda.synchronize()
     el = t0.elapsed_time(t1) / 1e3
     k = min(steps, 200)
-    spl = y.steps_per_launch  # 2: two steps fused per launch (no sources or probes here)
+    spl = y.steps_per_launch  # steps fused per launch (no sources or probes here)
     ms = y.step_timed(k) / k * spl  # per launch
     cells = big * big
     alg = 24.0 * cells  # Ez, Hx, Hy read and written once per launch

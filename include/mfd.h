@@ -379,9 +379,9 @@ mfd_status mfd_yee_set_probes(mfd_yee* y, int count, const int64_t* cell, int64_
 mfd_status mfd_yee_step(mfd_yee* y, int64_t nsteps);
 /* nsteps steps, each launch bracketed by CUDA events; *ms = the summed launch times. */
 mfd_status mfd_yee_step_timed(mfd_yee* y, int64_t nsteps, double* ms);
-/* Steps one kernel launch advances: 2 without sources and probes (two steps
- * fused in one launch, halving the DRAM traffic per step; results equal the
- * one-step kernel's bit for bit), else 1. */
+/* Steps one kernel launch advances: 4 without sources and probes (four steps
+ * fused in one launch, a quarter of the DRAM traffic per step; results equal
+ * the one-step kernel's bit for bit), else 1. */
 int mfd_yee_steps_per_launch(const mfd_yee* y);
 /* host: steps x count FP64; *steps receives the recorded steps. */
 mfd_status mfd_yee_read_probes(mfd_yee* y, double* host, int64_t* steps);
