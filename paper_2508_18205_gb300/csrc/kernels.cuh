@@ -140,6 +140,8 @@ template <typename T> struct AccPlain {
     T s = T(0);
     __device__ __forceinline__ void add(T w, T f) { s = fma(w, f, s); }
     __device__ __forceinline__ T get() const { return s; }
+    // adds the partial sum of the lane `off` lanes away (all lanes of the warp call it)
+    __device__ __forceinline__ void merge_xor(int off) { s += __shfl_xor_sync(0xffffffffu, s, off); }
 };
 // Compensated FP32 dot product (Ogita, Rump, Oishi, "Accurate sum and dot
 // product", SIAM J. Sci. Comput. 2005, Dot2): the exact product error comes
@@ -156,6 +158,16 @@ struct AccComp {
         c = __fadd_rn(c, __fadd_rn(r, e));
     }
     __device__ __forceinline__ float get() const { return __fadd_rn(s, c); }
+    // adds the compensated partial sum of the lane `off` lanes away: the two
+    // leading parts by Knuth's two-sum, the error terms added to c
+    __device__ __forceinline__ void merge_xor(int off) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, off), c2 = __shfl_xor_sync(0xffffffffu, c, off);
+        const float t = __fadd_rn(s, s2);
+        const float z = __fsub_rn(t, s);
+        const float r = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(s2, z));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(r, c2));
+    }
 };
 template <typename T, bool COMP> struct AccSel { using type = AccPlain<T>; };
 template <> struct AccSel<float, true> { using type = AccComp; };

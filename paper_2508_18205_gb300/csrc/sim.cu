@@ -400,6 +400,10 @@ Launch2D make2d(mfd_sim* sim, int parity) {
     L.kd.gamma = sim->d.gamma;
     L.block[0] = sim->block[0];
     L.block[1] = sim->block[1];
+    // collocated rows shared by both stencils: four lanes per node while one thread per node
+    // would occupy less than a quarter of the GPU's threads
+    if (!L.staggered && sim->hp.idx_v.p == nullptr && sim->ne * 4 <= (int64_t)sim->ctx->sm_count * 512)
+        L.lanes = 4;
     if (!L.staggered) {
         L.A = sim->s0.p;
         L.B = sim->s1.p;

@@ -17,9 +17,14 @@ namespace mfd {
 
 // ------------------------------------------------------------ collocated
 
-template <typename T, int NC, int NV, bool SHARED, bool COMP>
+// P lanes per node (P = 1, or 4 for problems too small to fill the GPU with one
+// thread per node): lane `part` of the node sums chunks part, part + P, ... of the
+// row (SHARED layout); the partial sums are merged across the node's lanes by the
+// caller (merge_xor), which every lane of the warp must reach.
+template <typename T, int NC, int NV, bool SHARED, bool COMP, int P = 1>
 __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const typename Vec<T>::V4* __restrict__ A,
-                                              int64_t i, T& dxE, T& dyE, T& vx, T& vy, T& ve) {
+                                              int64_t i, T& dxE, T& dyE, T& vx, T& vy, T& ve, bool act = true,
+                                              int part = 0) {
     using V4 = typename Vec<T>::V4;
     using Acc = typename AccSel<T, COMP>::type;  // curl sums (compensated when COMP)
     using AccV = AccPlain<T>;                    // hyperviscosity sums (scaled by gamma)
@@ -36,7 +41,7 @@ __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const 
         const V4* py = s.wy + slice * nc * 32 + lane;
         const V4* pv = s.wv + slice * nv * 32 + lane;
 #pragma unroll
-        for (int c = 0; c < ni; ++c) {
+        for (int c = part; c < (act ? ni : 0); c += P) {
             const int4 id = ld_stream(ip + c * 32);
             V4 wx, wy, wv;
             if (c < nc) {
@@ -63,7 +68,7 @@ __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const 
         const V4* py = s.wy + slice * nc * 32 + lane;
         const V4* pv = s.wv + slice * nv * 32 + lane;
 #pragma unroll
-        for (int c = 0; c < nc; ++c) {
+        for (int c = part; c < (act ? nc : 0); c += P) {
             const int4 id = ld_stream(ic + c * 32);
             const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32);
             const T f0 = ld_gather(A + id.x).x, f1 = ld_gather(A + id.y).x;
@@ -72,7 +77,7 @@ __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const 
             ay.add(wy.x, f0); ay.add(wy.y, f1); ay.add(wy.z, f2); ay.add(wy.w, f3);
         }
 #pragma unroll
-        for (int c = 0; c < nv; ++c) {
+        for (int c = part; c < (act ? nv : 0); c += P) {
             const int4 id = ld_stream(iv + c * 32);
             const V4 wv = ld_stream(pv + c * 32);
             const V4 f0 = ld_gather(A + id.x), f1 = ld_gather(A + id.y);
@@ -82,6 +87,14 @@ __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const 
             he.add(wv.x, f0.x); he.add(wv.y, f1.x); he.add(wv.z, f2.x); he.add(wv.w, f3.x);
         }
     }
+#pragma unroll
+    for (int off = 1; off < P; off <<= 1) {
+        ax.merge_xor(off);
+        ay.merge_xor(off);
+        hx.merge_xor(off);
+        hy.merge_xor(off);
+        he.merge_xor(off);
+    }
     dxE = ax.get();
     dyE = ay.get();
     vx = hx.get();
@@ -89,15 +102,18 @@ __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const 
     ve = he.get();
 }
 
-template <typename T, int NC, int NV, bool SHARED, bool COMP>
+template <typename T, int NC, int NV, bool SHARED, bool COMP, int P>
 __global__ void __launch_bounds__(512) k_h_colloc(StencilStreams<T> s, Coefs<T> k,
                                                   const typename Vec<T>::V4* __restrict__ A,
                                                   typename Vec<T>::V4* __restrict__ B) {
     using V4 = typename Vec<T>::V4;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= s.n) return;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = t / P;
+    const int part = (int)(t % P);
+    if (P == 1 && i >= s.n) return;  // with P > 1 every lane takes part in the merges
     T dxE, dyE, vx, vy, ve;
-    h_colloc_node<T, NC, NV, SHARED, COMP>(s, A, i, dxE, dyE, vx, vy, ve);
+    h_colloc_node<T, NC, NV, SHARED, COMP, P>(s, A, i, dxE, dyE, vx, vy, ve, i < s.n, part);
+    if (i >= s.n || part != 0) return;
     const V4 me = ld_gather(A + i);
     V4 out;
     out.x = me.x + me.w * (k.gamma * ve);
@@ -107,13 +123,16 @@ __global__ void __launch_bounds__(512) k_h_colloc(StencilStreams<T> s, Coefs<T> 
     st4(B + i, out);
 }
 
-template <typename T, int NC, bool SHARED, bool COMP>
+template <typename T, int NC, bool SHARED, bool COMP, int P>
 __global__ void __launch_bounds__(512) k_e_colloc(StencilStreams<T> s, const typename Vec<T>::V4* __restrict__ B,
                                                   typename Vec<T>::V4* __restrict__ A) {
     using V4 = typename Vec<T>::V4;
     using Acc = typename AccSel<T, COMP>::type;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= s.n) return;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = t / P;
+    const int part = (int)(t % P);
+    if (P == 1 && i >= s.n) return;  // with P > 1 every lane takes part in the merges
+    const bool act = i < s.n;
     const int nc = NC ? NC : s.nc;
     const int ni = SHARED ? s.ni : nc;
     const int64_t slice = i >> 5;
@@ -123,7 +142,7 @@ __global__ void __launch_bounds__(512) k_e_colloc(StencilStreams<T> s, const typ
     const V4* py = s.wy + slice * nc * 32 + lane;
     Acc dxHy, dyHx;
 #pragma unroll
-    for (int c = 0; c < nc; ++c) {
+    for (int c = part; c < (act ? nc : 0); c += P) {
         const int4 id = ld_stream(ip + c * 32);
         const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32);
         const V4 f0 = ld_gather(B + id.x), f1 = ld_gather(B + id.y);
@@ -131,6 +150,12 @@ __global__ void __launch_bounds__(512) k_e_colloc(StencilStreams<T> s, const typ
         dxHy.add(wx.x, f0.z); dxHy.add(wx.y, f1.z); dxHy.add(wx.z, f2.z); dxHy.add(wx.w, f3.z);
         dyHx.add(wy.x, f0.y); dyHx.add(wy.y, f1.y); dyHx.add(wy.z, f2.y); dyHx.add(wy.w, f3.y);
     }
+#pragma unroll
+    for (int off = 1; off < P; off <<= 1) {
+        dxHy.merge_xor(off);
+        dyHx.merge_xor(off);
+    }
+    if (!act || part != 0) return;
     const V4 me = ld_gather(B + i);
     V4 out;
     out.x = me.x + me.w * (dxHy.get() - dyHx.get());
@@ -294,38 +319,46 @@ __global__ void __launch_bounds__(256) k_energy_stag(StencilStreams<T> s, Coefs<
 
 // ------------------------------------------------------------ dispatch
 
-template <typename T, bool COMP>
-static cudaError_t launch_colloc_pass(int pass, const StencilStreams<T>& s, const Coefs<T>& k, void* A, void* B,
-                                      int block, cudaStream_t st) {
+template <typename T, bool COMP, int P>
+static cudaError_t launch_colloc_pass_p(int pass, const StencilStreams<T>& s, const Coefs<T>& k, void* A, void* B,
+                                        int block, cudaStream_t st) {
     using V4 = typename Vec<T>::V4;
     const bool shared = s.idx_v == s.idx_c;
-    const unsigned grid = (unsigned)((s.n + block - 1) / block);
+    const unsigned grid = (unsigned)((s.n * P + block - 1) / block);
     V4* a = static_cast<V4*>(A);
     V4* b = static_cast<V4*>(B);
-#define MFD_H(NC, NV)                                                                    \
-    if (s.nc == NC && s.nv == NV) {                                                      \
-        if (shared) k_h_colloc<T, NC, NV, true, COMP><<<grid, block, 0, st>>>(s, k, a, b); \
-        else k_h_colloc<T, NC, NV, false, COMP><<<grid, block, 0, st>>>(s, k, a, b);       \
-        return cudaGetLastError();                                                       \
+#define MFD_H(NC, NV)                                                                       \
+    if (s.nc == NC && s.nv == NV) {                                                         \
+        if (shared) k_h_colloc<T, NC, NV, true, COMP, P><<<grid, block, 0, st>>>(s, k, a, b); \
+        else k_h_colloc<T, NC, NV, false, COMP, P><<<grid, block, 0, st>>>(s, k, a, b);       \
+        return cudaGetLastError();                                                          \
     }
-#define MFD_E(NC)                                                                     \
-    if (s.nc == NC) {                                                                 \
-        if (shared) k_e_colloc<T, NC, true, COMP><<<grid, block, 0, st>>>(s, b, a);     \
-        else k_e_colloc<T, NC, false, COMP><<<grid, block, 0, st>>>(s, b, a);           \
-        return cudaGetLastError();                                                    \
+#define MFD_E(NC)                                                                        \
+    if (s.nc == NC) {                                                                    \
+        if (shared) k_e_colloc<T, NC, true, COMP, P><<<grid, block, 0, st>>>(s, b, a);     \
+        else k_e_colloc<T, NC, false, COMP, P><<<grid, block, 0, st>>>(s, b, a);           \
+        return cudaGetLastError();                                                       \
     }
     if (pass == 0) {
         MFD_H(3, 8) MFD_H(5, 8) MFD_H(8, 8) MFD_H(10, 8)
-        if (shared) k_h_colloc<T, 0, 0, true, COMP><<<grid, block, 0, st>>>(s, k, a, b);
-        else k_h_colloc<T, 0, 0, false, COMP><<<grid, block, 0, st>>>(s, k, a, b);
+        if (shared) k_h_colloc<T, 0, 0, true, COMP, P><<<grid, block, 0, st>>>(s, k, a, b);
+        else k_h_colloc<T, 0, 0, false, COMP, P><<<grid, block, 0, st>>>(s, k, a, b);
     } else {
         MFD_E(3) MFD_E(5) MFD_E(8) MFD_E(10)
-        if (shared) k_e_colloc<T, 0, true, COMP><<<grid, block, 0, st>>>(s, b, a);
-        else k_e_colloc<T, 0, false, COMP><<<grid, block, 0, st>>>(s, b, a);
+        if (shared) k_e_colloc<T, 0, true, COMP, P><<<grid, block, 0, st>>>(s, b, a);
+        else k_e_colloc<T, 0, false, COMP, P><<<grid, block, 0, st>>>(s, b, a);
     }
 #undef MFD_H
 #undef MFD_E
     return cudaGetLastError();
+}
+
+// lanes per node: 4 when one thread per node would leave SMs idle
+template <typename T, bool COMP>
+static cudaError_t launch_colloc_pass(int pass, const StencilStreams<T>& s, const Coefs<T>& k, void* A, void* B,
+                                      int block, cudaStream_t st, int lanes) {
+    if (lanes == 4) return launch_colloc_pass_p<T, COMP, 4>(pass, s, k, A, B, block, st);
+    return launch_colloc_pass_p<T, COMP, 1>(pass, s, k, A, B, block, st);
 }
 
 template <typename T, bool COMP>
@@ -357,9 +390,9 @@ cudaError_t launch_2d(const Launch2D& L, int pass, cudaStream_t st) {
         if (L.comp) return launch_stag_pass<float, true>(pass, pass == 0 ? L.hs.f : L.es.f, L.kf, L.stag, b, st);
         return launch_stag_pass<float, false>(pass, pass == 0 ? L.hs.f : L.es.f, L.kf, L.stag, b, st);
     }
-    if (L.fp64) return launch_colloc_pass<double, false>(pass, L.hs.d, L.kd, L.A, L.B, b, st);
-    if (L.comp) return launch_colloc_pass<float, true>(pass, L.hs.f, L.kf, L.A, L.B, b, st);
-    return launch_colloc_pass<float, false>(pass, L.hs.f, L.kf, L.A, L.B, b, st);
+    if (L.fp64) return launch_colloc_pass<double, false>(pass, L.hs.d, L.kd, L.A, L.B, b, st, L.lanes);
+    if (L.comp) return launch_colloc_pass<float, true>(pass, L.hs.f, L.kf, L.A, L.B, b, st, L.lanes);
+    return launch_colloc_pass<float, false>(pass, L.hs.f, L.kf, L.A, L.B, b, st, L.lanes);
 }
 
 cudaError_t launch_energy_2d(const Launch2D& L, const double* eps_r, int64_t ne, double eta2, double* partial,
