@@ -353,12 +353,13 @@ static cudaError_t launch_colloc_pass_p(int pass, const StencilStreams<T>& s, co
     return cudaGetLastError();
 }
 
-// lanes per node: 4 or 8 when one thread per node would leave SMs idle
+// lanes per node: 2, 4 or 8 when one thread per node would leave SMs idle
 template <typename T, bool COMP>
 static cudaError_t launch_colloc_pass(int pass, const StencilStreams<T>& s, const Coefs<T>& k, void* A, void* B,
                                       int block, cudaStream_t st, int lanes) {
     if (lanes == 8) return launch_colloc_pass_p<T, COMP, 8>(pass, s, k, A, B, block, st);
     if (lanes == 4) return launch_colloc_pass_p<T, COMP, 4>(pass, s, k, A, B, block, st);
+    if (lanes == 2) return launch_colloc_pass_p<T, COMP, 2>(pass, s, k, A, B, block, st);
     return launch_colloc_pass_p<T, COMP, 1>(pass, s, k, A, B, block, st);
 }
 
