@@ -428,3 +428,49 @@ def test_staggered_q16_indices_with_two_windows_and_wide_slices(ctx, prec, comp,
     prob = O.tmz_staggered(e, h, n, 5, 4, alpha, dt, eps0, mu0, c)
     re, rx, ry, _, _ = O.run_tmz(prob, *f, 20)
     assert _rel_all(runs[0], [re, rx, ry]) <= tol
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("prec,tol", [(1, 1e-10), (0, 1e-5)])
+def test_collocated_with_separate_stencil_objects(ctx, dim, prec, tol):
+    """Collocated curl and HV weights built on two stencils objects (the kernels
+    then read two index streams, with the small-set split over four lanes per
+    node in 2D): the same stencils as the shared row the oracle builds, so the
+    same fields within the tolerance."""
+    import math as _m
+    S, c = 0.5, (4e-3 if dim == 2 else 1e-3)
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    if dim == 2:
+        nodes = W.pec_box((23, 19), 0.25, 51)
+        n, k, m, alpha, steps = 12, 3, 2, 2, 60
+    else:
+        nodes = W.periodic_box((10, 10, 10), 0.25, 52)
+        n, k, m, alpha, steps = 40, 3, 3, 2, 20
+    nhv = 2 * _m.comb(2 * alpha + dim, dim) + 1
+    nd = M.Nodes(ctx, nodes.xyz, nodes.period)
+    curl = M.Weights(M.Stencils(nd, nd, n), n, k, m, M.MFD_OP_GRAD)
+    hv = M.Weights(M.Stencils(nd, nd, nhv), nhv, 2 * alpha + 1, 2 * alpha, M.MFD_OP_LAP_POW, alpha)
+    sim = M.Sim(ctx, dim, prec, dt, eps0, mu0, -c, curl, hv, compensated=prec == 0)
+    rng = np.random.default_rng(53)
+    f = [rng.standard_normal(nodes.n) for _ in range(3 if dim == 2 else 6)]
+    if dim == 2:
+        sim.set_materials(None, nodes.pec)
+        f[0][nodes.pec == 1] = 0
+        comps = (M.MFD_EZ, M.MFD_HX, M.MFD_HY)
+    else:
+        comps = tuple(range(6))
+    if prec == 0:
+        f = [a.astype(np.float32).astype(np.float64) for a in f]
+    for cc, v in zip(comps, f):
+        sim.set_field(cc, v)
+    sim.step(steps)
+    got = [sim.get_field(cc) for cc in comps]
+    if dim == 2:
+        prob, _ = O.tmz_collocated(nodes, n, k, m, alpha, dt, eps0, mu0, -c)
+        ref = list(O.run_tmz(prob, *f, steps)[:3])
+    else:
+        prob, _ = O.max3d_collocated(nodes, n, k, m, alpha, dt, eps0, mu0, -c)
+        prob.wall[:] = 0
+        RE, RH, _, _ = O.run_3d(prob, np.array(f[:3]), np.array(f[3:]), steps)
+        ref = list(RE) + list(RH)
+    assert _rel_all(got, ref) <= tol
