@@ -389,8 +389,11 @@ def main():
             "event_timed_ms_per_step": (ms[0] + ms[1]) / a.steps,
             "index_i32": {"ms_per_step": i32_ms, "steps": k32,
                           "value": per_step_updates / (i32_ms / 1e3) * world}}
+    # the single-GPU sections (FP64 step, accuracy, the other workloads, the CPU baseline) run
+    # at N = 1 only: with replicas they would hold every GPU while rank 0 alone works
+    solo = world == 1
     # the plain FP64 GPU step on the same GPU, and FP32 accuracy against it
-    if rank == 0 and not a.no_fp64 and prec == M.MFD_FP32:
+    if solo and not a.no_fp64 and prec == M.MFD_FP32:
         k64 = min(a.steps, 1000)
         s64 = make_sim(M, ctx, wts, M.MFD_FP64, False)
         reset(s64, 8)
@@ -423,13 +426,13 @@ def main():
         del s64
         if a.accuracy_steps:
             line["accuracy"] = accuracy(M, ctx, wts, a.accuracy_steps, reset)
-    if rank == 0 and not a.no_extra:
+    if solo and not a.no_extra:
         line["dispersion"] = dispersion(M, ctx, wts, e, reset, comp)
-    if rank == 0 and a.batched_steps:
+    if solo and a.batched_steps:
         line["batched"] = batched(M, ctx, a.batched_steps, peak, peak_kind)
-    if rank == 0 and a.cube_steps:
+    if solo and a.cube_steps:
         line["cube3d"] = cube3d(M, ctx, a.cube_steps, peak, peak_kind)
-    if rank == 0 and not a.no_extra:
+    if solo and not a.no_extra:
         line["cavity_fp64"] = cavity(M, ctx)
         line["adjoint"] = adjoint(M, ctx)
         line["hv_search"] = hv_search(M, ctx)
@@ -458,7 +461,7 @@ def main():
         line["e2e"] = {"value": per_step_updates * a.steps / el * world, "unit": UNIT,
                        "h2d_bytes_per_step": h2d / a.steps, "d2h_bytes_per_step": d2h / a.steps,
                        "wall_s": el}
-    if rank == 0 and not a.no_cpu:
+    if solo and not a.no_cpu:
         try:
             line["cpu_baseline"] = cpu_baseline()
         except Exception as ex:  # the oracle is test infrastructure; report why it is missing
