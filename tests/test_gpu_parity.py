@@ -434,9 +434,8 @@ def test_staggered_q16_indices_with_two_windows_and_wide_slices(ctx, prec, comp,
 @pytest.mark.parametrize("prec,tol", [(1, 1e-10), (0, 1e-5)])
 def test_collocated_with_separate_stencil_objects(ctx, dim, prec, tol):
     """Collocated curl and HV weights built on two stencils objects (the kernels
-    then read two index streams, with the small-set split over four lanes per
-    node in 2D): the same stencils as the shared row the oracle builds, so the
-    same fields within the tolerance."""
+    then read two index streams, one thread per node): the same stencils as the
+    shared row the oracle builds, so the same fields within the tolerance."""
     import math as _m
     S, c = 0.5, (4e-3 if dim == 2 else 1e-3)
     dt, eps0, mu0, c0, eta0 = W.units(S)
