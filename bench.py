@@ -234,7 +234,35 @@ def cpu_baseline(budget_s=20.0):
     updates = (e.n + 2 * h.n) * steps
     return {"value": updates / el, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
             "sample": f"{nx}x{nx}+{nx}x{nx} staggered periodic sub-square, same stencils, {steps} steps "
-                      f"in {el:.1f} s (FP64)"}
+                      f"in {el:.1f} s (FP64)",
+            "cavity_fp64": cavity_cpu(O)}
+
+
+def cavity_cpu(O, steps=1000):
+    """The oracle on the whole FP64 cavity workload of cavity() (100 x 100 PEC
+    square, n = 12, Delta^2 HV, TM11 mode, 1000 steps), on all host cores and
+    on one thread, with its relative L2 error against the exact mode."""
+    S, c = 0.5, 4e-3
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    nodes = W.pec_box((100, 100), 0.25, 1)
+    prob, _ = O.tmz_collocated(nodes, 12, 3, 2, 2, dt, eps0, mu0, -c)
+    ez, hx, hy = W.tm11_fields(nodes.xyz, 99.0, c0, mu0, 0.0, -0.5 * dt)
+    ez[nodes.pec == 1] = 0
+    cores = O.threads()
+    out = {"workload": "cavity TM11, 100x100 PEC, n=12, FP64, 1000 steps"}
+    for key, th in (("all_cores", cores), ("one_thread", 1)):
+        O.threads(th)
+        t = time.perf_counter()
+        res = O.run_tmz(prob, ez, hx, hy, steps)
+        el = time.perf_counter() - t
+        out[key] = {"value": nodes.n * 3 * steps / el, "unit": UNIT, "cores": th,
+                    "ms_per_step": el / steps * 1e3}
+    O.threads(cores)
+    T = steps * dt
+    ea, xa, ya = W.tm11_fields(nodes.xyz, 99.0, c0, mu0, T, T - 0.5 * dt)
+    got, ref = np.concatenate(res[:3]), np.concatenate([ea, xa, ya])
+    out["rel_l2_vs_exact_mode"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    return out
 
 
 def run_reference(a, rank, world):

@@ -70,10 +70,10 @@ def _check(st, what):
         raise RuntimeError(f"oracle {what} failed with status {st}")
 
 
-def threads() -> int:
-    """OpenMP threads the oracle uses (OMP_NUM_THREADS, else all cores)."""
-    v = os.environ.get("OMP_NUM_THREADS")
-    return int(v) if v else (os.cpu_count() or 1)
+def threads(n: int = 0) -> int:
+    """OpenMP threads of the oracle's parallel loops (OMP_NUM_THREADS, else all
+    cores); n > 0 sets the count for the calls that follow."""
+    return int(lib().orc_threads(int(n)))
 
 
 # ------------------------------------------------------------------ O-1

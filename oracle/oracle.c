@@ -29,6 +29,7 @@
  * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -454,6 +455,14 @@ int orc_weights(int dim, int64_t nc, const double* xc, const double* xs, const d
         free(wl);
     }
     return status;
+}
+
+/* OpenMP threads of the parallel loops below: n > 0 sets the count for the
+   calls that follow; returns the count in force. */
+int orc_threads(int n)
+{
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
 }
 
 /* ------------------------------------------------------------------ O-3 */

@@ -361,3 +361,25 @@ def test_3d_sampled_step_equals_full_step():
     E1, H1, hs = O.max3d_sample_step(nodes, ids, 40, 3, 3, 2, dt, eps0, mu0, -1e-3, E, H, eps_r=er)
     assert np.allclose(E1, E1f[:, ids], rtol=0, atol=1e-12)
     assert np.allclose(H1, H1f[:, hs], rtol=0, atol=1e-12)
+
+
+def test_step_does_not_depend_on_the_thread_count():
+    """Every node's stencil sums run in stencil order on one thread, so the
+    oracle's steps (timed on all host cores and on one thread) give the same
+    bits whatever the OpenMP thread count."""
+    dt, eps0, mu0, c0, eta0 = _units(0.5)
+    nodes = W.pec_box((24, 24), 0.25, 1)
+    prob, _ = O.tmz_collocated(nodes, 12, 3, 2, 2, dt, eps0, mu0, -4e-3)
+    ez, hx, hy = W.tm11_fields(nodes.xyz, 23.0, c0, mu0, 0.0, -0.5 * dt)
+    ez[nodes.pec == 1] = 0
+    cores = O.threads()
+    try:
+        O.threads(1)
+        assert O.threads() == 1
+        one = O.run_tmz(prob, ez, hx, hy, 50)
+        O.threads(max(cores, 2))
+        many = O.run_tmz(prob, ez, hx, hy, 50)
+    finally:
+        O.threads(cores)
+    for a, b in zip(one[:3], many[:3]):
+        assert np.array_equal(a, b)
