@@ -118,8 +118,11 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
     ve[2] = ez.get();
 }
 
+// The H pass may take up to 128 registers: at 256 threads per block the
+// compensated FP32 kernel runs 2 blocks per SM with 32 bytes of spills; caps
+// of 80 (3 blocks) and 64 registers (4 blocks) spilled more and were slower.
 template <typename T, int NC, int NV, bool SHARED, bool COMP>
-__global__ void __launch_bounds__(512, 2) k_h3(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V4* __restrict__ F,
+__global__ void __launch_bounds__(512, 1) k_h3(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V4* __restrict__ F,
                                             typename Vec<T>::V4* __restrict__ Es,
                                             typename Vec<T>::V4* __restrict__ Hn) {
     using V4 = typename Vec<T>::V4;
