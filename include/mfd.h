@@ -362,10 +362,12 @@ mfd_status mfd_fma_peak(int device, double* fp64_gflops, double* fp32_gflops);
  * (i h, (j + 1/2) h) and Hy[j][i] at ((i + 1/2) h, j h), both at (n - 1/2) dt.
  * A step is Eq. 5 with S_c / eta0 = dt / (mu0 h) and eta0 S_c = dt / (eps0 h)
  * (stable for S_c <= 1/sqrt(2)), then soft Ricker sources (as mfd_set_sources,
- * cell index j nx + i), then probes. One fused kernel per step (two steps per
- * launch when there are no sources and probes); long runs replay a CUDA graph. FP64 results equal the reference arithmetic of Eq. 5
- * taken term by term (no fused multiply-add) bit for bit.
- * 2 <= nx < 2^30, 2 <= ny <= 2097120; fields in host arrays are ny x nx FP64. */
+ * cell index j nx + i), then probes. One fused kernel per step (four steps per
+ * launch when there are no sources and probes); long runs replay a CUDA graph.
+ * FP64 results equal the reference arithmetic of Eq. 5 taken term by term (no
+ * fused multiply-add) bit for bit.
+ * 2 <= nx < 2^30, 2 <= ny <= 1834980 (65535 rows of blocks of the four-step kernel's
+ * 28-row tiles); fields in host arrays are ny x nx FP64. */
 typedef struct mfd_yee mfd_yee;
 mfd_status mfd_yee_create(mfd_ctx* ctx, int64_t nx, int64_t ny, int precision, double dt, double h, double eps0,
                           double mu0, mfd_yee** out);

@@ -36,21 +36,21 @@ template <bool BIG> __device__ __forceinline__ int wrap(int v, int n) {
 
 // The step kernel, S steps per launch (S > 1, temporal blocking, for runs
 // without sources or probes, whose terms sit between the steps). A block holds
-// a 32-column by 36-row window of the grid in registers: lane c of warp w holds
-// column x0 - S + c of rows y0 - S + 4w .. y0 - S + 3 + 4w (nine warps, 36 rows;
+// a 32-column by 4 YW_W-row window of the grid in registers: lane c of warp w
+// holds column x0 - S + c of rows y0 - S + 4w .. y0 - S + 3 + 4w (YW_W warps;
 // S = the steps per launch), Ez and the old Hx, Hy of each. It computes
 // H^{n+1/2} and E^{n+1}, then the next half steps up to E^{n+S}: neighbours
 // along x come from the adjacent lane by a shuffle, neighbours along y from the
 // thread's own registers or, across warps, through one shared row per warp and
 // half step. The valid region shrinks by a cell per half step on the sides the
-// stencil reads, leaving a (32 - 2S) x (36 - 2S) tile (window columns and rows
+// stencil reads, leaving a (32 - 2S) x (4 YW_W - 2S) tile (window columns and rows
 // S .. end - S), written once: 6 reals of DRAM traffic per cell and launch.
 // Arithmetic follows Eq. 5 term by term with round-to-nearest operations (no
 // contraction), in the oracle's order, so FP64 results are reproducible bit for
 // bit and do not depend on the steps per launch.
 constexpr int YW_W = 9;  // warps; four window rows each
 template <int S> constexpr int yee_tile_x() { return 32 - 2 * S; }
-template <int S> constexpr int yee_tile_y() { return 36 - 2 * S; }
+template <int S> constexpr int yee_tile_y() { return 4 * YW_W - 2 * S; }
 
 template <typename T, bool BIG, int S>
 __global__ void __launch_bounds__(32 * YW_W) k_yee(int nx, int ny, T ch, T ce, const T* __restrict__ ez,
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(32 * YW_W) k_yee(int nx, int ny, T ch, T ce, c
         if (st + 1 < S) {
             xe[w][lane] = e[0];
             __syncthreads();  // also: every warp has read xh above
-            e[4] = w + 1 < YW_W ? xe[w + 1][lane] : e[3];  // E of row r0 + 4 (row 36: outside)
+            e[4] = w + 1 < YW_W ? xe[w + 1][lane] : e[3];  // E of row r0 + 4 (row 4 YW_W: outside)
         }
     }
 }
@@ -195,9 +195,9 @@ template <int S> cudaError_t yee_launch(mfd_yee* y) {
                     (unsigned)((y->ny + yee_tile_y<S>() - 1) / yee_tile_y<S>()));
     const dim3 block(32, YW_W);
     const int a = y->cur, b = y->cur ^ 1;
-    // one compare per wrap while the window (columns x0-S .. x0-S+31, rows y0-S .. y0-S+36)
+    // one compare per wrap while the window (columns x0-S .. x0-S+31, rows y0-S .. y0-S+4 YW_W)
     // stays within one period of the grid on either side
-    const bool big = y->nx >= 32 && y->ny >= 37;
+    const bool big = y->nx >= 32 && y->ny >= 4 * YW_W + 1;
     const int nx = (int)y->nx, ny = (int)y->ny;
     if (y->fp64) {
         const double *e = y->f[a][0].as<double>(), *hx = y->f[a][1].as<double>(), *hy = y->f[a][2].as<double>();
@@ -300,8 +300,9 @@ mfd_status mfd_yee_create(mfd_ctx* ctx, int64_t nx, int64_t ny, int precision, d
                           double mu0, mfd_yee** out) {
     if (!ctx || !out) return fail(MFD_ERR_ARG, "mfd_yee_create: NULL argument");
     *out = nullptr;
-    if (nx < 2 || ny < 2 || nx > INT32_MAX / 2 || ny > 65535LL * yee_tile_y<2>())
-        return fail(MFD_ERR_ARG, "mfd_yee_create: need 2 <= nx < 2^30 and 2 <= ny <= 2097120");
+    if (nx < 2 || ny < 2 || nx > INT32_MAX / 2 || ny > 65535LL * yee_tile_y<4>())
+        return fail(MFD_ERR_ARG, "mfd_yee_create: need 2 <= nx < 2^30 and 2 <= ny <= " +
+                                     std::to_string(65535LL * yee_tile_y<4>()));
     if (!(dt > 0) || !(h > 0) || !(eps0 > 0) || !(mu0 > 0)) return fail(MFD_ERR_ARG, "dt, h, eps0, mu0 must be > 0");
     if (precision != MFD_FP32 && precision != MFD_FP64) return fail(MFD_ERR_ARG, "precision");
     MFD_CUDA(cudaSetDevice(ctx->device));

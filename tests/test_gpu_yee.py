@@ -102,3 +102,19 @@ def test_yee_dispersion_follows_eq6():
     assert abs(kidx[j0] - nx / lam) <= 1
     c_eq6 = D.fdtd_phase_speed(2 * math.pi * j0 / (nt * stride), S, 0.0)
     assert abs(c[j0] - c_eq6) <= c_eq6 / (nx / lam - 1)
+
+
+def test_yee_tallest_grid_and_the_bound():
+    """The tallest grid mfd_yee_create accepts (65535 rows of blocks of the
+    four-step kernel's 28-row tiles, here two columns wide) steps bit for bit
+    with the oracle through four-step launches; one row more is refused."""
+    ctx = M.Ctx(0)
+    nx, ny = 2, 65535 * 28
+    f = _fields(nx, ny, 11)
+    y, dt, eps0, mu0 = _yee(ctx, nx, ny, M.MFD_FP64, 0.5, f)
+    y.step(8)
+    ref = O.run_yee(nx, ny, dt / mu0, dt / eps0, dt, *f, 8)
+    for comp, r in zip((M.MFD_EZ, M.MFD_HX, M.MFD_HY), ref[:3]):
+        assert np.array_equal(y.get_field(comp), r), comp
+    with pytest.raises(M.MfdError):
+        M.Yee(ctx, nx, ny + 1, M.MFD_FP64, dt, 1.0, eps0, mu0)
