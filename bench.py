@@ -250,14 +250,16 @@ def cavity_cpu(O, steps=1000):
     ez[nodes.pec == 1] = 0
     cores = O.threads()
     out = {"workload": "cavity TM11, 100x100 PEC, n=12, FP64, 1000 steps"}
-    for key, th in (("all_cores", cores), ("one_thread", 1)):
-        O.threads(th)
-        t = time.perf_counter()
-        res = O.run_tmz(prob, ez, hx, hy, steps)
-        el = time.perf_counter() - t
-        out[key] = {"value": nodes.n * 3 * steps / el, "unit": UNIT, "cores": th,
-                    "ms_per_step": el / steps * 1e3}
-    O.threads(cores)
+    try:
+        for key, th in (("all_cores", cores), ("one_thread", 1)):
+            O.threads(th)
+            t = time.perf_counter()
+            res = O.run_tmz(prob, ez, hx, hy, steps)
+            el = time.perf_counter() - t
+            out[key] = {"value": nodes.n * 3 * steps / el, "unit": UNIT, "cores": th,
+                        "ms_per_step": el / steps * 1e3}
+    finally:
+        O.threads(cores)
     T = steps * dt
     ea, xa, ya = W.tm11_fields(nodes.xyz, 99.0, c0, mu0, T, T - 0.5 * dt)
     got, ref = np.concatenate(res[:3]), np.concatenate([ea, xa, ya])
