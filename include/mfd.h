@@ -73,6 +73,16 @@ typedef struct mfd_sim mfd_sim;
 const char* mfd_last_error(void);
 int mfd_version(void);
 
+/* Fault injection for tests of the error paths (the paper has no
+ * counterpart): the next `after` device allocations of the library succeed
+ * and the one after them fails with MFD_ERR_OOM without calling cudaMalloc;
+ * after < 0 turns it off. Process-wide; it fires once. Every object whose
+ * creation failed this way has been freed, and objects created before stay
+ * valid. Host only. */
+mfd_status mfd_debug_fail_alloc(int64_t after);
+/* Allocations left before the injected failure fires; -1 when none is pending. */
+int64_t mfd_debug_alloc_pending(void);
+
 /* ------------------------------------------------------------- context */
 
 /* Binds the library to CUDA device `device`. stream: a cudaStream_t to
@@ -263,6 +273,23 @@ mfd_status mfd_sim_index_stats(const mfd_sim* sim, int64_t* out);
 mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, double* g_eps, double* g_amp);
 /* Number of steps taken since the last mfd_set_field(MFD_EZ). */
 int64_t mfd_sim_steps(const mfd_sim* sim);
+/* Checkpoint / resume of a long run (the paper has no counterpart). The state
+ * is what the next step reads, as it sits on the device (bit for bit, in the
+ * library's internal node order): E at t_n and H at t_n - dt/2 with the
+ * layout's ping-pong buffers (in the collocated 2D layout the per-node E
+ * coefficient dt / (eps0 eps_r) sits beside the fields and travels with
+ * them), the step index n, and the probe records since mfd_set_probes.
+ * Weights, materials, sources and the probe nodes are configuration, not
+ * state: load into a simulation built the same way (same weights, layout,
+ * precision, materials and sources; the same probes with at least the saved
+ * records' capacity), and the run continued from the loaded state is
+ * bit-identical to the unbroken run. host is a caller buffer (save: at least
+ * mfd_sim_state_size bytes; load: `bytes` bytes of a saved state). A blob whose
+ * header does not match (kind, version, layout, precision, node counts, buffer
+ * sizes, probes) is MFD_ERR_ARG before anything is changed. */
+mfd_status mfd_sim_state_size(const mfd_sim* sim, size_t* bytes);
+mfd_status mfd_sim_save_state(mfd_sim* sim, void* host, size_t bytes);
+mfd_status mfd_sim_load_state(mfd_sim* sim, const void* host, size_t bytes);
 void mfd_sim_destroy(mfd_sim* sim);
 
 
@@ -300,7 +327,19 @@ mfd_status mfd_batch_set_sources(mfd_batch* b, int dom, int count, const int64_t
 /* Probes of domain dom: Ez of every right-hand side after each step, for at
  * most `capacity` steps (the batch keeps the largest capacity asked). */
 mfd_status mfd_batch_set_probes(mfd_batch* b, int dom, int count, const int64_t* node, int64_t capacity);
+/* Advances every domain and right-hand side nsteps steps. A grid barrier
+ * that waits longer than the spin limit (mfd_batch_set_spin_limit) makes every
+ * block leave the kernel: the call returns MFD_ERR_TIMEOUT, the step counter
+ * is not advanced and the fields are left part way through the call (set
+ * them again before stepping on); the batch stays usable. */
 mfd_status mfd_batch_step(mfd_batch* b, int64_t nsteps);
+/* Bound of the grid-barrier waits of the batched kernel (failure detection:
+ * a persistent kernel never waits without limit on a shared GPU). A waiting
+ * block polls the barrier at most `limit` times, napping 64 ns between polls,
+ * then raises the error flag that makes every block leave. Default 2^25 (a
+ * few seconds). limit = 0 makes any block that has to wait give up at its
+ * first poll, which exercises the timeout path. */
+mfd_status mfd_batch_set_spin_limit(mfd_batch* b, uint64_t limit);
 /* host: steps x count x nrhs FP64; *steps receives the recorded steps. */
 mfd_status mfd_batch_read_probes(mfd_batch* b, int dom, double* host, int64_t* steps);
 int64_t mfd_batch_nodes(const mfd_batch* b);
@@ -316,6 +355,13 @@ mfd_status mfd_batch_set_gamma(mfd_batch* b, int dom, const double* gamma);
  * averaged between t - dt/2 and t + dt/2 (the next H half step is computed,
  * not applied), eta0^2 = mu0 / eps0, as mfd_energy. */
 mfd_status mfd_batch_energy(mfd_batch* b, int dom, double* u);
+/* Checkpoint / resume of a batch, as mfd_sim_save_state: every domain's and
+ * right-hand side's fields at step n (FP32, internal order), n, and the probe
+ * records since mfd_batch_set_probes. Load into a batch created from the same
+ * domains and nrhs, with the same materials, sources, gammas and probes. */
+mfd_status mfd_batch_state_size(const mfd_batch* b, size_t* bytes);
+mfd_status mfd_batch_save_state(mfd_batch* b, void* host, size_t bytes);
+mfd_status mfd_batch_load_state(mfd_batch* b, const void* host, size_t bytes);
 void mfd_batch_destroy(mfd_batch* b);
 
 /* ------------------------------------------------- hyperviscosity search */

@@ -117,6 +117,15 @@ _SIGS = {
     "mfd_batch_set_gamma": (_I, [_VP, _I, _VP]),
     "mfd_batch_energy": (_I, [_VP, _I, _VP]),
     "mfd_batch_destroy": (None, [_VP]),
+    "mfd_batch_set_spin_limit": (_I, [_VP, C.c_uint64]),
+    "mfd_sim_state_size": (_I, [_VP, _VP]),
+    "mfd_sim_save_state": (_I, [_VP, _VP, C.c_size_t]),
+    "mfd_sim_load_state": (_I, [_VP, _VP, C.c_size_t]),
+    "mfd_batch_state_size": (_I, [_VP, _VP]),
+    "mfd_batch_save_state": (_I, [_VP, _VP, C.c_size_t]),
+    "mfd_batch_load_state": (_I, [_VP, _VP, C.c_size_t]),
+    "mfd_debug_fail_alloc": (_I, [_I64]),
+    "mfd_debug_alloc_pending": (_I64, []),
     "mfd_hv_search": (_I, [_VP, _VP, _VP, _D, _D, _D, _VP, _VP, _VP, _VP, _VP, _D, _D, _I, _I, _I64, _I64, _D, _VP,
                            _VP]),
 }
@@ -236,6 +245,24 @@ def fdtd_phase_speed(omega_dt, courant, phi):
     c = np.zeros(1)
     _ck(lib().mfd_fdtd_phase_speed(float(omega_dt), float(courant), float(phi), _p(c)))
     return float(c[0])
+
+
+def _save_state(size_fn, save_fn, h):
+    n = C.c_size_t(0)
+    _ck(size_fn(h, C.byref(n)))
+    buf = C.create_string_buffer(n.value)
+    _ck(save_fn(h, buf, n.value))
+    return buf.raw
+
+
+def debug_fail_alloc(after):
+    """Makes the device allocation after the next `after` ones fail with MFD_ERR_OOM (-1: off)."""
+    _ck(lib().mfd_debug_fail_alloc(int(after)))
+
+
+def debug_alloc_pending():
+    """Allocations left before the injected failure fires (-1: none pending)."""
+    return int(lib().mfd_debug_alloc_pending())
 
 
 def fma_peak(device=0):
@@ -585,6 +612,14 @@ class Sim:
         _ck(lib().mfd_sim_autotune(self.h, int(reps), _p(ch)))
         return int(ch[0]), int(ch[1])
 
+    def save_state(self):
+        """Checkpoint of the fields, the step index and the probe records (bytes, mfd_sim_save_state)."""
+        return _save_state(lib().mfd_sim_state_size, lib().mfd_sim_save_state, self.h)
+
+    def load_state(self, blob):
+        """Resumes from a checkpoint of save_state (a simulation built the same way)."""
+        _ck(lib().mfd_sim_load_state(self.h, blob, len(blob)))
+
     def grad(self, nsteps, every=0, nsrc=0):
         """(J, dJ/deps_r per E node, dJ/d amplitude per source) over the next nsteps (mfd_grad)."""
         J = np.zeros(1)
@@ -662,6 +697,18 @@ class Batch:
 
     def step(self, n):
         _ck(lib().mfd_batch_step(self.h, int(n)))
+
+    def save_state(self):
+        """Checkpoint of every domain's fields, the step index and the probe records (bytes)."""
+        return _save_state(lib().mfd_batch_state_size, lib().mfd_batch_save_state, self.h)
+
+    def load_state(self, blob):
+        """Resumes from a checkpoint of save_state (a batch built the same way)."""
+        _ck(lib().mfd_batch_load_state(self.h, blob, len(blob)))
+
+    def set_spin_limit(self, limit):
+        """Polls a waiting block makes at a grid barrier before the call gives up (mfd_batch_set_spin_limit)."""
+        _ck(lib().mfd_batch_set_spin_limit(self.h, int(limit)))
 
     def read_probes(self, dom):
         steps = C.c_int64(0)

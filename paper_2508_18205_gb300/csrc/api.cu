@@ -9,11 +9,31 @@ namespace mfd {
 
 static thread_local std::string g_last_error;
 
+std::atomic<long long> g_alloc_fail_in{-1};
+
 void set_error(const std::string& msg) { g_last_error = msg; }
 
 mfd_status fail(mfd_status st, const std::string& msg) {
     g_last_error = msg;
     return st;
+}
+
+static const char kStateMagic[8] = {'M', 'F', 'D', 'S', 'T', 'A', 'T', 'E'};
+
+void state_head_init(StateHead* h, int32_t kind) {
+    std::memset(h, 0, sizeof(*h));
+    std::memcpy(h->magic, kStateMagic, 8);
+    h->version = kStateVersion;
+    h->kind = kind;
+}
+
+mfd_status state_head_check(const void* blob, size_t size, int32_t kind, StateHead* out) {
+    if (!blob || size < sizeof(StateHead)) return fail(MFD_ERR_ARG, "state blob too small");
+    std::memcpy(out, blob, sizeof(StateHead));
+    if (std::memcmp(out->magic, kStateMagic, 8) != 0) return fail(MFD_ERR_ARG, "not a state blob");
+    if (out->version != kStateVersion) return fail(MFD_ERR_ARG, "state blob of another version");
+    if (out->kind != kind) return fail(MFD_ERR_ARG, "state blob of another object kind");
+    return MFD_OK;
 }
 
 mfd_status order_streams(cudaStream_t from, cudaStream_t to) {
@@ -114,6 +134,13 @@ extern "C" {
 const char* mfd_last_error(void) { return g_last_error.c_str(); }
 
 int mfd_version(void) { return 1; }
+
+mfd_status mfd_debug_fail_alloc(int64_t after) {
+    g_alloc_fail_in.store(after < 0 ? -1 : (long long)after);
+    return MFD_OK;
+}
+
+int64_t mfd_debug_alloc_pending(void) { return g_alloc_fail_in.load(); }
 
 mfd_status mfd_ctx_create(int device, void* stream, mfd_ctx** out) {
     if (!out) return fail(MFD_ERR_ARG, "out is NULL");

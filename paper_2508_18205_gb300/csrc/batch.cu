@@ -473,6 +473,7 @@ struct mfd_batch {
     int64_t steps = 0;
     int grid = 0;
     int tile_nodes = 64;
+    unsigned long long spin_limit = 1ull << 25;  // polls with 64 ns naps: a few seconds before giving up
     bool use_graph = true;
     cudaGraphExec_t graph = nullptr;
     int graph_steps = -1;
@@ -595,7 +596,7 @@ BArgs make_args(mfd_batch* b, int nsteps) {
     a.counter = b->counter.as<int64_t>();
     a.nsteps = nsteps;
     a.bar = b->bar.as<unsigned int>();
-    a.spin_limit = 1ull << 25;  // polls with 64 ns naps: a few seconds before giving up
+    a.spin_limit = b->spin_limit;
     return a;
 }
 
@@ -908,6 +909,11 @@ mfd_status mfd_batch_set_probes(mfd_batch* b, int dom, int count, const int64_t*
         cap = std::max(cap, X.prb_cap);
     }
     MFD_CUDA(cudaSetDevice(b->ctx->device));
+    // the tables are rebuilt before the next launch; until the buffer is in
+    // place no probe is recorded
+    b->tables_dirty = true;
+    b->prb_cap = 0;
+    b->prb_slots = 0;
     MFD_TRY(b->prb_buf.alloc(std::max<int64_t>(1, cap * slots) * b->R * 4));
     b->prb_slots = slots;
     b->prb_cap = cap;
@@ -923,12 +929,13 @@ mfd_status mfd_batch_step(mfd_batch* b, int64_t nsteps) {
     if (nsteps == 0) return MFD_OK;
     MFD_CUDA(cudaSetDevice(b->ctx->device));
     if (b->tables_dirty) {
-        MFD_TRY(build_tables(b));
+        // the graph points at the tables' arrays: drop it before they are replaced
         if (b->graph) {
             cudaGraphExecDestroy(b->graph);
             b->graph = nullptr;
         }
         b->graph_steps = -1;
+        MFD_TRY(build_tables(b));
     }
     cudaStream_t s = b->ctx->stream;
     if (b->use_graph && b->graph_steps != (int)nsteps) {
@@ -957,15 +964,98 @@ mfd_status mfd_batch_step(mfd_batch* b, int64_t nsteps) {
     }
     if (b->use_graph) MFD_CUDA(cudaGraphLaunch(b->graph, s));
     else MFD_CUDA(launch_batch(b, (int)nsteps));
-    b->steps += nsteps;
     unsigned int flags[3];
     MFD_CUDA(cudaMemcpyAsync(flags, b->bar.p, sizeof(flags), cudaMemcpyDeviceToHost, s));
     MFD_CUDA(cudaStreamSynchronize(s));
     if (flags[2] != 0u) {
-        cudaMemsetAsync(b->bar.p, 0, 16, s);
-        cudaStreamSynchronize(s);
+        // every block has left the kernel; the barrier words are cleared for the
+        // next launch, the step counters stay where they were and the fields are
+        // left part way through the call (the caller sets them again)
+        MFD_CUDA(cudaMemsetAsync(b->bar.p, 0, 16, s));
+        MFD_CUDA(cudaStreamSynchronize(s));
         return fail(MFD_ERR_TIMEOUT, "a grid barrier of the batched kernel timed out");
     }
+    b->steps += nsteps;
+    return MFD_OK;
+}
+
+// checkpoint / resume: buffer A holds every field at step boundaries (B is
+// rewritten by the H half step before it is read), then the probe records
+static void batch_state_layout(const mfd_batch* b, StateHead* h) {
+    state_head_init(h, 2);
+    h->ne = b->ntot;
+    h->nrhs = b->R;
+    h->steps = b->steps;
+    h->probe_from = b->prb_from;
+    h->nprobe = b->prb_slots;
+    int64_t rec = std::min(b->steps - b->prb_from, b->prb_cap);
+    h->rec = b->prb_slots > 0 && rec > 0 ? rec : 0;
+    h->bytes[0] = (int64_t)b->A.bytes;
+}
+
+static size_t batch_state_total(const StateHead& h) {
+    return sizeof(StateHead) + (size_t)h.bytes[0] + (size_t)h.rec * h.nprobe * h.nrhs * 4;
+}
+
+mfd_status mfd_batch_state_size(const mfd_batch* b, size_t* bytes) {
+    if (!b || !bytes) return fail(MFD_ERR_ARG, "NULL argument");
+    StateHead h;
+    batch_state_layout(b, &h);
+    *bytes = batch_state_total(h);
+    return MFD_OK;
+}
+
+mfd_status mfd_batch_save_state(mfd_batch* b, void* host, size_t bytes) {
+    if (!b || !host) return fail(MFD_ERR_ARG, "NULL argument");
+    StateHead h;
+    batch_state_layout(b, &h);
+    if (bytes < batch_state_total(h)) return fail(MFD_ERR_ARG, "state buffer smaller than mfd_batch_state_size");
+    MFD_CUDA(cudaSetDevice(b->ctx->device));
+    cudaStream_t s = b->ctx->stream;
+    char* o = static_cast<char*>(host);
+    std::memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    MFD_CUDA(cudaMemcpyAsync(o, b->A.p, (size_t)h.bytes[0], cudaMemcpyDeviceToHost, s));
+    o += h.bytes[0];
+    if (h.rec) MFD_CUDA(cudaMemcpyAsync(o, b->prb_buf.p, (size_t)h.rec * h.nprobe * h.nrhs * 4, cudaMemcpyDeviceToHost, s));
+    MFD_CUDA(cudaStreamSynchronize(s));
+    return MFD_OK;
+}
+
+mfd_status mfd_batch_load_state(mfd_batch* b, const void* host, size_t bytes) {
+    if (!b || !host) return fail(MFD_ERR_ARG, "NULL argument");
+    StateHead in, mine;
+    MFD_TRY(state_head_check(host, bytes, 2, &in));
+    batch_state_layout(b, &mine);
+    if (in.ne != mine.ne || in.nrhs != mine.nrhs || in.bytes[0] != mine.bytes[0])
+        return fail(MFD_ERR_ARG, "state blob of another batch (node count or right-hand sides differ)");
+    if (in.rec > 0 && (in.nprobe != b->prb_slots || in.rec > b->prb_cap))
+        return fail(MFD_ERR_ARG, "state blob probe records need the same probes with enough capacity");
+    if (bytes < batch_state_total(in)) return fail(MFD_ERR_ARG, "state blob truncated");
+    MFD_CUDA(cudaSetDevice(b->ctx->device));
+    cudaStream_t s = b->ctx->stream;
+    const char* o = static_cast<const char*>(host) + sizeof(in);
+    MFD_CUDA(cudaMemcpyAsync(b->A.p, o, (size_t)in.bytes[0], cudaMemcpyHostToDevice, s));
+    o += in.bytes[0];
+    if (in.rec) MFD_CUDA(cudaMemcpyAsync(b->prb_buf.p, o, (size_t)in.rec * in.nprobe * in.nrhs * 4, cudaMemcpyHostToDevice, s));
+    b->steps = in.steps;
+    b->prb_from = in.rec > 0 ? in.probe_from : in.steps;
+    const int64_t words[2] = {b->steps, b->prb_from};
+    MFD_CUDA(cudaMemcpyAsync(b->counter.p, &words[0], 8, cudaMemcpyHostToDevice, s));
+    MFD_CUDA(cudaMemcpyAsync(b->pstep0.p, &words[1], 8, cudaMemcpyHostToDevice, s));
+    MFD_CUDA(cudaStreamSynchronize(s));
+    return MFD_OK;
+}
+
+mfd_status mfd_batch_set_spin_limit(mfd_batch* b, uint64_t limit) {
+    if (!b) return fail(MFD_ERR_ARG, "bad arguments");
+    b->spin_limit = limit;
+    if (b->graph) {  // the limit is a kernel argument baked into the captured graph
+        MFD_CUDA(cudaSetDevice(b->ctx->device));
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->graph_steps = -1;
     return MFD_OK;
 }
 

@@ -32,6 +32,10 @@ mfd_status fail(mfd_status st, const std::string& msg);
 
 // ------------------------------------------------------------ device buffers
 
+// Fault injection for tests (mfd_debug_fail_alloc): the number of device
+// allocations that still succeed before one fails; negative = off.
+extern std::atomic<long long> g_alloc_fail_in;
+
 // An owning device allocation (cudaMalloc); freed with the object holding it.
 struct DevBuf {
     void* p = nullptr;
@@ -48,6 +52,8 @@ struct DevBuf {
     mfd_status alloc(size_t n) {
         release();
         if (n == 0) n = 16;
+        if (g_alloc_fail_in.load(std::memory_order_relaxed) >= 0 && g_alloc_fail_in.fetch_sub(1) == 0)
+            return fail(MFD_ERR_OOM, std::string("injected allocation failure (") + std::to_string(n) + " bytes)");
         cudaError_t e = cudaMalloc(&p, n);
         if (e != cudaSuccess) {
             p = nullptr;
@@ -122,6 +128,29 @@ void release(const mfd_ctx* c);
 void release(const mfd_nodes* n);
 void release(const mfd_stencils* s);
 void release(const mfd_weights* w);
+
+// ------------------------------------------------------------ state blobs
+
+// Header of a checkpoint (mfd_sim_save_state, mfd_batch_save_state): the
+// device buffers that hold the fields follow in order, then the probe records.
+struct StateHead {
+    char magic[8];        // "MFDSTATE"
+    int32_t version;      // 1
+    int32_t kind;         // 1 simulation, 2 batch
+    int32_t layout;       // simulation layout (0 for a batch)
+    int32_t fp64;         // 1 for FP64 fields
+    int64_t ne, nh, nrhs; // E nodes, H nodes (batch: total nodes, 0), right-hand sides
+    int64_t steps;        // step index n of the saved fields (E at t_n, H at t_n - dt/2)
+    int64_t probe_from;   // step at which probe recording started
+    int32_t parity;       // ping-pong buffer holding the current fields
+    int32_t nprobe;       // probes (batch: probe slots over all domains)
+    int64_t rec;          // probe records in the blob
+    int64_t bytes[6];     // sizes of the device buffers that follow
+};
+constexpr int32_t kStateVersion = 1;
+void state_head_init(StateHead* h, int32_t kind);
+// checks magic, version and kind of a blob of `size` bytes
+mfd_status state_head_check(const void* blob, size_t size, int32_t kind, StateHead* out);
 
 // ------------------------------------------------------------ setup kernels
 

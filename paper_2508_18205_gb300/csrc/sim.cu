@@ -827,6 +827,10 @@ mfd_status mfd_set_sources(mfd_sim* sim, int count, const int64_t* node, const i
         if (!(f0[s] > 0)) return fail(MFD_ERR_ARG, "source frequency must be > 0");
         dev_node[s] = sim->eset->h_inv[node[s]];
     }
+    // the arrays are replaced one by one: until all are in place the
+    // simulation has no sources and no graph that points at the old arrays
+    sim->nsrc = 0;
+    sim->graph_ok = false;
     MFD_TRY(upload(ctx, sim->src_node, dev_node.data(), count * 8));
     MFD_TRY(upload(ctx, sim->src_amp, amp, count * 8));
     MFD_TRY(upload(ctx, sim->src_f0, f0, count * 8));
@@ -847,6 +851,10 @@ mfd_status mfd_set_probes(mfd_sim* sim, int count, const int64_t* node, int64_t 
         if (node[p] < 0 || node[p] >= sim->ne) return fail(MFD_ERR_ARG, "probe node out of range");
         dev_node[p] = sim->eset->h_inv[node[p]];
     }
+    // as in mfd_set_sources: no probes and no graph until both arrays are in place
+    sim->nprobe = 0;
+    sim->probe_cap = 0;
+    sim->graph_ok = false;
     MFD_TRY(upload(ctx, sim->probe_node, dev_node.data(), count * 8));
     MFD_TRY(sim->probe_buf.alloc(std::max<int64_t>(1, capacity * count) * sim->rs));
     sim->nprobe = count;
@@ -1005,6 +1013,98 @@ mfd_status mfd_energy(mfd_sim* sim, double* u) {
 }
 
 int64_t mfd_sim_steps(const mfd_sim* sim) { return sim ? sim->steps : -1; }
+
+// checkpoint / resume: the device field buffers as they are (bit-exact), the
+// step index and ping-pong parity, and the probe records so far
+static void sim_state_layout(const mfd_sim* sim, StateHead* h, DevBuf* const* bufs) {
+    state_head_init(h, 1);
+    h->layout = (int32_t)sim->layout;
+    h->fp64 = sim->fp64 ? 1 : 0;
+    h->ne = sim->ne;
+    h->nh = sim->nh;
+    h->nrhs = 1;
+    h->steps = sim->steps;
+    h->probe_from = sim->probe_from;
+    h->parity = sim->parity;
+    h->nprobe = sim->nprobe;
+    int64_t rec = std::min(sim->steps - sim->probe_from, sim->probe_cap);
+    h->rec = sim->nprobe > 0 && rec > 0 ? rec : 0;
+    for (int b = 0; b < 6; ++b) h->bytes[b] = bufs[b]->p ? (int64_t)bufs[b]->bytes : 0;
+}
+
+static size_t state_total(const StateHead& h, size_t rs) {
+    size_t t = sizeof(StateHead) + (size_t)h.rec * h.nprobe * rs;
+    for (int b = 0; b < 6; ++b) t += (size_t)h.bytes[b];
+    return t;
+}
+
+mfd_status mfd_sim_state_size(const mfd_sim* sim, size_t* bytes) {
+    if (!sim || !bytes) return fail(MFD_ERR_ARG, "NULL argument");
+    mfd_sim* m = const_cast<mfd_sim*>(sim);
+    DevBuf* bufs[6] = {&m->s0, &m->s1, &m->s2, &m->s3, &m->s4, &m->s5};
+    StateHead h;
+    sim_state_layout(sim, &h, bufs);
+    *bytes = state_total(h, sim->rs);
+    return MFD_OK;
+}
+
+mfd_status mfd_sim_save_state(mfd_sim* sim, void* host, size_t bytes) {
+    if (!sim || !host) return fail(MFD_ERR_ARG, "NULL argument");
+    DevBuf* bufs[6] = {&sim->s0, &sim->s1, &sim->s2, &sim->s3, &sim->s4, &sim->s5};
+    StateHead h;
+    sim_state_layout(sim, &h, bufs);
+    if (bytes < state_total(h, sim->rs)) return fail(MFD_ERR_ARG, "state buffer smaller than mfd_sim_state_size");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    char* o = static_cast<char*>(host);
+    std::memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    for (int b = 0; b < 6; ++b) {
+        if (!h.bytes[b]) continue;
+        MFD_CUDA(cudaMemcpyAsync(o, bufs[b]->p, (size_t)h.bytes[b], cudaMemcpyDeviceToHost, ctx->stream));
+        o += h.bytes[b];
+    }
+    if (h.rec)
+        MFD_CUDA(cudaMemcpyAsync(o, sim->probe_buf.p, (size_t)h.rec * h.nprobe * sim->rs, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    MFD_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MFD_OK;
+}
+
+mfd_status mfd_sim_load_state(mfd_sim* sim, const void* host, size_t bytes) {
+    if (!sim || !host) return fail(MFD_ERR_ARG, "NULL argument");
+    StateHead in, mine;
+    MFD_TRY(state_head_check(host, bytes, 1, &in));
+    DevBuf* bufs[6] = {&sim->s0, &sim->s1, &sim->s2, &sim->s3, &sim->s4, &sim->s5};
+    sim_state_layout(sim, &mine, bufs);
+    if (in.layout != mine.layout || in.fp64 != mine.fp64 || in.ne != mine.ne || in.nh != mine.nh)
+        return fail(MFD_ERR_ARG, "state blob of another layout, precision or node count");
+    for (int b = 0; b < 6; ++b)
+        if (in.bytes[b] != mine.bytes[b]) return fail(MFD_ERR_ARG, "state blob buffers differ from this simulation");
+    if (in.rec > 0 && (in.nprobe != sim->nprobe || in.rec > sim->probe_cap))
+        return fail(MFD_ERR_ARG, "state blob probe records need the same probes with enough capacity");
+    if (bytes < state_total(in, sim->rs)) return fail(MFD_ERR_ARG, "state blob truncated");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    const char* o = static_cast<const char*>(host) + sizeof(in);
+    for (int b = 0; b < 6; ++b) {
+        if (!in.bytes[b]) continue;
+        MFD_CUDA(cudaMemcpyAsync(bufs[b]->p, o, (size_t)in.bytes[b], cudaMemcpyHostToDevice, ctx->stream));
+        o += in.bytes[b];
+    }
+    if (in.rec)
+        MFD_CUDA(cudaMemcpyAsync(sim->probe_buf.p, o, (size_t)in.rec * in.nprobe * sim->rs, cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    sim->steps = in.steps;
+    sim->parity = in.parity;
+    sim->probe_from = in.rec > 0 ? in.probe_from : in.steps;
+    const int64_t words[2] = {sim->steps, sim->probe_from};
+    MFD_CUDA(cudaMemcpyAsync(sim->counter.p, &words[0], 8, cudaMemcpyHostToDevice, ctx->stream));
+    MFD_CUDA(cudaMemcpyAsync(sim->pstep0.p, &words[1], 8, cudaMemcpyHostToDevice, ctx->stream));
+    MFD_CUDA(cudaStreamSynchronize(ctx->stream));
+    sim->graph_ok = false;
+    return MFD_OK;
+}
 
 static bool block_ok(int b) { return b == 64 || b == 128 || b == 256 || b == 512; }
 

@@ -390,6 +390,10 @@ mfd_status mfd_yee_set_sources(mfd_yee* y, int count, const int64_t* cell, const
         if (bytes) MFD_CUDA(cudaMemcpyAsync(b.p, p, bytes, cudaMemcpyHostToDevice, ctx->stream));
         return MFD_OK;
     };
+    // no sources and no graph until every array is in place (a failed call
+    // leaves a grid without sources, never a count that outlives its arrays)
+    y->nsrc = 0;
+    y->graph_ok = false;
     MFD_TRY(up(y->src_node, cell, count * 8));
     MFD_TRY(up(y->src_amp, amp, count * 8));
     MFD_TRY(up(y->src_f0, f0, count * 8));
@@ -404,6 +408,9 @@ mfd_status mfd_yee_set_probes(mfd_yee* y, int count, const int64_t* cell, int64_
     for (int p = 0; p < count; ++p)
         if (cell[p] < 0 || cell[p] >= y->nx * y->ny) return fail(MFD_ERR_ARG, "probe cell out of range");
     MFD_CUDA(cudaSetDevice(y->ctx->device));
+    y->nprobe = 0;
+    y->probe_cap = 0;
+    y->graph_ok = false;
     MFD_TRY(y->probe_node.alloc(std::max(1, count) * 8));
     if (count) MFD_CUDA(cudaMemcpyAsync(y->probe_node.p, cell, count * 8, cudaMemcpyHostToDevice, y->ctx->stream));
     MFD_TRY(y->probe_buf.alloc(std::max<int64_t>(1, capacity * count) * y->rs));
