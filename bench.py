@@ -238,6 +238,131 @@ def cpu_baseline(budget_s=20.0):
             "cavity_fp64": cavity_cpu(O)}
 
 
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def _maxabs(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))))
+
+
+def oracle_checks(gpu):
+    """Relative L2 and largest absolute error of every workload's GPU results
+    against the FP64 oracle, which runs here on the host cores from the same
+    seeded inputs (node sets, fields, sources, materials) the GPU sections
+    used; nothing the GPU computed is an input of the oracle. gpu: the
+    host-side results the GPU sections kept (their "_gpu" entries)."""
+    import oracle as O
+    out = {}
+    t_all = time.perf_counter()
+    # headline problem on a 160^2 + 160^2 sub-square, the whole 5000 steps
+    g = gpu.get("pulse_reduced")
+    if g:
+        t = time.perf_counter()
+        S, n, k, m, alpha, c = (PARAMS[x] for x in ("S", "n", "k", "m", "alpha", "c"))
+        dt, eps0, mu0, c0, eta0 = W.units(S)
+        e, h = node_sets(g["nx"])
+        prob = O.tmz_staggered(e, h, n, k, m, alpha, dt, eps0, mu0, c * (-1) ** (alpha - 1))
+        ez, hx, hy = pulse_fields(e, h, g["nx"], dt)
+        probes = W.interior_nodes(e, 16, 24)
+        ref, rp, every = [ez, hx, hy], [], g["every"]
+        snaps = []
+        for kk in range(g["steps"] // every):
+            o = O.run_tmz(prob, *ref, every, step0=kk * every, probes=probes)
+            ref = list(o[:3])
+            rp.append(o[3])
+            snaps.append(np.concatenate(ref))
+        rp = np.concatenate(rp)
+        res = {"workload": f"pulse2d-staggered-{g['nx']}x{g['nx']}x2 (same stencils and pulse as the headline)",
+               "steps": g["steps"], "compared_every": every}
+        for tag in ("fp32_compensated", "fp32_plain", "fp64"):
+            errs = [_rel(a, b) for a, b in zip(g[tag]["snaps"], snaps)]
+            res[tag] = {"rel_l2_max_over_checks": max(errs), "rel_l2_end": errs[-1],
+                        "max_abs_end": _maxabs(g[tag]["snaps"][-1], snaps[-1]),
+                        "probe_rel_l2": _rel(g[tag]["probes"], rp)}
+        res["oracle_s"] = round(time.perf_counter() - t, 2)
+        out["pulse2d_staggered"] = res
+    # the plain method's cavity (FP64), the whole workload
+    g = gpu.get("cavity_fp64")
+    if g:
+        S, c = 0.5, 4e-3
+        dt, eps0, mu0, c0, eta0 = W.units(S)
+        nodes = W.pec_box((100, 100), 0.25, 1)
+        prob, _ = O.tmz_collocated(nodes, 12, 3, 2, 2, dt, eps0, mu0, -c)
+        ez, hx, hy = W.tm11_fields(nodes.xyz, 99.0, c0, mu0, 0.0, -0.5 * dt)
+        ez[nodes.pec == 1] = 0
+        o = O.run_tmz(prob, ez, hx, hy, g["steps"], probes=W.interior_nodes(nodes, 16, 14))
+        ref = np.concatenate(o[:3])
+        out["cavity_fp64"] = {"workload": "cavity TM11, 100x100 PEC, n=12, FP64 (whole workload)",
+                              "steps": g["steps"], "rel_l2": _rel(g["fields"], ref),
+                              "max_abs": _maxabs(g["fields"], ref), "probe_rel_l2": _rel(g["probes"], o[3])}
+    # 3D: the first step at full size (sampled nodes) and a whole run of a 32^3 cube
+    g = gpu.get("cube3d")
+    if g:
+        t = time.perf_counter()
+        S, cc, n, k, m, alpha = (CUBE[x] for x in ("S", "c", "n", "k", "m", "alpha"))
+        dt, eps0, mu0, c0, eta0 = W.units(S)
+        sm = g["sampled"]
+        ids = sm["ids"]
+        RE, RH, hs = O.max3d_sample_step(sm["nodes"], ids, n, k, m, alpha, dt, eps0, mu0, -cc, sm["E0"], sm["H0"],
+                                         eps_r=sm["eps_r"], h_ids=ids)
+        RHi = RH[:, np.searchsorted(hs, ids)]
+        got = np.concatenate([sm["E1"].ravel(), sm["H1"].ravel()])
+        ref = np.concatenate([RE.ravel(), RHi.ravel()])
+        res = {"workload": "cube3d periodic", "full_size_first_step": {
+            "nodes": sm["nodes"].n, "sampled_nodes": len(ids), "rel_l2": _rel(got, ref), "max_abs": _maxabs(got, ref)}}
+        sg = g["small"]
+        prob, _ = O.max3d_collocated(sg["nodes"], n, k, m, alpha, dt, eps0, mu0, -cc, eps_r=sg["eps_r"])
+        RE, RH, _, _ = O.run_3d(prob, sg["E0"], sg["H0"], sg["steps"])
+        ref = np.concatenate([RE, RH])
+        res[f"cube_{sg['nx']}^3_whole_run"] = {"steps": sg["steps"], "rel_l2": _rel(sg["fields"], ref),
+                                              "max_abs": _maxabs(sg["fields"], ref)}
+        res["oracle_s"] = round(time.perf_counter() - t, 2)
+        out["cube3d"] = res
+    # batched: whole domains (one of each stencil size), four right-hand sides each
+    g = gpu.get("batched")
+    if g:
+        t = time.perf_counter()
+        S = 0.5
+        dt, eps0, mu0, c0, eta0 = W.units(S)
+        doms = []
+        worst = 0.0
+        for D in g["domains"]:
+            ns, n = D["nodes"], D["n"]
+            prob, _ = O.tmz_collocated(ns, n, 3, W.poly_degree_for(n), 2, dt, eps0, mu0, -g["c"])
+            z = np.zeros(ns.n)
+            got, ref = [], []
+            for j, r in enumerate(D["rhs"]):
+                sel = D["src"].rhs == r
+                src = D["src"]
+                sub = W.Sources(node=src.node[sel], rhs=src.rhs[sel], amp=src.amp[sel], f0=src.f0[sel],
+                                t0=src.t0[sel])
+                o = O.run_tmz(prob, z, z, z, g["steps"], sources=sub)
+                ref.append(np.concatenate(o[:3]))
+                got.append(np.concatenate([D["ez"][:, j], D["hx"][:, j], D["hy"][:, j]]))
+            got, ref = np.concatenate(got), np.concatenate(ref)
+            e_ = _rel(got, ref)
+            worst = max(worst, e_)
+            doms.append({"domain": D["dom"], "nodes": ns.n, "n": n, "rhs": D["rhs"], "rel_l2": e_,
+                         "max_abs": _maxabs(got, ref)})
+        out["batched"] = {"steps": g["steps"], "domains": doms, "rel_l2_max": worst,
+                          "oracle_s": round(time.perf_counter() - t, 2)}
+    # adjoint: the gradient of the FP32 GPU adjoint against the FP64 oracle adjoint
+    g = gpu.get("adjoint")
+    if g:
+        P = _adjoint_problem(g["nx"])
+        dt, eps0, mu0, c0, eta0 = W.units(P["S"])
+        prob, _ = O.tmz_collocated(P["nodes"], 20, 3, 2, 2, dt, eps0, mu0, -P["c"], eps_r=P["eps"])
+        z = np.zeros(P["nodes"].n)
+        J, ge, ga = O.grad_tmz(prob, z, z, z, g["steps"], P["src"], P["probes"])
+        out["adjoint"] = {"workload": f"adjoint {g['nx']}x{g['nx']} PEC, n=20, FP32 GPU vs FP64 oracle",
+                          "steps": g["steps"], "J_rel": abs(g["J"] - J) / abs(J), "g_eps_rel_l2": _rel(g["g_eps"], ge),
+                          "g_eps_max_abs": _maxabs(g["g_eps"], ge), "g_amp_rel_l2": _rel(g["g_amp"], ga)}
+    out["oracle_s_total"] = round(time.perf_counter() - t_all, 2)
+    out["cores"] = O.threads()
+    return out
+
+
 def cavity_cpu(O, steps=1000):
     """The oracle on the whole FP64 cavity workload of cavity() (100 x 100 PEC
     square, n = 12, Delta^2 HV, TM11 mode, 1000 steps), on all host cores and
@@ -340,6 +465,7 @@ def main():
             r = dispersion(M, ctx, wts, e, reset, not a.plain)
         else:
             r = cube3d(M, ctx, a.cube_steps, peak, peak_kind, nx=a.cube_nx)
+        r.pop("_gpu", None)
         print(json.dumps(r), flush=True)
         return
     dist = None
@@ -456,6 +582,9 @@ def main():
         del s64
         if a.accuracy_steps:
             line["accuracy"] = accuracy(M, ctx, wts, a.accuracy_steps, reset)
+    gpu_kept = {}
+    if solo and not a.no_fp64 and not a.no_cpu and prec == M.MFD_FP32 and a.accuracy_steps:
+        gpu_kept["pulse_reduced"] = pulse_reduced_gpu(M, ctx, 160, a.accuracy_steps)
     if solo and not a.no_extra:
         line["dispersion"] = dispersion(M, ctx, wts, e, reset, comp)
     if solo and a.batched_steps:
@@ -491,11 +620,19 @@ def main():
         line["e2e"] = {"value": per_step_updates * a.steps / el * world, "unit": UNIT,
                        "h2d_bytes_per_step": h2d / a.steps, "d2h_bytes_per_step": d2h / a.steps,
                        "wall_s": el}
+    for key in ("cavity_fp64", "cube3d", "batched", "adjoint"):
+        if isinstance(line.get(key), dict) and "_gpu" in line[key]:
+            gpu_kept[key] = line[key].pop("_gpu")
     if solo and not a.no_cpu:
         try:
             line["cpu_baseline"] = cpu_baseline()
         except Exception as ex:  # the oracle is test infrastructure; report why it is missing
             line["cpu_baseline"] = {"value": None, "error": str(ex)}
+        try:
+            line["accuracy_vs_oracle"] = oracle_checks(gpu_kept)
+        except Exception as ex:
+            line["accuracy_vs_oracle"] = {"error": str(ex)}
+    del gpu_kept
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -518,28 +655,44 @@ def format_bytes(n, nhv, s, stats):
 
 
 def roofline(ms, steps, e, h, nhv, s, peak, peak_kind, stats=None):
-    """Dominant half-step kernel: algorithmic bytes per launch / its average
-    event-timed duration. The algorithmic bytes count 32-bit indices; with
-    index statistics, the bytes of the 16-bit index format the kernels read
-    are reported beside them."""
+    """Dominant half-step kernel: compulsory bytes per launch / its average
+    event-timed duration. The compulsory bytes are those of the index format
+    the kernels read: with 16-bit index streams (index statistics given and
+    nonzero) 2 bytes per entry (4 in slices that keep 32-bit entries) plus the
+    slice bases, else 32-bit indices. The count with 32-bit indices everywhere
+    (the per-node figure of the method's layout, 836 / 832 B at n = 30,
+    N_h = 57 in FP32) is reported beside it."""
     bh, be = algorithmic_bytes(PARAMS["n"], nhv, s)
     h_avg = ms[0] / steps / 1e3
     e_avg = ms[1] / steps / 1e3
     dom = "h" if h_avg >= e_avg else "e"
     dom_t = max(h_avg, e_avg)
-    dom_bytes = (bh * h.n) if dom == "h" else (be * e.n)
+    other_t = min(h_avg, e_avg)
+    i32_bytes = (bh * h.n) if dom == "h" else (be * e.n)
+    i32_other = (be * e.n) if dom == "h" else (bh * h.n)
+    q16 = stats is not None and stats["h"][0] > 0
+    if q16:
+        fh, fe = format_bytes(PARAMS["n"], nhv, s, stats)
+        dom_bytes = (fh * h.n) if dom == "h" else (fe * e.n)
+        other_bytes = (fe * e.n) if dom == "h" else (fh * h.n)
+        basis = ("compulsory bytes of the 16-bit index format the kernel reads (2 B per entry, 4 B in slices "
+                 "that keep 32-bit entries, two 4-byte bases per slice and stream), weights, fields")
+    else:
+        dom_bytes, other_bytes = i32_bytes, i32_other
+        basis = "compulsory bytes with 32-bit indices, weights, fields"
     achieved = dom_bytes / dom_t / 1e9
     kname = "k_h_stag" if dom == "h" else "k_e_stag"
     r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
          "traffic": traffic_record(kname, s), "kernel": kname, "peak_kind": peak_kind,
-         "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_t * 1e3,
-         "other_kernel_avg_launch_ms": min(h_avg, e_avg) * 1e3,
-         "other_kernel_achieved_gbs": ((be * e.n) if dom == "h" else (bh * h.n)) / min(h_avg, e_avg) / 1e9}
-    if stats is not None and stats["h"][0] > 0:
-        fh, fe = format_bytes(PARAMS["n"], nhv, s, stats)
-        fb = (fh * h.n) if dom == "h" else (fe * e.n)
-        r["index_format"] = {"name": "q16", "bytes_per_launch": fb, "achieved": fb / dom_t / 1e9,
-                             "frac": fb / dom_t / 1e9 / peak,
+         "algorithmic_bytes_per_launch": dom_bytes, "bytes_basis": basis, "avg_launch_ms": dom_t * 1e3,
+         "other_kernel_avg_launch_ms": other_t * 1e3,
+         "other_kernel_achieved_gbs": other_bytes / other_t / 1e9,
+         "int32_index_count": {"bytes_per_launch": i32_bytes, "achieved": i32_bytes / dom_t / 1e9,
+                               "frac": i32_bytes / dom_t / 1e9 / peak,
+                               "note": "the same launch counted with 32-bit indices everywhere; the kernel "
+                                       "reads fewer bytes than this, so this fraction can exceed 1"}}
+    if q16:
+        r["index_format"] = {"name": "q16",
                              "slices_with_32bit_entries": {"h_pass": list(stats["h"][1:]),
                                                            "e_pass": list(stats["e"][1:]),
                                                            "slices": stats["h"][0]}}
@@ -571,7 +724,10 @@ def batched(M, ctx, steps, peak, peak_kind, ndom=256, nrhs=16):
         bt.set_sources(d, src.node, src.rhs, src.amp, src.f0, src.t0)
     setup_s = time.time() - t
     import torch
+    blob0 = bt.save_state()  # t = 0: the timed run starts here again after the warm-up
     bt.step(steps)  # captures the graph and warms up
+    bt.load_state(blob0)
+    del blob0
     stream = ctx.torch_stream()
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
@@ -583,6 +739,18 @@ def batched(M, ctx, steps, peak, peak_kind, ndom=256, nrhs=16):
     el = t0.elapsed_time(t1) / 1e3
     ntot = sum(ns.n for ns, _ in specs)
     upd = ntot * 3 * nrhs
+    # for the comparison with the oracle: the smallest domain of each stencil size,
+    # four of its right-hand sides, after the timed run (the whole step count from t = 0)
+    pick = []
+    for nn in sorted({n for _, n in specs}):
+        cand = [d for d, (ns, n) in enumerate(specs) if n == nn]
+        pick.append(min(cand, key=lambda d: specs[d][0].n))
+    rhs_pick = [0, nrhs // 3, 2 * nrhs // 3, nrhs - 1]
+    check = {"steps": steps, "c": c, "domains": [
+        {"dom": d, "n": specs[d][1], "nodes": specs[d][0], "rhs": rhs_pick,
+         "src": W.ricker_sources(specs[d][0], nrhs, 500 + d, c0, nrhs=nrhs, one_per_rhs=True),
+         "ez": bt.get_field(d, M.MFD_EZ)[:, rhs_pick], "hx": bt.get_field(d, M.MFD_HX)[:, rhs_pick],
+         "hy": bt.get_field(d, M.MFD_HY)[:, rhs_pick]} for d in pick]}
     byt = sum(ns.n * (4 * (max(n, 31) + n) + 4 * (4 * n + 31) + 10 * 4 * nrhs) for ns, n in specs)
     ach = byt * steps / el / 1e9
     return {"workload": f"batched {ndom} domains (squares and disks, 2k-60k nodes), {nrhs} RHS",
@@ -592,7 +760,8 @@ def batched(M, ctx, steps, peak, peak_kind, ndom=256, nrhs=16):
                          "traffic": traffic_record("k_batch16_256dom", 4) if (ndom, nrhs) == (256, 16) else None,
                          "traffic_unit": "DRAM bytes per step (the persistent launch runs all steps)",
                          "kernel": "k_batch<16>", "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_step": byt}}
+                         "algorithmic_bytes_per_step": byt},
+            "_gpu": check}
 
 
 def cube3d(M, ctx, steps, peak, peak_kind, nx=200):
@@ -637,6 +806,17 @@ def cube3d(M, ctx, steps, peak, peak_kind, nx=200):
     el = t0.elapsed_time(t1) / 1e3
     ms = sim.step_timed(min(steps, 100))
     kk = min(steps, 100)
+    # for the comparison with the oracle: the first step from the seeded initial
+    # state at 24 sampled nodes, in the timed launch configuration
+    rng = np.random.default_rng(12)
+    ids = np.sort(rng.choice(nodes.n, 24, replace=False))
+    for comp, v in zip(range(6), (ex, ey, ez, hx, hy, hz)):
+        sim.set_field(comp, v)
+    sim.step(1)
+    sampled = {"ids": ids, "E1": np.stack([sim.get_field(a)[ids] for a in range(3)]),
+               "H1": np.stack([sim.get_field(3 + a)[ids] for a in range(3)]), "nodes": nodes, "eps_r": er,
+               "E0": np.stack([ex, ey, ez]), "H0": np.stack([hx, hy, hz])}
+    small = _cube_small_gpu(M, ctx, 32, 2000)
     s4 = 4
     bh = 4 * max(n, nhv) + s4 * (3 * n + nhv) + 12 * s4
     be = 4 * n + s4 * 3 * n + 9 * s4
@@ -652,7 +832,33 @@ def cube3d(M, ctx, steps, peak, peak_kind, nx=200):
                          "traffic": traffic_record(dom, s4), "kernel": dom, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": dom_b, "avg_launch_ms": dom_t * 1e3,
                          "other_kernel_avg_launch_ms": min(h_avg, e_avg) * 1e3,
-                         "step_achieved_gbs": (bh + be) * nodes.n / (el / steps) / 1e9}}
+                         "step_achieved_gbs": (bh + be) * nodes.n / (el / steps) / 1e9},
+            "_gpu": {"sampled": sampled, "small": small}}
+
+
+CUBE = dict(S=0.5, c=1e-3, n=40, k=3, m=3, alpha=2)
+
+
+def _cube_small_gpu(M, ctx, nx, steps):
+    """The 3D workload's problem on an nx^3 cube (same stencils, coefficients,
+    eps_r recipe and TM110 fields), every field after `steps` FP32 steps."""
+    S, c, n, k, m, alpha = (CUBE[x] for x in ("S", "c", "n", "k", "m", "alpha"))
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    nodes = W.periodic_box((nx, nx, nx), 0.25, 3)
+    er = W.eps_r_smooth_3d(nodes.xyz, nodes.box_hi, 33)
+    nd = M.Nodes(ctx, nodes.xyz, nodes.period)
+    nhv = 2 * math.comb(2 * alpha + 3, 3) + 1
+    st = M.Stencils(nd, nd, max(n, nhv))
+    cw = M.Weights(st, n, k, m, M.MFD_OP_GRAD)
+    hw = M.Weights(st, nhv, 2 * alpha + 1, 2 * alpha, M.MFD_OP_LAP_POW, alpha)
+    sim = M.Sim(ctx, 3, M.MFD_FP32, dt, eps0, mu0, -c, cw, hw, compensated=True)
+    sim.set_materials(er, None)
+    E0, H0 = W.tm110_fields_3d(nodes.xyz, nx / 2, c0, mu0, 0.0, -0.5 * dt)
+    for comp, v in zip(range(6), (*E0, *H0)):
+        sim.set_field(comp, v)
+    sim.step(steps)
+    return {"nx": nx, "steps": steps, "fields": np.stack([sim.get_field(a) for a in range(6)]),
+            "nodes": nodes, "eps_r": er, "E0": np.stack(E0), "H0": np.stack(H0)}
 
 
 def cavity(M, ctx, steps=1000):
@@ -699,7 +905,8 @@ def cavity(M, ctx, steps=1000):
     return {"workload": "cavity TM11, 100x100 PEC, n=12, FP64, 1000 steps", "nodes": nodes.n,
             "value": nodes.n * 3 * steps / el, "unit": UNIT, "steps": steps, "ms_per_step": el / steps * 1e3,
             "roofline": "n/a (L2-resident, latency-bound)",
-            "rel_l2_vs_exact_mode": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+            "rel_l2_vs_exact_mode": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "_gpu": {"fields": got, "probes": sim.read_probes(), "steps": steps}}
 
 
 def adjoint(M, ctx, steps=4000, every=64):
@@ -752,13 +959,45 @@ def adjoint(M, ctx, steps=4000, every=64):
     t = time.perf_counter()
     J0, ge0, ga0 = sim.grad(steps, 0, len(src.node))
     gw = time.perf_counter() - t
+    small = _adjoint_small_gpu(M, ctx)
     return {"workload": "adjoint 500x500 PEC, n=20, FP32, 4000 steps, checkpoints every 64", "nodes": nodes.n,
+            "_gpu": small,
             "forward_value": nodes.n * 3 * steps / fwd, "unit": UNIT, "forward_ms_per_step": fwd / steps * 1e3,
             "gradient_s": gs, "gradient_over_forward": gs / fwd, "J": J,
             "grad_norm_eps": float(np.linalg.norm(ge)), "grad_amp": [float(x) for x in ga],
             "whole_history": {"gradient_s": gw, "gradient_over_forward": gw / fwd,
                               "history_bytes": (steps + 1) * nodes.n * 4,
                               "max_rel_diff_vs_checkpoints": float(np.max(np.abs(ge0 - ge)) / np.max(np.abs(ge)))}}
+
+
+def _adjoint_problem(nx):
+    """The differentiation workload's recipe on an nx x nx PEC box."""
+    S, c = 0.5, 4e-3
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    nodes = W.pec_box((nx, nx), 0.25, 5)
+    return dict(S=S, c=c, nodes=nodes, eps=W.eps_r_uniform(nodes.n, 55), src=W.ricker_sources(nodes, 4, 56, c0),
+                probes=W.interior_nodes(nodes, 8, 57))
+
+
+def _adjoint_small_gpu(M, ctx, nx=60, steps=400):
+    """J and its gradient (FP32, whole Ez history) on a reduced 60 x 60 box for the oracle's adjoint."""
+    P = _adjoint_problem(nx)
+    dt, eps0, mu0, c0, eta0 = W.units(P["S"])
+    ns = P["nodes"]
+    nd = M.Nodes(ctx, ns.xyz, ns.period)
+    st = M.Stencils(nd, nd, 31)
+    cw = M.Weights(st, 20, 3, 2, M.MFD_OP_GRAD)
+    hw = M.Weights(st, 31, 5, 4, M.MFD_OP_LAP_POW, 2)
+    sim = M.Sim(ctx, 2, M.MFD_FP32, dt, eps0, mu0, -P["c"], cw, hw, compensated=True)
+    sim.set_materials(P["eps"], ns.pec)
+    z = np.zeros(ns.n)
+    for cc in (M.MFD_EZ, M.MFD_HX, M.MFD_HY):
+        sim.set_field(cc, z)
+    src = P["src"]
+    sim.set_sources(src.node, src.amp, src.f0, src.t0)
+    sim.set_probes(P["probes"], steps)
+    J, ge, ga = sim.grad(steps, 0, len(src.node))
+    return {"nx": nx, "steps": steps, "J": J, "g_eps": ge, "g_amp": ga}
 
 
 def yee(M, ctx, peak, peak_kind, big=8192, steps=1000, nx=1000, pulse_steps=5000, stride=4):
@@ -965,6 +1204,33 @@ def dispersion(M, ctx, wts, e, reset, comp, steps=5000, stride=4):
     sim.set_probes(diag, steps)
     out["phi_45"] = _line_analysis(M, sim, steps, stride, math.sqrt(2), math.pi / 4)
     del sim, wts45
+    return out
+
+
+def pulse_reduced_gpu(M, ctx, nx=160, steps=5000, every=100):
+    """The headline workload's problem on an nx x nx + nx x nx staggered periodic
+    square (same stencils, coefficients and pulse), stepped on the GPU for the
+    full step count in FP32 (compensated and plain sums) and FP64: all fields
+    after every `every` steps and the probe series, kept for the comparison
+    with the oracle (oracle_checks)."""
+    e, h = node_sets(nx)
+    wts, _, _ = build_weights(M, ctx, e, h)
+    dt = W.units(PARAMS["S"])[0]
+    ez, hx, hy = pulse_fields(e, h, nx, dt)
+    probes = W.interior_nodes(e, 16, 24)
+    out = {"nx": nx, "steps": steps, "every": every}
+    for tag, prec, comp in (("fp32_compensated", M.MFD_FP32, True), ("fp32_plain", M.MFD_FP32, False),
+                            ("fp64", M.MFD_FP64, False)):
+        sim = make_sim(M, ctx, wts, prec, comp)
+        for c_, v in ((M.MFD_EZ, ez), (M.MFD_HX, hx), (M.MFD_HY, hy)):
+            sim.set_field(c_, v)
+        sim.set_probes(probes, steps)
+        snaps = []
+        for _ in range(steps // every):
+            sim.step(every)
+            snaps.append(np.concatenate([sim.get_field(c_) for c_ in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)]))
+        out[tag] = {"snaps": snaps, "probes": sim.read_probes()}
+        del sim
     return out
 
 
