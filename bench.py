@@ -184,6 +184,15 @@ def aggregate(elapsed_s, units, dist=None):
     return elapsed_s, units * world / elapsed_s
 
 
+def _sm_max_mhz():
+    """The maximum SM clock (MHz) from the measured peaks, else the GB300's 2070 MHz."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f).get("sm_max_mhz", 2070.0))
+    except (OSError, ValueError):
+        return 2070.0
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -725,6 +734,7 @@ def batched(M, ctx, steps, peak, peak_kind, ndom=256, nrhs=16):
     setup_s = time.time() - t
     import torch
     blob0 = bt.save_state()  # t = 0: the timed run starts here again after the warm-up
+    variant, variant_ms = bt.autotune(20)  # the work split, timed on this batch (state put back)
     bt.step(steps)  # captures the graph and warms up
     bt.load_state(blob0)
     del blob0
@@ -753,14 +763,29 @@ def batched(M, ctx, steps, peak, peak_kind, ndom=256, nrhs=16):
          "hy": bt.get_field(d, M.MFD_HY)[:, rhs_pick]} for d in pick]}
     byt = sum(ns.n * (4 * (max(n, 31) + n) + 4 * (4 * n + 31) + 10 * 4 * nrhs) for ns, n in specs)
     ach = byt * steps / el / 1e9
+    # the L1 data path: bytes the gathers deliver to registers per step (every H-pass
+    # entry brings Ez, Hx and Hy of all right-hand sides, every E-pass entry Hx and Hy)
+    # plus the stencil streams once per node, against 128 B per clock per SM
+    l1b = sum(ns.n * (max(n, 31) * 3 * 4 * nrhs + n * 2 * 4 * nrhs + 4 * (max(n, 31) + n) + 4 * (4 * n + 31))
+              for ns, n in specs)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    l1_peak = sms * 128 * _sm_max_mhz() * 1e6 / 1e9
     return {"workload": f"batched {ndom} domains (squares and disks, 2k-60k nodes), {nrhs} RHS",
             "nodes": ntot, "value": upd * steps / el, "unit": UNIT, "steps": steps,
             "ms_per_step": el / steps * 1e3, "graph": bt.uses_graph, "setup_s": round(setup_s, 2),
+            "autotuned": {"variant": variant,
+                          "variants": ["stream prefetch, 3 blocks of 256 per SM", "no prefetch, 4 blocks per SM"],
+                          "ms_per_step_by_variant": [float(x) for x in variant_ms]},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                          "traffic": traffic_record("k_batch16_256dom", 4) if (ndom, nrhs) == (256, 16) else None,
                          "traffic_unit": "DRAM bytes per step (the persistent launch runs all steps)",
                          "kernel": "k_batch<16>", "peak_kind": peak_kind,
                          "algorithmic_bytes_per_step": byt},
+            "l1_roofline": {"bound": "l1", "achieved": l1b * steps / el / 1e9, "peak": l1_peak, "unit": "GB/s",
+                            "frac": l1b * steps / el / 1e9 / l1_peak, "bytes_per_step": l1b,
+                            "peak_kind": f"nominal: {sms} SMs x 128 B per clock x the maximum SM clock",
+                            "basis": "gathered field bytes delivered to registers (3 fields x R x 4 B per H-pass "
+                                     "entry, 2 fields x R x 4 B per E-pass entry) + stencil streams once per node"},
             "_gpu": check}
 
 

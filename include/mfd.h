@@ -72,6 +72,15 @@ typedef struct mfd_sim mfd_sim;
 /* Message of the last failed call on this thread ("" if none). */
 const char* mfd_last_error(void);
 int mfd_version(void);
+/* How this copy of the library was built: MFD_BUILD_BOUNDS_CHECK is set in the
+ * bounds-checked debug build (compiled with MFD_BOUNDS_CHECK defined), where
+ * every stencil index is tested against the node set it points into before a
+ * kernel gathers through it, and where the stencil rows are tested when a
+ * simulation packs them. A failed test does not trap: the index is replaced
+ * by 0, and the call that ran the kernel returns MFD_ERR_STATE. It is the
+ * stand-in for a memory checker, for test runs; the paper has no counterpart. */
+#define MFD_BUILD_BOUNDS_CHECK 1
+int mfd_build_flags(void);
 
 /* Fault injection for tests of the error paths (the paper has no
  * counterpart): the next `after` device allocations of the library succeed
@@ -271,6 +280,38 @@ mfd_status mfd_sim_index_stats(const mfd_sim* sim, int64_t* out);
  * is left after step start + nsteps, with its probes recorded from the start
  * of the call. every < 0 is MFD_ERR_ARG. */
 mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, double* g_eps, double* g_amp);
+/* The gradient of mfd_grad in two halves, for automatic differentiation whose
+ * forward pass computes J and whose backward pass comes later, or not at all:
+ *   mfd_grad_forward runs the nsteps steps (from the current state, probes as
+ *   in mfd_grad) recording what the adjoint needs (the Ez history, or full
+ *   checkpoints every `every` steps, as mfd_grad), writes J and returns a tape;
+ *   mfd_grad_backward runs the adjoint sweep over the recorded run and writes
+ *   g_eps (count(E nodes), caller order) and g_amp (one per source): host
+ *   arrays with on_device = 0 (synchronous), or device FP64 arrays with
+ *   on_device = 1, ordered after the work queued on `stream` and before what
+ *   the caller queues on it afterwards.
+ * The sweep uses the simulation's weights, materials and sources: keep them as
+ * they were in the forward half, and do not step the simulation in between
+ * (MFD_ERR_STATE). A tape sweeps once (MFD_ERR_STATE after); the simulation is
+ * left at the end of the recorded run. mfd_tape_destroy frees a tape (before
+ * its simulation). mfd_grad is these two calls in turn. */
+typedef struct mfd_tape mfd_tape;
+mfd_status mfd_grad_forward(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, mfd_tape** tape);
+mfd_status mfd_grad_backward(mfd_tape* tape, double* g_eps, double* g_amp, int on_device, void* stream);
+void mfd_tape_destroy(mfd_tape* tape);
+/* The probe objective J = dt sum_n sum_p (Ez_p^n)^2 over the probe records
+ * since mfd_set_probes (Eq. 20's companion objective of the gradient calls),
+ * for a forward run that needs no gradient. */
+mfd_status mfd_probe_objective(mfd_sim* sim, double* J);
+/* Number of adjoint sweeps this simulation has run (mfd_grad, mfd_grad_backward). */
+int64_t mfd_sim_adjoint_sweeps(const mfd_sim* sim);
+/* Zero-copy variants of the differentiable inputs: eps_r (device FP64,
+ * count(E nodes), caller order; NULL = vacuum; values must be > 0, checked on
+ * the device: MFD_ERR_ARG) with pec (device uint8 in caller order, NULL = none)
+ * as mfd_set_materials; and the amplitudes of the sources already set (device
+ * FP64, one per source). Stream ordering as mfd_set_field_device. */
+mfd_status mfd_set_materials_device(mfd_sim* sim, const double* eps_r, const uint8_t* pec, void* stream);
+mfd_status mfd_set_source_amps_device(mfd_sim* sim, const double* amp, void* stream);
 /* Number of steps taken since the last mfd_set_field(MFD_EZ). */
 int64_t mfd_sim_steps(const mfd_sim* sim);
 /* Checkpoint / resume of a long run (the paper has no counterpart). The state
@@ -340,6 +381,21 @@ mfd_status mfd_batch_step(mfd_batch* b, int64_t nsteps);
  * few seconds). limit = 0 makes any block that has to wait give up at its
  * first poll, which exercises the timeout path. */
 mfd_status mfd_batch_set_spin_limit(mfd_batch* b, uint64_t limit);
+/* Variant of the batched kernel; the step's results are bit-identical in both
+ * (the same stencil sums in the same order). variant 0: every warp requests
+ * the index and weight streams of the next chunk of four stencil entries while
+ * it gathers the current one, three resident blocks of 256 threads per SM;
+ * variant 1: each chunk's streams are loaded when it starts, and the kernel is
+ * limited to the registers of four resident blocks per SM (more warps hide the
+ * latency instead). MFD_ERR_ARG for another variant. */
+mfd_status mfd_batch_set_variant(mfd_batch* b, int variant);
+int mfd_batch_variant(const mfd_batch* b);
+/* Autotuner: times `reps` steps of each variant on this batch (one launch
+ * each, CUDA events), keeps the fastest, and puts the fields, probe records and
+ * step counter back after every trial, so the batch does not advance.
+ * chosen (nullable) receives the variant, ms (nullable, 2 values) the
+ * milliseconds per step of each. */
+mfd_status mfd_batch_autotune(mfd_batch* b, int reps, int* chosen, double* ms);
 /* host: steps x count x nrhs FP64; *steps receives the recorded steps. */
 mfd_status mfd_batch_read_probes(mfd_batch* b, int dom, double* host, int64_t* steps);
 int64_t mfd_batch_nodes(const mfd_batch* b);
@@ -536,6 +592,8 @@ void mfd_halo_destroy(mfd_halo* halo);
  *   sorted by (squared distance, source index) -- the same stencils, entry
  *   for entry, that mfd_stencils_build + mfd_stencils_read return.
  *   stream: cudaStream_t (NULL = legacy default stream).
+ * Source coordinates of a periodic axis must lie in [0, period) (checked on
+ * the bounding box: MFD_ERR_ARG otherwise).
  * All scratch lives in one file-scope device array of 32 MiB (enough for
  * about 1,000,000 sources) that every GPU which loads the library holds until
  * the process exits; larger source sets are rejected with MFD_ERR_ARG and a
@@ -543,7 +601,9 @@ void mfd_halo_destroy(mfd_halo* halo);
  * calls that overlap on the GPU (other streams, other host threads) race: the
  * caller must order them. The first call on each device looks up the array's
  * device address with that device current (set-up); make that first call
- * before any stream capture. The call synchronises `stream` once (to read the
+ * before any stream capture. If the device's context is torn down and made
+ * again (cudaDeviceReset), the next call repeats the set-up. The call
+ * synchronises `stream` once (to read the
  * bounding box of the sources) and queues the rest asynchronously. */
 mfd_status mfd_knn_static(int dim, int64_t nc, const double* centres, int64_t ns, const double* sources,
                           const double* period, int n, int32_t* idx, void* stream);

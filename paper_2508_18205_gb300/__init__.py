@@ -17,7 +17,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libmfd.so")
+# MFD_LIB selects another build of the library (the bounds-checked one of build.build(bounds=True))
+LIB_PATH = os.environ.get("MFD_LIB") or os.path.join(_HERE, "_build", "libmfd.so")
 
 MFD_OK = 0
 MFD_ERR_ARG, MFD_ERR_OOM, MFD_ERR_CUDA, MFD_ERR_SINGULAR = -1, -2, -3, -4
@@ -26,6 +27,7 @@ MFD_OP_GRAD, MFD_OP_LAP_POW, MFD_OP_GRAD_VFD = 0, 1, 2
 MFD_FP32, MFD_FP64 = 0, 1
 MFD_INDEX_Q16, MFD_INDEX_I32 = 0, 1
 MFD_EX, MFD_EY, MFD_EZ, MFD_HX, MFD_HY, MFD_HZ = range(6)
+MFD_BUILD_BOUNDS_CHECK = 1
 
 
 class MfdError(RuntimeError):
@@ -118,6 +120,17 @@ _SIGS = {
     "mfd_batch_energy": (_I, [_VP, _I, _VP]),
     "mfd_batch_destroy": (None, [_VP]),
     "mfd_batch_set_spin_limit": (_I, [_VP, C.c_uint64]),
+    "mfd_batch_set_variant": (_I, [_VP, _I]),
+    "mfd_batch_variant": (_I, [_VP]),
+    "mfd_batch_autotune": (_I, [_VP, _I, _VP, _VP]),
+    "mfd_build_flags": (_I, []),
+    "mfd_grad_forward": (_I, [_VP, _I64, _I64, _VP, _VP]),
+    "mfd_grad_backward": (_I, [_VP, _VP, _VP, _I, _VP]),
+    "mfd_tape_destroy": (None, [_VP]),
+    "mfd_probe_objective": (_I, [_VP, _VP]),
+    "mfd_sim_adjoint_sweeps": (_I64, [_VP]),
+    "mfd_set_materials_device": (_I, [_VP, _VP, _VP, _VP]),
+    "mfd_set_source_amps_device": (_I, [_VP, _VP, _VP]),
     "mfd_sim_state_size": (_I, [_VP, _VP]),
     "mfd_sim_save_state": (_I, [_VP, _VP, C.c_size_t]),
     "mfd_sim_load_state": (_I, [_VP, _VP, C.c_size_t]),
@@ -587,6 +600,11 @@ class Sim:
         return spec, kidx, c, float(l1[0])
 
     @property
+    def adjoint_sweeps(self):
+        """Adjoint sweeps this simulation has run (mfd_sim_adjoint_sweeps)."""
+        return int(lib().mfd_sim_adjoint_sweeps(self.h))
+
+    @property
     def steps(self):
         return int(lib().mfd_sim_steps(self.h))
 
@@ -706,6 +724,22 @@ class Batch:
         """Resumes from a checkpoint of save_state (a batch built the same way)."""
         _ck(lib().mfd_batch_load_state(self.h, blob, len(blob)))
 
+    def set_variant(self, variant):
+        """Work split of the batched kernel (mfd_batch_set_variant): 0 = nrhs/4, 1 = nrhs/2 lanes per node."""
+        _ck(lib().mfd_batch_set_variant(self.h, int(variant)))
+
+    @property
+    def variant(self):
+        return int(lib().mfd_batch_variant(self.h))
+
+    def autotune(self, reps=20):
+        """Times both work splits on this batch and keeps the faster (mfd_batch_autotune):
+        (chosen variant, ms per step of each)."""
+        chosen = C.c_int(-1)
+        ms = np.zeros(2)
+        _ck(lib().mfd_batch_autotune(self.h, int(reps), C.byref(chosen), _p(ms)))
+        return chosen.value, ms
+
     def set_spin_limit(self, limit):
         """Polls a waiting block makes at a grid barrier before the call gives up (mfd_batch_set_spin_limit)."""
         _ck(lib().mfd_batch_set_spin_limit(self.h, int(limit)))
@@ -735,45 +769,112 @@ class Batch:
             pass
 
 
+def _host_f64(x):
+    if hasattr(x, "detach"):  # a torch tensor
+        x = x.detach().cpu().double().numpy()
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
 class ProbeObjective:
     """A collocated TMz run whose probe objective J(eps_r, amp) = dt sum_n sum_p Ez_p^n^2
-    is differentiable through ``ProbeEnergy`` (adjoint gradients from mfd_grad)."""
+    is differentiable through ``ProbeEnergy``: the forward pass runs the steps
+    (recording a tape only when a gradient may be asked for), the backward pass
+    runs the adjoint sweep over that tape (mfd_grad_forward / mfd_grad_backward).
+    eps_r and amp may be torch CUDA tensors (zero copy) or host arrays."""
 
     def __init__(self, sim: Sim, pec, fields, sources, probes, nsteps, every=0):
         self.sim, self.pec, self.fields = sim, pec, fields
         self.src, self.probes, self.nsteps, self.every = sources, probes, nsteps, every
+        self._pec_dev = None
+        self.last_forward_taped = None
 
-    def run(self, eps_r, amp):
+    def _setup(self, eps_r, amp):
         s = self.sim
-        s.set_materials(eps_r, self.pec)
+        if _is_cuda_tensor(eps_r):
+            import torch
+            eps = eps_r.detach().to(torch.float64).contiguous()
+            if self.pec is not None and self._pec_dev is None:
+                self._pec_dev = torch.as_tensor(np.ascontiguousarray(self.pec, dtype=np.uint8), device=eps.device)
+            pec = C.c_void_p(self._pec_dev.data_ptr()) if self.pec is not None else None
+            _ck(lib().mfd_set_materials_device(s.h, _dev_ptr(eps), pec, _torch_stream()))
+        else:
+            s.set_materials(_host_f64(eps_r), self.pec)
         for comp, v in self.fields.items():
             s.set_field(comp, v)
-        s.set_sources(self.src.node, amp, self.src.f0, self.src.t0)
+        if _is_cuda_tensor(amp):
+            import torch
+            a = amp.detach().to(torch.float64).contiguous()
+            s.set_sources(self.src.node, np.ones(len(self.src.node)), self.src.f0, self.src.t0)
+            _ck(lib().mfd_set_source_amps_device(s.h, _dev_ptr(a), _torch_stream()))
+        else:
+            s.set_sources(self.src.node, _host_f64(amp), self.src.f0, self.src.t0)
         s.set_probes(self.probes, self.nsteps)
-        return s.grad(self.nsteps, self.every, len(self.src.node))
+
+    def run(self, eps_r, amp):
+        """J and its gradient in one call (mfd_grad): (J, dJ/deps_r, dJ/d amplitude) on the host."""
+        self._setup(eps_r, amp)
+        return self.sim.grad(self.nsteps, self.every, len(self.src.node))
+
+    def forward(self, eps_r, amp, taped):
+        """The forward run and J; with taped, also the tape of mfd_grad_forward (else None)."""
+        self._setup(eps_r, amp)
+        self.last_forward_taped = bool(taped)
+        J = C.c_double(0.0)
+        if not taped:
+            self.sim.step(self.nsteps)
+            _ck(lib().mfd_probe_objective(self.sim.h, C.byref(J)))
+            return J.value, None
+        tape = C.c_void_p()
+        _ck(lib().mfd_grad_forward(self.sim.h, int(self.nsteps), int(self.every), C.byref(J), C.byref(tape)))
+        return J.value, tape
+
+    def backward(self, tape, device):
+        """The adjoint sweep over a tape: (dJ/deps_r, dJ/d amplitude) as float64 tensors on `device`."""
+        import torch
+        try:
+            ns = len(self.src.node)
+            ge = torch.empty(self.sim.ne, dtype=torch.float64, device=device)
+            ga = torch.empty(max(ns, 1), dtype=torch.float64, device=device)
+            if ge.is_cuda:
+                _ck(lib().mfd_grad_backward(tape, _dev_ptr(ge), _dev_ptr(ga), 1, _torch_stream()))
+            else:
+                _ck(lib().mfd_grad_backward(tape, C.c_void_p(ge.data_ptr()), C.c_void_p(ga.data_ptr()), 0, None))
+            return ge, ga[:ns]
+        finally:
+            lib().mfd_tape_destroy(tape)
 
 
 def _probe_energy_function():
     import torch
 
     class ProbeEnergy(torch.autograd.Function):
-        """J(eps_r, amp) of a ProbeObjective; backward returns the adjoint gradients."""
+        """J(eps_r, amp) of a ProbeObjective. forward runs the steps (and records a
+        tape when a gradient may follow); backward runs the adjoint sweep."""
 
         @staticmethod
-        def forward(ctx, eps_r, amp, obj):
-            J, ge, ga = obj.run(eps_r.detach().cpu().double().numpy(), amp.detach().cpu().double().numpy())
-            ctx.save_for_backward(torch.from_numpy(ge).to(eps_r.device, eps_r.dtype),
-                                  torch.from_numpy(np.ascontiguousarray(ga)).to(amp.device, amp.dtype))
+        def forward(ctx, eps_r, amp, obj, taped):
+            J, tape = obj.forward(eps_r, amp, taped)
+            ctx.obj, ctx.tape = obj, tape
+            ctx.dtypes = (eps_r.dtype, amp.dtype)
+            ctx.device = eps_r.device
             return torch.tensor(J, dtype=torch.float64, device=eps_r.device)
 
         @staticmethod
         def backward(ctx, gJ):
-            ge, ga = ctx.saved_tensors
-            return gJ.to(ge.dtype) * ge, gJ.to(ga.dtype) * ga, None
+            if ctx.tape is None:
+                raise RuntimeError("ProbeEnergy: the forward pass recorded no tape")
+            ge, ga = ctx.obj.backward(ctx.tape, ctx.device)
+            ctx.tape = None
+            g = gJ.to(torch.float64)
+            return (g * ge).to(ctx.dtypes[0]), (g * ga).to(ctx.dtypes[1]), None, None
 
     return ProbeEnergy
 
 
 def probe_energy(eps_r, amp, obj: ProbeObjective):
-    """Differentiable J(eps_r, amp) (torch tensors in, 0-d tensor out)."""
-    return _probe_energy_function().apply(eps_r, amp, obj)
+    """Differentiable J(eps_r, amp) (torch tensors in, 0-d tensor out). Under
+    torch.no_grad(), or when neither input requires a gradient, only the
+    forward run is made (no tape, no adjoint)."""
+    import torch
+    taped = torch.is_grad_enabled() and (eps_r.requires_grad or amp.requires_grad)
+    return _probe_energy_function().apply(eps_r, amp, obj, taped)

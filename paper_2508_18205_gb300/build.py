@@ -32,23 +32,33 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
 
 
-def _stale(objs, deps):
-    if not os.path.exists(LIB):
+def _stale(lib_path, deps):
+    if not os.path.exists(lib_path):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib_path)
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra=(), bounds: bool = False) -> str:
+    """Compiles libmfd.so; with bounds=True the bounds-checked debug build
+    (MFD_BOUNDS_CHECK, every stencil index tested before a gather) into
+    _build_bounds/libmfd.so instead (load it with MFD_LIB=<path>)."""
+    if bounds:
+        return _build(os.path.join(HERE, "_build_bounds"), force, verbose, (*extra, "-DMFD_BOUNDS_CHECK"))
+    return _build(OUT, force, verbose, extra)
+
+
+def _build(out_dir, force, verbose, extra):
+    lib_path = os.path.join(out_dir, "libmfd.so")
     srcs = sources()
     deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     deps.append(os.path.join(HERE, "..", "include", "mfd.h"))
     deps.append(os.path.abspath(__file__))
-    if not force and not _stale(None, deps):
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+    if not force and not _stale(lib_path, deps):
+        return lib_path
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
-    objs = [os.path.join(OUT, os.path.splitext(os.path.basename(s))[0] + ".o") for s in srcs]
+    objs = [os.path.join(out_dir, os.path.splitext(os.path.basename(s))[0] + ".o") for s in srcs]
 
     def one(args):
         src, obj = args
@@ -65,13 +75,13 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if bad:
         msg = "\n".join(f"{os.path.basename(s)}:\n{out}" for s, out in bad)
         raise RuntimeError("nvcc failed:\n" + msg)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

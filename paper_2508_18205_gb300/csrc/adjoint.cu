@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(256) k_adj_a(const int64_t* __restrict__ off, 
     T ax = 0, ay = 0, av = 0;
     for (int c = 0; c < nc; ++c) {
         const int64_t d = base + (int64_t)c * 32;
-        const int4 id = ld_stream(scol + d);
+        const int4 id = chk4(ld_stream(scol + d), n);
         const V4 wx = ld_stream(sx + d), wy = ld_stream(sy + d), wv = ld_stream(sv + d);
         const int ids[4] = {id.x, id.y, id.z, id.w};
         const T* wxs = &wx.x;
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(256) k_adj_b(const int64_t* __restrict__ off, 
     T vx = 0, vy = 0, cx = 0, cy = 0;
     for (int c = 0; c < nc; ++c) {
         const int64_t d = base + (int64_t)c * 32;
-        const int4 id = ld_stream(scol + d);
+        const int4 id = chk4(ld_stream(scol + d), n);
         const V4 wx = ld_stream(sx + d), wy = ld_stream(sy + d), wv = ld_stream(sv + d);
         const int ids[4] = {id.x, id.y, id.z, id.w};
         const T* wxs = &wx.x;
@@ -403,6 +403,8 @@ template <typename T> __global__ void k_init_lambda(T* __restrict__ LA, const T*
     LA[4 * i + 2] = T(0);
     LA[4 * i + 3] = A[4 * i + 3];
 }
+
+unsigned long long bounds_take_adjoint(cudaStream_t s) { return bounds_take_local(s); }
 
 cudaError_t init_lambda(bool fp64, void* LA, const void* A, int64_t n, cudaStream_t s) {
     const unsigned g = (unsigned)((n + 255) / 256);

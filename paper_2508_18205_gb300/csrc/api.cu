@@ -135,6 +135,14 @@ const char* mfd_last_error(void) { return g_last_error.c_str(); }
 
 int mfd_version(void) { return 1; }
 
+int mfd_build_flags(void) {
+#ifdef MFD_BOUNDS_CHECK
+    return MFD_BUILD_BOUNDS_CHECK;
+#else
+    return 0;
+#endif
+}
+
 mfd_status mfd_debug_fail_alloc(int64_t after) {
     g_alloc_fail_in.store(after < 0 ? -1 : (long long)after);
     return MFD_OK;

@@ -78,6 +78,7 @@ struct BArgs {
     int nsteps;
     unsigned int* bar;  // [0] arrivals, [1] generation, [2] error flag
     unsigned long long spin_limit;
+    int64_t ntot;  // nodes over all domains (the range of the stencil indices)
 };
 
 __device__ __forceinline__ float4 f4_fma(float w, float4 f, float4 a) {
@@ -122,7 +123,11 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned long long limit) {
     return ok != 0;
 }
 
-template <int R>
+// PF: the stream values of chunk c + 1 are requested before the gathers of
+// chunk c (more registers, DRAM latency of the streams hidden in the warp);
+// without PF each chunk's streams are loaded when it starts (fewer registers,
+// more resident warps hide it). Both give the same sums in the same order.
+template <int R, bool PF>
 __device__ void h_tile(const BArgs& a, const BTile t) {
     constexpr int LPN = R / 4;         // lanes per node
     constexpr int NPW = 32 / LPN;      // nodes per warp
@@ -137,20 +142,29 @@ __device__ void h_tile(const BArgs& a, const BTile t) {
     const float4* py = a.wy + d.wc0 + slice * d.nc * NPW + g;
     const float4* pv = a.wv + d.wv0 + slice * d.nv * NPW + g;
     float4 dx = {0, 0, 0, 0}, dy = dx, vx = dx, vy = dx, ve = dx;
-    // the stream values of chunk c + 1 are requested before the gathers of
-    // chunk c, so the DRAM latency of the streams overlaps the gathers
     const float4 z4 = {0, 0, 0, 0};
-    int4 nid = ld_stream(ip);
-    float4 nwx = d.nc > 0 ? ld_stream(px) : z4, nwy = d.nc > 0 ? ld_stream(py) : z4;
-    float4 nwv = d.nv > 0 ? ld_stream(pv) : z4;
+    int4 nid = PF ? chk4(ld_stream(ip), a.ntot) : make_int4(0, 0, 0, 0);
+    float4 nwx = PF && d.nc > 0 ? ld_stream(px) : z4, nwy = PF && d.nc > 0 ? ld_stream(py) : z4;
+    float4 nwv = PF && d.nv > 0 ? ld_stream(pv) : z4;
     for (int c = 0; c < d.ni; ++c) {
-        const int4 id = nid;
-        const float4 wx = nwx, wy = nwy, wv = nwv;
-        if (c + 1 < d.ni) {
-            nid = ld_stream(ip + (c + 1) * NPW);
-            nwx = c + 1 < d.nc ? ld_stream(px + (c + 1) * NPW) : z4;
-            nwy = c + 1 < d.nc ? ld_stream(py + (c + 1) * NPW) : z4;
-            nwv = c + 1 < d.nv ? ld_stream(pv + (c + 1) * NPW) : z4;
+        int4 id;
+        float4 wx, wy, wv;
+        if constexpr (PF) {
+            id = nid;
+            wx = nwx;
+            wy = nwy;
+            wv = nwv;
+            if (c + 1 < d.ni) {
+                nid = chk4(ld_stream(ip + (c + 1) * NPW), a.ntot);
+                nwx = c + 1 < d.nc ? ld_stream(px + (c + 1) * NPW) : z4;
+                nwy = c + 1 < d.nc ? ld_stream(py + (c + 1) * NPW) : z4;
+                nwv = c + 1 < d.nv ? ld_stream(pv + (c + 1) * NPW) : z4;
+            }
+        } else {
+            id = chk4(ld_stream(ip + c * NPW), a.ntot);
+            wx = c < d.nc ? ld_stream(px + c * NPW) : z4;
+            wy = c < d.nc ? ld_stream(py + c * NPW) : z4;
+            wv = c < d.nv ? ld_stream(pv + c * NPW) : z4;
         }
         const int ids[4] = {id.x, id.y, id.z, id.w};
         const float wxs[4] = {wx.x, wx.y, wx.z, wx.w}, wys[4] = {wy.x, wy.y, wy.z, wy.w};
@@ -190,7 +204,7 @@ __device__ void h_tile(const BArgs& a, const BTile t) {
     st_f4(out + 2 * R, hyn);
 }
 
-template <int R>
+template <int R, bool PF>
 __device__ void e_tile(const BArgs& a, const BTile t) {
     constexpr int LPN = R / 4;
     constexpr int NPW = 32 / LPN;
@@ -204,15 +218,24 @@ __device__ void e_tile(const BArgs& a, const BTile t) {
         const float4* px = a.wx + d.wc0 + slice * d.nc * NPW + g;
         const float4* py = a.wy + d.wc0 + slice * d.nc * NPW + g;
         float4 dxhy = {0, 0, 0, 0}, dyhx = dxhy;
-        int4 nid = ld_stream(ip);
-        float4 nwx = ld_stream(px), nwy = ld_stream(py);
+        int4 nid = PF ? chk4(ld_stream(ip), a.ntot) : make_int4(0, 0, 0, 0);
+        float4 nwx = PF ? ld_stream(px) : dxhy, nwy = PF ? ld_stream(py) : dxhy;
         for (int c = 0; c < d.nc; ++c) {
-            const int4 id = nid;
-            const float4 wx = nwx, wy = nwy;
-            if (c + 1 < d.nc) {
-                nid = ld_stream(ip + (c + 1) * NPW);
-                nwx = ld_stream(px + (c + 1) * NPW);
-                nwy = ld_stream(py + (c + 1) * NPW);
+            int4 id;
+            float4 wx, wy;
+            if constexpr (PF) {
+                id = nid;
+                wx = nwx;
+                wy = nwy;
+                if (c + 1 < d.nc) {
+                    nid = chk4(ld_stream(ip + (c + 1) * NPW), a.ntot);
+                    nwx = ld_stream(px + (c + 1) * NPW);
+                    nwy = ld_stream(py + (c + 1) * NPW);
+                }
+            } else {
+                id = chk4(ld_stream(ip + c * NPW), a.ntot);
+                wx = ld_stream(px + c * NPW);
+                wy = ld_stream(py + c * NPW);
             }
             const int ids[4] = {id.x, id.y, id.z, id.w};
             const float wxs[4] = {wx.x, wx.y, wx.z, wx.w}, wys[4] = {wy.x, wy.y, wy.z, wy.w};
@@ -239,20 +262,22 @@ __device__ void e_tile(const BArgs& a, const BTile t) {
     }
 }
 
-template <int R>
-__global__ void __launch_bounds__(BT_THREADS) k_batch(BArgs a) {
+// variant 0: stream prefetch, three resident blocks of 256 per SM (80
+// registers); variant 1: no prefetch, four resident blocks (64 registers)
+template <int R, int V>
+__global__ void __launch_bounds__(BT_THREADS, V ? 4 : 3) k_batch(BArgs a) {
     __shared__ int64_t step0_s;
     if (threadIdx.x == 0) step0_s = *a.counter;
     __syncthreads();
     const int64_t step0 = step0_s;
     const double pi = 3.14159265358979323846;
     for (int s = 0; s < a.nsteps; ++s) {
-        for (int k = blockIdx.x; k < a.ntile; k += gridDim.x) h_tile<R>(a, a.tile[k]);
+        for (int k = blockIdx.x; k < a.ntile; k += gridDim.x) h_tile<R, V == 0>(a, a.tile[k]);
         if (!grid_barrier(a.bar, a.spin_limit)) return;
         const int64_t n = step0 + s;  // step n -> n + 1
         for (int k = blockIdx.x; k < a.ntile; k += gridDim.x) {
             const BTile t = a.tile[k];
-            e_tile<R>(a, t);
+            e_tile<R, V == 0>(a, t);
             __syncthreads();
             const int s0 = a.src_start[k], s1 = a.src_start[k + 1];
             if (s1 > s0) {
@@ -311,7 +336,7 @@ __global__ void __launch_bounds__(BT_THREADS) k_benergy(BArgs a, int dom, int ti
         const float4* pv = a.wv + d.wv0 + sl * d.nv * NPW + g;
         float4 dx = {0, 0, 0, 0}, dy = dx, vx = dx, vy = dx;
         for (int c = 0; c < d.ni; ++c) {
-            const int4 id = ip[c * NPW];
+            const int4 id = chk4(ip[c * NPW], a.ntot);
             const int ids[4] = {id.x, id.y, id.z, id.w};
             const float4 wx = c < d.nc ? px[c * NPW] : make_float4(0, 0, 0, 0);
             const float4 wy = c < d.nc ? py[c * NPW] : make_float4(0, 0, 0, 0);
@@ -473,6 +498,7 @@ struct mfd_batch {
     int64_t steps = 0;
     int grid = 0;
     int tile_nodes = 64;
+    int variant = 0;  // kernel variant (mfd_batch_set_variant, mfd_batch_autotune)
     unsigned long long spin_limit = 1ull << 25;  // polls with 64 ns naps: a few seconds before giving up
     bool use_graph = true;
     cudaGraphExec_t graph = nullptr;
@@ -597,18 +623,34 @@ BArgs make_args(mfd_batch* b, int nsteps) {
     a.nsteps = nsteps;
     a.bar = b->bar.as<unsigned int>();
     a.spin_limit = b->spin_limit;
+    a.ntot = b->ntot;
     return a;
 }
 
-template <int R> void* kernel_ptr() { return (void*)k_batch<R>; }
+template <int R> void* kernel_ptr(int variant) { return variant ? (void*)k_batch<R, 1> : (void*)k_batch<R, 0>; }
 
-void* batch_kernel(int R) {
+void* batch_kernel(int R, int variant) {
     switch (R) {
-        case 4: return kernel_ptr<4>();
-        case 8: return kernel_ptr<8>();
-        case 16: return kernel_ptr<16>();
-        default: return kernel_ptr<32>();
+        case 4: return kernel_ptr<4>(variant);
+        case 8: return kernel_ptr<8>(variant);
+        case 16: return kernel_ptr<16>(variant);
+        default: return kernel_ptr<32>(variant);
     }
+}
+
+// the persistent grid of a variant: every block that can be resident on every SM
+mfd_status set_variant(mfd_batch* b, int variant) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(b->R, variant), BT_THREADS, 0);
+    if (e != cudaSuccess || per_sm < 1) return fail(MFD_ERR_CUDA, "occupancy query failed");
+    b->variant = variant;
+    b->grid = std::min(per_sm * b->ctx->sm_count, std::max(1, b->ntile));
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->graph_steps = -1;
+    return MFD_OK;
 }
 
 cudaError_t launch_batch(mfd_batch* b, int nsteps) {
@@ -623,7 +665,7 @@ cudaError_t launch_batch(mfd_batch* b, int nsteps) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, batch_kernel(b->R), args);
+    return cudaLaunchKernelExC(&cfg, batch_kernel(b->R, b->variant), args);
 }
 
 }  // namespace
@@ -744,10 +786,7 @@ mfd_status mfd_batch_create(mfd_ctx* ctx, int ndom, const mfd_sim_desc* descs, i
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bail(fail(MFD_ERR_CUDA, cudaGetErrorString(e)));
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)batch_kernel(R), BT_THREADS, 0);
-    if (e != cudaSuccess || per_sm < 1) return bail(fail(MFD_ERR_CUDA, "occupancy query failed"));
-    b->grid = std::min(per_sm * ctx->sm_count, std::max(1, b->ntile));
+    if ((st = set_variant(b, 0))) return bail(st);
     if ((st = b->prb_buf.alloc(16))) return bail(st);
     if ((st = build_tables(b))) return bail(st);
     e = cudaStreamSynchronize(s);
@@ -976,6 +1015,8 @@ mfd_status mfd_batch_step(mfd_batch* b, int64_t nsteps) {
         return fail(MFD_ERR_TIMEOUT, "a grid barrier of the batched kernel timed out");
     }
     b->steps += nsteps;
+    if (const unsigned long long hits = bounds_take_local(s))
+        return fail(MFD_ERR_STATE, std::to_string(hits) + " stencil indices out of range (bounds-checked build)");
     return MFD_OK;
 }
 
@@ -1044,6 +1085,80 @@ mfd_status mfd_batch_load_state(mfd_batch* b, const void* host, size_t bytes) {
     MFD_CUDA(cudaMemcpyAsync(b->counter.p, &words[0], 8, cudaMemcpyHostToDevice, s));
     MFD_CUDA(cudaMemcpyAsync(b->pstep0.p, &words[1], 8, cudaMemcpyHostToDevice, s));
     MFD_CUDA(cudaStreamSynchronize(s));
+    return MFD_OK;
+}
+
+mfd_status mfd_batch_set_variant(mfd_batch* b, int variant) {
+    if (!b || (variant != 0 && variant != 1)) return fail(MFD_ERR_ARG, "variant must be 0 or 1");
+    MFD_CUDA(cudaSetDevice(b->ctx->device));
+    MFD_TRY(set_variant(b, variant));
+    MFD_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    return MFD_OK;
+}
+
+int mfd_batch_variant(const mfd_batch* b) { return b ? b->variant : -1; }
+
+mfd_status mfd_batch_autotune(mfd_batch* b, int reps, int* chosen, double* ms) {
+    if (!b || reps < 1) return fail(MFD_ERR_ARG, "bad arguments");
+    MFD_CUDA(cudaSetDevice(b->ctx->device));
+    cudaStream_t s = b->ctx->stream;
+    // every trial starts from the same state and leaves nothing behind: the fields,
+    // the probe records and the step counters are put back after each
+    DevBuf saveA, saveP;
+    MFD_TRY(saveA.alloc(b->A.bytes));
+    MFD_TRY(saveP.alloc(b->prb_buf.bytes));
+    MFD_CUDA(cudaMemcpyAsync(saveA.p, b->A.p, b->A.bytes, cudaMemcpyDeviceToDevice, s));
+    MFD_CUDA(cudaMemcpyAsync(saveP.p, b->prb_buf.p, b->prb_buf.bytes, cudaMemcpyDeviceToDevice, s));
+    const int64_t steps0 = b->steps;
+    auto restore = [&]() -> mfd_status {
+        MFD_CUDA(cudaMemcpyAsync(b->A.p, saveA.p, b->A.bytes, cudaMemcpyDeviceToDevice, s));
+        MFD_CUDA(cudaMemcpyAsync(b->prb_buf.p, saveP.p, b->prb_buf.bytes, cudaMemcpyDeviceToDevice, s));
+        MFD_CUDA(cudaMemcpyAsync(b->counter.p, &steps0, 8, cudaMemcpyHostToDevice, s));
+        MFD_CUDA(cudaStreamSynchronize(s));
+        b->steps = steps0;
+        return MFD_OK;
+    };
+    cudaEvent_t e0, e1;
+    MFD_CUDA(cudaEventCreate(&e0));
+    MFD_CUDA(cudaEventCreate(&e1));
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } eg{e0, e1};
+    const int start_variant = b->variant;
+    int best = start_variant;
+    float tbest = 1e30f;
+    for (int v = 0; v < 2; ++v) {
+        MFD_TRY(set_variant(b, v));
+        if (b->tables_dirty) MFD_TRY(build_tables(b));
+        MFD_CUDA(launch_batch(b, 1));  // first launch of this kernel: loads it
+        MFD_CUDA(cudaEventRecord(e0, s));
+        MFD_CUDA(launch_batch(b, reps));
+        MFD_CUDA(cudaEventRecord(e1, s));
+        MFD_CUDA(cudaEventSynchronize(e1));
+        float t = 0;
+        MFD_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        unsigned int flags[3];
+        MFD_CUDA(cudaMemcpy(flags, b->bar.p, sizeof(flags), cudaMemcpyDeviceToHost));
+        MFD_TRY(restore());
+        if (flags[2] != 0u) {
+            MFD_CUDA(cudaMemsetAsync(b->bar.p, 0, 16, s));
+            MFD_TRY(set_variant(b, start_variant));
+            MFD_CUDA(cudaStreamSynchronize(s));
+            return fail(MFD_ERR_TIMEOUT, "a grid barrier of the batched kernel timed out during autotuning");
+        }
+        if (ms) ms[v] = (double)t / reps;
+        if (t < tbest) {
+            tbest = t;
+            best = v;
+        }
+    }
+    MFD_TRY(set_variant(b, best));
+    MFD_CUDA(cudaStreamSynchronize(s));
+    if (chosen) *chosen = best;
     return MFD_OK;
 }
 

@@ -186,7 +186,45 @@ template <typename T> struct StencilStreams {
     const typename Vec<T>::V4* wv = nullptr;
     int nc = 0, nv = 0, ni = 0;  // chunks per row: curl weights, HV weights, index (shared: max)
     int64_t n = 0;               // nodes
+    int64_t src_c = 0, src_v = 0;  // sizes of the node sets the curl and HV indices point into
 };
+
+// ---- bounds-checked build (compiled with -DMFD_BOUNDS_CHECK): every stencil
+// index is tested against the size of the node set it points into before a
+// kernel gathers through it. An index outside that set is counted in this
+// translation unit's device word and replaced by 0, so nothing is read out of
+// bounds and nothing traps; the public call that launched the kernel returns
+// MFD_ERR_STATE (bounds_take_* on the host). Without the flag the checks
+// compile to nothing.
+#ifdef MFD_BOUNDS_CHECK
+static __device__ unsigned long long g_bounds_hits;
+__device__ __forceinline__ int chk_id(int id, int64_t n) {
+    if ((unsigned long long)(long long)id >= (unsigned long long)n) {
+        atomicAdd(&g_bounds_hits, 1ull);
+        return 0;
+    }
+    return id;
+}
+#else
+__device__ __forceinline__ int chk_id(int id, int64_t) { return id; }
+#endif
+__device__ __forceinline__ int4 chk4(int4 v, int64_t n) {
+    return make_int4(chk_id(v.x, n), chk_id(v.y, n), chk_id(v.z, n), chk_id(v.w, n));
+}
+// host: indices this translation unit's kernels found out of range since the
+// last call (the count is reset); synchronises s in the checked build only
+static inline unsigned long long bounds_take_local(cudaStream_t s) {
+#ifdef MFD_BOUNDS_CHECK
+    unsigned long long v = 0, z = 0;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return 0;
+    if (cudaMemcpyFromSymbol(&v, g_bounds_hits, sizeof(v)) != cudaSuccess) return 0;
+    if (v) cudaMemcpyToSymbol(g_bounds_hits, &z, sizeof(z));
+    return v;
+#else
+    (void)s;
+    return 0;
+#endif
+}
 
 // ---- Q16 index decoding (see the layout notes at the top)
 __device__ __forceinline__ int q16_id(unsigned u, int2 b) { return (int)u + ((u & 0x8000u) ? b.y : b.x); }
@@ -202,7 +240,8 @@ __device__ __forceinline__ int4 q16_hi(uint4 u, int2 b) {
 // the Q16 stream when the slice has one and from the 32-bit stream otherwise.
 template <int N4, typename Body>
 __device__ __forceinline__ void for_idx4(int n4_rt, int64_t slice, int lane, const int4* __restrict__ idx,
-                                         const uint4* __restrict__ q, const int2* __restrict__ qb, Body&& body) {
+                                         const uint4* __restrict__ q, const int2* __restrict__ qb, int64_t bound,
+                                         Body&& body) {
     const int n4 = N4 ? N4 : n4_rt;
     const int n8 = (n4 + 1) >> 1;
     const int2 b = q ? ld_stream(qb + slice) : make_int2(-1, 0);
@@ -211,13 +250,13 @@ __device__ __forceinline__ void for_idx4(int n4_rt, int64_t slice, int lane, con
 #pragma unroll
         for (int c8 = 0; c8 < (N4 ? (N4 + 1) / 2 : n8); ++c8) {
             const uint4 u = ld_stream(p + c8 * 32);
-            body(2 * c8, q16_lo(u, b));
-            if (2 * c8 + 1 < n4) body(2 * c8 + 1, q16_hi(u, b));
+            body(2 * c8, chk4(q16_lo(u, b), bound));
+            if (2 * c8 + 1 < n4) body(2 * c8 + 1, chk4(q16_hi(u, b), bound));
         }
     } else {
         const int4* p = idx + slice * n4 * 32 + lane;
 #pragma unroll
-        for (int c = 0; c < n4; ++c) body(c, ld_stream(p + c * 32));
+        for (int c = 0; c < n4; ++c) body(c, chk4(ld_stream(p + c * 32), bound));
     }
 }
 

@@ -769,6 +769,17 @@ static void* g_knn_scratch_ptr[128] = {};
 static mfd_status knn_scratch_address(int device, unsigned char** out) {
     if (device < 0 || device >= 128) return fail(MFD_ERR_ARG, "device id out of range");
     std::lock_guard<std::mutex> lock(g_knn_scratch_mu);
+    if (g_knn_scratch_ptr[device]) {
+        // a context torn down and made again (cudaDeviceReset) reloads the module
+        // elsewhere: an address that no longer names device memory of this device
+        // is looked up again
+        cudaPointerAttributes at;
+        const cudaError_t e = cudaPointerGetAttributes(&at, g_knn_scratch_ptr[device]);
+        if (e != cudaSuccess || at.type != cudaMemoryTypeDevice || at.device != device) {
+            cudaGetLastError();
+            g_knn_scratch_ptr[device] = nullptr;
+        }
+    }
     if (!g_knn_scratch_ptr[device]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_knn_scratch);
@@ -849,6 +860,8 @@ extern "C" mfd_status mfd_knn_static(int dim, int64_t nc, const double* centres,
     for (int a = 0; a < dim; ++a) {
         lo[a] = key_dbl(hb[a]);
         hi[a] = key_dbl(hb[3 + a]);
+        if (per[a] > 0 && !(lo[a] >= 0.0 && hi[a] < per[a]))
+            return fail(MFD_ERR_ARG, "coordinates of a periodic axis must lie in [0, period)");
     }
     // the same cell grid as mfd_stencils_build: about one source per cell
     Grid g;

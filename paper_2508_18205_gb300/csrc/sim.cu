@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -223,6 +224,7 @@ struct PackedStencil {
     int64_t wide_c = 0, wide_v = 0;  // slices left on the 32-bit streams
     int nc = 0, nv = 0, ni = 0;
     int64_t n = 0;
+    int64_t src_c = 0, src_v = 0;  // sizes of the node sets the curl and HV indices point into
 };
 
 struct mfd_sim {
@@ -251,6 +253,7 @@ struct mfd_sim {
     std::vector<cudaEvent_t> events;
     AdjT adj;
     bool adj_ok = false;
+    int64_t adj_sweeps = 0;  // adjoint sweeps run (mfd_grad_backward)
     int block[2] = {256, 256};  // threads per block of the H and E half-step kernels (autotuned)
     bool q16 = true;            // staggered kernels read Q16 indices (mfd_sim_set_index_format)
     int64_t watch_every = 0;    // energy watchdog: check every this many steps (0: off)
@@ -293,6 +296,28 @@ mfd_status pack_weights(mfd_ctx* ctx, const mfd_weights* w, int out_index, int c
 
 int chunks_of(int n) { return (n + 3) / 4; }
 
+#ifdef MFD_BOUNDS_CHECK
+__global__ void k_check_rows(const int32_t* __restrict__ idx, int stride, int64_t N, int n_use, int64_t nsrc) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < N * n_use) chk_id(idx[(e / n_use) * stride + e % n_use], nsrc);
+}
+
+void check_rows(mfd_ctx* ctx, const mfd_stencils* st, int n_use) {
+    const int64_t total = st->centres->n * n_use;
+    k_check_rows<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(st->idx.as<int32_t>(), st->n,
+                                                                           st->centres->n, n_use, st->sources->n);
+}
+#endif
+
+// MFD_ERR_STATE when a kernel of the bounds-checked build met a stencil index
+// outside its node set (always MFD_OK in the default build)
+mfd_status bounds_status(cudaStream_t s) {
+    const unsigned long long hits = bounds_take_local(s) + bounds_take_step2d(s) + bounds_take_step3d(s) +
+                                    bounds_take_adjoint(s);
+    if (hits) return fail(MFD_ERR_STATE, std::to_string(hits) + " stencil indices out of range (bounds-checked build)");
+    return MFD_OK;
+}
+
 // a host vector into a new device buffer (at least one element), synchronously
 template <typename T> mfd_status upload_host(DevBuf& b, const std::vector<T>& v) {
     MFD_TRY(b.alloc(std::max<size_t>(1, v.size()) * sizeof(T)));
@@ -330,6 +355,13 @@ mfd_status pack_q16(mfd_ctx* ctx, const mfd_stencils* st, int n_use, int chunks4
 // packs the curl and HV streams of one pass
 mfd_status pack_pass(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* hv, int dim, bool fp64, PackedStencil& p) {
     p.n = curl->st->centres->n;
+    p.src_c = curl->st->sources->n;
+    p.src_v = hv->st->sources->n;
+#ifdef MFD_BOUNDS_CHECK
+    // pack-time row check: every stencil entry lies in the node set it points into
+    check_rows(ctx, curl->st, curl->n_use);
+    check_rows(ctx, hv->st, hv->n_use);
+#endif
     p.nc = chunks_of(curl->n_use);
     p.nv = chunks_of(hv->n_use);
     const bool shared = curl->st == hv->st;
@@ -380,6 +412,8 @@ template <typename T> StencilStreams<T> streams(const PackedStencil& p, bool q16
     s.nv = p.nv;
     s.ni = p.ni;
     s.n = p.n;
+    s.src_c = p.src_c;
+    s.src_v = p.idx_v.p ? p.src_v : p.src_c;
     return s;
 }
 
@@ -543,6 +577,54 @@ mfd_status check_set(const mfd_weights* curl, const mfd_weights* hv, const mfd_n
     return MFD_OK;
 }
 
+// per-node materials from device arrays in caller order (eps_r: NULL = vacuum;
+// pec: NULL = none): the E coefficient dt / (eps0 eps_r) (0 on held nodes),
+// eps_r in device order, the held mask, and held components zeroed
+mfd_status apply_materials(mfd_sim* sim, const double* de, const uint8_t* dp) {
+    mfd_ctx* ctx = sim->ctx;
+    const int64_t ne = sim->ne;
+    const double dt_eps0 = sim->d.dt / sim->d.eps0;
+    void* ce;
+    int stride, offset;
+    if (sim->layout == STAG2D) {
+        ce = sim->s4.p;
+        stride = 1;
+        offset = 0;
+    } else {
+        ce = sim->s0.p;
+        stride = sim->layout == COLLOC3D ? 8 : 4;
+        offset = 3;
+    }
+    const bool zero_ce = sim->layout != COLLOC3D;
+    unsigned g = (unsigned)((ne + 255) / 256);
+    if (sim->fp64)
+        k_materials<double><<<g, 256, 0, ctx->stream>>>(de, dp, sim->eset->perm.as<int64_t>(), ne, dt_eps0, zero_ce,
+                                                        (double*)ce, stride, offset, sim->eps.as<double>(),
+                                                        sim->mask.as<uint8_t>());
+    else
+        k_materials<float><<<g, 256, 0, ctx->stream>>>(de, dp, sim->eset->perm.as<int64_t>(), ne, dt_eps0, zero_ce,
+                                                       (float*)ce, stride, offset, sim->eps.as<double>(),
+                                                       sim->mask.as<uint8_t>());
+    MFD_CUDA(cudaGetLastError());
+    sim->has_mask = dp != nullptr;
+    sim->graph_ok = false;
+    if (sim->has_mask) {
+        void* ez;
+        int st2;
+        ez_location(sim, sim->parity, &ez, &st2);
+        void* base = sim->layout == COLLOC3D ? sim->s0.p : ez;
+        if (sim->fp64)
+            k_zero_held<double><<<g, 256, 0, ctx->stream>>>((double*)base, st2, sim->mask.as<uint8_t>(), ne,
+                                                            sim->layout == COLLOC3D);
+        else
+            k_zero_held<float><<<g, 256, 0, ctx->stream>>>((float*)base, st2, sim->mask.as<uint8_t>(), ne,
+                                                           sim->layout == COLLOC3D);
+        MFD_CUDA(cudaGetLastError());
+    }
+    MFD_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MFD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -612,6 +694,7 @@ mfd_status mfd_sim_create(mfd_ctx* ctx, const mfd_sim_desc* desc, mfd_sim** out)
     cudaMemsetAsync(sim->pstep0.p, 0, 8, ctx->stream);
     *out = sim;
     st = mfd_set_materials(sim, nullptr, nullptr);
+    if (!st) st = bounds_status(ctx->stream);  // pack-time row checks of the bounds-checked build
     if (st) {
         *out = nullptr;
         return bail(st);
@@ -641,47 +724,7 @@ mfd_status mfd_set_materials(mfd_sim* sim, const double* eps_r, const uint8_t* p
     DevBuf de, dp;
     if (eps_r) MFD_TRY(upload(ctx, de, eps_r, ne * 8));
     if (pec) MFD_TRY(upload(ctx, dp, pec, ne));
-    const double dt_eps0 = sim->d.dt / sim->d.eps0;
-    void* ce;
-    int stride, offset;
-    if (sim->layout == STAG2D) {
-        ce = sim->s4.p;
-        stride = 1;
-        offset = 0;
-    } else {
-        ce = sim->s0.p;
-        stride = sim->layout == COLLOC3D ? 8 : 4;
-        offset = 3;
-    }
-    const bool zero_ce = sim->layout != COLLOC3D;
-    unsigned g = (unsigned)((ne + 255) / 256);
-    if (sim->fp64)
-        k_materials<double><<<g, 256, 0, ctx->stream>>>(de.as<double>(), dp.as<uint8_t>(), sim->eset->perm.as<int64_t>(),
-                                                        ne, dt_eps0, zero_ce, (double*)ce, stride, offset,
-                                                        sim->eps.as<double>(), sim->mask.as<uint8_t>());
-    else
-        k_materials<float><<<g, 256, 0, ctx->stream>>>(de.as<double>(), dp.as<uint8_t>(), sim->eset->perm.as<int64_t>(),
-                                                       ne, dt_eps0, zero_ce, (float*)ce, stride, offset,
-                                                       sim->eps.as<double>(), sim->mask.as<uint8_t>());
-    MFD_CUDA(cudaGetLastError());
-    sim->has_mask = pec != nullptr;
-    sim->graph_ok = false;
-    if (sim->has_mask) {
-        void* ez;
-        int st2;
-        ez_location(sim, sim->parity, &ez, &st2);
-        void* base = sim->layout == COLLOC3D ? sim->s0.p : ez;
-        int stride2 = st2;
-        if (sim->fp64)
-            k_zero_held<double><<<g, 256, 0, ctx->stream>>>((double*)base, stride2, sim->mask.as<uint8_t>(), ne,
-                                                            sim->layout == COLLOC3D);
-        else
-            k_zero_held<float><<<g, 256, 0, ctx->stream>>>((float*)base, stride2, sim->mask.as<uint8_t>(), ne,
-                                                           sim->layout == COLLOC3D);
-        MFD_CUDA(cudaGetLastError());
-    }
-    MFD_CUDA(cudaStreamSynchronize(ctx->stream));
-    return MFD_OK;
+    return apply_materials(sim, de.as<double>(), dp.as<uint8_t>());
 }
 
 // locates (buffer, stride, offset, node set) of a component in the current state
@@ -887,7 +930,7 @@ static mfd_status step_plain(mfd_sim* sim, int64_t nsteps) {
         MFD_CUDA(enqueue_step(sim, nullptr));
         --left;
     }
-    return MFD_OK;
+    return bounds_status(sim->ctx->stream);
 }
 
 mfd_status mfd_step(mfd_sim* sim, int64_t nsteps) {
@@ -942,7 +985,7 @@ mfd_status mfd_step_timed(mfd_sim* sim, int64_t nsteps, double* ms) {
     }
     ms[0] = h;
     ms[1] = e;
-    return MFD_OK;
+    return bounds_status(sim->ctx->stream);
 }
 
 mfd_status mfd_read_probes(mfd_sim* sim, double* host, int64_t* steps) {
@@ -1009,7 +1052,7 @@ mfd_status mfd_energy(mfd_sim* sim, double* u) {
     MFD_CUDA(cudaGetLastError());
     MFD_CUDA(cudaMemcpyAsync(u, sim->energy_out.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
     MFD_CUDA(cudaStreamSynchronize(ctx->stream));
-    return MFD_OK;
+    return bounds_status(ctx->stream);
 }
 
 int64_t mfd_sim_steps(const mfd_sim* sim) { return sim ? sim->steps : -1; }
@@ -1206,12 +1249,69 @@ mfd_status mfd_sim_autotune(mfd_sim* sim, int reps, int* chosen) {
     return MFD_OK;
 }
 
-mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, double* g_eps, double* g_amp) {
-    if (!sim || nsteps < 1 || every < 0 || !J || !g_eps) return fail(MFD_ERR_ARG, "bad arguments");
-    if (sim->layout != COLLOC2D) return fail(MFD_ERR_ARG, "mfd_grad supports the collocated 2D layout");
-    if (sim->nsrc > 0 && !g_amp) return fail(MFD_ERR_ARG, "g_amp is NULL");
+}  // extern "C"
+
+// The gradient of the probe objective in two halves (mfd_grad_forward records,
+// mfd_grad_backward sweeps); mfd_grad runs both.
+struct mfd_tape {
+    mfd_sim* sim = nullptr;
+    int64_t nsteps = 0, G = 0, nseg = 0, start = 0, end = 0;
+    bool whole = false, used = false;
+    size_t sbytes = 0;
+    double J = 0;
+    DevBuf ckpt, fin, hist, Jd;
+    std::vector<int64_t> starts, slots;  // host sources of async copies: valid while the tape lives
+};
+
+namespace {
+
+template <typename Body>
+mfd_status capture_graph(mfd_sim* sim, cudaStream_t s, Body&& body, cudaGraphExec_t* out) {
+    const int64_t steps0 = sim->steps;
+    MFD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = body();
+    cudaGraph_t gr = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &gr);
+    sim->steps = steps0;  // the captured steps have not run
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        cudaGetLastError();
+        return fail(MFD_ERR_CUDA, std::string("gradient graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(out, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return fail(MFD_ERR_CUDA, std::string("gradient graph instantiate: ") + cudaGetErrorString(e));
+    return MFD_OK;
+}
+
+struct GraphGuard {
+    cudaGraphExec_t g = nullptr;
+    ~GraphGuard() {
+        if (g) cudaGraphExecDestroy(g);
+    }
+};
+
+__global__ void k_to_caller(const double* __restrict__ v, const int64_t* __restrict__ perm, int64_t n,
+                            double* __restrict__ out) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n) out[perm[k]] = v[k];
+}
+
+__global__ void k_count_nonpositive(const double* __restrict__ v, int64_t n, unsigned long long* __restrict__ bad) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n && !(v[k] > 0.0)) atomicAdd(bad, 1ull);
+}
+
+}  // namespace
+
+extern "C" {
+
+mfd_status mfd_grad_forward(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, mfd_tape** out) {
+    if (!sim || nsteps < 1 || every < 0 || !J || !out) return fail(MFD_ERR_ARG, "bad arguments");
+    *out = nullptr;
+    if (sim->layout != COLLOC2D) return fail(MFD_ERR_ARG, "the gradient supports the collocated 2D layout");
     if (sim->nprobe < 1 || sim->probe_cap < nsteps)
-        return fail(MFD_ERR_STATE, "mfd_grad needs probes with capacity >= nsteps (mfd_set_probes)");
+        return fail(MFD_ERR_STATE, "the gradient needs probes with capacity >= nsteps (mfd_set_probes)");
     mfd_ctx* ctx = sim->ctx;
     MFD_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t s = ctx->stream;
@@ -1222,6 +1322,12 @@ mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, doub
         MFD_TRY(adj_build(ctx, sim->d.h_curl, sim->d.h_hv, f64, sim->adj));
         sim->adj_ok = true;
     }
+    mfd_tape* tp = new (std::nothrow) mfd_tape();
+    if (!tp) return fail(MFD_ERR_OOM, "host allocation failed");
+    std::unique_ptr<mfd_tape> guard(tp);
+    mfd_tape& T = *tp;
+    T.sim = sim;
+    T.nsteps = nsteps;
     // The step is linear in the fields, so the adjoint needs the forward run only
     // through Ez of every level (the permittivity gradient). With every == 0 that
     // history is kept whole when it fits in a quarter of the free device memory
@@ -1230,75 +1336,47 @@ mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, doub
     // its checkpoint in the backward sweep.
     size_t free_b = 0, total_b = 0;
     MFD_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    const bool whole = every == 0 && (size_t)(nsteps + 1) * n * rs <= free_b / 4;
+    T.whole = every == 0 && (size_t)(nsteps + 1) * n * rs <= free_b / 4;
     if (every == 0) every = 64;
-    const int64_t G = whole ? 64 : every;  // steps per captured segment
-    const int64_t nseg = (nsteps + G - 1) / G;
-    const size_t sbytes = (size_t)n * 4 * rs;
-    DevBuf ckpt, fin, hist, LA, LB, geps, gamp, Jd, seg0, slot0;
-    if (!whole) {
-        MFD_TRY(ckpt.alloc((size_t)nseg * sbytes));
-        MFD_TRY(fin.alloc(sbytes));
+    T.G = T.whole ? 64 : every;  // steps per captured segment
+    T.nseg = (nsteps + T.G - 1) / T.G;
+    T.sbytes = (size_t)n * 4 * rs;
+    if (!T.whole) {
+        MFD_TRY(T.ckpt.alloc((size_t)T.nseg * T.sbytes));
+        MFD_TRY(T.fin.alloc(T.sbytes));
     }
-    MFD_TRY(hist.alloc((size_t)((whole ? nsteps : every) + 1) * n * rs));
-    MFD_TRY(LA.alloc(sbytes));
-    MFD_TRY(LB.alloc(sbytes));
-    MFD_TRY(geps.alloc((size_t)n * 8));
-    MFD_TRY(gamp.alloc(std::max(1, sim->nsrc) * 8));
-    MFD_TRY(Jd.alloc(8));
-    MFD_TRY(seg0.alloc(8));
-    MFD_TRY(slot0.alloc(8));
-    MFD_CUDA(cudaMemsetAsync(geps.p, 0, geps.bytes, s));
-    MFD_CUDA(cudaMemsetAsync(gamp.p, 0, gamp.bytes, s));
+    MFD_TRY(T.hist.alloc((size_t)((T.whole ? nsteps : every) + 1) * n * rs));
+    MFD_TRY(T.Jd.alloc(8));
     const int64_t start = sim->steps;
+    T.start = start;
+    T.end = start + nsteps;
     // probes record from the first step of this call
     sim->probe_from = start;
-    MFD_CUDA(cudaMemcpyAsync(sim->pstep0.p, &start, 8, cudaMemcpyHostToDevice, s));
-    MFD_CUDA(cudaMemcpyAsync(sim->counter.p, &start, 8, cudaMemcpyHostToDevice, s));
-    std::vector<int64_t> starts(nseg), slots(nseg);  // host sources of async copies: valid until the end
-    for (int64_t g = 0; g < nseg; ++g) {
-        starts[g] = start + g * G;
-        slots[g] = whole ? g * G : 0;
+    MFD_CUDA(cudaMemcpyAsync(sim->pstep0.p, &T.start, 8, cudaMemcpyHostToDevice, s));
+    MFD_CUDA(cudaMemcpyAsync(sim->counter.p, &T.start, 8, cudaMemcpyHostToDevice, s));
+    T.starts.resize(T.nseg);
+    T.slots.resize(T.nseg);
+    for (int64_t g = 0; g < T.nseg; ++g) {
+        T.starts[g] = start + g * T.G;
+        T.slots[g] = T.whole ? g * T.G : 0;
     }
-    struct GraphGuard {
-        cudaGraphExec_t g = nullptr;
-        ~GraphGuard() {
-            if (g) cudaGraphExecDestroy(g);
-        }
-    } gfwd, grec, gadj;
-    auto capture = [&](auto&& body, cudaGraphExec_t* out) -> mfd_status {
-        const int64_t steps0 = sim->steps;
-        MFD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = body();
-        cudaGraph_t gr = nullptr;
-        cudaError_t e2 = cudaStreamEndCapture(s, &gr);
-        sim->steps = steps0;  // the captured steps have not run
-        if (e != cudaSuccess || e2 != cudaSuccess) {
-            if (gr) cudaGraphDestroy(gr);
-            cudaGetLastError();
-            return fail(MFD_ERR_CUDA, std::string("gradient graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
-        }
-        e = cudaGraphInstantiate(out, gr, 0);
-        cudaGraphDestroy(gr);
-        if (e != cudaSuccess) return fail(MFD_ERR_CUDA, std::string("gradient graph instantiate: ") + cudaGetErrorString(e));
-        return MFD_OK;
-    };
-    // ---- forward
-    if (whole) {
+    if (T.whole) {
         // every step also writes its Ez level into the history (level = counter - start)
-        MFD_CUDA(copy_ez(f64, sim->s0.p, hist.p, n, s));
+        MFD_CUDA(copy_ez(f64, sim->s0.p, T.hist.p, n, s));
         auto fwd = [&](int64_t len) -> cudaError_t {
             cudaError_t e = cudaSuccess;
             for (int64_t k = 0; k < len && e == cudaSuccess; ++k) {
                 e = enqueue_step(sim, nullptr);
-                if (e == cudaSuccess) e = copy_ez_level(f64, sim->s0.p, hist.p, n, sim->counter.as<int64_t>(), start, s);
+                if (e == cudaSuccess)
+                    e = copy_ez_level(f64, sim->s0.p, T.hist.p, n, sim->counter.as<int64_t>(), start, s);
             }
             return e;
         };
-        for (int64_t g = 0; g < nseg; ++g) {
-            const int64_t len = std::min(G, nsteps - g * G);
-            if (len == G && nseg >= 2) {
-                if (!gfwd.g) MFD_TRY(capture([&] { return fwd(len); }, &gfwd.g));
+        GraphGuard gfwd;
+        for (int64_t g = 0; g < T.nseg; ++g) {
+            const int64_t len = std::min(T.G, nsteps - g * T.G);
+            if (len == T.G && T.nseg >= 2) {
+                if (!gfwd.g) MFD_TRY(capture_graph(sim, s, [&] { return fwd(len); }, &gfwd.g));
                 MFD_CUDA(cudaGraphLaunch(gfwd.g, s));
                 sim->steps += len;
             } else {
@@ -1307,13 +1385,49 @@ mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, doub
         }
     } else {
         // a checkpoint of the full state at the start of every segment
-        for (int64_t g = 0; g < nseg; ++g) {
-            MFD_CUDA(cudaMemcpyAsync((char*)ckpt.p + g * sbytes, sim->s0.p, sbytes, cudaMemcpyDeviceToDevice, s));
-            MFD_TRY(mfd_step(sim, std::min(G, nsteps - g * G)));
+        for (int64_t g = 0; g < T.nseg; ++g) {
+            MFD_CUDA(cudaMemcpyAsync((char*)T.ckpt.p + g * T.sbytes, sim->s0.p, T.sbytes, cudaMemcpyDeviceToDevice, s));
+            MFD_TRY(mfd_step(sim, std::min(T.G, nsteps - g * T.G)));
         }
-        MFD_CUDA(cudaMemcpyAsync(fin.p, sim->s0.p, sbytes, cudaMemcpyDeviceToDevice, s));
+        MFD_CUDA(cudaMemcpyAsync(T.fin.p, sim->s0.p, T.sbytes, cudaMemcpyDeviceToDevice, s));
     }
-    MFD_CUDA(probe_energy(f64, sim->probe_buf.p, nsteps * sim->nprobe, sim->d.dt, Jd.as<double>(), s));
+    MFD_CUDA(probe_energy(f64, sim->probe_buf.p, nsteps * sim->nprobe, sim->d.dt, T.Jd.as<double>(), s));
+    MFD_CUDA(cudaMemcpyAsync(&T.J, T.Jd.p, 8, cudaMemcpyDeviceToHost, s));
+    MFD_CUDA(cudaStreamSynchronize(s));
+    *J = T.J;
+    MFD_TRY(bounds_status(s));
+    *out = guard.release();
+    return MFD_OK;
+}
+
+mfd_status mfd_grad_backward(mfd_tape* tape, double* g_eps, double* g_amp, int on_device, void* stream) {
+    if (!tape || !g_eps) return fail(MFD_ERR_ARG, "bad arguments");
+    mfd_tape& T = *tape;
+    mfd_sim* sim = T.sim;
+    if (T.used) return fail(MFD_ERR_STATE, "this tape's adjoint sweep has run already");
+    if (sim->nsrc > 0 && !g_amp) return fail(MFD_ERR_ARG, "g_amp is NULL");
+    if (sim->steps != T.end)
+        return fail(MFD_ERR_STATE, "the simulation was stepped or reset after mfd_grad_forward");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    const bool f64 = sim->fp64;
+    const size_t rs = sim->rs;
+    const int64_t n = sim->ne;
+    const int64_t nsteps = T.nsteps, start = T.start, G = T.G, nseg = T.nseg;
+    const bool whole = T.whole;
+    const size_t sbytes = T.sbytes;
+    if (on_device) MFD_TRY(order_streams((cudaStream_t)stream, s));  // the caller is done with the outputs
+    DevBuf LA, LB, geps, gamp, seg0, slot0, gcall;
+    MFD_TRY(LA.alloc(sbytes));
+    MFD_TRY(LB.alloc(sbytes));
+    MFD_TRY(geps.alloc((size_t)n * 8));
+    MFD_TRY(gamp.alloc(std::max(1, sim->nsrc) * 8));
+    MFD_TRY(seg0.alloc(8));
+    MFD_TRY(slot0.alloc(8));
+    MFD_CUDA(cudaMemsetAsync(geps.p, 0, geps.bytes, s));
+    MFD_CUDA(cudaMemsetAsync(gamp.p, 0, gamp.bytes, s));
+    DevBuf& hist = T.hist;
     // lambda^N: dJ/dE^N at the probes, zero elsewhere
     MFD_CUDA(init_lambda(f64, LA.p, sim->s0.p, n, s));
     // Ez^N: the last level of the whole history, or staged in level 0 of the segment buffer
@@ -1399,41 +1513,116 @@ mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, doub
         }
         return e;
     };
+    T.used = true;
+    GraphGuard grec, gadj;
     for (int64_t g = nseg - 1; g >= 0; --g) {
         const int64_t len = std::min(G, nsteps - g * G);
-        MFD_CUDA(cudaMemcpyAsync(seg0.p, &starts[g], 8, cudaMemcpyHostToDevice, s));
-        MFD_CUDA(cudaMemcpyAsync(slot0.p, &slots[g], 8, cudaMemcpyHostToDevice, s));
+        MFD_CUDA(cudaMemcpyAsync(seg0.p, &T.starts[g], 8, cudaMemcpyHostToDevice, s));
+        MFD_CUDA(cudaMemcpyAsync(slot0.p, &T.slots[g], 8, cudaMemcpyHostToDevice, s));
         const bool graphs = len == G && nseg >= 2;
         if (!whole) {
-            MFD_CUDA(cudaMemcpyAsync(sim->s0.p, (char*)ckpt.p + g * sbytes, sbytes, cudaMemcpyDeviceToDevice, s));
-            MFD_CUDA(cudaMemcpyAsync(sim->counter.p, &starts[g], 8, cudaMemcpyHostToDevice, s));
-            sim->steps = starts[g];
+            MFD_CUDA(cudaMemcpyAsync(sim->s0.p, (char*)T.ckpt.p + g * sbytes, sbytes, cudaMemcpyDeviceToDevice, s));
+            MFD_CUDA(cudaMemcpyAsync(sim->counter.p, &T.starts[g], 8, cudaMemcpyHostToDevice, s));
+            sim->steps = T.starts[g];
             if (graphs) {
-                if (!grec.g) MFD_TRY(capture([&] { return recompute(len); }, &grec.g));
+                if (!grec.g) MFD_TRY(capture_graph(sim, s, [&] { return recompute(len); }, &grec.g));
                 MFD_CUDA(cudaGraphLaunch(grec.g, s));
             } else {
                 MFD_CUDA(recompute(len));
             }
         }
         if (graphs) {
-            if (!gadj.g) MFD_TRY(capture([&] { return sweep(len); }, &gadj.g));
+            if (!gadj.g) MFD_TRY(capture_graph(sim, s, [&] { return sweep(len); }, &gadj.g));
             MFD_CUDA(cudaGraphLaunch(gadj.g, s));
         } else {
             MFD_CUDA(sweep(len));
         }
     }
     // leave the simulation where a plain run of nsteps would
-    const int64_t end = start + nsteps;
-    if (!whole) MFD_CUDA(cudaMemcpyAsync(sim->s0.p, fin.p, sbytes, cudaMemcpyDeviceToDevice, s));
-    MFD_CUDA(cudaMemcpyAsync(sim->counter.p, &end, 8, cudaMemcpyHostToDevice, s));
-    sim->steps = end;
+    if (!whole) MFD_CUDA(cudaMemcpyAsync(sim->s0.p, T.fin.p, sbytes, cudaMemcpyDeviceToDevice, s));
+    MFD_CUDA(cudaMemcpyAsync(sim->counter.p, &T.end, 8, cudaMemcpyHostToDevice, s));
+    sim->steps = T.end;
+    sim->adj_sweeps += 1;
+    if (on_device) {
+        const unsigned gr = (unsigned)((n + 255) / 256);
+        k_to_caller<<<gr, 256, 0, s>>>(geps.as<double>(), sim->eset->perm.as<int64_t>(), n, g_eps);
+        MFD_CUDA(cudaGetLastError());
+        if (sim->nsrc > 0) MFD_CUDA(cudaMemcpyAsync(g_amp, gamp.p, sim->nsrc * 8, cudaMemcpyDeviceToDevice, s));
+        MFD_TRY(bounds_status(s));
+        MFD_TRY(order_streams(s, (cudaStream_t)stream));
+        // the temporaries are released at return (cudaFree waits for the queued work)
+        return MFD_OK;
+    }
     std::vector<double> gd(n);
     MFD_CUDA(cudaMemcpyAsync(gd.data(), geps.p, n * 8, cudaMemcpyDeviceToHost, s));
-    MFD_CUDA(cudaMemcpyAsync(J, Jd.p, 8, cudaMemcpyDeviceToHost, s));
     if (sim->nsrc > 0) MFD_CUDA(cudaMemcpyAsync(g_amp, gamp.p, sim->nsrc * 8, cudaMemcpyDeviceToHost, s));
     MFD_CUDA(cudaStreamSynchronize(s));
     for (int64_t k = 0; k < n; ++k) g_eps[sim->eset->h_perm[k]] = gd[k];
+    return bounds_status(s);
+}
+
+void mfd_tape_destroy(mfd_tape* tape) {
+    if (!tape) return;
+    cudaSetDevice(tape->sim->ctx->device);
+    cudaStreamSynchronize(tape->sim->ctx->stream);
+    delete tape;
+}
+
+mfd_status mfd_grad(mfd_sim* sim, int64_t nsteps, int64_t every, double* J, double* g_eps, double* g_amp) {
+    if (!sim || nsteps < 1 || every < 0 || !J || !g_eps) return fail(MFD_ERR_ARG, "bad arguments");
+    if (sim->nsrc > 0 && !g_amp) return fail(MFD_ERR_ARG, "g_amp is NULL");
+    mfd_tape* tape = nullptr;
+    MFD_TRY(mfd_grad_forward(sim, nsteps, every, J, &tape));
+    const mfd_status st = mfd_grad_backward(tape, g_eps, g_amp, 0, nullptr);
+    mfd_tape_destroy(tape);
+    return st;
+}
+
+int64_t mfd_sim_adjoint_sweeps(const mfd_sim* sim) { return sim ? sim->adj_sweeps : -1; }
+
+mfd_status mfd_probe_objective(mfd_sim* sim, double* J) {
+    if (!sim || !J) return fail(MFD_ERR_ARG, "NULL argument");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    int64_t rec = std::min(sim->steps - sim->probe_from, sim->probe_cap);
+    if (rec < 0 || sim->nprobe == 0) rec = 0;
+    MFD_CUDA(probe_energy(sim->fp64, sim->probe_buf.p, rec * sim->nprobe, sim->d.dt, sim->energy_out.as<double>(),
+                          ctx->stream));
+    MFD_CUDA(cudaMemcpyAsync(J, sim->energy_out.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    MFD_CUDA(cudaStreamSynchronize(ctx->stream));
     return MFD_OK;
+}
+
+mfd_status mfd_set_materials_device(mfd_sim* sim, const double* eps_r, const uint8_t* pec, void* stream) {
+    if (!sim) return fail(MFD_ERR_ARG, "sim is NULL");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    MFD_TRY(order_streams((cudaStream_t)stream, ctx->stream));  // the values are ready on the caller's stream
+    const int64_t ne = sim->ne;
+    const unsigned g = (unsigned)((ne + 255) / 256);
+    if (eps_r) {
+        DevBuf bad;
+        MFD_TRY(bad.alloc(8));
+        MFD_CUDA(cudaMemsetAsync(bad.p, 0, 8, ctx->stream));
+        k_count_nonpositive<<<g, 256, 0, ctx->stream>>>(eps_r, ne, bad.as<unsigned long long>());
+        MFD_CUDA(cudaGetLastError());
+        unsigned long long nb = 0;
+        MFD_CUDA(cudaMemcpyAsync(&nb, bad.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+        MFD_CUDA(cudaStreamSynchronize(ctx->stream));
+        if (nb) return fail(MFD_ERR_ARG, "eps_r must be > 0");
+    }
+    MFD_TRY(apply_materials(sim, eps_r, pec));
+    return order_streams(ctx->stream, (cudaStream_t)stream);
+}
+
+mfd_status mfd_set_source_amps_device(mfd_sim* sim, const double* amp, void* stream) {
+    if (!sim || (!amp && sim->nsrc > 0)) return fail(MFD_ERR_ARG, "NULL argument");
+    mfd_ctx* ctx = sim->ctx;
+    MFD_CUDA(cudaSetDevice(ctx->device));
+    MFD_TRY(order_streams((cudaStream_t)stream, ctx->stream));
+    if (sim->nsrc > 0)
+        MFD_CUDA(cudaMemcpyAsync(sim->src_amp.p, amp, sim->nsrc * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    return order_streams(ctx->stream, (cudaStream_t)stream);
 }
 
 void mfd_sim_destroy(mfd_sim* sim) {

@@ -52,4 +52,10 @@ cudaError_t launch_3d(const Launch3D& L, int pass, cudaStream_t st);
 cudaError_t launch_energy_3d(const Launch3D& L, const double* eps_r, double eta2, double* partial, unsigned grid,
                              cudaStream_t st);
 
+// stencil indices the bounds-checked build found out of range in each file's
+// kernels since the last call (0 in the default build)
+unsigned long long bounds_take_step2d(cudaStream_t s);
+unsigned long long bounds_take_step3d(cudaStream_t s);
+unsigned long long bounds_take_adjoint(cudaStream_t s);
+
 }  // namespace mfd

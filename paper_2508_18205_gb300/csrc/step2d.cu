@@ -42,7 +42,7 @@ __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const 
         const V4* pv = s.wv + slice * nv * 32 + lane;
 #pragma unroll
         for (int c = part; c < (act ? ni : 0); c += P) {
-            const int4 id = ld_stream(ip + c * 32);
+            const int4 id = chk4(ld_stream(ip + c * 32), s.src_c);
             V4 wx, wy, wv;
             if (c < nc) {
                 wx = ld_stream(px + c * 32);
@@ -69,7 +69,7 @@ __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const 
         const V4* pv = s.wv + slice * nv * 32 + lane;
 #pragma unroll
         for (int c = part; c < (act ? nc : 0); c += P) {
-            const int4 id = ld_stream(ic + c * 32);
+            const int4 id = chk4(ld_stream(ic + c * 32), s.src_c);
             const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32);
             const T f0 = ld_gather(A + id.x).x, f1 = ld_gather(A + id.y).x;
             const T f2 = ld_gather(A + id.z).x, f3 = ld_gather(A + id.w).x;
@@ -78,7 +78,7 @@ __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const 
         }
 #pragma unroll
         for (int c = part; c < (act ? nv : 0); c += P) {
-            const int4 id = ld_stream(iv + c * 32);
+            const int4 id = chk4(ld_stream(iv + c * 32), s.src_v);
             const V4 wv = ld_stream(pv + c * 32);
             const V4 f0 = ld_gather(A + id.x), f1 = ld_gather(A + id.y);
             const V4 f2 = ld_gather(A + id.z), f3 = ld_gather(A + id.w);
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(512) k_e_colloc(StencilStreams<T> s, const typ
     Acc dxHy, dyHx;
 #pragma unroll
     for (int c = part; c < (act ? nc : 0); c += P) {
-        const int4 id = ld_stream(ip + c * 32);
+        const int4 id = chk4(ld_stream(ip + c * 32), s.src_c);
         const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32);
         const V4 f0 = ld_gather(B + id.x), f1 = ld_gather(B + id.y);
         const V4 f2 = ld_gather(B + id.z), f3 = ld_gather(B + id.w);
@@ -218,14 +218,14 @@ __device__ __forceinline__ void h_stag_node(const StencilStreams<T>& s, const T*
     AccV hx, hy;
     // HV sums first: their H gathers are the larger share of the pass's loads, and issuing them
     // first measured 4 % faster than curl-first (the sums themselves do not depend on the order)
-    for_idx4<NV>(nv, slice, lane, s.idx_v, s.q_v, s.qb_v, [&](int c, int4 id) {
+    for_idx4<NV>(nv, slice, lane, s.idx_v, s.q_v, s.qb_v, s.src_v, [&](int c, int4 id) {
         const V4 wv = ld_stream(pv + c * 32);
         const V2 f0 = ld_gather(H + id.x), f1 = ld_gather(H + id.y);
         const V2 f2 = ld_gather(H + id.z), f3 = ld_gather(H + id.w);
         hx.add(wv.x, f0.x); hx.add(wv.y, f1.x); hx.add(wv.z, f2.x); hx.add(wv.w, f3.x);
         hy.add(wv.x, f0.y); hy.add(wv.y, f1.y); hy.add(wv.z, f2.y); hy.add(wv.w, f3.y);
     });
-    for_idx4<NC>(nc, slice, lane, s.idx_c, s.q_c, s.qb_c, [&](int c, int4 id) {
+    for_idx4<NC>(nc, slice, lane, s.idx_c, s.q_c, s.qb_c, s.src_c, [&](int c, int4 id) {
         const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32);
         const T f0 = ld_gather(Ez + id.x), f1 = ld_gather(Ez + id.y);
         const T f2 = ld_gather(Ez + id.z), f3 = ld_gather(Ez + id.w);
@@ -272,14 +272,14 @@ __global__ void __launch_bounds__(512) k_e_stag(StencilStreams<T> s, Coefs<T> k,
     const V4* pv = s.wv + slice * nv * 32 + lane;
     Acc dxHy, dyHx;
     AccPlain<T> he;
-    for_idx4<NC>(nc, slice, lane, s.idx_c, s.q_c, s.qb_c, [&](int c, int4 id) {
+    for_idx4<NC>(nc, slice, lane, s.idx_c, s.q_c, s.qb_c, s.src_c, [&](int c, int4 id) {
         const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32);
         const V2 f0 = ld_gather(Hn + id.x), f1 = ld_gather(Hn + id.y);
         const V2 f2 = ld_gather(Hn + id.z), f3 = ld_gather(Hn + id.w);
         dxHy.add(wx.x, f0.y); dxHy.add(wx.y, f1.y); dxHy.add(wx.z, f2.y); dxHy.add(wx.w, f3.y);
         dyHx.add(wy.x, f0.x); dyHx.add(wy.y, f1.x); dyHx.add(wy.z, f2.x); dyHx.add(wy.w, f3.x);
     });
-    for_idx4<NV>(nv, slice, lane, s.idx_v, s.q_v, s.qb_v, [&](int c, int4 id) {
+    for_idx4<NV>(nv, slice, lane, s.idx_v, s.q_v, s.qb_v, s.src_v, [&](int c, int4 id) {
         const V4 wv = ld_stream(pv + c * 32);
         const T f0 = ld_gather(Ez + id.x), f1 = ld_gather(Ez + id.y);
         const T f2 = ld_gather(Ez + id.z), f3 = ld_gather(Ez + id.w);
@@ -419,5 +419,7 @@ cudaError_t launch_energy_2d(const Launch2D& L, const double* eps_r, int64_t ne,
     }
     return cudaGetLastError();
 }
+
+unsigned long long bounds_take_step2d(cudaStream_t s) { return bounds_take_local(s); }
 
 }  // namespace mfd

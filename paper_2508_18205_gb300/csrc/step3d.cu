@@ -64,7 +64,7 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
         const int4* ip = s.idx_c + slice * ni * 32 + lane;
 #pragma unroll
         for (int c = 0; c < ni; ++c) {
-            const int4 id = ld_stream(ip + c * 32);
+            const int4 id = chk4(ld_stream(ip + c * 32), s.src_c);
             V4 e[4], h[4];
             if (c < nv) {
                 ld_gather_eh(F + 2 * (int64_t)id.x, e[0], h[0]);
@@ -85,7 +85,7 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
         const int4* iv = s.idx_v + slice * nv * 32 + lane;
 #pragma unroll
         for (int c = 0; c < nc; ++c) {
-            const int4 id = ld_stream(ic + c * 32);
+            const int4 id = chk4(ld_stream(ic + c * 32), s.src_c);
             V4 e[4];
             e[0] = ld_gather(F + 2 * (int64_t)id.x);
             e[1] = ld_gather(F + 2 * (int64_t)id.y);
@@ -95,7 +95,7 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
         }
 #pragma unroll
         for (int c = 0; c < nv; ++c) {
-            const int4 id = ld_stream(iv + c * 32);
+            const int4 id = chk4(ld_stream(iv + c * 32), s.src_v);
             V4 e[4], h[4];
             ld_gather_eh(F + 2 * (int64_t)id.x, e[0], h[0]);
             ld_gather_eh(F + 2 * (int64_t)id.y, e[1], h[1]);
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(512, 2) k_e3(StencilStreams<T> s, const typena
     Acc a_yz, a_zy, a_zx, a_xz, a_xy, a_yx;
 #pragma unroll
     for (int c = 0; c < nc; ++c) {
-        const int4 id = ld_stream(ip + c * 32);
+        const int4 id = chk4(ld_stream(ip + c * 32), s.src_c);
         const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32), wz = ld_stream(pz + c * 32);
         V4 f[4];
         f[0] = ld_gather(Hn + id.x);
@@ -274,5 +274,7 @@ cudaError_t launch_energy_3d(const Launch3D& L, const double* eps_r, double eta2
         k_energy3<float, false><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.F, eps_r, eta2, partial);
     return cudaGetLastError();
 }
+
+unsigned long long bounds_take_step3d(cudaStream_t s) { return bounds_take_local(s); }
 
 }  // namespace mfd

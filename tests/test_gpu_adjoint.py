@@ -109,6 +109,64 @@ def test_autograd_function_returns_adjoint_gradients():
     assert np.allclose(a.grad.numpy(), 3.0 * ga)
 
 
+def test_autograd_on_device_tensors_and_no_grad_forward():
+    """CUDA tensors in and out (zero copy): the gradient equals mfd_grad's bit for
+    bit; under torch.no_grad() (or without requires_grad) the forward pass records
+    no tape and no adjoint sweep runs, and J is the same."""
+    torch = pytest.importorskip("torch")
+    ctx = M.Ctx(0)
+    nodes = W.pec_box((18, 18), 0.25, 97)
+    src, probes, eps, ez, hx, hy = _setup(nodes, 98)
+    for prec in (1, 0):
+        sim = _problem(ctx, nodes, prec)
+        obj = M.ProbeObjective(sim, nodes.pec, {M.MFD_EZ: ez, M.MFD_HX: hx, M.MFD_HY: hy}, src, probes, 50, 0)
+        J_ref, ge_ref, ga_ref = obj.run(eps, src.amp)
+        sweeps = sim.adjoint_sweeps
+        e = torch.tensor(eps, dtype=torch.float64, device="cuda", requires_grad=True)
+        a = torch.tensor(src.amp, dtype=torch.float64, device="cuda", requires_grad=True)
+        with torch.no_grad():
+            J0 = M.probe_energy(e, a, obj)
+        assert obj.last_forward_taped is False and sim.adjoint_sweeps == sweeps
+        J1 = M.probe_energy(e.detach(), a.detach(), obj)
+        assert obj.last_forward_taped is False and sim.adjoint_sweeps == sweeps
+        J = M.probe_energy(e, a, obj)
+        assert obj.last_forward_taped is True and sim.adjoint_sweeps == sweeps  # forward only so far
+        J.backward()
+        assert sim.adjoint_sweeps == sweeps + 1
+        assert e.grad.is_cuda and a.grad.is_cuda
+        for Jx in (J0, J1, J):
+            assert abs(float(Jx) - J_ref) <= 1e-12 * abs(J_ref)
+        assert np.array_equal(e.grad.cpu().numpy(), ge_ref)
+        assert np.array_equal(a.grad.cpu().numpy(), ga_ref)
+
+
+def test_tape_sweeps_once_and_refuses_a_moved_simulation():
+    ctx = M.Ctx(0)
+    nodes = W.pec_box((14, 14), 0.25, 99)
+    src, probes, eps, ez, hx, hy = _setup(nodes, 100)
+    sim = _problem(ctx, nodes, 1)
+    obj = M.ProbeObjective(sim, nodes.pec, {M.MFD_EZ: ez, M.MFD_HX: hx, M.MFD_HY: hy}, src, probes, 20, 0)
+    lib = M.lib()
+    import ctypes as C
+    ge = np.zeros(nodes.n)
+    ga = np.zeros(len(src.node))
+    for moved in (False, True):
+        J, tape = obj.forward(eps, src.amp, True)
+        if moved:
+            sim.step(1)
+            st = lib.mfd_grad_backward(tape, C.c_void_p(ge.ctypes.data), C.c_void_p(ga.ctypes.data), 0, None)
+            assert st == M.MFD_ERR_STATE
+        else:
+            assert lib.mfd_grad_backward(tape, C.c_void_p(ge.ctypes.data), C.c_void_p(ga.ctypes.data), 0, None) == 0
+            st = lib.mfd_grad_backward(tape, C.c_void_p(ge.ctypes.data), C.c_void_p(ga.ctypes.data), 0, None)
+            assert st == M.MFD_ERR_STATE
+        lib.mfd_tape_destroy(tape)
+    J2, ge2, ga2 = obj.run(eps, src.amp)
+    J3, tape = obj.forward(eps, src.amp, True)
+    ge3, ga3 = obj.backward(tape, "cpu")
+    assert J3 == J2 and np.array_equal(ge3.numpy(), ge2) and np.array_equal(ga3.numpy(), ga2)
+
+
 def test_full_config_adjoint_fp32_fp64_and_finite_differences():
     """250k nodes (500 x 500 PEC box), n = 20, 4000 steps, checkpoints every 64 steps."""
     ctx = M.Ctx(0)

@@ -37,8 +37,8 @@ def _domains(ctx, specs):
     return doms, keep
 
 
-@pytest.mark.parametrize("R", [16, 4, 32])
-def test_batch_matches_single_rhs_oracle(R):
+@pytest.mark.parametrize("R,variant", [(16, 0), (16, 1), (4, 0), (32, 1)])
+def test_batch_matches_single_rhs_oracle(R, variant):
     ctx = M.Ctx(0)
     dt, eps0, mu0, c0, eta0 = W.units(S)
     specs = [(W.pec_box((30, 30), 0.25, 1), 12), (W.disk(15.0, 0.25, 2), 20),
@@ -48,6 +48,8 @@ def test_batch_matches_single_rhs_oracle(R):
         specs = specs[:2]
     doms, keep = _domains(ctx, specs)
     bt = M.Batch(ctx, doms, nrhs=R)
+    bt.set_variant(variant)
+    assert bt.variant == variant
     nsteps = 150
     rng = np.random.default_rng(R)
     init, srcs, probes = [], [], []
@@ -110,4 +112,46 @@ def test_batch_repeated_steps_continue():
             bt.step(80)
         out.append([bt.get_field(d, M.MFD_EZ) for d in range(len(specs))])
     for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("R", [16, 8])
+def test_variants_are_bit_identical_and_autotune_leaves_the_state(R):
+    """Both kernel variants (stream prefetch with three resident blocks per SM,
+    and no prefetch with four) take every stencil sum in the same order: the
+    fields, probes and energies agree bit for bit. The autotuner times both and
+    puts the fields, probes and step count back."""
+    ctx = M.Ctx(0)
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    specs = [(W.pec_box((26, 22), 0.25, 11), 12), (W.disk(13.0, 0.25, 12), 30), (W.pec_box((17, 17), 0.25, 13), 40),
+             (W.disk(8.0, 0.25, 14), 20)]
+    doms, keep = _domains(ctx, specs)
+    runs = []
+    for variant in (0, 1):
+        bt = M.Batch(ctx, doms, nrhs=R)
+        bt.set_variant(variant)
+        for d, (ns, n) in enumerate(specs):
+            bt.set_materials(d, W.eps_r_uniform(ns.n, 20 + d), ns.pec)
+            src = W.ricker_sources(ns, R, 30 + d, c0, nrhs=R, one_per_rhs=True)
+            bt.set_sources(d, src.node, src.rhs, src.amp, src.f0, src.t0)
+            bt.set_probes(d, W.interior_nodes(ns, 3, 40 + d), 200)
+        bt.step(70)
+        if variant == 1:
+            before = [bt.get_field(d, c) for d in range(len(specs)) for c in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)]
+            probes_before = bt.read_probes(0)
+            chosen, ms = bt.autotune(5)
+            assert chosen in (0, 1) and bt.variant == chosen and np.all(ms > 0)
+            after = [bt.get_field(d, c) for d in range(len(specs)) for c in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)]
+            for x, y in zip(before, after):
+                assert np.array_equal(x, y)
+            assert np.array_equal(bt.read_probes(0), probes_before)
+            bt.set_variant(1)
+        bt.step(50)
+        runs.append(([bt.get_field(d, c) for d in range(len(specs)) for c in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)],
+                     [bt.read_probes(d) for d in range(len(specs))], [bt.energy(d) for d in range(len(specs))]))
+    for a, b in zip(runs[0][0], runs[1][0]):
+        assert np.array_equal(a, b)
+    for a, b in zip(runs[0][1], runs[1][1]):
+        assert a.shape[0] == 120 and np.array_equal(a, b)
+    for a, b in zip(runs[0][2], runs[1][2]):
         assert np.array_equal(a, b)

@@ -22,17 +22,26 @@ torch = pytest.importorskip("torch")
 M = pytest.importorskip("paper_2508_18205_gb300")
 
 
-def _static_knn(ns, n):
+def _static_knn(ns, n, centres=None, period=True, check_free=False):
+    """The static-scratch kNN of the centres (default: the source set itself)
+    among the nodes of ns; with check_free, the free device memory reported by
+    the driver is the same before and after the call."""
     dev = torch.device("cuda", 0)
-    xyz = torch.from_numpy(np.ascontiguousarray(ns.xyz)).to(dev)
-    out = torch.full((ns.n, n), -1, dtype=torch.int32, device=dev)
+    xs = torch.from_numpy(np.ascontiguousarray(ns.xyz)).to(dev)
+    xc = xs if centres is None else torch.from_numpy(np.ascontiguousarray(centres)).to(dev)
+    nc = xc.shape[0]
+    out = torch.full((nc, n), -1, dtype=torch.int32, device=dev)
     per = np.ascontiguousarray(ns.period, dtype=np.float64)
     stream = torch.cuda.current_stream(dev).cuda_stream
-    st = M.lib().mfd_knn_static(ns.dim, ns.n, C.c_void_p(xyz.data_ptr()), ns.n, C.c_void_p(xyz.data_ptr()),
-                                per.ctypes.data_as(C.c_void_p), n, C.c_void_p(out.data_ptr()),
-                                C.c_void_p(stream))
+    torch.cuda.synchronize(dev)
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    st = M.lib().mfd_knn_static(ns.dim, nc, C.c_void_p(xc.data_ptr()), ns.n, C.c_void_p(xs.data_ptr()),
+                                per.ctypes.data_as(C.c_void_p) if period else None, n,
+                                C.c_void_p(out.data_ptr()), C.c_void_p(stream))
     M._ck(st)
     torch.cuda.synchronize(dev)
+    if check_free:
+        assert torch.cuda.mem_get_info(dev)[0] == free0
     return out.cpu().numpy().astype(np.int64)
 
 
@@ -49,6 +58,31 @@ def test_static_knn_matches_allocating_entry_point_twice():
     b = _static_knn(second, 40)
     assert np.array_equal(a, _allocating_knn(ctx, first, 31))
     assert np.array_equal(b, _allocating_knn(ctx, second, 40))
+
+
+def test_static_knn_allocates_nothing_and_covers_separate_centres_and_no_period():
+    """After a first call has loaded the kernels, a call leaves the free device
+    memory unchanged; centres other than the sources (a staggered set), and a
+    non-periodic set passed with period = NULL, give the allocating entry
+    point's stencils."""
+    ctx = M.Ctx(0)
+    e = W.periodic_box((40, 40), 0.25, 63)
+    h = W.periodic_box((40, 40), 0.25, 64, offset=(0.5, 0.5))
+    _static_knn(e, 30)  # loads the kernels
+    got = _static_knn(e, 30, centres=h.xyz, check_free=True)
+    ne, nh = M.Nodes(ctx, e.xyz, e.period), M.Nodes(ctx, h.xyz, h.period)
+    assert np.array_equal(got, M.Stencils(nh, ne, 30).read())
+    box = W.pec_box((30, 26), 0.25, 65)
+    got = _static_knn(box, 12, period=False, check_free=True)
+    assert np.array_equal(got, _allocating_knn(ctx, box, 12))
+
+
+def test_static_knn_rejects_periodic_coordinates_outside_the_period():
+    ns = W.periodic_box((20, 20), 0.25, 66)
+    bad = W.NodeSet(xyz=ns.xyz + np.array([20.0, 0.0]), pec=ns.pec, period=ns.period, box_lo=ns.box_lo,
+                    box_hi=ns.box_hi)
+    with pytest.raises(M.MfdError, match="period"):
+        _static_knn(bad, 12)
 
 
 def test_static_knn_rejects_oversized_source_sets():
