@@ -455,3 +455,109 @@ def max3d_sample_step(nodes, e_ids, n, phs_k, m, alpha, dt, eps0, mu0, gamma, E,
                                     C.c_double(dt), C.c_double(eps0), C.c_double(mu0), C.c_double(gamma),
                                     _p(E), _p(H), _p(H1), _p(E1)), "3d_sample_step")
     return E1, H1, hs
+
+
+# ------------------------------------------------------------------ PEC walls by images
+
+def mirror_doubled(nodes, axes=None):
+    """The PEC box as a periodic box of twice its size (image theory of a perfect
+    conductor): every node of `nodes` (a pec_box on [0, L] per axis) and, for
+    every non-empty subset r of the mirrored axes (bit a = axis a), its image
+    with x_a -> 2 L - x_a for a in r, skipping the images that fall on the node
+    itself (a wall node is its own image). The period is 2 L on the mirrored
+    axes. Nodes come first in their own order, then the images by (r, node id).
+    Returns (NodeSet of the doubled box, orig (node id of each entry), code (r of
+    each entry))."""
+    import workloads as W
+    d = nodes.dim
+    L = np.asarray(nodes.box_hi, dtype=np.float64) - np.asarray(nodes.box_lo, dtype=np.float64)
+    if axes is None:
+        axes = (1 << d) - 1
+    x = _f64(nodes.xyz)
+    n = len(x)
+    pts, orig, code = [x], [np.arange(n)], [np.zeros(n, np.int64)]
+    for r in range(1, 1 << d):
+        if r & ~axes:
+            continue
+        keep = np.ones(n, bool)
+        y = x.copy()
+        for a in range(d):
+            if (r >> a) & 1:
+                keep &= (x[:, a] > 0.0) & (x[:, a] < L[a])
+                y[:, a] = 2.0 * L[a] - x[:, a]
+        pts.append(y[keep])
+        orig.append(np.nonzero(keep)[0])
+        code.append(np.full(int(keep.sum()), r, np.int64))
+    per = np.array([2.0 * L[a] if (axes >> a) & 1 else 0.0 for a in range(d)])
+    xyz = np.concatenate(pts)
+    # no component is held at the walls: the mirror symmetry of the extension is
+    # the boundary condition (holding the tangential E of the wall nodes at 0 on
+    # top of it makes the scheme grow)
+    ns = W.NodeSet(xyz=xyz, pec=np.zeros(len(xyz), np.uint8), period=per, box_lo=np.zeros(d),
+                   box_hi=np.where(per > 0, per, L), normal_axes=np.zeros(len(xyz), np.uint8))
+    return ns, np.concatenate(orig), np.concatenate(code)
+
+
+def image_sign_tmz(code, comp):
+    """Sign of an image of TMz field `comp` ('ez', 'hx', 'hy') across the walls of
+    code r: Ez is tangential to every wall (odd across each), Hx normal to the x
+    walls (odd across them, even across the y walls), Hy normal to the y walls."""
+    code = np.asarray(code)
+    if comp == "ez":
+        k = (code & 1) + ((code >> 1) & 1)
+    elif comp == "hx":
+        k = code & 1
+    else:
+        k = (code >> 1) & 1
+    return 1.0 - 2.0 * (k & 1)
+
+
+def image_sign_3d(code, field, b):
+    """Sign of an image of component b of E or H across the walls of code r:
+    E_b is odd across every wall it is tangential to (axes a != b), H_b across
+    the wall it is normal to (axis b)."""
+    code = np.asarray(code)
+    if field == "e":
+        m = code & ~(1 << b) & 7
+        k = (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1)
+    else:
+        k = (code >> b) & 1
+    return 1.0 - 2.0 * (k & 1)
+
+
+def run_tmz_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, ez, hx, hy, nsteps, eps_r=None,
+                   sources=None, probes=None, energy=False):
+    """Eq. 19 on a PEC box with image stencils: the collocated problem on the
+    doubled periodic box (mirror_doubled) with the fields extended by their
+    parities; returns the box's (ez, hx, hy, probes, energy of the doubled box)."""
+    dbl, orig, code = mirror_doubled(nodes)
+    er = None if eps_r is None else _f64(eps_r)[orig]
+    prob, _ = tmz_collocated(dbl, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=er)
+    f = [_f64(v)[orig] * image_sign_tmz(code, c) for v, c in ((ez, "ez"), (hx, "hx"), (hy, "hy"))]
+    src = None
+    if sources is not None:
+        # a soft source at a node drives its images with the field's sign
+        import workloads as W
+        sel = np.isin(orig, sources.node)
+        ids = np.nonzero(sel)[0]
+        k = np.searchsorted(sources.node, orig[ids]) if np.all(np.diff(sources.node) > 0) else \
+            np.array([list(sources.node).index(o) for o in orig[ids]])
+        src = W.Sources(node=ids, rhs=np.zeros(len(ids), np.int64),
+                        amp=sources.amp[k] * image_sign_tmz(code[ids], "ez"), f0=sources.f0[k], t0=sources.t0[k])
+    e1, x1, y1, pr, en = run_tmz(prob, *f, nsteps, sources=src, probes=probes, energy=energy)
+    nb = nodes.n
+    return e1[:nb], x1[:nb], y1[:nb], pr, en
+
+
+def run_3d_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, E, H, nsteps, eps_r=None, energy=False):
+    """The 3D step on a PEC box with image stencils (see run_tmz_images)."""
+    dbl, orig, code = mirror_doubled(nodes)
+    er = None if eps_r is None else _f64(eps_r)[orig]
+    prob, _ = max3d_collocated(dbl, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=er)
+    E = _f64(E)
+    H = _f64(H)
+    Ed = np.stack([E[b][orig] * image_sign_3d(code, "e", b) for b in range(3)])
+    Hd = np.stack([H[b][orig] * image_sign_3d(code, "h", b) for b in range(3)])
+    E1, H1, _, en = run_3d(prob, Ed, Hd, nsteps, energy=energy)
+    nb = nodes.n
+    return E1[:, :nb], H1[:, :nb], en
