@@ -154,10 +154,13 @@ def ricker(t, f0, t0):
 
 @dataclass
 class Stencil:
-    """Stencil of one operator family: idx (N x n, ids into the source set) and weights."""
+    """Stencil of one operator family: idx (N x n, ids into the source set) and
+    weights; code (N x n uint8, or None): image codes of the entries (PEC walls
+    by images: bit a = the mirror image across the walls normal to axis a)."""
 
     idx: np.ndarray
     w: np.ndarray  # (nout, N, n)
+    code: np.ndarray | None = None
 
 
 @dataclass
@@ -260,9 +263,14 @@ def run_tmz(p: TMz, ez, hx, hy, nsteps, step0=0, sources=None, probes=None, ener
     pr = np.zeros(0, np.int64) if probes is None else _i64(probes)
     pout = np.zeros((nsteps, len(pr)))
     eout = np.zeros(nsteps) if energy else None
-    _check(lib().orc_run_tmz(*args, _p(ez), _p(hx), _p(hy), C.c_int64(step0), C.c_int64(nsteps),
-                             C.c_int(len(sn)), _p(sn), _p(sa), _p(sf), _p(st0), C.c_int(len(pr)),
-                             _p(pr), _p(pout), _p(eout)), "run_tmz")
+    tail = [_p(ez), _p(hx), _p(hy), C.c_int64(step0), C.c_int64(nsteps), C.c_int(len(sn)), _p(sn), _p(sa),
+            _p(sf), _p(st0), C.c_int(len(pr)), _p(pr), _p(pout), _p(eout)]
+    if any(st.code is not None for st in (p.hc, p.hv, p.ec, p.ev)):
+        codes = [None if st.code is None else np.ascontiguousarray(st.code, dtype=np.uint8)
+                 for st in (p.hc, p.hv, p.ec, p.ev)]
+        _check(lib().orc_run_tmz_img(*args, *tail, *[_p(c) for c in codes]), "run_tmz_img")
+    else:
+        _check(lib().orc_run_tmz(*args, *tail), "run_tmz")
     del keep
     return ez, hx, hy, pout, eout
 
@@ -330,9 +338,9 @@ class Max3D:
     gamma: float
 
 
-def max3d_collocated(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=None):
+def max3d_collocated(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=None, nh_override=None):
     import math
-    nhv = 2 * math.comb(2 * alpha + 3, 3) + 1
+    nhv = nh_override or (2 * math.comb(2 * alpha + 3, 3) + 1)
     L = max(n, nhv)
     idx = knn(nodes.xyz, nodes.xyz, nodes.period, L)
     c = _stencil(nodes.xyz, nodes.xyz, nodes.period, idx, n, phs_k, m, OP_GRAD)
@@ -357,13 +365,16 @@ def run_3d(p: Max3D, E, H, nsteps, step0=0, sources=None, probes=None, energy=Fa
     pr = np.zeros(0, np.int64) if probes is None else _i64(probes)
     pout = np.zeros((nsteps, len(pr)))
     eout = np.zeros(nsteps) if energy else None
-    _check(lib().orc_run_3d(C.c_int64(p.n), C.c_int(p.c.idx.shape[1]), _p(p.c.idx), _p(w[0]),
-                            _p(w[1]), _p(w[2]), C.c_int(p.v.idx.shape[1]), _p(p.v.idx), _p(wv),
-                            _p(p.eps_r), _p(p.wall), C.c_double(p.dt), C.c_double(p.eps0),
-                            C.c_double(p.mu0), C.c_double(p.gamma), _p(E), _p(H),
-                            C.c_int64(step0), C.c_int64(nsteps), C.c_int(len(sn)), _p(sn), _p(sa),
-                            _p(sf), _p(st0), C.c_int(len(pr)), _p(pr), _p(pout), _p(eout)),
-           "run_3d")
+    args = [C.c_int64(p.n), C.c_int(p.c.idx.shape[1]), _p(p.c.idx), _p(w[0]), _p(w[1]), _p(w[2]),
+            C.c_int(p.v.idx.shape[1]), _p(p.v.idx), _p(wv), _p(p.eps_r), _p(p.wall), C.c_double(p.dt),
+            C.c_double(p.eps0), C.c_double(p.mu0), C.c_double(p.gamma), _p(E), _p(H), C.c_int64(step0),
+            C.c_int64(nsteps), C.c_int(len(sn)), _p(sn), _p(sa), _p(sf), _p(st0), C.c_int(len(pr)), _p(pr),
+            _p(pout), _p(eout)]
+    if p.c.code is not None or p.v.code is not None:
+        codes = [None if st.code is None else np.ascontiguousarray(st.code, dtype=np.uint8) for st in (p.c, p.v)]
+        _check(lib().orc_run_3d_img(*args, *[_p(c) for c in codes]), "run_3d_img")
+    else:
+        _check(lib().orc_run_3d(*args), "run_3d")
     return E, H, pout, eout
 
 
@@ -525,39 +536,58 @@ def image_sign_3d(code, field, b):
     return 1.0 - 2.0 * (k & 1)
 
 
+def image_stencils(nodes, L_use):
+    """The L_use nearest of every node of a PEC box among the nodes and their
+    mirror images (the doubled box of mirror_doubled). Returns (doubled box,
+    ids into it, node id and image code of every doubled entry)."""
+    dbl, orig, code = mirror_doubled(nodes)
+    ids = knn(nodes.xyz, dbl.xyz, dbl.period, L_use)
+    return dbl, ids, orig, code
+
+
+def _image_stencil(nodes, dbl, ids, orig, code, n_use, phs_k, m, op, alpha=0):
+    w = weights(nodes.xyz, dbl.xyz, dbl.period, ids, n_use, phs_k, m, op, alpha)
+    sub = ids[:, :n_use]
+    return Stencil(idx=np.ascontiguousarray(orig[sub]), w=w, code=np.ascontiguousarray(code[sub], dtype=np.uint8))
+
+
+def tmz_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=None, nh_override=None):
+    """Collocated TMz problem of a PEC box with image stencils: every stencil
+    entry is a node of the box or its mirror image (node id and code); the
+    weights are those of the image positions; no component is held at the
+    walls (the symmetry is the boundary condition)."""
+    import math
+    nhv = nh_override or (2 * math.comb(2 * alpha + 2, 2) + 1)
+    dbl, ids, orig, code = image_stencils(nodes, max(n, nhv))
+    curl = _image_stencil(nodes, dbl, ids, orig, code, n, phs_k, m, OP_GRAD)
+    hv = _image_stencil(nodes, dbl, ids, orig, code, nhv, 2 * alpha + 1, 2 * alpha, OP_LAP_POW, alpha)
+    er = np.ones(nodes.n) if eps_r is None else _f64(eps_r)
+    return TMz(nh=nodes.n, ne=nodes.n, hc=curl, hv=hv, ec=curl, ev=hv, eps_r=er,
+               pec=np.zeros(nodes.n, np.uint8), dt=dt, eps0=eps0, mu0=mu0, gamma=gamma)
+
+
+def max3d_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=None, nh_override=None):
+    """The 3D collocated problem of a PEC box with image stencils (see tmz_images)."""
+    import math
+    nhv = nh_override or (2 * math.comb(2 * alpha + 3, 3) + 1)
+    dbl, ids, orig, code = image_stencils(nodes, max(n, nhv))
+    c = _image_stencil(nodes, dbl, ids, orig, code, n, phs_k, m, OP_GRAD)
+    v = _image_stencil(nodes, dbl, ids, orig, code, nhv, 2 * alpha + 1, 2 * alpha, OP_LAP_POW, alpha)
+    er = np.ones(nodes.n) if eps_r is None else _f64(eps_r)
+    return Max3D(n=nodes.n, c=c, v=v, eps_r=er, wall=np.zeros(nodes.n, np.uint8), dt=dt, eps0=eps0, mu0=mu0,
+                 gamma=gamma)
+
+
 def run_tmz_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, ez, hx, hy, nsteps, eps_r=None,
-                   sources=None, probes=None, energy=False):
-    """Eq. 19 on a PEC box with image stencils: the collocated problem on the
-    doubled periodic box (mirror_doubled) with the fields extended by their
-    parities; returns the box's (ez, hx, hy, probes, energy of the doubled box)."""
-    dbl, orig, code = mirror_doubled(nodes)
-    er = None if eps_r is None else _f64(eps_r)[orig]
-    prob, _ = tmz_collocated(dbl, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=er)
-    f = [_f64(v)[orig] * image_sign_tmz(code, c) for v, c in ((ez, "ez"), (hx, "hx"), (hy, "hy"))]
-    src = None
-    if sources is not None:
-        # a soft source at a node drives its images with the field's sign
-        import workloads as W
-        sel = np.isin(orig, sources.node)
-        ids = np.nonzero(sel)[0]
-        k = np.searchsorted(sources.node, orig[ids]) if np.all(np.diff(sources.node) > 0) else \
-            np.array([list(sources.node).index(o) for o in orig[ids]])
-        src = W.Sources(node=ids, rhs=np.zeros(len(ids), np.int64),
-                        amp=sources.amp[k] * image_sign_tmz(code[ids], "ez"), f0=sources.f0[k], t0=sources.t0[k])
-    e1, x1, y1, pr, en = run_tmz(prob, *f, nsteps, sources=src, probes=probes, energy=energy)
-    nb = nodes.n
-    return e1[:nb], x1[:nb], y1[:nb], pr, en
+                   sources=None, probes=None, energy=False, nh_override=None):
+    """Eq. 19 on a PEC box with image stencils (tmz_images): (ez, hx, hy, probes, energy)."""
+    prob = tmz_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r, nh_override)
+    return run_tmz(prob, ez, hx, hy, nsteps, sources=sources, probes=probes, energy=energy)
 
 
-def run_3d_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, E, H, nsteps, eps_r=None, energy=False):
-    """The 3D step on a PEC box with image stencils (see run_tmz_images)."""
-    dbl, orig, code = mirror_doubled(nodes)
-    er = None if eps_r is None else _f64(eps_r)[orig]
-    prob, _ = max3d_collocated(dbl, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=er)
-    E = _f64(E)
-    H = _f64(H)
-    Ed = np.stack([E[b][orig] * image_sign_3d(code, "e", b) for b in range(3)])
-    Hd = np.stack([H[b][orig] * image_sign_3d(code, "h", b) for b in range(3)])
-    E1, H1, _, en = run_3d(prob, Ed, Hd, nsteps, energy=energy)
-    nb = nodes.n
-    return E1[:, :nb], H1[:, :nb], en
+def run_3d_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, E, H, nsteps, eps_r=None, energy=False,
+                  nh_override=None):
+    """The 3D step on a PEC box with image stencils (max3d_images): (E, H, energy)."""
+    prob = max3d_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r, nh_override)
+    E1, H1, _, en = run_3d(prob, E, H, nsteps, energy=energy)
+    return E1, H1, en

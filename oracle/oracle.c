@@ -485,6 +485,40 @@ static double orc_apply(int n, const int64_t* idx, const double* w, const double
 }
 
 /*
+ * PEC walls by images: entry j of a stencil may be the mirror image of node
+ * idx[j] across the walls normal to the axes of code[j] (bit a). A perfect
+ * conductor flips the tangential E and the normal H under the reflection and
+ * keeps the normal E and the tangential H, so the gathered value enters with
+ * that sign. kind: 0 Ez (TMz, tangential to every wall), 1 Hx, 2 Hy (TMz);
+ * 3 + b the 3D E_b, 6 + b the 3D H_b. code == NULL: no images (orc_apply).
+ */
+static int orc_img_odd(unsigned r, int kind)
+{
+    unsigned m;
+    if (kind == 0) m = r & 3u;
+    else if (kind == 1) m = r & 1u;
+    else if (kind == 2) m = r & 2u;
+    else if (kind < 6) m = r & (7u & ~(1u << (kind - 3)));
+    else m = r & (1u << (kind - 6));
+    int k = 0;
+    for (; m; m >>= 1) k += (int)(m & 1u);
+    return k & 1;
+}
+
+static double orc_apply_img(int n, const int64_t* idx, const uint8_t* code, const double* w, const double* f,
+                            int kind)
+{
+    if (!code) return orc_apply(n, idx, w, f);
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double v = f[idx[j]];
+        if (code[j] && orc_img_odd(code[j], kind)) v = -v;
+        s += w[j] * v;
+    }
+    return s;
+}
+
+/*
  * TMz leapfrog (Eq. 19) on an H node set and an E node set. The collocated
  * method passes the same set twice (the paper's method); the staggered layout
  * passes two distinct sets.
@@ -497,7 +531,7 @@ static double orc_apply(int n, const int64_t* idx, const double* w, const double
  *   Ez[src] += amp r(t_{n+1}); Ez[pec] = 0; probes record Ez^{n+1}.
  * energy (optional, nsteps values): Eq. 20 at t_n, H averaged over n -+ 1/2.
  */
-int orc_run_tmz(int64_t nh, int nhc, const int64_t* hc_idx, const double* hc_wx, const double* hc_wy,
+static int orc_run_tmz_k(int64_t nh, int nhc, const int64_t* hc_idx, const double* hc_wx, const double* hc_wy,
                 int nhv, const int64_t* hv_idx, const double* hv_w,
                 int64_t ne, int nec, const int64_t* ec_idx, const double* ec_wx, const double* ec_wy,
                 int nev, const int64_t* ev_idx, const double* ev_w,
@@ -506,7 +540,9 @@ int orc_run_tmz(int64_t nh, int nhc, const int64_t* hc_idx, const double* hc_wx,
                 double* ez, double* hx, double* hy, int64_t step0, int64_t nsteps,
                 int nsrc, const int64_t* src_node, const double* src_amp, const double* src_f0,
                 const double* src_t0, int nprobe, const int64_t* probe_node, double* probe_out,
-                double* energy_out)
+                double* energy_out,
+                          const uint8_t* hc_code, const uint8_t* hv_code, const uint8_t* ec_code,
+                          const uint8_t* ev_code)
 {
     double* hx1 = (double*)malloc(sizeof(double) * nh);
     double* hy1 = (double*)malloc(sizeof(double) * nh);
@@ -519,10 +555,10 @@ int orc_run_tmz(int64_t nh, int nhc, const int64_t* hc_idx, const double* hc_wx,
         /* H half step: H^{n+1/2} from E^n and H^{n-1/2} */
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < nh; ++i) {
-            double dyE = orc_apply(nhc, hc_idx + i * nhc, hc_wy + i * nhc, ez);
-            double dxE = orc_apply(nhc, hc_idx + i * nhc, hc_wx + i * nhc, ez);
-            double vx = orc_apply(nhv, hv_idx + i * nhv, hv_w + i * nhv, hx);
-            double vy = orc_apply(nhv, hv_idx + i * nhv, hv_w + i * nhv, hy);
+            double dyE = orc_apply_img(nhc, hc_idx + i * nhc, hc_code ? hc_code + i * nhc : 0, hc_wy + i * nhc, ez, 0);
+            double dxE = orc_apply_img(nhc, hc_idx + i * nhc, hc_code ? hc_code + i * nhc : 0, hc_wx + i * nhc, ez, 0);
+            double vx = orc_apply_img(nhv, hv_idx + i * nhv, hv_code ? hv_code + i * nhv : 0, hv_w + i * nhv, hx, 1);
+            double vy = orc_apply_img(nhv, hv_idx + i * nhv, hv_code ? hv_code + i * nhv : 0, hv_w + i * nhv, hy, 2);
             hx1[i] = hx[i] - ch * (dyE - gamma * vx);
             hy1[i] = hy[i] + ch * (dxE + gamma * vy);
         }
@@ -539,9 +575,9 @@ int orc_run_tmz(int64_t nh, int nhc, const int64_t* hc_idx, const double* hc_wx,
         /* E half step: E^{n+1} from H^{n+1/2} and E^n */
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < ne; ++i) {
-            double dxH = orc_apply(nec, ec_idx + i * nec, ec_wx + i * nec, hy1);
-            double dyH = orc_apply(nec, ec_idx + i * nec, ec_wy + i * nec, hx1);
-            double ve = orc_apply(nev, ev_idx + i * nev, ev_w + i * nev, ez);
+            double dxH = orc_apply_img(nec, ec_idx + i * nec, ec_code ? ec_code + i * nec : 0, ec_wx + i * nec, hy1, 2);
+            double dyH = orc_apply_img(nec, ec_idx + i * nec, ec_code ? ec_code + i * nec : 0, ec_wy + i * nec, hx1, 1);
+            double ve = orc_apply_img(nev, ev_idx + i * nev, ev_code ? ev_code + i * nev : 0, ev_w + i * nev, ez, 0);
             double er = eps_r ? eps_r[i] : 1.0;
             ez1[i] = ez[i] + dt / (eps0 * er) * (dxH - dyH + gamma * ve);
         }
@@ -561,6 +597,41 @@ int orc_run_tmz(int64_t nh, int nhc, const int64_t* hc_idx, const double* hc_wx,
     return ORC_OK;
 }
 
+int orc_run_tmz(int64_t nh, int nhc, const int64_t* hc_idx, const double* hc_wx, const double* hc_wy,
+                int nhv, const int64_t* hv_idx, const double* hv_w,
+                int64_t ne, int nec, const int64_t* ec_idx, const double* ec_wx, const double* ec_wy,
+                int nev, const int64_t* ev_idx, const double* ev_w,
+                const double* eps_r, const uint8_t* pec,
+                double dt, double eps0, double mu0, double gamma,
+                double* ez, double* hx, double* hy, int64_t step0, int64_t nsteps,
+                int nsrc, const int64_t* src_node, const double* src_amp, const double* src_f0,
+                const double* src_t0, int nprobe, const int64_t* probe_node, double* probe_out,
+                double* energy_out)
+{
+    return orc_run_tmz_k(nh, nhc, hc_idx, hc_wx, hc_wy, nhv, hv_idx, hv_w, ne, nec, ec_idx, ec_wx, ec_wy, nev,
+                         ev_idx, ev_w, eps_r, pec, dt, eps0, mu0, gamma, ez, hx, hy, step0, nsteps, nsrc,
+                         src_node, src_amp, src_f0, src_t0, nprobe, probe_node, probe_out, energy_out, 0, 0, 0, 0);
+}
+
+/* orc_run_tmz with image codes per stencil entry (PEC walls by images): the
+ * code arrays have the shapes of the index arrays; NULL = no images there */
+int orc_run_tmz_img(int64_t nh, int nhc, const int64_t* hc_idx, const double* hc_wx, const double* hc_wy,
+                int nhv, const int64_t* hv_idx, const double* hv_w,
+                int64_t ne, int nec, const int64_t* ec_idx, const double* ec_wx, const double* ec_wy,
+                int nev, const int64_t* ev_idx, const double* ev_w,
+                const double* eps_r, const uint8_t* pec,
+                double dt, double eps0, double mu0, double gamma,
+                double* ez, double* hx, double* hy, int64_t step0, int64_t nsteps,
+                int nsrc, const int64_t* src_node, const double* src_amp, const double* src_f0,
+                const double* src_t0, int nprobe, const int64_t* probe_node, double* probe_out,
+                double* energy_out,
+                    const uint8_t* hc_code, const uint8_t* hv_code, const uint8_t* ec_code, const uint8_t* ev_code)
+{
+    return orc_run_tmz_k(nh, nhc, hc_idx, hc_wx, hc_wy, nhv, hv_idx, hv_w, ne, nec, ec_idx, ec_wx, ec_wy, nev,
+                         ev_idx, ev_w, eps_r, pec, dt, eps0, mu0, gamma, ez, hx, hy, step0, nsteps, nsrc,
+                         src_node, src_amp, src_f0, src_t0, nprobe, probe_node, probe_out, energy_out, hc_code, hv_code, ec_code, ev_code);
+}
+
 /*
  * 3D full-vector leapfrog, collocated (Eq. 2 with the hyperviscosity terms of
  * Eqs. 17-18 on every component):
@@ -572,14 +643,15 @@ int orc_run_tmz(int64_t nh, int nhc, const int64_t* hc_idx, const double* hc_wx,
  * sits on is zeroed (wall mask bit a = wall normal to axis a), then probes
  * record Ez.
  */
-int orc_run_3d(int64_t N, int nc, const int64_t* c_idx, const double* wx, const double* wy,
+static int orc_run_3d_k(int64_t N, int nc, const int64_t* c_idx, const double* wx, const double* wy,
                const double* wz, int nv, const int64_t* v_idx, const double* wv,
                const double* eps_r, const uint8_t* wall_mask,
                double dt, double eps0, double mu0, double gamma,
                double* E /* 3 x N */, double* H /* 3 x N */, int64_t step0, int64_t nsteps,
                int nsrc, const int64_t* src_node, const double* src_amp, const double* src_f0,
                const double* src_t0, int nprobe, const int64_t* probe_node, double* probe_out,
-               double* energy_out)
+               double* energy_out,
+                         const uint8_t* c_code, const uint8_t* v_code)
 {
     double* H1 = (double*)malloc(sizeof(double) * 3 * N);
     double* E1 = (double*)malloc(sizeof(double) * 3 * N);
@@ -592,13 +664,14 @@ int orc_run_3d(int64_t N, int nc, const int64_t* c_idx, const double* wx, const 
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < N; ++i) {
             const int64_t* ci = c_idx + i * nc;
-            double dyEz = orc_apply(nc, ci, wy + i * nc, Ez), dzEy = orc_apply(nc, ci, wz + i * nc, Ey);
-            double dzEx = orc_apply(nc, ci, wz + i * nc, Ex), dxEz = orc_apply(nc, ci, wx + i * nc, Ez);
-            double dxEy = orc_apply(nc, ci, wx + i * nc, Ey), dyEx = orc_apply(nc, ci, wy + i * nc, Ex);
+            const uint8_t* cc = c_code ? c_code + i * nc : 0;
+            double dyEz = orc_apply_img(nc, ci, cc, wy + i * nc, Ez, 5), dzEy = orc_apply_img(nc, ci, cc, wz + i * nc, Ey, 4);
+            double dzEx = orc_apply_img(nc, ci, cc, wz + i * nc, Ex, 3), dxEz = orc_apply_img(nc, ci, cc, wx + i * nc, Ez, 5);
+            double dxEy = orc_apply_img(nc, ci, cc, wx + i * nc, Ey, 4), dyEx = orc_apply_img(nc, ci, cc, wy + i * nc, Ex, 3);
             double cx = dyEz - dzEy, cy = dzEx - dxEz, cz = dxEy - dyEx;
             const int64_t* vi = v_idx + i * nv;
             for (int a = 0; a < 3; ++a) {
-                double vh = orc_apply(nv, vi, wv + i * nv, H + a * N);
+                double vh = orc_apply_img(nv, vi, v_code ? v_code + i * nv : 0, wv + i * nv, H + a * N, 6 + a);
                 double c = (a == 0) ? cx : (a == 1) ? cy : cz;
                 H1[a * N + i] = H[a * N + i] + ch * (-c + gamma * vh);
             }
@@ -618,14 +691,15 @@ int orc_run_3d(int64_t N, int nc, const int64_t* c_idx, const double* wx, const 
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < N; ++i) {
             const int64_t* ci = c_idx + i * nc;
-            double dyHz = orc_apply(nc, ci, wy + i * nc, Hz1), dzHy = orc_apply(nc, ci, wz + i * nc, Hy1);
-            double dzHx = orc_apply(nc, ci, wz + i * nc, Hx1), dxHz = orc_apply(nc, ci, wx + i * nc, Hz1);
-            double dxHy = orc_apply(nc, ci, wx + i * nc, Hy1), dyHx = orc_apply(nc, ci, wy + i * nc, Hx1);
+            const uint8_t* cc = c_code ? c_code + i * nc : 0;
+            double dyHz = orc_apply_img(nc, ci, cc, wy + i * nc, Hz1, 8), dzHy = orc_apply_img(nc, ci, cc, wz + i * nc, Hy1, 7);
+            double dzHx = orc_apply_img(nc, ci, cc, wz + i * nc, Hx1, 6), dxHz = orc_apply_img(nc, ci, cc, wx + i * nc, Hz1, 8);
+            double dxHy = orc_apply_img(nc, ci, cc, wx + i * nc, Hy1, 7), dyHx = orc_apply_img(nc, ci, cc, wy + i * nc, Hx1, 6);
             double cx = dyHz - dzHy, cy = dzHx - dxHz, cz = dxHy - dyHx;
             const int64_t* vi = v_idx + i * nv;
             double er = eps_r ? eps_r[i] : 1.0;
             for (int a = 0; a < 3; ++a) {
-                double ve = orc_apply(nv, vi, wv + i * nv, E + a * N);
+                double ve = orc_apply_img(nv, vi, v_code ? v_code + i * nv : 0, wv + i * nv, E + a * N, 3 + a);
                 double c = (a == 0) ? cx : (a == 1) ? cy : cz;
                 E1[a * N + i] = E[a * N + i] + dt / (eps0 * er) * (c + gamma * ve);
             }
@@ -648,6 +722,34 @@ int orc_run_3d(int64_t N, int nc, const int64_t* c_idx, const double* wx, const 
     free(H1);
     free(E1);
     return ORC_OK;
+}
+
+int orc_run_3d(int64_t N, int nc, const int64_t* c_idx, const double* wx, const double* wy,
+               const double* wz, int nv, const int64_t* v_idx, const double* wv,
+               const double* eps_r, const uint8_t* wall_mask,
+               double dt, double eps0, double mu0, double gamma,
+               double* E /* 3 x N */, double* H /* 3 x N */, int64_t step0, int64_t nsteps,
+               int nsrc, const int64_t* src_node, const double* src_amp, const double* src_f0,
+               const double* src_t0, int nprobe, const int64_t* probe_node, double* probe_out,
+               double* energy_out)
+{
+    return orc_run_3d_k(N, nc, c_idx, wx, wy, wz, nv, v_idx, wv, eps_r, wall_mask, dt, eps0, mu0, gamma, E, H, step0,
+                        nsteps, nsrc, src_node, src_amp, src_f0, src_t0, nprobe, probe_node, probe_out, energy_out, 0, 0);
+}
+
+/* orc_run_3d with image codes per stencil entry (PEC walls by images) */
+int orc_run_3d_img(int64_t N, int nc, const int64_t* c_idx, const double* wx, const double* wy,
+               const double* wz, int nv, const int64_t* v_idx, const double* wv,
+               const double* eps_r, const uint8_t* wall_mask,
+               double dt, double eps0, double mu0, double gamma,
+               double* E /* 3 x N */, double* H /* 3 x N */, int64_t step0, int64_t nsteps,
+               int nsrc, const int64_t* src_node, const double* src_amp, const double* src_f0,
+               const double* src_t0, int nprobe, const int64_t* probe_node, double* probe_out,
+               double* energy_out,
+                   const uint8_t* c_code, const uint8_t* v_code)
+{
+    return orc_run_3d_k(N, nc, c_idx, wx, wy, wz, nv, v_idx, wv, eps_r, wall_mask, dt, eps0, mu0, gamma, E, H, step0,
+                        nsteps, nsrc, src_node, src_amp, src_f0, src_t0, nprobe, probe_node, probe_out, energy_out, c_code, v_code);
 }
 
 /* ------------------------------------------------------------------ O-4 */

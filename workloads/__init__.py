@@ -113,6 +113,22 @@ def pec_box(shape, jitter: float, seed: int) -> NodeSet:
                    normal_axes=normal_axes, meta={"kind": "pec_box", "shape": shape})
 
 
+def pec_box_cells(shape, jitter: float, seed: int) -> NodeSet:
+    """Regular grid of `shape` nodes at the cell centres (i + 1/2) of the box
+    [0, shape[a]] per axis, every node moved by U(-jitter, jitter) per axis;
+    the PEC walls are the box faces, half a spacing beyond the outer layers, so
+    no node sits on a wall (the layout of PEC walls by images)."""
+    shape = tuple(int(s) for s in shape)
+    d = len(shape)
+    xyz = _grid(shape) + 0.5
+    n = xyz.shape[0]
+    u = uniform(seed, n * d).reshape(n, d)
+    xyz = xyz + (2.0 * u - 1.0) * jitter
+    hi = np.array(shape, dtype=np.float64)
+    return NodeSet(xyz=xyz, pec=np.zeros(n, np.uint8), period=np.zeros(d), box_lo=np.zeros(d), box_hi=hi,
+                   normal_axes=np.zeros(n, np.uint8), meta={"kind": "pec_box_cells", "shape": shape})
+
+
 def periodic_box(shape, jitter: float, seed: int, offset=None, seed_line_y=None,
                  seed_diagonal: bool = False) -> NodeSet:
     """Regular grid of `shape` nodes on the periodic box [0, shape[a]) per axis.
