@@ -115,6 +115,24 @@ void mfd_ctx_destroy(mfd_ctx* ctx);
 mfd_status mfd_nodes_create(mfd_ctx* ctx, int dim, int64_t n, const double* xyz,
                             const double* period, mfd_nodes** out);
 int64_t mfd_nodes_count(const mfd_nodes* nodes);
+/* PEC walls by images (a reading: the paper uses periodic boxes only). The
+ * walls of each axis a in `axes` (bit a) are the planes x_a = 0 and
+ * x_a = hi[a], and every node lies strictly between them (for example at the
+ * cell centres of a grid: a node on a mirror plane sees each neighbour and its
+ * image at one distance, and a stencil cut through such a pair is lopsided). A perfect conductor acts as a
+ * mirror: the tangential E and the normal H change sign under the reflection,
+ * the normal E and the tangential H do not, so the box is a periodic box of
+ * period 2 hi[a] holding fields of those parities. Stencils built on this set
+ * (own-set, mfd_stencils_build) take the n nearest among its nodes and their
+ * mirror images x_a -> 2 hi[a] - x_a; an entry
+ * that is an image carries its reflection code r (bit a: reflected across the
+ * walls normal to axis a), the weights are solved at the image positions, and
+ * the step kernels gather an image with the sign of the field's parity. No
+ * component needs holding at the walls (pass no PEC flags): the symmetry is
+ * the boundary condition. Call before building stencils; axes must not be
+ * periodic; fewer than 2^29 nodes. Supported by the collocated 2D and 3D
+ * layouts (not the staggered layout, the batch or the gradient: MFD_ERR_ARG). */
+mfd_status mfd_nodes_set_mirror(mfd_nodes* nodes, uint32_t axes, const double* hi);
 /* perm (host, n): perm[k] = caller id of the k-th node in device order. */
 mfd_status mfd_nodes_permutation(const mfd_nodes* nodes, int64_t* perm);
 void mfd_nodes_destroy(mfd_nodes* nodes);
@@ -131,7 +149,9 @@ void mfd_nodes_destroy(mfd_nodes* nodes);
 mfd_status mfd_stencils_build(const mfd_nodes* centres, const mfd_nodes* sources, int n,
                               mfd_stencils** out);
 /* idx (host, count(centres) x n): caller ids of the stencil nodes, rows in
- * the caller's centre order. */
+ * the caller's centre order; an image entry of a set with mirror walls
+ * (mfd_nodes_set_mirror) is the node's caller id + r * 2^32, r its reflection
+ * code. */
 mfd_status mfd_stencils_read(const mfd_stencils* st, int64_t* idx);
 void mfd_stencils_destroy(mfd_stencils* st);
 

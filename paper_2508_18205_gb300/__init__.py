@@ -124,6 +124,7 @@ _SIGS = {
     "mfd_batch_variant": (_I, [_VP]),
     "mfd_batch_autotune": (_I, [_VP, _I, _VP, _VP]),
     "mfd_build_flags": (_I, []),
+    "mfd_nodes_set_mirror": (_I, [_VP, C.c_uint32, _VP]),
     "mfd_grad_forward": (_I, [_VP, _I64, _I64, _VP, _VP]),
     "mfd_grad_backward": (_I, [_VP, _VP, _VP, _I, _VP]),
     "mfd_tape_destroy": (None, [_VP]),
@@ -327,6 +328,11 @@ class Nodes:
         h = C.c_void_p()
         _ck(lib().mfd_nodes_create(ctx.h, dim, n, _p(xyz), _p(per), C.byref(h)))
         self.h, self.ctx, self.n, self.dim = h, ctx, n, dim
+
+    def set_mirror(self, axes, hi):
+        """PEC walls by images at 0 and hi[a] on the axes of bit mask `axes` (mfd_nodes_set_mirror)."""
+        h = _f64(hi)
+        _ck(lib().mfd_nodes_set_mirror(self.h, int(axes), _p(h)))
 
     def permutation(self):
         out = np.empty(self.n, dtype=np.int64)

@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "kernels.cuh"
 
 namespace mfd {
 
@@ -111,7 +112,8 @@ __global__ void k_rows_to_user(const int32_t* __restrict__ idx, const int64_t* _
     if (e >= nc * n) return;
     int64_t u = e / n;  // caller centre id
     int j = (int)(e % n);
-    out[e] = perm_s[idx[inv_c[u] * n + j]];
+    const int32_t v = idx[inv_c[u] * n + j];  // an image entry carries its reflection code (kernels.cuh)
+    out[e] = perm_s[v & IMG_MASK] + ((int64_t)((unsigned)v >> IMG_SHIFT) << 32);
 }
 
 __global__ void k_w_to_user(const double* __restrict__ w, const int64_t* __restrict__ inv_c, int64_t nc, int n,
@@ -246,6 +248,27 @@ mfd_status mfd_nodes_permutation(const mfd_nodes* nodes, int64_t* perm) {
 
 void mfd_nodes_destroy(mfd_nodes* nodes) { release(nodes); }
 
+mfd_status mfd_nodes_set_mirror(mfd_nodes* nodes, uint32_t axes, const double* hi) {
+    if (!nodes || (axes && !hi)) return fail(MFD_ERR_ARG, "NULL argument");
+    const int dim = nodes->dim;
+    if (axes & ~((1u << dim) - 1u)) return fail(MFD_ERR_ARG, "mirror axes beyond the dimension");
+    if (nodes->n >= ((int64_t)1 << IMG_SHIFT)) return fail(MFD_ERR_ARG, "too many nodes for image codes");
+    std::vector<double> x((size_t)nodes->n * dim);
+    MFD_TRY(use_device(nodes->ctx));
+    MFD_CUDA(cudaMemcpy(x.data(), nodes->xyz.p, x.size() * 8, cudaMemcpyDeviceToHost));
+    for (int a = 0; a < dim; ++a) {
+        if (!((axes >> a) & 1u)) continue;
+        if (nodes->period[a] > 0) return fail(MFD_ERR_ARG, "a mirrored axis cannot be periodic");
+        if (!(hi[a] > 0)) return fail(MFD_ERR_ARG, "mirror walls need hi > 0");
+        for (int64_t i = 0; i < nodes->n; ++i)
+            if (!(x[i * dim + a] > 0.0 && x[i * dim + a] < hi[a]))
+                return fail(MFD_ERR_ARG, "nodes must lie strictly between the mirror walls (0 and hi)");
+    }
+    nodes->mirror_axes = axes;
+    for (int a = 0; a < 3; ++a) nodes->mirror_hi[a] = (a < dim && ((axes >> a) & 1u)) ? hi[a] : 0.0;
+    return MFD_OK;
+}
+
 mfd_status mfd_stencils_build(const mfd_nodes* centres, const mfd_nodes* sources, int n, mfd_stencils** out) {
     if (!centres || !sources || !out) return fail(MFD_ERR_ARG, "NULL argument");
     *out = nullptr;
@@ -261,7 +284,12 @@ mfd_status mfd_stencils_build(const mfd_nodes* centres, const mfd_nodes* sources
     s->sources = sources;
     s->n = n;
     mfd_status st = s->idx.alloc(centres->n * n * 4);
-    if (!st) st = knn_build(centres, sources, n, s->idx.as<int32_t>());
+    if (!st && sources->mirror_axes) {
+        if (centres != sources) st = fail(MFD_ERR_ARG, "stencils with mirror walls are own-set (collocated)");
+        else st = knn_build_mirror(centres, sources, n, s->idx.as<int32_t>());
+    } else if (!st) {
+        st = knn_build(centres, sources, n, s->idx.as<int32_t>());
+    }
     if (st) {
         delete s;
         return st;

@@ -703,6 +703,7 @@ mfd_status mfd_batch_create(mfd_ctx* ctx, int ndom, const mfd_sim_desc* descs, i
         if (cw->op == MFD_OP_LAP_POW || hw->op != MFD_OP_LAP_POW) return bail(fail(MFD_ERR_ARG, "weight operators"));
         const mfd_nodes* nd = cw->st->centres;
         if (cw->st->sources != nd || nd->ctx != ctx) return bail(fail(MFD_ERR_ARG, "stencils must be own-set"));
+        if (nd->mirror_axes) return bail(fail(MFD_ERR_ARG, "batched domains do not support mirror walls (images)"));
         if (!(s.dt > 0) || !(s.eps0 > 0) || !(s.mu0 > 0)) return bail(fail(MFD_ERR_ARG, "dt, eps0, mu0 must be > 0"));
         BatchDomain& D = b->dom[d];
         D.nodes = nd;

@@ -93,6 +93,8 @@ struct mfd_nodes {
     mfd::DevBuf inv;   // int64 [n]: caller id -> device order
     std::vector<int64_t> h_perm;
     std::vector<int64_t> h_inv;
+    uint32_t mirror_axes = 0;        // PEC walls by images on these axes (mfd_nodes_set_mirror)
+    double mirror_hi[3] = {0, 0, 0};  // the walls of mirrored axis a are at 0 and mirror_hi[a]
 };
 
 struct mfd_stencils {
@@ -157,6 +159,8 @@ mfd_status state_head_check(const void* blob, size_t size, int32_t kind, StateHe
 mfd_status morton_order(mfd_ctx* ctx, int dim, int64_t n, const double* d_xyz_user,
                         const double* period, double* d_xyz_sorted, int64_t* d_perm, int64_t* d_inv);
 mfd_status knn_build(const mfd_nodes* centres, const mfd_nodes* sources, int n, int32_t* d_idx);
+// kNN among the nodes of a set with mirror walls and their images (entries carry image codes)
+mfd_status knn_build_mirror(const mfd_nodes* centres, const mfd_nodes* sources, int n, int32_t* d_idx);
 mfd_status weights_solve(const mfd_stencils* st, int n_use, int phs_k, int poly_m, int op, int alpha,
                          double delta, double* d_w);
 // per row of a shared index array (n rows of `stride` entries, len <= 255 used):

@@ -187,6 +187,7 @@ template <typename T> struct StencilStreams {
     int nc = 0, nv = 0, ni = 0;  // chunks per row: curl weights, HV weights, index (shared: max)
     int64_t n = 0;               // nodes
     int64_t src_c = 0, src_v = 0;  // sizes of the node sets the curl and HV indices point into
+    bool mirror = false;           // entries carry image codes (PEC walls by images)
 };
 
 // ---- bounds-checked build (compiled with -DMFD_BOUNDS_CHECK): every stencil
@@ -224,6 +225,46 @@ static inline unsigned long long bounds_take_local(cudaStream_t s) {
     (void)s;
     return 0;
 #endif
+}
+
+// ---- PEC walls by images: an index entry of a node set with mirror walls
+// carries a reflection code r in its top three bits (bit a: the neighbour is the
+// mirror image of node `id` across the walls normal to axis a). A perfect
+// conductor reflects the tangential E and the normal H with a sign change and
+// the normal E and the tangential H without, so a gathered value enters the
+// stencil sum with the sign of its parity under r.
+constexpr int IMG_SHIFT = 29;
+constexpr int IMG_MASK = (1 << IMG_SHIFT) - 1;
+__device__ __forceinline__ float flip(float v, unsigned odd) { return __int_as_float(__float_as_int(v) ^ (int)(odd << 31)); }
+__device__ __forceinline__ double flip(double v, unsigned odd) {
+    return __longlong_as_double(__double_as_longlong(v) ^ (long long)((unsigned long long)odd << 63));
+}
+// splits raw entries into node ids (bounds-checked against n) and codes
+__device__ __forceinline__ int4 img_split(int4 raw, int64_t n, uint4& code) {
+    code = make_uint4((unsigned)raw.x >> IMG_SHIFT, (unsigned)raw.y >> IMG_SHIFT, (unsigned)raw.z >> IMG_SHIFT,
+                      (unsigned)raw.w >> IMG_SHIFT);
+    return chk4(make_int4(raw.x & IMG_MASK, raw.y & IMG_MASK, raw.z & IMG_MASK, raw.w & IMG_MASK), n);
+}
+// TMz {Ez, Hx, Hy, ce}: Ez is tangential to every wall, Hx normal to the x walls, Hy to the y walls
+template <typename V4> __device__ __forceinline__ V4 img_tmz(V4 f, unsigned r) {
+    f.x = flip(f.x, __popc(r & 3u) & 1u);
+    f.y = flip(f.y, r & 1u);
+    f.z = flip(f.z, (r >> 1) & 1u);
+    return f;
+}
+// 3D E block {Ex, Ey, Ez, ce}: E_b is tangential to the walls normal to the other axes
+template <typename V4> __device__ __forceinline__ V4 img_e3(V4 f, unsigned r) {
+    f.x = flip(f.x, __popc(r & 6u) & 1u);
+    f.y = flip(f.y, __popc(r & 5u) & 1u);
+    f.z = flip(f.z, __popc(r & 3u) & 1u);
+    return f;
+}
+// 3D H block {Hx, Hy, Hz, 0}: H_b is normal to the walls normal to axis b
+template <typename V4> __device__ __forceinline__ V4 img_h3(V4 f, unsigned r) {
+    f.x = flip(f.x, r & 1u);
+    f.y = flip(f.y, (r >> 1) & 1u);
+    f.z = flip(f.z, (r >> 2) & 1u);
+    return f;
 }
 
 // ---- Q16 index decoding (see the layout notes at the top)

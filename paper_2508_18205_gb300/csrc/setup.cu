@@ -11,6 +11,7 @@
 #include <mutex>
 
 #include "internal.cuh"
+#include "kernels.cuh"
 
 namespace mfd {
 
@@ -430,6 +431,128 @@ mfd_status knn_build(const mfd_nodes* centres, const mfd_nodes* sources, int n, 
     return MFD_OK;
 }
 
+// ------------------------------------------------------------ kNN with mirror walls (PEC by images)
+//
+// The nodes of a set with mirror walls on [0, hi] per mirrored axis and their
+// images x_a -> 2 hi - x_a (for every non-empty subset r of those axes, the
+// reflection code) form a periodic set of period 2 hi on those axes (a perfect
+// conductor as a mirror); a wall node is its own image and is not repeated.
+// The kNN runs on the nodes and the images of the nodes within a band D of the
+// walls they are reflected across (an image left out lies at least D outside
+// the box, so it cannot be among the n nearest of a centre whose n-th nearest is
+// closer than D; the band grows until that holds). Entries are then node device
+// ids with the code in the top bits. Images are listed after the nodes, by
+// (code, node caller id), so ties of equal distance break as in a set that holds
+// every image.
+
+__global__ void k_img_radius(const int32_t* __restrict__ idx, int n, int64_t nc, const double* __restrict__ xc,
+                             const double* __restrict__ xs, int dim, double p0, double p1, double p2,
+                             unsigned long long* __restrict__ worst) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const double per[3] = {p0, p1, p2};
+    const double d2 = sq_dist(dim, xc + c * dim, xs + (int64_t)idx[c * n + n - 1] * dim, per);
+    atomicMax(worst, (unsigned long long)__double_as_longlong(d2));  // non-negative doubles order as integers
+}
+
+__global__ void k_img_map(const int32_t* __restrict__ ext_idx, int64_t total, const int64_t* __restrict__ ext_perm,
+                          const int64_t* __restrict__ orig, const uint8_t* __restrict__ code,
+                          const int64_t* __restrict__ inv, int32_t* __restrict__ out) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int64_t u = ext_perm[ext_idx[e]];  // caller id in the extended set
+    out[e] = (int32_t)inv[orig[u]] | (int32_t)((unsigned)code[u] << IMG_SHIFT);
+}
+
+mfd_status knn_build_mirror(const mfd_nodes* centres, const mfd_nodes* sources, int n, int32_t* d_idx) {
+    mfd_ctx* ctx = sources->ctx;
+    cudaStream_t s = ctx->stream;
+    const int dim = sources->dim;
+    const int64_t N = sources->n;
+    const uint32_t axes = sources->mirror_axes;
+    if (n < 1 || n > KNN_MAX || n > N) return fail(MFD_ERR_ARG, "stencil size out of range");
+    // caller-order coordinates
+    std::vector<double> xd((size_t)N * dim), xu((size_t)N * dim);
+    MFD_CUDA(cudaMemcpy(xd.data(), sources->xyz.p, xd.size() * 8, cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < N; ++k)
+        for (int a = 0; a < dim; ++a) xu[sources->h_perm[k] * dim + a] = xd[k * dim + a];
+    double per[3] = {0, 0, 0}, ext[3] = {0, 0, 0}, vol = 1.0;
+    for (int a = 0; a < dim; ++a) {
+        double lo = 1e300, hi = -1e300;
+        for (int64_t i = 0; i < N; ++i) {
+            lo = std::min(lo, xu[i * dim + a]);
+            hi = std::max(hi, xu[i * dim + a]);
+        }
+        per[a] = ((axes >> a) & 1u) ? 2.0 * sources->mirror_hi[a] : sources->period[a];
+        ext[a] = ((axes >> a) & 1u) ? sources->mirror_hi[a] : (per[a] > 0 ? per[a] : hi - lo);
+        vol *= std::max(ext[a], 1e-300);
+    }
+    const double h = std::pow(vol / (double)N, 1.0 / dim);
+    const double pi = 3.14159265358979323846;
+    const double r_est = dim == 2 ? h * std::sqrt(n / pi) : h * std::cbrt(3.0 * n / (4.0 * pi));
+    double D = 2.0 * r_est + 2.0 * h;
+    const int64_t nc = centres->n;
+    for (int attempt = 0; attempt < 6; ++attempt, D *= 2.0) {
+        std::vector<double> xe(xu);
+        std::vector<int64_t> orig(N);
+        std::vector<uint8_t> code(N, 0);
+        for (int64_t i = 0; i < N; ++i) orig[i] = i;
+        for (uint32_t r = 1; r < (1u << dim); ++r) {
+            if (r & ~axes) continue;
+            for (int64_t i = 0; i < N; ++i) {
+                bool keep = true;
+                for (int a = 0; a < dim && keep; ++a) {
+                    if (!((r >> a) & 1u)) continue;
+                    const double x = xu[i * dim + a], hi = sources->mirror_hi[a];
+                    keep = x > 0.0 && x < hi && std::min(x, hi - x) < D;
+                }
+                if (!keep) continue;
+                for (int a = 0; a < dim; ++a) {
+                    const double x = xu[i * dim + a];
+                    xe.push_back(((r >> a) & 1u) ? 2.0 * sources->mirror_hi[a] - x : x);
+                }
+                orig.push_back(i);
+                code.push_back((uint8_t)r);
+            }
+        }
+        const int64_t ne = (int64_t)orig.size();
+        if (ne > INT32_MAX) return fail(MFD_ERR_ARG, "extended node set too large");
+        mfd_nodes* exts = nullptr;
+        MFD_TRY(mfd_nodes_create(ctx, dim, ne, xe.data(), per, &exts));
+        struct Rel {
+            mfd_nodes* p;
+            ~Rel() { mfd_nodes_destroy(p); }
+        } rel{exts};
+        DevBuf eidx, dorig, dcode, worst;
+        MFD_TRY(eidx.alloc((size_t)nc * n * 4));
+        MFD_TRY(knn_build(centres, exts, n, eidx.as<int32_t>()));
+        MFD_TRY(worst.alloc(8));
+        MFD_CUDA(cudaMemsetAsync(worst.p, 0, 8, s));
+        k_img_radius<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(eidx.as<int32_t>(), n, nc, centres->xyz.as<double>(),
+                                                                  exts->xyz.as<double>(), dim, per[0], per[1], per[2],
+                                                                  worst.as<unsigned long long>());
+        MFD_CUDA(cudaGetLastError());
+        unsigned long long wb = 0;
+        MFD_CUDA(cudaMemcpyAsync(&wb, worst.p, 8, cudaMemcpyDeviceToHost, s));
+        MFD_CUDA(cudaStreamSynchronize(s));
+        double w2;
+        std::memcpy(&w2, &wb, 8);
+        if (!(w2 < D * D)) continue;  // an image outside the band could be closer: widen it
+        MFD_TRY(dorig.alloc((size_t)ne * 8));
+        MFD_TRY(dcode.alloc((size_t)ne));
+        MFD_CUDA(cudaMemcpyAsync(dorig.p, orig.data(), ne * 8, cudaMemcpyHostToDevice, s));
+        MFD_CUDA(cudaMemcpyAsync(dcode.p, code.data(), ne, cudaMemcpyHostToDevice, s));
+        const int64_t total = nc * n;
+        k_img_map<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(eidx.as<int32_t>(), total, exts->perm.as<int64_t>(),
+                                                                  dorig.as<int64_t>(), dcode.as<uint8_t>(),
+                                                                  sources->inv.as<int64_t>(), d_idx);
+        MFD_CUDA(cudaGetLastError());
+        MFD_CUDA(cudaStreamSynchronize(s));
+        return MFD_OK;
+    }
+    return fail(MFD_ERR_STATE, "the image band did not cover the stencils");
+}
+
 // ------------------------------------------------------------ weights (batched FP64 solve)
 
 constexpr int WS_THREADS = 128;
@@ -443,6 +566,8 @@ struct WArgs {
     int64_t nc;
     int stride, n_use, dim, phs_k, M, op, alpha, nout;
     double period[3];
+    unsigned mirror;           // mirrored axes: an entry with image code r reflects x_a -> 2 mhi_a - x_a, a in r
+    double mhi[3];
     double lap_rbf;            // prod_{i<alpha} (k-2i)(k-2i+d-2)
     double delta;
     double* w;                 // [nout][nc][n_use]
@@ -477,11 +602,15 @@ __global__ void __launch_bounds__(WS_THREADS) k_weights(WArgs a) {
     for (int64_t c = blockIdx.x; c < a.nc; c += gridDim.x) {
         // offsets to the centre, minimum image
         for (int j = tid; j < n; j += WS_THREADS) {
-            int32_t sj = a.idx[c * a.stride + j];
+            const int32_t raw = a.idx[c * a.stride + j];
+            const unsigned code = a.mirror ? (unsigned)raw >> IMG_SHIFT : 0u;
+            const int32_t sj = a.mirror ? (raw & IMG_MASK) : raw;
             for (int q = 0; q < 3; ++q) {
                 double d = 0.0;
                 if (q < dim) {
-                    d = a.xs[(int64_t)sj * dim + q] - a.xc[c * dim + q];
+                    double x = a.xs[(int64_t)sj * dim + q];
+                    if ((code >> q) & 1u) x = 2.0 * a.mhi[q] - x;
+                    d = x - a.xc[c * dim + q];
                     double p = a.period[q];
                     if (p > 0) {
                         if (d > 0.5 * p) d -= p;
@@ -722,7 +851,12 @@ mfd_status weights_solve(const mfd_stencils* st, int n_use, int phs_k, int poly_
     a.op = op;
     a.alpha = alpha;
     a.nout = op == MFD_OP_LAP_POW ? 1 : dim;
-    for (int q = 0; q < 3; ++q) a.period[q] = q < dim ? src->period[q] : 0.0;
+    a.mirror = src->mirror_axes;
+    for (int q = 0; q < 3; ++q) {
+        const bool m = q < dim && ((src->mirror_axes >> q) & 1u);
+        a.mhi[q] = m ? src->mirror_hi[q] : 0.0;
+        a.period[q] = q < dim ? (m ? 2.0 * src->mirror_hi[q] : src->period[q]) : 0.0;
+    }
     double cf = 1.0;
     for (int i = 0; i < alpha; ++i) cf *= (double)(phs_k - 2 * i) * (double)(phs_k - 2 * i + dim - 2);
     a.lap_rbf = cf;

@@ -225,6 +225,7 @@ struct PackedStencil {
     int nc = 0, nv = 0, ni = 0;
     int64_t n = 0;
     int64_t src_c = 0, src_v = 0;  // sizes of the node sets the curl and HV indices point into
+    bool mirror = false;           // entries carry image codes (node set with mirror walls)
 };
 
 struct mfd_sim {
@@ -299,7 +300,7 @@ int chunks_of(int n) { return (n + 3) / 4; }
 #ifdef MFD_BOUNDS_CHECK
 __global__ void k_check_rows(const int32_t* __restrict__ idx, int stride, int64_t N, int n_use, int64_t nsrc) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e < N * n_use) chk_id(idx[(e / n_use) * stride + e % n_use], nsrc);
+    if (e < N * n_use) chk_id(idx[(e / n_use) * stride + e % n_use] & IMG_MASK, nsrc);
 }
 
 void check_rows(mfd_ctx* ctx, const mfd_stencils* st, int n_use) {
@@ -357,6 +358,7 @@ mfd_status pack_pass(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* h
     p.n = curl->st->centres->n;
     p.src_c = curl->st->sources->n;
     p.src_v = hv->st->sources->n;
+    p.mirror = curl->st->sources->mirror_axes != 0 || hv->st->sources->mirror_axes != 0;
 #ifdef MFD_BOUNDS_CHECK
     // pack-time row check: every stencil entry lies in the node set it points into
     check_rows(ctx, curl->st, curl->n_use);
@@ -414,6 +416,7 @@ template <typename T> StencilStreams<T> streams(const PackedStencil& p, bool q16
     s.n = p.n;
     s.src_c = p.src_c;
     s.src_v = p.idx_v.p ? p.src_v : p.src_c;
+    s.mirror = p.mirror;
     return s;
 }
 
@@ -649,6 +652,8 @@ mfd_status mfd_sim_create(mfd_ctx* ctx, const mfd_sim_desc* desc, mfd_sim** out)
     if (colloc && (desc->h_curl != desc->e_curl || desc->h_hv != desc->e_hv))
         return fail(MFD_ERR_ARG, "collocated: h_curl == e_curl and h_hv == e_hv expected");
     if (desc->dim == 3 && !colloc) return fail(MFD_ERR_ARG, "3D supports the collocated layout only");
+    if (!colloc && (desc->h_curl->st->sources->mirror_axes || desc->e_curl->st->sources->mirror_axes))
+        return fail(MFD_ERR_ARG, "mirror walls (images) are supported in the collocated layout");
     MFD_CUDA(cudaSetDevice(ctx->device));
     mfd_sim* sim = new (std::nothrow) mfd_sim();
     if (!sim) return fail(MFD_ERR_OOM, "host allocation failed");
@@ -1310,6 +1315,7 @@ mfd_status mfd_grad_forward(mfd_sim* sim, int64_t nsteps, int64_t every, double*
     if (!sim || nsteps < 1 || every < 0 || !J || !out) return fail(MFD_ERR_ARG, "bad arguments");
     *out = nullptr;
     if (sim->layout != COLLOC2D) return fail(MFD_ERR_ARG, "the gradient supports the collocated 2D layout");
+    if (sim->hp.mirror) return fail(MFD_ERR_ARG, "the gradient does not support mirror walls (images)");
     if (sim->nprobe < 1 || sim->probe_cap < nsteps)
         return fail(MFD_ERR_STATE, "the gradient needs probes with capacity >= nsteps (mfd_set_probes)");
     mfd_ctx* ctx = sim->ctx;

@@ -17,11 +17,32 @@ namespace mfd {
 
 // ------------------------------------------------------------ collocated
 
+// the TMz blocks of a chunk's four entries; MIR: entries carry image codes and
+// the values enter with their parities (kernels.cuh)
+template <bool MIR, typename V4>
+__device__ __forceinline__ void gather4_tmz(const V4* __restrict__ A, int4 raw, int64_t n, V4& f0, V4& f1, V4& f2,
+                                            V4& f3) {
+    if constexpr (MIR) {
+        uint4 r;
+        const int4 id = img_split(raw, n, r);
+        f0 = img_tmz(ld_gather(A + id.x), r.x);
+        f1 = img_tmz(ld_gather(A + id.y), r.y);
+        f2 = img_tmz(ld_gather(A + id.z), r.z);
+        f3 = img_tmz(ld_gather(A + id.w), r.w);
+    } else {
+        const int4 id = chk4(raw, n);
+        f0 = ld_gather(A + id.x);
+        f1 = ld_gather(A + id.y);
+        f2 = ld_gather(A + id.z);
+        f3 = ld_gather(A + id.w);
+    }
+}
+
 // P lanes per node (P = 1, or 4 for problems too small to fill the GPU with one
 // thread per node): lane `part` of the node sums chunks part, part + P, ... of the
 // row (SHARED layout); the partial sums are merged across the node's lanes by the
 // caller (merge_xor), which every lane of the warp must reach.
-template <typename T, int NC, int NV, bool SHARED, bool COMP, int P = 1>
+template <typename T, int NC, int NV, bool SHARED, bool COMP, int P = 1, bool MIR = false>
 __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const typename Vec<T>::V4* __restrict__ A,
                                               int64_t i, T& dxE, T& dyE, T& vx, T& vy, T& ve, bool act = true,
                                               int part = 0) {
@@ -42,15 +63,15 @@ __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const 
         const V4* pv = s.wv + slice * nv * 32 + lane;
 #pragma unroll
         for (int c = part; c < (act ? ni : 0); c += P) {
-            const int4 id = chk4(ld_stream(ip + c * 32), s.src_c);
+            const int4 raw = ld_stream(ip + c * 32);
             V4 wx, wy, wv;
             if (c < nc) {
                 wx = ld_stream(px + c * 32);
                 wy = ld_stream(py + c * 32);
             }
             if (c < nv) wv = ld_stream(pv + c * 32);
-            const V4 f0 = ld_gather(A + id.x), f1 = ld_gather(A + id.y);
-            const V4 f2 = ld_gather(A + id.z), f3 = ld_gather(A + id.w);
+            V4 f0, f1, f2, f3;
+            gather4_tmz<MIR>(A, raw, s.src_c, f0, f1, f2, f3);
             if (c < nc) {
                 ax.add(wx.x, f0.x); ax.add(wx.y, f1.x); ax.add(wx.z, f2.x); ax.add(wx.w, f3.x);
                 ay.add(wy.x, f0.x); ay.add(wy.y, f1.x); ay.add(wy.z, f2.x); ay.add(wy.w, f3.x);
@@ -69,19 +90,20 @@ __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const 
         const V4* pv = s.wv + slice * nv * 32 + lane;
 #pragma unroll
         for (int c = part; c < (act ? nc : 0); c += P) {
-            const int4 id = chk4(ld_stream(ic + c * 32), s.src_c);
+            const int4 raw = ld_stream(ic + c * 32);
             const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32);
-            const T f0 = ld_gather(A + id.x).x, f1 = ld_gather(A + id.y).x;
-            const T f2 = ld_gather(A + id.z).x, f3 = ld_gather(A + id.w).x;
+            V4 g0, g1, g2, g3;
+            gather4_tmz<MIR>(A, raw, s.src_c, g0, g1, g2, g3);
+            const T f0 = g0.x, f1 = g1.x, f2 = g2.x, f3 = g3.x;
             ax.add(wx.x, f0); ax.add(wx.y, f1); ax.add(wx.z, f2); ax.add(wx.w, f3);
             ay.add(wy.x, f0); ay.add(wy.y, f1); ay.add(wy.z, f2); ay.add(wy.w, f3);
         }
 #pragma unroll
         for (int c = part; c < (act ? nv : 0); c += P) {
-            const int4 id = chk4(ld_stream(iv + c * 32), s.src_v);
+            const int4 raw = ld_stream(iv + c * 32);
             const V4 wv = ld_stream(pv + c * 32);
-            const V4 f0 = ld_gather(A + id.x), f1 = ld_gather(A + id.y);
-            const V4 f2 = ld_gather(A + id.z), f3 = ld_gather(A + id.w);
+            V4 f0, f1, f2, f3;
+            gather4_tmz<MIR>(A, raw, s.src_v, f0, f1, f2, f3);
             hx.add(wv.x, f0.y); hx.add(wv.y, f1.y); hx.add(wv.z, f2.y); hx.add(wv.w, f3.y);
             hy.add(wv.x, f0.z); hy.add(wv.y, f1.z); hy.add(wv.z, f2.z); hy.add(wv.w, f3.z);
             he.add(wv.x, f0.x); he.add(wv.y, f1.x); he.add(wv.z, f2.x); he.add(wv.w, f3.x);
@@ -102,7 +124,7 @@ __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const 
     ve = he.get();
 }
 
-template <typename T, int NC, int NV, bool SHARED, bool COMP, int P>
+template <typename T, int NC, int NV, bool SHARED, bool COMP, int P, bool MIR = false>
 __global__ void __launch_bounds__(512) k_h_colloc(StencilStreams<T> s, Coefs<T> k,
                                                   const typename Vec<T>::V4* __restrict__ A,
                                                   typename Vec<T>::V4* __restrict__ B) {
@@ -112,7 +134,7 @@ __global__ void __launch_bounds__(512) k_h_colloc(StencilStreams<T> s, Coefs<T> 
     const int part = (int)(t % P);
     if (P == 1 && i >= s.n) return;  // with P > 1 every lane takes part in the merges
     T dxE, dyE, vx, vy, ve;
-    h_colloc_node<T, NC, NV, SHARED, COMP, P>(s, A, i, dxE, dyE, vx, vy, ve, i < s.n, part);
+    h_colloc_node<T, NC, NV, SHARED, COMP, P, MIR>(s, A, i, dxE, dyE, vx, vy, ve, i < s.n, part);
     if (i >= s.n || part != 0) return;
     const V4 me = ld_gather(A + i);
     V4 out;
@@ -123,7 +145,7 @@ __global__ void __launch_bounds__(512) k_h_colloc(StencilStreams<T> s, Coefs<T> 
     st4(B + i, out);
 }
 
-template <typename T, int NC, bool SHARED, bool COMP, int P>
+template <typename T, int NC, bool SHARED, bool COMP, int P, bool MIR = false>
 __global__ void __launch_bounds__(512) k_e_colloc(StencilStreams<T> s, const typename Vec<T>::V4* __restrict__ B,
                                                   typename Vec<T>::V4* __restrict__ A) {
     using V4 = typename Vec<T>::V4;
@@ -143,10 +165,10 @@ __global__ void __launch_bounds__(512) k_e_colloc(StencilStreams<T> s, const typ
     Acc dxHy, dyHx;
 #pragma unroll
     for (int c = part; c < (act ? nc : 0); c += P) {
-        const int4 id = chk4(ld_stream(ip + c * 32), s.src_c);
+        const int4 raw = ld_stream(ip + c * 32);
         const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32);
-        const V4 f0 = ld_gather(B + id.x), f1 = ld_gather(B + id.y);
-        const V4 f2 = ld_gather(B + id.z), f3 = ld_gather(B + id.w);
+        V4 f0, f1, f2, f3;
+        gather4_tmz<MIR>(B, raw, s.src_c, f0, f1, f2, f3);
         dxHy.add(wx.x, f0.z); dxHy.add(wx.y, f1.z); dxHy.add(wx.z, f2.z); dxHy.add(wx.w, f3.z);
         dyHx.add(wy.x, f0.y); dyHx.add(wy.y, f1.y); dyHx.add(wy.z, f2.y); dyHx.add(wy.w, f3.y);
     }
@@ -167,7 +189,7 @@ __global__ void __launch_bounds__(512) k_e_colloc(StencilStreams<T> s, const typ
 
 // energy (Eq. 20) of the collocated state at t_n: H averaged with the H
 // update computed on the fly; per-block partial sums in FP64
-template <typename T, bool COMP>
+template <typename T, bool COMP, bool MIR = false>
 __global__ void __launch_bounds__(256) k_energy_colloc(StencilStreams<T> s, Coefs<T> k,
                                                        const typename Vec<T>::V4* __restrict__ A,
                                                        const double* __restrict__ eps_r, double eta2,
@@ -179,9 +201,9 @@ __global__ void __launch_bounds__(256) k_energy_colloc(StencilStreams<T> s, Coef
     if (i < s.n) {
         T dxE, dyE, vx, vy, ve;
         if (s.idx_v == s.idx_c)
-            h_colloc_node<T, 0, 0, true, COMP>(s, A, i, dxE, dyE, vx, vy, ve);
+            h_colloc_node<T, 0, 0, true, COMP, 1, MIR>(s, A, i, dxE, dyE, vx, vy, ve);
         else
-            h_colloc_node<T, 0, 0, false, COMP>(s, A, i, dxE, dyE, vx, vy, ve);
+            h_colloc_node<T, 0, 0, false, COMP, 1, MIR>(s, A, i, dxE, dyE, vx, vy, ve);
         const V4 me = A[i];
         const double hx1 = (double)(me.y - k.ch * (dyE - k.gamma * vx));
         const double hy1 = (double)(me.z + k.ch * (dxE + k.gamma * vy));
@@ -339,6 +361,16 @@ static cudaError_t launch_colloc_pass_p(int pass, const StencilStreams<T>& s, co
         else k_e_colloc<T, NC, false, COMP, P><<<grid, block, 0, st>>>(s, b, a);           \
         return cudaGetLastError();                                                       \
     }
+    if (s.mirror) {  // node sets with mirror walls: the generic kernels with image codes
+        if (pass == 0) {
+            if (shared) k_h_colloc<T, 0, 0, true, COMP, P, true><<<grid, block, 0, st>>>(s, k, a, b);
+            else k_h_colloc<T, 0, 0, false, COMP, P, true><<<grid, block, 0, st>>>(s, k, a, b);
+        } else {
+            if (shared) k_e_colloc<T, 0, true, COMP, P, true><<<grid, block, 0, st>>>(s, b, a);
+            else k_e_colloc<T, 0, false, COMP, P, true><<<grid, block, 0, st>>>(s, b, a);
+        }
+        return cudaGetLastError();
+    }
     if (pass == 0) {
         MFD_H(3, 8) MFD_H(5, 8) MFD_H(8, 8) MFD_H(10, 8)
         if (shared) k_h_colloc<T, 0, 0, true, COMP, P><<<grid, block, 0, st>>>(s, k, a, b);
@@ -409,6 +441,16 @@ cudaError_t launch_energy_2d(const Launch2D& L, const double* eps_r, int64_t ne,
         else
             k_energy_stag<float, false><<<grid, 256, 0, st>>>(L.hs.f, L.kf, (const float*)L.stag.ez,
                                                               (const float2*)L.stag.h, eps_r, ne, eta2, partial);
+    } else if (L.hs.f.mirror) {
+        if (L.fp64)
+            k_energy_colloc<double, false, true><<<grid, 256, 0, st>>>(L.hs.d, L.kd, (const dbl4*)L.A, eps_r, eta2,
+                                                                      partial);
+        else if (L.comp)
+            k_energy_colloc<float, true, true><<<grid, 256, 0, st>>>(L.hs.f, L.kf, (const float4*)L.A, eps_r, eta2,
+                                                                    partial);
+        else
+            k_energy_colloc<float, false, true><<<grid, 256, 0, st>>>(L.hs.f, L.kf, (const float4*)L.A, eps_r, eta2,
+                                                                     partial);
     } else {
         if (L.fp64)
             k_energy_colloc<double, false><<<grid, 256, 0, st>>>(L.hs.d, L.kd, (const dbl4*)L.A, eps_r, eta2, partial);

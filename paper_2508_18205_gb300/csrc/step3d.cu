@@ -18,7 +18,15 @@ template <typename T> struct Curl {
     T dyz, dzy, dzx, dxz, dxy, dyx;  // Dy Fz, Dz Fy, Dz Fx, Dx Fz, Dx Fy, Dy Fx
 };
 
-template <typename T, int NC, int NV, bool SHARED, bool COMP>
+// raw index entries of a chunk -> node ids (and image codes when MIR)
+template <bool MIR>
+__device__ __forceinline__ int4 ids3(int4 raw, int64_t n, uint4& r) {
+    if constexpr (MIR) return img_split(raw, n, r);
+    r = make_uint4(0u, 0u, 0u, 0u);
+    return chk4(raw, n);
+}
+
+template <typename T, int NC, int NV, bool SHARED, bool COMP, bool MIR = false>
 __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typename Vec<T>::V4* __restrict__ F,
                                         int64_t i, Curl<T>& cu, T vh[3], T ve[3]) {
     using V4 = typename Vec<T>::V4;
@@ -64,18 +72,31 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
         const int4* ip = s.idx_c + slice * ni * 32 + lane;
 #pragma unroll
         for (int c = 0; c < ni; ++c) {
-            const int4 id = chk4(ld_stream(ip + c * 32), s.src_c);
+            uint4 r;
+            const int4 id = ids3<MIR>(ld_stream(ip + c * 32), s.src_c, r);
             V4 e[4], h[4];
             if (c < nv) {
                 ld_gather_eh(F + 2 * (int64_t)id.x, e[0], h[0]);
                 ld_gather_eh(F + 2 * (int64_t)id.y, e[1], h[1]);
                 ld_gather_eh(F + 2 * (int64_t)id.z, e[2], h[2]);
                 ld_gather_eh(F + 2 * (int64_t)id.w, e[3], h[3]);
+                if constexpr (MIR) {
+                    h[0] = img_h3(h[0], r.x);
+                    h[1] = img_h3(h[1], r.y);
+                    h[2] = img_h3(h[2], r.z);
+                    h[3] = img_h3(h[3], r.w);
+                }
             } else {
                 e[0] = ld_gather(F + 2 * (int64_t)id.x);
                 e[1] = ld_gather(F + 2 * (int64_t)id.y);
                 e[2] = ld_gather(F + 2 * (int64_t)id.z);
                 e[3] = ld_gather(F + 2 * (int64_t)id.w);
+            }
+            if constexpr (MIR) {
+                e[0] = img_e3(e[0], r.x);
+                e[1] = img_e3(e[1], r.y);
+                e[2] = img_e3(e[2], r.z);
+                e[3] = img_e3(e[3], r.w);
             }
             if (c < nc) curl4(ld_stream(px + c * 32), ld_stream(py + c * 32), ld_stream(pz + c * 32), e);
             if (c < nv) hv4(ld_stream(pv + c * 32), e, h);
@@ -85,22 +106,38 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
         const int4* iv = s.idx_v + slice * nv * 32 + lane;
 #pragma unroll
         for (int c = 0; c < nc; ++c) {
-            const int4 id = chk4(ld_stream(ic + c * 32), s.src_c);
+            uint4 r;
+            const int4 id = ids3<MIR>(ld_stream(ic + c * 32), s.src_c, r);
             V4 e[4];
             e[0] = ld_gather(F + 2 * (int64_t)id.x);
             e[1] = ld_gather(F + 2 * (int64_t)id.y);
             e[2] = ld_gather(F + 2 * (int64_t)id.z);
             e[3] = ld_gather(F + 2 * (int64_t)id.w);
+            if constexpr (MIR) {
+                e[0] = img_e3(e[0], r.x);
+                e[1] = img_e3(e[1], r.y);
+                e[2] = img_e3(e[2], r.z);
+                e[3] = img_e3(e[3], r.w);
+            }
             curl4(ld_stream(px + c * 32), ld_stream(py + c * 32), ld_stream(pz + c * 32), e);
         }
 #pragma unroll
         for (int c = 0; c < nv; ++c) {
-            const int4 id = chk4(ld_stream(iv + c * 32), s.src_v);
+            uint4 r;
+            const int4 id = ids3<MIR>(ld_stream(iv + c * 32), s.src_v, r);
             V4 e[4], h[4];
             ld_gather_eh(F + 2 * (int64_t)id.x, e[0], h[0]);
             ld_gather_eh(F + 2 * (int64_t)id.y, e[1], h[1]);
             ld_gather_eh(F + 2 * (int64_t)id.z, e[2], h[2]);
             ld_gather_eh(F + 2 * (int64_t)id.w, e[3], h[3]);
+            if constexpr (MIR) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const unsigned rq = q == 0 ? r.x : q == 1 ? r.y : q == 2 ? r.z : r.w;
+                    e[q] = img_e3(e[q], rq);
+                    h[q] = img_h3(h[q], rq);
+                }
+            }
             hv4(ld_stream(pv + c * 32), e, h);
         }
     }
@@ -121,7 +158,7 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
 // The H pass may take up to 128 registers: at 256 threads per block the
 // compensated FP32 kernel runs 2 blocks per SM with 32 bytes of spills; caps
 // of 80 (3 blocks) and 64 registers (4 blocks) spilled more and were slower.
-template <typename T, int NC, int NV, bool SHARED, bool COMP>
+template <typename T, int NC, int NV, bool SHARED, bool COMP, bool MIR = false>
 __global__ void __launch_bounds__(512, 1) k_h3(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V4* __restrict__ F,
                                             typename Vec<T>::V4* __restrict__ Es,
                                             typename Vec<T>::V4* __restrict__ Hn) {
@@ -130,7 +167,7 @@ __global__ void __launch_bounds__(512, 1) k_h3(StencilStreams<T> s, Coefs<T> k, 
     if (i >= s.n) return;
     Curl<T> cu;
     T vh[3], ve[3];
-    h3_node<T, NC, NV, SHARED, COMP>(s, F, i, cu, vh, ve);
+    h3_node<T, NC, NV, SHARED, COMP, MIR>(s, F, i, cu, vh, ve);
     V4 e, h;
     ld_gather_eh(F + 2 * i, e, h);
     V4 ho, eo;
@@ -146,7 +183,7 @@ __global__ void __launch_bounds__(512, 1) k_h3(StencilStreams<T> s, Coefs<T> k, 
     st4(Es + i, eo);
 }
 
-template <typename T, int NC, bool SHARED, bool COMP>
+template <typename T, int NC, bool SHARED, bool COMP, bool MIR = false>
 __global__ void __launch_bounds__(512, 2) k_e3(StencilStreams<T> s, const typename Vec<T>::V4* __restrict__ Hn,
                                             const typename Vec<T>::V4* __restrict__ Es,
                                             const uint8_t* __restrict__ wall, typename Vec<T>::V4* __restrict__ F) {
@@ -165,13 +202,20 @@ __global__ void __launch_bounds__(512, 2) k_e3(StencilStreams<T> s, const typena
     Acc a_yz, a_zy, a_zx, a_xz, a_xy, a_yx;
 #pragma unroll
     for (int c = 0; c < nc; ++c) {
-        const int4 id = chk4(ld_stream(ip + c * 32), s.src_c);
+        uint4 r;
+        const int4 id = ids3<MIR>(ld_stream(ip + c * 32), s.src_c, r);
         const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32), wz = ld_stream(pz + c * 32);
         V4 f[4];
         f[0] = ld_gather(Hn + id.x);
         f[1] = ld_gather(Hn + id.y);
         f[2] = ld_gather(Hn + id.z);
         f[3] = ld_gather(Hn + id.w);
+        if constexpr (MIR) {
+            f[0] = img_h3(f[0], r.x);
+            f[1] = img_h3(f[1], r.y);
+            f[2] = img_h3(f[2], r.z);
+            f[3] = img_h3(f[3], r.w);
+        }
         const T* wxa = &wx.x;
         const T* wya = &wy.x;
         const T* wza = &wz.x;
@@ -202,7 +246,7 @@ __global__ void __launch_bounds__(512, 2) k_e3(StencilStreams<T> s, const typena
     st_eh(F + 2 * i, o, hown);
 }
 
-template <typename T, bool COMP>
+template <typename T, bool COMP, bool MIR = false>
 __global__ void __launch_bounds__(256) k_energy3(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V4* __restrict__ F,
                                                  const double* __restrict__ eps_r, double eta2,
                                                  double* __restrict__ partial) {
@@ -214,9 +258,9 @@ __global__ void __launch_bounds__(256) k_energy3(StencilStreams<T> s, Coefs<T> k
         Curl<T> cu;
         T vh[3], ve[3];
         if (s.idx_v == s.idx_c)
-            h3_node<T, 0, 0, true, COMP>(s, F, i, cu, vh, ve);
+            h3_node<T, 0, 0, true, COMP, MIR>(s, F, i, cu, vh, ve);
         else
-            h3_node<T, 0, 0, false, COMP>(s, F, i, cu, vh, ve);
+            h3_node<T, 0, 0, false, COMP, MIR>(s, F, i, cu, vh, ve);
         const V4 e = F[2 * i], h = F[2 * i + 1];
         const double h1[3] = {(double)(h.x + k.ch * (-(cu.dyz - cu.dzy) + k.gamma * vh[0])),
                               (double)(h.y + k.ch * (-(cu.dzx - cu.dxz) + k.gamma * vh[1])),
@@ -246,6 +290,16 @@ static cudaError_t launch3(const Launch3D& L, const StencilStreams<T>& s, const 
     V4* F = static_cast<V4*>(L.F);
     V4* Es = static_cast<V4*>(L.Es);
     V4* Hn = static_cast<V4*>(L.Hn);
+    if (s.mirror) {  // node sets with mirror walls: the generic kernels with image codes
+        if (pass == 0) {
+            if (shared) k_h3<T, 0, 0, true, COMP, true><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
+            else k_h3<T, 0, 0, false, COMP, true><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
+        } else {
+            if (shared) k_e3<T, 0, true, COMP, true><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F);
+            else k_e3<T, 0, false, COMP, true><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F);
+        }
+        return cudaGetLastError();
+    }
     if (pass == 0) {
         if (shared && s.nc == 10 && s.nv == 18) k_h3<T, 10, 18, true, COMP><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
         else if (shared) k_h3<T, 0, 0, true, COMP><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
@@ -266,12 +320,17 @@ cudaError_t launch_3d(const Launch3D& L, int pass, cudaStream_t st) {
 
 cudaError_t launch_energy_3d(const Launch3D& L, const double* eps_r, double eta2, double* partial, unsigned grid,
                              cudaStream_t st) {
-    if (L.fp64)
-        k_energy3<double, false><<<grid, 256, 0, st>>>(L.s.d, L.kd, (const dbl4*)L.F, eps_r, eta2, partial);
-    else if (L.comp)
-        k_energy3<float, true><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.F, eps_r, eta2, partial);
-    else
-        k_energy3<float, false><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.F, eps_r, eta2, partial);
+    const bool mir = L.s.f.mirror;
+    if (L.fp64) {
+        if (mir) k_energy3<double, false, true><<<grid, 256, 0, st>>>(L.s.d, L.kd, (const dbl4*)L.F, eps_r, eta2, partial);
+        else k_energy3<double, false><<<grid, 256, 0, st>>>(L.s.d, L.kd, (const dbl4*)L.F, eps_r, eta2, partial);
+    } else if (L.comp) {
+        if (mir) k_energy3<float, true, true><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.F, eps_r, eta2, partial);
+        else k_energy3<float, true><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.F, eps_r, eta2, partial);
+    } else {
+        if (mir) k_energy3<float, false, true><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.F, eps_r, eta2, partial);
+        else k_energy3<float, false><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.F, eps_r, eta2, partial);
+    }
     return cudaGetLastError();
 }
 
