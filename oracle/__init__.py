@@ -139,6 +139,23 @@ def weights(xc, xs, period, idx, n_use, phs_k, poly_m, op, alpha=0, delta=0.0):
     return w
 
 
+def weights_sized(xc, xs, period, idx, n_per, phs_k, poly_m, op, alpha=0, delta=0.0):
+    """Weights with a stencil size per centre: centre c uses the first n_per[c]
+    entries of its row (Eq. 12 on that stencil). Rows are max(n_per) long,
+    zero beyond each centre's own size (an entry with weight 0 is not in the
+    stencil). Returns (nout, nc, max(n_per))."""
+    xc, idx = _f64(xc), _i64(idx)
+    n_per = _i64(n_per)
+    nmax = int(n_per.max())
+    d = xc.shape[1]
+    nout = 1 if op == OP_LAP_POW else d
+    w = np.zeros((nout, len(xc), nmax))
+    for n_use in np.unique(n_per):
+        sel = np.nonzero(n_per == n_use)[0]
+        w[:, sel, :n_use] = weights(xc[sel], xs, period, idx[sel], int(n_use), phs_k, poly_m, op, alpha, delta)
+    return w
+
+
 def gepp(A, B):
     A = _f64(A).copy()
     B = _f64(B).reshape(A.shape[0], -1).copy()
@@ -545,10 +562,29 @@ def image_stencils(nodes, L_use):
     return dbl, ids, orig, code
 
 
-def _image_stencil(nodes, dbl, ids, orig, code, n_use, phs_k, m, op, alpha=0):
-    w = weights(nodes.xyz, dbl.xyz, dbl.period, ids, n_use, phs_k, m, op, alpha)
+def _image_stencil(nodes, dbl, ids, orig, code, n_use, phs_k, m, op, alpha=0, n_per=None):
+    if n_per is None:
+        w = weights(nodes.xyz, dbl.xyz, dbl.period, ids, n_use, phs_k, m, op, alpha)
+    else:
+        w = weights_sized(nodes.xyz, dbl.xyz, dbl.period, ids, n_per, phs_k, m, op, alpha)
+        n_use = w.shape[2]
     sub = ids[:, :n_use]
     return Stencil(idx=np.ascontiguousarray(orig[sub]), w=w, code=np.ascontiguousarray(code[sub], dtype=np.uint8))
+
+
+def wall_sizes(nodes, n, n_wall, band=1.0):
+    """Stencil size per node of a PEC box: n_wall for the nodes closer than
+    `band` to a wall (the layer next to the walls), n elsewhere. Next to a
+    mirror plane the n nearest of the nodes and their images are a set with
+    mirror-paired nodes, and at n = 2 M_m (the fewest the rule of Sec. 4.1
+    allows) some of these stencils give the collocated curl an eigenvalue
+    with a large positive real part that the hyperviscosity does not
+    outweigh; a few more nodes in that layer remove it."""
+    x = _f64(nodes.xyz)
+    lo = np.asarray(nodes.box_lo, dtype=np.float64)
+    hi = np.asarray(nodes.box_hi, dtype=np.float64)
+    dw = np.minimum(x - lo, hi - x).min(axis=1)
+    return np.where(dw < band, n_wall, n).astype(np.int64)
 
 
 def tmz_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=None, nh_override=None):
@@ -566,12 +602,16 @@ def tmz_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=None, nh_o
                pec=np.zeros(nodes.n, np.uint8), dt=dt, eps0=eps0, mu0=mu0, gamma=gamma)
 
 
-def max3d_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=None, nh_override=None):
-    """The 3D collocated problem of a PEC box with image stencils (see tmz_images)."""
+def max3d_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=None, nh_override=None, n_wall=None,
+                 wall_band=1.0):
+    """The 3D collocated problem of a PEC box with image stencils (see
+    tmz_images). With n_wall, the curl stencils of the nodes closer than
+    wall_band to a wall take n_wall entries (wall_sizes)."""
     import math
     nhv = nh_override or (2 * math.comb(2 * alpha + 3, 3) + 1)
-    dbl, ids, orig, code = image_stencils(nodes, max(n, nhv))
-    c = _image_stencil(nodes, dbl, ids, orig, code, n, phs_k, m, OP_GRAD)
+    n_per = None if n_wall is None else wall_sizes(nodes, n, n_wall, wall_band)
+    dbl, ids, orig, code = image_stencils(nodes, max(n, nhv, n_wall or 0))
+    c = _image_stencil(nodes, dbl, ids, orig, code, n, phs_k, m, OP_GRAD, n_per=n_per)
     v = _image_stencil(nodes, dbl, ids, orig, code, nhv, 2 * alpha + 1, 2 * alpha, OP_LAP_POW, alpha)
     er = np.ones(nodes.n) if eps_r is None else _f64(eps_r)
     return Max3D(n=nodes.n, c=c, v=v, eps_r=er, wall=np.zeros(nodes.n, np.uint8), dt=dt, eps0=eps0, mu0=mu0,
@@ -586,8 +626,8 @@ def run_tmz_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, ez, hx, hy, 
 
 
 def run_3d_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, E, H, nsteps, eps_r=None, energy=False,
-                  nh_override=None):
+                  nh_override=None, n_wall=None, wall_band=1.0):
     """The 3D step on a PEC box with image stencils (max3d_images): (E, H, energy)."""
-    prob = max3d_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r, nh_override)
+    prob = max3d_images(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r, nh_override, n_wall, wall_band)
     E1, H1, _, en = run_3d(prob, E, H, nsteps, energy=energy)
     return E1, H1, en

@@ -181,3 +181,52 @@ def test_3d_pec_cube_with_images_is_stable_one_sided_walls_grow():
     E0, H0 = W.tm110_fields_3d(walls.xyz, 9.0, c0, mu0, 0.0, -0.5 * dt)
     _, _, _, en2 = O.run_3d(prob, np.array(E0), np.array(H0), 200, energy=True)
     assert en2[-1] / en2[0] > 1e3
+
+
+def _corner_of_the_100_cube():
+    """The cells [26, 38) x [60, 72) x [0, 8) of the 100^3 PEC box of seed 3 as a
+    PEC box of their own (its z = 0 face is the cube's wall): with 40-node
+    curl stencils (r^3, degree 3) the layer at that wall holds a mode that
+    grows by about e^0.05 per step under Delta^2 HV with c = 1e-3 (the 200^3
+    and 100^3 cubes of the 3D workload grew from such places)."""
+    full = W.pec_box_cells((100, 100, 100), 0.25, 3)
+    lo, size = np.array([26, 60, 0]), np.array([12, 12, 8])
+    cell = np.floor(full.xyz).astype(np.int64)
+    sel = np.all((cell >= lo) & (cell < lo + size), axis=1)
+    return W.NodeSet(xyz=full.xyz[sel] - lo, pec=np.zeros(int(sel.sum()), np.uint8), period=np.zeros(3),
+                     box_lo=np.zeros(3), box_hi=size.astype(float), normal_axes=np.zeros(int(sel.sum()), np.uint8))
+
+
+def test_wall_sized_stencils_are_the_plain_stencils_of_each_size():
+    box = W.pec_box_cells((6, 7, 5), 0.25, 17)
+    dt, eps0, mu0, c0, eta0 = W.units(0.5)
+    p = O.max3d_images(box, 40, 3, 3, 2, dt, eps0, mu0, -1e-3, n_wall=44)
+    sizes = O.wall_sizes(box, 40, 44)
+    assert set(np.unique(sizes)) == {40, 44}
+    dbl, ids, orig, code = O.image_stencils(box, 71)
+    for n_use in (40, 44):
+        sel = np.nonzero(sizes == n_use)[0]
+        ref = O.weights(box.xyz[sel], dbl.xyz, dbl.period, ids[sel], n_use, 3, 3, O.OP_GRAD)
+        assert np.array_equal(p.c.w[:, sel, :n_use], ref)
+        assert not np.any(p.c.w[:, sel, n_use:])
+        assert np.array_equal(p.c.idx[sel], orig[ids[sel, :44]])
+    # every weight row still differentiates the monomials up to degree 3 exactly
+    rel = dbl.xyz[ids[:, :44]] - box.xyz[:, None, :]
+    rel -= dbl.period * np.round(rel / dbl.period)  # minimum image on the doubled box
+    for e in O.monomials(3, 3):
+        vals = np.prod(rel ** e[None, None, :], axis=2)
+        for a in range(3):
+            want = float(e[a] == 1 and e.sum() == 1)
+            got = np.einsum("ij,ij->i", p.c.w[a], vals)
+            assert np.max(np.abs(got - want)) < 1e-8
+
+
+def test_a_larger_wall_layer_stencil_removes_the_growing_wall_mode():
+    box = _corner_of_the_100_cube()
+    dt, eps0, mu0, c0, eta0 = W.units(0.5)
+    rng = np.random.default_rng(1)
+    E0, H0 = rng.standard_normal((3, box.n)), rng.standard_normal((3, box.n))
+    _, _, en40 = O.run_3d_images(box, 40, 3, 3, 2, dt, eps0, mu0, -1e-3, E0, H0, 300, energy=True)
+    _, _, en44 = O.run_3d_images(box, 40, 3, 3, 2, dt, eps0, mu0, -1e-3, E0, H0, 300, energy=True, n_wall=44)
+    assert en40[-1] / en40[0] > 1e3
+    assert np.all(en44 / en44[0] <= 1.0 + 1e-6)
