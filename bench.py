@@ -49,8 +49,8 @@ def _args():
     ap.add_argument("--accuracy-steps", type=int, default=5000,
                     help="FP32-vs-FP64 (GPU) relative L2 error after this many steps (0: skip)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 step and the accuracy runs")
-    ap.add_argument("--cube-steps", type=int, default=200,
-                    help="steps of the 3D 200^3 workload (0: skip)")
+    ap.add_argument("--cube-steps", type=int, default=2000,
+                    help="steps of the 3D 200^3 PEC-cube workload (0: skip)")
     ap.add_argument("--cube-nx", type=int, default=200, help="nodes per side of the 3D cube")
     ap.add_argument("--yee-grid", type=int, default=8192, help="cells per side of the FDTD roofline grid")
     ap.add_argument("--batched-ndom", type=int, default=256, help="domains of the batched workload")
@@ -305,27 +305,49 @@ def oracle_checks(gpu):
         out["cavity_fp64"] = {"workload": "cavity TM11, 100x100 PEC, n=12, FP64 (whole workload)",
                               "steps": g["steps"], "rel_l2": _rel(g["fields"], ref),
                               "max_abs": _maxabs(g["fields"], ref), "probe_rel_l2": _rel(g["probes"], o[3])}
-    # 3D: the first step at full size (sampled nodes) and a whole run of a 32^3 cube
+    # 3D PEC cube: the first step at full size (sampled nodes far from the walls,
+    # and sampled nodes in a corner, where the stencils take images) and a whole
+    # run of a 32^3 cube
     g = gpu.get("cube3d")
     if g:
         t = time.perf_counter()
         S, cc, n, k, m, alpha = (CUBE[x] for x in ("S", "c", "n", "k", "m", "alpha"))
         dt, eps0, mu0, c0, eta0 = W.units(S)
         sm = g["sampled"]
-        ids = sm["ids"]
-        RE, RH, hs = O.max3d_sample_step(sm["nodes"], ids, n, k, m, alpha, dt, eps0, mu0, -cc, sm["E0"], sm["H0"],
+        nodes = sm["nodes"]
+        ids = sm["ids_in"]
+        # away from the walls no stencil of a node the step reads takes an image:
+        # the plain stencils of the box's own nodes
+        RE, RH, hs = O.max3d_sample_step(nodes, ids, n, k, m, alpha, dt, eps0, mu0, -cc, sm["E0"], sm["H0"],
                                          eps_r=sm["eps_r"], h_ids=ids)
         RHi = RH[:, np.searchsorted(hs, ids)]
-        got = np.concatenate([sm["E1"].ravel(), sm["H1"].ravel()])
+        got = np.concatenate([sm["E1_in"].ravel(), sm["H1_in"].ravel()])
         ref = np.concatenate([RE.ravel(), RHi.ravel()])
-        res = {"workload": "cube3d periodic", "full_size_first_step": {
-            "nodes": sm["nodes"].n, "sampled_nodes": len(ids), "rel_l2": _rel(got, ref), "max_abs": _maxabs(got, ref)}}
+        res = {"workload": "cube3d-pec (walls by images)", "full_size_first_step_interior": {
+            "nodes": nodes.n, "sampled_nodes": len(ids), "rel_l2": _rel(got, ref), "max_abs": _maxabs(got, ref)}}
+        # the corner: the oracle's image scheme on the 20^3 cells at the corner,
+        # a PEC box of its own whose far walls lie beyond what the sampled
+        # nodes' first step reads (two stencil radii, under 6 spacings)
+        cell = np.floor(nodes.xyz).astype(np.int64)
+        sub = np.nonzero(np.all(cell < 20, axis=1))[0]
+        crop = W.NodeSet(xyz=nodes.xyz[sub], pec=np.zeros(len(sub), np.uint8), period=np.zeros(3),
+                         box_lo=np.zeros(3), box_hi=np.full(3, 20.0), normal_axes=np.zeros(len(sub), np.uint8))
+        prob = O.max3d_images(crop, n, k, m, alpha, dt, eps0, mu0, -cc, eps_r=sm["eps_r"][sub], n_wall=CUBE["n_wall"])
+        RE, RH, _, _ = O.run_3d(prob, sm["E0"][:, sub], sm["H0"][:, sub], 1)
+        at = np.searchsorted(sub, sm["ids_wall"])
+        got = np.concatenate([sm["E1_wall"].ravel(), sm["H1_wall"].ravel()])
+        ref = np.concatenate([RE[:, at].ravel(), RH[:, at].ravel()])
+        res["full_size_first_step_corner"] = {"sampled_nodes": len(at), "rel_l2": _rel(got, ref),
+                                              "max_abs": _maxabs(got, ref)}
         sg = g["small"]
-        prob, _ = O.max3d_collocated(sg["nodes"], n, k, m, alpha, dt, eps0, mu0, -cc, eps_r=sg["eps_r"])
-        RE, RH, _, _ = O.run_3d(prob, sg["E0"], sg["H0"], sg["steps"])
+        RE, RH, en = O.run_3d_images(sg["nodes"], n, k, m, alpha, dt, eps0, mu0, -cc, sg["E0"], sg["H0"],
+                                     sg["steps"], eps_r=sg["eps_r"], energy=True, n_wall=CUBE["n_wall"])
         ref = np.concatenate([RE, RH])
+        u = en / en[0]
         res[f"cube_{sg['nx']}^3_whole_run"] = {"steps": sg["steps"], "rel_l2": _rel(sg["fields"], ref),
-                                              "max_abs": _maxabs(sg["fields"], ref)}
+                                              "max_abs": _maxabs(sg["fields"], ref),
+                                              "oracle_energy_rel": {"min": float(u.min()), "max": float(u.max()),
+                                                                    "end": float(u[-1])}}
         res["oracle_s"] = round(time.perf_counter() - t, 2)
         out["cube3d"] = res
     # batched: whole domains (one of each stencil size), four right-hand sides each
@@ -789,35 +811,69 @@ def batched(M, ctx, steps, peak, peak_kind, ndom=256, nrhs=16):
             "_gpu": check}
 
 
-def cube3d(M, ctx, steps, peak, peak_kind, nx=200):
-    """3D full-vector workload: 200^3 = 8M jittered nodes, collocated, curl
-    stencils of 40 nodes (PHS r^3, degree 3), Delta^2 HV on 71 nodes (r^5,
-    degree 4), eps_r = 1 + 3 g (smoothed Gaussian random field), FP32 state with
-    compensated sums, FP64 weight solves, TM110 initial fields. The cube is
-    periodic: with PEC walls the 3D scheme grew for every Courant number and HV
-    coefficient tried in the oracle."""
-    S, c, n, k, m, alpha = 0.5, 1e-3, 40, 3, 3, 2
+def _pec_cube(M, ctx, nx):
+    """The 3D workload's node set and operators: nx^3 jittered cell-centred
+    nodes in the PEC cube [0, nx]^3 (walls by images), curl stencils of 40 nodes
+    (PHS r^3, degree 3) and of 44 nodes in the layer next to the walls, Delta^2
+    HV on 71 nodes (r^5, degree 4), eps_r = 1 + 3 g (smoothed Gaussian random
+    field), FP32 state with compensated sums, TM110 initial fields."""
+    S, c, n, k, m, alpha, n_wall = (CUBE[x] for x in ("S", "c", "n", "k", "m", "alpha", "n_wall"))
     dt, eps0, mu0, c0, eta0 = W.units(S)
     t = time.time()
-    nodes = W.periodic_box((nx, nx, nx), 0.25, 3)
+    nodes = W.pec_box_cells((nx, nx, nx), 0.25, 3)
     er = W.eps_r_smooth_3d(nodes.xyz, nodes.box_hi, 33)
+    E0, H0 = W.tm110_fields_3d(nodes.xyz, float(nx), c0, mu0, 0.0, -0.5 * dt)
     gen_s = time.time() - t
     t = time.time()
     nd = M.Nodes(ctx, nodes.xyz, nodes.period)
+    nd.set_mirror(7, nodes.box_hi)
     nhv = 2 * math.comb(2 * alpha + 3, 3) + 1
-    st = M.Stencils(nd, nd, max(n, nhv))
+    st = M.Stencils(nd, nd, max(n_wall, nhv))
     ctx.sync()
     t_knn = time.time() - t
     t = time.time()
-    cw = M.Weights(st, n, k, m, M.MFD_OP_GRAD)
+    sizes = M.wall_layer_sizes(nodes.xyz, nodes.box_lo, nodes.box_hi, n, n_wall)
+    cw = M.Weights(st, sizes, k, m, M.MFD_OP_GRAD)
     hw = M.Weights(st, nhv, 2 * alpha + 1, 2 * alpha, M.MFD_OP_LAP_POW, alpha)
     ctx.sync()
     t_w = time.time() - t
     sim = M.Sim(ctx, 3, M.MFD_FP32, dt, eps0, mu0, -c, cw, hw, compensated=True)
     sim.set_materials(er, None)
-    (ex, ey, ez), (hx, hy, hz) = W.tm110_fields_3d(nodes.xyz, nx / 2, c0, mu0, 0.0, -0.5 * dt)
-    for comp, v in zip(range(6), (ex, ey, ez, hx, hy, hz)):
+    for comp, v in zip(range(6), (*E0, *H0)):
         sim.set_field(comp, v)
+    return sim, (nd, st, cw, hw), nodes, er, np.stack(E0), np.stack(H0), {
+        "generate": round(gen_s, 2), "morton_knn_images": round(t_knn, 2), "weights_fp64": round(t_w, 2),
+        "curl_nodes_mean": float(sizes.mean())}
+
+
+def cube3d(M, ctx, steps, peak, peak_kind, nx=200):
+    """3D full-vector workload: 200^3 = 8M jittered nodes in a PEC cube, walls
+    by images (every stencil among the nodes and their mirror images, image
+    values signed by the parity of the field component), 2000 FP32 steps (see
+    _pec_cube for the operators). Also the first step from the seeded state at
+    sampled nodes (in the timed launch configuration) and a whole 32^3 run, for
+    the comparison with the oracle."""
+    n, alpha = CUBE["n"], CUBE["alpha"]
+    nhv = 2 * math.comb(2 * alpha + 3, 3) + 1
+    sim, keep, nodes, er, E0, H0, setup = _pec_cube(M, ctx, nx)
+    nbar = setup["curl_nodes_mean"]  # curl entries per node (40, and 44 next to the walls)
+    u0 = sim.energy()  # Eq. 20 of the initial state
+    # the first step from the seeded initial state, before any other step
+    sim.step(1)
+    rng = np.random.default_rng(12)
+    cell = np.floor(nodes.xyz).astype(np.int64)
+    far = np.all((cell >= 12) & (cell < nx - 12), axis=1)
+    corner = np.all(cell < 6, axis=1)
+    ids_in = np.sort(rng.choice(np.nonzero(far)[0], 24, replace=False))
+    ids_wall = np.sort(rng.choice(np.nonzero(corner)[0], 24, replace=False))
+    E1 = np.stack([sim.get_field(a) for a in range(3)])
+    H1 = np.stack([sim.get_field(3 + a) for a in range(3)])
+    sampled = {"nx": nx, "nodes": nodes, "eps_r": er, "E0": E0, "H0": H0, "ids_in": ids_in, "ids_wall": ids_wall,
+               "E1_in": E1[:, ids_in], "H1_in": H1[:, ids_in], "E1_wall": E1[:, ids_wall], "H1_wall": H1[:, ids_wall]}
+    del E1, H1
+    for comp in range(3):
+        sim.set_field(comp, E0[comp])
+        sim.set_field(3 + comp, H0[comp])
     import torch
     stream = ctx.torch_stream()
     sim.step(10)
@@ -829,61 +885,41 @@ def cube3d(M, ctx, steps, peak, peak_kind, nx=200):
     t1.record(stream)
     torch.cuda.synchronize()
     el = t0.elapsed_time(t1) / 1e3
-    ms = sim.step_timed(min(steps, 100))
+    u_end = sim.energy()
     kk = min(steps, 100)
-    # for the comparison with the oracle: the first step from the seeded initial
-    # state at 24 sampled nodes, in the timed launch configuration
-    rng = np.random.default_rng(12)
-    ids = np.sort(rng.choice(nodes.n, 24, replace=False))
-    for comp, v in zip(range(6), (ex, ey, ez, hx, hy, hz)):
-        sim.set_field(comp, v)
-    sim.step(1)
-    sampled = {"ids": ids, "E1": np.stack([sim.get_field(a)[ids] for a in range(3)]),
-               "H1": np.stack([sim.get_field(3 + a)[ids] for a in range(3)]), "nodes": nodes, "eps_r": er,
-               "E0": np.stack([ex, ey, ez]), "H0": np.stack([hx, hy, hz])}
+    ms = sim.step_timed(kk)
     small = _cube_small_gpu(M, ctx, 32, 2000)
     s4 = 4
-    bh = 4 * max(n, nhv) + s4 * (3 * n + nhv) + 12 * s4
-    be = 4 * n + s4 * 3 * n + 9 * s4
+    bh = 4 * max(nbar, nhv) + s4 * (3 * nbar + nhv) + 12 * s4
+    be = 4 * nbar + s4 * 3 * nbar + 9 * s4
     h_avg, e_avg = ms[0] / kk / 1e3, ms[1] / kk / 1e3
     dom = "k_h3" if h_avg >= e_avg else "k_e3"
     dom_b = (bh if dom == "k_h3" else be) * nodes.n
     dom_t = max(h_avg, e_avg)
     ach = dom_b / dom_t / 1e9
-    return {"workload": f"cube3d {nx}^3 periodic, n={n}, N_h={nhv}, FP32", "nodes": nodes.n,
+    return {"workload": f"cube3d-pec {nx}^3 (walls by images), n={n} (44 next to the walls), N_h={nhv}, FP32",
+            "nodes": nodes.n,
             "value": nodes.n * 6 * steps / el, "unit": UNIT, "steps": steps, "ms_per_step": el / steps * 1e3,
-            "setup_s": {"generate": round(gen_s, 2), "morton_knn": round(t_knn, 2), "weights_fp64": round(t_w, 2)},
+            "setup_s": setup, "energy_rel_after_run": float(u_end / u0), "energy_after_steps": steps + 10,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "traffic": traffic_record(dom, s4), "kernel": dom, "peak_kind": peak_kind,
+                         "traffic": traffic_record(dom + "_images", s4), "kernel": dom, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": dom_b, "avg_launch_ms": dom_t * 1e3,
                          "other_kernel_avg_launch_ms": min(h_avg, e_avg) * 1e3,
                          "step_achieved_gbs": (bh + be) * nodes.n / (el / steps) / 1e9},
             "_gpu": {"sampled": sampled, "small": small}}
 
 
-CUBE = dict(S=0.5, c=1e-3, n=40, k=3, m=3, alpha=2)
+CUBE = dict(S=0.5, c=1e-3, n=40, k=3, m=3, alpha=2, n_wall=44)
 
 
 def _cube_small_gpu(M, ctx, nx, steps):
-    """The 3D workload's problem on an nx^3 cube (same stencils, coefficients,
-    eps_r recipe and TM110 fields), every field after `steps` FP32 steps."""
-    S, c, n, k, m, alpha = (CUBE[x] for x in ("S", "c", "n", "k", "m", "alpha"))
-    dt, eps0, mu0, c0, eta0 = W.units(S)
-    nodes = W.periodic_box((nx, nx, nx), 0.25, 3)
-    er = W.eps_r_smooth_3d(nodes.xyz, nodes.box_hi, 33)
-    nd = M.Nodes(ctx, nodes.xyz, nodes.period)
-    nhv = 2 * math.comb(2 * alpha + 3, 3) + 1
-    st = M.Stencils(nd, nd, max(n, nhv))
-    cw = M.Weights(st, n, k, m, M.MFD_OP_GRAD)
-    hw = M.Weights(st, nhv, 2 * alpha + 1, 2 * alpha, M.MFD_OP_LAP_POW, alpha)
-    sim = M.Sim(ctx, 3, M.MFD_FP32, dt, eps0, mu0, -c, cw, hw, compensated=True)
-    sim.set_materials(er, None)
-    E0, H0 = W.tm110_fields_3d(nodes.xyz, nx / 2, c0, mu0, 0.0, -0.5 * dt)
-    for comp, v in zip(range(6), (*E0, *H0)):
-        sim.set_field(comp, v)
+    """The 3D workload's problem on an nx^3 PEC cube (same stencils,
+    coefficients, eps_r recipe and TM110 fields), every field after `steps`
+    FP32 steps."""
+    sim, keep, nodes, er, E0, H0, _ = _pec_cube(M, ctx, nx)
     sim.step(steps)
     return {"nx": nx, "steps": steps, "fields": np.stack([sim.get_field(a) for a in range(6)]),
-            "nodes": nodes, "eps_r": er, "E0": np.stack(E0), "H0": np.stack(H0)}
+            "nodes": nodes, "eps_r": er, "E0": E0, "H0": H0}
 
 
 def cavity(M, ctx, steps=1000):

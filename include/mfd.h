@@ -170,6 +170,17 @@ void mfd_stencils_destroy(mfd_stencils* st);
  * Returns MFD_ERR_SINGULAR if any system had an exactly zero pivot. */
 mfd_status mfd_weights_compute(const mfd_stencils* st, int n_use, int phs_k, int poly_m, int op,
                                int alpha, double delta, mfd_weights** out);
+/* mfd_weights_compute with a stencil size per centre: centre c takes the first
+ * n_per_centre[c] entries of its stencil (host array, caller's centre order,
+ * each in 1..n of the stencils object). Rows are max(n_per_centre) long, zero
+ * past the centre's own size (mfd_weights_read). A simulation takes such
+ * weights as the curl weights of the 3D layout, where each 32-node slice of the
+ * packed streams reads only the chunks its centres need; elsewhere (the 2D
+ * layouts, hyperviscosity weights, batches) they are refused with MFD_ERR_ARG.
+ * The method fixes one n per operator (Sec. 4.1); a larger curl stencil in the
+ * layer next to mirror walls keeps the 3D scheme with images stable there. */
+mfd_status mfd_weights_compute_sized(const mfd_stencils* st, const int32_t* n_per_centre, int phs_k, int poly_m,
+                                     int op, int alpha, double delta, mfd_weights** out);
 /* w (host, nout x count(centres) x n_use) in the caller's centre order,
  * entry j of a row being the weight of stencil entry j (mfd_stencils_read). */
 mfd_status mfd_weights_read(const mfd_weights* w, double* host_w);

@@ -355,12 +355,17 @@ class Max3D:
     gamma: float
 
 
-def max3d_collocated(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=None, nh_override=None):
+def max3d_collocated(nodes, n, phs_k, m, alpha, dt, eps0, mu0, gamma, eps_r=None, nh_override=None, n_per=None):
+    """The 3D collocated problem; n_per: a curl stencil size per node (weights_sized) instead of n."""
     import math
     nhv = nh_override or (2 * math.comb(2 * alpha + 3, 3) + 1)
-    L = max(n, nhv)
+    L = max(n, nhv) if n_per is None else max(int(np.max(n_per)), nhv)
     idx = knn(nodes.xyz, nodes.xyz, nodes.period, L)
-    c = _stencil(nodes.xyz, nodes.xyz, nodes.period, idx, n, phs_k, m, OP_GRAD)
+    if n_per is None:
+        c = _stencil(nodes.xyz, nodes.xyz, nodes.period, idx, n, phs_k, m, OP_GRAD)
+    else:
+        w = weights_sized(nodes.xyz, nodes.xyz, nodes.period, idx, n_per, phs_k, m, OP_GRAD)
+        c = Stencil(idx=np.ascontiguousarray(idx[:, :w.shape[2]]), w=w)
     v = _stencil(nodes.xyz, nodes.xyz, nodes.period, idx, nhv, 2 * alpha + 1, 2 * alpha,
                  OP_LAP_POW, alpha)
     er = np.ones(nodes.n) if eps_r is None else _f64(eps_r)

@@ -58,6 +58,7 @@ _SIGS = {
     "mfd_stencils_read": (_I, [_VP, _VP]),
     "mfd_stencils_destroy": (None, [_VP]),
     "mfd_weights_compute": (_I, [_VP, _I, _I, _I, _I, _I, _D, C.POINTER(_VP)]),
+    "mfd_weights_compute_sized": (_I, [_VP, _VP, _I, _I, _I, _I, _D, C.POINTER(_VP)]),
     "mfd_weights_read": (_I, [_VP, _VP]),
     "mfd_weights_destroy": (None, [_VP]),
     "mfd_sim_create": (_I, [_VP, C.POINTER(mfd_sim_desc), C.POINTER(_VP)]),
@@ -368,12 +369,34 @@ class Stencils:
             pass
 
 
+def wall_layer_sizes(xyz, box_lo, box_hi, n, n_wall, band=1.0):
+    """Stencil size per node for mfd_weights_compute_sized: n_wall for the nodes
+    closer than `band` to a face of the box [box_lo, box_hi] (the layer next to
+    mirror walls), n elsewhere."""
+    x = np.asarray(xyz, dtype=np.float64)
+    d = np.minimum(x - np.asarray(box_lo, dtype=np.float64), np.asarray(box_hi, dtype=np.float64) - x).min(axis=1)
+    return np.where(d < band, int(n_wall), int(n)).astype(np.int32)
+
+
 class Weights:
-    def __init__(self, st: Stencils, n_use: int, phs_k: int, poly_m: int, op: int, alpha: int = 0,
+    """Stencil weights (mfd_weights_compute). n_use: one stencil size, or an
+    array with the size of every centre (caller order;
+    mfd_weights_compute_sized), the rows then being max(n_use) long."""
+
+    def __init__(self, st: Stencils, n_use, phs_k: int, poly_m: int, op: int, alpha: int = 0,
                  delta: float = 0.0):
         h = C.c_void_p()
-        _ck(lib().mfd_weights_compute(st.h, n_use, phs_k, poly_m, op, alpha, float(delta), C.byref(h)))
-        self.h, self.st, self.n_use, self.op = h, st, n_use, op
+        if np.ndim(n_use) == 0:
+            _ck(lib().mfd_weights_compute(st.h, int(n_use), phs_k, poly_m, op, alpha, float(delta), C.byref(h)))
+            n = int(n_use)
+        else:
+            sizes = np.ascontiguousarray(n_use, dtype=np.int32)
+            if sizes.shape != (st.centres.n,):
+                raise ValueError("one stencil size per centre expected")
+            _ck(lib().mfd_weights_compute_sized(st.h, _p(sizes), phs_k, poly_m, op, alpha, float(delta),
+                                                C.byref(h)))
+            n = int(sizes.max()) if sizes.size else 1
+        self.h, self.st, self.n_use, self.op = h, st, n, op
         self.nout = 1 if op == MFD_OP_LAP_POW else st.centres.dim
 
     def read(self):

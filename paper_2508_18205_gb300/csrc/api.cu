@@ -1,4 +1,6 @@
 // api.cu -- C ABI: errors, contexts, node sets, stencils and weights (include/mfd.h).
+#include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -318,10 +320,33 @@ mfd_status mfd_stencils_read(const mfd_stencils* st, int64_t* idx) {
 
 void mfd_stencils_destroy(mfd_stencils* st) { release(st); }
 
-mfd_status mfd_weights_compute(const mfd_stencils* st, int n_use, int phs_k, int poly_m, int op, int alpha,
-                               double delta, mfd_weights** out) {
+}  // extern "C"
+
+namespace {
+
+__global__ void k_sizes_to_device(const int32_t* __restrict__ user, const int64_t* __restrict__ perm, int64_t n,
+                                  int32_t* __restrict__ dev) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n) dev[k] = user[perm[k]];
+}
+
+// mfd_weights_compute(_sized): sizes == NULL for one stencil size n_use
+mfd_status weights_create(const mfd_stencils* st, int n_use, const int32_t* sizes, int phs_k, int poly_m, int op,
+                          int alpha, double delta, mfd_weights** out) {
     if (!st || !out) return fail(MFD_ERR_ARG, "NULL argument");
     *out = nullptr;
+    const int64_t N = st->centres->n;
+    int n_min = n_use;
+    if (sizes) {
+        n_use = 0;
+        n_min = INT32_MAX;
+        for (int64_t i = 0; i < N; ++i) {
+            n_use = std::max(n_use, (int)sizes[i]);
+            n_min = std::min(n_min, (int)sizes[i]);
+        }
+        if (N == 0) n_use = n_min = 1;
+        if (n_min < 1) return fail(MFD_ERR_ARG, "a stencil size is below 1");
+    }
     if (n_use < 1 || n_use > st->n) return fail(MFD_ERR_ARG, "n_use out of range");
     if (phs_k < 1 || phs_k > 9 || phs_k % 2 == 0) return fail(MFD_ERR_ARG, "phs_k must be odd, 1..9");
     if (poly_m < 0) return fail(MFD_ERR_ARG, "poly_m < 0");
@@ -334,14 +359,32 @@ mfd_status mfd_weights_compute(const mfd_stencils* st, int n_use, int phs_k, int
     if (!w) return fail(MFD_ERR_OOM, "host allocation failed");
     w->st = st;
     w->n_use = n_use;
+    w->n_min = n_min;
     w->nout = op == MFD_OP_LAP_POW ? 1 : st->centres->dim;
     w->op = op;
     w->phs_k = phs_k;
     w->poly_m = poly_m;
     w->alpha = alpha;
     w->delta = delta;
-    mfd_status s = w->w.alloc((size_t)w->nout * st->centres->n * n_use * 8);
-    if (!s) s = weights_solve(st, n_use, phs_k, poly_m, op, alpha, delta, w->w.as<double>());
+    mfd_status s = w->w.alloc((size_t)w->nout * N * n_use * 8);
+    if (!s && sizes && n_min < n_use) {  // sizes to device order
+        DevBuf user;
+        s = user.alloc(N * 4);
+        if (!s) s = w->nsz.alloc(N * 4);
+        if (!s) {
+            cudaStream_t cs = st->centres->ctx->stream;
+            cudaError_t e = cudaMemcpyAsync(user.p, sizes, N * 4, cudaMemcpyHostToDevice, cs);
+            if (e == cudaSuccess) {
+                k_sizes_to_device<<<(unsigned)((N + 255) / 256), 256, 0, cs>>>(
+                    user.as<int32_t>(), st->centres->perm.as<int64_t>(), N, w->nsz.as<int32_t>());
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+            if (e != cudaSuccess) s = fail(MFD_ERR_CUDA, cudaGetErrorString(e));
+        }
+    }
+    if (!s) s = weights_solve(st, n_use, w->nsz.p ? w->nsz.as<int32_t>() : nullptr, phs_k, poly_m, op, alpha, delta,
+                              w->w.as<double>());
     if (s) {
         delete w;
         return s;
@@ -349,6 +392,21 @@ mfd_status mfd_weights_compute(const mfd_stencils* st, int n_use, int phs_k, int
     retain(st);
     *out = w;
     return MFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mfd_status mfd_weights_compute(const mfd_stencils* st, int n_use, int phs_k, int poly_m, int op, int alpha,
+                               double delta, mfd_weights** out) {
+    return weights_create(st, n_use, nullptr, phs_k, poly_m, op, alpha, delta, out);
+}
+
+mfd_status mfd_weights_compute_sized(const mfd_stencils* st, const int32_t* n_per_centre, int phs_k, int poly_m,
+                                     int op, int alpha, double delta, mfd_weights** out) {
+    if (!n_per_centre) return fail(MFD_ERR_ARG, "NULL argument");
+    return weights_create(st, 0, n_per_centre, phs_k, poly_m, op, alpha, delta, out);
 }
 
 mfd_status mfd_weights_read(const mfd_weights* w, double* host_w) {

@@ -704,6 +704,8 @@ mfd_status mfd_batch_create(mfd_ctx* ctx, int ndom, const mfd_sim_desc* descs, i
         const mfd_nodes* nd = cw->st->centres;
         if (cw->st->sources != nd || nd->ctx != ctx) return bail(fail(MFD_ERR_ARG, "stencils must be own-set"));
         if (nd->mirror_axes) return bail(fail(MFD_ERR_ARG, "batched domains do not support mirror walls (images)"));
+        if (cw->nsz.p || hw->nsz.p)
+            return bail(fail(MFD_ERR_ARG, "batched domains take one stencil size per operator"));
         if (!(s.dt > 0) || !(s.eps0 > 0) || !(s.mu0 > 0)) return bail(fail(MFD_ERR_ARG, "dt, eps0, mu0 must be > 0"));
         BatchDomain& D = b->dom[d];
         D.nodes = nd;
@@ -760,8 +762,8 @@ mfd_status mfd_batch_create(mfd_ctx* ctx, int ndom, const mfd_sim_desc* descs, i
         DevBuf perm;
         if (plen <= 255) {
             if ((st = perm.alloc(N * plen))) return bail(st);
-            e0 = launch_row_perm(cw->st->idx.as<int32_t>(), cw->st->n, N, std::min(cw->n_use, hw->n_use), plen,
-                                 perm.as<uint8_t>(), s);
+            const int m = std::min(cw->n_use, hw->n_use);
+            e0 = launch_row_perm(cw->st->idx.as<int32_t>(), cw->st->n, N, m, m, plen, perm.as<uint8_t>(), s);
             if (e0 != cudaSuccess) return bail(fail(MFD_ERR_CUDA, cudaGetErrorString(e0)));
         }
         const uint8_t* pm = perm.p ? perm.as<uint8_t>() : nullptr;

@@ -113,7 +113,9 @@ struct mfd_weights {
     int op = 0;
     int phs_k = 0, poly_m = 0, alpha = 0;
     double delta = 0;
-    mfd::DevBuf w;  // double [nout][centres.n][n_use], centre device order
+    int n_min = 0;    // smallest stencil size of a centre (== n_use unless sizes vary)
+    mfd::DevBuf nsz;  // int32 stencil size per centre (device order) when sizes vary, else empty
+    mfd::DevBuf w;    // double [nout][centres.n][n_use], centre device order; a row is zero past its centre's size
 };
 
 namespace mfd {
@@ -161,11 +163,13 @@ mfd_status morton_order(mfd_ctx* ctx, int dim, int64_t n, const double* d_xyz_us
 mfd_status knn_build(const mfd_nodes* centres, const mfd_nodes* sources, int n, int32_t* d_idx);
 // kNN among the nodes of a set with mirror walls and their images (entries carry image codes)
 mfd_status knn_build_mirror(const mfd_nodes* centres, const mfd_nodes* sources, int n, int32_t* d_idx);
-mfd_status weights_solve(const mfd_stencils* st, int n_use, int phs_k, int poly_m, int op, int alpha,
-                         double delta, double* d_w);
+// n_use: row length (the largest stencil); d_nsz: per-centre sizes (device order) or NULL
+mfd_status weights_solve(const mfd_stencils* st, int n_use, const int32_t* d_nsz, int phs_k, int poly_m, int op,
+                         int alpha, double delta, double* d_w);
 // per row of a shared index array (n rows of `stride` entries, len <= 255 used):
 // the order that sorts entries [0, m) and [m, len) by neighbour id (k_row_perm)
-cudaError_t launch_row_perm(const int32_t* idx, int stride, int64_t n, int m, int len, uint8_t* perm,
+// entries sorted by neighbour id within [0, m1), [m1, m2) and [m2, len)
+cudaError_t launch_row_perm(const int32_t* idx, int stride, int64_t n, int m1, int m2, int len, uint8_t* perm,
                             cudaStream_t s);
 
 // ------------------------------------------------------------ dispersion (Sec. 6)

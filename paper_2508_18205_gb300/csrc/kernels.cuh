@@ -188,6 +188,8 @@ template <typename T> struct StencilStreams {
     int64_t n = 0;               // nodes
     int64_t src_c = 0, src_v = 0;  // sizes of the node sets the curl and HV indices point into
     bool mirror = false;           // entries carry image codes (PEC walls by images)
+    const uint8_t* cext = nullptr;  // curl chunks each 32-node slice reads (per-centre sizes), or null: nc
+    int nc0 = 0;                    // with cext: the fewest curl chunks of any slice
 };
 
 // ---- bounds-checked build (compiled with -DMFD_BOUNDS_CHECK): every stencil

@@ -99,22 +99,24 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v) {  // 21 bits -> every t
 }
 
 // Order of the packed entries of a shared index row: ascending neighbour id
-// within [0, m) and within [m, L), one thread per row (m = the shorter of the
-// two stencils sharing the row, both prefixes of it, so each keeps its entries).
+// within [0, m1), [m1, m2) and [m2, L), one thread per row (the split points
+// are the stencil sizes below L of the stencils sharing the row, each a prefix
+// of it, so each stencil keeps its entries; with per-centre sizes m1 and m2
+// are the smallest and largest curl stencil).
 // The entries keep their weights (the same permutation packs both), so a
 // stencil sum is the same sum in another order. Adjacent centres' neighbour
 // sets overlap, so ordering by id lines up the k-th gathers of a warp's
 // centres, which then touch fewer cache lines per warp load (on the jittered
 // 3D lattice 15 % fewer) in passes bound by the L1 data pipeline.
-__global__ void k_row_perm(const int32_t* __restrict__ src, int stride, int64_t N, int m, int L,
+__global__ void k_row_perm(const int32_t* __restrict__ src, int stride, int64_t N, int m1, int m2, int L,
                            uint8_t* __restrict__ perm) {
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= N) return;
     const int32_t* s = src + r * stride;
     uint8_t p[255];
     for (int j = 0; j < L; ++j) p[j] = (uint8_t)j;
-    const int lo[2] = {0, m}, hi[2] = {m, L};
-    for (int part = 0; part < 2; ++part)
+    const int lo[3] = {0, m1, m2}, hi[3] = {m1, m2, L};
+    for (int part = 0; part < 3; ++part)
         for (int j = lo[part] + 1; j < hi[part]; ++j) {
             const uint8_t pj = p[j];
             const int32_t v = s[pj];
@@ -128,10 +130,10 @@ __global__ void k_row_perm(const int32_t* __restrict__ src, int stride, int64_t 
     for (int j = 0; j < L; ++j) perm[r * L + j] = p[j];
 }
 
-cudaError_t launch_row_perm(const int32_t* idx, int stride, int64_t n, int m, int len, uint8_t* perm,
+cudaError_t launch_row_perm(const int32_t* idx, int stride, int64_t n, int m1, int m2, int len, uint8_t* perm,
                             cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_row_perm<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(idx, stride, n, m, len, perm);
+    k_row_perm<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(idx, stride, n, m1, m2, len, perm);
     return cudaGetLastError();
 }
 
@@ -564,13 +566,14 @@ struct WArgs {
     const double* xs;
     const int32_t* idx;
     int64_t nc;
-    int stride, n_use, dim, phs_k, M, op, alpha, nout;
+    int stride, n_use, dim, phs_k, M, op, alpha, nout;  // n_use: row length of w
+    const int32_t* nsz;        // stencil size per centre, or NULL (all n_use)
     double period[3];
     unsigned mirror;           // mirrored axes: an entry with image code r reflects x_a -> 2 mhi_a - x_a, a in r
     double mhi[3];
     double lap_rbf;            // prod_{i<alpha} (k-2i)(k-2i+d-2)
     double delta;
-    double* w;                 // [nout][nc][n_use]
+    double* w;                 // [nout][nc][n_use], zero past a centre's own size
     int* status;
 };
 
@@ -591,15 +594,17 @@ __device__ __forceinline__ double mono(const double* z, int q, int dim) {
 
 __global__ void __launch_bounds__(WS_THREADS) k_weights(WArgs a) {
     extern __shared__ double sm[];
-    const int n = a.n_use, M = a.M, K = n + M, nout = a.nout, ld = K + nout, dim = a.dim;
-    double* A = sm;                 // K x ld (augmented)
-    double* z = A + K * ld;         // n x 3 scaled offsets
-    double* fac = z + 3 * n;        // K elimination factors
+    const int M = a.M, nout = a.nout, dim = a.dim;
     __shared__ double red[WS_THREADS];
     __shared__ int redi[WS_THREADS];
     __shared__ int piv_s;
     const int tid = threadIdx.x;
     for (int64_t c = blockIdx.x; c < a.nc; c += gridDim.x) {
+        // this centre's system (the shared memory is sized for the largest)
+        const int n = a.nsz ? a.nsz[c] : a.n_use, K = n + M, ld = K + nout;
+        double* A = sm;                 // K x ld (augmented)
+        double* z = A + K * ld;         // n x 3 scaled offsets
+        double* fac = z + 3 * n;        // K elimination factors
         // offsets to the centre, minimum image
         for (int j = tid; j < n; j += WS_THREADS) {
             const int32_t raw = a.idx[c * a.stride + j];
@@ -775,9 +780,10 @@ __global__ void __launch_bounds__(WS_THREADS) k_weights(WArgs a) {
         __syncthreads();
         const int l = a.op == MFD_OP_LAP_POW ? 2 * a.alpha : 1;
         const double sl = ipow(inv, l);
-        for (int e = tid; e < n * nout; e += WS_THREADS) {
-            int o = e / n, j = e % n;
-            a.w[((int64_t)o * a.nc + c) * n + j] = A[j * ld + K + o] * sl;
+        const int rl = a.n_use;
+        for (int e = tid; e < rl * nout; e += WS_THREADS) {
+            int o = e / rl, j = e % rl;
+            a.w[((int64_t)o * a.nc + c) * rl + j] = j < n ? A[j * ld + K + o] * sl : 0.0;
         }
         __syncthreads();
     }
@@ -816,8 +822,8 @@ static void poly_tables(int dim, int m, int alpha, std::vector<std::array<int, 3
     }
 }
 
-mfd_status weights_solve(const mfd_stencils* st, int n_use, int phs_k, int poly_m, int op, int alpha, double delta,
-                         double* d_w) {
+mfd_status weights_solve(const mfd_stencils* st, int n_use, const int32_t* d_nsz, int phs_k, int poly_m, int op,
+                         int alpha, double delta, double* d_w) {
     const mfd_nodes* cen = st->centres;
     const mfd_nodes* src = st->sources;
     mfd_ctx* ctx = cen->ctx;
@@ -845,6 +851,7 @@ mfd_status weights_solve(const mfd_stencils* st, int n_use, int phs_k, int poly_
     a.nc = cen->n;
     a.stride = st->n;
     a.n_use = n_use;
+    a.nsz = d_nsz;
     a.dim = dim;
     a.phs_k = phs_k;
     a.M = M;

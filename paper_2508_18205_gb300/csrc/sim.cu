@@ -226,6 +226,8 @@ struct PackedStencil {
     int64_t n = 0;
     int64_t src_c = 0, src_v = 0;  // sizes of the node sets the curl and HV indices point into
     bool mirror = false;           // entries carry image codes (node set with mirror walls)
+    DevBuf cext;                   // uint8 curl chunks per slice when the curl stencil size varies, else empty
+    int nc0 = 0;                   // chunks of the smallest curl stencil
 };
 
 struct mfd_sim {
@@ -353,6 +355,15 @@ mfd_status pack_q16(mfd_ctx* ctx, const mfd_stencils* st, int n_use, int chunks4
     return MFD_OK;
 }
 
+// curl chunks of each 32-node slice: the most any of its centres needs
+__global__ void k_slice_chunks(const int32_t* __restrict__ nsz, int64_t N, int64_t slices, uint8_t* __restrict__ out) {
+    const int64_t sl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (sl >= slices) return;
+    int c = 0;
+    for (int64_t i = sl * 32; i < sl * 32 + 32 && i < N; ++i) c = max(c, (nsz[i] + 3) / 4);
+    out[sl] = (uint8_t)c;
+}
+
 // packs the curl and HV streams of one pass
 mfd_status pack_pass(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* hv, int dim, bool fp64, PackedStencil& p) {
     p.n = curl->st->centres->n;
@@ -365,7 +376,15 @@ mfd_status pack_pass(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* h
     check_rows(ctx, hv->st, hv->n_use);
 #endif
     p.nc = chunks_of(curl->n_use);
+    p.nc0 = chunks_of(curl->n_min);
     p.nv = chunks_of(hv->n_use);
+    if (curl->nsz.p) {  // per-centre curl sizes: each slice reads the chunks its centres need
+        const int64_t slices = (p.n + 31) / 32;
+        MFD_TRY(p.cext.alloc(std::max<int64_t>(slices, 1)));
+        k_slice_chunks<<<(unsigned)((slices + 127) / 128), 128, 0, ctx->stream>>>(curl->nsz.as<int32_t>(), p.n,
+                                                                                   slices, p.cext.as<uint8_t>());
+        MFD_CUDA(cudaGetLastError());
+    }
     const bool shared = curl->st == hv->st;
     DevBuf perm;
     int plen = 0;
@@ -375,8 +394,12 @@ mfd_status pack_pass(mfd_ctx* ctx, const mfd_weights* curl, const mfd_weights* h
         if (plen <= 255) {  // rows in ascending id order (launch_row_perm)
             const int64_t N = curl->st->centres->n;
             MFD_TRY(perm.alloc(N * plen));
-            MFD_CUDA(launch_row_perm(curl->st->idx.as<int32_t>(), curl->st->n, N,
-                                     std::min(curl->n_use, hv->n_use), plen, perm.as<uint8_t>(), ctx->stream));
+            // split points: the stencil sizes below plen (the smallest and the largest curl
+            // stencil and the HV stencil), so every stencil keeps its entries
+            int cut[3] = {curl->n_min, curl->n_use, hv->n_use};
+            std::sort(cut, cut + 3);
+            MFD_CUDA(launch_row_perm(curl->st->idx.as<int32_t>(), curl->st->n, N, cut[0], cut[1], plen,
+                                     perm.as<uint8_t>(), ctx->stream));
         }
         MFD_TRY(pack_stream(ctx, curl->st, plen, p.ni, p.idx_c, &perm, plen));
     } else {
@@ -417,6 +440,8 @@ template <typename T> StencilStreams<T> streams(const PackedStencil& p, bool q16
     s.src_c = p.src_c;
     s.src_v = p.idx_v.p ? p.src_v : p.src_c;
     s.mirror = p.mirror;
+    s.cext = p.cext.p ? p.cext.as<const uint8_t>() : nullptr;
+    s.nc0 = p.nc0;
     return s;
 }
 
@@ -654,6 +679,10 @@ mfd_status mfd_sim_create(mfd_ctx* ctx, const mfd_sim_desc* desc, mfd_sim** out)
     if (desc->dim == 3 && !colloc) return fail(MFD_ERR_ARG, "3D supports the collocated layout only");
     if (!colloc && (desc->h_curl->st->sources->mirror_axes || desc->e_curl->st->sources->mirror_axes))
         return fail(MFD_ERR_ARG, "mirror walls (images) are supported in the collocated layout");
+    if ((desc->h_hv && desc->h_hv->nsz.p) || (desc->e_hv && desc->e_hv->nsz.p))
+        return fail(MFD_ERR_ARG, "hyperviscosity weights take one stencil size");
+    if (desc->dim != 3 && (desc->h_curl->nsz.p || desc->e_curl->nsz.p))
+        return fail(MFD_ERR_ARG, "per-centre curl stencil sizes are supported in the 3D layout");
     MFD_CUDA(cudaSetDevice(ctx->device));
     mfd_sim* sim = new (std::nothrow) mfd_sim();
     if (!sim) return fail(MFD_ERR_OOM, "host allocation failed");

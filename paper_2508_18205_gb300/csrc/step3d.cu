@@ -26,7 +26,11 @@ __device__ __forceinline__ int4 ids3(int4 raw, int64_t n, uint4& r) {
     return chk4(raw, n);
 }
 
-template <typename T, int NC, int NV, bool SHARED, bool COMP, bool MIR = false>
+// VARN: the curl stencil size varies per centre (s.cext holds the chunks of
+// each slice); the other instantiations read nc chunks for every node. A
+// VARN instantiation with NC chunks is launched only when every slice reads
+// at least NC - 1 of them (s.nc0), so only the last chunk is conditional.
+template <typename T, int NC, int NV, bool SHARED, bool COMP, bool MIR = false, bool VARN = false>
 __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typename Vec<T>::V4* __restrict__ F,
                                         int64_t i, Curl<T>& cu, T vh[3], T ve[3]) {
     using V4 = typename Vec<T>::V4;
@@ -35,6 +39,10 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
     const int nv = NV ? NV : s.nv;
     const int64_t slice = i >> 5;
     const int lane = (int)(i & 31);
+    // curl chunks of this slice (warp-uniform): fewer than nc when the stencil
+    // size varies per centre and no centre of the slice needs the last ones
+    const int ncs = VARN ? (int)s.cext[slice] : nc;
+    constexpr int G = VARN ? (NC ? NC - 1 : 0) : NC;   // curl chunks every slice reads (NC = 0: none known)
     Acc a_yz, a_zy, a_zx, a_xz, a_xy, a_yx;            // curl sums (compensated when COMP)
     AccPlain<T> hx, hy, hz, ex, ey, ez;                 // hyperviscosity sums (scaled by gamma)
     const V4* px = s.wx + slice * nc * 32 + lane;
@@ -98,7 +106,11 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
                 e[2] = img_e3(e[2], r.z);
                 e[3] = img_e3(e[3], r.w);
             }
-            if (c < nc) curl4(ld_stream(px + c * 32), ld_stream(py + c * 32), ld_stream(pz + c * 32), e);
+            if constexpr (VARN) {
+                if (c < nc && (c < G || c < ncs)) curl4(ld_stream(px + c * 32), ld_stream(py + c * 32), ld_stream(pz + c * 32), e);
+            } else {
+                if (c < nc) curl4(ld_stream(px + c * 32), ld_stream(py + c * 32), ld_stream(pz + c * 32), e);
+            }
             if (c < nv) hv4(ld_stream(pv + c * 32), e, h);
         }
     } else {
@@ -106,6 +118,7 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
         const int4* iv = s.idx_v + slice * nv * 32 + lane;
 #pragma unroll
         for (int c = 0; c < nc; ++c) {
+            if (VARN && c >= G && c >= ncs) break;
             uint4 r;
             const int4 id = ids3<MIR>(ld_stream(ic + c * 32), s.src_c, r);
             V4 e[4];
@@ -158,7 +171,7 @@ __device__ __forceinline__ void h3_node(const StencilStreams<T>& s, const typena
 // The H pass may take up to 128 registers: at 256 threads per block the
 // compensated FP32 kernel runs 2 blocks per SM with 32 bytes of spills; caps
 // of 80 (3 blocks) and 64 registers (4 blocks) spilled more and were slower.
-template <typename T, int NC, int NV, bool SHARED, bool COMP, bool MIR = false>
+template <typename T, int NC, int NV, bool SHARED, bool COMP, bool MIR = false, bool VARN = false>
 __global__ void __launch_bounds__(512, 1) k_h3(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V4* __restrict__ F,
                                             typename Vec<T>::V4* __restrict__ Es,
                                             typename Vec<T>::V4* __restrict__ Hn) {
@@ -167,7 +180,7 @@ __global__ void __launch_bounds__(512, 1) k_h3(StencilStreams<T> s, Coefs<T> k, 
     if (i >= s.n) return;
     Curl<T> cu;
     T vh[3], ve[3];
-    h3_node<T, NC, NV, SHARED, COMP, MIR>(s, F, i, cu, vh, ve);
+    h3_node<T, NC, NV, SHARED, COMP, MIR, VARN>(s, F, i, cu, vh, ve);
     V4 e, h;
     ld_gather_eh(F + 2 * i, e, h);
     V4 ho, eo;
@@ -183,7 +196,7 @@ __global__ void __launch_bounds__(512, 1) k_h3(StencilStreams<T> s, Coefs<T> k, 
     st4(Es + i, eo);
 }
 
-template <typename T, int NC, bool SHARED, bool COMP, bool MIR = false>
+template <typename T, int NC, bool SHARED, bool COMP, bool MIR = false, bool VARN = false>
 __global__ void __launch_bounds__(512, 2) k_e3(StencilStreams<T> s, const typename Vec<T>::V4* __restrict__ Hn,
                                             const typename Vec<T>::V4* __restrict__ Es,
                                             const uint8_t* __restrict__ wall, typename Vec<T>::V4* __restrict__ F) {
@@ -199,9 +212,12 @@ __global__ void __launch_bounds__(512, 2) k_e3(StencilStreams<T> s, const typena
     const V4* px = s.wx + slice * nc * 32 + lane;
     const V4* py = s.wy + slice * nc * 32 + lane;
     const V4* pz = s.wz + slice * nc * 32 + lane;
+    const int ncs = VARN ? (int)s.cext[slice] : nc;  // curl chunks of this slice (see h3_node)
+    constexpr int G = VARN ? (NC ? NC - 1 : 0) : NC;
     Acc a_yz, a_zy, a_zx, a_xz, a_xy, a_yx;
 #pragma unroll
     for (int c = 0; c < nc; ++c) {
+        if (VARN && c >= G && c >= ncs) break;
         uint4 r;
         const int4 id = ids3<MIR>(ld_stream(ip + c * 32), s.src_c, r);
         const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32), wz = ld_stream(pz + c * 32);
@@ -246,7 +262,7 @@ __global__ void __launch_bounds__(512, 2) k_e3(StencilStreams<T> s, const typena
     st_eh(F + 2 * i, o, hown);
 }
 
-template <typename T, bool COMP, bool MIR = false>
+template <typename T, bool COMP, bool MIR = false, bool VARN = false>
 __global__ void __launch_bounds__(256) k_energy3(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V4* __restrict__ F,
                                                  const double* __restrict__ eps_r, double eta2,
                                                  double* __restrict__ partial) {
@@ -258,9 +274,9 @@ __global__ void __launch_bounds__(256) k_energy3(StencilStreams<T> s, Coefs<T> k
         Curl<T> cu;
         T vh[3], ve[3];
         if (s.idx_v == s.idx_c)
-            h3_node<T, 0, 0, true, COMP, MIR>(s, F, i, cu, vh, ve);
+            h3_node<T, 0, 0, true, COMP, MIR, VARN>(s, F, i, cu, vh, ve);
         else
-            h3_node<T, 0, 0, false, COMP, MIR>(s, F, i, cu, vh, ve);
+            h3_node<T, 0, 0, false, COMP, MIR, VARN>(s, F, i, cu, vh, ve);
         const V4 e = F[2 * i], h = F[2 * i + 1];
         const double h1[3] = {(double)(h.x + k.ch * (-(cu.dyz - cu.dzy) + k.gamma * vh[0])),
                               (double)(h.y + k.ch * (-(cu.dzx - cu.dxz) + k.gamma * vh[1])),
@@ -281,33 +297,40 @@ __global__ void __launch_bounds__(256) k_energy3(StencilStreams<T> s, Coefs<T> k
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
-template <typename T, bool COMP>
-static cudaError_t launch3(const Launch3D& L, const StencilStreams<T>& s, const Coefs<T>& k, int pass, cudaStream_t st) {
+// node sets with mirror walls (MIR): the same kernels with image codes;
+// per-centre curl sizes (VARN): each slice reads its own number of curl chunks
+template <typename T, bool COMP, bool MIR, bool VARN>
+static void launch3_k(const Launch3D& L, const StencilStreams<T>& s, const Coefs<T>& k, int pass, unsigned grid,
+                      int block, cudaStream_t st) {
     using V4 = typename Vec<T>::V4;
-    const int block = L.block[pass];
-    const unsigned grid = (unsigned)((s.n + block - 1) / block);
     const bool shared = s.idx_v == s.idx_c;
     V4* F = static_cast<V4*>(L.F);
     V4* Es = static_cast<V4*>(L.Es);
     V4* Hn = static_cast<V4*>(L.Hn);
-    if (s.mirror) {  // node sets with mirror walls: the generic kernels with image codes
-        if (pass == 0) {
-            if (shared) k_h3<T, 0, 0, true, COMP, true><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
-            else k_h3<T, 0, 0, false, COMP, true><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
-        } else {
-            if (shared) k_e3<T, 0, true, COMP, true><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F);
-            else k_e3<T, 0, false, COMP, true><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F);
-        }
-        return cudaGetLastError();
-    }
+    // the specialised chunk counts: n = 40 (and 41..44 next to mirror walls), N_h = 71
+    constexpr int NCS = VARN ? 11 : 10;
+    const bool spec = s.nc == NCS && (!VARN || s.nc0 >= NCS - 1);
     if (pass == 0) {
-        if (shared && s.nc == 10 && s.nv == 18) k_h3<T, 10, 18, true, COMP><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
-        else if (shared) k_h3<T, 0, 0, true, COMP><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
-        else k_h3<T, 0, 0, false, COMP><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
+        if (shared && spec && s.nv == 18) k_h3<T, NCS, 18, true, COMP, MIR, VARN><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
+        else if (shared) k_h3<T, 0, 0, true, COMP, MIR, VARN><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
+        else k_h3<T, 0, 0, false, COMP, MIR, VARN><<<grid, block, 0, st>>>(s, k, F, Es, Hn);
     } else {
-        if (shared && s.nc == 10) k_e3<T, 10, true, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F);
-        else if (shared) k_e3<T, 0, true, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F);
-        else k_e3<T, 0, false, COMP><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F);
+        if (shared && spec) k_e3<T, NCS, true, COMP, MIR, VARN><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F);
+        else if (shared) k_e3<T, 0, true, COMP, MIR, VARN><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F);
+        else k_e3<T, 0, false, COMP, MIR, VARN><<<grid, block, 0, st>>>(s, Hn, Es, L.wall, F);
+    }
+}
+
+template <typename T, bool COMP>
+static cudaError_t launch3(const Launch3D& L, const StencilStreams<T>& s, const Coefs<T>& k, int pass, cudaStream_t st) {
+    const int block = L.block[pass];
+    const unsigned grid = (unsigned)((s.n + block - 1) / block);
+    if (s.cext) {
+        if (s.mirror) launch3_k<T, COMP, true, true>(L, s, k, pass, grid, block, st);
+        else launch3_k<T, COMP, false, true>(L, s, k, pass, grid, block, st);
+    } else {
+        if (s.mirror) launch3_k<T, COMP, true, false>(L, s, k, pass, grid, block, st);
+        else launch3_k<T, COMP, false, false>(L, s, k, pass, grid, block, st);
     }
     return cudaGetLastError();
 }
@@ -318,19 +341,25 @@ cudaError_t launch_3d(const Launch3D& L, int pass, cudaStream_t st) {
     return launch3<float, false>(L, L.s.f, L.kf, pass, st);
 }
 
+template <typename T, bool COMP>
+static void energy3_k(const StencilStreams<T>& s, const Coefs<T>& k, const void* F, const double* eps_r, double eta2,
+                      double* partial, unsigned grid, cudaStream_t st) {
+    using V4 = typename Vec<T>::V4;
+    const V4* f = static_cast<const V4*>(F);
+    if (s.cext) {
+        if (s.mirror) k_energy3<T, COMP, true, true><<<grid, 256, 0, st>>>(s, k, f, eps_r, eta2, partial);
+        else k_energy3<T, COMP, false, true><<<grid, 256, 0, st>>>(s, k, f, eps_r, eta2, partial);
+    } else {
+        if (s.mirror) k_energy3<T, COMP, true><<<grid, 256, 0, st>>>(s, k, f, eps_r, eta2, partial);
+        else k_energy3<T, COMP><<<grid, 256, 0, st>>>(s, k, f, eps_r, eta2, partial);
+    }
+}
+
 cudaError_t launch_energy_3d(const Launch3D& L, const double* eps_r, double eta2, double* partial, unsigned grid,
                              cudaStream_t st) {
-    const bool mir = L.s.f.mirror;
-    if (L.fp64) {
-        if (mir) k_energy3<double, false, true><<<grid, 256, 0, st>>>(L.s.d, L.kd, (const dbl4*)L.F, eps_r, eta2, partial);
-        else k_energy3<double, false><<<grid, 256, 0, st>>>(L.s.d, L.kd, (const dbl4*)L.F, eps_r, eta2, partial);
-    } else if (L.comp) {
-        if (mir) k_energy3<float, true, true><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.F, eps_r, eta2, partial);
-        else k_energy3<float, true><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.F, eps_r, eta2, partial);
-    } else {
-        if (mir) k_energy3<float, false, true><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.F, eps_r, eta2, partial);
-        else k_energy3<float, false><<<grid, 256, 0, st>>>(L.s.f, L.kf, (const float4*)L.F, eps_r, eta2, partial);
-    }
+    if (L.fp64) energy3_k<double, false>(L.s.d, L.kd, L.F, eps_r, eta2, partial, grid, st);
+    else if (L.comp) energy3_k<float, true>(L.s.f, L.kf, L.F, eps_r, eta2, partial, grid, st);
+    else energy3_k<float, false>(L.s.f, L.kf, L.F, eps_r, eta2, partial, grid, st);
     return cudaGetLastError();
 }
 
