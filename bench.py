@@ -57,6 +57,8 @@ def _args():
     ap.add_argument("--no-extra", action="store_true", help="skip the cavity (FP64) and adjoint sections")
     ap.add_argument("--only", default="all", choices=["all", "batched", "cube3d", "cavity", "adjoint", "dispersion", "hv_search", "yee"],
                     help="run one section alone (profiling); prints that section as the JSON line")
+    ap.add_argument("--adjoint-steps", type=int, default=4000,
+                    help="steps of the differentiation workload (--only adjoint)")
     ap.add_argument("--batched-steps", type=int, default=3000,
                     help="steps of the batched 256-domain x 16-RHS workload (0: skip)")
     return ap.parse_args()
@@ -479,7 +481,7 @@ def main():
         elif a.only == "cavity":
             r = cavity(M, ctx)
         elif a.only == "adjoint":
-            r = adjoint(M, ctx)
+            r = adjoint(M, ctx, steps=a.adjoint_steps)
         elif a.only == "hv_search":
             r = hv_search(M, ctx)
         elif a.only == "yee":

@@ -269,10 +269,22 @@ mfd_status mfd_set_watchdog(mfd_sim* sim, int64_t every, double max_ratio);
  * 256 by default). */
 mfd_status mfd_sim_set_blocks(mfd_sim* sim, int block_h, int block_e);
 /* Autotuner: times each half-step kernel on this problem `reps` times with
- * 128, 256 and 512 threads per block, keeps the fastest for each (chosen[0]:
- * H pass, chosen[1]: E pass; may be NULL) and restores the fields, so the
+ * 128, 256 and 512 threads per block and, in the collocated 2D layout with one
+ * index row for both stencils, 1, 2 or 4 threads per node (each summing a
+ * share of the node's stencil chunks; the shares are added across the node's
+ * threads, so the choice changes the order of the stencil sums, not their
+ * terms); keeps the fastest for each pass (chosen[0]: H pass, chosen[1]: E
+ * pass, threads per block; may be NULL) and restores the fields, so the
  * simulation does not advance. */
 mfd_status mfd_sim_autotune(mfd_sim* sim, int reps, int* chosen);
+/* Threads per node of the H and E passes (1, 2 or 4) in the collocated 2D
+ * layout whose curl and HV stencils share one index row (else MFD_ERR_ARG). */
+mfd_status mfd_sim_set_lanes(mfd_sim* sim, int lanes_h, int lanes_e);
+/* The launch configuration in use: block[2] threads per block and lanes[2]
+ * threads per node of the H and E passes (1 outside the collocated 2D layout;
+ * before any autotuning 4 for node sets too small to fill the GPU, else 1).
+ * Either may be NULL. */
+mfd_status mfd_sim_launch_config(const mfd_sim* sim, int* block, int* lanes);
 /* Index format of the staggered step kernels. The stencil sums are the same
  * in both formats (same entries, same order), so the fields are bit-identical.
  *   MFD_INDEX_Q16 (the default): per slice of 32 nodes (one warp) and per

@@ -79,6 +79,8 @@ _SIGS = {
     "mfd_sim_set_blocks": (_I, [_VP, _I, _I]),
     "mfd_set_watchdog": (_I, [_VP, _I64, _D]),
     "mfd_sim_autotune": (_I, [_VP, _I, _VP]),
+    "mfd_sim_launch_config": (_I, [_VP, _VP, _VP]),
+    "mfd_sim_set_lanes": (_I, [_VP, _I, _I]),
     "mfd_sim_set_index_format": (_I, [_VP, _I]),
     "mfd_sim_index_stats": (_I, [_VP, _VP]),
     "mfd_sim_destroy": (None, [_VP]),
@@ -654,10 +656,22 @@ class Sim:
         return {"h": tuple(int(x) for x in out[:3]), "e": tuple(int(x) for x in out[3:])}
 
     def autotune(self, reps=20):
-        """Times 128/256/512 threads per block for each half-step kernel and keeps the fastest."""
+        """Times 128/256/512 threads per block (and, collocated 2D, 1/2/4 threads
+        per node) for each half-step kernel and keeps the fastest: the blocks."""
         ch = np.zeros(2, dtype=np.int32)
         _ck(lib().mfd_sim_autotune(self.h, int(reps), _p(ch)))
         return int(ch[0]), int(ch[1])
+
+    def set_lanes(self, lanes_h, lanes_e):
+        """Threads per node of the H and E passes (collocated 2D, mfd_sim_set_lanes)."""
+        _ck(lib().mfd_sim_set_lanes(self.h, int(lanes_h), int(lanes_e)))
+
+    def launch_config(self):
+        """((block H, block E), (lanes H, lanes E)) in use (mfd_sim_launch_config)."""
+        b = np.zeros(2, dtype=np.int32)
+        ln = np.zeros(2, dtype=np.int32)
+        _ck(lib().mfd_sim_launch_config(self.h, _p(b), _p(ln)))
+        return (int(b[0]), int(b[1])), (int(ln[0]), int(ln[1]))
 
     def save_state(self):
         """Checkpoint of the fields, the step index and the probe records (bytes, mfd_sim_save_state)."""

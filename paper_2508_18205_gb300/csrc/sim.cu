@@ -258,6 +258,7 @@ struct mfd_sim {
     bool adj_ok = false;
     int64_t adj_sweeps = 0;  // adjoint sweeps run (mfd_grad_backward)
     int block[2] = {256, 256};  // threads per block of the H and E half-step kernels (autotuned)
+    int lanes[2] = {0, 0};      // collocated 2D: lanes per node of each pass (0: the size rule; autotuned)
     bool q16 = true;            // staggered kernels read Q16 indices (mfd_sim_set_index_format)
     int64_t watch_every = 0;    // energy watchdog: check every this many steps (0: off)
     double watch_ratio = 0, watch_u0 = 0;
@@ -463,9 +464,11 @@ Launch2D make2d(mfd_sim* sim, int parity) {
     L.block[0] = sim->block[0];
     L.block[1] = sim->block[1];
     // collocated rows shared by both stencils: four lanes per node while one thread per node
-    // would occupy less than a quarter of the GPU's threads
-    if (!L.staggered && sim->hp.idx_v.p == nullptr && sim->ne * 4 <= (int64_t)sim->ctx->sm_count * 512)
-        L.lanes = 4;
+    // would occupy less than a quarter of the GPU's threads, unless the autotuner chose
+    if (!L.staggered && sim->hp.idx_v.p == nullptr) {
+        const int rule = sim->ne * 4 <= (int64_t)sim->ctx->sm_count * 512 ? 4 : 1;
+        for (int p = 0; p < 2; ++p) L.lanes[p] = sim->lanes[p] ? sim->lanes[p] : rule;
+    }
     if (!L.staggered) {
         L.A = sim->s0.p;
         L.B = sim->s1.p;
@@ -1185,6 +1188,28 @@ mfd_status mfd_sim_load_state(mfd_sim* sim, const void* host, size_t bytes) {
 
 static bool block_ok(int b) { return b == 64 || b == 128 || b == 256 || b == 512; }
 
+mfd_status mfd_sim_set_lanes(mfd_sim* sim, int lanes_h, int lanes_e) {
+    if (!sim) return fail(MFD_ERR_ARG, "NULL argument");
+    auto ok = [](int l) { return l == 1 || l == 2 || l == 4; };
+    if (!ok(lanes_h) || !ok(lanes_e)) return fail(MFD_ERR_ARG, "lanes per node: 1, 2 or 4");
+    if (sim->layout != COLLOC2D || sim->hp.idx_v.p != nullptr)
+        return fail(MFD_ERR_ARG, "lanes per node apply to the collocated 2D layout with one index row per node");
+    sim->lanes[0] = lanes_h;
+    sim->lanes[1] = lanes_e;
+    sim->graph_ok = false;
+    return MFD_OK;
+}
+
+mfd_status mfd_sim_launch_config(const mfd_sim* sim, int* block, int* lanes) {
+    if (!sim) return fail(MFD_ERR_ARG, "NULL argument");
+    const Launch2D L = sim->layout == COLLOC3D ? Launch2D{} : make2d(const_cast<mfd_sim*>(sim), sim->parity);
+    for (int p = 0; p < 2; ++p) {
+        if (block) block[p] = sim->block[p];
+        if (lanes) lanes[p] = sim->layout == COLLOC2D ? L.lanes[p] : 1;
+    }
+    return MFD_OK;
+}
+
 mfd_status mfd_sim_set_blocks(mfd_sim* sim, int block_h, int block_e) {
     if (!sim || !block_ok(block_h) || !block_ok(block_e)) return fail(MFD_ERR_ARG, "block sizes: 64, 128, 256 or 512");
     sim->block[0] = block_h;
@@ -1229,14 +1254,24 @@ mfd_status mfd_sim_autotune(mfd_sim* sim, int reps, int* chosen) {
     cudaEvent_t e0, e1;
     MFD_CUDA(cudaEventCreate(&e0));
     MFD_CUDA(cudaEventCreate(&e1));
+    // candidates: threads per block, and (collocated 2D rows shared by both
+    // stencils) lanes per node; the sums of a node are split over its lanes, so
+    // a choice changes the summation order, not the stencils
     const int cand[3] = {128, 256, 512};
+    const bool lanes_tuned = sim->layout == COLLOC2D && sim->hp.idx_v.p == nullptr;
+    const int lcand[3] = {1, 2, 4};
+    const int nl = lanes_tuned ? 3 : 1;
+    const Launch2D L0 = sim->layout == COLLOC3D ? Launch2D{} : make2d(sim, sim->parity);
     int best[2] = {sim->block[0], sim->block[1]};
+    int bestl[2] = {L0.lanes[0], L0.lanes[1]};
     mfd_status st = MFD_OK;
     for (int pass = 0; pass < 2 && st == MFD_OK; ++pass) {
         float tbest = 1e30f;
-        for (int c = 0; c < 3 && st == MFD_OK; ++c) {
+        for (int c = 0; c < 3 * nl && st == MFD_OK; ++c) {
             int blk[2] = {best[0], best[1]};
-            blk[pass] = cand[c];
+            int lan[2] = {bestl[0], bestl[1]};
+            blk[pass] = cand[c % 3];
+            if (lanes_tuned) lan[pass] = lcand[c / 3];
             cudaError_t e = cudaSuccess;
             auto launch = [&]() {
                 if (sim->layout == COLLOC3D) {
@@ -1248,6 +1283,10 @@ mfd_status mfd_sim_autotune(mfd_sim* sim, int reps, int* chosen) {
                 Launch2D L = make2d(sim, sim->parity);
                 L.block[0] = blk[0];
                 L.block[1] = blk[1];
+                if (lanes_tuned) {
+                    L.lanes[0] = lan[0];
+                    L.lanes[1] = lan[1];
+                }
                 return launch_2d(L, pass, s);
             };
             e = launch();
@@ -1263,7 +1302,8 @@ mfd_status mfd_sim_autotune(mfd_sim* sim, int reps, int* chosen) {
             }
             if (ms < tbest) {
                 tbest = ms;
-                best[pass] = cand[c];
+                best[pass] = blk[pass];
+                bestl[pass] = lan[pass];
             }
         }
     }
@@ -1275,6 +1315,10 @@ mfd_status mfd_sim_autotune(mfd_sim* sim, int reps, int* chosen) {
     if (st != MFD_OK) return st;
     sim->block[0] = best[0];
     sim->block[1] = best[1];
+    if (lanes_tuned) {
+        sim->lanes[0] = bestl[0];
+        sim->lanes[1] = bestl[1];
+    }
     sim->graph_ok = false;
     if (chosen) {
         chosen[0] = best[0];

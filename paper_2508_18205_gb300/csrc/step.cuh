@@ -25,7 +25,7 @@ struct Launch2D {
     Coefs<float> kf;
     Coefs<double> kd;
     int block[2] = {256, 256};  // threads per block of the H pass and the E pass
-    int lanes = 1;              // collocated: lanes per node (1, or 4 for small node sets)
+    int lanes[2] = {1, 1};      // collocated, per pass (H, E): lanes per node (1, 2 or 4)
     void* A = nullptr;  // collocated state {Ez, Hx, Hy, ce}^n
     void* B = nullptr;  // collocated intermediate {E*, Hx', Hy', ce}
     Stag2DPtrs stag;

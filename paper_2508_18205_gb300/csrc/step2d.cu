@@ -385,7 +385,7 @@ static cudaError_t launch_colloc_pass_p(int pass, const StencilStreams<T>& s, co
     return cudaGetLastError();
 }
 
-// lanes per node: 2, 4 or 8 when one thread per node would leave SMs idle
+// lanes per node: 2, 4 or 8 to put more threads on each node's gathers
 template <typename T, bool COMP>
 static cudaError_t launch_colloc_pass(int pass, const StencilStreams<T>& s, const Coefs<T>& k, void* A, void* B,
                                       int block, cudaStream_t st, int lanes) {
@@ -424,9 +424,9 @@ cudaError_t launch_2d(const Launch2D& L, int pass, cudaStream_t st) {
         if (L.comp) return launch_stag_pass<float, true>(pass, pass == 0 ? L.hs.f : L.es.f, L.kf, L.stag, b, st);
         return launch_stag_pass<float, false>(pass, pass == 0 ? L.hs.f : L.es.f, L.kf, L.stag, b, st);
     }
-    if (L.fp64) return launch_colloc_pass<double, false>(pass, L.hs.d, L.kd, L.A, L.B, b, st, L.lanes);
-    if (L.comp) return launch_colloc_pass<float, true>(pass, L.hs.f, L.kf, L.A, L.B, b, st, L.lanes);
-    return launch_colloc_pass<float, false>(pass, L.hs.f, L.kf, L.A, L.B, b, st, L.lanes);
+    if (L.fp64) return launch_colloc_pass<double, false>(pass, L.hs.d, L.kd, L.A, L.B, b, st, L.lanes[pass]);
+    if (L.comp) return launch_colloc_pass<float, true>(pass, L.hs.f, L.kf, L.A, L.B, b, st, L.lanes[pass]);
+    return launch_colloc_pass<float, false>(pass, L.hs.f, L.kf, L.A, L.B, b, st, L.lanes[pass]);
 }
 
 cudaError_t launch_energy_2d(const Launch2D& L, const double* eps_r, int64_t ne, double eta2, double* partial,

@@ -168,3 +168,48 @@ def test_zero_copy_field_io_matches_host_path():
     back = bt.get_field(0, M.MFD_EZ, out=torch.empty((nodes.n, 4), dtype=torch.float64, device="cuda"))
     torch.cuda.synchronize()
     assert np.array_equal(back.cpu().numpy(), v.astype(np.float32).astype(np.float64))
+
+
+@pytest.mark.parametrize("prec,tol", [(M.MFD_FP64, 1e-10), (M.MFD_FP32, 1e-5)])
+def test_lanes_per_node_match_the_oracle(prec, tol):
+    """1, 2 or 4 threads per node (each summing a share of the stencil chunks)
+    give the oracle's fields on a collocated PEC cavity with sources and probes;
+    the autotuner's choice is one of them and leaves the state."""
+    ctx = M.Ctx(0)
+    S, c = 0.5, 4e-3
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    nodes = W.pec_box((160, 160), 0.25, 21)
+    nd = M.Nodes(ctx, nodes.xyz, nodes.period)
+    st = M.Stencils(nd, nd, 31)
+    cw = M.Weights(st, 20, 3, 2, M.MFD_OP_GRAD)
+    hw = M.Weights(st, 31, 5, 4, M.MFD_OP_LAP_POW, 2)
+    eps = W.eps_r_uniform(nodes.n, 22)
+    src = W.ricker_sources(nodes, 4, 23, c0)
+    probes = W.interior_nodes(nodes, 8, 24)
+    ez, hx, hy = W.tm11_fields(nodes.xyz, 159.0, c0, mu0, 0.0, -0.5 * dt)
+    ez[nodes.pec == 1] = 0
+    order = np.argsort(src.node)
+    srt = W.Sources(node=src.node[order], rhs=src.rhs[order], amp=src.amp[order], f0=src.f0[order], t0=src.t0[order])
+    prob, _ = O.tmz_collocated(nodes, 20, 3, 2, 2, dt, eps0, mu0, -c, eps_r=eps)
+    e1, x1, y1, pr, _ = O.run_tmz(prob, ez, hx, hy, 120, sources=srt, probes=probes)
+    ref = np.concatenate([e1, x1, y1])
+    for lanes in ((1, 1), (2, 2), (4, 2), "tune"):
+        sim = M.Sim(ctx, 2, prec, dt, eps0, mu0, -c, cw, hw, compensated=prec == M.MFD_FP32)
+        sim.set_materials(eps, nodes.pec)
+        for comp, f in ((M.MFD_EZ, ez), (M.MFD_HX, hx), (M.MFD_HY, hy)):
+            sim.set_field(comp, f)
+        sim.set_sources(src.node, src.amp, src.f0, src.t0)
+        sim.set_probes(probes, 120)
+        if lanes == "tune":
+            sim.autotune(3)
+            assert sim.steps == 0
+            blocks, ln = sim.launch_config()
+            assert all(x in (1, 2, 4) for x in ln) and all(b in (128, 256, 512) for b in blocks)
+        else:
+            sim.set_lanes(*lanes)
+            assert sim.launch_config()[1] == lanes
+        sim.step(120)
+        got = np.concatenate([sim.get_field(cc) for cc in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)])
+        assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref), lanes
+        gp = sim.read_probes()
+        assert np.linalg.norm(gp - pr) <= tol * np.linalg.norm(pr), lanes
