@@ -524,6 +524,7 @@ def main():
         s_.set_probes(probes, cap)
 
     reset(sim, a.steps + a.warmup + 8)
+    u0 = sim.energy()  # Eq. 20 of the initial state
     blocks = sim.autotune(20)
     stream = ctx.torch_stream()
     sim.step(a.warmup)
@@ -543,6 +544,7 @@ def main():
     # per-kernel durations: the same number of steps, every launch bracketed by CUDA events
     ms = sim.step_timed(a.steps)
     clocks = sampler.stop()
+    u_rel = sim.energy() / u0  # after warm-up + min(K, 64) + 2K steps
     per_step_updates = e.n + 2 * h.n
     elapsed, value = aggregate(elapsed, per_step_updates * a.steps, dist)
     if dist:
@@ -575,6 +577,7 @@ def main():
                        "parallelism": f"replicas{world}", "setup_s": setup,
                        "autotuned_blocks": {"h_pass": blocks[0], "e_pass": blocks[1]}},
             "roofline": roof, "clocks": clocks, "gpu_launches": 3 * a.steps,
+            "energy_rel_end": {"u": u_rel, "after_steps": a.warmup + min(a.steps, 64) + 2 * a.steps},
             "event_timed_ms_per_step": (ms[0] + ms[1]) / a.steps,
             "index_i32": {"ms_per_step": i32_ms, "steps": k32,
                           "value": per_step_updates / (i32_ms / 1e3) * world}}

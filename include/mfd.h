@@ -241,9 +241,17 @@ mfd_status mfd_get_field_device(mfd_sim* sim, int comp, int rhs, double* dev, vo
  * a = (pi f0 (t - t0))^2, added to Ez after each E update. */
 mfd_status mfd_set_sources(mfd_sim* sim, int count, const int64_t* node, const int32_t* rhs,
                            const double* amp, const double* f0, const double* t0);
-/* Probes: Ez at `count` E nodes (caller ids) is recorded after every step for
- * every rhs, for at most `capacity` steps; recording restarts at 0. */
+/* Probes: Ez (or the component of mfd_set_probe_component) at `count` E nodes
+ * (caller ids) is recorded after every step for every rhs, for at most
+ * `capacity` steps; recording restarts at 0. */
 mfd_status mfd_set_probes(mfd_sim* sim, int count, const int64_t* node, int64_t capacity);
+/* The component the probes record after each step (MFD_EZ by default): in the
+ * collocated layouts also MFD_HX, MFD_HY (2D) or any of MFD_EX..MFD_HZ (3D),
+ * H at t_{n+1/2}, the level the leapfrog holds after step n -> n+1; the
+ * staggered layout records Ez only (its H lives on the other node set). The
+ * gradient calls need Ez probes (MFD_ERR_ARG otherwise). Takes effect from
+ * the next step; the recorded series is not cleared. */
+mfd_status mfd_set_probe_component(mfd_sim* sim, int comp);
 /* Advances nsteps (>= 0) leapfrog steps on the context stream (launches
  * replay a captured CUDA graph for long runs). */
 mfd_status mfd_step(mfd_sim* sim, int64_t nsteps);
@@ -317,7 +325,10 @@ mfd_status mfd_sim_index_stats(const mfd_sim* sim, int64_t* out);
  *     checkpoint, so device memory grows as nsteps / every states plus
  *     `every` Ez fields.
  * Both give the same gradient up to the order of atomic additions where two
- * sources or two probes share a node. Collocated 2D problems; probes must hold
+ * sources or two probes share a node. Collocated 2D problems (the staggered
+ * layout would need the transposes of its two cross-set curl stencils and
+ * two node sets' adjoint states, and the 3D layout six adjoint components; the
+ * differentiation workload is collocated 2D, so only it is built); probes must hold
  * >= nsteps steps. g_eps: host, count(E nodes), caller's order; g_amp: host,
  * one per source (may be NULL without sources); *J receives J. The simulation
  * is left after step start + nsteps, with its probes recorded from the start

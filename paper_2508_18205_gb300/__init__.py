@@ -81,6 +81,7 @@ _SIGS = {
     "mfd_sim_autotune": (_I, [_VP, _I, _VP]),
     "mfd_sim_launch_config": (_I, [_VP, _VP, _VP]),
     "mfd_sim_set_lanes": (_I, [_VP, _I, _I]),
+    "mfd_set_probe_component": (_I, [_VP, _I]),
     "mfd_sim_set_index_format": (_I, [_VP, _I]),
     "mfd_sim_index_stats": (_I, [_VP, _VP]),
     "mfd_sim_destroy": (None, [_VP]),
@@ -661,6 +662,10 @@ class Sim:
         ch = np.zeros(2, dtype=np.int32)
         _ck(lib().mfd_sim_autotune(self.h, int(reps), _p(ch)))
         return int(ch[0]), int(ch[1])
+
+    def set_probe_component(self, comp):
+        """The component the probes record (mfd_set_probe_component; MFD_EZ by default)."""
+        _ck(lib().mfd_set_probe_component(self.h, int(comp)))
 
     def set_lanes(self, lanes_h, lanes_e):
         """Threads per node of the H and E passes (collocated 2D, mfd_sim_set_lanes)."""

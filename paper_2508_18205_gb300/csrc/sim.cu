@@ -166,8 +166,8 @@ template <typename T>
 __global__ void k_post(T* __restrict__ ez, int ez_stride, const uint8_t* __restrict__ mask, unsigned held_bits,
                        int nsrc, const int64_t* __restrict__ sn, const double* __restrict__ sa,
                        const double* __restrict__ sf, const double* __restrict__ st0, int nprobe,
-                       const int64_t* __restrict__ pn, T* __restrict__ pbuf, int64_t pcap,
-                       const int64_t* __restrict__ pstep0, int64_t* __restrict__ counter, double dt) {
+                       const int64_t* __restrict__ pn, const T* pv, int pv_stride, T* __restrict__ pbuf,
+                       int64_t pcap, const int64_t* __restrict__ pstep0, int64_t* __restrict__ counter, double dt) {
     __shared__ int64_t n_s;
     if (threadIdx.x == 0) n_s = *counter;
     __syncthreads();
@@ -186,7 +186,7 @@ __global__ void k_post(T* __restrict__ ez, int ez_stride, const uint8_t* __restr
     if (nprobe > 0) {
         const int64_t rec = n - *pstep0;
         if (rec >= 0 && rec < pcap)
-            for (int p = threadIdx.x; p < nprobe; p += blockDim.x) pbuf[rec * nprobe + p] = ez[pn[p] * ez_stride];
+            for (int p = threadIdx.x; p < nprobe; p += blockDim.x) pbuf[rec * nprobe + p] = pv[pn[p] * pv_stride];
     }
     __syncthreads();
     if (threadIdx.x == 0) *counter = n + 1;
@@ -259,6 +259,7 @@ struct mfd_sim {
     int64_t adj_sweeps = 0;  // adjoint sweeps run (mfd_grad_backward)
     int block[2] = {256, 256};  // threads per block of the H and E half-step kernels (autotuned)
     int lanes[2] = {0, 0};      // collocated 2D: lanes per node of each pass (0: the size rule; autotuned)
+    int probe_comp = MFD_EZ;    // the component the probes record
     bool q16 = true;            // staggered kernels read Q16 indices (mfd_sim_set_index_format)
     int64_t watch_every = 0;    // energy watchdog: check every this many steps (0: off)
     double watch_ratio = 0, watch_u0 = 0;
@@ -522,6 +523,15 @@ cudaError_t launch_post(mfd_sim* sim, int parity_after) {
     void* ez;
     int stride;
     ez_location(sim, parity_after, &ez, &stride);
+    // the probed component (mfd_set_probe_component): Ez, or another component
+    // of the collocated state (H at the half step the leapfrog holds)
+    char* pv = static_cast<char*>(ez);
+    int pstride = stride;
+    if (sim->probe_comp != MFD_EZ) {
+        const int off = sim->layout == COLLOC2D ? (sim->probe_comp == MFD_HX ? 1 : 2)
+                                                : (sim->probe_comp <= MFD_EZ ? sim->probe_comp : 4 + sim->probe_comp - MFD_HX);
+        pv = static_cast<char*>(sim->s0.p) + (size_t)off * sim->rs;
+    }
     const uint8_t* mask = sim->has_mask ? sim->mask.as<const uint8_t>() : nullptr;
     unsigned held = sim->layout == COLLOC3D ? 3u : 0xFFu;
     const double dt = sim->d.dt;
@@ -529,12 +539,14 @@ cudaError_t launch_post(mfd_sim* sim, int parity_after) {
         k_post<double><<<1, 256, 0, sim->ctx->stream>>>(
             (double*)ez, stride, mask, held, sim->nsrc, sim->src_node.as<int64_t>(), sim->src_amp.as<double>(),
             sim->src_f0.as<double>(), sim->src_t0.as<double>(), sim->nprobe, sim->probe_node.as<int64_t>(),
-            sim->probe_buf.as<double>(), sim->probe_cap, sim->pstep0.as<int64_t>(), sim->counter.as<int64_t>(), dt);
+            (const double*)pv, pstride, sim->probe_buf.as<double>(), sim->probe_cap, sim->pstep0.as<int64_t>(),
+            sim->counter.as<int64_t>(), dt);
     else
         k_post<float><<<1, 256, 0, sim->ctx->stream>>>(
             (float*)ez, stride, mask, held, sim->nsrc, sim->src_node.as<int64_t>(), sim->src_amp.as<double>(),
             sim->src_f0.as<double>(), sim->src_t0.as<double>(), sim->nprobe, sim->probe_node.as<int64_t>(),
-            sim->probe_buf.as<float>(), sim->probe_cap, sim->pstep0.as<int64_t>(), sim->counter.as<int64_t>(), dt);
+            (const float*)pv, pstride, sim->probe_buf.as<float>(), sim->probe_cap, sim->pstep0.as<int64_t>(),
+            sim->counter.as<int64_t>(), dt);
     return cudaGetLastError();
 }
 
@@ -944,6 +956,16 @@ mfd_status mfd_set_probes(mfd_sim* sim, int count, const int64_t* node, int64_t 
     MFD_CUDA(cudaMemcpyAsync(sim->pstep0.p, &from, 8, cudaMemcpyHostToDevice, ctx->stream));
     sim->graph_ok = false;
     MFD_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MFD_OK;
+}
+
+mfd_status mfd_set_probe_component(mfd_sim* sim, int comp) {
+    if (!sim) return fail(MFD_ERR_ARG, "NULL argument");
+    const bool ok = comp == MFD_EZ || (sim->layout == COLLOC2D && (comp == MFD_HX || comp == MFD_HY)) ||
+                    (sim->layout == COLLOC3D && comp >= MFD_EX && comp <= MFD_HZ);
+    if (!ok) return fail(MFD_ERR_ARG, "probed component: Ez, or a component of the collocated layouts");
+    sim->probe_comp = comp;
+    sim->graph_ok = false;
     return MFD_OK;
 }
 
@@ -1389,6 +1411,7 @@ mfd_status mfd_grad_forward(mfd_sim* sim, int64_t nsteps, int64_t every, double*
     *out = nullptr;
     if (sim->layout != COLLOC2D) return fail(MFD_ERR_ARG, "the gradient supports the collocated 2D layout");
     if (sim->hp.mirror) return fail(MFD_ERR_ARG, "the gradient does not support mirror walls (images)");
+    if (sim->probe_comp != MFD_EZ) return fail(MFD_ERR_ARG, "the gradient's objective is over Ez probes");
     if (sim->nprobe < 1 || sim->probe_cap < nsteps)
         return fail(MFD_ERR_STATE, "the gradient needs probes with capacity >= nsteps (mfd_set_probes)");
     mfd_ctx* ctx = sim->ctx;

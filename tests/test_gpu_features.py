@@ -213,3 +213,73 @@ def test_lanes_per_node_match_the_oracle(prec, tol):
         assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref), lanes
         gp = sim.read_probes()
         assert np.linalg.norm(gp - pr) <= tol * np.linalg.norm(pr), lanes
+
+
+def test_probes_of_other_components_match_the_oracle():
+    """Probes record Hx (collocated 2D) or Ex, Hz (3D) after each step, H at the
+    half step the leapfrog holds: the oracle's state sampled after each of its
+    steps (FP64, 1e-10); the staggered layout and the gradient refuse them."""
+    ctx = M.Ctx(0)
+    dt, eps0, mu0, c0, eta0 = W.units(0.5)
+    sq = W.pec_box((20, 20), 0.25, 31)
+    nd = M.Nodes(ctx, sq.xyz, sq.period)
+    st = M.Stencils(nd, nd, 31)
+    cw = M.Weights(st, 12, 3, 2, M.MFD_OP_GRAD)
+    hw = M.Weights(st, 31, 5, 4, M.MFD_OP_LAP_POW, 2)
+    src = W.ricker_sources(sq, 2, 32, c0)
+    probes = W.interior_nodes(sq, 5, 33)
+    sim = M.Sim(ctx, 2, M.MFD_FP64, dt, eps0, mu0, -4e-3, cw, hw)
+    sim.set_materials(None, sq.pec)
+    sim.set_sources(src.node, src.amp, src.f0, src.t0)
+    sim.set_probes(probes, 30)
+    sim.set_probe_component(M.MFD_HX)
+    sim.step(30)
+    got = sim.read_probes()
+    prob, _ = O.tmz_collocated(sq, 12, 3, 2, 2, dt, eps0, mu0, -4e-3)
+    order = np.argsort(src.node)
+    srt = W.Sources(node=src.node[order], rhs=src.rhs[order], amp=src.amp[order], f0=src.f0[order], t0=src.t0[order])
+    ez, hx, hy = np.zeros((3, sq.n))
+    ref = []
+    for n in range(30):
+        ez, hx, hy, _, _ = O.run_tmz(prob, ez, hx, hy, 1, step0=n, sources=srt)
+        ref.append(hx[probes])
+    ref = np.array(ref)
+    assert np.linalg.norm(got.reshape(ref.shape) - ref) <= 1e-10 * np.linalg.norm(ref)
+    with pytest.raises(M.MfdError):  # the gradient's objective is over Ez probes
+        sim.grad(10, 0, len(src.node))
+    # 3D: Ex and Hz
+    box = W.periodic_box((8, 8, 8), 0.25, 34)
+    nd3 = M.Nodes(ctx, box.xyz, box.period)
+    st3 = M.Stencils(nd3, nd3, 71)
+    cw3 = M.Weights(st3, 40, 3, 3, M.MFD_OP_GRAD)
+    hw3 = M.Weights(st3, 71, 5, 4, M.MFD_OP_LAP_POW, 2)
+    rng = np.random.default_rng(35)
+    E0, H0 = rng.standard_normal((3, box.n)), rng.standard_normal((3, box.n))
+    p3 = W.interior_nodes(box, 4, 36)
+    prob3, _ = O.max3d_collocated(box, 40, 3, 3, 2, dt, eps0, mu0, -1e-3)
+    for comp in (M.MFD_EX, M.MFD_HZ):
+        sim3 = M.Sim(ctx, 3, M.MFD_FP64, dt, eps0, mu0, -1e-3, cw3, hw3)
+        for b in range(3):
+            sim3.set_field(b, E0[b])
+            sim3.set_field(3 + b, H0[b])
+        sim3.set_probes(p3, 12)
+        sim3.set_probe_component(comp)
+        sim3.step(12)
+        got3 = sim3.read_probes().reshape(12, len(p3))
+        E, H = E0, H0
+        ref3 = []
+        for n in range(12):
+            E, H, _, _ = O.run_3d(prob3, E, H, 1, step0=n)
+            ref3.append((E[0] if comp == M.MFD_EX else H[2])[p3])
+        ref3 = np.array(ref3)
+        assert np.linalg.norm(got3 - ref3) <= 1e-10 * np.linalg.norm(ref3), comp
+    e = W.periodic_box((12, 12), 0.25, 37)
+    h = W.periodic_box((12, 12), 0.25, 38, offset=(0.5, 0.5))
+    de, dh = M.Nodes(ctx, e.xyz, e.period), M.Nodes(ctx, h.xyz, h.period)
+    stag = M.Sim(ctx, 2, M.MFD_FP32, dt, eps0, mu0, 4e-5,
+                 M.Weights(M.Stencils(dh, de, 30), 30, 5, 4, M.MFD_OP_GRAD),
+                 M.Weights(M.Stencils(dh, dh, 57), 57, 7, 6, M.MFD_OP_LAP_POW, 3),
+                 M.Weights(M.Stencils(de, dh, 30), 30, 5, 4, M.MFD_OP_GRAD),
+                 M.Weights(M.Stencils(de, de, 57), 57, 7, 6, M.MFD_OP_LAP_POW, 3))
+    with pytest.raises(M.MfdError):
+        stag.set_probe_component(M.MFD_HX)
