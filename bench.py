@@ -203,17 +203,19 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def traffic_record(kernel, s):
-    """DRAM bytes per launch of `kernel` (s-byte reals) from the committed ncu
-    summary (profiles/traffic.json), if the source files that define the
-    kernel are unchanged since that capture (else None)."""
+def traffic_record(kernel, s, algorithmic):
+    """DRAM bytes per launch of `kernel` (s-byte reals): the ratio of DRAM bytes
+    to algorithmic bytes that ncu measured on a smaller case of the same
+    kernel (profiles/traffic.json) times this launch's algorithmic bytes, if
+    the source files that define the kernel are unchanged since that capture
+    (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     rec = json.load(open(p)).get("kernels", {}).get(f"{kernel}_fp{8 * s}")
     if not rec or rec.get("sha") != sources_sha(rec.get("sources", [])):
         return None
-    return rec.get("bytes")
+    return round(rec["ratio"] * algorithmic) if "ratio" in rec else rec.get("bytes")
 
 
 def sources_sha(files):
@@ -719,7 +721,7 @@ def roofline(ms, steps, e, h, nhv, s, peak, peak_kind, stats=None):
     achieved = dom_bytes / dom_t / 1e9
     kname = "k_h_stag" if dom == "h" else "k_e_stag"
     r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-         "traffic": traffic_record(kname, s), "kernel": kname, "peak_kind": peak_kind,
+         "traffic": traffic_record(kname, s, dom_bytes), "kernel": kname, "peak_kind": peak_kind,
          "algorithmic_bytes_per_launch": dom_bytes, "bytes_basis": basis, "avg_launch_ms": dom_t * 1e3,
          "other_kernel_avg_launch_ms": other_t * 1e3,
          "other_kernel_achieved_gbs": other_bytes / other_t / 1e9,
@@ -804,7 +806,7 @@ def batched(M, ctx, steps, peak, peak_kind, ndom=256, nrhs=16):
                           "variants": ["stream prefetch, 3 blocks of 256 per SM", "no prefetch, 4 blocks per SM"],
                           "ms_per_step_by_variant": [float(x) for x in variant_ms]},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "traffic": traffic_record("k_batch16_256dom", 4) if (ndom, nrhs) == (256, 16) else None,
+                         "traffic": traffic_record("k_batch16", 4, byt) if nrhs == 16 else None,
                          "traffic_unit": "DRAM bytes per step (the persistent launch runs all steps)",
                          "kernel": "k_batch<16>", "peak_kind": peak_kind,
                          "algorithmic_bytes_per_step": byt},
@@ -907,7 +909,7 @@ def cube3d(M, ctx, steps, peak, peak_kind, nx=200):
             "value": nodes.n * 6 * steps / el, "unit": UNIT, "steps": steps, "ms_per_step": el / steps * 1e3,
             "setup_s": setup, "energy_rel_after_run": float(u_end / u0), "energy_after_steps": steps + 10,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "traffic": traffic_record(dom + "_images", s4), "kernel": dom, "peak_kind": peak_kind,
+                         "traffic": traffic_record(dom + "_images", s4, dom_b), "kernel": dom, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": dom_b, "avg_launch_ms": dom_t * 1e3,
                          "other_kernel_avg_launch_ms": min(h_avg, e_avg) * 1e3,
                          "step_achieved_gbs": (bh + be) * nodes.n / (el / steps) / 1e9},
@@ -1103,7 +1105,7 @@ def yee(M, ctx, peak, peak_kind, big=8192, steps=1000, nx=1000, pulse_steps=5000
                    "value": 3 * cells * steps / el, "unit": UNIT, "steps_per_launch": spl,
                    "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                                 "frac": alg / (ms / 1e3) / 1e9 / peak,
-                                "traffic": traffic_record(f"k_yee{spl}_{big}", 4),
+                                "traffic": traffic_record(f"k_yee{spl}_{big}", 4, alg),
                                 "kernel": f"k_yee<float, S={spl}>",
                                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg,
                                 "avg_launch_ms": ms}}
@@ -1121,7 +1123,7 @@ def yee(M, ctx, peak, peak_kind, big=8192, steps=1000, nx=1000, pulse_steps=5000
                             "value": 3 * cells * steps / el1, "unit": UNIT, "steps_per_launch": 1,
                             "roofline": {"bound": "hbm", "achieved": alg / (ms1 / 1e3) / 1e9, "peak": peak,
                                          "unit": "GB/s", "frac": alg / (ms1 / 1e3) / 1e9 / peak,
-                                         "traffic": traffic_record(f"k_yee1_{big}", 4),
+                                         "traffic": traffic_record(f"k_yee1_{big}", 4, alg),
                                          "kernel": "k_yee<float, S=1> (+ k_yee_post)", "peak_kind": peak_kind,
                                          "algorithmic_bytes_per_launch": alg, "avg_launch_ms": ms1}}
     del y
