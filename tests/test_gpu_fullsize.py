@@ -80,39 +80,65 @@ def test_fullsize_one_step_sampled(setup, prec, tol):
     assert err <= tol, err
 
 
+def _crop(nodes, lo, size):
+    """The cells [lo, lo + size) of a cell-centred PEC box as a PEC box of their
+    own (shifted to the origin; coordinates shift exactly)."""
+    cell = np.floor(nodes.xyz).astype(np.int64)
+    sub = np.nonzero(np.all((cell >= lo) & (cell < np.asarray(lo) + size), axis=1))[0]
+    crop = W.NodeSet(xyz=nodes.xyz[sub] - np.asarray(lo, dtype=np.float64), pec=np.zeros(len(sub), np.uint8),
+                     period=np.zeros(3), box_lo=np.zeros(3), box_hi=np.asarray(size, dtype=np.float64),
+                     normal_axes=np.zeros(len(sub), np.uint8))
+    return crop, sub
+
+
 def test_cube3d_8M_one_step_sampled():
-    """The 3D workload at its full size (200^3 = 8M nodes, n = 40, N_h = 71, eps_r
-    field): one step from seeded random fields on all six components, sampled
-    at 24 nodes, against the oracle's sampled 3D step from the same fields
-    (FP32 1e-6, FP64 1e-12)."""
-    import math
+    """The 3D workload at its full size: the 200^3 PEC cube (walls by images,
+    40-node curl stencils and 44 in the layer next to the walls, Delta^2 HV on
+    71 nodes, eps_r field), one step from seeded random fields on all six
+    components, in the launch configuration bench.py times. Sampled against
+    the oracle: 24 nodes away from the walls (the oracle's plain stencils,
+    which no image reaches there), 24 in a corner and 24 next to the middle of
+    the x = 200 face (the oracle's image scheme on a box of cells around them
+    whose other faces lie beyond what those nodes' first step reads). FP32
+    1e-6, FP64 1e-12."""
     ctx = M.Ctx(0)
-    S, c, n, k, m, alpha = 0.5, 1e-3, 40, 3, 3, 2
+    C = bench.CUBE
+    S, c, n, k, m, alpha = (C[x] for x in ("S", "c", "n", "k", "m", "alpha"))
     dt, eps0, mu0, c0, eta0 = W.units(S)
-    nx = 200
-    nodes = W.periodic_box((nx, nx, nx), 0.25, 3)
-    er = W.eps_r_smooth_3d(nodes.xyz, nodes.box_hi, 33)
-    nd = M.Nodes(ctx, nodes.xyz, nodes.period)
-    nhv = 2 * math.comb(2 * alpha + 3, 3) + 1
-    st = M.Stencils(nd, nd, max(n, nhv))
-    cw = M.Weights(st, n, k, m, M.MFD_OP_GRAD)
-    hw = M.Weights(st, nhv, 2 * alpha + 1, 2 * alpha, M.MFD_OP_LAP_POW, alpha)
+    sim32, keep, nodes, er, _, _, _ = bench._pec_cube(M, ctx, 200)
+    del sim32
+    nd, st, cw, hw = keep
     rng = np.random.default_rng(12)
     E0 = rng.standard_normal((3, nodes.n))
     H0 = rng.standard_normal((3, nodes.n))
-    ids = np.sort(rng.choice(nodes.n, 24, replace=False))
-    for prec, tol in ((0, 1e-6), (1, 1e-12)):
+    cell = np.floor(nodes.xyz).astype(np.int64)
+    ids_in = np.sort(rng.choice(np.nonzero(np.all((cell >= 12) & (cell < 188), axis=1))[0], 24, replace=False))
+    regions = {"corner": ((0, 0, 0), (20, 20, 20), np.all(cell < 6, axis=1)),
+               "face": ((180, 80, 80), (20, 40, 40),
+                        (cell[:, 0] >= 194) & np.all((cell[:, 1:] >= 90) & (cell[:, 1:] < 110), axis=1))}
+    refs = {}
+    RE, RH, hs = O.max3d_sample_step(nodes, ids_in, n, k, m, alpha, dt, eps0, mu0, -c, E0, H0, eps_r=er, h_ids=ids_in)
+    refs["interior"] = (ids_in, RE, RH[:, np.searchsorted(hs, ids_in)])
+    for name, (lo, size, sel) in regions.items():
+        ids = np.sort(rng.choice(np.nonzero(sel)[0], 24, replace=False))
+        crop, sub = _crop(nodes, lo, size)
+        prob = O.max3d_images(crop, n, k, m, alpha, dt, eps0, mu0, -c, eps_r=er[sub], n_wall=C["n_wall"])
+        RE, RH, _, _ = O.run_3d(prob, E0[:, sub], H0[:, sub], 1)
+        at = np.searchsorted(sub, ids)
+        refs[name] = (ids, RE[:, at], RH[:, at])
+    for prec, tol in ((M.MFD_FP32, 1e-6), (M.MFD_FP64, 1e-12)):
         sim = M.Sim(ctx, 3, prec, dt, eps0, mu0, -c, cw, hw, compensated=True)
         sim.set_materials(er, None)
         for comp, v in zip(range(6), (*E0, *H0)):
             sim.set_field(comp, v)
         sim.step(1)
-        E1 = np.stack([sim.get_field(a)[ids] for a in range(3)])
-        RE, RH, hs = O.max3d_sample_step(nodes, ids, n, k, m, alpha, dt, eps0, mu0, -c, E0, H0, eps_r=er)
-        H1 = np.stack([sim.get_field(3 + a)[hs] for a in range(3)])
-        got = np.concatenate([E1.reshape(-1), H1.reshape(-1)])
-        ref = np.concatenate([RE.reshape(-1), RH.reshape(-1)])
-        assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref), (prec, np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        E1 = np.stack([sim.get_field(a) for a in range(3)])
+        H1 = np.stack([sim.get_field(3 + a) for a in range(3)])
+        for name, (ids, RE, RH) in refs.items():
+            got = np.concatenate([E1[:, ids].ravel(), H1[:, ids].ravel()])
+            ref = np.concatenate([RE.ravel(), RH.ravel()])
+            err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert err <= tol, (prec, name, err)
         del sim
 
 

@@ -44,3 +44,35 @@ def test_pulse_5000_steps_against_oracle_every_100():
         gp = g[tag]["probes"]
         assert gp.shape == rp.shape
         assert np.linalg.norm(gp - rp) <= tol * np.linalg.norm(rp), tag
+
+
+def test_pec_cube_2000_steps_against_oracle_every_500():
+    """The 3D workload's problem (PEC cube by images, 40-node curl stencils and
+    44 in the wall layer, Delta^2 HV, eps_r field, TM110 fields, Courant
+    number 0.5) on a 24^3 cube over the configuration's 2000 steps, against the
+    FP64 oracle every 500 steps: FP32 (compensated) within 1e-5, FP64 within
+    1e-10, every field; the oracle's energy stays within 1 % of its start."""
+    ctx = M.Ctx(0)
+    C = bench.CUBE
+    S, c, n, k, m, alpha = (C[x] for x in ("S", "c", "n", "k", "m", "alpha"))
+    dt, eps0, mu0, c0, eta0 = W.units(S)
+    sim32, keep, nodes, er, E0, H0, _ = bench._pec_cube(M, ctx, 24)
+    nd, st, cw, hw = keep
+    sim64 = M.Sim(ctx, 3, M.MFD_FP64, dt, eps0, mu0, -c, cw, hw)
+    sim64.set_materials(er, None)
+    for comp, v in zip(range(6), (*E0, *H0)):
+        sim64.set_field(comp, v)
+    prob = O.max3d_images(nodes, n, k, m, alpha, dt, eps0, mu0, -c, eps_r=er, n_wall=C["n_wall"])
+    RE, RH = E0, H0
+    u = []
+    for blk in range(4):
+        RE, RH, _, en = O.run_3d(prob, RE, RH, 500, step0=500 * blk, energy=True)
+        u.append(en)
+        ref = np.concatenate([RE.ravel(), RH.ravel()])
+        for sim, tol in ((sim32, 1e-5), (sim64, 1e-10)):
+            sim.step(500)
+            got = np.concatenate([sim.get_field(a) for a in range(6)])
+            err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert err <= tol, (tol, 500 * (blk + 1), err)
+    u = np.concatenate(u)
+    assert np.all(np.abs(u / u[0] - 1.0) <= 1e-2)
