@@ -64,7 +64,15 @@ def _args():
     return ap.parse_args()
 
 
-PARAMS = dict(S=0.5, n=30, k=5, m=4, alpha=3, c=4e-5, wavelength=12.0)
+def config(name):
+    """One workload's parameters (configs/<name>.json)."""
+    return json.load(open(os.path.join(ROOT, "configs", name + ".json")))
+
+
+C1, C2, C3, C4, C5 = (config(x) for x in ("c1_cavity", "c2_pulse", "c3_cube", "c4_batched", "c5_adjoint"))
+CAV_L = float(C1["nodes"]["shape"][0] - 1)  # side of the cavity: the PEC box's wall nodes sit at 0 and L
+PARAMS = dict(S=C2["courant"], n=C2["curl"]["n"], k=C2["curl"]["phs_k"], m=C2["curl"]["poly_m"],
+              alpha=C2["hv"]["alpha"], c=C2["hv"]["c"], wavelength=C2["wavelength"])
 
 
 def pulse_fields(e, h, nx, dt):
@@ -77,8 +85,9 @@ def pulse_fields(e, h, nx, dt):
 
 
 def node_sets(nx):
-    e = W.periodic_box((nx, nx), 0.25, 2, seed_line_y=nx // 2)
-    h = W.periodic_box((nx, nx), 0.25, 3, offset=(0.5, 0.5))
+    nd = C2["nodes"]
+    e = W.periodic_box((nx, nx), nd["jitter"], nd["e_seed"], seed_line_y=nx // 2)
+    h = W.periodic_box((nx, nx), nd["jitter"], nd["h_seed"], offset=tuple(nd["h_offset"]))
     return e, h
 
 
@@ -298,13 +307,12 @@ def oracle_checks(gpu):
     # the plain method's cavity (FP64), the whole workload
     g = gpu.get("cavity_fp64")
     if g:
-        S, c = 0.5, 4e-3
+        S, c, nodes, (n, k, m, alpha) = cavity_setup()
         dt, eps0, mu0, c0, eta0 = W.units(S)
-        nodes = W.pec_box((100, 100), 0.25, 1)
-        prob, _ = O.tmz_collocated(nodes, 12, 3, 2, 2, dt, eps0, mu0, -c)
-        ez, hx, hy = W.tm11_fields(nodes.xyz, 99.0, c0, mu0, 0.0, -0.5 * dt)
+        prob, _ = O.tmz_collocated(nodes, n, k, m, alpha, dt, eps0, mu0, -c)
+        ez, hx, hy = W.tm11_fields(nodes.xyz, CAV_L, c0, mu0, 0.0, -0.5 * dt)
         ez[nodes.pec == 1] = 0
-        o = O.run_tmz(prob, ez, hx, hy, g["steps"], probes=W.interior_nodes(nodes, 16, 14))
+        o = O.run_tmz(prob, ez, hx, hy, g["steps"], probes=W.interior_nodes(nodes, C1["probes"]["count"], C1["probes"]["seed"]))
         ref = np.concatenate(o[:3])
         out["cavity_fp64"] = {"workload": "cavity TM11, 100x100 PEC, n=12, FP64 (whole workload)",
                               "steps": g["steps"], "rel_l2": _rel(g["fields"], ref),
@@ -358,13 +366,14 @@ def oracle_checks(gpu):
     g = gpu.get("batched")
     if g:
         t = time.perf_counter()
-        S = 0.5
+        S = C4["courant"]
         dt, eps0, mu0, c0, eta0 = W.units(S)
         doms = []
         worst = 0.0
         for D in g["domains"]:
             ns, n = D["nodes"], D["n"]
-            prob, _ = O.tmz_collocated(ns, n, 3, W.poly_degree_for(n), 2, dt, eps0, mu0, -g["c"])
+            prob, _ = O.tmz_collocated(ns, n, C4["curl"]["phs_k"], W.poly_degree_for(n), C4["hv"]["alpha"], dt, eps0,
+                                       mu0, -g["c"], nh_override=C4["hv"]["n"])
             z = np.zeros(ns.n)
             got, ref = [], []
             for j, r in enumerate(D["rhs"]):
@@ -387,7 +396,9 @@ def oracle_checks(gpu):
     if g:
         P = _adjoint_problem(g["nx"])
         dt, eps0, mu0, c0, eta0 = W.units(P["S"])
-        prob, _ = O.tmz_collocated(P["nodes"], 20, 3, 2, 2, dt, eps0, mu0, -P["c"], eps_r=P["eps"])
+        n, k, m, nh, alpha = P["stencil"]
+        prob, _ = O.tmz_collocated(P["nodes"], n, k, m, alpha, dt, eps0, mu0, -P["c"], eps_r=P["eps"],
+                                   nh_override=nh)
         z = np.zeros(P["nodes"].n)
         J, ge, ga = O.grad_tmz(prob, z, z, z, g["steps"], P["src"], P["probes"])
         out["adjoint"] = {"workload": f"adjoint {g['nx']}x{g['nx']} PEC, n=20, FP32 GPU vs FP64 oracle",
@@ -402,11 +413,10 @@ def cavity_cpu(O, steps=1000):
     """The oracle on the whole FP64 cavity workload of cavity() (100 x 100 PEC
     square, n = 12, Delta^2 HV, TM11 mode, 1000 steps), on all host cores and
     on one thread, with its relative L2 error against the exact mode."""
-    S, c = 0.5, 4e-3
+    S, c, nodes, (n, k, m, alpha) = cavity_setup()
     dt, eps0, mu0, c0, eta0 = W.units(S)
-    nodes = W.pec_box((100, 100), 0.25, 1)
-    prob, _ = O.tmz_collocated(nodes, 12, 3, 2, 2, dt, eps0, mu0, -c)
-    ez, hx, hy = W.tm11_fields(nodes.xyz, 99.0, c0, mu0, 0.0, -0.5 * dt)
+    prob, _ = O.tmz_collocated(nodes, n, k, m, alpha, dt, eps0, mu0, -c)
+    ez, hx, hy = W.tm11_fields(nodes.xyz, CAV_L, c0, mu0, 0.0, -0.5 * dt)
     ez[nodes.pec == 1] = 0
     cores = O.threads()
     out = {"workload": "cavity TM11, 100x100 PEC, n=12, FP64, 1000 steps"}
@@ -421,7 +431,7 @@ def cavity_cpu(O, steps=1000):
     finally:
         O.threads(cores)
     T = steps * dt
-    ea, xa, ya = W.tm11_fields(nodes.xyz, 99.0, c0, mu0, T, T - 0.5 * dt)
+    ea, xa, ya = W.tm11_fields(nodes.xyz, CAV_L, c0, mu0, T, T - 0.5 * dt)
     got, ref = np.concatenate(res[:3]), np.concatenate([ea, xa, ya])
     out["rel_l2_vs_exact_mode"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     return out
@@ -743,22 +753,24 @@ def batched(M, ctx, steps, peak, peak_kind, ndom=256, nrhs=16):
     largest m with 2 M_m <= n; Delta^2 HV on 31 nodes), 16 Ricker sources per
     domain, each its own right-hand side; FP32; all steps in one persistent
     cooperative launch replayed from a CUDA graph."""
-    S, c = 0.5, 4e-3
+    S, c = C4["courant"], C4["hv"]["c"]
+    nh, alpha, k = C4["hv"]["n"], C4["hv"]["alpha"], C4["curl"]["phs_k"]
     dt, eps0, mu0, c0, eta0 = W.units(S)
     t = time.time()
-    specs = W.batch_domains(ndom, 4)
+    dd = C4["domains"]
+    specs = W.batch_domains(ndom, dd["seed"], dd["n_min"], dd["n_max"], tuple(dd["stencils"]))
     doms, keep = [], []
     for ns, n in specs:
         nd = M.Nodes(ctx, ns.xyz, ns.period)
-        st = M.Stencils(nd, nd, max(n, 31))
-        cw = M.Weights(st, n, 3, W.poly_degree_for(n), M.MFD_OP_GRAD)
-        hw = M.Weights(st, 31, 5, 4, M.MFD_OP_LAP_POW, 2)
+        st = M.Stencils(nd, nd, max(n, nh))
+        cw = M.Weights(st, n, k, W.poly_degree_for(n), M.MFD_OP_GRAD)
+        hw = M.Weights(st, nh, 2 * alpha + 1, 2 * alpha, M.MFD_OP_LAP_POW, alpha)
         doms.append((cw, hw, dt, eps0, mu0, -c))
         keep.append((nd, st))
     bt = M.Batch(ctx, doms, nrhs=nrhs)
     for d, (ns, n) in enumerate(specs):
         bt.set_materials(d, None, ns.pec)
-        src = W.ricker_sources(ns, nrhs, 500 + d, c0, nrhs=nrhs, one_per_rhs=True)
+        src = W.ricker_sources(ns, nrhs, C4["sources_seed0"] + d, c0, nrhs=nrhs, one_per_rhs=True)
         bt.set_sources(d, src.node, src.rhs, src.amp, src.f0, src.t0)
     setup_s = time.time() - t
     import torch
@@ -916,7 +928,8 @@ def cube3d(M, ctx, steps, peak, peak_kind, nx=200):
             "_gpu": {"sampled": sampled, "small": small}}
 
 
-CUBE = dict(S=0.5, c=1e-3, n=40, k=3, m=3, alpha=2, n_wall=44)
+CUBE = dict(S=C3["courant"], c=C3["hv"]["c"], n=C3["curl"]["n"], k=C3["curl"]["phs_k"], m=C3["curl"]["poly_m"],
+            alpha=C3["hv"]["alpha"], n_wall=C3["curl"]["n_wall"])
 
 
 def _cube_small_gpu(M, ctx, nx, steps):
@@ -929,24 +942,32 @@ def _cube_small_gpu(M, ctx, nx, steps):
             "nodes": nodes, "eps_r": er, "E0": E0, "H0": H0}
 
 
+def cavity_setup():
+    """The plain method's cavity (configs/c1_cavity.json): (S_c, c, PEC box, (n, PHS k, m, alpha))."""
+    nd = C1["nodes"]
+    nodes = W.pec_box(tuple(nd["shape"]), nd["jitter"], nd["seed"])
+    cu = C1["curl"]
+    return C1["courant"], C1["hv"]["c"], nodes, (cu["n"], cu["phs_k"], cu["poly_m"], C1["hv"]["alpha"])
+
+
 def cavity(M, ctx, steps=1000):
     """The plain method of the paper, FP64: 100 x 100 jittered nodes in a PEC
     square, collocated 12-node stencils (r^3, degree 2), Delta^2 HV, TM11 mode,
     CFL 0.5, 1000 steps, Ez probed at 16 nodes. L2-resident (about 9 MB per
     step): latency-bound, so only updates/s are reported. Also the relative L2
     error against the exact TM11 mode at the end."""
-    S, c = 0.5, 4e-3
+    S, c, nodes, (n, k, m, alpha) = cavity_setup()
     dt, eps0, mu0, c0, eta0 = W.units(S)
-    nodes = W.pec_box((100, 100), 0.25, 1)
+    nhv = 2 * math.comb(2 * alpha + 2, 2) + 1
     nd = M.Nodes(ctx, nodes.xyz, nodes.period)
-    st = M.Stencils(nd, nd, 31)
-    cw = M.Weights(st, 12, 3, 2, M.MFD_OP_GRAD)
-    hw = M.Weights(st, 31, 5, 4, M.MFD_OP_LAP_POW, 2)
+    st = M.Stencils(nd, nd, max(n, nhv))
+    cw = M.Weights(st, n, k, m, M.MFD_OP_GRAD)
+    hw = M.Weights(st, nhv, 2 * alpha + 1, 2 * alpha, M.MFD_OP_LAP_POW, alpha)
     sim = M.Sim(ctx, 2, M.MFD_FP64, dt, eps0, mu0, -c, cw, hw)
     sim.set_materials(None, nodes.pec)
-    ez, hx, hy = W.tm11_fields(nodes.xyz, 99.0, c0, mu0, 0.0, -0.5 * dt)
+    ez, hx, hy = W.tm11_fields(nodes.xyz, CAV_L, c0, mu0, 0.0, -0.5 * dt)
     ez[nodes.pec == 1] = 0
-    probes = W.interior_nodes(nodes, 16, 14)
+    probes = W.interior_nodes(nodes, C1["probes"]["count"], C1["probes"]["seed"])
     import torch
 
     def run():
@@ -967,7 +988,7 @@ def cavity(M, ctx, steps=1000):
     run()
     el = run()
     T = steps * dt
-    ea, xa, ya = W.tm11_fields(nodes.xyz, 99.0, c0, mu0, T, T - 0.5 * dt)
+    ea, xa, ya = W.tm11_fields(nodes.xyz, CAV_L, c0, mu0, T, T - 0.5 * dt)
     got = np.concatenate([sim.get_field(cc) for cc in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)])
     ref = np.concatenate([ea, xa, ya])
     return {"workload": "cavity TM11, 100x100 PEC, n=12, FP64, 1000 steps", "nodes": nodes.n,
@@ -977,24 +998,20 @@ def cavity(M, ctx, steps=1000):
             "_gpu": {"fields": got, "probes": sim.read_probes(), "steps": steps}}
 
 
-def adjoint(M, ctx, steps=4000, every=64):
+def adjoint(M, ctx, steps=C5["steps"], every=C5["checkpoint_every"]):
     """Differentiation workload: 500 x 500 PEC box, n = 20 (r^3, degree 2),
     Delta^2 HV, eps_r = 1 + 0.5 U, 4 Ricker sources, 8 probes, FP32, 4000
     steps: J = dt sum Ez_p^2 and dJ/deps_r, dJ/d amplitudes by the adjoint with
     checkpoints every 64 steps. Reports the forward step rate and the time of one
     gradient (forward with checkpoints + segment recomputation + adjoint), and
     of the same gradient with the whole Ez history kept on the device."""
-    S, c = 0.5, 4e-3
+    nodes_side = C5["nodes"]["shape"][0]
+    P = _adjoint_problem(nodes_side)
+    S, c, nodes = P["S"], P["c"], P["nodes"]
     dt, eps0, mu0, c0, eta0 = W.units(S)
-    nodes = W.pec_box((500, 500), 0.25, 5)
-    nd = M.Nodes(ctx, nodes.xyz, nodes.period)
-    st = M.Stencils(nd, nd, 31)
-    cw = M.Weights(st, 20, 3, 2, M.MFD_OP_GRAD)
-    hw = M.Weights(st, 31, 5, 4, M.MFD_OP_LAP_POW, 2)
+    cw, hw, keep = _adjoint_weights(M, ctx, P)
     sim = M.Sim(ctx, 2, M.MFD_FP32, dt, eps0, mu0, -c, cw, hw, compensated=True)
-    eps = W.eps_r_uniform(nodes.n, 55)
-    src = W.ricker_sources(nodes, 4, 56, c0)
-    probes = W.interior_nodes(nodes, 8, 57)
+    eps, src, probes = P["eps"], P["src"], P["probes"]
     z = np.zeros(nodes.n)
 
     def setup():
@@ -1028,7 +1045,7 @@ def adjoint(M, ctx, steps=4000, every=64):
     J0, ge0, ga0 = sim.grad(steps, 0, len(src.node))
     gw = time.perf_counter() - t
     small = _adjoint_small_gpu(M, ctx)
-    return {"workload": "adjoint 500x500 PEC, n=20, FP32, 4000 steps, checkpoints every 64", "nodes": nodes.n,
+    return {"workload": f"adjoint {nodes_side}x{nodes_side} PEC, n={P['stencil'][0]}, FP32, {steps} steps, checkpoints every {every}", "nodes": nodes.n,
             "_gpu": small,
             "forward_value": nodes.n * 3 * steps / fwd, "unit": UNIT, "forward_ms_per_step": fwd / steps * 1e3,
             "gradient_s": gs, "gradient_over_forward": gs / fwd, "J": J,
@@ -1039,12 +1056,26 @@ def adjoint(M, ctx, steps=4000, every=64):
 
 
 def _adjoint_problem(nx):
-    """The differentiation workload's recipe on an nx x nx PEC box."""
-    S, c = 0.5, 4e-3
+    """The differentiation workload's recipe (configs/c5_adjoint.json) on an nx x nx PEC box."""
+    S, c = C5["courant"], C5["hv"]["c"]
     dt, eps0, mu0, c0, eta0 = W.units(S)
-    nodes = W.pec_box((nx, nx), 0.25, 5)
-    return dict(S=S, c=c, nodes=nodes, eps=W.eps_r_uniform(nodes.n, 55), src=W.ricker_sources(nodes, 4, 56, c0),
-                probes=W.interior_nodes(nodes, 8, 57))
+    nodes = W.pec_box((nx, nx), C5["nodes"]["jitter"], C5["nodes"]["seed"])
+    er, so, pr = C5["eps_r"], C5["sources"], C5["probes"]
+    cu, hv = C5["curl"], C5["hv"]
+    return dict(S=S, c=c, nodes=nodes, eps=W.eps_r_uniform(nodes.n, er["seed"], er["lo"], er["span"]),
+                src=W.ricker_sources(nodes, so["count"], so["seed"], c0),
+                probes=W.interior_nodes(nodes, pr["count"], pr["seed"]),
+                stencil=(cu["n"], cu["phs_k"], cu["poly_m"], hv["n"], hv["alpha"]))
+
+
+def _adjoint_weights(M, ctx, P):
+    n, k, m, nh, alpha = P["stencil"]
+    ns = P["nodes"]
+    nd = M.Nodes(ctx, ns.xyz, ns.period)
+    st = M.Stencils(nd, nd, max(n, nh))
+    cw = M.Weights(st, n, k, m, M.MFD_OP_GRAD)
+    hw = M.Weights(st, nh, 2 * alpha + 1, 2 * alpha, M.MFD_OP_LAP_POW, alpha)
+    return cw, hw, (nd, st)
 
 
 def _adjoint_small_gpu(M, ctx, nx=60, steps=400):
@@ -1052,10 +1083,7 @@ def _adjoint_small_gpu(M, ctx, nx=60, steps=400):
     P = _adjoint_problem(nx)
     dt, eps0, mu0, c0, eta0 = W.units(P["S"])
     ns = P["nodes"]
-    nd = M.Nodes(ctx, ns.xyz, ns.period)
-    st = M.Stencils(nd, nd, 31)
-    cw = M.Weights(st, 20, 3, 2, M.MFD_OP_GRAD)
-    hw = M.Weights(st, 31, 5, 4, M.MFD_OP_LAP_POW, 2)
+    cw, hw, keep = _adjoint_weights(M, ctx, P)
     sim = M.Sim(ctx, 2, M.MFD_FP32, dt, eps0, mu0, -P["c"], cw, hw, compensated=True)
     sim.set_materials(P["eps"], ns.pec)
     z = np.zeros(ns.n)
