@@ -131,7 +131,11 @@ int64_t mfd_nodes_count(const mfd_nodes* nodes);
  * component needs holding at the walls (pass no PEC flags): the symmetry is
  * the boundary condition. Call before building stencils; axes must not be
  * periodic; fewer than 2^29 nodes. Supported by the collocated 2D and 3D
- * layouts (not the staggered layout, the batch or the gradient: MFD_ERR_ARG). */
+ * layouts (not the staggered layout, the batch or the gradient: MFD_ERR_ARG).
+ * With curl stencils of the fewest nodes the monomials allow (n = 2 M_m),
+ * some stencils of the layer next to a wall give the 3D curl a growing mode;
+ * a few more nodes in that layer (mfd_weights_compute_sized, e.g. 44 instead
+ * of 40) remove it. */
 mfd_status mfd_nodes_set_mirror(mfd_nodes* nodes, uint32_t axes, const double* hi);
 /* perm (host, n): perm[k] = caller id of the k-th node in device order. */
 mfd_status mfd_nodes_permutation(const mfd_nodes* nodes, int64_t* perm);
