@@ -61,6 +61,9 @@ def _args():
                     help="steps of the differentiation workload (--only adjoint)")
     ap.add_argument("--batched-steps", type=int, default=3000,
                     help="steps of the batched 256-domain x 16-RHS workload (0: skip)")
+    ap.add_argument("--l2-keep", type=float, default=None,
+                    help="fraction of the stencil streams kept in L2 for the headline and adjoint "
+                         "simulations (mfd_sim_set_l2_keep; default: sized from the L2)")
     return ap.parse_args()
 
 
@@ -493,7 +496,7 @@ def main():
         elif a.only == "cavity":
             r = cavity(M, ctx)
         elif a.only == "adjoint":
-            r = adjoint(M, ctx, steps=a.adjoint_steps)
+            r = adjoint(M, ctx, steps=a.adjoint_steps, l2_keep=a.l2_keep)
         elif a.only == "hv_search":
             r = hv_search(M, ctx)
         elif a.only == "yee":
@@ -524,6 +527,8 @@ def main():
     ctx = M.Ctx(local)
     wts, setup, nhv = build_weights(M, ctx, e, h)
     sim = make_sim(M, ctx, wts, prec, comp)
+    if a.l2_keep is not None:
+        sim.set_l2_keep(a.l2_keep)
     S = PARAMS["S"]
     dt = W.units(S)[0]
     ez, hx, hy = pulse_fields(e, h, nx, dt)
@@ -587,7 +592,8 @@ def main():
                        "hv_stencil": nhv, "phs": PARAMS["k"], "poly_m": PARAMS["m"], "alpha": PARAMS["alpha"],
                        "courant": S, "compensated": comp, "l2_flush": f"inputs larger than L2 ({step_gb:.2f} GB/step)",
                        "parallelism": f"replicas{world}", "setup_s": setup,
-                       "autotuned_blocks": {"h_pass": blocks[0], "e_pass": blocks[1]}},
+                       "autotuned_blocks": {"h_pass": blocks[0], "e_pass": blocks[1]},
+                       "l2_keep": sim.l2_keep},
             "roofline": roof, "clocks": clocks, "gpu_launches": 3 * a.steps,
             "energy_rel_end": {"u": u_rel, "after_steps": a.warmup + min(a.steps, 64) + 2 * a.steps},
             "event_timed_ms_per_step": (ms[0] + ms[1]) / a.steps,
@@ -641,7 +647,7 @@ def main():
         line["cube3d"] = cube3d(M, ctx, a.cube_steps, peak, peak_kind)
     if solo and not a.no_extra:
         line["cavity_fp64"] = cavity(M, ctx)
-        line["adjoint"] = adjoint(M, ctx)
+        line["adjoint"] = adjoint(M, ctx, l2_keep=a.l2_keep)
         line["hv_search"] = hv_search(M, ctx)
         line["yee"] = yee(M, ctx, peak, peak_kind)
     # end to end through the public API: host fields in, steps, host Ez + probes out
@@ -998,7 +1004,7 @@ def cavity(M, ctx, steps=1000):
             "_gpu": {"fields": got, "probes": sim.read_probes(), "steps": steps}}
 
 
-def adjoint(M, ctx, steps=C5["steps"], every=C5["checkpoint_every"]):
+def adjoint(M, ctx, steps=C5["steps"], every=C5["checkpoint_every"], l2_keep=None):
     """Differentiation workload: 500 x 500 PEC box, n = 20 (r^3, degree 2),
     Delta^2 HV, eps_r = 1 + 0.5 U, 4 Ricker sources, 8 probes, FP32, 4000
     steps: J = dt sum Ez_p^2 and dJ/deps_r, dJ/d amplitudes by the adjoint with
@@ -1011,6 +1017,8 @@ def adjoint(M, ctx, steps=C5["steps"], every=C5["checkpoint_every"]):
     dt, eps0, mu0, c0, eta0 = W.units(S)
     cw, hw, keep = _adjoint_weights(M, ctx, P)
     sim = M.Sim(ctx, 2, M.MFD_FP32, dt, eps0, mu0, -c, cw, hw, compensated=True)
+    if l2_keep is not None:
+        sim.set_l2_keep(l2_keep)
     eps, src, probes = P["eps"], P["src"], P["probes"]
     z = np.zeros(nodes.n)
 
@@ -1048,6 +1056,7 @@ def adjoint(M, ctx, steps=C5["steps"], every=C5["checkpoint_every"]):
     return {"workload": f"adjoint {nodes_side}x{nodes_side} PEC, n={P['stencil'][0]}, FP32, {steps} steps, checkpoints every {every}", "nodes": nodes.n,
             "_gpu": small,
             "forward_value": nodes.n * 3 * steps / fwd, "unit": UNIT, "forward_ms_per_step": fwd / steps * 1e3,
+            "l2_keep": sim.l2_keep,
             "gradient_s": gs, "gradient_over_forward": gs / fwd, "J": J,
             "grad_norm_eps": float(np.linalg.norm(ge)), "grad_amp": [float(x) for x in ga],
             "whole_history": {"gradient_s": gw, "gradient_over_forward": gw / fwd,

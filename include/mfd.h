@@ -314,6 +314,22 @@ mfd_status mfd_sim_set_index_format(mfd_sim* sim, int format);
  * whose HV stream is 32-bit} of the H pass, then the same of the E pass;
  * zeros when the layout has no Q16 streams (collocated, 3D). */
 mfd_status mfd_sim_index_stats(const mfd_sim* sim, int64_t* out);
+/* L2 residency of the stencil streams (no counterpart in the paper: a cache
+ * policy of this GPU). The step kernels read the index and weight streams once
+ * per half step; a fraction `keep` of their cache lines is loaded with the L2
+ * policy evict_last and the rest with evict_first. When a problem's streams
+ * are about the size of the L2, the kept lines stay in L2 from one step to the
+ * next and the rest stream through without evicting them or the gathered
+ * fields. By default (keep < 0) the fraction is sized so that the kept lines
+ * fill about 40 % of the device's L2 (1 for problems whose streams fit in
+ * that, 0 below a tenth); keep in [0, 1] fixes it. The adjoint sweep sizes its
+ * own fraction from the transposed streams. The 3D kernels mark every line
+ * evict_first whatever keep is (their problems are far larger than the L2).
+ * Results do not depend on keep (bit-identical fields). MFD_ERR_ARG for
+ * keep > 1 or NaN. */
+mfd_status mfd_sim_set_l2_keep(mfd_sim* sim, double keep);
+/* The fraction the forward step kernels use (0 for the 3D layout, -1 for a NULL sim). */
+double mfd_sim_l2_keep(const mfd_sim* sim);
 /* Gradient of the probe objective J = dt sum_{n=1..N} sum_p (Ez_p^n)^2
  * (Ez at the probes of mfd_set_probes after each of the next N = nsteps
  * steps) with respect to the relative permittivity of every E node and the

@@ -84,6 +84,8 @@ _SIGS = {
     "mfd_set_probe_component": (_I, [_VP, _I]),
     "mfd_sim_set_index_format": (_I, [_VP, _I]),
     "mfd_sim_index_stats": (_I, [_VP, _VP]),
+    "mfd_sim_set_l2_keep": (_I, [_VP, _D]),
+    "mfd_sim_l2_keep": (_D, [_VP]),
     "mfd_sim_destroy": (None, [_VP]),
     "mfd_knn_static": (_I, [_I, _I64, _VP, _I64, _VP, _VP, _I, _VP, _VP]),
     "mfd_yee_create": (_I, [_VP, _I64, _I64, _I, _D, _D, _D, _D, C.POINTER(_VP)]),
@@ -646,6 +648,16 @@ class Sim:
     def set_blocks(self, block_h, block_e):
         _ck(lib().mfd_sim_set_blocks(self.h, int(block_h), int(block_e)))
 
+    def set_l2_keep(self, keep):
+        """Fraction of the stencil streams' L2 lines kept from step to step (mfd_sim_set_l2_keep);
+        negative: sized from the device's L2."""
+        _ck(lib().mfd_sim_set_l2_keep(self.h, float(keep)))
+
+    @property
+    def l2_keep(self):
+        """The fraction the step kernels use (mfd_sim_l2_keep)."""
+        return float(lib().mfd_sim_l2_keep(self.h))
+
     def set_index_format(self, fmt):
         """MFD_INDEX_Q16 (default) or MFD_INDEX_I32 indices in the staggered kernels (mfd_sim_set_index_format)."""
         _ck(lib().mfd_sim_set_index_format(self.h, int(fmt)))
@@ -773,7 +785,8 @@ class Batch:
         _ck(lib().mfd_batch_load_state(self.h, blob, len(blob)))
 
     def set_variant(self, variant):
-        """Work split of the batched kernel (mfd_batch_set_variant): 0 = nrhs/4, 1 = nrhs/2 lanes per node."""
+        """Variant of the batched kernel (mfd_batch_set_variant): 0 = next-chunk stream
+        prefetch, three resident blocks per SM; 1 = no prefetch, four blocks per SM."""
         _ck(lib().mfd_batch_set_variant(self.h, int(variant)))
 
     @property
@@ -781,7 +794,7 @@ class Batch:
         return int(lib().mfd_batch_variant(self.h))
 
     def autotune(self, reps=20):
-        """Times both work splits on this batch and keeps the faster (mfd_batch_autotune):
+        """Times both variants on this batch and keeps the faster (mfd_batch_autotune):
         (chosen variant, ms per step of each)."""
         chosen = C.c_int(-1)
         ms = np.zeros(2)

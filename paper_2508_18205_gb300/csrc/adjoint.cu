@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(256) k_adj_a(const int64_t* __restrict__ off, 
                                                typename Vec<T>::V4* __restrict__ LB, T gamma,
                                                const T* __restrict__ ez, const int64_t* __restrict__ slot0, int kl,
                                                const double* __restrict__ eps, double* __restrict__ g_eps,
-                                               AdjTerms tm) {
+                                               AdjTerms tm, float keep) {
     using V4 = typename Vec<T>::V4;
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -266,11 +266,12 @@ __global__ void __launch_bounds__(256) k_adj_a(const int64_t* __restrict__ off, 
     const int64_t sl = j >> 5;
     const int64_t base = off[sl] * 32 + (j & 31);
     const int nc = (int)(off[sl + 1] - off[sl]);
+    const uint64_t pol = stream_policy(keep);
     T ax = 0, ay = 0, av = 0;
     for (int c = 0; c < nc; ++c) {
         const int64_t d = base + (int64_t)c * 32;
-        const int4 id = chk4(ld_stream(scol + d), n);
-        const V4 wx = ld_stream(sx + d), wy = ld_stream(sy + d), wv = ld_stream(sv + d);
+        const int4 id = chk4(ld_stream(scol + d, pol), n);
+        const V4 wx = ld_stream(sx + d, pol), wy = ld_stream(sy + d, pol), wv = ld_stream(sv + d, pol);
         const int ids[4] = {id.x, id.y, id.z, id.w};
         const T* wxs = &wx.x;
         const T* wys = &wy.x;
@@ -306,18 +307,19 @@ __global__ void __launch_bounds__(256) k_adj_b(const int64_t* __restrict__ off, 
                                                const typename Vec<T>::V4* __restrict__ LB,
                                                typename Vec<T>::V4* __restrict__ LA, T ch, T gamma,
                                                const T* __restrict__ ez, const int64_t* __restrict__ slot0, int kl,
-                                               AdjTerms tm) {
+                                               AdjTerms tm, float keep) {
     using V4 = typename Vec<T>::V4;
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
     const int64_t sl = j >> 5;
     const int64_t base = off[sl] * 32 + (j & 31);
     const int nc = (int)(off[sl + 1] - off[sl]);
+    const uint64_t pol = stream_policy(keep);
     T vx = 0, vy = 0, cx = 0, cy = 0;
     for (int c = 0; c < nc; ++c) {
         const int64_t d = base + (int64_t)c * 32;
-        const int4 id = chk4(ld_stream(scol + d), n);
-        const V4 wx = ld_stream(sx + d), wy = ld_stream(sy + d), wv = ld_stream(sv + d);
+        const int4 id = chk4(ld_stream(scol + d, pol), n);
+        const V4 wx = ld_stream(sx + d, pol), wy = ld_stream(sy + d, pol), wv = ld_stream(sv + d, pol);
         const int ids[4] = {id.x, id.y, id.z, id.w};
         const T* wxs = &wx.x;
         const T* wys = &wy.x;
@@ -353,18 +355,18 @@ cudaError_t adj_pass(const AdjArgs& a, int pass, cudaStream_t s) {
         const dbl4 *x = (const dbl4*)a.sx, *y = (const dbl4*)a.sy, *v = (const dbl4*)a.sv;
         if (pass == 0)
             k_adj_a<double><<<g, 256, 0, s>>>(a.off, a.scol, x, y, v, a.n, (const dbl4*)a.LA, (dbl4*)a.LB, a.gamma,
-                                              (const double*)a.ez, a.slot0, a.k, a.eps, a.g_eps, tm);
+                                              (const double*)a.ez, a.slot0, a.k, a.eps, a.g_eps, tm, a.l2_keep);
         else
             k_adj_b<double><<<g, 256, 0, s>>>(a.off, a.scol, x, y, v, a.n, (const dbl4*)a.LB, (dbl4*)a.LA, a.ch,
-                                              a.gamma, (const double*)a.ez, a.slot0, a.k, tm);
+                                              a.gamma, (const double*)a.ez, a.slot0, a.k, tm, a.l2_keep);
     } else {
         const float4 *x = (const float4*)a.sx, *y = (const float4*)a.sy, *v = (const float4*)a.sv;
         if (pass == 0)
             k_adj_a<float><<<g, 256, 0, s>>>(a.off, a.scol, x, y, v, a.n, (const float4*)a.LA, (float4*)a.LB,
-                                             (float)a.gamma, (const float*)a.ez, a.slot0, a.k, a.eps, a.g_eps, tm);
+                                             (float)a.gamma, (const float*)a.ez, a.slot0, a.k, a.eps, a.g_eps, tm, a.l2_keep);
         else
             k_adj_b<float><<<g, 256, 0, s>>>(a.off, a.scol, x, y, v, a.n, (const float4*)a.LB, (float4*)a.LA,
-                                             (float)a.ch, (float)a.gamma, (const float*)a.ez, a.slot0, a.k, tm);
+                                             (float)a.ch, (float)a.gamma, (const float*)a.ez, a.slot0, a.k, tm, a.l2_keep);
     }
     return cudaGetLastError();
 }

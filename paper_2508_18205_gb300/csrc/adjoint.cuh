@@ -53,6 +53,7 @@ struct AdjArgs {
     // the per-step source and probe terms, done by the threads of their nodes
     // inside the passes (see AdjTerms)
     const struct AdjTerms* terms = nullptr;
+    float l2_keep = 0.0f;  // fraction of the transposed streams' lines kept in L2 (stream_policy)
 };
 
 // Source and probe terms of a backward step, fused into the passes: the thread

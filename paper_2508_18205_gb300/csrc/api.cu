@@ -175,6 +175,9 @@ mfd_status mfd_ctx_create(int device, void* stream, mfd_ctx** out) {
         c->own_stream = true;
     }
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
+    c->l2_bytes = l2;
     *out = c;
     return MFD_OK;
 }

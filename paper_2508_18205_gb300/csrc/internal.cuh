@@ -79,6 +79,7 @@ struct mfd_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int sm_count = 0;
+    int64_t l2_bytes = 0;  // L2 cache size of the device
     mfd::DevBuf status;  // device status words (int32[8]) shared by bounded waits
 };
 

@@ -15,7 +15,13 @@
 //    arrays from which the E half step reassembles the block.
 //    ce = dt / (eps0 eps_r) of the node, 0 at a PEC node in 2D.
 //  * weight and index streams are read with L1::no_allocate so that L1 keeps
-//    the gathered fields of the Morton neighbourhood.
+//    the gathered fields of the Morton neighbourhood, and with an L2 policy:
+//    a fraction `keep` of their lines is marked evict_last, the rest
+//    evict_first. The streams are read once per half step, so they should
+//    neither push the gathered fields out of L2 nor, when a problem's streams
+//    are about the size of L2, evict one another before the next step: the
+//    kept fraction then stays in L2 from one step to the next (the host sizes
+//    keep from the L2 capacity and the streams' bytes; 0 for large problems).
 //  * the staggered step kernels read their indices in a 16-bit form (Q16):
 //    per slice and stream two bases {b0, b1 - 32768}; entry u < 32768 is node
 //    b0 + u, entry u >= 32768 is node b1 + (u - 32768), so one slice may draw
@@ -45,39 +51,58 @@ template <> struct Vec<double> {
     using V4 = dbl4;
 };
 
-// ---- streamed (read once) loads: bypass L1 allocation
-__device__ __forceinline__ int4 ld_stream(const int4* p) {
+// ---- streamed (read once) loads: bypass L1 allocation, L2 policy `pol`
+// (stream_policy); the overloads without a policy mark every line evict_first
+__device__ __forceinline__ uint64_t stream_policy(float keep) {
+    uint64_t p;
+    if (keep > 0.0f)
+        asm("createpolicy.fractional.L2::evict_last.L2::evict_first.b64 %0, %1;" : "=l"(p) : "f"(fminf(keep, 1.0f)));
+    else
+        asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ int4 ld_stream(const int4* p, uint64_t pol) {
     int4 v;
-    asm("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p), "l"(pol));
     return v;
 }
-__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
+__device__ __forceinline__ uint4 ld_stream(const uint4* p, uint64_t pol) {
     uint4 v;
-    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p), "l"(pol));
     return v;
 }
-__device__ __forceinline__ int2 ld_stream(const int2* p) {
+__device__ __forceinline__ int2 ld_stream(const int2* p, uint64_t pol) {
     int2 v;
-    asm("ld.global.nc.L1::no_allocate.v2.s32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.s32 {%0,%1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
     return v;
 }
-__device__ __forceinline__ float4 ld_stream(const float4* p) {
+__device__ __forceinline__ float4 ld_stream(const float4* p, uint64_t pol) {
     float4 v;
-    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p), "l"(pol));
     return v;
 }
-__device__ __forceinline__ dbl4 ld_stream(const dbl4* p) {
+__device__ __forceinline__ dbl4 ld_stream(const dbl4* p, uint64_t pol) {
     dbl4 v;
     const double2* q = reinterpret_cast<const double2*>(p);
-    asm("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(q));
-    asm("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(v.z), "=d"(v.w) : "l"(q + 1));
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(q), "l"(pol));
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;"
+        : "=d"(v.z), "=d"(v.w)
+        : "l"(q + 1), "l"(pol));
     return v;
+}
+template <typename P> __device__ __forceinline__ auto ld_stream(const P* p) { return ld_stream(p, stream_policy(0.0f)); }
+// KEEP = false: every line evict_first, the policy made at the load (pol unused); this
+// form measured 1-2 % faster in the staggered kernels than one policy register
+// carried through the loop. KEEP = true: the policy register `pol`.
+template <bool KEEP, typename P> __device__ __forceinline__ auto ld_stream_k(const P* p, uint64_t pol) {
+    if constexpr (KEEP) return ld_stream(p, pol);
+    else return ld_stream(p);
 }
 
 // ---- gathered (reused by neighbours) loads: through L1
@@ -190,6 +215,7 @@ template <typename T> struct StencilStreams {
     bool mirror = false;           // entries carry image codes (PEC walls by images)
     const uint8_t* cext = nullptr;  // curl chunks each 32-node slice reads (per-centre sizes), or null: nc
     int nc0 = 0;                    // with cext: the fewest curl chunks of any slice
+    float l2_keep = 0.0f;           // fraction of the stream lines kept in L2 (stream_policy)
 };
 
 // ---- bounds-checked build (compiled with -DMFD_BOUNDS_CHECK): every stencil
@@ -281,25 +307,25 @@ __device__ __forceinline__ int4 q16_hi(uint4 u, int2 b) {
 // Calls body(c, id) for the N4 (or n4_rt when N4 == 0) chunks of 4 stencil
 // entries of the node in lane `lane` of slice `slice`, taking the indices from
 // the Q16 stream when the slice has one and from the 32-bit stream otherwise.
-template <int N4, typename Body>
+template <int N4, bool KEEP, typename Body>
 __device__ __forceinline__ void for_idx4(int n4_rt, int64_t slice, int lane, const int4* __restrict__ idx,
                                          const uint4* __restrict__ q, const int2* __restrict__ qb, int64_t bound,
-                                         Body&& body) {
+                                         uint64_t pol, Body&& body) {
     const int n4 = N4 ? N4 : n4_rt;
     const int n8 = (n4 + 1) >> 1;
-    const int2 b = q ? ld_stream(qb + slice) : make_int2(-1, 0);
+    const int2 b = q ? ld_stream_k<KEEP>(qb + slice, pol) : make_int2(-1, 0);
     if (b.x >= 0) {
         const uint4* p = q + slice * n8 * 32 + lane;
 #pragma unroll
         for (int c8 = 0; c8 < (N4 ? (N4 + 1) / 2 : n8); ++c8) {
-            const uint4 u = ld_stream(p + c8 * 32);
+            const uint4 u = ld_stream_k<KEEP>(p + c8 * 32, pol);
             body(2 * c8, chk4(q16_lo(u, b), bound));
             if (2 * c8 + 1 < n4) body(2 * c8 + 1, chk4(q16_hi(u, b), bound));
         }
     } else {
         const int4* p = idx + slice * n4 * 32 + lane;
 #pragma unroll
-        for (int c = 0; c < n4; ++c) body(c, chk4(ld_stream(p + c * 32), bound));
+        for (int c = 0; c < n4; ++c) body(c, chk4(ld_stream_k<KEEP>(p + c * 32, pol), bound));
     }
 }
 

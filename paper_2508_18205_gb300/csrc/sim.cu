@@ -261,6 +261,7 @@ struct mfd_sim {
     int lanes[2] = {0, 0};      // collocated 2D: lanes per node of each pass (0: the size rule; autotuned)
     int probe_comp = MFD_EZ;    // the component the probes record
     bool q16 = true;            // staggered kernels read Q16 indices (mfd_sim_set_index_format)
+    double l2_keep_set = -1.0;  // fraction of the stream lines kept in L2; < 0: sized from the L2 (mfd_sim_set_l2_keep)
     int64_t watch_every = 0;    // energy watchdog: check every this many steps (0: off)
     double watch_ratio = 0, watch_u0 = 0;
     ~mfd_sim() {
@@ -447,6 +448,35 @@ template <typename T> StencilStreams<T> streams(const PackedStencil& p, bool q16
     return s;
 }
 
+// the fraction of the stencil streams' cache lines marked evict_last (stream_policy):
+// the kept lines fill about 40 % of the L2 (the rest holds the fields and the lines
+// in flight; on a two-die part a line read from both dies may be held in both
+// halves of the L2, and on the 250k-node collocated problem 40 % ran 10 % faster
+// per step while 60 % and more thrashed); below a tenth nothing is kept (every
+// line evict_first)
+float keep_for(int64_t stream_bytes, int64_t l2_bytes) {
+    if (stream_bytes <= 0 || l2_bytes <= 0) return 0.0f;
+    const double k = 0.4 * (double)l2_bytes / (double)stream_bytes;
+    return k >= 1.0 ? 1.0f : (k < 0.1 ? 0.0f : (float)k);
+}
+
+// bytes of the stencil streams one step reads: the weights and the index form the kernels take
+int64_t step_stream_bytes(const mfd_sim* sim) {
+    auto one = [&](const PackedStencil& p) {
+        int64_t b = (int64_t)(p.wx.bytes + p.wy.bytes + p.wz.bytes + p.wv.bytes);
+        if (sim->q16 && p.q_c.p && p.q_v.p) b += (int64_t)(p.q_c.bytes + p.q_v.bytes + p.qb_c.bytes + p.qb_v.bytes);
+        else b += (int64_t)(p.idx_c.bytes + p.idx_v.bytes);
+        return b;
+    };
+    return one(sim->hp) + (sim->layout == STAG2D ? one(sim->ep) : 0);
+}
+
+float sim_keep(const mfd_sim* sim) {
+    if (sim->layout == COLLOC3D) return 0.0f;  // the 3D kernels stream every line evict_first
+    if (sim->l2_keep_set >= 0) return (float)sim->l2_keep_set;
+    return keep_for(step_stream_bytes(sim), sim->ctx->l2_bytes);
+}
+
 Launch2D make2d(mfd_sim* sim, int parity) {
     Launch2D L;
     L.staggered = sim->layout == STAG2D;
@@ -458,6 +488,8 @@ Launch2D make2d(mfd_sim* sim, int parity) {
         L.es.f = streams<float>(sim->ep, sim->q16);
         L.es.d = streams<double>(sim->ep, sim->q16);
     }
+    const float keep = sim_keep(sim);
+    L.hs.f.l2_keep = L.hs.d.l2_keep = L.es.f.l2_keep = L.es.d.l2_keep = keep;
     L.kf.ch = (float)(sim->d.dt / sim->d.mu0);
     L.kf.gamma = (float)sim->d.gamma;
     L.kd.ch = sim->d.dt / sim->d.mu0;
@@ -491,6 +523,7 @@ Launch3D make3d(mfd_sim* sim, int parity) {
     L.comp = sim->comp;
     L.s.f = streams<float>(sim->hp);
     L.s.d = streams<double>(sim->hp);
+    L.s.f.l2_keep = L.s.d.l2_keep = sim_keep(sim);
     L.kf.ch = (float)(sim->d.dt / sim->d.mu0);
     L.kf.gamma = (float)sim->d.gamma;
     L.kd.ch = sim->d.dt / sim->d.mu0;
@@ -1247,6 +1280,15 @@ mfd_status mfd_sim_set_index_format(mfd_sim* sim, int format) {
     return MFD_OK;
 }
 
+mfd_status mfd_sim_set_l2_keep(mfd_sim* sim, double keep) {
+    if (!sim || !(keep <= 1.0) || std::isnan(keep)) return fail(MFD_ERR_ARG, "keep must be <= 1 (negative: automatic)");
+    sim->l2_keep_set = keep < 0 ? -1.0 : keep;
+    sim->graph_ok = false;  // the fraction is a kernel argument of the captured steps
+    return MFD_OK;
+}
+
+double mfd_sim_l2_keep(const mfd_sim* sim) { return sim ? (double)sim_keep(sim) : -1.0; }
+
 mfd_status mfd_sim_index_stats(const mfd_sim* sim, int64_t* out) {
     if (!sim || !out) return fail(MFD_ERR_ARG, "NULL argument");
     const PackedStencil* ps[2] = {&sim->hp, &sim->ep};
@@ -1552,6 +1594,11 @@ mfd_status mfd_grad_backward(mfd_tape* tape, double* g_eps, double* g_amp, int o
     a.g_eps = geps.as<double>();
     a.ez = hist.p;
     a.slot0 = slot0.as<int64_t>();
+    // both transposed passes of a backward step read the same streams
+    a.l2_keep = sim->l2_keep_set >= 0
+                    ? (float)sim->l2_keep_set
+                    : keep_for((int64_t)(sim->adj.scol.bytes + sim->adj.sx.bytes + sim->adj.sy.bytes + sim->adj.sv.bytes),
+                               sim->ctx->l2_bytes);
     // the per-step source and probe terms, fused into the passes: node bits and node-sorted lists
     AdjTerms terms;
     DevBuf d_smask, d_pmask, d_snode, d_sidx, d_pnode;

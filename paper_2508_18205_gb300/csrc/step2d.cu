@@ -53,6 +53,7 @@ __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const 
     const int nv = NV ? NV : s.nv;
     const int64_t slice = i >> 5;
     const int lane = (int)(i & 31);
+    const uint64_t pol = stream_policy(s.l2_keep);
     Acc ax, ay;
     AccV hx, hy, he;
     if constexpr (SHARED) {
@@ -63,13 +64,13 @@ __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const 
         const V4* pv = s.wv + slice * nv * 32 + lane;
 #pragma unroll
         for (int c = part; c < (act ? ni : 0); c += P) {
-            const int4 raw = ld_stream(ip + c * 32);
+            const int4 raw = ld_stream(ip + c * 32, pol);
             V4 wx, wy, wv;
             if (c < nc) {
-                wx = ld_stream(px + c * 32);
-                wy = ld_stream(py + c * 32);
+                wx = ld_stream(px + c * 32, pol);
+                wy = ld_stream(py + c * 32, pol);
             }
-            if (c < nv) wv = ld_stream(pv + c * 32);
+            if (c < nv) wv = ld_stream(pv + c * 32, pol);
             V4 f0, f1, f2, f3;
             gather4_tmz<MIR>(A, raw, s.src_c, f0, f1, f2, f3);
             if (c < nc) {
@@ -90,8 +91,8 @@ __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const 
         const V4* pv = s.wv + slice * nv * 32 + lane;
 #pragma unroll
         for (int c = part; c < (act ? nc : 0); c += P) {
-            const int4 raw = ld_stream(ic + c * 32);
-            const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32);
+            const int4 raw = ld_stream(ic + c * 32, pol);
+            const V4 wx = ld_stream(px + c * 32, pol), wy = ld_stream(py + c * 32, pol);
             V4 g0, g1, g2, g3;
             gather4_tmz<MIR>(A, raw, s.src_c, g0, g1, g2, g3);
             const T f0 = g0.x, f1 = g1.x, f2 = g2.x, f3 = g3.x;
@@ -100,8 +101,8 @@ __device__ __forceinline__ void h_colloc_node(const StencilStreams<T>& s, const 
         }
 #pragma unroll
         for (int c = part; c < (act ? nv : 0); c += P) {
-            const int4 raw = ld_stream(iv + c * 32);
-            const V4 wv = ld_stream(pv + c * 32);
+            const int4 raw = ld_stream(iv + c * 32, pol);
+            const V4 wv = ld_stream(pv + c * 32, pol);
             V4 f0, f1, f2, f3;
             gather4_tmz<MIR>(A, raw, s.src_v, f0, f1, f2, f3);
             hx.add(wv.x, f0.y); hx.add(wv.y, f1.y); hx.add(wv.z, f2.y); hx.add(wv.w, f3.y);
@@ -162,11 +163,12 @@ __global__ void __launch_bounds__(512) k_e_colloc(StencilStreams<T> s, const typ
     const int4* ip = s.idx_c + slice * ni * 32 + lane;
     const V4* px = s.wx + slice * nc * 32 + lane;
     const V4* py = s.wy + slice * nc * 32 + lane;
+    const uint64_t pol = stream_policy(s.l2_keep);
     Acc dxHy, dyHx;
 #pragma unroll
     for (int c = part; c < (act ? nc : 0); c += P) {
-        const int4 raw = ld_stream(ip + c * 32);
-        const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32);
+        const int4 raw = ld_stream(ip + c * 32, pol);
+        const V4 wx = ld_stream(px + c * 32, pol), wy = ld_stream(py + c * 32, pol);
         V4 f0, f1, f2, f3;
         gather4_tmz<MIR>(B, raw, s.src_c, f0, f1, f2, f3);
         dxHy.add(wx.x, f0.z); dxHy.add(wx.y, f1.z); dxHy.add(wx.z, f2.z); dxHy.add(wx.w, f3.z);
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(256) k_energy_colloc(StencilStreams<T> s, Coef
 
 // ------------------------------------------------------------ staggered
 
-template <typename T, int NC, int NV, bool COMP>
+template <typename T, int NC, int NV, bool COMP, bool KEEP>
 __device__ __forceinline__ void h_stag_node(const StencilStreams<T>& s, const T* __restrict__ Ez,
                                             const typename Vec<T>::V2* __restrict__ H, int64_t i, T& dxE, T& dyE,
                                             T& vx, T& vy) {
@@ -236,19 +238,20 @@ __device__ __forceinline__ void h_stag_node(const StencilStreams<T>& s, const T*
     const V4* px = s.wx + slice * nc * 32 + lane;
     const V4* py = s.wy + slice * nc * 32 + lane;
     const V4* pv = s.wv + slice * nv * 32 + lane;
+    const uint64_t pol = KEEP ? stream_policy(s.l2_keep) : 0;
     Acc ax, ay;
     AccV hx, hy;
     // HV sums first: their H gathers are the larger share of the pass's loads, and issuing them
     // first measured 4 % faster than curl-first (the sums themselves do not depend on the order)
-    for_idx4<NV>(nv, slice, lane, s.idx_v, s.q_v, s.qb_v, s.src_v, [&](int c, int4 id) {
-        const V4 wv = ld_stream(pv + c * 32);
+    for_idx4<NV, KEEP>(nv, slice, lane, s.idx_v, s.q_v, s.qb_v, s.src_v, pol, [&](int c, int4 id) {
+        const V4 wv = ld_stream_k<KEEP>(pv + c * 32, pol);
         const V2 f0 = ld_gather(H + id.x), f1 = ld_gather(H + id.y);
         const V2 f2 = ld_gather(H + id.z), f3 = ld_gather(H + id.w);
         hx.add(wv.x, f0.x); hx.add(wv.y, f1.x); hx.add(wv.z, f2.x); hx.add(wv.w, f3.x);
         hy.add(wv.x, f0.y); hy.add(wv.y, f1.y); hy.add(wv.z, f2.y); hy.add(wv.w, f3.y);
     });
-    for_idx4<NC>(nc, slice, lane, s.idx_c, s.q_c, s.qb_c, s.src_c, [&](int c, int4 id) {
-        const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32);
+    for_idx4<NC, KEEP>(nc, slice, lane, s.idx_c, s.q_c, s.qb_c, s.src_c, pol, [&](int c, int4 id) {
+        const V4 wx = ld_stream_k<KEEP>(px + c * 32, pol), wy = ld_stream_k<KEEP>(py + c * 32, pol);
         const T f0 = ld_gather(Ez + id.x), f1 = ld_gather(Ez + id.y);
         const T f2 = ld_gather(Ez + id.z), f3 = ld_gather(Ez + id.w);
         ax.add(wx.x, f0); ax.add(wx.y, f1); ax.add(wx.z, f2); ax.add(wx.w, f3);
@@ -260,7 +263,7 @@ __device__ __forceinline__ void h_stag_node(const StencilStreams<T>& s, const T*
     vy = hy.get();
 }
 
-template <typename T, int NC, int NV, bool COMP>
+template <typename T, int NC, int NV, bool COMP, bool KEEP>
 __global__ void __launch_bounds__(512) k_h_stag(StencilStreams<T> s, Coefs<T> k, const T* __restrict__ Ez,
                                                 const typename Vec<T>::V2* __restrict__ H,
                                                 typename Vec<T>::V2* __restrict__ Hn) {
@@ -268,7 +271,7 @@ __global__ void __launch_bounds__(512) k_h_stag(StencilStreams<T> s, Coefs<T> k,
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= s.n) return;
     T dxE, dyE, vx, vy;
-    h_stag_node<T, NC, NV, COMP>(s, Ez, H, i, dxE, dyE, vx, vy);
+    h_stag_node<T, NC, NV, COMP, KEEP>(s, Ez, H, i, dxE, dyE, vx, vy);
     const V2 me = ld_gather(H + i);
     V2 out;
     out.x = me.x - k.ch * (dyE - k.gamma * vx);
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(512) k_h_stag(StencilStreams<T> s, Coefs<T> k,
     Hn[i] = out;
 }
 
-template <typename T, int NC, int NV, bool COMP>
+template <typename T, int NC, int NV, bool COMP, bool KEEP>
 __global__ void __launch_bounds__(512) k_e_stag(StencilStreams<T> s, Coefs<T> k, const typename Vec<T>::V2* __restrict__ Hn,
                                                 const T* __restrict__ Ez, const T* __restrict__ ce,
                                                 T* __restrict__ Ezn) {
@@ -292,17 +295,18 @@ __global__ void __launch_bounds__(512) k_e_stag(StencilStreams<T> s, Coefs<T> k,
     const V4* px = s.wx + slice * nc * 32 + lane;
     const V4* py = s.wy + slice * nc * 32 + lane;
     const V4* pv = s.wv + slice * nv * 32 + lane;
+    const uint64_t pol = KEEP ? stream_policy(s.l2_keep) : 0;
     Acc dxHy, dyHx;
     AccPlain<T> he;
-    for_idx4<NC>(nc, slice, lane, s.idx_c, s.q_c, s.qb_c, s.src_c, [&](int c, int4 id) {
-        const V4 wx = ld_stream(px + c * 32), wy = ld_stream(py + c * 32);
+    for_idx4<NC, KEEP>(nc, slice, lane, s.idx_c, s.q_c, s.qb_c, s.src_c, pol, [&](int c, int4 id) {
+        const V4 wx = ld_stream_k<KEEP>(px + c * 32, pol), wy = ld_stream_k<KEEP>(py + c * 32, pol);
         const V2 f0 = ld_gather(Hn + id.x), f1 = ld_gather(Hn + id.y);
         const V2 f2 = ld_gather(Hn + id.z), f3 = ld_gather(Hn + id.w);
         dxHy.add(wx.x, f0.y); dxHy.add(wx.y, f1.y); dxHy.add(wx.z, f2.y); dxHy.add(wx.w, f3.y);
         dyHx.add(wy.x, f0.x); dyHx.add(wy.y, f1.x); dyHx.add(wy.z, f2.x); dyHx.add(wy.w, f3.x);
     });
-    for_idx4<NV>(nv, slice, lane, s.idx_v, s.q_v, s.qb_v, s.src_v, [&](int c, int4 id) {
-        const V4 wv = ld_stream(pv + c * 32);
+    for_idx4<NV, KEEP>(nv, slice, lane, s.idx_v, s.q_v, s.qb_v, s.src_v, pol, [&](int c, int4 id) {
+        const V4 wv = ld_stream_k<KEEP>(pv + c * 32, pol);
         const T f0 = ld_gather(Ez + id.x), f1 = ld_gather(Ez + id.y);
         const T f2 = ld_gather(Ez + id.z), f3 = ld_gather(Ez + id.w);
         he.add(wv.x, f0); he.add(wv.y, f1); he.add(wv.z, f2); he.add(wv.w, f3);
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(256) k_energy_stag(StencilStreams<T> s, Coefs<
     double u = 0.0;
     if (i < s.n) {
         T dxE, dyE, vx, vy;
-        h_stag_node<T, 0, 0, COMP>(s, Ez, H, i, dxE, dyE, vx, vy);
+        h_stag_node<T, 0, 0, COMP, true>(s, Ez, H, i, dxE, dyE, vx, vy);
         const V2 me = H[i];
         const double hx1 = (double)(me.x - k.ch * (dyE - k.gamma * vx));
         const double hy1 = (double)(me.y + k.ch * (dxE + k.gamma * vy));
@@ -395,9 +399,9 @@ static cudaError_t launch_colloc_pass(int pass, const StencilStreams<T>& s, cons
     return launch_colloc_pass_p<T, COMP, 1>(pass, s, k, A, B, block, st);
 }
 
-template <typename T, bool COMP>
-static cudaError_t launch_stag_pass(int pass, const StencilStreams<T>& s, const Coefs<T>& k, const Stag2DPtrs& p,
-                                    int block, cudaStream_t st) {
+template <typename T, bool COMP, bool KEEP>
+static cudaError_t launch_stag_pass_k(int pass, const StencilStreams<T>& s, const Coefs<T>& k, const Stag2DPtrs& p,
+                                      int block, cudaStream_t st) {
     using V2 = typename Vec<T>::V2;
     const unsigned grid = (unsigned)((s.n + block - 1) / block);
     const T* ez = static_cast<const T*>(p.ez);
@@ -406,15 +410,23 @@ static cudaError_t launch_stag_pass(int pass, const StencilStreams<T>& s, const 
     V2* hn = static_cast<V2*>(p.hn);
     const T* ce = static_cast<const T*>(p.ce);
     if (pass == 0) {
-        if (s.nc == 8 && s.nv == 15) k_h_stag<T, 8, 15, COMP><<<grid, block, 0, st>>>(s, k, ez, h, hn);
-        else if (s.nc == 3 && s.nv == 8) k_h_stag<T, 3, 8, COMP><<<grid, block, 0, st>>>(s, k, ez, h, hn);
-        else k_h_stag<T, 0, 0, COMP><<<grid, block, 0, st>>>(s, k, ez, h, hn);
+        if (s.nc == 8 && s.nv == 15) k_h_stag<T, 8, 15, COMP, KEEP><<<grid, block, 0, st>>>(s, k, ez, h, hn);
+        else if (s.nc == 3 && s.nv == 8) k_h_stag<T, 3, 8, COMP, KEEP><<<grid, block, 0, st>>>(s, k, ez, h, hn);
+        else k_h_stag<T, 0, 0, COMP, KEEP><<<grid, block, 0, st>>>(s, k, ez, h, hn);
     } else {
-        if (s.nc == 8 && s.nv == 15) k_e_stag<T, 8, 15, COMP><<<grid, block, 0, st>>>(s, k, hn, ez, ce, ezn);
-        else if (s.nc == 3 && s.nv == 8) k_e_stag<T, 3, 8, COMP><<<grid, block, 0, st>>>(s, k, hn, ez, ce, ezn);
-        else k_e_stag<T, 0, 0, COMP><<<grid, block, 0, st>>>(s, k, hn, ez, ce, ezn);
+        if (s.nc == 8 && s.nv == 15) k_e_stag<T, 8, 15, COMP, KEEP><<<grid, block, 0, st>>>(s, k, hn, ez, ce, ezn);
+        else if (s.nc == 3 && s.nv == 8) k_e_stag<T, 3, 8, COMP, KEEP><<<grid, block, 0, st>>>(s, k, hn, ez, ce, ezn);
+        else k_e_stag<T, 0, 0, COMP, KEEP><<<grid, block, 0, st>>>(s, k, hn, ez, ce, ezn);
     }
     return cudaGetLastError();
+}
+
+// streams kept in L2 (keep > 0) or every line evict_first
+template <typename T, bool COMP>
+static cudaError_t launch_stag_pass(int pass, const StencilStreams<T>& s, const Coefs<T>& k, const Stag2DPtrs& p,
+                                    int block, cudaStream_t st) {
+    return s.l2_keep > 0.0f ? launch_stag_pass_k<T, COMP, true>(pass, s, k, p, block, st)
+                            : launch_stag_pass_k<T, COMP, false>(pass, s, k, p, block, st);
 }
 
 cudaError_t launch_2d(const Launch2D& L, int pass, cudaStream_t st) {

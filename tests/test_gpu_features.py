@@ -283,3 +283,57 @@ def test_probes_of_other_components_match_the_oracle():
                  M.Weights(M.Stencils(de, de, 57), 57, 7, 6, M.MFD_OP_LAP_POW, 3))
     with pytest.raises(M.MfdError):
         stag.set_probe_component(M.MFD_HX)
+
+
+def test_l2_keep_leaves_results_bit_identical():
+    """The L2 policy of the stencil streams (mfd_sim_set_l2_keep) changes where
+    lines live, not what is computed: staggered and collocated steps and a
+    collocated gradient give the same bits for every kept fraction. A problem
+    whose streams fit in the L2 keeps all of them by default; a fraction above 1
+    is refused."""
+    ctx = M.Ctx(0)
+    dt, eps0, mu0, c0, eta0 = W.units(0.5)
+    e = W.periodic_box((40, 40), 0.25, 1)
+    h = W.periodic_box((40, 40), 0.25, 2, offset=(0.5, 0.5))
+    de, dh = M.Nodes(ctx, e.xyz, e.period), M.Nodes(ctx, h.xyz, h.period)
+    hc = M.Weights(M.Stencils(dh, de, 30), 30, 5, 4, M.MFD_OP_GRAD)
+    hv = M.Weights(M.Stencils(dh, dh, 57), 57, 7, 6, M.MFD_OP_LAP_POW, 3)
+    ec = M.Weights(M.Stencils(de, dh, 30), 30, 5, 4, M.MFD_OP_GRAD)
+    ev = M.Weights(M.Stencils(de, de, 57), 57, 7, 6, M.MFD_OP_LAP_POW, 3)
+    rng = np.random.default_rng(5)
+    f = [rng.standard_normal(e.n), rng.standard_normal(h.n), rng.standard_normal(h.n)]
+    box = W.pec_box((30, 30), 0.25, 6)
+    eps = W.eps_r_uniform(box.n, 7)
+    src = W.ricker_sources(box, 3, 8, c0)
+    probes = W.interior_nodes(box, 4, 9)
+    outs, grads = [], []
+    for keep in (-1.0, 0.0, 0.4, 1.0):
+        sim = M.Sim(ctx, 2, 0, dt, eps0, mu0, 4e-5, hc, hv, ec, ev, compensated=True)
+        sim.set_l2_keep(keep)
+        if keep < 0:
+            assert sim.l2_keep == 1.0  # a 1600 + 1600 node problem: its streams fit in the L2
+        else:
+            assert sim.l2_keep == pytest.approx(keep)
+        for c, v in zip((M.MFD_EZ, M.MFD_HX, M.MFD_HY), f):
+            sim.set_field(c, v)
+        sim.step(40)
+        col = _colloc(ctx, box, -4e-3, prec=0)
+        col.set_l2_keep(keep)
+        col.set_materials(eps, box.pec)
+        col.set_sources(src.node, src.amp, src.f0, src.t0)
+        col.set_probes(probes, 60)
+        col.step(30)
+        outs.append([sim.get_field(c) for c in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)] +
+                    [col.get_field(c) for c in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)])
+        col.set_field(M.MFD_EZ, np.zeros(box.n))
+        col.set_field(M.MFD_HX, np.zeros(box.n))
+        col.set_field(M.MFD_HY, np.zeros(box.n))
+        col.set_probes(probes, 60)
+        grads.append(col.grad(60, 0, len(src.node)))
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
+    for J, ge, ga in grads[1:]:
+        assert J == grads[0][0] and np.array_equal(ge, grads[0][1]) and np.array_equal(ga, grads[0][2])
+    with pytest.raises(M.MfdError):
+        sim.set_l2_keep(1.5)
