@@ -103,6 +103,17 @@ def algorithmic_bytes(n, nhv, s):
     return h, e
 
 
+def colloc_bytes(n, nhv, s):
+    """Compulsory bytes per node of each half step of the collocated 2D layout (one shared
+    index row of max(n, N_h) int32 entries, s bytes per real). H pass: the whole row, curl
+    weights 2 n s and HV weights N_h s, the node's {Ez, Hx, Hy, ce} block read and its
+    {E*, Hx', Hy', ce} block written (neighbour gathers of the same array counted once).
+    E pass: the first n entries of the row, 2 n s of curl weights, one block read, one written."""
+    h = 4 * max(n, nhv) + s * (2 * n + nhv) + 8 * s
+    e = 4 * n + s * 2 * n + 8 * s
+    return h, e
+
+
 def build_weights(M, ctx, e, h):
     """Node sets, kNN stencils and FP64 weights of the staggered workload (setup, timed apart)."""
     n, k, m, alpha = (PARAMS[x] for x in ("n", "k", "m", "alpha"))
@@ -1043,6 +1054,10 @@ def adjoint(M, ctx, steps=C5["steps"], every=C5["checkpoint_every"], l2_keep=Non
     t1.record(stream)
     torch.cuda.synchronize()
     fwd = t0.elapsed_time(t1) / 1e3
+    peak, peak_kind = peaks()
+    n_c, n_hv = P["stencil"][0], C5["hv"]["n"]
+    node_b = sum(colloc_bytes(n_c, n_hv, 4))
+    fwd_gbs = node_b * nodes.n * steps / fwd / 1e9
     setup()
     t = time.perf_counter()
     J, ge, ga = sim.grad(steps, every, len(src.node))
@@ -1057,6 +1072,12 @@ def adjoint(M, ctx, steps=C5["steps"], every=C5["checkpoint_every"], l2_keep=Non
             "_gpu": small,
             "forward_value": nodes.n * 3 * steps / fwd, "unit": UNIT, "forward_ms_per_step": fwd / steps * 1e3,
             "l2_keep": sim.l2_keep,
+            "forward_roofline": {"bound": "hbm", "achieved": fwd_gbs, "peak": peak, "unit": "GB/s",
+                                 "frac": fwd_gbs / peak, "traffic": None, "peak_kind": peak_kind,
+                                 "bytes_per_node_step": node_b,
+                                 "note": "whole step (H and E passes and the source/probe launch) against the "
+                                         "collocated layout's compulsory bytes; with part of the streams kept in "
+                                         "L2 from step to step the DRAM bytes are fewer than these"},
             "gradient_s": gs, "gradient_over_forward": gs / fwd, "J": J,
             "grad_norm_eps": float(np.linalg.norm(ge)), "grad_amp": [float(x) for x in ga],
             "whole_history": {"gradient_s": gw, "gradient_over_forward": gw / fwd,

@@ -8,7 +8,12 @@ numerators), checked against values fixed outside bench.py:
   and 2640 B in FP64;
 * the 16-bit index format: 2 bytes per entry plus the two 4-byte bases a
   32-node slice carries per stream (0.5 B per node for both streams), 4
-  bytes per entry in slices that keep 32-bit entries.
+  bytes per entry in slices that keep 32-bit entries;
+* the collocated 2D step of the differentiation workload (n = 20, N_h = 31):
+  one shared row of 31 int32 indices, 2 n + N_h weights and two 16-byte node
+  blocks in the H pass, the first 20 indices, 2 n weights and two blocks in
+  the E pass: 440 + 272 = 712 B in FP32 (the cold ncu capture of the same
+  passes measured 443 and 258 B per node).
 """
 import pytest
 
@@ -36,3 +41,8 @@ def test_16_bit_format_bytes():
 
 def test_layouts_without_16_bit_streams_count_32_bit_indices():
     assert bench.format_bytes(30, 57, 4, {"h": (0, 0, 0), "e": (0, 0, 0)}) == bench.algorithmic_bytes(30, 57, 4)
+
+
+def test_collocated_step_bytes():
+    assert bench.colloc_bytes(20, 31, 4) == (440, 272)
+    assert sum(bench.colloc_bytes(20, 31, 8)) == (4 * 31 + 8 * 71 + 64) + (4 * 20 + 8 * 40 + 64)
