@@ -821,29 +821,40 @@ def batched(M, ctx, steps, peak, peak_kind, ndom=256, nrhs=16):
          "hy": bt.get_field(d, M.MFD_HY)[:, rhs_pick]} for d in pick]}
     byt = sum(ns.n * (4 * (max(n, 31) + n) + 4 * (4 * n + 31) + 10 * 4 * nrhs) for ns, n in specs)
     ach = byt * steps / el / 1e9
-    # the L1 data path: bytes the gathers deliver to registers per step (every H-pass
-    # entry brings Ez, Hx and Hy of all right-hand sides, every E-pass entry Hx and Hy)
-    # plus the stencil streams once per node, against 128 B per clock per SM
-    l1b = sum(ns.n * (max(n, 31) * 3 * 4 * nrhs + n * 2 * 4 * nrhs + 4 * (max(n, 31) + n) + 4 * (4 * n + 31))
-              for ns, n in specs)
+    # the L1 data path: bytes the gathers deliver to registers per step plus the stencil
+    # streams once per pass, against 128 B per clock per SM. Variants 0, 1: every H-pass
+    # entry of the row (L = max(n, 31)) brings Ez, Hx and Hy of all right-hand sides,
+    # every E-pass curl entry Hx and Hy; variants 2, 3 (H row's HV term in the E pass):
+    # every H-pass entry Ez, every E-pass entry of the row Hx and Hy
+    if variant < 2:
+        l1b = sum(ns.n * (max(n, 31) * 3 * 4 * nrhs + n * 2 * 4 * nrhs + 4 * (max(n, 31) + n) + 4 * (4 * n + 31))
+                  for ns, n in specs)
+        l1_basis = ("gathered field bytes delivered to registers (3 fields x R x 4 B per H-pass entry, "
+                    "2 fields x R x 4 B per E-pass curl entry) + stencil streams once per pass")
+    else:
+        l1b = sum(ns.n * (max(n, 31) * 3 * 4 * nrhs + 2 * (4 * max(n, 31) + 4 * (2 * n + 31))) for ns, n in specs)
+        l1_basis = ("gathered field bytes delivered to registers (Ez x R x 4 B per H-pass entry, "
+                    "2 fields x R x 4 B per E-pass entry of the row) + stencil streams once per pass")
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     l1_peak = sms * 128 * _sm_max_mhz() * 1e6 / 1e9
     return {"workload": f"batched {ndom} domains (squares and disks, 2k-60k nodes), {nrhs} RHS",
             "nodes": ntot, "value": upd * steps / el, "unit": UNIT, "steps": steps,
             "ms_per_step": el / steps * 1e3, "graph": bt.uses_graph, "setup_s": round(setup_s, 2),
             "autotuned": {"variant": variant,
-                          "variants": ["stream prefetch, 3 blocks of 256 per SM", "no prefetch, 4 blocks per SM"],
+                          "variants": ["stream prefetch, 3 blocks of 256 per SM", "no prefetch, 4 blocks per SM",
+                                       "stream prefetch, H-row HV term in the E pass (H*)",
+                                       "no prefetch, H-row HV term in the E pass (H*)"],
                           "ms_per_step_by_variant": [float(x) for x in variant_ms]},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "traffic": traffic_record("k_batch16", 4, byt) if nrhs == 16 else None,
+                         "traffic": traffic_record("k_batch16" if variant == 0 else f"k_batch16v{variant}", 4, byt)
+                         if nrhs == 16 else None,
                          "traffic_unit": "DRAM bytes per step (the persistent launch runs all steps)",
-                         "kernel": "k_batch<16>", "peak_kind": peak_kind,
+                         "kernel": f"k_batch<16, {variant}>", "peak_kind": peak_kind,
                          "algorithmic_bytes_per_step": byt},
             "l1_roofline": {"bound": "l1", "achieved": l1b * steps / el / 1e9, "peak": l1_peak, "unit": "GB/s",
                             "frac": l1b * steps / el / 1e9 / l1_peak, "bytes_per_step": l1b,
                             "peak_kind": f"nominal: {sms} SMs x 128 B per clock x the maximum SM clock",
-                            "basis": "gathered field bytes delivered to registers (3 fields x R x 4 B per H-pass "
-                                     "entry, 2 fields x R x 4 B per E-pass entry) + stencil streams once per node"},
+                            "basis": l1_basis},
             "_gpu": check}
 
 

@@ -455,19 +455,31 @@ mfd_status mfd_batch_step(mfd_batch* b, int64_t nsteps);
  * few seconds). limit = 0 makes any block that has to wait give up at its
  * first poll, which exercises the timeout path. */
 mfd_status mfd_batch_set_spin_limit(mfd_batch* b, uint64_t limit);
-/* Variant of the batched kernel; the step's results are bit-identical in both
- * (the same stencil sums in the same order). variant 0: every warp requests
- * the index and weight streams of the next chunk of four stencil entries while
- * it gathers the current one, three resident blocks of 256 threads per SM;
- * variant 1: each chunk's streams are loaded when it starts, and the kernel is
- * limited to the registers of four resident blocks per SM (more warps hide the
- * latency instead). MFD_ERR_ARG for another variant. */
+/* Variant of the batched kernel. Bit 0 selects the stream loads: clear, every
+ * warp requests the index and weight streams of the next chunk of four stencil
+ * entries while it gathers the current one, three resident blocks of 256
+ * threads per SM; set, each chunk's streams are loaded when it starts, and the
+ * kernel is limited to the registers of four resident blocks per SM (more warps
+ * hide the latency instead). Bit 1 selects where the hyperviscosity term of the
+ * H row of Eq. 19 is summed: clear, in the H pass, which gathers Ez, Hx and Hy
+ * over the whole index row, while the E pass gathers Hx, Hy over the curl
+ * stencil; set, in the E pass of the step before (it depends only on
+ * H^{n-1/2}, which that pass gathers for its curl): the E pass gathers Hx, Hy
+ * over the whole row and keeps H* = H + (dt/mu0) gamma D H beside the state
+ * (8 nrhs bytes per node, allocated when such a variant is first selected),
+ * and the H pass gathers only Ez, so a step gathers 3L rows of right-hand sides
+ * per node instead of 3L + 2n (L the row length, n the curl stencil). Variants
+ * with the same bit 1 give bit-identical results; the two forms agree to
+ * rounding (the HV term is added to H before the curl term instead of after).
+ * After a host write to the fields, materials or gamma, the next step of a
+ * variant 2 or 3 first computes H* of the state (one extra pass). Variants 0-3;
+ * MFD_ERR_ARG for another. */
 mfd_status mfd_batch_set_variant(mfd_batch* b, int variant);
 int mfd_batch_variant(const mfd_batch* b);
 /* Autotuner: times `reps` steps of each variant on this batch (one launch
  * each, CUDA events), keeps the fastest, and puts the fields, probe records and
  * step counter back after every trial, so the batch does not advance.
- * chosen (nullable) receives the variant, ms (nullable, 2 values) the
+ * chosen (nullable) receives the variant, ms (nullable, 4 values) the
  * milliseconds per step of each. */
 mfd_status mfd_batch_autotune(mfd_batch* b, int reps, int* chosen, double* ms);
 /* host: steps x count x nrhs FP64; *steps receives the recorded steps. */

@@ -785,8 +785,9 @@ class Batch:
         _ck(lib().mfd_batch_load_state(self.h, blob, len(blob)))
 
     def set_variant(self, variant):
-        """Variant of the batched kernel (mfd_batch_set_variant): 0 = next-chunk stream
-        prefetch, three resident blocks per SM; 1 = no prefetch, four blocks per SM."""
+        """Variant of the batched kernel (mfd_batch_set_variant): bit 0 = no next-chunk stream
+        prefetch (four resident blocks per SM instead of three); bit 1 = the H row's HV term
+        summed in the E pass of the step before (H* kept beside the state)."""
         _ck(lib().mfd_batch_set_variant(self.h, int(variant)))
 
     @property
@@ -794,10 +795,10 @@ class Batch:
         return int(lib().mfd_batch_variant(self.h))
 
     def autotune(self, reps=20):
-        """Times both variants on this batch and keeps the faster (mfd_batch_autotune):
+        """Times the four variants on this batch and keeps the fastest (mfd_batch_autotune):
         (chosen variant, ms per step of each)."""
         chosen = C.c_int(-1)
-        ms = np.zeros(2)
+        ms = np.zeros(4)
         _ck(lib().mfd_batch_autotune(self.h, int(reps), C.byref(chosen), _p(ms)))
         return chosen.value, ms
 

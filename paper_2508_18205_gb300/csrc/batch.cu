@@ -57,6 +57,7 @@ struct BArgs {
     const float4* wv;
     float* A;   // [node][3][R]: Ez, Hx, Hy
     float* B;   // [node][3][R]: E*, Hx', Hy'
+    float* Hs;  // [node][2][R]: H* = H + (dt/mu0) gamma D H of the current H (variants 2, 3)
     const float* ce;
     const float* gam;  // [domain][R]: the hyperviscosity coefficient gamma of every right-hand side
     // sources grouped by tile
@@ -262,22 +263,207 @@ __device__ void e_tile(const BArgs& a, const BTile t) {
     }
 }
 
+// Variants 2 and 3 move the hyperviscosity term of the H row (Eq. 19) one pass
+// earlier. It depends only on H^{n-1/2}, which the E pass of the step before
+// gathers anyway for its curl; so that pass gathers Hx', Hy' over the whole
+// index row (the curl stencil is its first n entries, the HV stencil its first
+// N_h), writes H* = H' + (dt/mu0) gamma D H' beside the state, and the next H
+// pass gathers only Ez (curl and the E row's HV term) and reads its own node's
+// H*. A node-step then gathers 3L field rows instead of 3L + 2n (L = max(n, N_h)).
+// The same sums in the same order; the HV term is added to H before the curl
+// term instead of after, so results agree with variants 0 and 1 to rounding.
+template <int R, bool PF>
+__device__ void h_tile_s(const BArgs& a, const BTile t) {
+    constexpr int LPN = R / 4;
+    constexpr int NPW = 32 / LPN;
+    const BDom d = a.dom[t.dom];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane / LPN, q = lane % LPN;
+    const int local = t.first + warp * NPW + g;
+    if (local >= d.n) return;
+    const int64_t slice = local / NPW;
+    const int4* ip = a.idx + d.idx0 + slice * d.ni * NPW + g;
+    const float4* px = a.wx + d.wc0 + slice * d.nc * NPW + g;
+    const float4* py = a.wy + d.wc0 + slice * d.nc * NPW + g;
+    const float4* pv = a.wv + d.wv0 + slice * d.nv * NPW + g;
+    float4 dx = {0, 0, 0, 0}, dy = dx, ve = dx;
+    const float4 z4 = {0, 0, 0, 0};
+    int4 nid = PF ? chk4(ld_stream(ip), a.ntot) : make_int4(0, 0, 0, 0);
+    float4 nwx = PF && d.nc > 0 ? ld_stream(px) : z4, nwy = PF && d.nc > 0 ? ld_stream(py) : z4;
+    float4 nwv = PF && d.nv > 0 ? ld_stream(pv) : z4;
+    for (int c = 0; c < d.ni; ++c) {
+        int4 id;
+        float4 wx, wy, wv;
+        if constexpr (PF) {
+            id = nid;
+            wx = nwx;
+            wy = nwy;
+            wv = nwv;
+            if (c + 1 < d.ni) {
+                nid = chk4(ld_stream(ip + (c + 1) * NPW), a.ntot);
+                nwx = c + 1 < d.nc ? ld_stream(px + (c + 1) * NPW) : z4;
+                nwy = c + 1 < d.nc ? ld_stream(py + (c + 1) * NPW) : z4;
+                nwv = c + 1 < d.nv ? ld_stream(pv + (c + 1) * NPW) : z4;
+            }
+        } else {
+            id = chk4(ld_stream(ip + c * NPW), a.ntot);
+            wx = c < d.nc ? ld_stream(px + c * NPW) : z4;
+            wy = c < d.nc ? ld_stream(py + c * NPW) : z4;
+            wv = c < d.nv ? ld_stream(pv + c * NPW) : z4;
+        }
+        const int ids[4] = {id.x, id.y, id.z, id.w};
+        const float wxs[4] = {wx.x, wx.y, wx.z, wx.w}, wys[4] = {wy.x, wy.y, wy.z, wy.w};
+        const float wvs[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float4 ez = ld_f4(a.A + (int64_t)ids[e] * 3 * R + 4 * q);
+            dx = f4_fma(wxs[e], ez, dx);
+            dy = f4_fma(wys[e], ez, dy);
+            ve = f4_fma(wvs[e], ez, ve);
+        }
+    }
+    const int64_t i = d.node0 + local;
+    const float cei = a.ce[i];
+    const float4 ez = ld_f4(a.A + i * 3 * R + 4 * q);
+    const float* hs = a.Hs + i * 2 * R + 4 * q;
+    const float4 hx = ld_f4(hs), hy = ld_f4(hs + R);
+    const float4 gm = ld_f4(a.gam + t.dom * R + 4 * q);
+    float4 es, hxn, hyn;
+    es.x = ez.x + cei * (gm.x * ve.x);
+    es.y = ez.y + cei * (gm.y * ve.y);
+    es.z = ez.z + cei * (gm.z * ve.z);
+    es.w = ez.w + cei * (gm.w * ve.w);
+    hxn.x = hx.x - d.ch * dy.x;
+    hxn.y = hx.y - d.ch * dy.y;
+    hxn.z = hx.z - d.ch * dy.z;
+    hxn.w = hx.w - d.ch * dy.w;
+    hyn.x = hy.x + d.ch * dx.x;
+    hyn.y = hy.y + d.ch * dx.y;
+    hyn.z = hy.z + d.ch * dx.z;
+    hyn.w = hy.w + d.ch * dx.w;
+    float* out = a.B + i * 3 * R + 4 * q;
+    st_f4(out, es);
+    st_f4(out + R, hxn);
+    st_f4(out + 2 * R, hyn);
+}
+
+// H* of one node from the gathered HV sums: H + ch gamma (D H)
+__device__ __forceinline__ float4 hstar(float4 h, float ch, float4 gm, float4 v) {
+    h.x = h.x + ch * (gm.x * v.x);
+    h.y = h.y + ch * (gm.y * v.y);
+    h.z = h.z + ch * (gm.z * v.z);
+    h.w = h.w + ch * (gm.w * v.w);
+    return h;
+}
+
+// E pass of variants 2 and 3 (WRITE_E) and the prologue that makes H* of the
+// current state (WRITE_E = false: reads A, writes Hs only)
+template <int R, bool PF, bool WRITE_E>
+__device__ void e_tile_s(const BArgs& a, const BTile t) {
+    constexpr int LPN = R / 4;
+    constexpr int NPW = 32 / LPN;
+    const BDom d = a.dom[t.dom];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane / LPN, q = lane % LPN;
+    const int local = t.first + warp * NPW + g;
+    if (local >= d.n) return;
+    const float* src = WRITE_E ? a.B : a.A;  // H' after the H pass, or the current state
+    const int64_t slice = local / NPW;
+    const int4* ip = a.idx + d.idx0 + slice * d.ni * NPW + g;
+    const float4* px = a.wx + d.wc0 + slice * d.nc * NPW + g;
+    const float4* py = a.wy + d.wc0 + slice * d.nc * NPW + g;
+    const float4* pv = a.wv + d.wv0 + slice * d.nv * NPW + g;
+    const int nch = WRITE_E ? d.ni : d.nv;
+    float4 dxhy = {0, 0, 0, 0}, dyhx = dxhy, vx = dxhy, vy = dxhy;
+    const float4 z4 = {0, 0, 0, 0};
+    int4 nid = PF ? chk4(ld_stream(ip), a.ntot) : make_int4(0, 0, 0, 0);
+    float4 nwx = PF && WRITE_E && d.nc > 0 ? ld_stream(px) : z4, nwy = PF && WRITE_E && d.nc > 0 ? ld_stream(py) : z4;
+    float4 nwv = PF && d.nv > 0 ? ld_stream(pv) : z4;
+    for (int c = 0; c < nch; ++c) {
+        int4 id;
+        float4 wx, wy, wv;
+        if constexpr (PF) {
+            id = nid;
+            wx = nwx;
+            wy = nwy;
+            wv = nwv;
+            if (c + 1 < nch) {
+                nid = chk4(ld_stream(ip + (c + 1) * NPW), a.ntot);
+                nwx = WRITE_E && c + 1 < d.nc ? ld_stream(px + (c + 1) * NPW) : z4;
+                nwy = WRITE_E && c + 1 < d.nc ? ld_stream(py + (c + 1) * NPW) : z4;
+                nwv = c + 1 < d.nv ? ld_stream(pv + (c + 1) * NPW) : z4;
+            }
+        } else {
+            id = chk4(ld_stream(ip + c * NPW), a.ntot);
+            wx = WRITE_E && c < d.nc ? ld_stream(px + c * NPW) : z4;
+            wy = WRITE_E && c < d.nc ? ld_stream(py + c * NPW) : z4;
+            wv = c < d.nv ? ld_stream(pv + c * NPW) : z4;
+        }
+        const int ids[4] = {id.x, id.y, id.z, id.w};
+        const float wxs[4] = {wx.x, wx.y, wx.z, wx.w}, wys[4] = {wy.x, wy.y, wy.z, wy.w};
+        const float wvs[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float* f = src + (int64_t)ids[e] * 3 * R + 4 * q;
+            const float4 hx = ld_f4(f + R), hy = ld_f4(f + 2 * R);
+            if constexpr (WRITE_E) {
+                dxhy = f4_fma(wxs[e], hy, dxhy);
+                dyhx = f4_fma(wys[e], hx, dyhx);
+            }
+            vx = f4_fma(wvs[e], hx, vx);
+            vy = f4_fma(wvs[e], hy, vy);
+        }
+    }
+    const int64_t i = d.node0 + local;
+    const float* me = src + i * 3 * R + 4 * q;
+    const float4 hx = ld_f4(me + R), hy = ld_f4(me + 2 * R);
+    const float4 gm = ld_f4(a.gam + t.dom * R + 4 * q);
+    float* hs = a.Hs + i * 2 * R + 4 * q;
+    st_f4(hs, hstar(hx, d.ch, gm, vx));
+    st_f4(hs + R, hstar(hy, d.ch, gm, vy));
+    if constexpr (WRITE_E) {
+        const float cei = a.ce[i];
+        const float4 es = ld_f4(me);
+        float4 ez;
+        ez.x = es.x + cei * (dxhy.x - dyhx.x);
+        ez.y = es.y + cei * (dxhy.y - dyhx.y);
+        ez.z = es.z + cei * (dxhy.z - dyhx.z);
+        ez.w = es.w + cei * (dxhy.w - dyhx.w);
+        float* out = a.A + i * 3 * R + 4 * q;
+        st_f4(out, ez);
+        st_f4(out + R, hx);
+        st_f4(out + 2 * R, hy);
+    }
+}
+
+// H* of the current state for every tile (one block per tile): run before the
+// first launch of variants 2 and 3 after the state or gamma changed on the host
+template <int R>
+__global__ void __launch_bounds__(BT_THREADS) k_bhstar(BArgs a) { e_tile_s<R, false, false>(a, a.tile[blockIdx.x]); }
+
 // variant 0: stream prefetch, three resident blocks of 256 per SM (80
-// registers); variant 1: no prefetch, four resident blocks (64 registers)
+// registers); variant 1: no prefetch, four resident blocks (64 registers);
+// variants 2 and 3: the same two with the H row's HV term in the E pass (H*)
 template <int R, int V>
-__global__ void __launch_bounds__(BT_THREADS, V ? 4 : 3) k_batch(BArgs a) {
+__global__ void __launch_bounds__(BT_THREADS, (V & 1) ? 4 : 3) k_batch(BArgs a) {
+    constexpr bool PF = (V & 1) == 0;
+    constexpr bool HS = V >= 2;
     __shared__ int64_t step0_s;
     if (threadIdx.x == 0) step0_s = *a.counter;
     __syncthreads();
     const int64_t step0 = step0_s;
     const double pi = 3.14159265358979323846;
     for (int s = 0; s < a.nsteps; ++s) {
-        for (int k = blockIdx.x; k < a.ntile; k += gridDim.x) h_tile<R, V == 0>(a, a.tile[k]);
+        for (int k = blockIdx.x; k < a.ntile; k += gridDim.x) {
+            if constexpr (HS) h_tile_s<R, PF>(a, a.tile[k]);
+            else h_tile<R, PF>(a, a.tile[k]);
+        }
         if (!grid_barrier(a.bar, a.spin_limit)) return;
         const int64_t n = step0 + s;  // step n -> n + 1
         for (int k = blockIdx.x; k < a.ntile; k += gridDim.x) {
             const BTile t = a.tile[k];
-            e_tile<R, V == 0>(a, t);
+            if constexpr (HS) e_tile_s<R, PF, true>(a, t);
+            else e_tile<R, PF>(a, t);
             __syncthreads();
             const int s0 = a.src_start[k], s1 = a.src_start[k + 1];
             if (s1 > s0) {
@@ -499,6 +685,8 @@ struct mfd_batch {
     int grid = 0;
     int tile_nodes = 64;
     int variant = 0;  // kernel variant (mfd_batch_set_variant, mfd_batch_autotune)
+    DevBuf Hs;              // H* of the current state (variants 2, 3), allocated with the first such variant
+    bool hs_valid = false;  // H* matches the state and gamma (the kernel keeps it so; host writes clear it)
     unsigned long long spin_limit = 1ull << 25;  // polls with 64 ns naps: a few seconds before giving up
     bool use_graph = true;
     cudaGraphExec_t graph = nullptr;
@@ -604,6 +792,7 @@ BArgs make_args(mfd_batch* b, int nsteps) {
     a.wv = b->wv.as<const float4>();
     a.A = b->A.as<float>();
     a.B = b->B.as<float>();
+    a.Hs = b->Hs.p ? b->Hs.as<float>() : nullptr;
     a.ce = b->ce.as<const float>();
     a.gam = b->gam.as<const float>();
     a.src_start = b->src_start.as<const int>();
@@ -627,7 +816,14 @@ BArgs make_args(mfd_batch* b, int nsteps) {
     return a;
 }
 
-template <int R> void* kernel_ptr(int variant) { return variant ? (void*)k_batch<R, 1> : (void*)k_batch<R, 0>; }
+template <int R> void* kernel_ptr(int variant) {
+    switch (variant) {
+        case 0: return (void*)k_batch<R, 0>;
+        case 1: return (void*)k_batch<R, 1>;
+        case 2: return (void*)k_batch<R, 2>;
+        default: return (void*)k_batch<R, 3>;
+    }
+}
 
 void* batch_kernel(int R, int variant) {
     switch (R) {
@@ -643,6 +839,10 @@ mfd_status set_variant(mfd_batch* b, int variant) {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(b->R, variant), BT_THREADS, 0);
     if (e != cudaSuccess || per_sm < 1) return fail(MFD_ERR_CUDA, "occupancy query failed");
+    if (variant >= 2 && !b->Hs.p) {
+        MFD_TRY(b->Hs.alloc((size_t)b->ntot * 2 * b->R * 4));
+        b->hs_valid = false;
+    }
     b->variant = variant;
     b->grid = std::min(per_sm * b->ctx->sm_count, std::max(1, b->ntile));
     if (b->graph) {
@@ -651,6 +851,28 @@ mfd_status set_variant(mfd_batch* b, int variant) {
     }
     b->graph_steps = -1;
     return MFD_OK;
+}
+
+// H* of the current state before a launch of variant 2 or 3, when the host has
+// changed the state or gamma since the last launch (one block per tile)
+cudaError_t ensure_hstar(mfd_batch* b) {
+    if (b->variant < 2) {  // the launch advances the state without H*
+        b->hs_valid = false;
+        return cudaSuccess;
+    }
+    if (b->hs_valid) return cudaSuccess;
+    BArgs a = make_args(b, 0);
+    const unsigned g = (unsigned)std::max(1, b->ntile);
+    cudaStream_t s = b->ctx->stream;
+    switch (b->R) {
+        case 4: k_bhstar<4><<<g, BT_THREADS, 0, s>>>(a); break;
+        case 8: k_bhstar<8><<<g, BT_THREADS, 0, s>>>(a); break;
+        case 16: k_bhstar<16><<<g, BT_THREADS, 0, s>>>(a); break;
+        default: k_bhstar<32><<<g, BT_THREADS, 0, s>>>(a); break;
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) b->hs_valid = true;
+    return e;
 }
 
 cudaError_t launch_batch(mfd_batch* b, int nsteps) {
@@ -820,6 +1042,7 @@ mfd_status mfd_batch_set_materials(mfd_batch* b, int dom, const double* eps_r, c
         MFD_TRY(dp.alloc(D.n));
         MFD_CUDA(cudaMemcpyAsync(dp.p, pec, D.n, cudaMemcpyHostToDevice, b->ctx->stream));
     }
+    b->hs_valid = false;
     k_bmaterials<<<(unsigned)((D.n + 255) / 256), 256, 0, b->ctx->stream>>>(
         de.as<double>(), dp.as<uint8_t>(), D.nodes->perm.as<int64_t>(), D.n, D.node0, D.dt / D.eps0, b->ce.as<float>(),
         b->A.as<float>(), b->R);
@@ -841,6 +1064,7 @@ static mfd_status batch_field_args(mfd_batch* b, int dom, int comp, int rhs, int
 static mfd_status batch_scatter(mfd_batch* b, int dom, int comp, int rhs, const double* dsrc) {
     int c, nr;
     MFD_TRY(batch_field_args(b, dom, comp, rhs, &c, &nr));
+    b->hs_valid = false;
     const BatchDomain& D = b->dom[dom];
     const int64_t tot = (int64_t)D.n * nr;
     k_bscatter<<<(unsigned)((tot + 255) / 256), 256, 0, b->ctx->stream>>>(
@@ -1004,6 +1228,7 @@ mfd_status mfd_batch_step(mfd_batch* b, int64_t nsteps) {
             b->use_graph = false;
         }
     }
+    MFD_CUDA(ensure_hstar(b));
     if (b->use_graph) MFD_CUDA(cudaGraphLaunch(b->graph, s));
     else MFD_CUDA(launch_batch(b, (int)nsteps));
     unsigned int flags[3];
@@ -1015,6 +1240,7 @@ mfd_status mfd_batch_step(mfd_batch* b, int64_t nsteps) {
         // left part way through the call (the caller sets them again)
         MFD_CUDA(cudaMemsetAsync(b->bar.p, 0, 16, s));
         MFD_CUDA(cudaStreamSynchronize(s));
+        b->hs_valid = false;
         return fail(MFD_ERR_TIMEOUT, "a grid barrier of the batched kernel timed out");
     }
     b->steps += nsteps;
@@ -1080,6 +1306,7 @@ mfd_status mfd_batch_load_state(mfd_batch* b, const void* host, size_t bytes) {
     cudaStream_t s = b->ctx->stream;
     const char* o = static_cast<const char*>(host) + sizeof(in);
     MFD_CUDA(cudaMemcpyAsync(b->A.p, o, (size_t)in.bytes[0], cudaMemcpyHostToDevice, s));
+    b->hs_valid = false;
     o += in.bytes[0];
     if (in.rec) MFD_CUDA(cudaMemcpyAsync(b->prb_buf.p, o, (size_t)in.rec * in.nprobe * in.nrhs * 4, cudaMemcpyHostToDevice, s));
     b->steps = in.steps;
@@ -1092,7 +1319,7 @@ mfd_status mfd_batch_load_state(mfd_batch* b, const void* host, size_t bytes) {
 }
 
 mfd_status mfd_batch_set_variant(mfd_batch* b, int variant) {
-    if (!b || (variant != 0 && variant != 1)) return fail(MFD_ERR_ARG, "variant must be 0 or 1");
+    if (!b || variant < 0 || variant > 3) return fail(MFD_ERR_ARG, "variant must be 0, 1, 2 or 3");
     MFD_CUDA(cudaSetDevice(b->ctx->device));
     MFD_TRY(set_variant(b, variant));
     MFD_CUDA(cudaStreamSynchronize(b->ctx->stream));
@@ -1118,6 +1345,7 @@ mfd_status mfd_batch_autotune(mfd_batch* b, int reps, int* chosen, double* ms) {
         MFD_CUDA(cudaMemcpyAsync(b->prb_buf.p, saveP.p, b->prb_buf.bytes, cudaMemcpyDeviceToDevice, s));
         MFD_CUDA(cudaMemcpyAsync(b->counter.p, &steps0, 8, cudaMemcpyHostToDevice, s));
         MFD_CUDA(cudaStreamSynchronize(s));
+        b->hs_valid = false;
         b->steps = steps0;
         return MFD_OK;
     };
@@ -1134,9 +1362,10 @@ mfd_status mfd_batch_autotune(mfd_batch* b, int reps, int* chosen, double* ms) {
     const int start_variant = b->variant;
     int best = start_variant;
     float tbest = 1e30f;
-    for (int v = 0; v < 2; ++v) {
+    for (int v = 0; v < 4; ++v) {
         MFD_TRY(set_variant(b, v));
         if (b->tables_dirty) MFD_TRY(build_tables(b));
+        MFD_CUDA(ensure_hstar(b));
         MFD_CUDA(launch_batch(b, 1));  // first launch of this kernel: loads it
         MFD_CUDA(cudaEventRecord(e0, s));
         MFD_CUDA(launch_batch(b, reps));
@@ -1203,6 +1432,7 @@ mfd_status mfd_batch_set_gamma(mfd_batch* b, int dom, const double* gamma) {
         if (!std::isfinite(gamma[r])) return fail(MFD_ERR_ARG, "gamma must be finite");
         g[r] = (float)gamma[r];
     }
+    b->hs_valid = false;  // H* carries gamma
     MFD_CUDA(cudaSetDevice(b->ctx->device));
     MFD_CUDA(cudaMemcpyAsync(b->gam.as<float>() + (size_t)dom * b->R, g.data(), b->R * 4, cudaMemcpyHostToDevice,
                              b->ctx->stream));

@@ -37,7 +37,7 @@ def _domains(ctx, specs):
     return doms, keep
 
 
-@pytest.mark.parametrize("R,variant", [(16, 0), (16, 1), (4, 0), (32, 1)])
+@pytest.mark.parametrize("R,variant", [(16, 0), (16, 1), (4, 0), (32, 1), (16, 2), (16, 3), (8, 2), (32, 3)])
 def test_batch_matches_single_rhs_oracle(R, variant):
     ctx = M.Ctx(0)
     dt, eps0, mu0, c0, eta0 = W.units(S)
@@ -92,8 +92,10 @@ def test_batch_matches_single_rhs_oracle(R, variant):
         assert np.all(got[0][ns.pec == 1] == 0)
 
 
-def test_batch_repeated_steps_continue():
-    """Two step calls of k steps equal one call of 2k steps (the step counter and sources carry on)."""
+@pytest.mark.parametrize("variant", [0, 2])
+def test_batch_repeated_steps_continue(variant):
+    """Two step calls of k steps equal one call of 2k steps (the step counter, the sources
+    and, in variant 2, H* carry on)."""
     ctx = M.Ctx(0)
     dt, eps0, mu0, c0, eta0 = W.units(S)
     specs = [(W.pec_box((20, 20), 0.25, 7), 12), (W.disk(11.0, 0.25, 8), 20)]
@@ -101,6 +103,7 @@ def test_batch_repeated_steps_continue():
     for split in (False, True):
         doms, keep = _domains(ctx, specs)
         bt = M.Batch(ctx, doms, nrhs=16)
+        bt.set_variant(variant)
         for d, (ns, n) in enumerate(specs):
             bt.set_materials(d, None, ns.pec)
             src = W.ricker_sources(ns, 16, 400 + d, c0, nrhs=16, one_per_rhs=True)
@@ -117,17 +120,19 @@ def test_batch_repeated_steps_continue():
 
 @pytest.mark.parametrize("R", [16, 8])
 def test_variants_are_bit_identical_and_autotune_leaves_the_state(R):
-    """Both kernel variants (stream prefetch with three resident blocks per SM,
-    and no prefetch with four) take every stencil sum in the same order: the
-    fields, probes and energies agree bit for bit. The autotuner times both and
-    puts the fields, probes and step count back."""
+    """Variants with and without stream prefetch (three or four resident blocks
+    per SM) take every stencil sum in the same order: within each form of the
+    H row's HV term (H pass: variants 0, 1; E pass of the step before, with H*:
+    variants 2, 3) the fields, probes and energies agree bit for bit, and the
+    two forms agree to rounding (1e-6 relative). The autotuner times all four
+    and puts the fields, probes and step count back."""
     ctx = M.Ctx(0)
     dt, eps0, mu0, c0, eta0 = W.units(S)
     specs = [(W.pec_box((26, 22), 0.25, 11), 12), (W.disk(13.0, 0.25, 12), 30), (W.pec_box((17, 17), 0.25, 13), 40),
              (W.disk(8.0, 0.25, 14), 20)]
     doms, keep = _domains(ctx, specs)
     runs = []
-    for variant in (0, 1):
+    for variant in (0, 1, 2, 3):
         bt = M.Batch(ctx, doms, nrhs=R)
         bt.set_variant(variant)
         for d, (ns, n) in enumerate(specs):
@@ -140,7 +145,7 @@ def test_variants_are_bit_identical_and_autotune_leaves_the_state(R):
             before = [bt.get_field(d, c) for d in range(len(specs)) for c in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)]
             probes_before = bt.read_probes(0)
             chosen, ms = bt.autotune(5)
-            assert chosen in (0, 1) and bt.variant == chosen and np.all(ms > 0)
+            assert chosen in (0, 1, 2, 3) and bt.variant == chosen and np.all(ms > 0) and ms.shape == (4,)
             after = [bt.get_field(d, c) for d in range(len(specs)) for c in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)]
             for x, y in zip(before, after):
                 assert np.array_equal(x, y)
@@ -149,9 +154,16 @@ def test_variants_are_bit_identical_and_autotune_leaves_the_state(R):
         bt.step(50)
         runs.append(([bt.get_field(d, c) for d in range(len(specs)) for c in (M.MFD_EZ, M.MFD_HX, M.MFD_HY)],
                      [bt.read_probes(d) for d in range(len(specs))], [bt.energy(d) for d in range(len(specs))]))
-    for a, b in zip(runs[0][0], runs[1][0]):
-        assert np.array_equal(a, b)
-    for a, b in zip(runs[0][1], runs[1][1]):
-        assert a.shape[0] == 120 and np.array_equal(a, b)
-    for a, b in zip(runs[0][2], runs[1][2]):
-        assert np.array_equal(a, b)
+    for i, j in ((0, 1), (2, 3)):
+        for a, b in zip(runs[i][0], runs[j][0]):
+            assert np.array_equal(a, b)
+        for a, b in zip(runs[i][1], runs[j][1]):
+            assert a.shape[0] == 120 and np.array_equal(a, b)
+        for a, b in zip(runs[i][2], runs[j][2]):
+            assert np.array_equal(a, b)
+    for a, b in zip(runs[0][0], runs[2][0]):
+        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(a)
+    for a, b in zip(runs[0][1], runs[2][1]):
+        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(a)
+    for a, b in zip(runs[0][2], runs[2][2]):
+        assert np.allclose(a, b, rtol=1e-6, atol=0)
