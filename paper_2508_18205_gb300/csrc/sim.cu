@@ -246,6 +246,7 @@ struct mfd_sim {
     DevBuf src_node, src_amp, src_f0, src_t0;
     int nsrc = 0;
     DevBuf probe_node, probe_buf;
+    DevBuf stage;  // FP64 staging of host field I/O (mfd_set_field / mfd_get_field), kept between calls
     int nprobe = 0;
     int64_t probe_cap = 0, probe_from = 0;
     DevBuf partial, energy_out;
@@ -636,6 +637,14 @@ mfd_status ensure_graph(mfd_sim* sim) {
     return MFD_OK;
 }
 
+// the simulation's staging buffer of at least `bytes` (grown, never shrunk): host field
+// I/O then allocates and frees nothing per call (cudaFree synchronises the device)
+mfd_status staging(mfd_sim* sim, size_t bytes, double** out) {
+    if (sim->stage.bytes < bytes) MFD_TRY(sim->stage.alloc(bytes));
+    *out = sim->stage.as<double>();
+    return MFD_OK;
+}
+
 mfd_status upload(mfd_ctx* ctx, DevBuf& dst, const void* host, size_t bytes) {
     MFD_TRY(dst.alloc(bytes));
     if (bytes) MFD_CUDA(cudaMemcpyAsync(dst.p, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
@@ -897,9 +906,10 @@ mfd_status mfd_set_field(mfd_sim* sim, int comp, int rhs, const double* host) {
     MFD_CUDA(cudaSetDevice(ctx->device));
     int64_t n = 0;
     MFD_TRY(gather_field(sim, comp, nullptr, &n));
-    DevBuf tmp;
-    MFD_TRY(upload(ctx, tmp, host, n * 8));
-    MFD_TRY(scatter_field(sim, comp, tmp.as<double>()));
+    double* d = nullptr;
+    MFD_TRY(staging(sim, (size_t)n * 8, &d));
+    MFD_CUDA(cudaMemcpyAsync(d, host, (size_t)n * 8, cudaMemcpyHostToDevice, ctx->stream));
+    MFD_TRY(scatter_field(sim, comp, d));
     MFD_CUDA(cudaStreamSynchronize(ctx->stream));
     return MFD_OK;
 }
@@ -911,10 +921,10 @@ mfd_status mfd_get_field(mfd_sim* sim, int comp, int rhs, double* host) {
     MFD_CUDA(cudaSetDevice(ctx->device));
     int64_t n = 0;
     MFD_TRY(gather_field(sim, comp, nullptr, &n));
-    DevBuf tmp;
-    MFD_TRY(tmp.alloc(n * 8));
-    MFD_TRY(gather_field(sim, comp, tmp.as<double>(), nullptr));
-    MFD_CUDA(cudaMemcpyAsync(host, tmp.p, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    double* d = nullptr;
+    MFD_TRY(staging(sim, (size_t)n * 8, &d));
+    MFD_TRY(gather_field(sim, comp, d, nullptr));
+    MFD_CUDA(cudaMemcpyAsync(host, d, (size_t)n * 8, cudaMemcpyDeviceToHost, ctx->stream));
     MFD_CUDA(cudaStreamSynchronize(ctx->stream));
     return MFD_OK;
 }
@@ -976,12 +986,19 @@ mfd_status mfd_set_probes(mfd_sim* sim, int count, const int64_t* node, int64_t 
         if (node[p] < 0 || node[p] >= sim->ne) return fail(MFD_ERR_ARG, "probe node out of range");
         dev_node[p] = sim->eset->h_inv[node[p]];
     }
-    // as in mfd_set_sources: no probes and no graph until both arrays are in place
+    // as in mfd_set_sources: no probes and no graph until both arrays are in place;
+    // arrays large enough for the new probes are kept (no allocation, no device-wide
+    // synchronisation by cudaFree)
     sim->nprobe = 0;
     sim->probe_cap = 0;
     sim->graph_ok = false;
-    MFD_TRY(upload(ctx, sim->probe_node, dev_node.data(), count * 8));
-    MFD_TRY(sim->probe_buf.alloc(std::max<int64_t>(1, capacity * count) * sim->rs));
+    const size_t node_bytes = (size_t)std::max(1, count) * 8;
+    const size_t buf_bytes = (size_t)std::max<int64_t>(1, capacity * count) * sim->rs;
+    if (sim->probe_node.bytes < node_bytes) MFD_TRY(sim->probe_node.alloc(node_bytes));
+    if (count > 0)
+        MFD_CUDA(cudaMemcpyAsync(sim->probe_node.p, dev_node.data(), (size_t)count * 8, cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    if (sim->probe_buf.bytes < buf_bytes) MFD_TRY(sim->probe_buf.alloc(buf_bytes));
     sim->nprobe = count;
     sim->probe_cap = capacity;
     sim->probe_from = sim->steps;
