@@ -905,6 +905,7 @@ def cube3d(M, ctx, steps, peak, peak_kind, nx=200):
     sim, keep, nodes, er, E0, H0, setup = _pec_cube(M, ctx, nx)
     nbar = setup["curl_nodes_mean"]  # curl entries per node (40, and 44 next to the walls)
     u0 = sim.energy()  # Eq. 20 of the initial state
+    blocks3 = sim.autotune(10)  # block sizes of the two passes, timed on this cube (the state is put back)
     # the first step from the seeded initial state, before any other step
     sim.step(1)
     rng = np.random.default_rng(12)
@@ -945,7 +946,7 @@ def cube3d(M, ctx, steps, peak, peak_kind, nx=200):
     dom_t = max(h_avg, e_avg)
     ach = dom_b / dom_t / 1e9
     return {"workload": f"cube3d-pec {nx}^3 (walls by images), n={n} (44 next to the walls), N_h={nhv}, FP32",
-            "nodes": nodes.n,
+            "autotuned_blocks": {"h_pass": blocks3[0], "e_pass": blocks3[1]}, "nodes": nodes.n,
             "value": nodes.n * 6 * steps / el, "unit": UNIT, "steps": steps, "ms_per_step": el / steps * 1e3,
             "setup_s": setup, "energy_rel_after_run": float(u_end / u0), "energy_after_steps": steps + 10,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
@@ -993,6 +994,7 @@ def cavity(M, ctx, steps=1000):
     hw = M.Weights(st, nhv, 2 * alpha + 1, 2 * alpha, M.MFD_OP_LAP_POW, alpha)
     sim = M.Sim(ctx, 2, M.MFD_FP64, dt, eps0, mu0, -c, cw, hw)
     sim.set_materials(None, nodes.pec)
+    blocks = sim.autotune(10)  # block sizes and threads per node of the two passes (the state is put back)
     ez, hx, hy = W.tm11_fields(nodes.xyz, CAV_L, c0, mu0, 0.0, -0.5 * dt)
     ez[nodes.pec == 1] = 0
     probes = W.interior_nodes(nodes, C1["probes"]["count"], C1["probes"]["seed"])
@@ -1021,7 +1023,7 @@ def cavity(M, ctx, steps=1000):
     ref = np.concatenate([ea, xa, ya])
     return {"workload": "cavity TM11, 100x100 PEC, n=12, FP64, 1000 steps", "nodes": nodes.n,
             "value": nodes.n * 3 * steps / el, "unit": UNIT, "steps": steps, "ms_per_step": el / steps * 1e3,
-            "roofline": "n/a (L2-resident, latency-bound)",
+            "roofline": "n/a (L2-resident, latency-bound)", "autotuned_blocks": {"h_pass": blocks[0], "e_pass": blocks[1]},
             "rel_l2_vs_exact_mode": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
             "_gpu": {"fields": got, "probes": sim.read_probes(), "steps": steps}}
 
