@@ -322,7 +322,8 @@ mfd_status mfd_sim_index_stats(const mfd_sim* sim, int64_t* out);
  * next and the rest stream through without evicting them or the gathered
  * fields. By default (keep < 0) the fraction is sized so that the kept lines
  * fill about 40 % of the device's L2 (1 for problems whose streams fit in
- * that, 0 below a tenth); keep in [0, 1] fixes it. The adjoint sweep sizes its
+ * that, 0 when that fraction is below 0.15: streams larger than about 2.7
+ * times the L2 gain nothing from kept lines); keep in [0, 1] fixes it. The adjoint sweep sizes its
  * own fraction from the transposed streams. The 3D kernels mark every line
  * evict_first whatever keep is (their problems are far larger than the L2).
  * Results do not depend on keep (bit-identical fields). MFD_ERR_ARG for

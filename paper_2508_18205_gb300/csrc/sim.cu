@@ -452,13 +452,15 @@ template <typename T> StencilStreams<T> streams(const PackedStencil& p, bool q16
 // the fraction of the stencil streams' cache lines marked evict_last (stream_policy):
 // the kept lines fill about 40 % of the L2 (the rest holds the fields and the lines
 // in flight; on a two-die part a line read from both dies may be held in both
-// halves of the L2, and on the 250k-node collocated problem 40 % ran 10 % faster
-// per step while 60 % and more thrashed); below a tenth nothing is kept (every
-// line evict_first)
+// halves of the L2). Measured: the 250k-node collocated problem (streams 0.8x the
+// L2) ran 10 % faster per step at that fraction while 60 % and more thrashed; the
+// 400^2 staggered problem (1.7x) 5 % faster; at 600^2 (3.7x) every kept fraction
+// was slower. So below 0.15 (streams above about 2.7 L2 sizes) nothing is kept
+// and every line is evict_first.
 float keep_for(int64_t stream_bytes, int64_t l2_bytes) {
     if (stream_bytes <= 0 || l2_bytes <= 0) return 0.0f;
     const double k = 0.4 * (double)l2_bytes / (double)stream_bytes;
-    return k >= 1.0 ? 1.0f : (k < 0.1 ? 0.0f : (float)k);
+    return k >= 1.0 ? 1.0f : (k < 0.15 ? 0.0f : (float)k);
 }
 
 // bytes of the stencil streams one step reads: the weights and the index form the kernels take
