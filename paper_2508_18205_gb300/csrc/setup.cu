@@ -557,7 +557,7 @@ mfd_status knn_build_mirror(const mfd_nodes* centres, const mfd_nodes* sources, 
 
 // ------------------------------------------------------------ weights (batched FP64 solve)
 
-constexpr int WS_THREADS = 128;  // threads per system; 256 for systems that leave room for at most two CTAs of 128 per SM
+constexpr int WS_THREADS = 128;  // threads per system; 256 for systems that leave room for at most three CTAs of 128 per SM
 constexpr int WS_MAX_K = 160;
 constexpr int WS_MAX_M = 64;
 
@@ -880,9 +880,10 @@ mfd_status weights_solve(const mfd_stencils* st, int n_use, const int32_t* d_nsz
     int per_sm = 0;
     MFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_weights<WS_THREADS>, WS_THREADS, smem));
     if (per_sm < 1) return fail(MFD_ERR_ARG, "local system does not fit in shared memory");
-    // a system so large that at most two CTAs fit on an SM gets twice the threads (more
-    // warps to cover the FP64 latency: 3D systems of 106 unknowns 9 % faster, the same weights)
-    const bool wide = per_sm <= 2;
+    // a system so large that at most three CTAs fit on an SM gets twice the threads (more
+    // warps to cover the FP64 latency: 3D systems of 106 unknowns 11 % faster, the 2D HV
+    // systems of 85 unknowns 2 %, the same weights; 512 threads were slower)
+    const bool wide = per_sm <= 3;
     if (wide) {
         MFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_weights<2 * WS_THREADS>, 2 * WS_THREADS, smem));
         if (per_sm < 1) return fail(MFD_ERR_ARG, "local system does not fit in shared memory");
