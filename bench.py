@@ -114,6 +114,18 @@ def colloc_bytes(n, nhv, s):
     return h, e
 
 
+def solve_flops(K, nout):
+    """FP64 flops of one local weight system solved by Gaussian elimination on its
+    K x (K + nout) augmented matrix (an FMA counted as two): the eliminations
+    sum_p 2 (K - 1 - p)(K + nout - 1 - p), plus nout back substitutions of K^2."""
+    return sum(2 * (K - 1 - p) * (K + nout - 1 - p) for p in range(K)) + nout * K * K
+
+
+def poly_count(m, dim=2):
+    """Monomials of total degree <= m in dim variables."""
+    return math.comb(m + dim, dim)
+
+
 def build_weights(M, ctx, e, h):
     """Node sets, kNN stencils and FP64 weights of the staggered workload (setup, timed apart)."""
     n, k, m, alpha = (PARAMS[x] for x in ("n", "k", "m", "alpha"))
@@ -537,6 +549,16 @@ def main():
     e, h = node_sets(nx)
     ctx = M.Ctx(local)
     wts, setup, nhv = build_weights(M, ctx, e, h)
+    # the batched FP64 weight solve (setup) against the FP64 FMA peak measured on this GPU:
+    # curl systems n + M_m (two right-hand sides) and HV systems N_h + M_{2 alpha} (one), per node
+    g64_peak = M.fma_peak(local)[0]
+    sys_fl = (solve_flops(PARAMS["n"] + poly_count(PARAMS["m"]), 2)
+              + solve_flops(nhv + poly_count(2 * PARAMS["alpha"]), 1)) * (e.n + h.n)
+    weights_roof = {"bound": "alu", "achieved": sys_fl / setup["weights_fp64_s"] / 1e12, "peak": g64_peak / 1e3,
+                    "unit": "TFLOP/s", "frac": sys_fl / setup["weights_fp64_s"] / 1e9 / g64_peak,
+                    "flops": sys_fl, "seconds": setup["weights_fp64_s"], "kernel": "k_weights",
+                    "peak_kind": "measured live (FP64 FMA chains, mfd_fma_peak)",
+                    "note": "elimination flops only (the PHS and monomial evaluations that assemble the systems are not counted)"}
     sim = make_sim(M, ctx, wts, prec, comp)
     if a.l2_keep is not None:
         sim.set_l2_keep(a.l2_keep)
@@ -602,7 +624,7 @@ def main():
                        "nodes_per_set": nx * nx, "layout": "staggered", "curl_stencil": PARAMS["n"],
                        "hv_stencil": nhv, "phs": PARAMS["k"], "poly_m": PARAMS["m"], "alpha": PARAMS["alpha"],
                        "courant": S, "compensated": comp, "l2_flush": f"inputs larger than L2 ({step_gb:.2f} GB/step)",
-                       "parallelism": f"replicas{world}", "setup_s": setup,
+                       "parallelism": f"replicas{world}", "setup_s": setup, "weights_roofline": weights_roof,
                        "autotuned_blocks": {"h_pass": blocks[0], "e_pass": blocks[1]},
                        "l2_keep": sim.l2_keep},
             "roofline": roof, "clocks": clocks, "gpu_launches": 3 * a.steps,

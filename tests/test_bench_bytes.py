@@ -13,7 +13,11 @@ numerators), checked against values fixed outside bench.py:
   one shared row of 31 int32 indices, 2 n + N_h weights and two 16-byte node
   blocks in the H pass, the first 20 indices, 2 n weights and two blocks in
   the E pass: 440 + 272 = 712 B in FP32 (the cold ncu capture of the same
-  passes measured 443 and 258 B per node).
+  passes measured 443 and 258 B per node);
+* the flops of one local weight system (the weight solve's roofline): the
+  elimination of a K x (K + r) augmented matrix sums 2 j (j + r) over
+  j < K, i.e. 2 [(K - 1) K (2K - 1) / 6 + r (K - 1) K / 2], plus r K^2 for
+  the back substitutions.
 """
 import pytest
 
@@ -46,3 +50,11 @@ def test_layouts_without_16_bit_streams_count_32_bit_indices():
 def test_collocated_step_bytes():
     assert bench.colloc_bytes(20, 31, 4) == (440, 272)
     assert sum(bench.colloc_bytes(20, 31, 8)) == (4 * 31 + 8 * 71 + 64) + (4 * 20 + 8 * 40 + 64)
+
+
+def test_weight_solve_flops_closed_form():
+    for K, r in ((45, 2), (85, 1), (106, 1), (62, 3)):
+        closed = 2 * ((K - 1) * K * (2 * K - 1) // 6 + r * (K - 1) * K // 2) + r * K * K
+        assert bench.solve_flops(K, r) == closed
+    assert bench.solve_flops(45, 2) == 66750
+    assert bench.poly_count(4) == 15 and bench.poly_count(6) == 28 and bench.poly_count(3, 3) == 20
