@@ -104,13 +104,14 @@ def algorithmic_bytes(n, nhv, s):
 
 
 def colloc_bytes(n, nhv, s):
-    """Compulsory bytes per node of each half step of the collocated 2D layout (one shared
-    index row of max(n, N_h) int32 entries, s bytes per real). H pass: the whole row, curl
-    weights 2 n s and HV weights N_h s, the node's {Ez, Hx, Hy, ce} block read and its
-    {E*, Hx', Hy', ce} block written (neighbour gathers of the same array counted once).
-    E pass: the first n entries of the row, 2 n s of curl weights, one block read, one written."""
-    h = 4 * max(n, nhv) + s * (2 * n + nhv) + 8 * s
-    e = 4 * n + s * 2 * n + 8 * s
+    """Algorithmic bytes per node of each half step of the collocated 2D step, as SURVEY
+    section 8(d) counts them (s bytes per real; neighbour gathers counted once). H pass:
+    the shared index row of max(n, N_h) int32 entries, curl weights 2 n s and HV weights
+    N_h s, Ez, Hx, Hy read and E*, Hx', Hy' written (6 s). E pass: the first n entries of
+    the row, 2 n s of curl weights, E* and ce read and Ez written with H' gathered (4 s).
+    (The {Ez, Hx, Hy, ce} layout moves a whole 16-byte block per node and pass: 24 B more.)"""
+    h = 4 * max(n, nhv) + s * (2 * n + nhv) + 6 * s
+    e = 4 * n + s * 2 * n + 4 * s
     return h, e
 
 
@@ -1110,9 +1111,10 @@ def adjoint(M, ctx, steps=C5["steps"], every=C5["checkpoint_every"], l2_keep=Non
             "forward_roofline": {"bound": "hbm", "achieved": fwd_gbs, "peak": peak, "unit": "GB/s",
                                  "frac": fwd_gbs / peak, "traffic": None, "peak_kind": peak_kind,
                                  "bytes_per_node_step": node_b,
-                                 "note": "whole step (H and E passes and the source/probe launch) against the "
-                                         "collocated layout's compulsory bytes; with part of the streams kept in "
-                                         "L2 from step to step the DRAM bytes are fewer than these"},
+                                 "note": "whole step (H and E passes and the source/probe launch) against "
+                                         "SURVEY 8(d)'s 688 B per node and step (204 index, 444 weight, 40 field "
+                                         "bytes); with part of the streams kept in L2 from step to step the DRAM "
+                                         "bytes are fewer than these"},
             "gradient_s": gs, "gradient_over_forward": gs / fwd, "J": J,
             "grad_norm_eps": float(np.linalg.norm(ge)), "grad_amp": [float(x) for x in ga],
             "whole_history": {"gradient_s": gw, "gradient_over_forward": gw / fwd,

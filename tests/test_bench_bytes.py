@@ -9,11 +9,10 @@ numerators), checked against values fixed outside bench.py:
 * the 16-bit index format: 2 bytes per entry plus the two 4-byte bases a
   32-node slice carries per stream (0.5 B per node for both streams), 4
   bytes per entry in slices that keep 32-bit entries;
-* the collocated 2D step of the differentiation workload (n = 20, N_h = 31):
-  one shared row of 31 int32 indices, 2 n + N_h weights and two 16-byte node
-  blocks in the H pass, the first 20 indices, 2 n weights and two blocks in
-  the E pass: 440 + 272 = 712 B in FP32 (the cold ncu capture of the same
-  passes measured 443 and 258 B per node);
+* the collocated 2D step of the differentiation workload (n = 20, N_h = 31)
+  as the survey's per-node table counts it: 4 (20 + 31) = 204 B of indices,
+  4 (2 * 20 + 31) + 4 * 2 * 20 = 444 B of weights and 10 field reals (40 B):
+  688 B in FP32;
 * the flops of one local weight system (the weight solve's roofline): the
   elimination of a K x (K + r) augmented matrix sums 2 j (j + r) over
   j < K, i.e. 2 [(K - 1) K (2K - 1) / 6 + r (K - 1) K / 2], plus r K^2 for
@@ -48,8 +47,9 @@ def test_layouts_without_16_bit_streams_count_32_bit_indices():
 
 
 def test_collocated_step_bytes():
-    assert bench.colloc_bytes(20, 31, 4) == (440, 272)
-    assert sum(bench.colloc_bytes(20, 31, 8)) == (4 * 31 + 8 * 71 + 64) + (4 * 20 + 8 * 40 + 64)
+    assert sum(bench.colloc_bytes(20, 31, 4)) == 204 + 444 + 40 == 688
+    assert bench.colloc_bytes(20, 31, 4) == (432, 256)
+    assert sum(bench.colloc_bytes(20, 31, 8)) == 204 + 2 * 444 + 80
 
 
 def test_weight_solve_flops_closed_form():
