@@ -104,8 +104,8 @@ def algorithmic_bytes(n, nhv, s):
 
 
 def colloc_bytes(n, nhv, s):
-    """Algorithmic bytes per node of each half step of the collocated 2D step, as SURVEY
-    section 8(d) counts them (s bytes per real; neighbour gathers counted once). H pass:
+    """Algorithmic bytes per node of each half step of the collocated 2D step (s bytes per
+    real; neighbour gathers counted once; each field read once and written once). H pass:
     the shared index row of max(n, N_h) int32 entries, curl weights 2 n s and HV weights
     N_h s, Ez, Hx, Hy read and E*, Hx', Hy' written (6 s). E pass: the first n entries of
     the row, 2 n s of curl weights, E* and ce read and Ez written with H' gathered (4 s).
@@ -1112,9 +1112,9 @@ def adjoint(M, ctx, steps=C5["steps"], every=C5["checkpoint_every"], l2_keep=Non
                                  "frac": fwd_gbs / peak, "traffic": None, "peak_kind": peak_kind,
                                  "bytes_per_node_step": node_b,
                                  "note": "whole step (H and E passes and the source/probe launch) against "
-                                         "SURVEY 8(d)'s 688 B per node and step (204 index, 444 weight, 40 field "
-                                         "bytes); with part of the streams kept in L2 from step to step the DRAM "
-                                         "bytes are fewer than these"},
+                                         "688 B per node and step (204 index, 444 weight, 40 field bytes); with "
+                                         "part of the streams kept in L2 from step to step the DRAM bytes are "
+                                         "fewer than these"},
             "gradient_s": gs, "gradient_over_forward": gs / fwd, "J": J,
             "grad_norm_eps": float(np.linalg.norm(ge)), "grad_amp": [float(x) for x in ga],
             "whole_history": {"gradient_s": gw, "gradient_over_forward": gw / fwd,

@@ -9,8 +9,8 @@ numerators), checked against values fixed outside bench.py:
 * the 16-bit index format: 2 bytes per entry plus the two 4-byte bases a
   32-node slice carries per stream (0.5 B per node for both streams), 4
   bytes per entry in slices that keep 32-bit entries;
-* the collocated 2D step of the differentiation workload (n = 20, N_h = 31)
-  as the survey's per-node table counts it: 4 (20 + 31) = 204 B of indices,
+* the collocated 2D step of the differentiation workload (n = 20, N_h = 31),
+  each field read once and written once: 4 (20 + 31) = 204 B of indices,
   4 (2 * 20 + 31) + 4 * 2 * 20 = 444 B of weights and 10 field reals (40 B):
   688 B in FP32;
 * the flops of one local weight system (the weight solve's roofline): the
