@@ -281,7 +281,7 @@ mfd_status mfd_set_watchdog(mfd_sim* sim, int64_t every, double max_ratio);
  * 256 by default). */
 mfd_status mfd_sim_set_blocks(mfd_sim* sim, int block_h, int block_e);
 /* Autotuner: times each half-step kernel on this problem `reps` times with
- * 128, 256 and 512 threads per block and, in the collocated 2D layout with one
+ * 64, 128, 256 and 512 threads per block and, in the collocated 2D layout with one
  * index row for both stencils, 1, 2 or 4 threads per node (each summing a
  * share of the node's stencil chunks; the shares are added across the node's
  * threads, so the choice changes the order of the stencil sums, not their

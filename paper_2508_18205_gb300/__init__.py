@@ -669,7 +669,7 @@ class Sim:
         return {"h": tuple(int(x) for x in out[:3]), "e": tuple(int(x) for x in out[3:])}
 
     def autotune(self, reps=20):
-        """Times 128/256/512 threads per block (and, collocated 2D, 1/2/4 threads
+        """Times 64/128/256/512 threads per block (and, collocated 2D, 1/2/4 threads
         per node) for each half-step kernel and keeps the fastest: the blocks."""
         ch = np.zeros(2, dtype=np.int32)
         _ck(lib().mfd_sim_autotune(self.h, int(reps), _p(ch)))

@@ -1340,7 +1340,8 @@ mfd_status mfd_sim_autotune(mfd_sim* sim, int reps, int* chosen) {
     // candidates: threads per block, and (collocated 2D rows shared by both
     // stencils) lanes per node; the sums of a node are split over its lanes, so
     // a choice changes the summation order, not the stencils
-    const int cand[3] = {128, 256, 512};
+    constexpr int NB = 4;
+    const int cand[NB] = {64, 128, 256, 512};
     const bool lanes_tuned = sim->layout == COLLOC2D && sim->hp.idx_v.p == nullptr;
     const int lcand[3] = {1, 2, 4};
     const int nl = lanes_tuned ? 3 : 1;
@@ -1350,11 +1351,11 @@ mfd_status mfd_sim_autotune(mfd_sim* sim, int reps, int* chosen) {
     mfd_status st = MFD_OK;
     for (int pass = 0; pass < 2 && st == MFD_OK; ++pass) {
         float tbest = 1e30f;
-        for (int c = 0; c < 3 * nl && st == MFD_OK; ++c) {
+        for (int c = 0; c < NB * nl && st == MFD_OK; ++c) {
             int blk[2] = {best[0], best[1]};
             int lan[2] = {bestl[0], bestl[1]};
-            blk[pass] = cand[c % 3];
-            if (lanes_tuned) lan[pass] = lcand[c / 3];
+            blk[pass] = cand[c % NB];
+            if (lanes_tuned) lan[pass] = lcand[c / NB];
             cudaError_t e = cudaSuccess;
             auto launch = [&]() {
                 if (sim->layout == COLLOC3D) {

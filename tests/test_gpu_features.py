@@ -50,7 +50,7 @@ def test_autotune_keeps_state_and_blocks_do_not_change_results():
             sim.set_field(c, v)
         if blocks == "tune":
             ch = sim.autotune(5)
-            assert all(b in (128, 256, 512) for b in ch)
+            assert all(b in (64, 128, 256, 512) for b in ch)
             assert sim.steps == 0
             assert np.array_equal(sim.get_field(M.MFD_EZ), f[0].astype(np.float32).astype(np.float64))
         else:
@@ -204,7 +204,7 @@ def test_lanes_per_node_match_the_oracle(prec, tol):
             sim.autotune(3)
             assert sim.steps == 0
             blocks, ln = sim.launch_config()
-            assert all(x in (1, 2, 4) for x in ln) and all(b in (128, 256, 512) for b in blocks)
+            assert all(x in (1, 2, 4) for x in ln) and all(b in (64, 128, 256, 512) for b in blocks)
         else:
             sim.set_lanes(*lanes)
             assert sim.launch_config()[1] == lanes
